@@ -1,0 +1,1550 @@
+// ============================================================================
+// ORACLE -- test infrastructure only.
+//
+// A plain, slow, FP64 CPU implementation of the fixed-mesh (Eulerian)
+// ADER-CWENO finite-volume step of Dumbser, Boscheri, Semplice & Russo,
+// "Central WENO schemes on unstructured meshes" (arXiv 1612.09335).
+// It is used only by tests/, by the smoke check and by the CPU-baseline /
+// reference arm of bench.py.  The product (the CUDA path) never calls it,
+// links it or includes it, and it shares no code with the product.
+//
+// Representation: polynomials are kept as sparse lists of monomials in the
+// reference coordinates (xi, eta, zeta, tau) and integrated exactly with the
+// closed form  int_{T_E} xi^a eta^b zeta^c = a! b! c! / (a+b+c+d)!.
+// The product path uses an orthonormal Dubiner basis and numerical
+// quadrature instead; every quantity compared between the two is a value
+// (basis independent), never a coefficient.
+//
+// Paper passages followed (section / equation labels of the paper):
+//   affine map                           Sec. 2, Eq. (xietaTransf)
+//   cell averages                        Eq. (cellaverage)
+//   central stencil, recursive fill      Sec. 2.1, Eq. (stencil)
+//   constrained least squares P_opt      Eq. (CWENO:Popt), (recpolydef)
+//   sectorial stencils and P_s           Sec. 2.1 (cone rule), Eq. (CWENO:Ps)
+//   P_0 and linear weights               Eq. (CWENO:P0), lambda_0=1e5, lambda_s=1
+//   nonlinear weights, indicators        Eq. (CWENO:Prec), (weights), (weights2),
+//                                        oscillation matrix Sigma_lm
+//   time step                            Eq. (timestep)
+//   space-time Galerkin predictor        Sec. 2.2, Eqs. (PDExi2)-(CGfinal)
+//   one-step finite volume update        Sec. 2.4, Eq. (PDEfinal), Eulerian case
+//   Rusanov flux                         Eq. (rusanov)
+//   Euler equations / EOS                Eqs. (eulerTerms), (eos)
+//   ideal MHD with GLM cleaning          Eqs. (MHDTerms), (MHDeos)
+//
+// Readings where the paper is silent (documented in the design notes):
+//   * stencil fill = face-neighbour BFS by layers, candidates of a layer ranked
+//     by distance of the (minimum-image) barycentre, then by its coordinates;
+//   * sector s = first d cells of that ranked BFS sequence (extended by two
+//     layers beyond the central stencil) whose barycentre has strictly positive
+//     barycentric coordinates for every vertex except s; else the sector is
+//     dropped and the linear weights are renormalised over the kept ones;
+//   * lambda_0 = 1e5, lambda_s = 1 normalised to sum 1;
+//   * predictor nodes = equispaced principal lattice of the (d+1)-simplex
+//     {xi >= 0, sum(xi) + tau <= 1} with step 1/M; test functions = nodal
+//     functions of the tau > 0 nodes; M+1 Picard iterations from w(xi);
+//   * Rusanov s_max per quadrature point, max over both sides;
+//   * MHD EOS p = (gamma-1)(rho E - rho|v|^2/2 - |B|^2/(8 pi)).
+// ============================================================================
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+namespace {
+
+// ---------------------------------------------------------------- polynomials
+struct Term {
+  int e[4];
+  double c;
+};
+typedef std::vector<Term> Poly;
+
+double factorial(int n) {
+  double f = 1.0;
+  for (int k = 2; k <= n; ++k) f *= k;
+  return f;
+}
+
+bool exp_less(const Term& a, const Term& b) {
+  for (int k = 0; k < 4; ++k)
+    if (a.e[k] != b.e[k]) return a.e[k] < b.e[k];
+  return false;
+}
+
+bool exp_equal(const Term& a, const Term& b) {
+  for (int k = 0; k < 4; ++k)
+    if (a.e[k] != b.e[k]) return false;
+  return true;
+}
+
+// Merge equal monomials, drop exact zeros.
+Poly normalise(Poly p) {
+  std::sort(p.begin(), p.end(), exp_less);
+  Poly out;
+  for (const Term& t : p) {
+    if (!out.empty() && exp_equal(out.back(), t))
+      out.back().c += t.c;
+    else
+      out.push_back(t);
+  }
+  Poly res;
+  for (const Term& t : out)
+    if (t.c != 0.0) res.push_back(t);
+  return res;
+}
+
+Term monomial(int a, int b, int c, int t, double coef) {
+  Term x;
+  x.e[0] = a;
+  x.e[1] = b;
+  x.e[2] = c;
+  x.e[3] = t;
+  x.c = coef;
+  return x;
+}
+
+Poly poly_mul(const Poly& a, const Poly& b) {
+  Poly r;
+  r.reserve(a.size() * b.size());
+  for (const Term& x : a)
+    for (const Term& y : b) {
+      Term z;
+      for (int k = 0; k < 4; ++k) z.e[k] = x.e[k] + y.e[k];
+      z.c = x.c * y.c;
+      r.push_back(z);
+    }
+  return normalise(r);
+}
+
+Poly poly_axpy(double alpha, const Poly& a, double beta, const Poly& b) {
+  Poly r;
+  for (const Term& x : a) {
+    Term z = x;
+    z.c *= alpha;
+    r.push_back(z);
+  }
+  for (const Term& x : b) {
+    Term z = x;
+    z.c *= beta;
+    r.push_back(z);
+  }
+  return normalise(r);
+}
+
+Poly poly_deriv(const Poly& p, int var) {
+  Poly r;
+  for (const Term& x : p) {
+    if (x.e[var] == 0) continue;
+    Term z = x;
+    z.c *= x.e[var];
+    z.e[var] -= 1;
+    r.push_back(z);
+  }
+  return normalise(r);
+}
+
+double poly_eval(const Poly& p, const double* x /* 4 coordinates */) {
+  double s = 0.0;
+  for (const Term& t : p) {
+    double v = t.c;
+    for (int k = 0; k < 4; ++k)
+      for (int q = 0; q < t.e[k]; ++q) v *= x[k];
+    s += v;
+  }
+  return s;
+}
+
+// Exact integral over the unit d-simplex of xi^a eta^b (zeta^c).
+double simplex_integral(int d, const int* e) {
+  double num = 1.0;
+  int tot = 0;
+  for (int k = 0; k < d; ++k) {
+    num *= factorial(e[k]);
+    tot += e[k];
+  }
+  return num / factorial(tot + d);
+}
+
+// Exact integral of a polynomial over T_E (spatial variables 0..d-1, no tau).
+double integrate_simplex(const Poly& p, int d) {
+  double s = 0.0;
+  for (const Term& t : p) s += t.c * simplex_integral(d, t.e);
+  return s;
+}
+
+// Exact integral over the space-time element T_E x [0,1]; tau is variable 3.
+double integrate_prism(const Poly& p, int d) {
+  double s = 0.0;
+  for (const Term& t : p) s += t.c * simplex_integral(d, t.e) / (t.e[3] + 1.0);
+  return s;
+}
+
+// p(A + B u): substitute xi_k = A[k] + sum_m B[k][m] u_m for the d spatial
+// variables (tau untouched).
+Poly poly_compose_affine(const Poly& p, int d, const double* A, const double B[3][3]) {
+  std::vector<Poly> lin(d);
+  for (int k = 0; k < d; ++k) {
+    Poly l;
+    l.push_back(monomial(0, 0, 0, 0, A[k]));
+    for (int m = 0; m < d; ++m) {
+      int e[4] = {0, 0, 0, 0};
+      e[m] = 1;
+      l.push_back(monomial(e[0], e[1], e[2], e[3], B[k][m]));
+    }
+    lin[k] = normalise(l);
+  }
+  Poly r;
+  for (const Term& t : p) {
+    Poly prod;
+    prod.push_back(monomial(0, 0, 0, t.e[3], t.c));
+    for (int k = 0; k < d; ++k)
+      for (int q = 0; q < t.e[k]; ++q) prod = poly_mul(prod, lin[k]);
+    r.insert(r.end(), prod.begin(), prod.end());
+  }
+  return normalise(r);
+}
+
+// Monomial exponents of total degree <= M in nvar variables (graded order).
+std::vector<std::array<int, 4>> monomial_list(int nvar, int M) {
+  std::vector<std::array<int, 4>> out;
+  for (int deg = 0; deg <= M; ++deg) {
+    if (nvar == 2) {
+      for (int b = 0; b <= deg; ++b) out.push_back({deg - b, b, 0, 0});
+    } else if (nvar == 3) {
+      for (int c = 0; c <= deg; ++c)
+        for (int b = 0; b <= deg - c; ++b) out.push_back({deg - b - c, b, c, 0});
+    } else {
+      for (int t = 0; t <= deg; ++t)
+        for (int c = 0; c <= deg - t; ++c)
+          for (int b = 0; b <= deg - t - c; ++b) out.push_back({deg - b - c - t, b, c, t});
+    }
+  }
+  return out;
+}
+
+// Number of coefficients of P_M in d variables, Eq. (cwenoM).
+int Mcal(int M, int d) {
+  double p = 1.0;
+  for (int l = 1; l <= d; ++l) p *= (M + l);
+  return (int)std::lround(p / factorial(d));
+}
+
+// ------------------------------------------------------------ linear algebra
+// Gaussian elimination with partial pivoting; solves A X = B in place
+// (A n x n row-major, B n x nrhs row-major).  Returns false if singular.
+bool gauss_solve(int n, std::vector<double> A, std::vector<double>& B, int nrhs) {
+  for (int k = 0; k < n; ++k) {
+    int p = k;
+    for (int i = k + 1; i < n; ++i)
+      if (std::fabs(A[i * n + k]) > std::fabs(A[p * n + k])) p = i;
+    if (A[p * n + k] == 0.0) return false;
+    if (p != k) {
+      for (int j = 0; j < n; ++j) std::swap(A[k * n + j], A[p * n + j]);
+      for (int j = 0; j < nrhs; ++j) std::swap(B[k * nrhs + j], B[p * nrhs + j]);
+    }
+    for (int i = k + 1; i < n; ++i) {
+      double f = A[i * n + k] / A[k * n + k];
+      if (f == 0.0) continue;
+      for (int j = k; j < n; ++j) A[i * n + j] -= f * A[k * n + j];
+      for (int j = 0; j < nrhs; ++j) B[i * nrhs + j] -= f * B[k * nrhs + j];
+    }
+  }
+  for (int k = n - 1; k >= 0; --k)
+    for (int j = 0; j < nrhs; ++j) {
+      double s = B[k * nrhs + j];
+      for (int i = k + 1; i < n; ++i) s -= A[k * n + i] * B[i * nrhs + j];
+      B[k * nrhs + j] = s / A[k * n + k];
+    }
+  return true;
+}
+
+// Least squares min ||A x - b|| (A m x n, m >= n, row-major) for nrhs right
+// hand sides by Householder QR.  Returns false if rank deficient.
+bool householder_lsq(int m, int n, std::vector<double> A, std::vector<double> B, int nrhs,
+                     std::vector<double>& X) {
+  for (int k = 0; k < n; ++k) {
+    double norm = 0.0;
+    for (int i = k; i < m; ++i) norm += A[i * n + k] * A[i * n + k];
+    norm = std::sqrt(norm);
+    if (norm == 0.0) return false;
+    double alpha = A[k * n + k] > 0 ? -norm : norm;
+    std::vector<double> v(m, 0.0);
+    for (int i = k; i < m; ++i) v[i] = A[i * n + k];
+    v[k] -= alpha;
+    double vv = 0.0;
+    for (int i = k; i < m; ++i) vv += v[i] * v[i];
+    if (vv == 0.0) continue;
+    for (int j = k; j < n; ++j) {
+      double s = 0.0;
+      for (int i = k; i < m; ++i) s += v[i] * A[i * n + j];
+      s = 2.0 * s / vv;
+      for (int i = k; i < m; ++i) A[i * n + j] -= s * v[i];
+    }
+    for (int j = 0; j < nrhs; ++j) {
+      double s = 0.0;
+      for (int i = k; i < m; ++i) s += v[i] * B[i * nrhs + j];
+      s = 2.0 * s / vv;
+      for (int i = k; i < m; ++i) B[i * nrhs + j] -= s * v[i];
+    }
+  }
+  double dmax = 0.0;
+  for (int k = 0; k < n; ++k) dmax = std::max(dmax, std::fabs(A[k * n + k]));
+  for (int k = 0; k < n; ++k)
+    if (std::fabs(A[k * n + k]) <= 1e-13 * dmax) return false;
+  X.assign((size_t)n * nrhs, 0.0);
+  for (int k = n - 1; k >= 0; --k)
+    for (int j = 0; j < nrhs; ++j) {
+      double s = B[k * nrhs + j];
+      for (int i = k + 1; i < n; ++i) s -= A[k * n + i] * X[i * nrhs + j];
+      X[k * nrhs + j] = s / A[k * n + k];
+    }
+  return true;
+}
+
+double det3(const double J[3][3], int d) {
+  if (d == 2) return J[0][0] * J[1][1] - J[0][1] * J[1][0];
+  return J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+         J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+         J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+}
+
+void inv3(const double J[3][3], int d, double Ji[3][3]) {
+  double det = det3(J, d);
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) Ji[a][b] = 0.0;
+  if (d == 2) {
+    Ji[0][0] = J[1][1] / det;
+    Ji[0][1] = -J[0][1] / det;
+    Ji[1][0] = -J[1][0] / det;
+    Ji[1][1] = J[0][0] / det;
+    return;
+  }
+  Ji[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / det;
+  Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+  Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+  Ji[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / det;
+  Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+  Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+  Ji[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / det;
+  Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+  Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+}
+
+// ------------------------------------------------------------ Gauss rules
+// Legendre polynomial P_n and derivative at x by the three-term recurrence.
+void legendre(int n, double x, double& p, double& dp) {
+  double p0 = 1.0, p1 = x;
+  if (n == 0) {
+    p = 1.0;
+    dp = 0.0;
+    return;
+  }
+  for (int k = 2; k <= n; ++k) {
+    double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+    p0 = p1;
+    p1 = p2;
+  }
+  p = p1;
+  dp = n * (x * p1 - p0) / (x * x - 1.0);
+}
+
+// n-point Gauss-Legendre rule on [0,1], weights summing to 1.
+void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(pi * (i + 0.75) / (n + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double p, dp;
+      legendre(n, z, p, dp);
+      double dz = p / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    double p, dp;
+    legendre(n, z, p, dp);
+    x[n - 1 - i] = 0.5 * (z + 1.0);
+    w[n - 1 - i] = 1.0 / ((1.0 - z * z) * dp * dp);  // 2/(..)/2
+  }
+}
+
+// Nodes of the degree-n polynomial orthogonal on [0,1] w.r.t. weight (1-t)
+// (Gauss-Jacobi alpha=1, beta=0), found as roots by bisection of the
+// recurrence-generated orthogonal polynomial; weights from the moment
+// equations int_0^1 (1-t) t^k dt = 1/((k+1)(k+2)), normalised to sum 1.
+void gauss_jacobi10_01(int n, std::vector<double>& x, std::vector<double>& w) {
+  // Orthogonal polynomials for weight (1-t) on [0,1] via Stieltjes with exact
+  // moments: build monic p_k by Gram-Schmidt on monomials using moment matrix.
+  auto moment = [](int k) { return 1.0 / ((k + 1.0) * (k + 2.0)); };
+  // coefficients of monic orthogonal polys in the monomial basis
+  std::vector<std::vector<double>> P;
+  P.push_back({1.0});
+  for (int k = 1; k <= n; ++k) {
+    std::vector<double> q(k + 1, 0.0);
+    q[k] = 1.0;
+    for (int j = 0; j < k; ++j) {
+      // <t^k, P_j> / <P_j, P_j>
+      double num = 0.0, den = 0.0;
+      for (size_t a = 0; a < P[j].size(); ++a) num += P[j][a] * moment(k + (int)a);
+      for (size_t a = 0; a < P[j].size(); ++a)
+        for (size_t b = 0; b < P[j].size(); ++b) den += P[j][a] * P[j][b] * moment((int)(a + b));
+      for (size_t a = 0; a < P[j].size(); ++a) q[a] -= num / den * P[j][a];
+    }
+    P.push_back(q);
+  }
+  auto evalp = [&](double t) {
+    double s = 0.0;
+    for (int a = n; a >= 0; --a) s = s * t + P[n][a];
+    return s;
+  };
+  // bracket roots on a fine grid, then bisect
+  std::vector<double> roots;
+  const int NG = 20000;
+  double t0 = 0.0, f0 = evalp(0.0);
+  for (int g = 1; g <= NG; ++g) {
+    double t1 = (double)g / NG, f1 = evalp(t1);
+    if (f0 == 0.0) roots.push_back(t0);
+    else if (f0 * f1 < 0.0) {
+      double a = t0, b = t1, fa = f0;
+      for (int it = 0; it < 200; ++it) {
+        double m = 0.5 * (a + b), fm = evalp(m);
+        if (fa * fm <= 0.0) b = m;
+        else {
+          a = m;
+          fa = fm;
+        }
+      }
+      roots.push_back(0.5 * (a + b));
+    }
+    t0 = t1;
+    f0 = f1;
+  }
+  x = roots;
+  std::vector<double> V((size_t)n * n), b(n);
+  for (int k = 0; k < n; ++k) {
+    for (int i = 0; i < n; ++i) V[k * n + i] = std::pow(x[i], k);
+    b[k] = moment(k);
+  }
+  gauss_solve(n, V, b, 1);
+  double s = 0.0;
+  for (int i = 0; i < n; ++i) s += b[i];
+  w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) w[i] = b[i] / s;
+}
+
+// ------------------------------------------------------------------ physics
+enum { PDE_EULER = 0, PDE_MHD = 1 };
+
+struct Params {
+  double eps, r, lam0, lams, gamma, ch, cfl;
+  int niter, linear_weights;
+};
+
+const double PI = 3.14159265358979323846;
+
+int nvars(int pde, int d) { return pde == PDE_EULER ? d + 2 : 9; }
+
+// Physical flux in direction m (0..d-1) for state q, Eq. (eulerTerms) or
+// Eq. (MHDTerms).  f has nvars entries.
+void flux(int pde, int d, const Params& P, const double* q, int m, double* f) {
+  if (pde == PDE_EULER) {
+    double rho = q[0];
+    double v[3] = {0, 0, 0};
+    for (int k = 0; k < d; ++k) v[k] = q[1 + k] / rho;
+    double rhoE = q[d + 1];
+    double v2 = 0.0;
+    for (int k = 0; k < d; ++k) v2 += v[k] * v[k];
+    double p = (P.gamma - 1.0) * (rhoE - 0.5 * rho * v2);  // Eq. (eos)
+    f[0] = rho * v[m];
+    for (int k = 0; k < d; ++k) f[1 + k] = rho * v[k] * v[m] + (k == m ? p : 0.0);
+    f[d + 1] = v[m] * (rhoE + p);
+    return;
+  }
+  // MHD-GLM: (rho, rho v(3), rho E, B(3), psi), Gaussian units
+  double rho = q[0];
+  double v[3] = {q[1] / rho, q[2] / rho, q[3] / rho};
+  double rhoE = q[4];
+  double B[3] = {q[5], q[6], q[7]};
+  double psi = q[8];
+  double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+  double B2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+  double p = (P.gamma - 1.0) * (rhoE - 0.5 * rho * v2 - B2 / (8.0 * PI));  // Eq. (MHDeos)
+  double pm = B2 / (8.0 * PI);
+  double vB = v[0] * B[0] + v[1] * B[1] + v[2] * B[2];
+  f[0] = rho * v[m];
+  for (int k = 0; k < 3; ++k) f[1 + k] = rho * v[k] * v[m] + (k == m ? p + pm : 0.0) - B[k] * B[m] / (4.0 * PI);
+  f[4] = v[m] * (rhoE + p + pm) - B[m] * vB / (4.0 * PI);
+  for (int k = 0; k < 3; ++k) f[5 + k] = v[m] * B[k] - B[m] * v[k] + (k == m ? psi : 0.0);
+  f[8] = P.ch * P.ch * B[m];
+}
+
+// Largest |eigenvalue| of the flux Jacobian in unit direction n.
+double max_speed_normal(int pde, int d, const Params& P, const double* q, const double* n) {
+  if (pde == PDE_EULER) {
+    double rho = q[0];
+    double vn = 0.0, v2 = 0.0;
+    for (int k = 0; k < d; ++k) {
+      double vk = q[1 + k] / rho;
+      vn += vk * n[k];
+      v2 += vk * vk;
+    }
+    double p = (P.gamma - 1.0) * (q[d + 1] - 0.5 * rho * v2);
+    double c = std::sqrt(P.gamma * p / rho);
+    return std::fabs(vn) + c;
+  }
+  double rho = q[0];
+  double v[3] = {q[1] / rho, q[2] / rho, q[3] / rho};
+  double B[3] = {q[5], q[6], q[7]};
+  double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+  double B2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+  double p = (P.gamma - 1.0) * (q[4] - 0.5 * rho * v2 - B2 / (8.0 * PI));
+  double vn = 0.0, Bn = 0.0;
+  for (int k = 0; k < d; ++k) {
+    vn += v[k] * n[k];
+    Bn += B[k] * n[k];
+  }
+  double a2 = P.gamma * p / rho;
+  double b2 = B2 / (4.0 * PI * rho);
+  double bn2 = Bn * Bn / (4.0 * PI * rho);
+  double cf2 = 0.5 * (a2 + b2 + std::sqrt(std::max(0.0, (a2 + b2) * (a2 + b2) - 4.0 * a2 * bn2)));
+  return std::max(std::fabs(vn) + std::sqrt(cf2), P.ch);
+}
+
+// Largest |eigenvalue| over all directions (for the time step).
+double max_speed(int pde, int d, const Params& P, const double* q) {
+  double rho = q[0];
+  if (pde == PDE_EULER) {
+    double v2 = 0.0;
+    for (int k = 0; k < d; ++k) v2 += (q[1 + k] / rho) * (q[1 + k] / rho);
+    double p = (P.gamma - 1.0) * (q[d + 1] - 0.5 * rho * v2);
+    return std::sqrt(v2) + std::sqrt(P.gamma * p / rho);
+  }
+  double v[3] = {q[1] / rho, q[2] / rho, q[3] / rho};
+  double B[3] = {q[5], q[6], q[7]};
+  double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+  double B2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+  double p = (P.gamma - 1.0) * (q[4] - 0.5 * rho * v2 - B2 / (8.0 * PI));
+  double a2 = P.gamma * p / rho;
+  double b2 = B2 / (4.0 * PI * rho);
+  return std::max(std::sqrt(v2) + std::sqrt(a2 + b2), P.ch);
+}
+
+// --------------------------------------------------------------------- mesh
+struct OMesh {
+  int d = 2;
+  long nv = 0, nc = 0;
+  std::vector<double> xyz;
+  std::vector<long> cells;
+  bool per[3] = {false, false, false};
+  double L[3] = {0, 0, 0};
+  std::vector<double> X;     // nc x (d+1) x 3 unwrapped vertex coordinates
+  std::vector<double> vol;   // |T_i|
+  std::vector<double> bary;  // nc x 3
+  std::vector<long> nbr;     // nc x (d+1): neighbour across face k (opposite vertex k)
+  double qscale = 1.0;       // length scale for ranking tolerances
+};
+
+double vx(const OMesh& m, long c, int k, int a) { return m.X[((size_t)c * (m.d + 1) + k) * 3 + a]; }
+
+// Shift to add to cell j's coordinates to bring it next to cell i
+// (minimum image of the barycentre difference).
+void min_image_shift(const OMesh& m, long i, long j, double* s) {
+  for (int a = 0; a < 3; ++a) {
+    s[a] = 0.0;
+    if (a < m.d && m.per[a]) {
+      double diff = m.bary[i * 3 + a] - m.bary[j * 3 + a];
+      s[a] = m.L[a] * std::nearbyint(diff / m.L[a]);
+    }
+  }
+}
+
+// Jacobian J[a][k] = X_{k+1,a} - X_{0,a} of the map (xietaTransf) of cell c.
+void cell_jacobian(const OMesh& m, long c, double J[3][3]) {
+  for (int a = 0; a < 3; ++a)
+    for (int k = 0; k < 3; ++k) J[a][k] = 0.0;
+  for (int a = 0; a < m.d; ++a)
+    for (int k = 0; k < m.d; ++k) J[a][k] = vx(m, c, k + 1, a) - vx(m, c, 0, a);
+}
+
+// Reference coordinates in cell c of a physical point x (already in c's frame).
+void to_ref(const OMesh& m, long c, const double* x, double* xi) {
+  double J[3][3], Ji[3][3];
+  cell_jacobian(m, c, J);
+  inv3(J, m.d, Ji);
+  for (int a = 0; a < 3; ++a) xi[a] = 0.0;
+  for (int a = 0; a < m.d; ++a)
+    for (int b = 0; b < m.d; ++b) xi[a] += Ji[a][b] * (x[b] - vx(m, c, 0, b));
+}
+
+bool build_mesh(OMesh& m, std::string& err) {
+  int d = m.d;
+  m.X.assign((size_t)m.nc * (d + 1) * 3, 0.0);
+  m.vol.assign(m.nc, 0.0);
+  m.bary.assign((size_t)m.nc * 3, 0.0);
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (long v = 0; v < m.nv; ++v)
+    for (int a = 0; a < d; ++a) {
+      lo[a] = std::min(lo[a], m.xyz[v * d + a]);
+      hi[a] = std::max(hi[a], m.xyz[v * d + a]);
+    }
+  m.qscale = 0.0;
+  for (int a = 0; a < d; ++a) m.qscale = std::max(m.qscale, hi[a] - lo[a]);
+  for (long c = 0; c < m.nc; ++c) {
+    for (int k = 0; k <= d; ++k) {
+      long v = m.cells[c * (d + 1) + k];
+      if (v < 0 || v >= m.nv) {
+        err = "vertex index out of range";
+        return false;
+      }
+      for (int a = 0; a < d; ++a) {
+        double x = m.xyz[v * d + a];
+        if (m.per[a] && k > 0) {
+          double x0 = m.xyz[m.cells[c * (d + 1)] * d + a];
+          x += m.L[a] * std::nearbyint((x0 - x) / m.L[a]);
+        }
+        m.X[((size_t)c * (d + 1) + k) * 3 + a] = x;
+      }
+    }
+    double J[3][3];
+    cell_jacobian(m, c, J);
+    double det = det3(J, d);
+    m.vol[c] = det / factorial(d);
+    if (!(m.vol[c] > 0.0)) {
+      err = "cell with non-positive volume";
+      return false;
+    }
+    for (int a = 0; a < d; ++a) {
+      double s = 0.0;
+      for (int k = 0; k <= d; ++k) s += vx(m, c, k, a);
+      m.bary[c * 3 + a] = s / (d + 1);
+    }
+  }
+  // face matching by sorted global vertex ids
+  struct FaceKey {
+    long v[3];
+    long cell;
+    int face;
+  };
+  std::vector<FaceKey> keys;
+  keys.reserve((size_t)m.nc * (d + 1));
+  for (long c = 0; c < m.nc; ++c)
+    for (int k = 0; k <= d; ++k) {
+      FaceKey f;
+      int n = 0;
+      for (int q = 0; q <= d; ++q)
+        if (q != k) f.v[n++] = m.cells[c * (d + 1) + q];
+      if (d == 2) f.v[2] = -1;
+      std::sort(f.v, f.v + d);
+      f.cell = c;
+      f.face = k;
+      keys.push_back(f);
+    }
+  std::sort(keys.begin(), keys.end(), [](const FaceKey& a, const FaceKey& b) {
+    for (int q = 0; q < 3; ++q)
+      if (a.v[q] != b.v[q]) return a.v[q] < b.v[q];
+    return a.cell < b.cell;
+  });
+  m.nbr.assign((size_t)m.nc * (d + 1), -1);
+  for (size_t i = 0; i < keys.size();) {
+    size_t j = i + 1;
+    while (j < keys.size() && keys[j].v[0] == keys[i].v[0] && keys[j].v[1] == keys[i].v[1] &&
+           keys[j].v[2] == keys[i].v[2])
+      ++j;
+    if (j - i > 2) {
+      err = "face shared by more than two cells";
+      return false;
+    }
+    if (j - i == 2) {
+      m.nbr[keys[i].cell * (d + 1) + keys[i].face] = keys[i + 1].cell;
+      m.nbr[keys[i + 1].cell * (d + 1) + keys[i + 1].face] = keys[i].cell;
+    }
+    i = j;
+  }
+  return true;
+}
+
+// Characteristic size h_i: incircle (2D) / insphere (3D) diameter, Eq. (timestep).
+double cell_h(const OMesh& m, long c) {
+  int d = m.d;
+  double surf = 0.0;
+  for (int k = 0; k <= d; ++k) {
+    double P[3][3];
+    int n = 0;
+    for (int q = 0; q <= d; ++q)
+      if (q != k) {
+        for (int a = 0; a < 3; ++a) P[n][a] = vx(m, c, q, a);
+        ++n;
+      }
+    if (d == 2) {
+      surf += std::hypot(P[1][0] - P[0][0], P[1][1] - P[0][1]);
+    } else {
+      double u[3], w[3];
+      for (int a = 0; a < 3; ++a) {
+        u[a] = P[1][a] - P[0][a];
+        w[a] = P[2][a] - P[0][a];
+      }
+      double cx = u[1] * w[2] - u[2] * w[1], cy = u[2] * w[0] - u[0] * w[2], cz = u[0] * w[1] - u[1] * w[0];
+      surf += 0.5 * std::sqrt(cx * cx + cy * cy + cz * cz);
+    }
+  }
+  return 2.0 * d * m.vol[c] / surf;
+}
+
+// ------------------------------------------------------------------ solver
+struct Stencil {
+  std::vector<long> S0;                  // n_e cells, S0[0] = i
+  std::vector<std::vector<long>> sector;  // d+1 sectors, each d cells or empty (dropped)
+};
+
+struct CellRec {
+  bool ready = false;
+  Stencil st;
+  // reduced LSQ matrix (rows j in S0\{i}, columns monomials e != 0): a_j[e] - a_i[e]
+  std::vector<double> Ared;
+  std::vector<double> ai;  // constraint row avg_{T_E} xi^e
+  // sectors: d x d matrix rows (xi(b_j) - xi_bary) for the chosen cells
+  std::vector<std::vector<double>> Bsec;
+};
+
+struct OSolver {
+  OMesh* mesh = nullptr;
+  int M = 2, pde = 0, nu = 4, d = 2;
+  Params P;
+  int Mc = 0, ne = 0, Lc = 0, L0 = 0;
+  std::vector<std::array<int, 4>> mono;  // spatial monomials of P_M
+  // predictor
+  std::vector<std::array<double, 4>> st_nodes;  // space-time nodes (xi..., tau in slot 3)
+  std::vector<Poly> theta;                      // nodal basis
+  std::vector<double> Ktau, Mmat;               // rows: unknown nodes (L-L0) x L columns
+  std::vector<std::array<double, 4>> lat;       // spatial lattice (M), same as tau=0 nodes
+  std::map<long, CellRec> cache;
+};
+
+// Spatial principal lattice of degree K on T_E with step 1/M.  Enumeration:
+// outer loop over zeta index, then eta index, then xi index.
+std::vector<std::array<double, 4>> spatial_lattice(int d, int K, int M) {
+  std::vector<std::array<double, 4>> out;
+  if (d == 2) {
+    for (int j = 0; j <= K; ++j)
+      for (int i = 0; i <= K - j; ++i) out.push_back({(double)i / M, (double)j / M, 0.0, 0.0});
+  } else {
+    for (int k = 0; k <= K; ++k)
+      for (int j = 0; j <= K - k; ++j)
+        for (int i = 0; i <= K - j - k; ++i) out.push_back({(double)i / M, (double)j / M, (double)k / M, 0.0});
+  }
+  if (K == 0 && M == 0) out.assign(1, {0, 0, 0, 0});
+  return out;
+}
+
+// Ranked, layer-by-layer breadth-first sequence of face neighbours of cell i
+// (cell i itself excluded), continued `extra` layers beyond the layer in which
+// `need` cells (i included) are first reached.
+std::vector<long> ranked_bfs(const OMesh& m, long i, int need, int extra, std::string& err) {
+  int d = m.d;
+  std::vector<long> seq;
+  std::vector<long> frontier(1, i);
+  std::map<long, bool> seen;
+  seen[i] = true;
+  int complete_layer = -1;
+  for (int layer = 1;; ++layer) {
+    std::vector<long> next;
+    for (long c : frontier)
+      for (int k = 0; k <= d; ++k) {
+        long j = m.nbr[c * (d + 1) + k];
+        if (j < 0 || seen.count(j)) continue;
+        seen[j] = true;
+        next.push_back(j);
+      }
+    if (next.empty()) break;
+    // rank: quantised squared distance of the minimum-image barycentre, then
+    // its coordinates (x, y, z), then the cell index
+    struct Key {
+      long long q[4];
+      long cell;
+    };
+    std::vector<Key> keys;
+    double tol = 1e-9 * m.qscale;
+    for (long j : next) {
+      double s[3];
+      min_image_shift(m, i, j, s);
+      double b[3], d2 = 0.0;
+      for (int a = 0; a < 3; ++a) b[a] = 0.0;
+      for (int a = 0; a < d; ++a) {
+        b[a] = m.bary[j * 3 + a] + s[a];
+        double diff = b[a] - m.bary[i * 3 + a];
+        d2 += diff * diff;
+      }
+      Key key;
+      key.q[0] = std::llround(d2 / (tol * m.qscale));
+      for (int a = 0; a < 3; ++a) key.q[1 + a] = std::llround(b[a] / tol);
+      key.cell = j;
+      keys.push_back(key);
+    }
+    std::sort(keys.begin(), keys.end(), [](const Key& a, const Key& b) {
+      for (int q = 0; q < 4; ++q)
+        if (a.q[q] != b.q[q]) return a.q[q] < b.q[q];
+      return a.cell < b.cell;
+    });
+    for (const Key& k : keys) seq.push_back(k.cell);
+    if (complete_layer < 0 && (long)seq.size() + 1 >= need) complete_layer = layer;
+    if (complete_layer >= 0 && layer >= complete_layer + extra) break;
+    frontier = next;
+  }
+  if ((long)seq.size() + 1 < need) err = "mesh too small for the central stencil";
+  return seq;
+}
+
+// Reference coordinates (in cell i) of the minimum-image barycentre of cell j.
+void bary_in_ref(const OMesh& m, long i, long j, double* xi) {
+  double s[3];
+  min_image_shift(m, i, j, s);
+  double b[3] = {0, 0, 0};
+  for (int a = 0; a < m.d; ++a) b[a] = m.bary[j * 3 + a] + s[a];
+  to_ref(m, i, b, xi);
+}
+
+bool prepare_cell(OSolver& S, long i, std::string& err) {
+  CellRec& R = S.cache[i];
+  if (R.ready) return true;
+  const OMesh& m = *S.mesh;
+  int d = m.d;
+  // --- stencils, Eq. (stencil) and the sector rule
+  std::vector<long> seq = ranked_bfs(m, i, S.ne, 2, err);
+  if (!err.empty()) return false;
+  R.st.S0.assign(1, i);
+  for (int k = 0; k < S.ne - 1; ++k) R.st.S0.push_back(seq[k]);
+  R.st.sector.assign(d + 1, std::vector<long>());
+  R.Bsec.assign(d + 1, std::vector<double>());
+  double xb = 1.0 / (d + 1);
+  for (int s = 0; s <= d; ++s) {
+    std::vector<long> chosen;
+    for (long j : seq) {
+      double xi[3];
+      bary_in_ref(m, i, j, xi);
+      double lam[4];
+      lam[0] = 1.0;
+      for (int a = 0; a < d; ++a) {
+        lam[a + 1] = xi[a];
+        lam[0] -= xi[a];
+      }
+      bool inside = true;
+      for (int q = 0; q <= d; ++q)
+        if (q != s && !(lam[q] > 1e-9)) inside = false;
+      if (inside) chosen.push_back(j);
+      if ((int)chosen.size() == d) break;
+    }
+    if ((int)chosen.size() < d) continue;  // dropped sector
+    std::vector<double> B((size_t)d * d);
+    for (int k = 0; k < d; ++k) {
+      double xi[3];
+      bary_in_ref(m, i, chosen[k], xi);
+      for (int a = 0; a < d; ++a) B[k * d + a] = xi[a] - xb;
+    }
+    double Bm[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int k = 0; k < d; ++k)
+      for (int a = 0; a < d; ++a) Bm[k][a] = B[k * d + a];
+    if (std::fabs(det3(Bm, d)) < 1e-8) continue;  // degenerate sector: dropped
+    R.st.sector[s] = chosen;
+    R.Bsec[s] = B;
+  }
+  // --- least-squares rows, Eq. (CWENO:Popt): averages of the monomials over
+  // each stencil cell, in the reference frame of cell i
+  int nmono = S.Mc;
+  R.ai.assign(nmono, 0.0);
+  for (int e = 0; e < nmono; ++e) {
+    int ex[4] = {S.mono[e][0], S.mono[e][1], S.mono[e][2], 0};
+    R.ai[e] = simplex_integral(d, ex) * factorial(d);  // average over T_E (|T_E| = 1/d!)
+  }
+  int nrow = S.ne - 1;
+  R.Ared.assign((size_t)nrow * (nmono - 1), 0.0);
+  for (int r = 0; r < nrow; ++r) {
+    long j = R.st.S0[r + 1];
+    double s[3];
+    min_image_shift(m, i, j, s);
+    // vertices of T_j (shifted) in the reference coordinates of T_i
+    double V[4][3];
+    for (int k = 0; k <= d; ++k) {
+      double x[3] = {0, 0, 0};
+      for (int a = 0; a < d; ++a) x[a] = vx(m, j, k, a) + s[a];
+      to_ref(m, i, x, V[k]);
+    }
+    double A[3] = {0, 0, 0}, B[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int a = 0; a < d; ++a) {
+      A[a] = V[0][a];
+      for (int q = 0; q < d; ++q) B[a][q] = V[q + 1][a] - V[0][a];
+    }
+    for (int e = 1; e < nmono; ++e) {
+      Poly p;
+      p.push_back(monomial(S.mono[e][0], S.mono[e][1], S.mono[e][2], 0, 1.0));
+      Poly pc = poly_compose_affine(p, d, A, B);
+      double avg = integrate_simplex(pc, d) * factorial(d);
+      R.Ared[(size_t)r * (nmono - 1) + (e - 1)] = avg - R.ai[e];
+    }
+  }
+  R.ready = true;
+  return true;
+}
+
+// Polynomial in the spatial monomials from coefficients (index = mono order).
+Poly poly_from_coef(const OSolver& S, const double* c) {
+  Poly p;
+  for (int e = 0; e < S.Mc; ++e) p.push_back(monomial(S.mono[e][0], S.mono[e][1], S.mono[e][2], 0, c[e]));
+  return normalise(p);
+}
+
+// Oscillation indicator: sum over multi-indices 1 <= |alpha| <= M of the
+// integral over T_E of (d^alpha p)^2.
+double sigma_of(const OSolver& S, const Poly& p) {
+  int d = S.d;
+  double s = 0.0;
+  std::vector<std::array<int, 4>> alphas = monomial_list(d, S.M);
+  for (const auto& a : alphas) {
+    int tot = a[0] + a[1] + a[2];
+    if (tot < 1) continue;
+    Poly q = p;
+    for (int k = 0; k < d; ++k)
+      for (int r = 0; r < a[k]; ++r) q = poly_deriv(q, k);
+    s += integrate_simplex(poly_mul(q, q), d);
+  }
+  return s;
+}
+
+struct RecOut {
+  std::vector<Poly> w;              // per variable
+  std::vector<Poly> popt;           // per variable
+  std::vector<double> omega;        // (d+2) x nu, dropped sectors get 0
+  std::vector<double> sigma;        // (d+2) x nu
+};
+
+bool reconstruct_cell(OSolver& S, const double* Q, long i, RecOut& out, std::string& err) {
+  if (!prepare_cell(S, i, err)) return false;
+  const CellRec& R = S.cache[i];
+  int d = S.d, nu = S.nu, nm = S.Mc;
+  int nrow = S.ne - 1;
+  out.w.assign(nu, Poly());
+  out.popt.assign(nu, Poly());
+  out.omega.assign((size_t)(d + 2) * nu, 0.0);
+  out.sigma.assign((size_t)(d + 2) * nu, 0.0);
+  // --- P_opt, Eq. (CWENO:Popt): the constraint fixes the constant coefficient,
+  // the remaining ones solve the reduced least-squares problem
+  std::vector<double> rhs((size_t)nrow * nu);
+  for (int r = 0; r < nrow; ++r)
+    for (int v = 0; v < nu; ++v) rhs[r * nu + v] = Q[R.st.S0[r + 1] * nu + v] - Q[i * nu + v];
+  std::vector<double> X;
+  if (!householder_lsq(nrow, nm - 1, R.Ared, rhs, nu, X)) {
+    err = "rank-deficient least-squares system";
+    return false;
+  }
+  std::vector<Poly> Popt(nu);
+  for (int v = 0; v < nu; ++v) {
+    std::vector<double> c(nm, 0.0);
+    double c0 = Q[i * nu + v];
+    for (int e = 1; e < nm; ++e) {
+      c[e] = X[(e - 1) * nu + v];
+      c0 -= R.ai[e] * c[e];
+    }
+    c[0] = c0;
+    Popt[v] = poly_from_coef(S, c.data());
+  }
+  out.popt = Popt;
+  // --- sectorial polynomials, Eq. (CWENO:Ps): P_s(xi) = Q_i + g.(xi - xi_b)
+  double xb = 1.0 / (d + 1);
+  std::vector<std::vector<Poly>> Ps(d + 1, std::vector<Poly>(nu));
+  std::vector<bool> kept(d + 1, false);
+  int Ns = 0;
+  for (int s = 0; s <= d; ++s) {
+    if (R.st.sector[s].empty()) continue;
+    kept[s] = true;
+    ++Ns;
+    std::vector<double> g((size_t)d * nu);
+    for (int k = 0; k < d; ++k)
+      for (int v = 0; v < nu; ++v) g[k * nu + v] = Q[R.st.sector[s][k] * nu + v] - Q[i * nu + v];
+    if (!gauss_solve(d, R.Bsec[s], g, nu)) {
+      err = "singular sector system";
+      return false;
+    }
+    for (int v = 0; v < nu; ++v) {
+      Poly p;
+      double c0 = Q[i * nu + v];
+      for (int a = 0; a < d; ++a) {
+        int e[3] = {0, 0, 0};
+        e[a] = 1;
+        p.push_back(monomial(e[0], e[1], e[2], 0, g[a * nu + v]));
+        c0 -= g[a * nu + v] * xb;
+      }
+      p.push_back(monomial(0, 0, 0, 0, c0));
+      Ps[s][v] = normalise(p);
+    }
+  }
+  // --- linear weights (normalised), Eq. (CWENO:P0)
+  double lam0 = S.P.lam0 / (S.P.lam0 + Ns * S.P.lams);
+  double lams = S.P.lams / (S.P.lam0 + Ns * S.P.lams);
+  for (int v = 0; v < nu; ++v) {
+    Poly P0 = Popt[v];
+    for (int s = 0; s <= d; ++s)
+      if (kept[s]) P0 = poly_axpy(1.0, P0, -lams, Ps[s][v]);
+    P0 = poly_axpy(1.0 / lam0, P0, 0.0, Poly());
+    // --- indicators and nonlinear weights, Eqs. (weights), (weights2)
+    std::vector<double> wt(d + 2, 0.0), sig(d + 2, 0.0);
+    sig[0] = sigma_of(S, P0);
+    wt[0] = lam0 / std::pow(sig[0] + S.P.eps, S.P.r);
+    for (int s = 0; s <= d; ++s) {
+      if (!kept[s]) continue;
+      sig[s + 1] = sigma_of(S, Ps[s][v]);
+      wt[s + 1] = lams / std::pow(sig[s + 1] + S.P.eps, S.P.r);
+    }
+    if (S.P.linear_weights) {
+      wt[0] = lam0;
+      for (int s = 0; s <= d; ++s) wt[s + 1] = kept[s] ? lams : 0.0;
+    }
+    double tot = 0.0;
+    for (double x : wt) tot += x;
+    for (double& x : wt) x /= tot;
+    // --- reconstruction polynomial, Eq. (CWENO:Prec)
+    Poly w = poly_axpy(wt[0], P0, 0.0, Poly());
+    for (int s = 0; s <= d; ++s)
+      if (kept[s]) w = poly_axpy(1.0, w, wt[s + 1], Ps[s][v]);
+    out.w[v] = w;
+    for (int s = 0; s < d + 2; ++s) {
+      out.omega[s * nu + v] = wt[s];
+      out.sigma[s * nu + v] = sig[s];
+    }
+  }
+  return true;
+}
+
+// --------------------------------------------------------------- predictor
+void init_predictor(OSolver& S) {
+  int d = S.d, M = S.M;
+  // space-time nodes: time level t (tau = t/M) carries the spatial lattice of
+  // degree M - t with step 1/M, i.e. the principal lattice of the (d+1)-simplex
+  S.st_nodes.clear();
+  for (int t = 0; t <= M; ++t) {
+    std::vector<std::array<double, 4>> sl = spatial_lattice(d, M - t, M);
+    for (auto x : sl) {
+      x[3] = (double)t / M;
+      S.st_nodes.push_back(x);
+    }
+  }
+  S.Lc = (int)S.st_nodes.size();
+  S.L0 = S.Mc;
+  S.lat = spatial_lattice(d, M, M);
+  // nodal basis: theta_l = sum_k C[k][l] m_k with V[n][k] = m_k(node_n), C = V^{-1}
+  std::vector<std::array<int, 4>> stm = monomial_list(d + 1, M);
+  for (auto& e : stm)
+    if (d == 2) {  // variables (xi, eta, tau): move the 3rd exponent into the tau slot
+      e[3] = e[2];
+      e[2] = 0;
+    }
+  int L = S.Lc;
+  std::vector<double> V((size_t)L * L), C((size_t)L * L, 0.0);
+  for (int n = 0; n < L; ++n)
+    for (int k = 0; k < L; ++k) {
+      double v = 1.0;
+      for (int a = 0; a < 4; ++a) v *= std::pow(S.st_nodes[n][a], stm[k][a]);
+      V[n * L + k] = v;
+    }
+  for (int k = 0; k < L; ++k) C[k * L + k] = 1.0;
+  gauss_solve(L, V, C, L);
+  S.theta.assign(L, Poly());
+  for (int l = 0; l < L; ++l) {
+    Poly p;
+    for (int k = 0; k < L; ++k) p.push_back(monomial(stm[k][0], stm[k][1], stm[k][2], stm[k][3], C[k * L + l]));
+    S.theta[l] = normalise(p);
+  }
+  // Galerkin matrices, Eq. (cgPDE), test functions = unknown (tau > 0) nodes
+  int L1 = L - S.L0;
+  S.Ktau.assign((size_t)L1 * L, 0.0);
+  S.Mmat.assign((size_t)L1 * L, 0.0);
+  for (int k = 0; k < L1; ++k)
+    for (int l = 0; l < L; ++l) {
+      const Poly& tk = S.theta[S.L0 + k];
+      S.Ktau[k * L + l] = integrate_prism(poly_mul(tk, poly_deriv(S.theta[l], 3)), d);
+      S.Mmat[k * L + l] = integrate_prism(poly_mul(tk, S.theta[l]), d);
+    }
+}
+
+// Space-time predictor of cell i from its reconstruction w (per variable),
+// Eq. (CGfinal).  qhat: L x nu nodal values.
+void predictor_cell(const OSolver& S, long i, const std::vector<Poly>& w, double dt, std::vector<double>& qhat) {
+  int d = S.d, nu = S.nu, L = S.Lc, L0 = S.L0, L1 = L - L0;
+  const OMesh& m = *S.mesh;
+  double J[3][3], Ji[3][3];
+  cell_jacobian(m, i, J);
+  inv3(J, d, Ji);  // Ji[e][m] = d xi_e / d x_m
+  qhat.assign((size_t)L * nu, 0.0);
+  // known DOFs (tau = 0) and initial guess (w extended constantly in time)
+  for (int l = 0; l < L; ++l) {
+    double x[4] = {S.st_nodes[l][0], S.st_nodes[l][1], S.st_nodes[l][2], 0.0};
+    for (int v = 0; v < nu; ++v) qhat[l * nu + v] = poly_eval(w[v], x);
+  }
+  // derivatives of the nodal basis at the nodes: dtheta[e][n][l]
+  std::vector<double> dth((size_t)d * L * L);
+  for (int e = 0; e < d; ++e)
+    for (int l = 0; l < L; ++l) {
+      Poly dp = poly_deriv(S.theta[l], e);
+      for (int n = 0; n < L; ++n) {
+        double x[4] = {S.st_nodes[n][0], S.st_nodes[n][1], S.st_nodes[n][2], S.st_nodes[n][3]};
+        dth[((size_t)e * L + n) * L + l] = poly_eval(dp, x);
+      }
+    }
+  std::vector<double> K1((size_t)L1 * L1);
+  for (int k = 0; k < L1; ++k)
+    for (int l = 0; l < L1; ++l) K1[k * L1 + l] = S.Ktau[k * L + L0 + l];
+  std::vector<double> F((size_t)L * d * nu), H((size_t)L * nu);
+  for (int it = 0; it < S.P.niter; ++it) {
+    // nodal fluxes F_hat, Eq. (PDEterm)
+    for (int l = 0; l < L; ++l)
+      for (int mm = 0; mm < d; ++mm) flux(S.pde, d, S.P, &qhat[l * nu], mm, &F[((size_t)l * d + mm) * nu]);
+    // H at the nodes: sum_m sum_e (d xi_e/d x_m) d F_m / d xi_e, Eq. (Hterm), Eulerian
+    for (int n = 0; n < L; ++n)
+      for (int v = 0; v < nu; ++v) {
+        double h = 0.0;
+        for (int mm = 0; mm < d; ++mm)
+          for (int e = 0; e < d; ++e) {
+            double dF = 0.0;
+            for (int l = 0; l < L; ++l) dF += dth[((size_t)e * L + n) * L + l] * F[((size_t)l * d + mm) * nu + v];
+            h += Ji[e][mm] * dF;
+          }
+        H[n * nu + v] = h;
+      }
+    // K_tau^1 q^1 = -dt M H - K_tau^0 q^0, Eq. (CGfinal)
+    std::vector<double> rhs((size_t)L1 * nu, 0.0);
+    for (int k = 0; k < L1; ++k)
+      for (int v = 0; v < nu; ++v) {
+        double s = 0.0;
+        for (int l = 0; l < L; ++l) s -= dt * S.Mmat[k * L + l] * H[l * nu + v];
+        for (int l = 0; l < L0; ++l) s -= S.Ktau[k * L + l] * qhat[l * nu + v];
+        rhs[k * nu + v] = s;
+      }
+    gauss_solve(L1, K1, rhs, nu);
+    for (int k = 0; k < L1; ++k)
+      for (int v = 0; v < nu; ++v) qhat[(L0 + k) * nu + v] = rhs[k * nu + v];
+  }
+}
+
+// Value of the predictor polynomial of a cell at reference point (xi, tau).
+void eval_qh(const OSolver& S, const std::vector<double>& qhat, const double* xt, double* q) {
+  for (int v = 0; v < S.nu; ++v) q[v] = 0.0;
+  for (int l = 0; l < S.Lc; ++l) {
+    double th = poly_eval(S.theta[l], xt);
+    for (int v = 0; v < S.nu; ++v) q[v] += th * qhat[l * S.nu + v];
+  }
+}
+
+// Face quadrature points in physical space for face k of cell i: the face
+// vertices are taken in ascending global vertex id; edge: Gauss-Legendre on
+// [A,B]; triangle: conical product x = A + s(1-t)(B-A) + t(C-A) with
+// Gauss-Legendre in s and Gauss-Jacobi(1,0) in t.  Weights sum to 1.
+void face_points(const OSolver& S, long i, int k, std::vector<std::array<double, 3>>& pts, std::vector<double>& wts,
+                 double* nrm, double& area) {
+  const OMesh& m = *S.mesh;
+  int d = m.d, M = S.M;
+  std::vector<std::pair<long, int>> fv;
+  for (int q = 0; q <= d; ++q)
+    if (q != k) fv.push_back({m.cells[i * (d + 1) + q], q});
+  std::sort(fv.begin(), fv.end());
+  double P[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  for (int r = 0; r < d; ++r)
+    for (int a = 0; a < d; ++a) P[r][a] = vx(m, i, fv[r].second, a);
+  std::vector<double> xs, ws;
+  gauss_legendre01(M + 1, xs, ws);
+  pts.clear();
+  wts.clear();
+  double out[3] = {0, 0, 0};
+  if (d == 2) {
+    for (int q = 0; q <= M; ++q) {
+      pts.push_back({P[0][0] + xs[q] * (P[1][0] - P[0][0]), P[0][1] + xs[q] * (P[1][1] - P[0][1]), 0.0});
+      wts.push_back(ws[q]);
+    }
+    double tx = P[1][0] - P[0][0], ty = P[1][1] - P[0][1];
+    area = std::hypot(tx, ty);
+    out[0] = ty / area;
+    out[1] = -tx / area;
+  } else {
+    std::vector<double> xt, wt;
+    gauss_jacobi10_01(M + 1, xt, wt);
+    for (int a = 0; a <= M; ++a)
+      for (int b = 0; b <= M; ++b) {
+        double s = xs[a], t = xt[b];
+        std::array<double, 3> x;
+        for (int c = 0; c < 3; ++c) x[c] = P[0][c] + s * (1.0 - t) * (P[1][c] - P[0][c]) + t * (P[2][c] - P[0][c]);
+        pts.push_back(x);
+        wts.push_back(ws[a] * wt[b]);
+      }
+    double u[3], w[3];
+    for (int c = 0; c < 3; ++c) {
+      u[c] = P[1][c] - P[0][c];
+      w[c] = P[2][c] - P[0][c];
+    }
+    double cr[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
+    double nn = std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+    area = 0.5 * nn;
+    for (int c = 0; c < 3; ++c) out[c] = cr[c] / nn;
+  }
+  // orient outward from cell i
+  double dot = 0.0;
+  for (int a = 0; a < d; ++a) dot += out[a] * (P[0][a] - m.bary[i * 3 + a]);
+  for (int a = 0; a < 3; ++a) nrm[a] = dot > 0 ? out[a] : -out[a];
+}
+
+}  // namespace
+
+// ============================================================================
+// C API (ctypes)
+// ============================================================================
+extern "C" {
+
+static void set_err(char* buf, int len, const std::string& s) {
+  if (buf && len > 0) {
+    std::snprintf(buf, (size_t)len, "%s", s.c_str());
+  }
+}
+
+void* orc_mesh_new(int d, int64_t nv, const double* xyz, int64_t nc, const int64_t* cells, const double* period,
+                   char* err, int errlen) {
+  OMesh* m = new OMesh();
+  m->d = d;
+  m->nv = nv;
+  m->nc = nc;
+  m->xyz.assign(xyz, xyz + nv * d);
+  m->cells.assign(cells, cells + nc * (d + 1));
+  for (int a = 0; a < d; ++a)
+    if (period && period[a] > 0) {
+      m->per[a] = true;
+      m->L[a] = period[a];
+    }
+  std::string e;
+  if (!build_mesh(*m, e)) {
+    set_err(err, errlen, e);
+    delete m;
+    return nullptr;
+  }
+  return m;
+}
+
+void orc_mesh_free(void* p) { delete (OMesh*)p; }
+
+// vol[nc], bary[nc*3], h[nc], nbr[nc*(d+1)]
+int orc_mesh_geometry(void* p, double* vol, double* bary, double* h, int64_t* nbr) {
+  OMesh* m = (OMesh*)p;
+  for (long c = 0; c < m->nc; ++c) {
+    if (vol) vol[c] = m->vol[c];
+    if (bary)
+      for (int a = 0; a < 3; ++a) bary[c * 3 + a] = m->bary[c * 3 + a];
+    if (h) h[c] = cell_h(*m, c);
+    if (nbr)
+      for (int k = 0; k <= m->d; ++k) nbr[c * (m->d + 1) + k] = m->nbr[c * (m->d + 1) + k];
+  }
+  return 0;
+}
+
+// params: eps, r, lam0, lams, gamma, ch, cfl, niter, linear_weights
+void* orc_solver_new(void* mesh, int M, int pde, const double* prm, char* err, int errlen) {
+  OMesh* m = (OMesh*)mesh;
+  if (M < 1 || M > 4 || (pde != PDE_EULER && pde != PDE_MHD)) {
+    set_err(err, errlen, "unsupported order or PDE");
+    return nullptr;
+  }
+  OSolver* S = new OSolver();
+  S->mesh = m;
+  S->M = M;
+  S->pde = pde;
+  S->d = m->d;
+  S->nu = nvars(pde, m->d);
+  S->P.eps = prm[0];
+  S->P.r = prm[1];
+  S->P.lam0 = prm[2];
+  S->P.lams = prm[3];
+  S->P.gamma = prm[4];
+  S->P.ch = prm[5];
+  S->P.cfl = prm[6];
+  S->P.niter = (int)prm[7];
+  S->P.linear_weights = (int)prm[8];
+  S->Mc = Mcal(M, m->d);
+  S->ne = m->d * S->Mc;
+  S->mono = monomial_list(m->d, M);
+  init_predictor(*S);
+  return S;
+}
+
+void orc_solver_free(void* p) { delete (OSolver*)p; }
+
+int orc_sizes(void* p, int* out /* Mc, ne, L, L0, nu */) {
+  OSolver* S = (OSolver*)p;
+  out[0] = S->Mc;
+  out[1] = S->ne;
+  out[2] = S->Lc;
+  out[3] = S->L0;
+  out[4] = S->nu;
+  return 0;
+}
+
+// Central stencil (ne ids, S0[0] = cell) and sectors ((d+1) x d ids, -1 if dropped).
+int orc_stencil(void* p, int64_t cell, int64_t* S0, int64_t* sec, char* err, int errlen) {
+  OSolver* S = (OSolver*)p;
+  std::string e;
+  if (!prepare_cell(*S, cell, e)) {
+    set_err(err, errlen, e);
+    return -1;
+  }
+  const CellRec& R = S->cache[cell];
+  for (int k = 0; k < S->ne; ++k) S0[k] = R.st.S0[k];
+  for (int s = 0; s <= S->d; ++s)
+    for (int k = 0; k < S->d; ++k) sec[s * S->d + k] = R.st.sector[s].empty() ? -1 : R.st.sector[s][k];
+  return 0;
+}
+
+// Reconstruction at the lattice nodes for cells ids[0..n) (ids NULL -> all).
+// w: n x Mc x nu, popt (nullable): n x Mc x nu, omega/sigma (nullable): n x (d+2) x nu.
+int orc_reconstruct(void* p, const double* Q, int64_t n, const int64_t* ids, double* w, double* popt, double* omega,
+                    double* sigma, char* err, int errlen) {
+  OSolver* S = (OSolver*)p;
+  long cnt = ids ? n : S->mesh->nc;
+  int nu = S->nu, Mc = S->Mc, d = S->d;
+  for (long c = 0; c < cnt; ++c) {
+    long i = ids ? ids[c] : c;
+    RecOut R;
+    std::string e;
+    if (!reconstruct_cell(*S, Q, i, R, e)) {
+      set_err(err, errlen, e);
+      return -1;
+    }
+    for (int node = 0; node < Mc; ++node) {
+      double x[4] = {S->lat[node][0], S->lat[node][1], S->lat[node][2], 0.0};
+      for (int v = 0; v < nu; ++v) {
+        if (w) w[((size_t)c * Mc + node) * nu + v] = poly_eval(R.w[v], x);
+        if (popt) popt[((size_t)c * Mc + node) * nu + v] = poly_eval(R.popt[v], x);
+      }
+    }
+    for (int s = 0; s < d + 2; ++s)
+      for (int v = 0; v < nu; ++v) {
+        if (omega) omega[((size_t)c * (d + 2) + s) * nu + v] = R.omega[s * nu + v];
+        if (sigma) sigma[((size_t)c * (d + 2) + s) * nu + v] = R.sigma[s * nu + v];
+      }
+  }
+  return 0;
+}
+
+// Predictor nodal values q_hat (n x L x nu) for cells ids (NULL -> all).
+int orc_predictor(void* p, const double* Q, double dt, int64_t n, const int64_t* ids, double* qhat, char* err,
+                  int errlen) {
+  OSolver* S = (OSolver*)p;
+  long cnt = ids ? n : S->mesh->nc;
+  int nu = S->nu, L = S->Lc;
+  for (long c = 0; c < cnt; ++c) {
+    long i = ids ? ids[c] : c;
+    RecOut R;
+    std::string e;
+    if (!reconstruct_cell(*S, Q, i, R, e)) {
+      set_err(err, errlen, e);
+      return -1;
+    }
+    std::vector<double> qh;
+    predictor_cell(*S, i, R.w, dt, qh);
+    for (int l = 0; l < L; ++l)
+      for (int v = 0; v < nu; ++v) qhat[((size_t)c * L + l) * nu + v] = qh[l * nu + v];
+  }
+  return 0;
+}
+
+// Predictor from given reconstruction values at the lattice nodes (Mc x nu).
+int orc_predictor_from_w(void* p, int64_t cell, const double* wnodal, double dt, double* qhat) {
+  OSolver* S = (OSolver*)p;
+  int nu = S->nu, Mc = S->Mc, d = S->d;
+  // interpolate: monomial coefficients from lattice values
+  std::vector<double> V((size_t)Mc * Mc), C((size_t)Mc * nu);
+  for (int n = 0; n < Mc; ++n) {
+    for (int k = 0; k < Mc; ++k) {
+      double v = 1.0;
+      for (int a = 0; a < d; ++a) v *= std::pow(S->lat[n][a], S->mono[k][a]);
+      V[n * Mc + k] = v;
+    }
+    for (int v = 0; v < nu; ++v) C[n * nu + v] = wnodal[n * nu + v];
+  }
+  gauss_solve(Mc, V, C, nu);
+  std::vector<Poly> w(nu);
+  for (int v = 0; v < nu; ++v) {
+    std::vector<double> c(Mc);
+    for (int k = 0; k < Mc; ++k) c[k] = C[k * nu + v];
+    w[v] = poly_from_coef(*S, c.data());
+  }
+  std::vector<double> qh;
+  predictor_cell(*S, cell, w, dt, qh);
+  for (size_t k = 0; k < qh.size(); ++k) qhat[k] = qh[k];
+  return 0;
+}
+
+// One ADER-CWENO step, Eq. (PDEfinal) (Eulerian), for cells ids (NULL -> all).
+// Qnew: n x nu.
+int orc_step(void* p, const double* Q, double dt, int64_t n, const int64_t* ids, double* Qnew, char* err,
+             int errlen) {
+  OSolver* S = (OSolver*)p;
+  const OMesh& m = *S->mesh;
+  int d = S->d, nu = S->nu, M = S->M;
+  long cnt = ids ? n : m.nc;
+  // predictors of every cell involved
+  std::map<long, std::vector<double>> pred;
+  for (long c = 0; c < cnt; ++c) {
+    long i = ids ? ids[c] : c;
+    std::vector<long> need(1, i);
+    for (int k = 0; k <= d; ++k)
+      if (m.nbr[i * (d + 1) + k] >= 0) need.push_back(m.nbr[i * (d + 1) + k]);
+    for (long j : need) {
+      if (pred.count(j)) continue;
+      RecOut R;
+      std::string e;
+      if (!reconstruct_cell(*S, Q, j, R, e)) {
+        set_err(err, errlen, e);
+        return -1;
+      }
+      predictor_cell(*S, j, R.w, dt, pred[j]);
+    }
+  }
+  std::vector<double> tx, tw;
+  gauss_legendre01(M + 1, tx, tw);
+  std::vector<double> qm(nu), qp(nu), fm(nu), fp(nu), fdir(nu);
+  for (long c = 0; c < cnt; ++c) {
+    long i = ids ? ids[c] : c;
+    std::vector<double> acc(nu, 0.0);
+    for (int k = 0; k <= d; ++k) {
+      long j = m.nbr[i * (d + 1) + k];
+      std::vector<std::array<double, 3>> pts;
+      std::vector<double> wts;
+      double nrm[3], area;
+      face_points(*S, i, k, pts, wts, nrm, area);
+      double sj[3] = {0, 0, 0};
+      if (j >= 0) min_image_shift(m, i, j, sj);
+      for (size_t q = 0; q < pts.size(); ++q) {
+        double xi_i[3], xi_j[3];
+        to_ref(m, i, pts[q].data(), xi_i);
+        if (j >= 0) {
+          double xj[3] = {pts[q][0] - sj[0], pts[q][1] - sj[1], pts[q][2] - sj[2]};
+          to_ref(m, j, xj, xi_j);
+        }
+        for (int t = 0; t <= M; ++t) {
+          double xt[4] = {xi_i[0], xi_i[1], xi_i[2], tx[t]};
+          eval_qh(*S, pred[i], xt, qm.data());
+          if (j >= 0) {
+            double xtj[4] = {xi_j[0], xi_j[1], xi_j[2], tx[t]};
+            eval_qh(*S, pred[j], xtj, qp.data());
+          } else {
+            qp = qm;  // transmissive boundary
+          }
+          // Rusanov flux, Eq. (rusanov), Eulerian normal (n |f| dt, 0)
+          for (int v = 0; v < nu; ++v) {
+            fm[v] = 0.0;
+            fp[v] = 0.0;
+          }
+          for (int mm = 0; mm < d; ++mm) {
+            flux(S->pde, d, S->P, qm.data(), mm, fdir.data());
+            for (int v = 0; v < nu; ++v) fm[v] += fdir[v] * nrm[mm];
+            flux(S->pde, d, S->P, qp.data(), mm, fdir.data());
+            for (int v = 0; v < nu; ++v) fp[v] += fdir[v] * nrm[mm];
+          }
+          double smax = std::max(max_speed_normal(S->pde, d, S->P, qm.data(), nrm),
+                                 max_speed_normal(S->pde, d, S->P, qp.data(), nrm));
+          for (int v = 0; v < nu; ++v) {
+            double G = 0.5 * (fm[v] + fp[v]) - 0.5 * smax * (qp[v] - qm[v]);
+            acc[v] += dt * area * wts[q] * tw[t] * G;
+          }
+        }
+      }
+    }
+    for (int v = 0; v < nu; ++v) Qnew[c * nu + v] = Q[i * nu + v] - acc[v] / m.vol[i];
+  }
+  return 0;
+}
+
+// Global time step, Eq. (timestep).
+double orc_stable_dt(void* p, const double* Q, double cfl) {
+  OSolver* S = (OSolver*)p;
+  const OMesh& m = *S->mesh;
+  double best = 1e300;
+  for (long c = 0; c < m.nc; ++c) {
+    double lam = max_speed(S->pde, S->d, S->P, &Q[c * S->nu]);
+    best = std::min(best, cell_h(m, c) / lam);
+  }
+  return cfl * best;
+}
+
+// --- building blocks exposed for pins -------------------------------------
+int orc_physical_flux(int pde, int d, const double* prm, const double* q, int m, double* f) {
+  Params P;
+  P.gamma = prm[4];
+  P.ch = prm[5];
+  flux(pde, d, P, q, m, f);
+  return 0;
+}
+
+double orc_max_speed_normal(int pde, int d, const double* prm, const double* q, const double* n) {
+  Params P;
+  P.gamma = prm[4];
+  P.ch = prm[5];
+  return max_speed_normal(pde, d, P, q, n);
+}
+
+double orc_max_speed(int pde, int d, const double* prm, const double* q) {
+  Params P;
+  P.gamma = prm[4];
+  P.ch = prm[5];
+  return max_speed(pde, d, P, q);
+}
+
+// kind 0: Gauss-Legendre on [0,1]; kind 1: Gauss-Jacobi weight (1-t) on [0,1]
+int orc_gauss_rule(int kind, int n, double* x, double* w) {
+  std::vector<double> xs, ws;
+  if (kind == 0) gauss_legendre01(n, xs, ws);
+  else gauss_jacobi10_01(n, xs, ws);
+  for (int i = 0; i < n; ++i) {
+    x[i] = xs[i];
+    w[i] = ws[i];
+  }
+  return 0;
+}
+
+// Exact integral over T_E of a monomial (nvar spatial dims).
+double orc_simplex_integral(int d, const int* e) { return simplex_integral(d, e); }
+
+// Oscillation indicator of the polynomial given by monomial coefficients in
+// the solver's monomial order (orc_monomials).
+double orc_sigma(void* p, const double* coef) {
+  OSolver* S = (OSolver*)p;
+  return sigma_of(*S, poly_from_coef(*S, coef));
+}
+
+int orc_monomials(void* p, int* exps /* Mc x 3 */) {
+  OSolver* S = (OSolver*)p;
+  for (int e = 0; e < S->Mc; ++e)
+    for (int a = 0; a < 3; ++a) exps[e * 3 + a] = S->mono[e][a];
+  return 0;
+}
+
+// Space-time nodes (L x 4: xi, eta, zeta, tau).
+int orc_st_nodes(void* p, double* out) {
+  OSolver* S = (OSolver*)p;
+  for (int l = 0; l < S->Lc; ++l)
+    for (int a = 0; a < 4; ++a) out[l * 4 + a] = S->st_nodes[l][a];
+  return 0;
+}
+
+// Face quadrature of face k of a cell (points npts x 3, weights, normal, area).
+int orc_face_points(void* p, int64_t cell, int k, double* pts, double* wts, double* nrm, double* area) {
+  OSolver* S = (OSolver*)p;
+  std::vector<std::array<double, 3>> P;
+  std::vector<double> W;
+  face_points(*S, cell, k, P, W, nrm, *area);
+  for (size_t q = 0; q < P.size(); ++q) {
+    for (int a = 0; a < 3; ++a) pts[q * 3 + a] = P[q][a];
+    wts[q] = W[q];
+  }
+  return (int)P.size();
+}
+
+}  // extern "C"
