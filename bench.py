@@ -1,0 +1,422 @@
+#!/usr/bin/env python
+"""ADER-CWENO cell-updates/s on GB300.
+
+One bench "step" is one full ADER-CWENO time step (reconstruction +
+predictor, face fluxes, conservative update and the CFL bound for the next
+step) over the whole mesh of the workload, run through the C ABI.  The
+default workload is the 2D explosion: 512 x 512 x 2 = 524,288 jittered
+triangles on [-1,1]^2 with transmissive boundaries, fourth order (P3), Euler,
+CFL 0.5, FP32-mixed arithmetic; the FP64 mode is timed beside it.
+
+Prints ONE JSON line.  `value` is whole-job cell-updates/s (N GPUs run
+independent replicas, weak scaling); `e2e` is the same metric with the
+state uploaded from and downloaded to pinned host memory every step.
+`--impl reference` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "explosion2d_p3": dict(dim=2, order=4, pde=0, n=512, desc="512x512x2 jittered triangles on [-1,1]^2, "
+                           "transmissive, circular explosion, Euler gamma 1.4, P3, CFL 0.5"),
+    "densitywave3d_p2": dict(dim=3, order=3, pde=0, n=64, desc="64^3 x 6 jittered Kuhn tetrahedra, periodic "
+                             "unit cube, density wave, Euler, P2, CFL 1/3"),
+    "orszagtang2d_p3": dict(dim=2, order=4, pde=1, n=724, desc="724x724x2 jittered triangles, periodic "
+                            "[0,2pi]^2, Orszag-Tang, MHD-GLM gamma 5/3 c_h 2, P3, CFL 0.5"),
+    "vortex2d_p2": dict(dim=2, order=3, pde=0, n=32, desc="32x32x2 jittered triangles, periodic unit "
+                        "square, isentropic vortex, Euler, P2, CFL 0.5"),
+}
+METRIC = "ADER-CWENO cell-updates/s"
+
+
+def make_inputs(name, n=None):
+    from paper_1612_09335_gb300 import workloads as wl
+    cfg = WORKLOADS[name]
+    n = cfg["n"] if n is None else n
+    if name == "explosion2d_p3":
+        return wl.explosion_2d(n)
+    if name == "densitywave3d_p2":
+        return wl.density_wave_3d(n)
+    if name == "orszagtang2d_p3":
+        return wl.orszag_tang_2d(n)
+    return wl.vortex_2d(n)
+
+
+# ------------------------------------------------------------ algorithmic counts
+def mcal(M, d):
+    return math.comb(M + d, d)
+
+
+def algorithmic(dim, order, pde, fp32=True):
+    """Algorithmic bytes and flops per unit of each kernel (a unit is a cell
+    for the reconstruction/predictor and update kernels, a face for the flux
+    kernel).  Bytes count each datum the method must move once; flops count
+    the method's arithmetic (an FMA is 2 flops)."""
+    d, M = dim, order - 1
+    nv = 9 if pde == 1 else d + 2
+    Mc, L = mcal(M, d), mcal(M, d + 1)
+    ne, L0 = d * Mc, mcal(M, d)
+    L1 = L - L0
+    r = 4 if fp32 else 8
+    nqs = (M + 1) ** (d - 1)
+    nqt = M + 1
+    niter = M + 1
+    fl_flux = 3 * d * nv + 10 if pde == 0 else 60 + 4 * nv      # one normal flux incl. primitives
+    rec_bytes = (4 * (ne - 1) + r * (Mc - 1) * (ne - 1) + 4 * (d + 1) * d + r * (d + 1) * d * d + 1 + r * d * d
+                 + (8 if fp32 else 8) * nv + r * L * nv)
+    rec_flops = (3 * (ne - 1) * nv + 2 * (Mc - 1) * (ne - 1) * nv + (2 * d * d + 3 * d) * (d + 1) * nv
+                 + nv * (2 * (Mc - 1) ** 2 + (d + 1) * 2 * d * d + 4 * (Mc - 1) + 40)
+                 + L0 * nv * 2 * (Mc - 1) + L0 * (d * fl_flux + 2 * L1 * nv * (d + 2))
+                 + niter * L1 * (d * fl_flux + 2 * L1 * nv * (d + 1)))
+    flux_bytes_face = (2 / (d + 1)) * r * L * nv + 4 + 4 + 2 + r * d + r + r * nv
+    flux_flops_face = nqt * nqs * (2 * 2 * L * nv + 2 * fl_flux + 2 * 25 + 5 * nv)
+    upd_bytes = 4 * (d + 1) + (2 * r * nv) + 8 * nv * 2 + (8 * nv if fp32 else 0) + 16
+    upd_flops = (d + 1) * nv * 2 + 2 * nv + 30
+    return dict(rec=(rec_bytes, rec_flops), flux=(flux_bytes_face, flux_flops_face), update=(upd_bytes, upd_flops))
+
+
+def peaks():
+    p = {"hbm_gbs": 6800.0, "src": "fallback"}
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        mp = json.load(open(path))
+        p = {"hbm_gbs": float(mp["hbm_gbs"]), "src": "measured", "sm_max_mhz": float(mp.get("sm_max_mhz", 2070))}
+    p.setdefault("sm_max_mhz", 2070.0)
+    # FP32 FMA pipe: 152 SMs x 128 lanes x 2 flops x max SM clock (nominal units, max clock)
+    p["fp32_tflops"] = 152 * 128 * 2 * p["sm_max_mhz"] * 1e6 / 1e12
+    p["fp64_tflops"] = 1.25  # GB300 nominal FP64
+    return p
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("kernels.cuh",):
+        h.update(open(os.path.join(ROOT, "paper_1612_09335_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel, workload):
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path))
+    except Exception:
+        return None
+    for r in rec.get("entries", []):
+        if r.get("kernel") == kernel and r.get("workload") == workload and r.get("source") == kernel_source_hash():
+            return r.get("dram_bytes_per_launch")
+    return None
+
+
+# ---------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0, period_ms=50):
+        self.rows = []
+        self.proc = None
+        self.t = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", f"-lms={period_ms}"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append((time.perf_counter(), line.strip()))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        rows = [r for t, r in self.rows if t0 - 0.06 <= t <= t1 + 0.06] or [r for _, r in self.rows[-3:]]
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            f = [x.strip() for x in r.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                mhz.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+# --------------------------------------------------------------------- helpers
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline_run(name, seconds_budget=20.0, cells_hint=None):
+    """Time the FP64 oracle (single host thread, as it stands) on a bounded
+    sample of the workload: the same scheme on a coarser mesh of the same
+    family, one untimed warm step (lazy per-cell setup), then timed steps."""
+    import oracle
+    from paper_1612_09335_gb300 import workloads as wl
+    cfg = WORKLOADS[name]
+    per_cell = {(2, 4, 0): 200e-6, (2, 3, 0): 65e-6, (3, 3, 0): 400e-6, (2, 4, 1): 900e-6}.get(
+        (cfg["dim"], cfg["order"], cfg["pde"]), 300e-6)
+    target = cells_hint or max(512, int(seconds_budget / 3 / per_cell))
+    if cfg["dim"] == 2:
+        n = max(8, int(math.sqrt(target / 2)))
+    else:
+        n = max(4, int(round((target / 6) ** (1 / 3))))
+    mesh, Q = make_inputs(name, n)
+    o = oracle.Oracle(mesh, cfg["order"], cfg["pde"])
+    dt = o.stable_dt(Q)
+    Q = o.step(Q, dt)
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        Q = o.step(Q, dt)
+        steps += 1
+        if time.perf_counter() - t0 > seconds_budget * 0.5 or steps >= 3:
+            break
+    el = time.perf_counter() - t0
+    return dict(value=mesh.nc * steps / el, unit="cell-updates/s", cores=1, kind="oracle",
+                sample=f"{mesh.nc} cells ({n}-cell grid of the same workload family), {steps} steps after one "
+                       f"untimed warm step, single host thread")
+
+
+# ---------------------------------------------------------------------- ours
+def run_ours(args):
+    import numpy as np
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1612_09335_gb300 import binding as cw
+
+    name = args.workload
+    cfg = WORKLOADS[name]
+    mesh, Q0 = make_inputs(name, args.n)
+    N = mesh.nc
+    stream = torch.cuda.current_stream()
+    m = cw.Mesh.from_workload(mesh)
+    s = cw.Solver(m, cfg["order"], cfg["pde"], cw.FP32_MIXED, stream=stream.cuda_stream)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+
+    s.set_state(Q0)
+    for _ in range(args.warmup):
+        s.step(0.0)
+    s.sync()
+    s.set_state(Q0)
+    s.profile(True)
+    clk = ClockSampler(local)
+    time.sleep(0.3)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record(stream)
+    for _ in range(args.steps):
+        s.step(0.0)
+    e1.record(stream)
+    barrier()
+    t1 = time.perf_counter()
+    clk.stop()
+    ms = e0.elapsed_time(e1)
+    kms, kn = s.profile_read()
+    s.profile(False)
+    s.sync()
+    sim_time = s.time()
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * N * args.steps / (ms / 1e3)
+    out = {"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic"}
+    r_bytes = 4 * (mcal(cfg["order"] - 1, cfg["dim"]) - 1) * (cfg["dim"] * mcal(cfg["order"] - 1, cfg["dim"]) - 1) * N
+    out["config"] = {"workload": name, "mesh": WORKLOADS[name]["desc"] if args.n is None else f"n={args.n}",
+                     "cells": N, "faces": s.nf, "order": cfg["order"],
+                     "pde": "euler" if cfg["pde"] == 0 else "mhd_glm", "dim": cfg["dim"],
+                     "precision": "fp32_mixed (FP32 arithmetic; FP64 setup, FP64 cell-average accumulator)",
+                     "time_step": "CFL bound computed on the device every step",
+                     "l2": f"inputs larger than L2 (reconstruction matrices {r_bytes / 1e6:.0f} MB)",
+                     "parallelism": f"replicas x{ws}", "simulated_time": sim_time}
+    # per-kernel roofline
+    pk = peaks()
+    alg = algorithmic(cfg["dim"], cfg["order"], cfg["pde"], fp32=True)
+    units = {"rec": N, "flux": s.nf, "update": N}
+    kern = {"rec": "k_rec_pred", "flux": "k_flux", "update": "k_update"}
+    kernels = {}
+    tot = sum(kms)
+    for k, key in enumerate(("rec", "flux", "update")):
+        if kn[k] == 0:
+            continue
+        dur = kms[k] / kn[k] / 1e3
+        b, f = alg[key]
+        ach_gbs = b * units[key] / dur / 1e9
+        ach_tf = f * units[key] / dur / 1e12
+        kernels[kern[key]] = {"ms": kms[k] / kn[k], "share": kms[k] / tot, "GB/s": ach_gbs, "TFLOP/s": ach_tf,
+                              "hbm_frac": ach_gbs / pk["hbm_gbs"], "fp32_frac": ach_tf / pk["fp32_tflops"]}
+    dom = max(kernels, key=lambda k: kernels[k]["share"])
+    kd = kernels[dom]
+    key = {v: k for k, v in kern.items()}[dom]
+    b, f = alg[key]
+    intensity = f / b
+    ridge = pk["fp32_tflops"] * 1e12 / (pk["hbm_gbs"] * 1e9)
+    traffic = measured_traffic(dom, name)
+    if intensity > ridge:
+        out["roofline"] = {"bound": "alu", "achieved": kd["TFLOP/s"], "peak": pk["fp32_tflops"], "unit": "TFLOP/s",
+                           "frac": kd["fp32_frac"], "traffic": traffic, "kernel": dom,
+                           "peak_src": f"derived: 152 SM x 128 FP32 lanes x 2 x {pk['sm_max_mhz']:.0f} MHz",
+                           "hbm_frac": kd["hbm_frac"]}
+    else:
+        out["roofline"] = {"bound": "hbm", "achieved": kd["GB/s"], "peak": pk["hbm_gbs"], "unit": "GB/s",
+                           "frac": kd["hbm_frac"], "traffic": traffic, "kernel": dom,
+                           "peak_src": pk["src"], "fp32_frac": kd["fp32_frac"]}
+    out["kernels"] = kernels
+    out["gpu_launches"] = int(sum(kn))
+    out["clocks"] = clk.summary(t0, t1)
+    # FP64 mode, same workload (the other precision of the metric)
+    if not args.no_fp64:
+        s64 = cw.Solver(m, cfg["order"], cfg["pde"], cw.FP64, stream=stream.cuda_stream)
+        s64.set_state(Q0)
+        s64.step(0.0)
+        s64.sync()
+        k64 = max(3, min(args.steps, 20))
+        barrier()
+        e0.record(stream)
+        for _ in range(k64):
+            s64.step(0.0)
+        e1.record(stream)
+        barrier()
+        ms64 = e0.elapsed_time(e1)
+        out["fp64"] = {"value": ws * N * k64 / (ms64 / 1e3), "unit": "cell-updates/s", "steps": k64,
+                       "ms_per_step": ms64 / k64}
+        s64.close()
+    # end to end through the C ABI with pinned host buffers
+    if not args.no_e2e:
+        nv = s.nv
+        hin = torch.empty((N, nv), dtype=torch.float64, pin_memory=True)
+        hin.numpy()[:] = Q0
+        hout = torch.empty((N, nv), dtype=torch.float64, pin_memory=True)
+        ke = max(3, min(args.steps, 30))
+        s.set_state(hin)
+        s.step(0.0)
+        s.get_state(hout)
+        barrier()
+        ta = time.perf_counter()
+        for _ in range(ke):
+            s.set_state(hin)
+            s.step(0.0)
+            s.get_state(hout)
+        barrier()
+        tb = time.perf_counter()
+        el = tb - ta
+        if ws > 1:
+            t = torch.tensor([el], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            el = float(t.item())
+        out["e2e"] = {"value": ws * N * ke / el, "unit": "cell-updates/s", "h2d_bytes_per_step": N * nv * 8,
+                      "d2h_bytes_per_step": N * nv * 8, "steps": ke,
+                      "path": "cweno_set_state(pinned host) + ader_cweno_step + cweno_get_state(pinned host)"}
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_run(name)
+    if rank == 0:
+        print(json.dumps(out))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    name = args.workload
+    cfg = WORKLOADS[name]
+    oracle.build()
+    per_cell = {(2, 4, 0): 200e-6, (2, 3, 0): 65e-6, (3, 3, 0): 400e-6, (2, 4, 1): 900e-6}.get(
+        (cfg["dim"], cfg["order"], cfg["pde"]), 300e-6)
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    cells = max(256, int(budget / per_cell))
+    n = max(8, int(math.sqrt(cells / 2))) if cfg["dim"] == 2 else max(4, int(round((cells / 6) ** (1 / 3))))
+    mesh, Q = make_inputs(name, n)
+    o = oracle.Oracle(mesh, cfg["order"], cfg["pde"])
+    for _ in range(max(1, args.warmup)):
+        Q = o.step(Q, o.stable_dt(Q))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        Q = o.step(Q, o.stable_dt(Q))
+    el = time.perf_counter() - t0
+    v = mesh.nc * args.steps / el
+    out = {"metric": METRIC, "value": v, "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": name, "cells": mesh.nc, "order": cfg["order"],
+                      "pde": "euler" if cfg["pde"] == 0 else "mhd_glm", "dim": cfg["dim"],
+                      "precision": "fp64 (oracle)"},
+           "cpu_baseline": {"value": v, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                            "sample": f"{mesh.nc}-cell mesh of the same workload family per step "
+                                      f"(bounded sample), single host thread"},
+           "e2e": {"value": v, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="explosion2d_p3", choices=sorted(WORKLOADS))
+    ap.add_argument("--n", type=int, default=None, help="mesh resolution override (small profiling cases)")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,553 @@
+// C ABI: handles, error reporting, device uploads and the step sequence.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/cweno.h"
+#include "api_internal.h"
+#include "host.h"
+#include "ops.h"
+#include "refelem.h"
+
+namespace cw {
+
+static thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  g_err = std::string(where) + ": " + cudaGetErrorString(e);
+  return CWENO_ECUDA;
+}
+
+#define CK(call)                                      \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+// Reference tables are universal per (d, M): built once per process.
+static std::mutex g_ref_mu;
+static std::map<int, std::unique_ptr<RefElem>> g_ref;
+
+const RefElem& ref_elem(int d, int M) {
+  std::lock_guard<std::mutex> lk(g_ref_mu);
+  int key = d * 16 + M;
+  auto it = g_ref.find(key);
+  if (it != g_ref.end()) return *it->second;
+  std::unique_ptr<RefElem> r(new RefElem());
+  r->init(d, M);
+  const RefElem& out = *r;
+  g_ref[key] = std::move(r);
+  return out;
+}
+
+}  // namespace cw
+
+using namespace cw;
+
+struct cweno_mesh {
+  MeshHost m;
+};
+
+// ---------------------------------------------------------------- helpers
+static int dev_alloc(cweno_solver* s, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(CWENO_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+  }
+  s->allocs.push_back(*p);
+  s->bytes += bytes;
+  return CWENO_OK;
+}
+
+template <typename TV>
+static int upload(cweno_solver* s, const std::vector<TV>& h, const void** out) {
+  void* p = nullptr;
+  int rc = dev_alloc(s, &p, h.size() * sizeof(TV));
+  if (rc) return rc;
+  if (!h.empty()) {
+    cudaError_t e = cudaMemcpy(p, h.data(), h.size() * sizeof(TV), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "upload");
+  }
+  *out = p;
+  return CWENO_OK;
+}
+
+// double matrix in AoS-by-cell (nc x K) -> SoA (K x nc) of type TV
+template <typename TV>
+static std::vector<TV> soa(const std::vector<double>& a, int64_t nc, int K) {
+  std::vector<TV> o((size_t)nc * K);
+  for (int64_t c = 0; c < nc; ++c)
+    for (int k = 0; k < K; ++k) o[(size_t)k * nc + c] = (TV)a[(size_t)c * K + k];
+  return o;
+}
+template <typename TI>
+static std::vector<TI> soa_i(const std::vector<TI>& a, int64_t nc, int K) {
+  std::vector<TI> o((size_t)nc * K);
+  for (int64_t c = 0; c < nc; ++c)
+    for (int k = 0; k < K; ++k) o[(size_t)k * nc + c] = a[(size_t)c * K + k];
+  return o;
+}
+
+static int upload_real(cweno_solver* s, const std::vector<double>& a, int64_t n, int K, const void** out) {
+  if (s->prec == CWENO_FP32_MIXED) {
+    std::vector<float> v = soa<float>(a, n, K);
+    return upload(s, v, out);
+  }
+  std::vector<double> v = soa<double>(a, n, K);
+  return upload(s, v, out);
+}
+
+extern "C" {
+
+void cweno_default_params(cweno_params* p, int dim, int pde) {
+  if (!p) return;
+  p->eps = 1e-14;
+  p->r = 4.0;
+  p->lambda0 = 1e5;
+  p->lambda_s = 1.0;
+  p->gamma = pde == CWENO_MHD_GLM ? 5.0 / 3.0 : 1.4;
+  p->c_h = 2.0;
+  p->cfl = dim == 3 ? 1.0 / 3.0 : 0.5;
+  p->picard_iters = 0;
+  p->linear_weights = 0;
+}
+
+const char* cweno_last_error(void) { return g_err.c_str(); }
+
+int cweno_nvars(int dim, int pde) { return pde == CWENO_MHD_GLM ? 9 : dim + 2; }
+
+int cweno_mesh_create(int dim, int64_t nv, const double* xyz, int64_t nc, const int32_t* cells, const double* period,
+                      cweno_mesh** out) {
+  if (!out) return fail(CWENO_EINVAL, "null output handle");
+  *out = nullptr;
+  std::unique_ptr<cweno_mesh> m(new cweno_mesh());
+  std::string err;
+  int rc = build_mesh(dim, nv, xyz, nc, cells, period, m->m, err);
+  if (rc) return fail(rc, err);
+  *out = m.release();
+  return CWENO_OK;
+}
+
+void cweno_mesh_destroy(cweno_mesh* m) { delete m; }
+
+int cweno_mesh_info(const cweno_mesh* m, int64_t* ncells, int64_t* nfaces, int64_t* nboundary) {
+  if (!m) return fail(CWENO_EINVAL, "null mesh");
+  if (ncells) *ncells = m->m.nc;
+  if (nfaces) *nfaces = m->m.nf;
+  if (nboundary) *nboundary = m->m.nbnd;
+  return CWENO_OK;
+}
+
+int cweno_mesh_stencils(const cweno_mesh* mesh, int order, int32_t* S0, int32_t* sec) {
+  if (!mesh || !S0 || !sec) return fail(CWENO_EINVAL, "null argument");
+  if (order < 2 || order > 4) return fail(CWENO_EINVAL, "order must be 2, 3 or 4");
+  const MeshHost& m = mesh->m;
+  const RefElem& re = ref_elem(m.d, order - 1);
+  CellSetup cs;
+  std::string err;
+  int rc = build_cell_setup(m, re, cs, err, (int)std::max(1u, std::thread::hardware_concurrency()));
+  if (rc) return fail(rc, err);
+  const int ne = re.ne, d = m.d, nvx = d + 1;
+  for (int64_t i = 0; i < m.nc; ++i) {
+    int64_t u = m.perm[i];
+    S0[u * ne] = (int32_t)u;
+    for (int k = 0; k < ne - 1; ++k) S0[u * ne + 1 + k] = m.perm[cs.sten[(size_t)i * (ne - 1) + k]];
+    for (int q = 0; q < nvx * d; ++q) {
+      int32_t c = cs.sec[(size_t)i * nvx * d + q];
+      sec[u * nvx * d + q] = c < 0 ? -1 : m.perm[c];
+    }
+  }
+  return CWENO_OK;
+}
+
+void cweno_solver_destroy(cweno_solver* s) {
+  if (!s) return;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  cudaSetDevice(s->dev);
+  cudaStreamSynchronize(s->stream);
+  for (auto& kv : s->graphs)
+    if (kv.second) cudaGraphExecDestroy(kv.second);
+  for (auto& u : s->ev_used) {
+    cudaEventDestroy(u.first.first);
+    cudaEventDestroy(u.first.second);
+  }
+  for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
+  for (void* p : s->allocs) cudaFree(p);
+  if (s->own_stream) cudaStreamDestroy(s->stream);
+  if (cur >= 0) cudaSetDevice(cur);
+  delete s;
+}
+
+int cweno_setup(const cweno_mesh* mesh, int order, int pde, int precision, const cweno_params* params, void* stream,
+                cweno_solver** out) {
+  if (!out) return fail(CWENO_EINVAL, "null output handle");
+  *out = nullptr;
+  if (!mesh) return fail(CWENO_EINVAL, "null mesh");
+  const MeshHost& m = mesh->m;
+  if (order < 2 || order > 4) return fail(CWENO_EINVAL, "order must be 2, 3 or 4");
+  if (pde != CWENO_EULER && pde != CWENO_MHD_GLM) return fail(CWENO_EINVAL, "unknown pde");
+  if (pde == CWENO_MHD_GLM && m.d != 2) return fail(CWENO_EINVAL, "MHD-GLM is built for 2D meshes only");
+  if (precision != CWENO_FP64 && precision != CWENO_FP32_MIXED) return fail(CWENO_EINVAL, "unknown precision");
+  cweno_params prm;
+  cweno_default_params(&prm, m.d, pde);
+  if (params) prm = *params;
+  if (prm.r != 4.0) return fail(CWENO_EINVAL, "only r = 4 is built (Eq. weights2)");
+  if (!(prm.eps > 0) || !(prm.lambda0 > 0) || !(prm.lambda_s > 0) || !(prm.gamma > 1.0) || !(prm.cfl > 0))
+    return fail(CWENO_EINVAL, "bad scheme parameters");
+  const int M = order - 1;
+  std::unique_ptr<cweno_solver> s(new cweno_solver());
+  s->dim = m.d;
+  s->order = order;
+  s->M = M;
+  s->pde = pde;
+  s->prec = precision;
+  s->nv = cweno_nvars(m.d, pde);
+  s->prm = prm;
+  s->ph.gamma = prm.gamma;
+  s->ph.ch = prm.c_h;
+  s->ph.eps = prm.eps;
+  s->ph.lam0 = prm.lambda0;
+  s->ph.lams = prm.lambda_s;
+  s->ph.niter = prm.picard_iters > 0 ? prm.picard_iters : M + 1;
+  s->ph.linear_weights = prm.linear_weights;
+  s->nc = m.nc;
+  s->nf = m.nf;
+  CK(cudaGetDevice(&s->dev));
+  const RefElem& re = ref_elem(m.d, M);
+  s->re = &re;
+  if (pde == CWENO_EULER && m.d == 2) s->ops = make_ops_euler2(M, precision == CWENO_FP32_MIXED, re);
+  else if (pde == CWENO_EULER && m.d == 3) s->ops = make_ops_euler3(M, precision == CWENO_FP32_MIXED, re);
+  else s->ops = make_ops_mhd2(M, precision == CWENO_FP32_MIXED, re);
+  if (!s->ops) return fail(CWENO_EINVAL, "configuration not built");
+  CellSetup cs;
+  std::string err;
+  int nth = (int)std::max(1u, std::thread::hardware_concurrency());
+  int rc = build_cell_setup(m, re, cs, err, nth);
+  if (rc) return fail(rc, err);
+  if (stream) {
+    s->stream = (cudaStream_t)stream;
+    s->own_stream = false;
+  } else {
+    CK(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+    s->own_stream = true;
+  }
+  const int64_t N = m.nc, F = m.nf;
+  const int d = m.d, nvx = d + 1, nv = s->nv;
+  DevState& ds = s->ds;
+  ds.N = N;
+  ds.F = F;
+  ds.nv = nv;
+  const size_t es = s->ops->elem_size();
+  // state
+  void* p = nullptr;
+  if ((rc = dev_alloc(s.get(), &p, sizeof(double) * N * nv))) return rc;
+  ds.Q = (double*)p;
+  CK(cudaMemset(ds.Q, 0, sizeof(double) * N * nv));
+  if (precision == CWENO_FP32_MIXED) {
+    if ((rc = dev_alloc(s.get(), &p, sizeof(float) * N * nv))) return rc;
+    ds.Qhi = (float*)p;
+    if ((rc = dev_alloc(s.get(), &p, sizeof(float) * N * nv))) return rc;
+    ds.Qlo = (float*)p;
+    CK(cudaMemset(ds.Qhi, 0, sizeof(float) * N * nv));
+    CK(cudaMemset(ds.Qlo, 0, sizeof(float) * N * nv));
+  }
+  if ((rc = upload(s.get(), m.perm, (const void**)&ds.perm))) return rc;
+  if ((rc = upload(s.get(), soa_i(cs.sten, N, re.ne - 1), (const void**)&ds.sten))) return rc;
+  if ((rc = upload_real(s.get(), cs.R, N, (re.Mc - 1) * (re.ne - 1), &ds.R))) return rc;
+  if ((rc = upload(s.get(), soa_i(cs.sec, N, nvx * d), (const void**)&ds.sec))) return rc;
+  if ((rc = upload_real(s.get(), cs.Binv, N, nvx * d * d, &ds.Binv))) return rc;
+  if ((rc = upload(s.get(), cs.nsec, (const void**)&ds.nsec))) return rc;
+  if ((rc = upload_real(s.get(), cs.Jinv, N, d * d, &ds.Jinv))) return rc;
+  if ((rc = dev_alloc(s.get(), &p, es * N * nv * re.L))) return rc;
+  ds.qhat = p;
+  if ((rc = upload(s.get(), m.fL, (const void**)&ds.fL))) return rc;
+  if ((rc = upload(s.get(), m.fR, (const void**)&ds.fR))) return rc;
+  if ((rc = upload(s.get(), m.codeL, (const void**)&ds.codeL))) return rc;
+  if ((rc = upload(s.get(), m.codeR, (const void**)&ds.codeR))) return rc;
+  {
+    std::vector<double> fn((size_t)F * d);
+    for (int64_t f = 0; f < F; ++f)
+      for (int a = 0; a < d; ++a) fn[(size_t)f * d + a] = m.fn[f * 3 + a];
+    if ((rc = upload_real(s.get(), fn, F, d, &ds.fn))) return rc;
+    if ((rc = upload_real(s.get(), m.farea, F, 1, &ds.farea))) return rc;
+  }
+  if ((rc = dev_alloc(s.get(), &p, es * F * nv))) return rc;
+  ds.G = p;
+  {
+    std::vector<unsigned char> tb(s->ops->table_bytes());
+    s->ops->pack_tables(tb.data());
+    if ((rc = upload(s.get(), tb, &ds.ftab))) return rc;
+  }
+  if ((rc = upload(s.get(), soa_i(m.cellface, N, nvx), (const void**)&ds.cellface))) return rc;
+  {
+    std::vector<double> iv(N);
+    for (int64_t i = 0; i < N; ++i) iv[i] = 1.0 / m.vol[i];
+    if ((rc = upload(s.get(), iv, (const void**)&ds.invvol))) return rc;
+    if ((rc = upload(s.get(), m.hsize, (const void**)&ds.hsize))) return rc;
+  }
+  if ((rc = dev_alloc(s.get(), &p, sizeof(unsigned long long) * 4 + sizeof(double) + sizeof(int) * 2))) return rc;
+  ds.dtmin = (unsigned long long*)p;
+  ds.time = (double*)((char*)p + sizeof(unsigned long long) * 4);
+  ds.status = (int*)((char*)p + sizeof(unsigned long long) * 4 + sizeof(double));
+  {
+    unsigned long long init[4] = {0x7ff0000000000000ull, 0x7ff0000000000000ull, 0x7ff0000000000000ull,
+                                  0x7ff0000000000000ull};
+    CK(cudaMemcpy(ds.dtmin, init, sizeof(init), cudaMemcpyHostToDevice));
+    CK(cudaMemset(ds.time, 0, sizeof(double) + 2 * sizeof(int)));
+  }
+  if ((rc = dev_alloc(s.get(), &p, sizeof(double) * N * nv))) return rc;
+  ds.stage = (double*)p;
+  CK(s->ops->prepare());
+  CK(cudaDeviceSynchronize());
+  *out = s.release();
+  return CWENO_OK;
+}
+
+int cweno_solver_info(const cweno_solver* s, int* nvars, int* mcal_, int* ne, int* lcal, int64_t* ncells,
+                      int64_t* nfaces) {
+  if (!s) return fail(CWENO_EINVAL, "null solver");
+  if (nvars) *nvars = s->nv;
+  if (mcal_) *mcal_ = s->re->Mc;
+  if (ne) *ne = s->re->ne;
+  if (lcal) *lcal = s->re->L;
+  if (ncells) *ncells = s->nc;
+  if (nfaces) *nfaces = s->nf;
+  return CWENO_OK;
+}
+
+int cweno_solver_footprint(const cweno_solver* s, size_t* bytes) {
+  if (!s || !bytes) return fail(CWENO_EINVAL, "null argument");
+  *bytes = s->bytes;
+  return CWENO_OK;
+}
+
+int cweno_set_state(cweno_solver* s, const double* Q, int on_device) {
+  if (!s || !Q) return fail(CWENO_EINVAL, "null argument");
+  CK(cudaSetDevice(s->dev));
+  const double* src = Q;
+  if (!on_device) {
+    CK(cudaMemcpyAsync(s->ds.stage, Q, sizeof(double) * s->nc * s->nv, cudaMemcpyHostToDevice, s->stream));
+    src = s->ds.stage;
+  }
+  CK(s->ops->set_state(s->ds, src, s->stream));
+  static const unsigned long long inf = 0x7ff0000000000000ull;
+  CK(cudaMemcpyAsync(s->ds.dtmin, &inf, sizeof(inf), cudaMemcpyHostToDevice, s->stream));
+  CK(cudaMemsetAsync(s->ds.time, 0, sizeof(double) + 2 * sizeof(int), s->stream));
+  CK(s->ops->stable_dt(s->ds, s->ph, 0, s->stream));
+  s->cur = 0;
+  return CWENO_OK;
+}
+
+int cweno_get_state(cweno_solver* s, double* Q, int on_device) {
+  if (!s || !Q) return fail(CWENO_EINVAL, "null argument");
+  CK(cudaSetDevice(s->dev));
+  if (on_device) {
+    CK(s->ops->get_state(s->ds, Q, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return CWENO_OK;
+  }
+  CK(s->ops->get_state(s->ds, s->ds.stage, s->stream));
+  CK(cudaMemcpyAsync(Q, s->ds.stage, sizeof(double) * s->nc * s->nv, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  return CWENO_OK;
+}
+
+static int ensure_out(cweno_solver* s, size_t bytes) {
+  if (s->outbuf_bytes >= bytes) return CWENO_OK;
+  void* p = nullptr;
+  int rc = dev_alloc(s, &p, bytes);
+  if (rc) return rc;
+  s->outbuf = (double*)p;
+  s->outbuf_bytes = bytes;
+  return CWENO_OK;
+}
+
+int cweno_reconstruct(cweno_solver* s, double* w, int on_device) {
+  if (!s || !w) return fail(CWENO_EINVAL, "null argument");
+  CK(cudaSetDevice(s->dev));
+  size_t bytes = sizeof(double) * s->nc * s->re->Mc * s->nv;
+  double* dst = w;
+  if (!on_device) {
+    int rc = ensure_out(s, bytes);
+    if (rc) return rc;
+    dst = s->outbuf;
+  }
+  CK(s->ops->reconstruct(s->ds, s->ph, dst, s->stream));
+  if (!on_device) CK(cudaMemcpyAsync(w, dst, bytes, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  return CWENO_OK;
+}
+
+int cweno_predictor(cweno_solver* s, double dt, double* qhat, int on_device) {
+  if (!s || !qhat || !(dt > 0)) return fail(CWENO_EINVAL, "bad argument");
+  CK(cudaSetDevice(s->dev));
+  size_t bytes = sizeof(double) * s->nc * s->re->L * s->nv;
+  double* dst = qhat;
+  if (!on_device) {
+    int rc = ensure_out(s, bytes);
+    if (rc) return rc;
+    dst = s->outbuf;
+  }
+  DtArgs a;
+  a.fixed = dt;
+  a.cur = -1;
+  CK(s->ops->rec_pred(s->ds, s->ph, a, s->stream));
+  CK(s->ops->qhat_out(s->ds, dst, s->stream));
+  if (!on_device) CK(cudaMemcpyAsync(qhat, dst, bytes, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  return CWENO_OK;
+}
+
+int cweno_stable_dt(cweno_solver* s, double cfl, double* dt) {
+  if (!s || !dt || !(cfl > 0)) return fail(CWENO_EINVAL, "bad argument");
+  CK(cudaSetDevice(s->dev));
+  static const unsigned long long inf = 0x7ff0000000000000ull;
+  CK(cudaMemcpyAsync(s->ds.dtmin + 2, &inf, sizeof(inf), cudaMemcpyHostToDevice, s->stream));
+  CK(s->ops->stable_dt(s->ds, s->ph, 2, s->stream));
+  unsigned long long bits = 0;
+  CK(cudaMemcpyAsync(&bits, s->ds.dtmin + 2, sizeof(bits), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  double h;
+  std::memcpy(&h, &bits, sizeof(h));
+  *dt = cfl * h;
+  return CWENO_OK;
+}
+
+}  // extern "C"
+
+namespace cw {
+static cudaError_t take_event(cweno_solver* s, cudaEvent_t* e) {
+  if (!s->ev_pool.empty()) {
+    *e = s->ev_pool.back();
+    s->ev_pool.pop_back();
+    return cudaSuccess;
+  }
+  return cudaEventCreate(e);
+}
+
+int enqueue_step(cweno_solver* s, double dt, int cur) {
+  DtArgs a;
+  a.fixed = dt > 0 ? dt : 0.0;
+  a.cfl = s->prm.cfl;
+  a.cur = cur;
+  for (int k = 0; k < 3; ++k) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (s->profile) {
+      CK(take_event(s, &e0));
+      CK(take_event(s, &e1));
+      CK(cudaEventRecord(e0, s->stream));
+    }
+    if (k == 0) CK(s->ops->rec_pred(s->ds, s->ph, a, s->stream));
+    if (k == 1) CK(s->ops->flux(s->ds, s->ph, a, s->stream));
+    if (k == 2) CK(s->ops->update(s->ds, s->ph, a, s->stream));
+    if (s->profile) {
+      CK(cudaEventRecord(e1, s->stream));
+      s->ev_used.push_back({{e0, e1}, k});
+    }
+  }
+  return CWENO_OK;
+}
+}  // namespace cw
+
+extern "C" {
+
+int ader_cweno_step(cweno_solver* s, double dt) {
+  if (!s) return fail(CWENO_EINVAL, "null solver");
+  CK(cudaSetDevice(s->dev));
+  int rc = enqueue_step(s, dt, s->cur);
+  if (rc) return rc;
+  s->cur ^= 1;
+  return CWENO_OK;
+}
+
+int ader_cweno_run(cweno_solver* s, int nsteps, double dt) {
+  if (!s || nsteps < 0) return fail(CWENO_EINVAL, "bad argument");
+  CK(cudaSetDevice(s->dev));
+  for (int k = 0; k < nsteps; ++k) {
+    // one graph per (time-step slot, dt): captured on first use, then replayed
+    std::pair<int, double> gk(s->cur, dt > 0 ? dt : 0.0);
+    cudaGraphExec_t& ex = s->graphs[gk];
+    if (!ex) {
+      cudaGraph_t g;
+      CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+      bool prof = s->profile;
+      s->profile = false;
+      int rc = enqueue_step(s, dt, s->cur);
+      s->profile = prof;
+      cudaError_t e = cudaStreamEndCapture(s->stream, &g);
+      if (rc) return rc;
+      if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+      e = cudaGraphInstantiate(&ex, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    CK(cudaGraphLaunch(ex, s->stream));
+    s->cur ^= 1;
+  }
+  return CWENO_OK;
+}
+
+int cweno_sync(cweno_solver* s) {
+  if (!s) return fail(CWENO_EINVAL, "null solver");
+  CK(cudaSetDevice(s->dev));
+  CK(cudaStreamSynchronize(s->stream));
+  int st = 0;
+  CK(cudaMemcpy(&st, s->ds.status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st) return fail(CWENO_ENAN, "a step produced NaN or non-positive density / pressure");
+  return CWENO_OK;
+}
+
+int cweno_get_time(cweno_solver* s, double* t) {
+  if (!s || !t) return fail(CWENO_EINVAL, "null argument");
+  CK(cudaSetDevice(s->dev));
+  CK(cudaStreamSynchronize(s->stream));
+  CK(cudaMemcpy(t, s->ds.time, sizeof(double), cudaMemcpyDeviceToHost));
+  return CWENO_OK;
+}
+
+void* cweno_stream(cweno_solver* s) { return s ? (void*)s->stream : nullptr; }
+
+int cweno_profile_enable(cweno_solver* s, int on) {
+  if (!s) return fail(CWENO_EINVAL, "null solver");
+  s->profile = on != 0;
+  return CWENO_OK;
+}
+
+int cweno_profile_read(cweno_solver* s, double* ms, int64_t* launches) {
+  if (!s || !ms || !launches) return fail(CWENO_EINVAL, "null argument");
+  CK(cudaSetDevice(s->dev));
+  CK(cudaStreamSynchronize(s->stream));
+  for (int k = 0; k < 3; ++k) {
+    ms[k] = 0.0;
+    launches[k] = 0;
+  }
+  for (auto& u : s->ev_used) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, u.first.first, u.first.second));
+    ms[u.second] += t;
+    launches[u.second] += 1;
+    s->ev_pool.push_back(u.first.first);
+    s->ev_pool.push_back(u.first.second);
+  }
+  s->ev_used.clear();
+  return CWENO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,43 @@
+// Solver handle layout shared by the C ABI and the serving loop.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <map>
+#include <memory>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/cweno.h"
+#include "ops.h"
+#include "refelem.h"
+
+struct cweno_solver {
+  int dim = 2, order = 2, M = 1, pde = 0, prec = 0, nv = 4;
+  cweno_params prm;
+  cw::PhysParams ph;
+  const cw::RefElem* re = nullptr;
+  std::unique_ptr<cw::Ops> ops;
+  cw::DevState ds;
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  int cur = 0;
+  int64_t nc = 0, nf = 0;
+  double* outbuf = nullptr;
+  size_t outbuf_bytes = 0;
+  std::map<std::pair<int, double>, cudaGraphExec_t> graphs;
+  // profiling: (start, stop, kernel) event triples recorded by enqueue_step
+  bool profile = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<std::pair<cudaEvent_t, cudaEvent_t>, int>> ev_used;
+};
+
+namespace cw {
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* where);
+int enqueue_step(cweno_solver* s, double dt, int cur);
+const RefElem& ref_elem(int d, int M);
+}  // namespace cw

@@ -1,0 +1,53 @@
+// Host-side mesh topology and per-cell reconstruction setup (FP64).
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "refelem.h"
+
+namespace cw {
+
+struct MeshHost {
+  int d = 2;
+  int64_t nv = 0, nc = 0;
+  std::vector<double> xyz;       // user vertices nv x d
+  bool per[3] = {false, false, false};
+  double Lper[3] = {0, 0, 0};
+  double qscale = 1.0;           // largest bounding-box extent (ranking tolerances)
+  // internal (Morton) order
+  std::vector<int32_t> perm;     // internal -> user cell index
+  std::vector<int32_t> iperm;    // user -> internal
+  std::vector<int64_t> gv;       // nc x (d+1) global vertex ids
+  std::vector<double> X;         // nc x (d+1) x 3 unwrapped coordinates
+  std::vector<double> vol;       // |T_i|
+  std::vector<double> bary;      // nc x 3
+  std::vector<double> hsize;     // incircle / insphere diameter
+  std::vector<int32_t> nbr;      // nc x (d+1): neighbour across local face k (opposite vertex k), -1 boundary
+  // faces (interior first in cell order, boundary faces included)
+  int64_t nf = 0, nbnd = 0;
+  std::vector<int32_t> fL, fR;   // fR = -1 on the boundary
+  std::vector<uint8_t> codeL, codeR;
+  std::vector<double> fn;        // nf x 3 unit normal, out of L
+  std::vector<double> farea;     // nf
+  std::vector<int32_t> cellface; // nc x (d+1): face id * 2 + (cell is R)
+};
+
+// Returns 0 or a CWENO_E* code, with a message in err.
+int build_mesh(int d, int64_t nv, const double* xyz, int64_t nc, const int32_t* cells, const double* period,
+               MeshHost& m, std::string& err);
+
+// Per-cell reconstruction data in internal order (FP64, SoA-ready).
+struct CellSetup {
+  int ne = 0, Mc = 0, d = 2;
+  std::vector<int32_t> sten;    // nc x (ne-1): S_i^0 \ {i}
+  std::vector<double> R;        // nc x (Mc-1) x (ne-1): pseudo-inverse rows
+  std::vector<int32_t> sec;     // nc x (d+1) x d sector cells, -1 if dropped
+  std::vector<double> Binv;     // nc x (d+1) x d x d
+  std::vector<uint8_t> nsec;    // kept sectors per cell
+  std::vector<double> Jinv;     // nc x d x d, Jinv[e][m] = d xi_e / d x_m
+};
+
+int build_cell_setup(const MeshHost& m, const RefElem& re, CellSetup& cs, std::string& err, int nthreads);
+
+}  // namespace cw

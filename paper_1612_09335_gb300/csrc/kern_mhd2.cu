@@ -1,0 +1,19 @@
+// Kernel instantiations: dimension 2, PDE 1 (0 Euler, 1 MHD-GLM), M = 1..3,
+// FP64 and FP32-mixed.
+#include "kernels.cuh"
+
+namespace cw {
+
+std::unique_ptr<Ops> make_ops_mhd2(int M, int fp32, const RefElem& re) {
+  switch (M * 2 + (fp32 ? 1 : 0)) {
+    case 2: return std::unique_ptr<Ops>(new OpsImpl<Cfg<2, 1, 1, double>>(re));
+    case 3: return std::unique_ptr<Ops>(new OpsImpl<Cfg<2, 1, 1, float>>(re));
+    case 4: return std::unique_ptr<Ops>(new OpsImpl<Cfg<2, 2, 1, double>>(re));
+    case 5: return std::unique_ptr<Ops>(new OpsImpl<Cfg<2, 2, 1, float>>(re));
+    case 6: return std::unique_ptr<Ops>(new OpsImpl<Cfg<2, 3, 1, double>>(re));
+    case 7: return std::unique_ptr<Ops>(new OpsImpl<Cfg<2, 3, 1, float>>(re));
+    default: return nullptr;
+  }
+}
+
+}  // namespace cw

@@ -1,0 +1,901 @@
+// CUDA kernels of the fixed-mesh ADER-CWENO step (sm_103a), templated on
+// dimension D, polynomial degree M, PDE and arithmetic type T.
+//
+//   k_rec_pred  one thread per cell: stencil gather, P_opt = R dQ
+//               (Eq. CWENO:Popt), sectorial P_s (Eq. CWENO:Ps), P_0
+//               (Eq. CWENO:P0), indicators and nonlinear weights (Eqs.
+//               weights, weights2), then the space-time Galerkin predictor
+//               (Eq. CGfinal) with the Picard iteration folded into
+//               q1 = C0 q0 - dt sum_e P_e G_e,  P_e = (K_tau^1)^-1 K_xi_e;
+//               writes the L space-time nodal values.
+//   k_flux      one thread per face (persistent grid): the predictor of both
+//               sides at the space-time Gauss points of the face, Rusanov
+//               flux (Eq. rusanov) with s_max per point, integrated with
+//               weights -> G_f = dt |f| sum w G.  Each face once.
+//   k_update    one thread per cell, gather by cell (deterministic, no
+//               atomics): Q -= (1/|T|) sum_f +-G_f in FP64 (Eq. PDEfinal),
+//               admissibility status, and the CFL bound of Eq. (timestep)
+//               for the next step (block min + atomicMin on the bits).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <algorithm>
+#include <cstring>
+#include <memory>
+#include <type_traits>
+#include <vector>
+
+#include "ops.h"
+
+namespace cw {
+
+constexpr int cmcal(int M, int d) {
+  return d == 2 ? (M + 1) * (M + 2) / 2
+                : d == 3 ? (M + 1) * (M + 2) * (M + 3) / 6 : (M + 1) * (M + 2) * (M + 3) * (M + 4) / 24;
+}
+
+template <int D_, int M_, int PDE_, typename T_>
+struct Cfg {
+  static constexpr int D = D_, M = M_, PDE = PDE_;
+  using T = T_;
+  static constexpr int NV = PDE == 0 ? D + 2 : 9;
+  static constexpr int MC = cmcal(M, D);
+  static constexpr int MC1 = MC - 1;
+  static constexpr int NE = D * MC;
+  static constexpr int NS = D + 1;
+  static constexpr int L = cmcal(M, D + 1);
+  static constexpr int L0 = MC;
+  static constexpr int L1 = L - MC;
+  static constexpr int NQS = D == 2 ? M + 1 : (M + 1) * (M + 1);
+  static constexpr int NQT = M + 1;
+  static constexpr int NCODE = D == 2 ? 6 : 24;
+  static constexpr int TABN = NCODE * NQT * NQS * L;
+  // time points processed per pass of the face kernel (register budget)
+  static constexpr int CH = (2 * NQT * NQS * NV <= 96) ? NQT
+                            : (NQT % 2 == 0 && 2 * 2 * NQS * NV <= 96) ? 2 : 1;
+};
+
+template <class C>
+struct CellTab {
+  using T = typename C::T;
+  T E[C::L0][C::MC1];
+  T Sig[C::MC1][C::MC1];
+  T C0[C::L1][C::L0];
+  T P[C::D][C::L1][C::L];
+};
+
+template <class C>
+struct KArgs {
+  using T = typename C::T;
+  int64_t N, F;
+  double* Q;
+  float* Qhi;
+  float* Qlo;
+  const int32_t* perm;
+  const int32_t* sten;
+  const T* R;
+  const int32_t* sec;
+  const T* Binv;
+  const uint8_t* nsec;
+  const T* Jinv;
+  T* qhat;
+  const int32_t* fL;
+  const int32_t* fR;
+  const uint8_t* codeL;
+  const uint8_t* codeR;
+  const T* fn;
+  const T* farea;
+  T* G;
+  const T* ftab;
+  const int32_t* cellface;
+  const double* invvol;
+  const double* hsize;
+  unsigned long long* dtmin;
+  double* time;
+  int* status;
+  double* out;
+  T gamma, ch, eps, lam0, lams;
+  int niter, linw;
+  double dt_fixed, cfl;
+  int cur, reset_next;
+};
+
+__device__ __forceinline__ double dt_of(double fixed, double cfl, const unsigned long long* dtmin, int cur) {
+  return fixed > 0.0 ? fixed : cfl * __longlong_as_double((long long)dtmin[cur]);
+}
+
+// ------------------------------------------------------------------ physics
+// Normal flux F.n for an arbitrary (not necessarily unit) vector n, which is
+// linear in n: used with unit face normals and with rows of d xi / d x.
+template <int D, int PDE, typename T>
+struct Phys;
+
+template <int D, typename T>
+struct Phys<D, 0, T> {  // Euler, Eqs. (eulerTerms), (eos)
+  static constexpr int NV = D + 2;
+  struct Prim {
+    T rho, ir, v[D], p, E;
+  };
+  __device__ __forceinline__ static Prim prim(const T* q, T gamma) {
+    Prim s;
+    s.rho = q[0];
+    s.ir = T(1) / q[0];
+    T v2 = T(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      s.v[a] = q[1 + a] * s.ir;
+      v2 += s.v[a] * s.v[a];
+    }
+    s.E = q[D + 1];
+    s.p = (gamma - T(1)) * (s.E - T(0.5) * s.rho * v2);
+    return s;
+  }
+  __device__ __forceinline__ static void fluxn(const T* q, const Prim& s, const T* n, T* Fn) {
+    T vn = T(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) vn += s.v[a] * n[a];
+    Fn[0] = s.rho * vn;
+#pragma unroll
+    for (int k = 0; k < D; ++k) Fn[1 + k] = q[1 + k] * vn + s.p * n[k];
+    Fn[D + 1] = vn * (s.E + s.p);
+  }
+  // largest |eigenvalue| in unit direction n
+  __device__ __forceinline__ static T smax(const Prim& s, const T* n, T gamma, T /*ch*/) {
+    T vn = T(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) vn += s.v[a] * n[a];
+    return fabs(vn) + sqrt(gamma * s.p * s.ir);
+  }
+  // largest |eigenvalue| over all directions
+  __device__ __forceinline__ static T speed(const T* q, T gamma, T /*ch*/) {
+    Prim s = prim(q, gamma);
+    T v2 = T(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) v2 += s.v[a] * s.v[a];
+    return sqrt(v2) + sqrt(gamma * s.p * s.ir);
+  }
+  __device__ __forceinline__ static bool admissible(const double* q, double gamma) {
+    double rho = q[0], v2 = 0.0;
+    for (int a = 0; a < D; ++a) v2 += (q[1 + a] / rho) * (q[1 + a] / rho);
+    double p = (gamma - 1.0) * (q[D + 1] - 0.5 * rho * v2);
+    return rho > 0.0 && p > 0.0 && isfinite(p);
+  }
+};
+
+template <int D, typename T>
+struct Phys<D, 1, T> {  // ideal MHD + GLM, Eqs. (MHDTerms), (MHDeos), Gaussian units
+  static constexpr int NV = 9;
+  struct Prim {
+    T rho, ir, v[3], B[3], p, pt, E, vB, psi;
+  };
+  __device__ __forceinline__ static Prim prim(const T* q, T gamma) {
+    Prim s;
+    s.rho = q[0];
+    s.ir = T(1) / q[0];
+    T v2 = T(0), B2 = T(0), vB = T(0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      s.v[a] = q[1 + a] * s.ir;
+      s.B[a] = q[5 + a];
+      v2 += s.v[a] * s.v[a];
+      B2 += s.B[a] * s.B[a];
+      vB += s.v[a] * s.B[a];
+    }
+    s.E = q[4];
+    s.psi = q[8];
+    const T i8pi = T(0.039788735772973836);  // 1/(8 pi)
+    s.p = (gamma - T(1)) * (s.E - T(0.5) * s.rho * v2 - B2 * i8pi);
+    s.pt = s.p + B2 * i8pi;
+    s.vB = vB;
+    return s;
+  }
+  __device__ __forceinline__ static void fluxn_ch(const T* q, const Prim& s, const T* n, T* Fn, T ch) {
+    const T i4pi = T(0.079577471545947673);  // 1/(4 pi)
+    T vn = T(0), Bn = T(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      vn += s.v[a] * n[a];
+      Bn += s.B[a] * n[a];
+    }
+    Fn[0] = s.rho * vn;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) Fn[1 + k] = q[1 + k] * vn - s.B[k] * Bn * i4pi + (k < D ? s.pt * n[k < D ? k : 0] : T(0));
+    Fn[4] = vn * (s.E + s.pt) - Bn * s.vB * i4pi;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) Fn[5 + k] = vn * s.B[k] - Bn * s.v[k] + (k < D ? s.psi * n[k < D ? k : 0] : T(0));
+    Fn[8] = ch * ch * Bn;
+  }
+  __device__ __forceinline__ static T smax(const Prim& s, const T* n, T gamma, T ch) {
+    const T i4pi = T(0.079577471545947673);
+    T vn = T(0), Bn = T(0), B2 = T(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      vn += s.v[a] * n[a];
+      Bn += s.B[a] * n[a];
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) B2 += s.B[a] * s.B[a];
+    T a2 = gamma * s.p * s.ir, b2 = B2 * i4pi * s.ir, bn2 = Bn * Bn * i4pi * s.ir;
+    T sum = a2 + b2;
+    T disc = sum * sum - T(4) * a2 * bn2;
+    disc = disc > T(0) ? disc : T(0);
+    T cf = sqrt(T(0.5) * (sum + sqrt(disc)));
+    T sp = fabs(vn) + cf;
+    return sp > ch ? sp : ch;
+  }
+  __device__ __forceinline__ static T speed(const T* q, T gamma, T ch) {
+    const T i4pi = T(0.079577471545947673);
+    Prim s = prim(q, gamma);
+    T v2 = T(0), B2 = T(0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      v2 += s.v[a] * s.v[a];
+      B2 += s.B[a] * s.B[a];
+    }
+    T sp = sqrt(v2) + sqrt(gamma * s.p * s.ir + B2 * i4pi * s.ir);
+    return sp > ch ? sp : ch;
+  }
+  __device__ __forceinline__ static bool admissible(const double* q, double gamma) {
+    double rho = q[0];
+    double v2 = 0.0, B2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      v2 += (q[1 + a] / rho) * (q[1 + a] / rho);
+      B2 += q[5 + a] * q[5 + a];
+    }
+    double p = (gamma - 1.0) * (q[4] - 0.5 * rho * v2 - B2 * 0.039788735772973836);
+    return rho > 0.0 && p > 0.0 && isfinite(p);
+  }
+};
+
+template <int D, int PDE, typename T>
+__device__ __forceinline__ void flux_normal(const T* q, const typename Phys<D, PDE, T>::Prim& s, const T* n, T* Fn,
+                                            T ch) {
+  if constexpr (PDE == 0) {
+    Phys<D, 0, T>::fluxn(q, s, n, Fn);
+  } else {
+    Phys<D, 1, T>::fluxn_ch(q, s, n, Fn, ch);
+  }
+}
+
+// --------------------------------------------------- state access helpers
+template <class C>
+__device__ __forceinline__ void load_state(const KArgs<C>& a, int64_t i, typename C::T* q,
+                                           typename C::T* lo) {
+  using T = typename C::T;
+#pragma unroll
+  for (int v = 0; v < C::NV; ++v) {
+    if constexpr (std::is_same<T, double>::value) {
+      q[v] = a.Q[v * a.N + i];
+      lo[v] = 0.0;
+    } else {
+      q[v] = a.Qhi[v * a.N + i];
+      lo[v] = a.Qlo[v * a.N + i];
+    }
+  }
+}
+
+// dq = Q_j - Q_i, formed from the FP32 hi/lo split in mixed mode (the hi
+// difference of nearby values is exact, the lo part restores FP64 accuracy)
+template <class C>
+__device__ __forceinline__ void load_diff(const KArgs<C>& a, int64_t j, const typename C::T* qi,
+                                          const typename C::T* qilo, typename C::T* dq) {
+  using T = typename C::T;
+#pragma unroll
+  for (int v = 0; v < C::NV; ++v) {
+    if constexpr (std::is_same<T, double>::value) {
+      dq[v] = a.Q[v * a.N + j] - qi[v];
+    } else {
+      dq[v] = (__ldg(a.Qhi + v * a.N + j) - qi[v]) + (__ldg(a.Qlo + v * a.N + j) - qilo[v]);
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T pow4(T x) {
+  T y = x * x;
+  return y * y;
+}
+
+// ---------------------------------------------------------- rec + predictor
+template <class C, bool REC_ONLY>
+__global__ void __launch_bounds__(128) k_rec_pred(KArgs<C> a, CellTab<C> tb) {
+  using T = typename C::T;
+  constexpr int D = C::D, NV = C::NV, MC1 = C::MC1, NE1 = C::NE - 1, NS = C::NS;
+  using PH = Phys<D, C::PDE, T>;
+  const int64_t N = a.N;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (!REC_ONLY && a.reset_next && blockIdx.x == 0 && threadIdx.x == 0) a.dtmin[1 - a.cur] = 0x7ff0000000000000ull;
+  if (i >= N) return;
+
+  T qi[NV], qlo[NV];
+  load_state<C>(a, i, qi, qlo);
+
+  // ---- P_opt: c = R dQ over the central stencil (constant part is Q_i)
+  T c[MC1][NV];
+#pragma unroll
+  for (int l = 0; l < MC1; ++l)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) c[l][v] = T(0);
+#pragma unroll 4
+  for (int k = 0; k < NE1; ++k) {
+    const int64_t j = __ldg(a.sten + k * N + i);
+    T dq[NV];
+    load_diff<C>(a, j, qi, qlo, dq);
+#pragma unroll
+    for (int l = 0; l < MC1; ++l) {
+      const T r = __ldg(a.R + (int64_t)(l * NE1 + k) * N + i);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) c[l][v] += r * dq[v];
+    }
+  }
+
+  // ---- sectorial polynomials: g_s = B_s^{-1} dQ_sector
+  T g[NS][D][NV];
+  bool keep[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const int64_t j0 = __ldg(a.sec + (s * D) * N + i);
+    keep[s] = j0 >= 0;
+#pragma unroll
+    for (int e = 0; e < D; ++e)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) g[s][e][v] = T(0);
+    if (keep[s]) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const int64_t j = __ldg(a.sec + (s * D + k) * N + i);
+        T dq[NV];
+        load_diff<C>(a, j, qi, qlo, dq);
+#pragma unroll
+        for (int e = 0; e < D; ++e) {
+          const T b = __ldg(a.Binv + (int64_t)((s * D + e) * D + k) * N + i);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) g[s][e][v] += b * dq[v];
+        }
+      }
+    }
+  }
+
+  // ---- linear weights (normalised over kept stencils), P_0, indicators, weights
+  const int ns = a.nsec[i];
+  const T lden = T(1) / (a.lam0 + T(ns) * a.lams);
+  const T lam0 = a.lam0 * lden, lams = a.lams * lden;
+  const T ilam0 = T(1) / lam0;
+  T w[MC1][NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    T p0[MC1];
+#pragma unroll
+    for (int l = 0; l < MC1; ++l) {
+      T s = c[l][v];
+      if (l < D) {
+#pragma unroll
+        for (int sc = 0; sc < NS; ++sc) s -= (keep[sc] ? lams : T(0)) * g[sc][l < D ? l : 0][v];
+      }
+      p0[l] = s * ilam0;
+    }
+    T sig0 = T(0);
+#pragma unroll
+    for (int l = 0; l < MC1; ++l) {
+      T t = T(0);
+#pragma unroll
+      for (int m = 0; m < MC1; ++m) t += tb.Sig[l][m] * p0[m];
+      sig0 += p0[l] * t;
+    }
+    T sig[NS];
+    T smin = sig0;
+#pragma unroll
+    for (int sc = 0; sc < NS; ++sc) {
+      T s = T(0);
+#pragma unroll
+      for (int l = 0; l < D; ++l) {
+        T t = T(0);
+#pragma unroll
+        for (int m = 0; m < D; ++m) t += tb.Sig[l][m] * g[sc][m][v];
+        s += g[sc][l][v] * t;
+      }
+      sig[sc] = s;
+      if (keep[sc] && s < smin) smin = s;
+    }
+    // omega_s proportional to lambda_s / (sigma_s + eps)^4, scaled by
+    // (sigma_min + eps)^4 so that nothing overflows in FP32
+    const T num = smin + a.eps;
+    T w0 = a.linw ? lam0 : lam0 * pow4(num / (sig0 + a.eps));
+    T ws[NS];
+    T tot = w0;
+#pragma unroll
+    for (int sc = 0; sc < NS; ++sc) {
+      ws[sc] = keep[sc] ? (a.linw ? lams : lams * pow4(num / (sig[sc] + a.eps))) : T(0);
+      tot += ws[sc];
+    }
+    const T itot = T(1) / tot;
+    w0 *= itot;
+#pragma unroll
+    for (int sc = 0; sc < NS; ++sc) ws[sc] *= itot;
+#pragma unroll
+    for (int l = 0; l < MC1; ++l) {
+      T s = w0 * p0[l];
+      if (l < D) {
+#pragma unroll
+        for (int sc = 0; sc < NS; ++sc) s += ws[sc] * g[sc][l < D ? l : 0][v];
+      }
+      w[l][v] = s;
+    }
+  }
+
+  if constexpr (REC_ONLY) {
+    // reconstruction values at the lattice nodes, caller's cell order
+    const int64_t u = a.perm[i];
+#pragma unroll
+    for (int n = 0; n < C::L0; ++n)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        T s = qi[v] + qlo[v];
+#pragma unroll
+        for (int l = 0; l < MC1; ++l) s += tb.E[n][l] * w[l][v];
+        a.out[(u * C::MC + n) * NV + v] = (double)s;
+      }
+    return;
+  } else {
+    constexpr int L = C::L, L0 = C::L0, L1 = C::L1;
+    const T dt = (T)dt_of(a.dt_fixed, a.cfl, a.dtmin, a.cur);
+    T J[D][D];
+#pragma unroll
+    for (int e = 0; e < D; ++e)
+#pragma unroll
+      for (int m = 0; m < D; ++m) J[e][m] = __ldg(a.Jinv + (e * D + m) * N + i);
+
+    // known degrees of freedom: w at the tau = 0 nodes (written out at once);
+    // base = C0 q0 - dt sum_e P_e[:, tau=0 nodes] G_e(q0) is fixed over the
+    // iterations; the initial guess of the unknown nodes is w at their
+    // spatial positions, which is C0 q0.
+    T base[L1][NV], q1[L1][NV];
+#pragma unroll
+    for (int k = 0; k < L1; ++k)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        base[k][v] = T(0);
+        q1[k][v] = T(0);
+      }
+#pragma unroll
+    for (int n = 0; n < L0; ++n) {
+      T q0[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        T s = qi[v] + qlo[v];
+#pragma unroll
+        for (int l = 0; l < MC1; ++l) s += tb.E[n][l] * w[l][v];
+        q0[v] = s;
+        a.qhat[(int64_t)(n * NV + v) * N + i] = s;
+      }
+      typename PH::Prim pr = PH::prim(q0, a.gamma);
+      T Ge[D][NV];
+#pragma unroll
+      for (int e = 0; e < D; ++e) flux_normal<D, C::PDE, T>(q0, pr, J[e], Ge[e], a.ch);
+#pragma unroll
+      for (int k = 0; k < L1; ++k)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const T cq = tb.C0[k][n] * q0[v];
+          T s = T(0);
+#pragma unroll
+          for (int e = 0; e < D; ++e) s += tb.P[e][k][n] * Ge[e][v];
+          base[k][v] += cq - dt * s;
+          q1[k][v] += cq;
+        }
+    }
+    // Picard iterations of Eq. (CGfinal)
+    for (int it = 0; it < a.niter; ++it) {
+      T nq[L1][NV];
+#pragma unroll
+      for (int k = 0; k < L1; ++k)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) nq[k][v] = base[k][v];
+#pragma unroll
+      for (int l = 0; l < L1; ++l) {
+        typename PH::Prim pr = PH::prim(q1[l], a.gamma);
+        T Ge[D][NV];
+#pragma unroll
+        for (int e = 0; e < D; ++e) flux_normal<D, C::PDE, T>(q1[l], pr, J[e], Ge[e], a.ch);
+#pragma unroll
+        for (int k = 0; k < L1; ++k)
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            T s = T(0);
+#pragma unroll
+            for (int e = 0; e < D; ++e) s += tb.P[e][k][L0 + l] * Ge[e][v];
+            nq[k][v] -= dt * s;
+          }
+      }
+#pragma unroll
+      for (int k = 0; k < L1; ++k)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) q1[k][v] = nq[k][v];
+    }
+#pragma unroll
+    for (int k = 0; k < L1; ++k)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) a.qhat[(int64_t)((L0 + k) * NV + v) * N + i] = q1[k][v];
+  }
+}
+
+// ----------------------------------------------------------------- fluxes
+template <class C>
+__global__ void __launch_bounds__(128) k_flux(KArgs<C> a, int use_smem) {
+  using T = typename C::T;
+  constexpr int D = C::D, NV = C::NV, L = C::L, NQS = C::NQS, NQT = C::NQT, CH = C::CH;
+  using PH = Phys<D, C::PDE, T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const T* tab = a.ftab;
+  if (use_smem) {
+    T* st = reinterpret_cast<T*>(smem_raw);
+    for (int k = threadIdx.x; k < C::TABN + NQS + NQT; k += blockDim.x) st[k] = a.ftab[k];
+    __syncthreads();
+    tab = st;
+  }
+  const T* wq = tab + C::TABN;
+  const T* wt = wq + NQS;
+  const T dt = (T)dt_of(a.dt_fixed, a.cfl, a.dtmin, a.cur);
+  const int64_t N = a.N, F = a.F;
+  for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < F; f += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t Lc = a.fL[f];
+    const int64_t Rc = a.fR[f];
+    const T* tL = tab + (int)a.codeL[f] * (NQT * NQS * L);
+    const T* tR = tab + (int)a.codeR[f] * (NQT * NQS * L);
+    T n[D];
+#pragma unroll
+    for (int e = 0; e < D; ++e) n[e] = a.fn[e * F + f];
+    const T area = a.farea[f];
+    T acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = T(0);
+#pragma unroll 1
+    for (int t0 = 0; t0 < NQT; t0 += CH) {
+      T trL[CH][NQS][NV], trR[CH][NQS][NV];
+#pragma unroll
+      for (int tt = 0; tt < CH; ++tt)
+#pragma unroll
+        for (int q = 0; q < NQS; ++q)
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            trL[tt][q][v] = T(0);
+            trR[tt][q][v] = T(0);
+          }
+#pragma unroll 2
+      for (int l = 0; l < L; ++l) {
+        T ql[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) ql[v] = __ldg(a.qhat + (int64_t)(l * NV + v) * N + Lc);
+#pragma unroll
+        for (int tt = 0; tt < CH; ++tt)
+#pragma unroll
+          for (int q = 0; q < NQS; ++q) {
+            const T th = tL[((t0 + tt) * NQS + q) * L + l];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) trL[tt][q][v] += th * ql[v];
+          }
+      }
+      if (Rc >= 0) {
+#pragma unroll 2
+        for (int l = 0; l < L; ++l) {
+          T ql[NV];
+#pragma unroll
+          for (int v = 0; v < NV; ++v) ql[v] = __ldg(a.qhat + (int64_t)(l * NV + v) * N + Rc);
+#pragma unroll
+          for (int tt = 0; tt < CH; ++tt)
+#pragma unroll
+            for (int q = 0; q < NQS; ++q) {
+              const T th = tR[((t0 + tt) * NQS + q) * L + l];
+#pragma unroll
+              for (int v = 0; v < NV; ++v) trR[tt][q][v] += th * ql[v];
+            }
+        }
+      } else {
+#pragma unroll
+        for (int tt = 0; tt < CH; ++tt)
+#pragma unroll
+          for (int q = 0; q < NQS; ++q)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) trR[tt][q][v] = trL[tt][q][v];  // transmissive
+      }
+#pragma unroll
+      for (int tt = 0; tt < CH; ++tt)
+#pragma unroll
+        for (int q = 0; q < NQS; ++q) {
+          typename PH::Prim pl = PH::prim(trL[tt][q], a.gamma);
+          typename PH::Prim pr = PH::prim(trR[tt][q], a.gamma);
+          T fl[NV], fr[NV];
+          flux_normal<D, C::PDE, T>(trL[tt][q], pl, n, fl, a.ch);
+          flux_normal<D, C::PDE, T>(trR[tt][q], pr, n, fr, a.ch);
+          T sl = PH::smax(pl, n, a.gamma, a.ch), sr = PH::smax(pr, n, a.gamma, a.ch);
+          const T s = sl > sr ? sl : sr;
+          const T wgt = wq[q] * wt[t0 + tt];
+#pragma unroll
+          for (int v = 0; v < NV; ++v)
+            acc[v] += wgt * (T(0.5) * (fl[v] + fr[v]) - T(0.5) * s * (trR[tt][q][v] - trL[tt][q][v]));
+        }
+    }
+    const T scale = dt * area;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) a.G[v * F + f] = scale * acc[v];
+  }
+}
+
+// ------------------------------------------------------------ block minimum
+__device__ __forceinline__ void block_min_atomic(double val, unsigned long long* target) {
+  __shared__ double red[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    double other = __shfl_xor_sync(0xffffffffu, val, o);
+    val = other < val ? other : val;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = val;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    val = lane < nw ? red[lane] : __longlong_as_double(0x7ff0000000000000ll);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      double other = __shfl_xor_sync(0xffffffffu, val, o);
+      val = other < val ? other : val;
+    }
+    if (lane == 0 && val > 0.0) atomicMin(target, (unsigned long long)__double_as_longlong(val));
+  }
+}
+
+// ------------------------------------------------------------------ update
+template <class C>
+__global__ void __launch_bounds__(256) k_update(KArgs<C> a) {
+  using T = typename C::T;
+  constexpr int D = C::D, NV = C::NV;
+  using PH = Phys<D, C::PDE, T>;
+  const int64_t N = a.N, F = a.F;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double ratio = __longlong_as_double(0x7ff0000000000000ll);
+  if (i < N) {
+    double acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+#pragma unroll
+    for (int k = 0; k <= D; ++k) {
+      const int cf = a.cellface[k * N + i];
+      const int64_t f = cf >> 1;
+      const double sgn = (cf & 1) ? -1.0 : 1.0;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[v] += sgn * (double)a.G[v * F + f];
+    }
+    const double iv = a.invvol[i];
+    double q[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      q[v] = a.Q[v * N + i] - iv * acc[v];
+      a.Q[v * N + i] = q[v];
+    }
+    T qt[NV];
+    if constexpr (std::is_same<T, float>::value) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const float hi = (float)q[v];
+        a.Qhi[v * N + i] = hi;
+        a.Qlo[v * N + i] = (float)(q[v] - (double)hi);
+        qt[v] = hi;
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) qt[v] = q[v];
+    }
+    if (!PH::admissible(q, (double)a.gamma)) atomicOr(a.status, 1);
+    const T sp = PH::speed(qt, a.gamma, a.ch);
+    ratio = a.hsize[i] / (double)sp;
+  }
+  block_min_atomic(ratio, a.dtmin + (1 - a.cur));
+  if (blockIdx.x == 0 && threadIdx.x == 0) *a.time += dt_of(a.dt_fixed, a.cfl, a.dtmin, a.cur);
+}
+
+template <class C>
+__global__ void __launch_bounds__(256) k_stable_dt(KArgs<C> a, int slot) {
+  using T = typename C::T;
+  using PH = Phys<C::D, C::PDE, T>;
+  const int64_t N = a.N;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double ratio = __longlong_as_double(0x7ff0000000000000ll);
+  if (i < N) {
+    T q[C::NV];
+#pragma unroll
+    for (int v = 0; v < C::NV; ++v) {
+      if constexpr (std::is_same<T, float>::value) q[v] = a.Qhi[v * N + i];
+      else q[v] = a.Q[v * N + i];
+    }
+    ratio = a.hsize[i] / (double)PH::speed(q, a.gamma, a.ch);
+  }
+  block_min_atomic(ratio, a.dtmin + slot);
+}
+
+template <class C>
+__global__ void k_set_state(KArgs<C> a, const double* user) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.N) return;
+  const int64_t u = a.perm[i];
+#pragma unroll
+  for (int v = 0; v < C::NV; ++v) {
+    const double q = user[u * C::NV + v];
+    a.Q[v * a.N + i] = q;
+    if constexpr (std::is_same<typename C::T, float>::value) {
+      const float hi = (float)q;
+      a.Qhi[v * a.N + i] = hi;
+      a.Qlo[v * a.N + i] = (float)(q - (double)hi);
+    }
+  }
+}
+
+template <class C>
+__global__ void k_get_state(KArgs<C> a, double* user) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.N) return;
+  const int64_t u = a.perm[i];
+#pragma unroll
+  for (int v = 0; v < C::NV; ++v) user[u * C::NV + v] = a.Q[v * a.N + i];
+}
+
+template <class C>
+__global__ void k_qhat_out(KArgs<C> a, double* user) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.N) return;
+  const int64_t u = a.perm[i];
+  for (int l = 0; l < C::L; ++l)
+#pragma unroll
+    for (int v = 0; v < C::NV; ++v)
+      user[(u * C::L + l) * C::NV + v] = (double)a.qhat[(int64_t)(l * C::NV + v) * a.N + i];
+}
+
+// ------------------------------------------------------------- host side
+template <class C>
+class OpsImpl final : public Ops {
+ public:
+  using T = typename C::T;
+  explicit OpsImpl(const RefElem& re) {
+    std::memset(&tab_, 0, sizeof(tab_));
+    for (int n = 0; n < C::L0; ++n)
+      for (int l = 0; l < C::MC1; ++l) tab_.E[n][l] = (T)re.E[n * C::MC1 + l];
+    for (int l = 0; l < C::MC1; ++l)
+      for (int m = 0; m < C::MC1; ++m) tab_.Sig[l][m] = (T)re.Sigma[l * C::MC1 + m];
+    for (int k = 0; k < C::L1; ++k)
+      for (int n = 0; n < C::L0; ++n) tab_.C0[k][n] = (T)re.C0[k * C::L0 + n];
+    for (int e = 0; e < C::D; ++e)
+      for (int k = 0; k < C::L1; ++k)
+        for (int l = 0; l < C::L; ++l) tab_.P[e][k][l] = (T)re.P[((size_t)e * C::L1 + k) * C::L + l];
+    ftab_.resize(C::TABN + C::NQS + C::NQT);
+    for (int k = 0; k < C::TABN; ++k) ftab_[k] = (T)re.ftab[k];
+    for (int q = 0; q < C::NQS; ++q) ftab_[C::TABN + q] = (T)re.wq[q];
+    for (int t = 0; t < C::NQT; ++t) ftab_[C::TABN + C::NQS + t] = (T)re.wt[t];
+  }
+  size_t table_bytes() const override { return ftab_.size() * sizeof(T); }
+  void pack_tables(void* host) const override { std::memcpy(host, ftab_.data(), table_bytes()); }
+  size_t elem_size() const override { return sizeof(T); }
+
+  KArgs<C> args(const DevState& s, const PhysParams& ph, DtArgs dt) const {
+    KArgs<C> a;
+    std::memset(&a, 0, sizeof(a));
+    a.N = s.N;
+    a.F = s.F;
+    a.Q = s.Q;
+    a.Qhi = s.Qhi;
+    a.Qlo = s.Qlo;
+    a.perm = s.perm;
+    a.sten = s.sten;
+    a.R = (const T*)s.R;
+    a.sec = s.sec;
+    a.Binv = (const T*)s.Binv;
+    a.nsec = s.nsec;
+    a.Jinv = (const T*)s.Jinv;
+    a.qhat = (T*)s.qhat;
+    a.fL = s.fL;
+    a.fR = s.fR;
+    a.codeL = s.codeL;
+    a.codeR = s.codeR;
+    a.fn = (const T*)s.fn;
+    a.farea = (const T*)s.farea;
+    a.G = (T*)s.G;
+    a.ftab = (const T*)s.ftab;
+    a.cellface = s.cellface;
+    a.invvol = s.invvol;
+    a.hsize = s.hsize;
+    a.dtmin = s.dtmin;
+    a.time = s.time;
+    a.status = s.status;
+    a.out = nullptr;
+    a.gamma = (T)ph.gamma;
+    a.ch = (T)ph.ch;
+    a.eps = (T)ph.eps;
+    a.lam0 = (T)ph.lam0;
+    a.lams = (T)ph.lams;
+    a.niter = ph.niter;
+    a.linw = ph.linear_weights;
+    a.dt_fixed = dt.fixed;
+    a.cfl = dt.cfl;
+    a.cur = dt.cur;
+    a.reset_next = 1;
+    return a;
+  }
+
+  static unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+  cudaError_t rec_pred(const DevState& s, const PhysParams& ph, DtArgs dt, cudaStream_t st) override {
+    KArgs<C> a = args(s, ph, dt);
+    if (dt.cur < 0) {  // diagnostic call: keep the next-step bound untouched
+      a.cur = 0;
+      a.reset_next = 0;
+    }
+    k_rec_pred<C, false><<<nblk(s.N, 128), 128, 0, st>>>(a, tab_);
+    return cudaGetLastError();
+  }
+  cudaError_t reconstruct(const DevState& s, const PhysParams& ph, double* out, cudaStream_t st) override {
+    KArgs<C> a = args(s, ph, DtArgs());
+    a.out = out;
+    a.reset_next = 0;
+    k_rec_pred<C, true><<<nblk(s.N, 128), 128, 0, st>>>(a, tab_);
+    return cudaGetLastError();
+  }
+  cudaError_t prepare() override {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const size_t smem = table_bytes();
+    use_smem_ = smem <= 100 * 1024 ? 1 : 0;
+    if (use_smem_) {
+      e = cudaFuncSetAttribute(k_flux<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_flux<C>, 128, use_smem_ ? smem : 0);
+    if (e != cudaSuccess) return e;
+    int nsm = 0;
+    e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    max_blocks_ = (int64_t)std::max(1, nb) * nsm;
+    return cudaSuccess;
+  }
+  cudaError_t flux(const DevState& s, const PhysParams& ph, DtArgs dt, cudaStream_t st) override {
+    KArgs<C> a = args(s, ph, dt);
+    if (dt.cur < 0) a.cur = 0;
+    const size_t smem = use_smem_ ? table_bytes() : 0;
+    unsigned nb = (unsigned)std::min<int64_t>(nblk(s.F, 128), max_blocks_);
+    k_flux<C><<<nb, 128, smem, st>>>(a, use_smem_);
+    return cudaGetLastError();
+  }
+  cudaError_t update(const DevState& s, const PhysParams& ph, DtArgs dt, cudaStream_t st) override {
+    KArgs<C> a = args(s, ph, dt);
+    k_update<C><<<nblk(s.N, 256), 256, 0, st>>>(a);
+    return cudaGetLastError();
+  }
+  cudaError_t stable_dt(const DevState& s, const PhysParams& ph, int slot, cudaStream_t st) override {
+    KArgs<C> a = args(s, ph, DtArgs());
+    k_stable_dt<C><<<nblk(s.N, 256), 256, 0, st>>>(a, slot);
+    return cudaGetLastError();
+  }
+  cudaError_t set_state(const DevState& s, const double* user, cudaStream_t st) override {
+    KArgs<C> a = args(s, PhysParams(), DtArgs());
+    k_set_state<C><<<nblk(s.N, 256), 256, 0, st>>>(a, user);
+    return cudaGetLastError();
+  }
+  cudaError_t get_state(const DevState& s, double* user, cudaStream_t st) override {
+    KArgs<C> a = args(s, PhysParams(), DtArgs());
+    k_get_state<C><<<nblk(s.N, 256), 256, 0, st>>>(a, user);
+    return cudaGetLastError();
+  }
+  cudaError_t qhat_out(const DevState& s, double* user, cudaStream_t st) override {
+    KArgs<C> a = args(s, PhysParams(), DtArgs());
+    k_qhat_out<C><<<nblk(s.N, 256), 256, 0, st>>>(a, user);
+    return cudaGetLastError();
+  }
+
+ private:
+  CellTab<C> tab_;
+  std::vector<T> ftab_;
+  int use_smem_ = 0;
+  int64_t max_blocks_ = 152;
+};
+
+}  // namespace cw

@@ -1,0 +1,82 @@
+// Host-side interface to the per-configuration CUDA kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <memory>
+#include <string>
+
+#include "refelem.h"
+
+namespace cw {
+
+// Device buffers of one solver (types are erased: T = float or double).
+struct DevState {
+  int64_t N = 0, F = 0;
+  int nv = 0;
+  double* Q = nullptr;          // nv x N (FP64 always)
+  float* Qhi = nullptr;         // nv x N (FP32 mode)
+  float* Qlo = nullptr;         // nv x N (FP32 mode)
+  const int32_t* perm = nullptr;  // internal -> user
+  const int32_t* sten = nullptr;  // (ne-1) x N
+  const void* R = nullptr;        // (Mc-1)(ne-1) x N
+  const int32_t* sec = nullptr;   // (d+1) d x N
+  const void* Binv = nullptr;     // (d+1) d d x N
+  const uint8_t* nsec = nullptr;  // N
+  const void* Jinv = nullptr;     // d d x N
+  void* qhat = nullptr;           // L nv x N
+  const int32_t* fL = nullptr;
+  const int32_t* fR = nullptr;
+  const uint8_t* codeL = nullptr;
+  const uint8_t* codeR = nullptr;
+  const void* fn = nullptr;       // d x F
+  const void* farea = nullptr;    // F
+  void* G = nullptr;              // nv x F
+  const void* ftab = nullptr;     // face basis table + wq + wt
+  const int32_t* cellface = nullptr;  // (d+1) x N
+  const double* invvol = nullptr;     // N
+  const double* hsize = nullptr;      // N
+  unsigned long long* dtmin = nullptr;  // 2 slots (double bits)
+  double* time = nullptr;
+  int* status = nullptr;
+  double* stage = nullptr;        // N x nv (user-order staging)
+};
+
+struct PhysParams {
+  double gamma = 1.4, ch = 2.0;
+  double eps = 1e-14, lam0 = 1e5, lams = 1.0;
+  int niter = 2, linear_weights = 0;
+};
+
+// Time step source: fixed > 0, else cfl * (min h/lambda) read from dtmin[cur].
+struct DtArgs {
+  double fixed = 0.0;
+  double cfl = 0.5;
+  int cur = 0;  // slot read; the other slot is reset and receives the next bound
+};
+
+class Ops {
+ public:
+  virtual ~Ops() {}
+  virtual size_t table_bytes() const = 0;
+  virtual void pack_tables(void* host) const = 0;  // face table (device copy made by caller)
+  virtual size_t elem_size() const = 0;
+  // Kernel attributes and launch shapes for the current device; call before
+  // the first launch (and before any stream capture).
+  virtual cudaError_t prepare() = 0;
+  virtual cudaError_t rec_pred(const DevState& s, const PhysParams& ph, DtArgs dt, cudaStream_t st) = 0;
+  virtual cudaError_t reconstruct(const DevState& s, const PhysParams& ph, double* out_user, cudaStream_t st) = 0;
+  virtual cudaError_t flux(const DevState& s, const PhysParams& ph, DtArgs dt, cudaStream_t st) = 0;
+  virtual cudaError_t update(const DevState& s, const PhysParams& ph, DtArgs dt, cudaStream_t st) = 0;
+  virtual cudaError_t stable_dt(const DevState& s, const PhysParams& ph, int slot, cudaStream_t st) = 0;
+  virtual cudaError_t set_state(const DevState& s, const double* user_dev, cudaStream_t st) = 0;
+  virtual cudaError_t get_state(const DevState& s, double* user_dev, cudaStream_t st) = 0;
+  virtual cudaError_t qhat_out(const DevState& s, double* user_dev, cudaStream_t st) = 0;
+};
+
+// Factories (one per translation unit); nullptr if (M, precision) is not built.
+std::unique_ptr<Ops> make_ops_euler2(int M, int fp32, const RefElem& re);
+std::unique_ptr<Ops> make_ops_euler3(int M, int fp32, const RefElem& re);
+std::unique_ptr<Ops> make_ops_mhd2(int M, int fp32, const RefElem& re);
+
+}  // namespace cw

@@ -1,0 +1,120 @@
+"""Host-side checks of the C ABI (no GPU): the library builds, loads and
+exports every entry point declared in include/cweno.h; mesh validation; the
+stencils chosen by the library's setup equal the oracle's."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def cw():
+    import paper_1612_09335_gb300 as pkg
+    pkg.build()
+    from paper_1612_09335_gb300 import binding
+    return binding
+
+
+def declared_functions():
+    txt = open(os.path.join(ROOT, "include", "cweno.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"\b((?:cweno|ader|serve)_\w+)\s*\(", txt)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol(cw):
+    L = cw.lib()
+    names = declared_functions()
+    assert len(names) >= 25
+    for n in names:
+        assert hasattr(L, n), n
+    bound = {s[0] for s in cw.SIGNATURES}
+    assert set(names) == bound
+
+
+def test_default_params_are_the_papers(cw):
+    p = cw.cweno_default_params(2, cw.EULER)
+    assert (p.eps, p.r, p.lambda0, p.lambda_s, p.gamma, p.cfl) == (1e-14, 4.0, 1e5, 1.0, 1.4, 0.5)
+    p3 = cw.cweno_default_params(3, cw.EULER)
+    assert abs(p3.cfl - 1 / 3) < 1e-15
+    pm = cw.cweno_default_params(2, cw.MHD_GLM)
+    assert abs(pm.gamma - 5 / 3) < 1e-15 and pm.c_h == 2.0
+    assert cw.cweno_nvars(2, cw.EULER) == 4 and cw.cweno_nvars(3, cw.EULER) == 5 and cw.cweno_nvars(2, cw.MHD_GLM) == 9
+
+
+def test_mesh_validation_errors(cw, wl):
+    m = wl.tri_mesh(4, jitter=0.1)
+    bad = m.cells.copy()
+    bad[3] = bad[3][[0, 2, 1]]  # clockwise cell
+    with pytest.raises(cw.CwenoError) as e:
+        cw.Mesh(2, m.xyz, bad, m.period)
+    assert e.value.code == cw.EDEGENERATE
+    bad = m.cells.copy()
+    bad[0, 0] = 10 ** 6
+    with pytest.raises(cw.CwenoError) as e:
+        cw.Mesh(2, m.xyz, bad, m.period)
+    assert e.value.code == cw.EINVAL
+    with pytest.raises(cw.CwenoError) as e:
+        cw.Mesh(4, m.xyz, m.cells, None)
+    assert e.value.code == cw.EINVAL
+    # a face shared by three cells
+    cells = np.array([[0, 1, 2], [1, 0, 3], [0, 1, 4]], dtype=np.int32)
+    xyz = np.array([[0, 0], [1, 0], [0, 1], [0.5, -1], [0.2, 2.0]])
+    with pytest.raises(cw.CwenoError) as e:
+        cw.Mesh(2, xyz, cells, None)
+    assert e.value.code in (cw.EINVAL, cw.EDEGENERATE)
+
+
+def test_mesh_counts(cw, wl):
+    m = wl.tri_mesh(6, periodic=True)
+    info = cw.Mesh.from_workload(m).info()
+    assert info == dict(ncells=72, nfaces=108, nboundary=0)
+    m = wl.tri_mesh(6, periodic=False)
+    info = cw.Mesh.from_workload(m).info()
+    assert info["nboundary"] == 24 and info["nfaces"] == (3 * 72 + 24) // 2
+    m = wl.tet_mesh(3, periodic=True)
+    info = cw.Mesh.from_workload(m).info()
+    assert info == dict(ncells=162, nfaces=324, nboundary=0)
+
+
+@pytest.mark.parametrize("case", [("tri", 10, True, 2), ("tri", 10, True, 3), ("tri", 10, True, 4),
+                                  ("tri", 8, False, 3), ("tri", 8, False, 4), ("tet", 5, True, 2),
+                                  ("tet", 5, True, 3), ("tet", 4, False, 3)])
+def test_stencils_match_oracle(cw, orc, wl, case):
+    kind, n, per, order = case
+    m = wl.tri_mesh(n, periodic=per, jitter=0.2, seed=17) if kind == "tri" else \
+        wl.tet_mesh(n, periodic=per, jitter=0.15, seed=17)
+    S0, sec = cw.Mesh.from_workload(m).stencils(order)
+    o = orc.Oracle(m, order)
+    for c in range(0, m.nc, max(1, m.nc // 40)):
+        s0o, seco = o.stencil(c)
+        assert S0[c, 0] == c
+        assert set(S0[c].tolist()) == set(s0o.tolist())
+        for s in range(m.dim + 1):
+            assert set(sec[c, s].tolist()) == set(seco[s].tolist()), (c, s)
+
+
+def test_stencils_unjittered_ties_match_oracle(cw, orc, wl):
+    """Exact distance ties (regular mesh) are broken the same way."""
+    m = wl.tri_mesh(8, periodic=True, jitter=0.0)
+    S0, sec = cw.Mesh.from_workload(m).stencils(3)
+    o = orc.Oracle(m, 3)
+    for c in range(0, m.nc, 5):
+        s0o, seco = o.stencil(c)
+        assert set(S0[c].tolist()) == set(s0o.tolist())
+        for s in range(3):
+            assert set(sec[c, s].tolist()) == set(seco[s].tolist())
+
+
+def test_product_path_refuses_without_gpu_or_library(cw, wl):
+    """Without a usable GPU, setup fails loudly (ECUDA); there is no CPU path."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    m = wl.tri_mesh(6)
+    with pytest.raises(cw.CwenoError) as e:
+        cw.Solver(cw.Mesh.from_workload(m), 3)
+    assert e.value.code == cw.ECUDA
