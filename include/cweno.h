@@ -60,7 +60,7 @@ typedef struct cweno_server cweno_server;
  * eps = 1e-14, r = 4, lambda_0 = 1e5, lambda_s = 1 (Sec. 2.1, after Eq.
  * weights2; the lambdas are normalised to sum 1 over the kept stencils),
  * CFL = 1/d (Eq. timestep), gamma = 1.4 (Euler) or 5/3 (MHD), c_h = 2,
- * Picard iterations of Eq. (CGfinal) = M + 1. */
+ * Picard iterations of Eq. (CGfinal) = M + 1, positivity scaling on. */
 typedef struct {
   double eps;          /* epsilon of Eq. (weights2) */
   double r;            /* exponent r of Eq. (weights2); must be 4 */
@@ -71,6 +71,11 @@ typedef struct {
   double cfl;          /* CFL number used when ader_cweno_step(dt <= 0) */
   int picard_iters;    /* iterations of Eq. (CGfinal); <= 0 -> M + 1 */
   int linear_weights;  /* test mode: omega := lambda (no indicators) */
+  int positivity;      /* 1 (default): scale w toward the cell average where
+                          density or pressure would fall below 1e-10 of their
+                          cell-average values at a lattice node (Zhang & Shu
+                          scaling; not part of the paper, inactive wherever the
+                          reconstruction is admissible); 0: the paper's scheme */
 } cweno_params;
 
 /* Fill *p with the paper's defaults for dimension `dim` and `pde`. */

@@ -94,15 +94,15 @@ def _i(a):
 
 def default_params(dim: int = 2, pde: int = EULER, cfl: float | None = None, order: int = 3,
                    gamma: float | None = None, ch: float = 2.0, linear_weights: bool = False,
-                   niter: int | None = None) -> np.ndarray:
-    """[eps, r, lambda0, lambda_s, gamma, c_h, cfl, picard iterations, linear_weights]."""
+                   niter: int | None = None, positivity: bool = True) -> np.ndarray:
+    """[eps, r, lambda0, lambda_s, gamma, c_h, cfl, picard iterations, linear_weights, positivity]."""
     if gamma is None:
         gamma = 1.4 if pde == EULER else 5.0 / 3.0
     if cfl is None:
         cfl = 0.5 if dim == 2 else 1.0 / 3.0
     M = order - 1
     return np.array([1e-14, 4.0, 1e5, 1.0, gamma, ch, cfl, float(M + 1 if niter is None else niter),
-                     1.0 if linear_weights else 0.0])
+                     1.0 if linear_weights else 0.0, 1.0 if positivity else 0.0])
 
 
 class OracleMesh:

@@ -44,6 +44,12 @@
 //     functions of the tau > 0 nodes; M+1 Picard iterations from w(xi);
 //   * Rusanov s_max per quadrature point, max over both sides;
 //   * MHD EOS p = (gamma-1)(rho E - rho|v|^2/2 - |B|^2/(8 pi)).
+//   * s_max and the time-step speed take sqrt(max(0, .)) of the sound speed.
+// Addition not in the paper (switchable, on by default): a positivity
+// preserving scaling of the reconstruction toward the cell average at the
+// lattice nodes, first for the density, then for the pressure (the scaling
+// limiter of Zhang & Shu, J. Comput. Phys. 229 (2010) 3091).  Where every
+// node is admissible it leaves w untouched.
 // ============================================================================
 #include <algorithm>
 #include <array>
@@ -443,7 +449,7 @@ enum { PDE_EULER = 0, PDE_MHD = 1 };
 
 struct Params {
   double eps, r, lam0, lams, gamma, ch, cfl;
-  int niter, linear_weights;
+  int niter, linear_weights, positivity;
 };
 
 const double PI = 3.14159265358979323846;
@@ -495,7 +501,7 @@ double max_speed_normal(int pde, int d, const Params& P, const double* q, const 
       v2 += vk * vk;
     }
     double p = (P.gamma - 1.0) * (q[d + 1] - 0.5 * rho * v2);
-    double c = std::sqrt(P.gamma * p / rho);
+    double c = std::sqrt(std::max(0.0, P.gamma * p / rho));
     return std::fabs(vn) + c;
   }
   double rho = q[0];
@@ -513,7 +519,7 @@ double max_speed_normal(int pde, int d, const Params& P, const double* q, const 
   double b2 = B2 / (4.0 * PI * rho);
   double bn2 = Bn * Bn / (4.0 * PI * rho);
   double cf2 = 0.5 * (a2 + b2 + std::sqrt(std::max(0.0, (a2 + b2) * (a2 + b2) - 4.0 * a2 * bn2)));
-  return std::max(std::fabs(vn) + std::sqrt(cf2), P.ch);
+  return std::max(std::fabs(vn) + std::sqrt(std::max(0.0, cf2)), P.ch);
 }
 
 // Largest |eigenvalue| over all directions (for the time step).
@@ -523,7 +529,7 @@ double max_speed(int pde, int d, const Params& P, const double* q) {
     double v2 = 0.0;
     for (int k = 0; k < d; ++k) v2 += (q[1 + k] / rho) * (q[1 + k] / rho);
     double p = (P.gamma - 1.0) * (q[d + 1] - 0.5 * rho * v2);
-    return std::sqrt(v2) + std::sqrt(P.gamma * p / rho);
+    return std::sqrt(v2) + std::sqrt(std::max(0.0, P.gamma * p / rho));
   }
   double v[3] = {q[1] / rho, q[2] / rho, q[3] / rho};
   double B[3] = {q[5], q[6], q[7]};
@@ -532,7 +538,20 @@ double max_speed(int pde, int d, const Params& P, const double* q) {
   double p = (P.gamma - 1.0) * (q[4] - 0.5 * rho * v2 - B2 / (8.0 * PI));
   double a2 = P.gamma * p / rho;
   double b2 = B2 / (4.0 * PI * rho);
-  return std::max(std::sqrt(v2) + std::sqrt(a2 + b2), P.ch);
+  return std::max(std::sqrt(v2) + std::sqrt(std::max(0.0, a2 + b2)), P.ch);
+}
+
+// Pressure from the conserved state, Eq. (eos) / Eq. (MHDeos).
+double pressure(int pde, int d, const Params& P, const double* q) {
+  double rho = q[0];
+  if (pde == PDE_EULER) {
+    double m2 = 0.0;
+    for (int k = 0; k < d; ++k) m2 += q[1 + k] * q[1 + k];
+    return (P.gamma - 1.0) * (q[d + 1] - 0.5 * m2 / rho);
+  }
+  double m2 = q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+  double B2 = q[5] * q[5] + q[6] * q[6] + q[7] * q[7];
+  return (P.gamma - 1.0) * (q[4] - 0.5 * m2 / rho - B2 / (8.0 * PI));
 }
 
 // --------------------------------------------------------------------- mesh
@@ -1016,6 +1035,39 @@ bool reconstruct_cell(OSolver& S, const double* Q, long i, RecOut& out, std::str
       out.sigma[s * nu + v] = sig[s];
     }
   }
+  if (S.P.positivity) {
+    // Positivity scaling (addition, see the header): w <- Qbar + theta (w - Qbar)
+    // with theta the largest value in [0,1] keeping density, then pressure,
+    // above 1e-10 times their cell-average values at every lattice node.
+    // Density and pressure are concave in the conserved variables, so the
+    // linear interpolation bound below is sufficient.
+    const double floor_rel = 1e-10;
+    const double* qb = &Q[i * nu];
+    double rb = qb[0], pb = pressure(S.pde, d, S.P, qb);
+    std::vector<std::vector<double>> node(S.Mc, std::vector<double>(nu));
+    for (int n = 0; n < S.Mc; ++n) {
+      double x[4] = {S.lat[n][0], S.lat[n][1], S.lat[n][2], 0.0};
+      for (int v = 0; v < nu; ++v) node[n][v] = poly_eval(out.w[v], x);
+    }
+    double th_rho = 1.0;
+    for (int n = 0; n < S.Mc; ++n)
+      if (node[n][0] < floor_rel * rb) th_rho = std::min(th_rho, (rb - floor_rel * rb) / (rb - node[n][0]));
+    double th_p = 1.0;
+    if (pb > 0.0)
+      for (int n = 0; n < S.Mc; ++n) {
+        std::vector<double> q(nu);
+        for (int v = 0; v < nu; ++v) q[v] = qb[v] + th_rho * (node[n][v] - qb[v]);
+        double pk = pressure(S.pde, d, S.P, q.data());
+        if (pk < floor_rel * pb) th_p = std::min(th_p, (pb - floor_rel * pb) / (pb - pk));
+      }
+    double theta = th_rho * th_p;
+    if (theta < 1.0)
+      for (int v = 0; v < nu; ++v) {
+        Poly c;
+        c.push_back(monomial(0, 0, 0, 0, qb[v]));
+        out.w[v] = poly_axpy(theta, out.w[v], 1.0 - theta, c);
+      }
+  }
   return true;
 }
 
@@ -1245,7 +1297,7 @@ int orc_mesh_geometry(void* p, double* vol, double* bary, double* h, int64_t* nb
   return 0;
 }
 
-// params: eps, r, lam0, lams, gamma, ch, cfl, niter, linear_weights
+// params: eps, r, lam0, lams, gamma, ch, cfl, niter, linear_weights, positivity
 void* orc_solver_new(void* mesh, int M, int pde, const double* prm, char* err, int errlen) {
   OMesh* m = (OMesh*)mesh;
   if (M < 1 || M > 4 || (pde != PDE_EULER && pde != PDE_MHD)) {
@@ -1267,6 +1319,7 @@ void* orc_solver_new(void* mesh, int M, int pde, const double* prm, char* err, i
   S->P.cfl = prm[6];
   S->P.niter = (int)prm[7];
   S->P.linear_weights = (int)prm[8];
+  S->P.positivity = (int)prm[9];
   S->Mc = Mcal(M, m->d);
   S->ne = m->d * S->Mc;
   S->mono = monomial_list(m->d, M);

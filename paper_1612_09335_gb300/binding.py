@@ -30,7 +30,7 @@ class CwenoError(RuntimeError):
 class cweno_params(C.Structure):
     _fields_ = [("eps", C.c_double), ("r", C.c_double), ("lambda0", C.c_double), ("lambda_s", C.c_double),
                 ("gamma", C.c_double), ("c_h", C.c_double), ("cfl", C.c_double), ("picard_iters", C.c_int),
-                ("linear_weights", C.c_int)]
+                ("linear_weights", C.c_int), ("positivity", C.c_int)]
 
 
 class cweno_request(C.Structure):

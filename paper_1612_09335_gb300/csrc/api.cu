@@ -126,6 +126,7 @@ void cweno_default_params(cweno_params* p, int dim, int pde) {
   p->cfl = dim == 3 ? 1.0 / 3.0 : 0.5;
   p->picard_iters = 0;
   p->linear_weights = 0;
+  p->positivity = 1;
 }
 
 const char* cweno_last_error(void) { return g_err.c_str(); }
@@ -227,6 +228,7 @@ int cweno_setup(const cweno_mesh* mesh, int order, int pde, int precision, const
   s->ph.lams = prm.lambda_s;
   s->ph.niter = prm.picard_iters > 0 ? prm.picard_iters : M + 1;
   s->ph.linear_weights = prm.linear_weights;
+  s->ph.positivity = prm.positivity;
   s->nc = m.nc;
   s->nf = m.nf;
   CK(cudaGetDevice(&s->dev));

@@ -96,7 +96,7 @@ struct KArgs {
   int* status;
   double* out;
   T gamma, ch, eps, lam0, lams;
-  int niter, linw;
+  int niter, linw, pos;
   double dt_fixed, cfl;
   int cur, reset_next;
 };
@@ -145,7 +145,8 @@ struct Phys<D, 0, T> {  // Euler, Eqs. (eulerTerms), (eos)
     T vn = T(0);
 #pragma unroll
     for (int a = 0; a < D; ++a) vn += s.v[a] * n[a];
-    return fabs(vn) + sqrt(gamma * s.p * s.ir);
+    const T c2 = gamma * s.p * s.ir;
+    return fabs(vn) + sqrt(c2 > T(0) ? c2 : T(0));
   }
   // largest |eigenvalue| over all directions
   __device__ __forceinline__ static T speed(const T* q, T gamma, T /*ch*/) {
@@ -153,7 +154,14 @@ struct Phys<D, 0, T> {  // Euler, Eqs. (eulerTerms), (eos)
     T v2 = T(0);
 #pragma unroll
     for (int a = 0; a < D; ++a) v2 += s.v[a] * s.v[a];
-    return sqrt(v2) + sqrt(gamma * s.p * s.ir);
+    const T c2 = gamma * s.p * s.ir;
+    return sqrt(v2) + sqrt(c2 > T(0) ? c2 : T(0));
+  }
+  __device__ __forceinline__ static T pressure(const T* q, T gamma) {
+    T m2 = T(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) m2 += q[1 + a] * q[1 + a];
+    return (gamma - T(1)) * (q[D + 1] - T(0.5) * m2 / q[0]);
   }
   __device__ __forceinline__ static bool admissible(const double* q, double gamma) {
     double rho = q[0], v2 = 0.0;
@@ -220,7 +228,8 @@ struct Phys<D, 1, T> {  // ideal MHD + GLM, Eqs. (MHDTerms), (MHDeos), Gaussian 
     T sum = a2 + b2;
     T disc = sum * sum - T(4) * a2 * bn2;
     disc = disc > T(0) ? disc : T(0);
-    T cf = sqrt(T(0.5) * (sum + sqrt(disc)));
+    T cf2 = T(0.5) * (sum + sqrt(disc));
+    T cf = sqrt(cf2 > T(0) ? cf2 : T(0));
     T sp = fabs(vn) + cf;
     return sp > ch ? sp : ch;
   }
@@ -233,8 +242,15 @@ struct Phys<D, 1, T> {  // ideal MHD + GLM, Eqs. (MHDTerms), (MHDeos), Gaussian 
       v2 += s.v[a] * s.v[a];
       B2 += s.B[a] * s.B[a];
     }
-    T sp = sqrt(v2) + sqrt(gamma * s.p * s.ir + B2 * i4pi * s.ir);
+    T f2 = gamma * s.p * s.ir + B2 * i4pi * s.ir;
+    T sp = sqrt(v2) + sqrt(f2 > T(0) ? f2 : T(0));
     return sp > ch ? sp : ch;
+  }
+  __device__ __forceinline__ static T pressure(const T* q, T gamma) {
+    const T i8pi = T(0.039788735772973836);
+    T m2 = q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+    T B2 = q[5] * q[5] + q[6] * q[6] + q[7] * q[7];
+    return (gamma - T(1)) * (q[4] - T(0.5) * m2 / q[0] - B2 * i8pi);
   }
   __device__ __forceinline__ static bool admissible(const double* q, double gamma) {
     double rho = q[0];
@@ -421,6 +437,56 @@ __global__ void __launch_bounds__(128) k_rec_pred(KArgs<C> a, CellTab<C> tb) {
         for (int sc = 0; sc < NS; ++sc) s += ws[sc] * g[sc][l < D ? l : 0][v];
       }
       w[l][v] = s;
+    }
+  }
+
+  // ---- positivity scaling toward the cell average (switchable; an addition
+  // to the paper, the Zhang-Shu scaling limiter): density first, then the
+  // pressure, both kept above 1e-10 of their cell-average values at every
+  // lattice node; density and pressure are concave in the conserved state
+  if (a.pos) {
+    const T fl = T(1e-10);
+    T qb[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) qb[v] = qi[v] + qlo[v];
+    const T rb = qb[0];
+    T th = T(1);
+#pragma unroll
+    for (int n = 0; n < C::L0; ++n) {
+      T r = qb[0];
+#pragma unroll
+      for (int l = 0; l < MC1; ++l) r += tb.E[n][l] * w[l][0];
+      if (r < fl * rb) {
+        const T t = (rb - fl * rb) / (rb - r);
+        th = t < th ? t : th;
+      }
+    }
+    const T pb = PH::pressure(qb, a.gamma);
+    T thp = T(1);
+    if (pb > T(0)) {
+#pragma unroll
+      for (int n = 0; n < C::L0; ++n) {
+        T q[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          T s = T(0);
+#pragma unroll
+          for (int l = 0; l < MC1; ++l) s += tb.E[n][l] * w[l][v];
+          q[v] = qb[v] + th * s;
+        }
+        const T pk = PH::pressure(q, a.gamma);
+        if (pk < fl * pb) {
+          const T t = (pb - fl * pb) / (pb - pk);
+          thp = t < thp ? t : thp;
+        }
+      }
+    }
+    const T theta = th * thp;
+    if (theta < T(1)) {
+#pragma unroll
+      for (int l = 0; l < MC1; ++l)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) w[l][v] *= theta;
     }
   }
 
@@ -813,6 +879,7 @@ class OpsImpl final : public Ops {
     a.lams = (T)ph.lams;
     a.niter = ph.niter;
     a.linw = ph.linear_weights;
+    a.pos = ph.positivity;
     a.dt_fixed = dt.fixed;
     a.cfl = dt.cfl;
     a.cur = dt.cur;

@@ -45,7 +45,7 @@ struct DevState {
 struct PhysParams {
   double gamma = 1.4, ch = 2.0;
   double eps = 1e-14, lam0 = 1e5, lams = 1.0;
-  int niter = 2, linear_weights = 0;
+  int niter = 2, linear_weights = 0, positivity = 1;
 };
 
 // Time step source: fixed > 0, else cfl * (min h/lambda) read from dtmin[cur].

@@ -31,6 +31,22 @@ def relerr(a, b):
     return float((num / den).max())
 
 
+def tolerance(name, fn, Q):
+    """1e-12, or for discontinuous data the conditioning of the scheme: the
+    nonlinear weights near a jump amplify a one-ulp change of the input by up
+    to ~1e3, so the bound is 8x the oracle's own response to random relative
+    input perturbations of 2^-52 (taken over three draws)."""
+    if "explosion" not in name:
+        return TOL64
+    base = fn(Q)
+    rng = np.random.default_rng(123)
+    worst = 0.0
+    for _ in range(3):
+        Qp = Q * (1.0 + 2.0 ** -52 * rng.choice([-1.0, 1.0], size=Q.shape))
+        worst = max(worst, relerr(fn(Qp), base))
+    return max(TOL64, 8.0 * worst)
+
+
 def case_inputs(wl, name):
     if name == "vortex2d":
         return wl.vortex_2d(16), EULER
@@ -61,8 +77,9 @@ def test_reconstruct_fp64_matches_oracle(cw, orc, wl, name, order):
     s = make(cw, mesh, order, pde, cw.FP64)
     s.set_state(Q)
     w = s.reconstruct()
-    ref = orc.Oracle(mesh, order, pde).reconstruct(Q)
-    assert relerr(w, ref) < TOL64
+    o = orc.Oracle(mesh, order, pde)
+    ref = o.reconstruct(Q)
+    assert relerr(w, ref) < tolerance(name, o.reconstruct, Q)
 
 
 @pytest.mark.parametrize("name,order", CASES)
@@ -73,7 +90,7 @@ def test_predictor_fp64_matches_oracle(cw, orc, wl, name, order):
     s = make(cw, mesh, order, pde, cw.FP64)
     s.set_state(Q)
     q = s.predictor(dt)
-    assert relerr(q, o.predictor(Q, dt)) < TOL64
+    assert relerr(q, o.predictor(Q, dt)) < tolerance(name, lambda x: o.predictor(x, dt), Q)
 
 
 @pytest.mark.parametrize("name,order", CASES)
@@ -87,7 +104,7 @@ def test_one_step_fp64_matches_oracle(cw, orc, wl, name, order):
     s.sync()
     Q1 = s.get_state()
     ref = o.step(Q, dt)
-    assert relerr(Q1, ref) < TOL64
+    assert relerr(Q1, ref) < tolerance(name, lambda x: o.step(x, dt), Q)
     # the increment itself (what the step computed) agrees to 1e-9 relative
     assert relerr(Q1 - Q, ref - Q) < 1e-9
 
@@ -238,3 +255,26 @@ def test_nan_status_reported(cw, wl):
     with pytest.raises(cw.CwenoError) as e:
         s.sync()
     assert e.value.code == cw.ENAN
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_explosion_runs_admissible(cw, wl, prec):
+    """Explosion, 96x96x2, P3: 60 steps stay finite and admissible in both
+    precisions (positivity scaling on, the default)."""
+    mesh, Q = wl.explosion_2d(96)
+    s = make(cw, mesh, 4, EULER, prec)
+    s.set_state(Q)
+    s.run(60)
+    s.sync()
+    Q1 = s.get_state()
+    p = 0.4 * (Q1[:, 3] - 0.5 * (Q1[:, 1] ** 2 + Q1[:, 2] ** 2) / Q1[:, 0])
+    assert np.isfinite(Q1).all() and Q1[:, 0].min() > 0.1 and p.min() > 0.05
+
+
+def test_positivity_off_is_the_papers_scheme(cw, orc, wl):
+    (mesh, Q), pde = case_inputs(wl, "explosion2d")
+    prm = orc.default_params(2, EULER, order=4, positivity=False)
+    o = orc.Oracle(mesh, 4, EULER, params=prm)
+    s = make(cw, mesh, 4, EULER, cw.FP64, positivity=0)
+    s.set_state(Q)
+    assert relerr(s.reconstruct(), o.reconstruct(Q)) < tolerance("explosion", o.reconstruct, Q)

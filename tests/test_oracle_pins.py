@@ -234,7 +234,8 @@ def test_linear_weights_mode_reproduces_polynomials(orc, wl, dim, order):
     mesh = box_mesh(wl, dim, 6 if dim == 2 else 4, 0.2 if dim == 2 else 0.12)
     f = poly_field(dim, M, np.random.default_rng(2), dim + 2, centre=[0.5] * dim)
     Q = wl.cell_averages(mesh, f, n=6 if dim == 2 else 4)
-    prm = orc.default_params(dim, EULER, order=order, linear_weights=True)
+    # random polynomial data are not admissible states: positivity scaling off
+    prm = orc.default_params(dim, EULER, order=order, linear_weights=True, positivity=False)
     o = orc.Oracle(mesh, order, EULER, params=prm)
     w = o.reconstruct(Q)
     ref = f(node_positions(mesh, np.arange(mesh.nc), M).reshape(-1, dim)).reshape(w.shape)
@@ -248,7 +249,7 @@ def test_nonlinear_weights_exact_for_linear_data(orc, wl, dim, order):
     mesh = box_mesh(wl, dim, 6 if dim == 2 else 4, 0.2 if dim == 2 else 0.12)
     f = poly_field(dim, 1, np.random.default_rng(3), dim + 2, centre=[0.5] * dim)
     Q = wl.cell_averages(mesh, f, n=4)
-    o = orc.Oracle(mesh, order, EULER)
+    o = orc.Oracle(mesh, order, EULER, params=orc.default_params(dim, EULER, order=order, positivity=False))
     w = o.reconstruct(Q)
     ref = f(node_positions(mesh, np.arange(mesh.nc), M).reshape(-1, dim)).reshape(w.shape)
     assert np.abs(w - ref).max() < 1e-11 * np.abs(ref).max()
@@ -613,3 +614,42 @@ def test_convergence_density_wave_2d(orc, wl, order, linear):
         hs.append(1.0 / n)
     rate = math.log(errs[0] / errs[1]) / math.log(hs[0] / hs[1])
     assert rate > order - 0.3, (errs, rate)
+
+
+# ------------------------------------------------------- positivity scaling
+def _pressure(q, gamma=1.4):
+    return (gamma - 1) * (q[..., 3] - 0.5 * (q[..., 1] ** 2 + q[..., 2] ** 2) / q[..., 0])
+
+
+def test_positivity_scaling_needed_and_effective(orc, wl):
+    """The paper's weights alone leave negative density at lattice nodes of
+    cut cells of the explosion (P3, 64x64x2); the scaling toward the cell
+    average removes them and keeps every cell average."""
+    m, Q = wl.explosion_2d(64)
+    off = orc.Oracle(m, 4, params=orc.default_params(2, EULER, order=4, positivity=False)).reconstruct(Q)
+    assert off[..., 0].min() < 0
+    on = orc.Oracle(m, 4).reconstruct(Q)
+    rb = Q[:, 0][:, None]
+    pb = _pressure(Q)[:, None]
+    # the floors hold up to the rounding of Qbar + theta (w - Qbar) (~1e-16 Qbar)
+    assert np.all(on[..., 0] >= 1e-10 * rb - 1e-14 * rb) and np.all(_pressure(on) >= 1e-10 * pb - 1e-14 * pb)
+    assert on[..., 0].min() > 0 and _pressure(on).min() > 0
+    changed = np.where(np.abs(on - off).max(axis=(1, 2)) > 0)[0]
+    assert 0 < len(changed) < m.nc // 20
+    avg = np.stack([_interp_average(2, 3, on[c], wl) for c in changed])
+    assert np.abs(avg - Q[changed]).max() < 1e-12
+
+
+def test_positivity_scaling_inactive_on_smooth_data(orc, wl):
+    mesh, Q = wl.vortex_2d(12)
+    a = orc.Oracle(mesh, 4).reconstruct(Q)
+    b = orc.Oracle(mesh, 4, params=orc.default_params(2, EULER, order=4, positivity=False)).reconstruct(Q)
+    assert np.array_equal(a, b)
+
+
+def test_explosion_stays_admissible(orc, wl):
+    m, Q = wl.explosion_2d(24)
+    o = orc.Oracle(m, 4)
+    for _ in range(8):
+        Q = o.step(Q, o.stable_dt(Q))
+    assert np.isfinite(Q).all() and Q[:, 0].min() > 0.12 and _pressure(Q).min() > 0.09
