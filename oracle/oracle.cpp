@@ -48,8 +48,10 @@
 // Addition not in the paper (switchable, on by default): a positivity
 // preserving scaling of the reconstruction toward the cell average at the
 // lattice nodes, first for the density, then for the pressure (the scaling
-// limiter of Zhang & Shu, J. Comput. Phys. 229 (2010) 3091).  Where every
-// node is admissible it leaves w untouched.
+// limiter of Zhang & Shu, J. Comput. Phys. 229 (2010) 3091), and, at a face
+// quadrature point where one side's predictor is not an admissible state,
+// that side's cell average in place of its trace.  Where everything is
+// admissible neither changes anything.
 // ============================================================================
 #include <algorithm>
 #include <array>
@@ -1489,6 +1491,12 @@ int orc_step(void* p, const double* Q, double dt, int64_t n, const int64_t* ids,
             eval_qh(*S, pred[j], xtj, qp.data());
           } else {
             qp = qm;  // transmissive boundary
+          }
+          if (S->P.positivity) {
+            if (!(qm[0] > 0.0 && pressure(S->pde, d, S->P, qm.data()) > 0.0))
+              for (int v = 0; v < nu; ++v) qm[v] = Q[i * nu + v];
+            if (!(qp[0] > 0.0 && pressure(S->pde, d, S->P, qp.data()) > 0.0))
+              for (int v = 0; v < nu; ++v) qp[v] = j >= 0 ? Q[j * nu + v] : Q[i * nu + v];
           }
           // Rusanov flux, Eq. (rusanov), Eulerian normal (n |f| dt, 0)
           for (int v = 0; v < nu; ++v) {

@@ -512,10 +512,24 @@ __global__ void __launch_bounds__(128) k_rec_pred(KArgs<C> a, CellTab<C> tb) {
 #pragma unroll
       for (int m = 0; m < D; ++m) J[e][m] = __ldg(a.Jinv + (e * D + m) * N + i);
 
+    // Deviations from the cell average: the Picard update subtracts the flux
+    // of the cell average, G_e(q) - G_e(Qbar), which P_e annihilates exactly
+    // (it differentiates constants to zero); q_hat is stored as q - Qbar.  The
+    // arithmetic is identical in exact arithmetic, and constant states stay
+    // exactly constant in FP32.
+    T qb[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) qb[v] = qi[v] + qlo[v];
+    T Gref[D][NV];
+    {
+      typename PH::Prim pr = PH::prim(qb, a.gamma);
+#pragma unroll
+      for (int e = 0; e < D; ++e) flux_normal<D, C::PDE, T>(qb, pr, J[e], Gref[e], a.ch);
+    }
     // known degrees of freedom: w at the tau = 0 nodes (written out at once);
-    // base = C0 q0 - dt sum_e P_e[:, tau=0 nodes] G_e(q0) is fixed over the
-    // iterations; the initial guess of the unknown nodes is w at their
-    // spatial positions, which is C0 q0.
+    // base = C0 dq0 - dt sum_e P_e[:, tau=0 nodes] (G_e(q0) - G_e(Qbar)) is
+    // fixed over the iterations; the initial guess of the unknown nodes is w
+    // at their spatial positions, Qbar + C0 dq0.
     T base[L1][NV], q1[L1][NV];
 #pragma unroll
     for (int k = 0; k < L1; ++k)
@@ -526,13 +540,14 @@ __global__ void __launch_bounds__(128) k_rec_pred(KArgs<C> a, CellTab<C> tb) {
       }
 #pragma unroll
     for (int n = 0; n < L0; ++n) {
-      T q0[NV];
+      T dq0[NV], q0[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        T s = qi[v] + qlo[v];
+        T s = T(0);
 #pragma unroll
         for (int l = 0; l < MC1; ++l) s += tb.E[n][l] * w[l][v];
-        q0[v] = s;
+        dq0[v] = s;
+        q0[v] = qb[v] + s;
         a.qhat[(int64_t)(n * NV + v) * N + i] = s;
       }
       typename PH::Prim pr = PH::prim(q0, a.gamma);
@@ -543,15 +558,15 @@ __global__ void __launch_bounds__(128) k_rec_pred(KArgs<C> a, CellTab<C> tb) {
       for (int k = 0; k < L1; ++k)
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          const T cq = tb.C0[k][n] * q0[v];
+          const T cq = tb.C0[k][n] * dq0[v];
           T s = T(0);
 #pragma unroll
-          for (int e = 0; e < D; ++e) s += tb.P[e][k][n] * Ge[e][v];
+          for (int e = 0; e < D; ++e) s += tb.P[e][k][n] * (Ge[e][v] - Gref[e][v]);
           base[k][v] += cq - dt * s;
           q1[k][v] += cq;
         }
     }
-    // Picard iterations of Eq. (CGfinal)
+    // Picard iterations of Eq. (CGfinal), on deviations
     for (int it = 0; it < a.niter; ++it) {
       T nq[L1][NV];
 #pragma unroll
@@ -560,17 +575,20 @@ __global__ void __launch_bounds__(128) k_rec_pred(KArgs<C> a, CellTab<C> tb) {
         for (int v = 0; v < NV; ++v) nq[k][v] = base[k][v];
 #pragma unroll
       for (int l = 0; l < L1; ++l) {
-        typename PH::Prim pr = PH::prim(q1[l], a.gamma);
+        T ql[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) ql[v] = qb[v] + q1[l][v];
+        typename PH::Prim pr = PH::prim(ql, a.gamma);
         T Ge[D][NV];
 #pragma unroll
-        for (int e = 0; e < D; ++e) flux_normal<D, C::PDE, T>(q1[l], pr, J[e], Ge[e], a.ch);
+        for (int e = 0; e < D; ++e) flux_normal<D, C::PDE, T>(ql, pr, J[e], Ge[e], a.ch);
 #pragma unroll
         for (int k = 0; k < L1; ++k)
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
             T s = T(0);
 #pragma unroll
-            for (int e = 0; e < D; ++e) s += tb.P[e][k][L0 + l] * Ge[e][v];
+            for (int e = 0; e < D; ++e) s += tb.P[e][k][L0 + l] * (Ge[e][v] - Gref[e][v]);
             nq[k][v] -= dt * s;
           }
       }
@@ -613,6 +631,18 @@ __global__ void __launch_bounds__(128) k_flux(KArgs<C> a, int use_smem) {
 #pragma unroll
     for (int e = 0; e < D; ++e) n[e] = a.fn[e * F + f];
     const T area = a.farea[f];
+    // cell averages of both sides: q_hat holds deviations from them
+    T qbL[NV], qbR[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      if constexpr (std::is_same<T, double>::value) {
+        qbL[v] = a.Q[v * N + Lc];
+        qbR[v] = Rc >= 0 ? a.Q[v * N + Rc] : qbL[v];
+      } else {
+        qbL[v] = __ldg(a.Qhi + v * N + Lc) + __ldg(a.Qlo + v * N + Lc);
+        qbR[v] = Rc >= 0 ? __ldg(a.Qhi + v * N + Rc) + __ldg(a.Qlo + v * N + Rc) : qbL[v];
+      }
+    }
     T acc[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] = T(0);
@@ -669,17 +699,34 @@ __global__ void __launch_bounds__(128) k_flux(KArgs<C> a, int use_smem) {
       for (int tt = 0; tt < CH; ++tt)
 #pragma unroll
         for (int q = 0; q < NQS; ++q) {
-          typename PH::Prim pl = PH::prim(trL[tt][q], a.gamma);
-          typename PH::Prim pr = PH::prim(trR[tt][q], a.gamma);
+          // traces = cell average + deviation; a side whose trace is not an
+          // admissible state (density or pressure <= 0) uses its cell average
+          // at this point (positivity safeguard, with the scaling above)
+          T ul[NV], ur[NV];
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            ul[v] = qbL[v] + trL[tt][q][v];
+            ur[v] = qbR[v] + trR[tt][q][v];
+          }
+          if (a.pos) {
+            if (!(ul[0] > T(0) && PH::pressure(ul, a.gamma) > T(0)))
+#pragma unroll
+              for (int v = 0; v < NV; ++v) ul[v] = qbL[v];
+            if (!(ur[0] > T(0) && PH::pressure(ur, a.gamma) > T(0)))
+#pragma unroll
+              for (int v = 0; v < NV; ++v) ur[v] = qbR[v];
+          }
+          typename PH::Prim pl = PH::prim(ul, a.gamma);
+          typename PH::Prim pr = PH::prim(ur, a.gamma);
           T fl[NV], fr[NV];
-          flux_normal<D, C::PDE, T>(trL[tt][q], pl, n, fl, a.ch);
-          flux_normal<D, C::PDE, T>(trR[tt][q], pr, n, fr, a.ch);
+          flux_normal<D, C::PDE, T>(ul, pl, n, fl, a.ch);
+          flux_normal<D, C::PDE, T>(ur, pr, n, fr, a.ch);
           T sl = PH::smax(pl, n, a.gamma, a.ch), sr = PH::smax(pr, n, a.gamma, a.ch);
           const T s = sl > sr ? sl : sr;
           const T wgt = wq[q] * wt[t0 + tt];
 #pragma unroll
           for (int v = 0; v < NV; ++v)
-            acc[v] += wgt * (T(0.5) * (fl[v] + fr[v]) - T(0.5) * s * (trR[tt][q][v] - trL[tt][q][v]));
+            acc[v] += wgt * (T(0.5) * (fl[v] + fr[v]) - T(0.5) * s * (ur[v] - ul[v]));
         }
     }
     const T scale = dt * area;
@@ -812,8 +859,14 @@ __global__ void k_qhat_out(KArgs<C> a, double* user) {
   const int64_t u = a.perm[i];
   for (int l = 0; l < C::L; ++l)
 #pragma unroll
-    for (int v = 0; v < C::NV; ++v)
-      user[(u * C::L + l) * C::NV + v] = (double)a.qhat[(int64_t)(l * C::NV + v) * a.N + i];
+    for (int v = 0; v < C::NV; ++v) {
+      double qbar;
+      if constexpr (std::is_same<typename C::T, float>::value)
+        qbar = (double)a.Qhi[v * a.N + i] + (double)a.Qlo[v * a.N + i];
+      else
+        qbar = a.Q[v * a.N + i];
+      user[(u * C::L + l) * C::NV + v] = qbar + (double)a.qhat[(int64_t)(l * C::NV + v) * a.N + i];
+    }
 }
 
 // ------------------------------------------------------------- host side
