@@ -229,7 +229,10 @@ def run_ours(args):
     cfg = WORKLOADS[name]
     mesh, Q0 = make_inputs(name, args.n)
     N = mesh.nc
-    stream = torch.cuda.current_stream()
+    # a dedicated (non-default) stream: the library launches on it and the
+    # CUDA events below are recorded on it
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     m = cw.Mesh.from_workload(mesh)
     s = cw.Solver(m, cfg["order"], cfg["pde"], cw.FP32_MIXED, stream=stream.cuda_stream)
 

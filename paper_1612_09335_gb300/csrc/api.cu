@@ -288,10 +288,15 @@ int cweno_setup(const cweno_mesh* mesh, int order, int pde, int precision, const
     for (int64_t f = 0; f < F; ++f)
       for (int a = 0; a < d; ++a) fn[(size_t)f * d + a] = m.fn[f * 3 + a];
     if ((rc = upload_real(s.get(), fn, F, d, &ds.fn))) return rc;
-    if ((rc = upload_real(s.get(), m.farea, F, 1, &ds.farea))) return rc;
+    std::vector<double> fa((size_t)F * d);
+    for (int64_t f = 0; f < F; ++f)
+      for (int a = 0; a < d; ++a) fa[(size_t)f * d + a] = m.fn[f * 3 + a] * m.farea[f];
+    std::vector<double> fa_soa = soa<double>(fa, F, d);
+    if ((rc = upload(s.get(), fa_soa, (const void**)&ds.fa))) return rc;
+    if ((rc = upload(s.get(), m.farea, (const void**)&ds.farea))) return rc;
   }
-  if ((rc = dev_alloc(s.get(), &p, es * F * nv))) return rc;
-  ds.G = p;
+  if ((rc = dev_alloc(s.get(), &p, sizeof(double) * F * nv))) return rc;
+  ds.G = (double*)p;
   {
     std::vector<unsigned char> tb(s->ops->table_bytes());
     s->ops->pack_tables(tb.data());

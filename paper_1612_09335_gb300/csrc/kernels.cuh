@@ -85,8 +85,9 @@ struct KArgs {
   const uint8_t* codeL;
   const uint8_t* codeR;
   const T* fn;
-  const T* farea;
-  T* G;
+  const double* fa;     // area-weighted normal |f| n, FP64, d x F
+  const double* farea;  // |f|, FP64
+  double* G;            // face flux integrals, FP64
   const T* ftab;
   const int32_t* cellface;
   const double* invvol;
@@ -162,12 +163,6 @@ struct Phys<D, 0, T> {  // Euler, Eqs. (eulerTerms), (eos)
 #pragma unroll
     for (int a = 0; a < D; ++a) m2 += q[1 + a] * q[1 + a];
     return (gamma - T(1)) * (q[D + 1] - T(0.5) * m2 / q[0]);
-  }
-  __device__ __forceinline__ static bool admissible(const double* q, double gamma) {
-    double rho = q[0], v2 = 0.0;
-    for (int a = 0; a < D; ++a) v2 += (q[1 + a] / rho) * (q[1 + a] / rho);
-    double p = (gamma - 1.0) * (q[D + 1] - 0.5 * rho * v2);
-    return rho > 0.0 && p > 0.0 && isfinite(p);
   }
 };
 
@@ -251,16 +246,6 @@ struct Phys<D, 1, T> {  // ideal MHD + GLM, Eqs. (MHDTerms), (MHDeos), Gaussian 
     T m2 = q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
     T B2 = q[5] * q[5] + q[6] * q[6] + q[7] * q[7];
     return (gamma - T(1)) * (q[4] - T(0.5) * m2 / q[0] - B2 * i8pi);
-  }
-  __device__ __forceinline__ static bool admissible(const double* q, double gamma) {
-    double rho = q[0];
-    double v2 = 0.0, B2 = 0.0;
-    for (int a = 0; a < 3; ++a) {
-      v2 += (q[1 + a] / rho) * (q[1 + a] / rho);
-      B2 += q[5 + a] * q[5 + a];
-    }
-    double p = (gamma - 1.0) * (q[4] - 0.5 * rho * v2 - B2 * 0.039788735772973836);
-    return rho > 0.0 && p > 0.0 && isfinite(p);
   }
 };
 
@@ -630,7 +615,6 @@ __global__ void __launch_bounds__(128) k_flux(KArgs<C> a, int use_smem) {
     T n[D];
 #pragma unroll
     for (int e = 0; e < D; ++e) n[e] = a.fn[e * F + f];
-    const T area = a.farea[f];
     // cell averages of both sides: q_hat holds deviations from them
     T qbL[NV], qbR[NV];
 #pragma unroll
@@ -643,9 +627,16 @@ __global__ void __launch_bounds__(128) k_flux(KArgs<C> a, int use_smem) {
         qbR[v] = Rc >= 0 ? __ldg(a.Qhi + v * N + Rc) + __ldg(a.Qlo + v * N + Rc) : qbL[v];
       }
     }
-    T acc[NV];
+    // sum_q w_q (F_m(q-) + F_m(q+)) per direction m, and sum_q w_q s_q (q+ - q-);
+    // the contraction with |f| n is done in FP64 below, so that a constant
+    // state gives bit-identical sums on every face and the update closes
+    T facc[D][NV], dacc[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) acc[v] = T(0);
+    for (int v = 0; v < NV; ++v) {
+      dacc[v] = T(0);
+#pragma unroll
+      for (int m = 0; m < D; ++m) facc[m][v] = T(0);
+    }
 #pragma unroll 1
     for (int t0 = 0; t0 < NQT; t0 += CH) {
       T trL[CH][NQS][NV], trR[CH][NQS][NV];
@@ -718,20 +709,37 @@ __global__ void __launch_bounds__(128) k_flux(KArgs<C> a, int use_smem) {
           }
           typename PH::Prim pl = PH::prim(ul, a.gamma);
           typename PH::Prim pr = PH::prim(ur, a.gamma);
-          T fl[NV], fr[NV];
-          flux_normal<D, C::PDE, T>(ul, pl, n, fl, a.ch);
-          flux_normal<D, C::PDE, T>(ur, pr, n, fr, a.ch);
           T sl = PH::smax(pl, n, a.gamma, a.ch), sr = PH::smax(pr, n, a.gamma, a.ch);
           const T s = sl > sr ? sl : sr;
           const T wgt = wq[q] * wt[t0 + tt];
 #pragma unroll
-          for (int v = 0; v < NV; ++v)
-            acc[v] += wgt * (T(0.5) * (fl[v] + fr[v]) - T(0.5) * s * (ur[v] - ul[v]));
+          for (int m = 0; m < D; ++m) {
+            T em[D];
+#pragma unroll
+            for (int e = 0; e < D; ++e) em[e] = e == m ? T(1) : T(0);
+            T fl[NV], fr[NV];
+            flux_normal<D, C::PDE, T>(ul, pl, em, fl, a.ch);
+            flux_normal<D, C::PDE, T>(ur, pr, em, fr, a.ch);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) facc[m][v] += wgt * (fl[v] + fr[v]);
+          }
+          const T ws = wgt * s;
+#pragma unroll
+          for (int v = 0; v < NV; ++v) dacc[v] += ws * (ur[v] - ul[v]);
         }
     }
-    const T scale = dt * area;
+    const double dtd = dt_of(a.dt_fixed, a.cfl, a.dtmin, a.cur);
+    double fa[D];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) a.G[v * F + f] = scale * acc[v];
+    for (int m = 0; m < D; ++m) fa[m] = a.fa[m * F + f];
+    const double area = a.farea[f];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      double g = -area * (double)dacc[v];
+#pragma unroll
+      for (int m = 0; m < D; ++m) g += fa[m] * (double)facc[m][v];
+      a.G[v * F + f] = 0.5 * dtd * g;
+    }
   }
 }
 
@@ -777,7 +785,7 @@ __global__ void __launch_bounds__(256) k_update(KArgs<C> a) {
       const int64_t f = cf >> 1;
       const double sgn = (cf & 1) ? -1.0 : 1.0;
 #pragma unroll
-      for (int v = 0; v < NV; ++v) acc[v] += sgn * (double)a.G[v * F + f];
+      for (int v = 0; v < NV; ++v) acc[v] += sgn * a.G[v * F + f];
     }
     const double iv = a.invvol[i];
     double q[NV];
@@ -799,9 +807,12 @@ __global__ void __launch_bounds__(256) k_update(KArgs<C> a) {
 #pragma unroll
       for (int v = 0; v < NV; ++v) qt[v] = q[v];
     }
-    if (!PH::admissible(q, (double)a.gamma)) atomicOr(a.status, 1);
+    // admissibility and the CFL bound in the arithmetic type (FP32 in mixed
+    // mode: FP64 divisions and square roots are slow on this part)
+    const T pk = PH::pressure(qt, a.gamma);
+    if (!(qt[0] > T(0) && pk > T(0) && isfinite(pk))) atomicOr(a.status, 1);
     const T sp = PH::speed(qt, a.gamma, a.ch);
-    ratio = a.hsize[i] / (double)sp;
+    ratio = (double)((T)a.hsize[i] / sp);
   }
   block_min_atomic(ratio, a.dtmin + (1 - a.cur));
   if (blockIdx.x == 0 && threadIdx.x == 0) *a.time += dt_of(a.dt_fixed, a.cfl, a.dtmin, a.cur);
@@ -821,7 +832,7 @@ __global__ void __launch_bounds__(256) k_stable_dt(KArgs<C> a, int slot) {
       if constexpr (std::is_same<T, float>::value) q[v] = a.Qhi[v * N + i];
       else q[v] = a.Q[v * N + i];
     }
-    ratio = a.hsize[i] / (double)PH::speed(q, a.gamma, a.ch);
+    ratio = (double)((T)a.hsize[i] / PH::speed(q, a.gamma, a.ch));
   }
   block_min_atomic(ratio, a.dtmin + slot);
 }
@@ -915,8 +926,9 @@ class OpsImpl final : public Ops {
     a.codeL = s.codeL;
     a.codeR = s.codeR;
     a.fn = (const T*)s.fn;
-    a.farea = (const T*)s.farea;
-    a.G = (T*)s.G;
+    a.fa = s.fa;
+    a.farea = s.farea;
+    a.G = s.G;
     a.ftab = (const T*)s.ftab;
     a.cellface = s.cellface;
     a.invvol = s.invvol;

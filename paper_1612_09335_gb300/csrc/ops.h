@@ -29,9 +29,10 @@ struct DevState {
   const int32_t* fR = nullptr;
   const uint8_t* codeL = nullptr;
   const uint8_t* codeR = nullptr;
-  const void* fn = nullptr;       // d x F
-  const void* farea = nullptr;    // F
-  void* G = nullptr;              // nv x F
+  const void* fn = nullptr;       // d x F unit normal (arithmetic type)
+  const double* fa = nullptr;     // d x F area-weighted normal (FP64)
+  const double* farea = nullptr;  // F (FP64)
+  double* G = nullptr;            // nv x F face flux integrals (FP64)
   const void* ftab = nullptr;     // face basis table + wq + wt
   const int32_t* cellface = nullptr;  // (d+1) x N
   const double* invvol = nullptr;     // N

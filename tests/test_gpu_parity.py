@@ -215,24 +215,27 @@ def test_free_stream_both_modes(cw, wl, dim, pde, order):
     else:
         q = np.array([1.2, 0.3, -0.2, 0.1, 3.0, 0.5, -0.7, 0.2, 0.0])
     Q = np.tile(q, (mesh.nc, 1))
-    # FP32: the face geometry is rounded to FP32, so sum_f n_f |f| closes
-    # only to ~1e-7 relative; bound 1e-6 * CFL per step over 3 steps
-    for prec, tol in ((cw.FP64, 1e-13), (cw.FP32_MIXED, 3 * 1e-6 * s_cfl(dim))):
+    # deviations from the cell average and the FP64 contraction of the face
+    # sums keep a constant state constant to FP64 rounding in both modes
+    # (error measured against the state's magnitude)
+    for prec in (cw.FP64, cw.FP32_MIXED):
         s = make(cw, mesh, order, pde, prec)
         s.set_state(Q)
         s.run(3)
         s.sync()
-        assert relerr(s.get_state(), Q) < tol
+        assert relerr(s.get_state(), Q, floor=1.0) < 1e-13
 
 
 # FP32-mixed bounds against the FP64 oracle, one step from identical input,
 # per variable relative L_inf with variables smaller than 1% of the state's
 # scale measured at that scale (FP32 rounding is relative to the largest
-# terms a variable is computed from).  Smooth data: 2e-6; discontinuous
-# data: 1e-4 (weights near jumps amplify FP32 rounding of the indicators).
+# terms a variable is computed from).  Smooth Euler data: 2e-6;
+# MHD-GLM: 3e-5 (psi and B_z come from cancellations in div B and the
+# induction fluxes); discontinuous data: 1e-4 (weights near jumps amplify
+# FP32 rounding of the indicators).
 @pytest.mark.parametrize("name,order,tol", [("vortex2d", 3, 2e-6), ("vortex2d", 4, 2e-6),
                                             ("explosion2d", 4, 1e-4), ("wave3d", 3, 2e-6),
-                                            ("orszag", 4, 2e-6)])
+                                            ("orszag", 3, 3e-5), ("orszag", 4, 3e-5)])
 def test_one_step_fp32_mixed_bounds(cw, orc, wl, name, order, tol):
     (mesh, Q), pde = case_inputs(wl, name)
     o = orc.Oracle(mesh, order, pde)
@@ -245,7 +248,8 @@ def test_one_step_fp32_mixed_bounds(cw, orc, wl, name, order, tol):
     s.sync()
     Q1 = s.get_state()
     ref = o.step(Q, dt)
-    assert relerr(Q1, ref, floor=1e-2) < tol
+    per_var = [relerr(Q1[:, [v]], ref[:, [v]]) for v in range(Q.shape[1])]
+    assert relerr(Q1, ref, floor=1e-2) < tol, per_var
 
 
 def test_linear_weights_mode_on_gpu(cw, orc, wl):
