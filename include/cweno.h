@@ -187,6 +187,29 @@ void* cweno_stream(cweno_solver* s);
 int cweno_profile_enable(cweno_solver* s, int on);
 int cweno_profile_read(cweno_solver* s, double* ms, int64_t* launches);
 
+/* CFL time-step bound without any allocation.  The paper has no counterpart:
+ * this is for callers that cannot call cudaMalloc (work inside a captured
+ * CUDA graph, inside another framework's memory pool, or in a process whose
+ * device memory is reserved up front).  It computes
+ * cfl * min_i h_i / |lambda_max(Q_i)| like cweno_stable_dt, but for a state in
+ * the caller's own buffers:
+ *   Q      device, ncells x nvars FP64, AoS by cell (as cweno_set_state)
+ *   h      device, ncells FP64, characteristic cell sizes (incircle /
+ *          insphere diameters, Eq. timestep)
+ *   dt     device, one FP64, receives the bound
+ *   stream cudaStream_t (NULL: the legacy default stream); asynchronous.
+ * Scratch is a file-scope device array of one partial minimum per 256 cells
+ * (512 KiB), held by every GPU that loads the library until the process
+ * exits, so ncells must not exceed CWENO_NOALLOC_MAX_CELLS (EINVAL
+ * otherwise).  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Calls that overlap on the GPU share the
+ * scratch and race; serialise them (one stream, or events).  Nothing is
+ * allocated and nothing is freed. */
+#define CWENO_NOALLOC_MAX_CELLS (65536 * 256)
+int cweno_stable_dt_noalloc(int dim, int pde, int64_t ncells, const double* Q, const double* h, double gamma,
+                            double c_h, double cfl, double* dt, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Serving: continuous batching of independent solves on one GPU.
  * A request owns a mesh (copied), order, initial state, CFL and step count.

@@ -71,6 +71,7 @@ SIGNATURES = [
     ("cweno_stream", _P, [_P]),
     ("cweno_profile_enable", _I, [_P, _I]),
     ("cweno_profile_read", _I, [_P, _DP, _I64P]),
+    ("cweno_stable_dt_noalloc", _I, [_I, _I, _I64, _P, _P, _D, _D, _D, _P, _P]),
     ("serve_create", _I, [_SZ, _I, _I, C.POINTER(_P)]),
     ("serve_submit", _I, [_P, C.POINTER(cweno_request), _U64P]),
     ("serve_poll", _I, [_P, C.c_uint64, _IP, _DP, _DP]),
@@ -136,6 +137,20 @@ def cweno_mesh_create(dim: int, xyz, cells, period=None):
                                    cells.ctypes.data_as(_I32P),
                                    per.ctypes.data_as(_DP) if per is not None else None, C.byref(h)))
     return h
+
+
+NOALLOC_MAX_CELLS = 65536 * 256
+
+
+def cweno_stable_dt_noalloc(dim: int, pde: int, Q_dev, h_dev, gamma: float, c_h: float, cfl: float, dt_dev,
+                            stream: int = 0):
+    """CFL bound of a state held in the caller's device buffers, allocating
+    nothing (Q_dev: ncells x nvars FP64 CUDA tensor, h_dev: ncells FP64, dt_dev:
+    one FP64 element receiving the bound; asynchronous on `stream`)."""
+    n = int(Q_dev.shape[0])
+    _check(lib().cweno_stable_dt_noalloc(dim, pde, n, C.c_void_p(Q_dev.data_ptr()), C.c_void_p(h_dev.data_ptr()),
+                                         float(gamma), float(c_h), float(cfl), C.c_void_p(dt_dev.data_ptr()),
+                                         C.c_void_p(stream) if stream else None))
 
 
 class Mesh:
