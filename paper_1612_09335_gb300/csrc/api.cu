@@ -21,6 +21,8 @@
 namespace cw {
 
 static thread_local std::string g_err;
+// host threads used by one setup (the serving loop lowers it for its workers)
+thread_local int g_setup_threads = 0;
 
 int fail(int code, const std::string& msg) {
   g_err = msg;
@@ -54,6 +56,24 @@ const RefElem& ref_elem(int d, int M) {
   return out;
 }
 
+// Device bytes cweno_setup allocates for a mesh of nc cells and nf faces.
+size_t footprint_estimate(int d, int64_t nc, int64_t nf, int order, int pde, int precision) {
+  const int M = order - 1;
+  const int Mc = (d == 2) ? (M + 1) * (M + 2) / 2 : (M + 1) * (M + 2) * (M + 3) / 6;
+  const int L = (d == 2) ? (M + 1) * (M + 2) * (M + 3) / 6 : (M + 1) * (M + 2) * (M + 3) * (M + 4) / 24;
+  const int ne = d * Mc, nvx = d + 1, nv = (pde == CWENO_MHD_GLM) ? 9 : d + 2;
+  const size_t es = precision == CWENO_FP32_MIXED ? 4 : 8;
+  size_t b = 0;
+  b += 8 * nc * nv * 2;                                     // Q, staging
+  if (precision == CWENO_FP32_MIXED) b += 8 * nc * nv;      // hi, lo
+  b += 4 * nc + 4 * nc * (ne - 1) + es * nc * (Mc - 1) * (ne - 1);
+  b += 4 * nc * nvx * d + es * nc * nvx * d * d + nc + es * nc * d * d;
+  b += es * nc * nv * L;                                    // q_hat
+  b += nf * (8 + 2 + es * d + 8 * d + 8 + 8 * nv);          // faces + G
+  b += 4 * nc * nvx + 16 * nc + 4096;                       // cell->face, 1/|T|, h, tables
+  return b + (size_t)64 * 1024;                             // allocation granularity slack
+}
+
 }  // namespace cw
 
 using namespace cw;
@@ -63,9 +83,11 @@ struct cweno_mesh {
 };
 
 // ---------------------------------------------------------------- helpers
+// Stream-ordered allocations on the solver's stream: no device-wide
+// synchronisation when solvers come and go while others run (serving).
 static int dev_alloc(cweno_solver* s, void** p, size_t bytes) {
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMalloc(p, bytes);
+  cudaError_t e = cudaMallocAsync(p, bytes, s->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(CWENO_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
@@ -81,7 +103,8 @@ static int upload(cweno_solver* s, const std::vector<TV>& h, const void** out) {
   int rc = dev_alloc(s, &p, h.size() * sizeof(TV));
   if (rc) return rc;
   if (!h.empty()) {
-    cudaError_t e = cudaMemcpy(p, h.data(), h.size() * sizeof(TV), cudaMemcpyHostToDevice);
+    // pageable source: staged before the call returns, so h may be released
+    cudaError_t e = cudaMemcpyAsync(p, h.data(), h.size() * sizeof(TV), cudaMemcpyHostToDevice, s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "upload");
   }
   *out = p;
@@ -190,8 +213,11 @@ void cweno_solver_destroy(cweno_solver* s) {
     cudaEventDestroy(u.first.second);
   }
   for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
-  for (void* p : s->allocs) cudaFree(p);
-  if (s->own_stream) cudaStreamDestroy(s->stream);
+  for (void* p : s->allocs) cudaFreeAsync(p, s->stream);
+  if (s->own_stream) {
+    cudaStreamSynchronize(s->stream);
+    cudaStreamDestroy(s->stream);
+  }
   if (cur >= 0) cudaSetDevice(cur);
   delete s;
 }
@@ -243,6 +269,20 @@ int cweno_setup(const cweno_mesh* mesh, int order, int pde, int precision, const
   int nth = (int)std::max(1u, std::thread::hardware_concurrency());
   int rc = build_cell_setup(m, re, cs, err, nth);
   if (rc) return fail(rc, err);
+  {
+    // keep freed blocks in the device's default pool for reuse (serving)
+    static std::mutex mu;
+    static bool done[64] = {false};
+    std::lock_guard<std::mutex> lk(mu);
+    if (s->dev >= 0 && s->dev < 64 && !done[s->dev]) {
+      cudaMemPool_t pool;
+      if (cudaDeviceGetDefaultMemPool(&pool, s->dev) == cudaSuccess) {
+        uint64_t thr = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+      }
+      done[s->dev] = true;
+    }
+  }
   if (stream) {
     s->stream = (cudaStream_t)stream;
     s->own_stream = false;
@@ -261,14 +301,14 @@ int cweno_setup(const cweno_mesh* mesh, int order, int pde, int precision, const
   void* p = nullptr;
   if ((rc = dev_alloc(s.get(), &p, sizeof(double) * N * nv))) return rc;
   ds.Q = (double*)p;
-  CK(cudaMemset(ds.Q, 0, sizeof(double) * N * nv));
+  CK(cudaMemsetAsync(ds.Q, 0, sizeof(double) * N * nv, s->stream));
   if (precision == CWENO_FP32_MIXED) {
     if ((rc = dev_alloc(s.get(), &p, sizeof(float) * N * nv))) return rc;
     ds.Qhi = (float*)p;
     if ((rc = dev_alloc(s.get(), &p, sizeof(float) * N * nv))) return rc;
     ds.Qlo = (float*)p;
-    CK(cudaMemset(ds.Qhi, 0, sizeof(float) * N * nv));
-    CK(cudaMemset(ds.Qlo, 0, sizeof(float) * N * nv));
+    CK(cudaMemsetAsync(ds.Qhi, 0, sizeof(float) * N * nv, s->stream));
+    CK(cudaMemsetAsync(ds.Qlo, 0, sizeof(float) * N * nv, s->stream));
   }
   if ((rc = upload(s.get(), m.perm, (const void**)&ds.perm))) return rc;
   if ((rc = upload(s.get(), soa_i(cs.sten, N, re.ne - 1), (const void**)&ds.sten))) return rc;
@@ -316,13 +356,13 @@ int cweno_setup(const cweno_mesh* mesh, int order, int pde, int precision, const
   {
     unsigned long long init[4] = {0x7ff0000000000000ull, 0x7ff0000000000000ull, 0x7ff0000000000000ull,
                                   0x7ff0000000000000ull};
-    CK(cudaMemcpy(ds.dtmin, init, sizeof(init), cudaMemcpyHostToDevice));
-    CK(cudaMemset(ds.time, 0, sizeof(double) + 2 * sizeof(int)));
+    CK(cudaMemcpyAsync(ds.dtmin, init, sizeof(init), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemsetAsync(ds.time, 0, sizeof(double) + 2 * sizeof(int), s->stream));
   }
   if ((rc = dev_alloc(s.get(), &p, sizeof(double) * N * nv))) return rc;
   ds.stage = (double*)p;
   CK(s->ops->prepare());
-  CK(cudaDeviceSynchronize());
+  CK(cudaStreamSynchronize(s->stream));
   *out = s.release();
   return CWENO_OK;
 }
@@ -514,9 +554,9 @@ int ader_cweno_run(cweno_solver* s, int nsteps, double dt) {
 int cweno_sync(cweno_solver* s) {
   if (!s) return fail(CWENO_EINVAL, "null solver");
   CK(cudaSetDevice(s->dev));
-  CK(cudaStreamSynchronize(s->stream));
   int st = 0;
-  CK(cudaMemcpy(&st, s->ds.status, sizeof(int), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpyAsync(&st, s->ds.status, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
   if (st) return fail(CWENO_ENAN, "a step produced NaN or non-positive density / pressure");
   return CWENO_OK;
 }
@@ -524,8 +564,8 @@ int cweno_sync(cweno_solver* s) {
 int cweno_get_time(cweno_solver* s, double* t) {
   if (!s || !t) return fail(CWENO_EINVAL, "null argument");
   CK(cudaSetDevice(s->dev));
+  CK(cudaMemcpyAsync(t, s->ds.time, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
-  CK(cudaMemcpy(t, s->ds.time, sizeof(double), cudaMemcpyDeviceToHost));
   return CWENO_OK;
 }
 

@@ -40,4 +40,6 @@ int fail(int code, const std::string& msg);
 int cuda_fail(cudaError_t e, const char* where);
 int enqueue_step(cweno_solver* s, double dt, int cur);
 const RefElem& ref_elem(int d, int M);
+size_t footprint_estimate(int d, int64_t nc, int64_t nf, int order, int pde, int precision);
+extern thread_local int g_setup_threads;
 }  // namespace cw

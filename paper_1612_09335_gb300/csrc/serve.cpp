@@ -1,17 +1,413 @@
-// Serving loop (continuous batching of independent solves).
+// Serving loop: continuous batching of independent ADER-CWENO solves on one
+// GPU.
+//
+// submit -> FIFO queue -> admission (a free slot and the request's device
+// footprint within the budget) -> host setup worker (mesh, stencils, FP64
+// least-squares inverses, uploads on the slot's stream) -> the request's whole
+// run (set_state, nsteps steps captured once as one CUDA graph, state copied
+// to pinned host memory) is launched on its slot stream -> a completion event
+// -> the scheduler retires it (stream-ordered frees), and admits the next.
+// Different requests overlap on the device through their streams; host setup
+// of waiting requests overlaps with the device work of running ones.  No
+// reduction spans requests, so every result equals the same solve run alone.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
 #include "../../include/cweno.h"
 #include "api_internal.h"
 
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Req {
+  uint64_t id = 0;
+  int dim = 2, order = 2, pde = 0, prec = 0, nsteps = 0, nvars = 4;
+  double cfl = 0.5;
+  int64_t nverts = 0, nc = 0;
+  std::vector<double> xyz, period, Q0;
+  std::vector<int32_t> cells;
+  bool has_period = false;
+  size_t est = 0;
+  int status = CWENO_REQ_QUEUED;
+  Clock::time_point t_submit, t_done;
+  cweno_mesh* mesh = nullptr;
+  cweno_solver* solver = nullptr;
+  int slot = -1;
+  cudaEvent_t done = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  double* hout = nullptr;  // pinned: nc * nvars
+  int* hstatus = nullptr;  // pinned
+  std::vector<double> Qout;
+  std::string err;
+};
+
+}  // namespace
+
+struct cweno_server {
+  int dev = 0;
+  size_t budget = 0, used = 0;
+  int max_slots = 1, nworkers = 1, threads_per_setup = 1;
+  std::vector<cudaStream_t> streams;
+  std::vector<int> free_slots;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<Req*> queue;     // submitted, waiting for admission
+  std::deque<Req*> setup_q;   // admitted, waiting for a setup worker
+  std::vector<Req*> inflight; // launched on the device
+  std::map<uint64_t, Req*> all;
+  int active = 0;             // admitted and not retired
+  uint64_t next_id = 1, n_sub = 0, n_adm = 0, n_done = 0, peak = 0;
+  double cell_updates = 0.0;
+  bool stop = false;
+  std::thread sched;
+  std::vector<std::thread> workers;
+  // pinned host buffers are pooled: freeing pinned memory can synchronise the
+  // whole device, which would stall the other requests
+  std::mutex pin_mu;
+  std::multimap<size_t, void*> pinned_free;
+  std::vector<void*> pinned_all;
+  std::map<void*, size_t> pinned_cap;
+};
+
+namespace {
+
+void* pin_get(cweno_server* S, size_t bytes) {
+  std::lock_guard<std::mutex> lk(S->pin_mu);
+  auto it = S->pinned_free.lower_bound(bytes);
+  if (it != S->pinned_free.end()) {
+    void* p = it->second;
+    S->pinned_free.erase(it);
+    return p;
+  }
+  void* p = nullptr;
+  size_t cap = std::max<size_t>(bytes, 4096);
+  if (cudaMallocHost(&p, cap) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  S->pinned_all.push_back(p);
+  S->pinned_cap[p] = cap;
+  return p;
+}
+
+void pin_put(cweno_server* S, void* p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(S->pin_mu);
+  S->pinned_free.insert({S->pinned_cap[p], p});
+}
+
+void release_slot(cweno_server* S, Req* r) {  // caller holds S->mu
+  if (r->slot >= 0) S->free_slots.push_back(r->slot);
+  r->slot = -1;
+  S->used -= std::min(S->used, r->est);
+  S->active -= 1;
+}
+
+void teardown(cweno_server* S, Req* r) {
+  if (r->graph) cudaGraphExecDestroy(r->graph);
+  r->graph = nullptr;
+  if (r->solver) cweno_solver_destroy(r->solver);
+  r->solver = nullptr;
+  if (r->mesh) cweno_mesh_destroy(r->mesh);
+  r->mesh = nullptr;
+  if (r->done) cudaEventDestroy(r->done);
+  r->done = nullptr;
+  pin_put(S, r->hout);
+  r->hout = nullptr;
+  pin_put(S, r->hstatus);
+  r->hstatus = nullptr;
+  std::vector<double>().swap(r->xyz);
+  std::vector<int32_t>().swap(r->cells);
+  std::vector<double>().swap(r->Q0);
+}
+
+// Host setup and launch of one admitted request (worker thread).
+int prepare_and_launch(cweno_server* S, Req* r, std::string& err) {
+  cudaStream_t st = S->streams[r->slot];
+  int rc = cweno_mesh_create(r->dim, r->nverts, r->xyz.data(), r->nc, r->cells.data(),
+                             r->has_period ? r->period.data() : nullptr, &r->mesh);
+  if (rc) return err = cweno_last_error(), rc;
+  cweno_params p;
+  cweno_default_params(&p, r->dim, r->pde);
+  p.cfl = r->cfl;
+  rc = cweno_setup(r->mesh, r->order, r->pde, r->prec, &p, st, &r->solver);
+  if (rc) return err = cweno_last_error(), rc;
+  size_t real = 0;
+  cweno_solver_footprint(r->solver, &real);
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->used = S->used - std::min(S->used, r->est) + real;
+    r->est = real;
+  }
+  r->hout = (double*)pin_get(S, sizeof(double) * r->nc * r->nvars);
+  r->hstatus = (int*)pin_get(S, sizeof(int));
+  if (!r->hout || !r->hstatus) {
+    err = "pinned host allocation failed";
+    return CWENO_ENOMEM;
+  }
+  rc = cweno_set_state(r->solver, r->Q0.data(), 0);
+  if (rc) return err = cweno_last_error(), rc;
+  // the whole run as one graph: nsteps x (rec+predictor, fluxes, update)
+  cweno_solver* s = r->solver;
+  cudaGraph_t g;
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    err = "stream capture failed to start";
+    return CWENO_ECUDA;
+  }
+  int erc = CWENO_OK;
+  for (int k = 0; k < r->nsteps && erc == CWENO_OK; ++k) {
+    erc = cw::enqueue_step(s, 0.0, s->cur);
+    s->cur ^= 1;
+  }
+  if (erc == CWENO_OK) erc = s->ops->get_state(s->ds, s->ds.stage, st) == cudaSuccess ? CWENO_OK : CWENO_ECUDA;
+  cudaError_t e = cudaStreamEndCapture(st, &g);
+  if (erc) return err = "step capture failed", erc;
+  if (e != cudaSuccess) return err = std::string("capture: ") + cudaGetErrorString(e), CWENO_ECUDA;
+  e = cudaGraphInstantiate(&r->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return err = std::string("instantiate: ") + cudaGetErrorString(e), CWENO_ECUDA;
+  if ((e = cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaGraphLaunch(r->graph, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(r->hout, s->ds.stage, sizeof(double) * r->nc * r->nvars, cudaMemcpyDeviceToHost, st)) !=
+          cudaSuccess ||
+      (e = cudaMemcpyAsync(r->hstatus, s->ds.status, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+      (e = cudaEventRecord(r->done, st)) != cudaSuccess)
+    return err = std::string("launch: ") + cudaGetErrorString(e), CWENO_ECUDA;
+  return CWENO_OK;
+}
+
+void worker_main(cweno_server* S) {
+  cudaSetDevice(S->dev);
+  cw::g_setup_threads = S->threads_per_setup;
+  for (;;) {
+    Req* r = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->cv.wait(lk, [&] { return S->stop || !S->setup_q.empty(); });
+      if (S->stop) return;
+      r = S->setup_q.front();
+      S->setup_q.pop_front();
+    }
+    std::string err;
+    int rc = prepare_and_launch(S, r, err);
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (rc) {
+      r->status = CWENO_REQ_ERROR;
+      r->err = err;
+      r->t_done = Clock::now();
+      if (r->slot >= 0) cudaStreamSynchronize(S->streams[r->slot]);
+      teardown(S, r);
+      release_slot(S, r);
+      S->n_done++;
+    } else {
+      r->status = CWENO_REQ_RUNNING;
+      S->inflight.push_back(r);
+    }
+    S->cv.notify_all();
+  }
+}
+
+void scheduler_main(cweno_server* S) {
+  cudaSetDevice(S->dev);
+  for (;;) {
+    std::vector<Req*> finished;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      if (S->stop) return;
+      // admission: FIFO, while a slot is free and the footprint fits
+      while (!S->queue.empty() && !S->free_slots.empty() && S->used + S->queue.front()->est <= S->budget) {
+        Req* r = S->queue.front();
+        S->queue.pop_front();
+        r->slot = S->free_slots.back();
+        S->free_slots.pop_back();
+        S->used += r->est;
+        S->active += 1;
+        S->n_adm++;
+        S->peak = std::max<uint64_t>(S->peak, (uint64_t)S->active);
+        S->setup_q.push_back(r);
+        S->cv.notify_all();
+      }
+      // completion
+      for (size_t k = 0; k < S->inflight.size();) {
+        Req* r = S->inflight[k];
+        if (cudaEventQuery(r->done) == cudaSuccess) {
+          finished.push_back(r);
+          S->inflight[k] = S->inflight.back();
+          S->inflight.pop_back();
+        } else {
+          ++k;
+        }
+      }
+    }
+    for (Req* r : finished) {
+      r->t_done = Clock::now();
+      r->Qout.assign(r->hout, r->hout + r->nc * r->nvars);
+      int st = *r->hstatus;
+      teardown(S, r);
+      std::lock_guard<std::mutex> lk(S->mu);
+      r->status = st ? CWENO_REQ_ERROR : CWENO_REQ_DONE;
+      if (st) r->err = "the solve produced NaN or non-positive density / pressure";
+      release_slot(S, r);
+      S->n_done++;
+      S->cell_updates += (double)r->nc * r->nsteps;
+      S->cv.notify_all();
+    }
+    if (finished.empty()) {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->cv.wait_for(lk, std::chrono::microseconds(100));
+    }
+  }
+}
+
+}  // namespace
+
 extern "C" {
-int serve_create(size_t, int, int, cweno_server** out) {
-  if (out) *out = nullptr;
-  return cw::fail(CWENO_EINVAL, "serving is not built yet");
+
+int serve_create(size_t mem_budget, int max_slots, int nworkers, cweno_server** out) {
+  if (!out) return cw::fail(CWENO_EINVAL, "null output handle");
+  *out = nullptr;
+  std::unique_ptr<cweno_server> S(new cweno_server());
+  if (cudaGetDevice(&S->dev) != cudaSuccess) return cw::fail(CWENO_ECUDA, "no CUDA device");
+  if (mem_budget == 0) {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return cw::fail(CWENO_ECUDA, "cudaMemGetInfo failed");
+    mem_budget = (size_t)(0.8 * (double)fr);
+  }
+  S->budget = mem_budget;
+  S->max_slots = max_slots > 0 ? max_slots : 64;
+  unsigned hc = std::max(1u, std::thread::hardware_concurrency());
+  S->nworkers = nworkers > 0 ? nworkers : (int)std::max(2u, hc / 4);
+  S->threads_per_setup = (int)std::max(1u, hc / (unsigned)S->nworkers);
+  S->streams.resize(S->max_slots);
+  for (int k = 0; k < S->max_slots; ++k) {
+    if (cudaStreamCreateWithFlags(&S->streams[k], cudaStreamNonBlocking) != cudaSuccess)
+      return cw::fail(CWENO_ECUDA, "stream creation failed");
+    S->free_slots.push_back(S->max_slots - 1 - k);
+  }
+  cweno_server* raw = S.get();
+  for (int k = 0; k < S->nworkers; ++k) S->workers.emplace_back(worker_main, raw);
+  S->sched = std::thread(scheduler_main, raw);
+  *out = S.release();
+  return CWENO_OK;
 }
-int serve_submit(cweno_server*, const cweno_request*, uint64_t*) { return cw::fail(CWENO_EINVAL, "no server"); }
-int serve_poll(cweno_server*, uint64_t, int*, double*, double*) { return cw::fail(CWENO_EINVAL, "no server"); }
-int serve_drain(cweno_server*, double) { return cw::fail(CWENO_EINVAL, "no server"); }
-int serve_stats(cweno_server*, uint64_t*, uint64_t*, uint64_t*, uint64_t*, double*) {
-  return cw::fail(CWENO_EINVAL, "no server");
+
+int serve_submit(cweno_server* S, const cweno_request* q, uint64_t* id) {
+  if (!S || !q || !id) return cw::fail(CWENO_EINVAL, "null argument");
+  if ((q->dim != 2 && q->dim != 3) || q->nv <= 0 || q->nc <= 0 || !q->xyz || !q->cells || !q->Q0 ||
+      q->order < 2 || q->order > 4 || q->nsteps < 0 || !(q->cfl > 0) ||
+      (q->pde != CWENO_EULER && q->pde != CWENO_MHD_GLM) ||
+      (q->precision != CWENO_FP64 && q->precision != CWENO_FP32_MIXED))
+    return cw::fail(CWENO_EINVAL, "bad request");
+  std::unique_ptr<Req> r(new Req());
+  r->dim = q->dim;
+  r->order = q->order;
+  r->pde = q->pde;
+  r->prec = q->precision;
+  r->nsteps = q->nsteps;
+  r->cfl = q->cfl;
+  r->nverts = q->nv;
+  r->nc = q->nc;
+  r->nvars = cweno_nvars(q->dim, q->pde);
+  r->xyz.assign(q->xyz, q->xyz + q->nv * q->dim);
+  r->cells.assign(q->cells, q->cells + q->nc * (q->dim + 1));
+  r->Q0.assign(q->Q0, q->Q0 + q->nc * r->nvars);
+  if (q->period) {
+    r->has_period = true;
+    r->period.assign(q->period, q->period + q->dim);
+  }
+  // faces <= (d+1) nc (every face counted from each side)
+  r->est = cw::footprint_estimate(q->dim, q->nc, (q->dim + 1) * q->nc, q->order, q->pde, q->precision);
+  r->t_submit = Clock::now();
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (r->est > S->budget)
+    return cw::fail(CWENO_EBUSY, "request footprint " + std::to_string(r->est) + " B exceeds the server budget " +
+                                     std::to_string(S->budget) + " B");
+  r->id = S->next_id++;
+  *id = r->id;
+  S->all[r->id] = r.get();
+  S->queue.push_back(r.release());
+  S->n_sub++;
+  S->cv.notify_all();
+  return CWENO_OK;
 }
-void serve_destroy(cweno_server*) {}
+
+int serve_poll(cweno_server* S, uint64_t id, int* status, double* Q_out, double* latency_s) {
+  if (!S || !status) return cw::fail(CWENO_EINVAL, "null argument");
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->all.find(id);
+  if (it == S->all.end()) return cw::fail(CWENO_ENOTFOUND, "unknown request id");
+  Req* r = it->second;
+  *status = r->status;
+  if (latency_s)
+    *latency_s = (r->status == CWENO_REQ_DONE || r->status == CWENO_REQ_ERROR)
+                     ? std::chrono::duration<double>(r->t_done - r->t_submit).count()
+                     : 0.0;
+  if (r->status == CWENO_REQ_ERROR) {
+    cw::fail(CWENO_ENAN, r->err);
+  }
+  if ((r->status == CWENO_REQ_DONE || r->status == CWENO_REQ_ERROR) && Q_out) {
+    if (r->status == CWENO_REQ_DONE) std::memcpy(Q_out, r->Qout.data(), sizeof(double) * r->Qout.size());
+    S->all.erase(it);
+    delete r;
+  }
+  return CWENO_OK;
 }
+
+int serve_drain(cweno_server* S, double timeout_s) {
+  if (!S) return cw::fail(CWENO_EINVAL, "null server");
+  std::unique_lock<std::mutex> lk(S->mu);
+  bool ok = S->cv.wait_for(lk, std::chrono::duration<double>(timeout_s), [&] { return S->n_done == S->n_sub; });
+  if (!ok) return cw::fail(CWENO_ETIMEDOUT, "requests still running after the timeout");
+  return CWENO_OK;
+}
+
+int serve_stats(cweno_server* S, uint64_t* submitted, uint64_t* admitted, uint64_t* completed, uint64_t* peak_running,
+                double* cell_updates) {
+  if (!S) return cw::fail(CWENO_EINVAL, "null server");
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (submitted) *submitted = S->n_sub;
+  if (admitted) *admitted = S->n_adm;
+  if (completed) *completed = S->n_done;
+  if (peak_running) *peak_running = S->peak;
+  if (cell_updates) *cell_updates = S->cell_updates;
+  return CWENO_OK;
+}
+
+void serve_destroy(cweno_server* S) {
+  if (!S) return;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+    S->cv.notify_all();
+  }
+  for (auto& t : S->workers) t.join();
+  if (S->sched.joinable()) S->sched.join();
+  cudaSetDevice(S->dev);
+  for (auto& kv : S->all) {
+    Req* r = kv.second;
+    if (r->slot >= 0) cudaStreamSynchronize(S->streams[r->slot]);
+    teardown(S, r);
+    delete r;
+  }
+  for (cudaStream_t st : S->streams) {
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  }
+  for (void* p : S->pinned_all) cudaFreeHost(p);
+  delete S;
+}
+
+}  // extern "C"
