@@ -212,6 +212,92 @@ def cpu_baseline_run(name, seconds_budget=20.0, cells_hint=None):
                        f"untimed warm step, single host thread")
 
 
+def serving_run(cw, nreq, steps=50, seed=42, max_slots=64, seq_sample=16):
+    """Serving mix shaped like the paper-scale serving workload: independent 2D
+    Euler solves (periodic meshes of 1k-200k cells, log-uniform; orders P1-P3;
+    vortex or explosion data), 50 steps at CFL 0.5, FP32-mixed.  Phase 1 runs
+    them as a closed batch to measure capacity; phase 2 submits them as a
+    seeded Poisson stream at 0.8x that capacity and reports latency
+    percentiles (submit to completion, host wall clock, setup included).
+    The sequential baseline runs a sample one after another through the
+    solver API in FP64 (setup included)."""
+    import numpy as np
+    from paper_1612_09335_gb300 import workloads as wl
+    stream = wl.serving_stream(nreq=nreq, seed=seed, rate=None)
+    inputs = [wl.serving_request_inputs(r) for r in stream]
+    cells = sum(m.nc for m, _ in inputs)
+    # phase 1: closed batch
+    srv = cw.Server(max_slots=max_slots)
+    t0 = time.perf_counter()
+    ids = [srv.submit(m, Q, r["order"], 0.5, steps) for (m, Q), r in zip(inputs, stream)]
+    srv.drain(3600)
+    t_closed = time.perf_counter() - t0
+    ok = sum(srv.poll(i)[0] == cw.REQ_DONE for i in ids)
+    peak1 = srv.stats()["peak_running"]
+    srv.close()
+    cap = nreq / t_closed
+    # phase 2: Poisson arrivals at 0.8x capacity
+    arr = wl.serving_stream(nreq=nreq, seed=seed, rate=0.8 * cap)
+    srv = cw.Server(max_slots=max_slots)
+    t0 = time.perf_counter()
+    ids = []
+    for (m, Q), r in zip(inputs, arr):
+        dt_wait = r["t"] - (time.perf_counter() - t0)
+        if dt_wait > 0:
+            time.sleep(dt_wait)
+        ids.append(srv.submit(m, Q, r["order"], 0.5, steps))
+    srv.drain(3600)
+    t_open = time.perf_counter() - t0
+    lat = []
+    for i in ids:
+        st, _, l = srv.poll(i)
+        if st == cw.REQ_DONE:
+            lat.append(l)
+    stats = srv.stats()
+    srv.close()
+    # sequential FP64 per-solve baseline on a sample of the same requests
+    k = min(seq_sample, nreq)
+    seq_cells = 0
+    ts = time.perf_counter()
+    for (m, Q), r in list(zip(inputs, stream))[:k]:
+        sv = cw.Solver(cw.Mesh.from_workload(m), r["order"], cw.EULER, cw.FP64, cfl=0.5)
+        sv.set_state(Q)
+        sv.run(steps)
+        sv.get_state()
+        sv.close()
+        seq_cells += m.nc
+    t_seq = time.perf_counter() - ts
+    lat = np.array(lat)
+    return {"requests": nreq, "steps_per_request": steps, "cells_total": cells, "completed_closed": ok,
+            "closed_batch_s": t_closed, "closed_cell_updates_per_s": cells * steps / t_closed,
+            "capacity_req_per_s": cap, "arrival_rate_req_per_s": 0.8 * cap, "open_wall_s": t_open,
+            "p50_latency_s": float(np.percentile(lat, 50)) if len(lat) else None,
+            "p99_latency_s": float(np.percentile(lat, 99)) if len(lat) else None,
+            "open_cell_updates_per_s": stats["cell_updates"] / t_open, "completed_open": len(lat),
+            "peak_running": int(max(peak1, stats["peak_running"])), "max_slots": max_slots,
+            "sequential_fp64_cell_updates_per_s": seq_cells * steps / t_seq,
+            "sequential_sample_requests": k,
+            "note": "wall clock includes host setup (mesh, stencils, FP64 least-squares inverses)"}
+
+
+def accuracy_run(cw, m, cfg, Q0, nsteps=10):
+    """FP32-mixed against the FP64 mode (itself parity-tested against the
+    oracle) after nsteps steps with one fixed time step; per-variable L1
+    (volume weighted, relative to the variable's L1 norm) and L_inf errors,
+    and the drift of sum |T_i| Q_i in the FP32-mixed run."""
+    a = cw.Solver(m, cfg["order"], cfg["pde"], cw.FP32_MIXED)
+    b = cw.Solver(m, cfg["order"], cfg["pde"], cw.FP64)
+    a.set_state(Q0)
+    b.set_state(Q0)
+    dt = b.stable_dt()
+    for _ in range(nsteps):
+        a.step(dt)
+        b.step(dt)
+    a.sync()
+    b.sync()
+    return a.get_state(), b.get_state(), dt
+
+
 # ---------------------------------------------------------------------- ours
 def run_ours(args):
     import numpy as np
@@ -358,6 +444,21 @@ def run_ours(args):
         out["e2e"] = {"value": ws * N * ke / el, "unit": "cell-updates/s", "h2d_bytes_per_step": N * nv * 8,
                       "d2h_bytes_per_step": N * nv * 8, "steps": ke,
                       "path": "cweno_set_state(pinned host) + ader_cweno_step + cweno_get_state(pinned host)"}
+    # accuracy of the FP32-mixed mode against the FP64 mode, and conservation
+    if not args.no_accuracy:
+        import numpy as np
+        qa, qb, dtf = accuracy_run(cw, m, cfg, Q0)
+        Xv = mesh.cell_vertices()
+        vol = np.abs(np.linalg.det(Xv[:, 1:] - Xv[:, :1])) / math.factorial(mesh.dim)
+        l1 = (vol @ np.abs(qa - qb)) / np.maximum(vol @ np.abs(qb), 1e-300)
+        linf = np.abs(qa - qb).max(axis=0) / np.maximum(np.abs(qb).max(axis=0), 1e-300)
+        tot0 = vol @ Q0
+        drift = np.abs(vol @ qa - tot0) / np.maximum(np.abs(tot0), vol @ np.abs(Q0))
+        out["accuracy"] = {"reference": "FP64 mode (parity-tested against the FP64 oracle)", "steps": 10,
+                           "dt": dtf, "L1_rel": [float(x) for x in l1], "Linf_rel": [float(x) for x in linf],
+                           "conservation_drift_rel": [float(x) for x in drift]}
+    if rank == 0 and not args.no_serve:
+        out["serving"] = serving_run(cw, args.serve_requests)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_run(name)
     if rank == 0:
@@ -412,6 +513,10 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=128,
+                    help="requests in the serving mix (the full mix has 512)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
