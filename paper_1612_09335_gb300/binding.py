@@ -293,6 +293,7 @@ class Server:
         _check(lib().serve_create(int(mem_budget), int(max_slots), int(nworkers), C.byref(h)))
         self.h = h
         self._keep = {}
+        self.errors = {}
 
     def submit(self, mesh, Q0, order: int, cfl: float, nsteps: int, pde: int = EULER,
                precision: int = FP32_MIXED) -> int:
@@ -317,6 +318,8 @@ class Server:
             out = np.zeros((nc, nv))
         _check(lib().serve_poll(self.h, C.c_uint64(rid), C.byref(st),
                                 out.ctypes.data_as(_DP) if out is not None else None, C.byref(lat)))
+        if st.value == REQ_ERROR:
+            self.errors[rid] = lib().cweno_last_error().decode()
         if st.value != REQ_DONE:
             out = None
         return st.value, out, lat.value

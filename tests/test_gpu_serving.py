@@ -43,7 +43,7 @@ def test_served_results_equal_alone(cw, wl):
     got = []
     for rid in ids:
         st, Q, lat = srv.poll(rid)
-        assert st == cw.REQ_DONE and Q is not None and lat > 0
+        assert st == cw.REQ_DONE and Q is not None and lat > 0, srv.errors
         got.append(Q)
     stats = srv.stats()
     assert stats["completed"] == len(reqs) and stats["peak_running"] <= 4
