@@ -453,7 +453,9 @@ def run_ours(args):
         l1 = (vol @ np.abs(qa - qb)) / np.maximum(vol @ np.abs(qb), 1e-300)
         linf = np.abs(qa - qb).max(axis=0) / np.maximum(np.abs(qb).max(axis=0), 1e-300)
         tot0 = vol @ Q0
-        drift = np.abs(vol @ qa - tot0) / np.maximum(np.abs(tot0), vol @ np.abs(Q0))
+        scale = np.maximum(np.maximum(np.abs(tot0), vol @ np.abs(Q0)), vol @ np.abs(qa))
+        scale = np.maximum(scale, 1e-6 * scale.max())
+        drift = np.abs(vol @ qa - tot0) / scale
         out["accuracy"] = {"reference": "FP64 mode (parity-tested against the FP64 oracle)", "steps": 10,
                            "dt": dtf, "L1_rel": [float(x) for x in l1], "Linf_rel": [float(x) for x in linf],
                            "conservation_drift_rel": [float(x) for x in drift]}

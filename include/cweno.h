@@ -72,7 +72,7 @@ typedef struct {
   int picard_iters;    /* iterations of Eq. (CGfinal); <= 0 -> M + 1 */
   int linear_weights;  /* test mode: omega := lambda (no indicators) */
   int positivity;      /* 1 (default): scale w toward the cell average where
-                          density or pressure would fall below 1e-10 of their
+                          density or pressure would fall below 1e-6 of their
                           cell-average values at a lattice node (Zhang & Shu
                           scaling; not part of the paper, inactive wherever the
                           reconstruction is admissible); 0: the paper's scheme */

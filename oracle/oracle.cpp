@@ -47,7 +47,8 @@
 //   * s_max and the time-step speed take sqrt(max(0, .)) of the sound speed.
 // Addition not in the paper (switchable, on by default): a positivity
 // preserving scaling of the reconstruction toward the cell average at the
-// lattice nodes, first for the density, then for the pressure (the scaling
+// lattice nodes, first for the density, then for the pressure, with floors
+// of 1e-6 of their cell-average values (the scaling
 // limiter of Zhang & Shu, J. Comput. Phys. 229 (2010) 3091), and, at a face
 // quadrature point where one side's predictor is not an admissible state,
 // that side's cell average in place of its trace.  Where everything is
@@ -1040,10 +1041,12 @@ bool reconstruct_cell(OSolver& S, const double* Q, long i, RecOut& out, std::str
   if (S.P.positivity) {
     // Positivity scaling (addition, see the header): w <- Qbar + theta (w - Qbar)
     // with theta the largest value in [0,1] keeping density, then pressure,
-    // above 1e-10 times their cell-average values at every lattice node.
-    // Density and pressure are concave in the conserved variables, so the
-    // linear interpolation bound below is sufficient.
-    const double floor_rel = 1e-10;
+    // above 1e-6 times their cell-average values at every lattice node (a
+    // floor above single-precision rounding, so both precisions of the
+    // product take the same decisions).  Density and pressure are concave in
+    // the conserved variables, so the linear interpolation bound below is
+    // sufficient; a node whose scaled density is not positive gives theta 0.
+    const double floor_rel = 1e-6;
     const double* qb = &Q[i * nu];
     double rb = qb[0], pb = pressure(S.pde, d, S.P, qb);
     std::vector<std::vector<double>> node(S.Mc, std::vector<double>(nu));
@@ -1059,6 +1062,10 @@ bool reconstruct_cell(OSolver& S, const double* Q, long i, RecOut& out, std::str
       for (int n = 0; n < S.Mc; ++n) {
         std::vector<double> q(nu);
         for (int v = 0; v < nu; ++v) q[v] = qb[v] + th_rho * (node[n][v] - qb[v]);
+        if (!(q[0] > 0.0)) {
+          th_p = 0.0;
+          continue;
+        }
         double pk = pressure(S.pde, d, S.P, q.data());
         if (pk < floor_rel * pb) th_p = std::min(th_p, (pb - floor_rel * pb) / (pb - pk));
       }

@@ -427,10 +427,11 @@ __global__ void __launch_bounds__(128) k_rec_pred(KArgs<C> a, CellTab<C> tb) {
 
   // ---- positivity scaling toward the cell average (switchable; an addition
   // to the paper, the Zhang-Shu scaling limiter): density first, then the
-  // pressure, both kept above 1e-10 of their cell-average values at every
-  // lattice node; density and pressure are concave in the conserved state
+  // pressure, both kept above 1e-6 of their cell-average values at every
+  // lattice node (a floor above FP32 rounding of Qbar + theta (w - Qbar));
+  // density and pressure are concave in the conserved state
   if (a.pos) {
-    const T fl = T(1e-10);
+    const T fl = T(1e-6);
     T qb[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) qb[v] = qi[v] + qlo[v];
@@ -458,6 +459,10 @@ __global__ void __launch_bounds__(128) k_rec_pred(KArgs<C> a, CellTab<C> tb) {
 #pragma unroll
           for (int l = 0; l < MC1; ++l) s += tb.E[n][l] * w[l][v];
           q[v] = qb[v] + th * s;
+        }
+        if (!(q[0] > T(0))) {
+          thp = T(0);
+          continue;
         }
         const T pk = PH::pressure(q, a.gamma);
         if (pk < fl * pb) {

@@ -632,7 +632,7 @@ def test_positivity_scaling_needed_and_effective(orc, wl):
     rb = Q[:, 0][:, None]
     pb = _pressure(Q)[:, None]
     # the floors hold up to the rounding of Qbar + theta (w - Qbar) (~1e-16 Qbar)
-    assert np.all(on[..., 0] >= 1e-10 * rb - 1e-14 * rb) and np.all(_pressure(on) >= 1e-10 * pb - 1e-14 * pb)
+    assert np.all(on[..., 0] >= 1e-6 * rb - 1e-14 * rb) and np.all(_pressure(on) >= 1e-6 * pb - 1e-14 * pb)
     assert on[..., 0].min() > 0 and _pressure(on).min() > 0
     changed = np.where(np.abs(on - off).max(axis=(1, 2)) > 0)[0]
     assert 0 < len(changed) < m.nc // 20
