@@ -86,10 +86,11 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            if not os.path.exists(_build.LIB):
+            path = os.environ.get("CWENO_LIBRARY") or _build.LIB   # a variant build, for launch sweeps
+            if not os.path.exists(path):
                 raise RuntimeError("libcweno.so is not built; run paper_1612_09335_gb300.build() "
                                    "(the CUDA path has no fallback)")
-            L = C.CDLL(_build.LIB)
+            L = C.CDLL(path)
             for name, res, args in SIGNATURES:
                 fn = getattr(L, name)
                 fn.restype = res

@@ -299,8 +299,17 @@ __device__ __forceinline__ T pow4(T x) {
 }
 
 // ---------------------------------------------------------- rec + predictor
+// Minimum resident blocks per SM requested from the register allocator
+// (launch shape sweeps); 1 leaves the allocation unconstrained.
+#ifndef CW_REC_MINB
+#define CW_REC_MINB 1
+#endif
+#ifndef CW_FLUX_MINB
+#define CW_FLUX_MINB 1
+#endif
+
 template <class C, bool REC_ONLY>
-__global__ void __launch_bounds__(128) k_rec_pred(KArgs<C> a, CellTab<C> tb) {
+__global__ void __launch_bounds__(128, CW_REC_MINB) k_rec_pred(KArgs<C> a, CellTab<C> tb) {
   using T = typename C::T;
   constexpr int D = C::D, NV = C::NV, MC1 = C::MC1, NE1 = C::NE - 1, NS = C::NS;
   using PH = Phys<D, C::PDE, T>;
@@ -543,17 +552,20 @@ __global__ void __launch_bounds__(128) k_rec_pred(KArgs<C> a, CellTab<C> tb) {
       typename PH::Prim pr = PH::prim(q0, a.gamma);
       T Ge[D][NV];
 #pragma unroll
-      for (int e = 0; e < D; ++e) flux_normal<D, C::PDE, T>(q0, pr, J[e], Ge[e], a.ch);
+      for (int e = 0; e < D; ++e) {
+        flux_normal<D, C::PDE, T>(q0, pr, J[e], Ge[e], a.ch);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Ge[e][v] = dt * (Ge[e][v] - Gref[e][v]);
+      }
 #pragma unroll
       for (int k = 0; k < L1; ++k)
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          const T cq = tb.C0[k][n] * dq0[v];
-          T s = T(0);
+          T b = base[k][v] + tb.C0[k][n] * dq0[v];
 #pragma unroll
-          for (int e = 0; e < D; ++e) s += tb.P[e][k][n] * (Ge[e][v] - Gref[e][v]);
-          base[k][v] += cq - dt * s;
-          q1[k][v] += cq;
+          for (int e = 0; e < D; ++e) b -= tb.P[e][k][n] * Ge[e][v];
+          base[k][v] = b;
+          q1[k][v] += tb.C0[k][n] * dq0[v];
         }
     }
     // Picard iterations of Eq. (CGfinal), on deviations
@@ -571,15 +583,19 @@ __global__ void __launch_bounds__(128) k_rec_pred(KArgs<C> a, CellTab<C> tb) {
         typename PH::Prim pr = PH::prim(ql, a.gamma);
         T Ge[D][NV];
 #pragma unroll
-        for (int e = 0; e < D; ++e) flux_normal<D, C::PDE, T>(ql, pr, J[e], Ge[e], a.ch);
+        for (int e = 0; e < D; ++e) {
+          flux_normal<D, C::PDE, T>(ql, pr, J[e], Ge[e], a.ch);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) Ge[e][v] = dt * (Ge[e][v] - Gref[e][v]);
+        }
 #pragma unroll
         for (int k = 0; k < L1; ++k)
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
-            T s = T(0);
+            T s = nq[k][v];
 #pragma unroll
-            for (int e = 0; e < D; ++e) s += tb.P[e][k][L0 + l] * (Ge[e][v] - Gref[e][v]);
-            nq[k][v] -= dt * s;
+            for (int e = 0; e < D; ++e) s -= tb.P[e][k][L0 + l] * Ge[e][v];
+            nq[k][v] = s;
           }
       }
 #pragma unroll
@@ -596,7 +612,7 @@ __global__ void __launch_bounds__(128) k_rec_pred(KArgs<C> a, CellTab<C> tb) {
 
 // ----------------------------------------------------------------- fluxes
 template <class C>
-__global__ void __launch_bounds__(128) k_flux(KArgs<C> a, int use_smem) {
+__global__ void __launch_bounds__(128, CW_FLUX_MINB) k_flux(KArgs<C> a, int use_smem) {
   using T = typename C::T;
   constexpr int D = C::D, NV = C::NV, L = C::L, NQS = C::NQS, NQT = C::NQT, CH = C::CH;
   using PH = Phys<D, C::PDE, T>;
