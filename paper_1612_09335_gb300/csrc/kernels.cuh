@@ -50,10 +50,18 @@ struct Cfg {
   static constexpr int NQS = D == 2 ? M + 1 : (M + 1) * (M + 1);
   static constexpr int NQT = M + 1;
   static constexpr int NCODE = D == 2 ? 6 : 24;
-  static constexpr int TABN = NCODE * NQT * NQS * L;
+  // face tables: each (code, time point, space point) row of L basis values
+  // is padded to a multiple of one 16-byte vector
+  static constexpr int VW = 16 / (int)sizeof(T_);
+  static constexpr int LP = (L + VW - 1) / VW * VW;
+  static constexpr int TABN = NCODE * NQT * NQS * LP;
   // time points processed per pass of the face kernel (register budget)
+#ifdef CW_FLUX_CH
+  static constexpr int CH = (NQT % CW_FLUX_CH == 0) ? CW_FLUX_CH : 1;
+#else
   static constexpr int CH = (2 * NQT * NQS * NV <= 96) ? NQT
                             : (NQT % 2 == 0 && 2 * 2 * NQS * NV <= 96) ? 2 : 1;
+#endif
 };
 
 template <class C>
@@ -296,6 +304,56 @@ template <typename T>
 __device__ __forceinline__ T pow4(T x) {
   T y = x * x;
   return y * y;
+}
+
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using V = float4;
+  __device__ __forceinline__ static float get(const float4& x, int j) {
+    return j == 0 ? x.x : j == 1 ? x.y : j == 2 ? x.z : x.w;
+  }
+  __device__ __forceinline__ static float4 make(const float* a) { return make_float4(a[0], a[1], a[2], a[3]); }
+};
+template <>
+struct Vec16<double> {
+  using V = double2;
+  __device__ __forceinline__ static double get(const double2& x, int j) { return j == 0 ? x.x : x.y; }
+  __device__ __forceinline__ static double2 make(const double* a) { return make_double2(a[0], a[1]); }
+};
+
+// The NV values of one space-time node of one cell are contiguous in q_hat
+// ([node][cell][var]); with NV * sizeof(T) a multiple of 16 bytes they move
+// as 128-bit accesses (coalesced across consecutive cells of a warp).
+template <int NV, typename T>
+__device__ __forceinline__ void load_node(const T* __restrict__ p, T* out) {
+  if constexpr ((NV * sizeof(T)) % 16 == 0) {
+    using V = typename Vec16<T>::V;
+    constexpr int W = 16 / sizeof(T);
+#pragma unroll
+    for (int k = 0; k < NV / W; ++k) {
+      const V x = __ldg(reinterpret_cast<const V*>(p) + k);
+#pragma unroll
+      for (int j = 0; j < W; ++j) out[k * W + j] = Vec16<T>::get(x, j);
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) out[v] = __ldg(p + v);
+  }
+}
+
+template <int NV, typename T>
+__device__ __forceinline__ void store_node(T* __restrict__ p, const T* in) {
+  if constexpr ((NV * sizeof(T)) % 16 == 0) {
+    using V = typename Vec16<T>::V;
+    constexpr int W = 16 / sizeof(T);
+#pragma unroll
+    for (int k = 0; k < NV / W; ++k) reinterpret_cast<V*>(p)[k] = Vec16<T>::make(in + k * W);
+  } else {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) p[v] = in[v];
+  }
 }
 
 // ---------------------------------------------------------- rec + predictor
@@ -547,8 +605,8 @@ __global__ void __launch_bounds__(128, CW_REC_MINB) k_rec_pred(KArgs<C> a, CellT
         for (int l = 0; l < MC1; ++l) s += tb.E[n][l] * w[l][v];
         dq0[v] = s;
         q0[v] = qb[v] + s;
-        a.qhat[(int64_t)(n * NV + v) * N + i] = s;
       }
+      store_node<NV, T>(a.qhat + ((int64_t)n * N + i) * NV, dq0);
       typename PH::Prim pr = PH::prim(q0, a.gamma);
       T Ge[D][NV];
 #pragma unroll
@@ -604,13 +662,50 @@ __global__ void __launch_bounds__(128, CW_REC_MINB) k_rec_pred(KArgs<C> a, CellT
         for (int v = 0; v < NV; ++v) q1[k][v] = nq[k][v];
     }
 #pragma unroll
-    for (int k = 0; k < L1; ++k)
-#pragma unroll
-      for (int v = 0; v < NV; ++v) a.qhat[(int64_t)((L0 + k) * NV + v) * N + i] = q1[k][v];
+    for (int k = 0; k < L1; ++k) store_node<NV, T>(a.qhat + ((int64_t)(L0 + k) * N + i) * NV, q1[k]);
   }
 }
 
 // ----------------------------------------------------------------- fluxes
+// Predictor deviations of cell c at the CH x NQS space-time points of one
+// pass: tr[tt][q][v] += theta_l(point) q_hat_l[v], basis values read from the
+// padded table as 16-byte vectors, VW nodes at a time.
+template <class C>
+__device__ __forceinline__ void face_traces(const typename C::T* __restrict__ qhat, int64_t c, int64_t N,
+                                            const typename C::T* tcode, int t0,
+                                            typename C::T (&tr)[C::CH][C::NQS][C::NV]) {
+  using T = typename C::T;
+  using V = typename Vec16<T>::V;
+  constexpr int NV = C::NV, L = C::L, LP = C::LP, VW = C::VW, NQS = C::NQS, CH = C::CH;
+#pragma unroll 1
+  for (int l4 = 0; l4 < LP; l4 += VW) {
+    T ql[VW][NV];
+#pragma unroll
+    for (int j = 0; j < VW; ++j) {
+      if (l4 + j < L) {
+        load_node<NV, T>(qhat + ((int64_t)(l4 + j) * N + c) * NV, ql[j]);
+      } else {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) ql[j][v] = T(0);
+      }
+    }
+#pragma unroll
+    for (int tt = 0; tt < CH; ++tt)
+#pragma unroll
+      for (int q = 0; q < NQS; ++q) {
+        const V th = *reinterpret_cast<const V*>(tcode + ((t0 + tt) * NQS + q) * LP + l4);
+#pragma unroll
+        for (int j = 0; j < VW; ++j) {
+          if (l4 + j < L) {
+            const T tj = Vec16<T>::get(th, j);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) tr[tt][q][v] += tj * ql[j][v];
+          }
+        }
+      }
+  }
+}
+
 template <class C>
 __global__ void __launch_bounds__(128, CW_FLUX_MINB) k_flux(KArgs<C> a, int use_smem) {
   using T = typename C::T;
@@ -631,8 +726,8 @@ __global__ void __launch_bounds__(128, CW_FLUX_MINB) k_flux(KArgs<C> a, int use_
   for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < F; f += (int64_t)gridDim.x * blockDim.x) {
     const int64_t Lc = a.fL[f];
     const int64_t Rc = a.fR[f];
-    const T* tL = tab + (int)a.codeL[f] * (NQT * NQS * L);
-    const T* tR = tab + (int)a.codeR[f] * (NQT * NQS * L);
+    const T* tL = tab + (int)a.codeL[f] * (NQT * NQS * C::LP);
+    const T* tR = tab + (int)a.codeR[f] * (NQT * NQS * C::LP);
     T n[D];
 #pragma unroll
     for (int e = 0; e < D; ++e) n[e] = a.fn[e * F + f];
@@ -670,35 +765,9 @@ __global__ void __launch_bounds__(128, CW_FLUX_MINB) k_flux(KArgs<C> a, int use_
             trL[tt][q][v] = T(0);
             trR[tt][q][v] = T(0);
           }
-#pragma unroll 2
-      for (int l = 0; l < L; ++l) {
-        T ql[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) ql[v] = __ldg(a.qhat + (int64_t)(l * NV + v) * N + Lc);
-#pragma unroll
-        for (int tt = 0; tt < CH; ++tt)
-#pragma unroll
-          for (int q = 0; q < NQS; ++q) {
-            const T th = tL[((t0 + tt) * NQS + q) * L + l];
-#pragma unroll
-            for (int v = 0; v < NV; ++v) trL[tt][q][v] += th * ql[v];
-          }
-      }
+      face_traces<C>(a.qhat, Lc, N, tL, t0, trL);
       if (Rc >= 0) {
-#pragma unroll 2
-        for (int l = 0; l < L; ++l) {
-          T ql[NV];
-#pragma unroll
-          for (int v = 0; v < NV; ++v) ql[v] = __ldg(a.qhat + (int64_t)(l * NV + v) * N + Rc);
-#pragma unroll
-          for (int tt = 0; tt < CH; ++tt)
-#pragma unroll
-            for (int q = 0; q < NQS; ++q) {
-              const T th = tR[((t0 + tt) * NQS + q) * L + l];
-#pragma unroll
-              for (int v = 0; v < NV; ++v) trR[tt][q][v] += th * ql[v];
-            }
-        }
+        face_traces<C>(a.qhat, Rc, N, tR, t0, trR);
       } else {
 #pragma unroll
         for (int tt = 0; tt < CH; ++tt)
@@ -897,7 +966,7 @@ __global__ void k_qhat_out(KArgs<C> a, double* user) {
         qbar = (double)a.Qhi[v * a.N + i] + (double)a.Qlo[v * a.N + i];
       else
         qbar = a.Q[v * a.N + i];
-      user[(u * C::L + l) * C::NV + v] = qbar + (double)a.qhat[(int64_t)(l * C::NV + v) * a.N + i];
+      user[(u * C::L + l) * C::NV + v] = qbar + (double)a.qhat[((int64_t)l * a.N + i) * C::NV + v];
     }
 }
 
@@ -917,8 +986,9 @@ class OpsImpl final : public Ops {
     for (int e = 0; e < C::D; ++e)
       for (int k = 0; k < C::L1; ++k)
         for (int l = 0; l < C::L; ++l) tab_.P[e][k][l] = (T)re.P[((size_t)e * C::L1 + k) * C::L + l];
-    ftab_.resize(C::TABN + C::NQS + C::NQT);
-    for (int k = 0; k < C::TABN; ++k) ftab_[k] = (T)re.ftab[k];
+    ftab_.assign(C::TABN + C::NQS + C::NQT, T(0));
+    for (int row = 0; row < C::NCODE * C::NQT * C::NQS; ++row)
+      for (int l = 0; l < C::L; ++l) ftab_[row * C::LP + l] = (T)re.ftab[(size_t)row * C::L + l];
     for (int q = 0; q < C::NQS; ++q) ftab_[C::TABN + q] = (T)re.wq[q];
     for (int t = 0; t < C::NQT; ++t) ftab_[C::TABN + C::NQS + t] = (T)re.wt[t];
   }
