@@ -59,8 +59,14 @@ struct Cfg {
 #ifdef CW_FLUX_CH
   static constexpr int CH = (NQT % CW_FLUX_CH == 0) ? CW_FLUX_CH : 1;
 #else
-  static constexpr int CH = (2 * NQT * NQS * NV <= 96) ? NQT
-                            : (NQT % 2 == 0 && 2 * 2 * NQS * NV <= 96) ? 2 : 1;
+  static constexpr int CH = 1;  // measured fastest (occupancy over reuse)
+#endif
+  // resident 128-thread blocks per SM requested from the register allocator:
+  // three for the FP32 reconstruction + predictor (<= 168 registers)
+#ifdef CW_REC_MINB
+  static constexpr int REC_MINB = CW_REC_MINB;
+#else
+  static constexpr int REC_MINB = sizeof(T_) == 4 ? 3 : 1;
 #endif
 };
 
@@ -357,17 +363,14 @@ __device__ __forceinline__ void store_node(T* __restrict__ p, const T* in) {
 }
 
 // ---------------------------------------------------------- rec + predictor
-// Minimum resident blocks per SM requested from the register allocator
+// Minimum resident flux blocks per SM requested from the register allocator
 // (launch shape sweeps); 1 leaves the allocation unconstrained.
-#ifndef CW_REC_MINB
-#define CW_REC_MINB 1
-#endif
 #ifndef CW_FLUX_MINB
 #define CW_FLUX_MINB 1
 #endif
 
 template <class C, bool REC_ONLY>
-__global__ void __launch_bounds__(128, CW_REC_MINB) k_rec_pred(KArgs<C> a, CellTab<C> tb) {
+__global__ void __launch_bounds__(128, C::REC_MINB) k_rec_pred(KArgs<C> a, CellTab<C> tb) {
   using T = typename C::T;
   constexpr int D = C::D, NV = C::NV, MC1 = C::MC1, NE1 = C::NE - 1, NS = C::NS;
   using PH = Phys<D, C::PDE, T>;
