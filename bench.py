@@ -298,6 +298,38 @@ def accuracy_run(cw, m, cfg, Q0, nsteps=10):
     return a.get_state(), b.get_state(), dt
 
 
+def workload_rate(cw, name, stream, barrier, steps=10):
+    """Cell-updates/s of another benchmark workload in both precisions (same
+    timing method: CUDA events on the solver stream, device CFL step)."""
+    import torch
+    cfg = WORKLOADS[name]
+    mesh, Q0 = make_inputs(name)
+    m = cw.Mesh.from_workload(mesh)
+    res = {"cells": mesh.nc, "mesh": cfg["desc"], "order": cfg["order"],
+           "pde": "euler" if cfg["pde"] == 0 else "mhd_glm"}
+    for prec, key, k in ((cw.FP32_MIXED, "fp32_mixed", steps), (cw.FP64, "fp64", max(3, steps // 2))):
+        s = cw.Solver(m, cfg["order"], cfg["pde"], prec, stream=stream.cuda_stream)
+        s.set_state(Q0)
+        for _ in range(3):
+            s.step(0.0)
+        s.sync()
+        s.profile(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        for _ in range(k):
+            s.step(0.0)
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        kms, kn = s.profile_read()
+        s.sync()
+        res[key] = {"value": mesh.nc * k / (ms / 1e3), "ms_per_step": ms / k, "steps": k,
+                    "kernel_ms": {"k_rec_pred": kms[0] / kn[0], "k_flux": kms[1] / kn[1], "k_update": kms[2] / kn[2]}}
+        s.close()
+    return res
+
+
 # ---------------------------------------------------------------------- ours
 def run_ours(args):
     import numpy as np
@@ -461,6 +493,12 @@ def run_ours(args):
                            "conservation_drift_rel": [float(x) for x in drift]}
     if rank == 0 and not args.no_serve:
         out["serving"] = serving_run(cw, args.serve_requests)
+    if not args.no_other:
+        out["other_workloads"] = {}
+        for other in ("densitywave3d_p2", "orszagtang2d_p3"):
+            if other == name:
+                continue
+            out["other_workloads"][other] = workload_rate(cw, other, stream, barrier, steps=10)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_run(name)
     if rank == 0:
@@ -517,6 +555,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-other", action="store_true", help="skip the 3D and MHD workloads")
     ap.add_argument("--serve-requests", type=int, default=128,
                     help="requests in the serving mix (the full mix has 512)")
     args = ap.parse_args()
