@@ -56,17 +56,21 @@ struct Cfg {
   static constexpr int LP = (L + VW - 1) / VW * VW;
   static constexpr int TABN = NCODE * NQT * NQS * LP;
   // time points processed per pass of the face kernel (register budget)
-#ifdef CW_FLUX_CH
-  static constexpr int CH = (NQT % CW_FLUX_CH == 0) ? CW_FLUX_CH : 1;
+  // threads cooperating on one face: each evaluates both traces and the
+  // Rusanov flux at its share of the NQS space points of every time point
+#ifdef CW_FLUX_P
+  static constexpr int FP = CW_FLUX_P;
 #else
-  static constexpr int CH = 1;  // measured fastest (occupancy over reuse)
+  static constexpr int FP = NQS >= 8 ? 4 : NQS >= 4 ? 2 : 1;
 #endif
+  static constexpr int QP = (NQS + FP - 1) / FP;
   // resident 128-thread blocks per SM requested from the register allocator:
-  // three for the FP32 reconstruction + predictor (<= 168 registers)
+  // three for the FP32 Euler reconstruction + predictor (<= 168 registers);
+  // unconstrained where that would spill (MHD, FP64)
 #ifdef CW_REC_MINB
   static constexpr int REC_MINB = CW_REC_MINB;
 #else
-  static constexpr int REC_MINB = sizeof(T_) == 4 ? 3 : 1;
+  static constexpr int REC_MINB = (sizeof(T_) == 4 && NV <= 5) ? 3 : 1;
 #endif
 };
 
@@ -670,16 +674,16 @@ __global__ void __launch_bounds__(128, C::REC_MINB) k_rec_pred(KArgs<C> a, CellT
 }
 
 // ----------------------------------------------------------------- fluxes
-// Predictor deviations of cell c at the CH x NQS space-time points of one
-// pass: tr[tt][q][v] += theta_l(point) q_hat_l[v], basis values read from the
+// Predictor deviations of cell c at the thread's QP space points of time
+// point t: tr[j][v] += theta_l(point) q_hat_l[v], basis values read from the
 // padded table as 16-byte vectors, VW nodes at a time.
 template <class C>
 __device__ __forceinline__ void face_traces(const typename C::T* __restrict__ qhat, int64_t c, int64_t N,
-                                            const typename C::T* tcode, int t0,
-                                            typename C::T (&tr)[C::CH][C::NQS][C::NV]) {
+                                            const typename C::T* tcode, int t, int q0,
+                                            typename C::T (&tr)[C::QP][C::NV]) {
   using T = typename C::T;
   using V = typename Vec16<T>::V;
-  constexpr int NV = C::NV, L = C::L, LP = C::LP, VW = C::VW, NQS = C::NQS, CH = C::CH;
+  constexpr int NV = C::NV, L = C::L, LP = C::LP, VW = C::VW, NQS = C::NQS, QP = C::QP;
 #pragma unroll 1
   for (int l4 = 0; l4 < LP; l4 += VW) {
     T ql[VW][NV];
@@ -693,26 +697,25 @@ __device__ __forceinline__ void face_traces(const typename C::T* __restrict__ qh
       }
     }
 #pragma unroll
-    for (int tt = 0; tt < CH; ++tt)
+    for (int jq = 0; jq < QP; ++jq) {
+      const int q = q0 + jq < NQS ? q0 + jq : NQS - 1;
+      const V th = *reinterpret_cast<const V*>(tcode + (t * NQS + q) * LP + l4);
 #pragma unroll
-      for (int q = 0; q < NQS; ++q) {
-        const V th = *reinterpret_cast<const V*>(tcode + ((t0 + tt) * NQS + q) * LP + l4);
+      for (int j = 0; j < VW; ++j) {
+        if (l4 + j < L) {
+          const T tj = Vec16<T>::get(th, j);
 #pragma unroll
-        for (int j = 0; j < VW; ++j) {
-          if (l4 + j < L) {
-            const T tj = Vec16<T>::get(th, j);
-#pragma unroll
-            for (int v = 0; v < NV; ++v) tr[tt][q][v] += tj * ql[j][v];
-          }
+          for (int v = 0; v < NV; ++v) tr[jq][v] += tj * ql[j][v];
         }
       }
+    }
   }
 }
 
 template <class C>
 __global__ void __launch_bounds__(128, CW_FLUX_MINB) k_flux(KArgs<C> a, int use_smem) {
   using T = typename C::T;
-  constexpr int D = C::D, NV = C::NV, L = C::L, NQS = C::NQS, NQT = C::NQT, CH = C::CH;
+  constexpr int D = C::D, NV = C::NV, NQS = C::NQS, NQT = C::NQT, FP = C::FP, QP = C::QP;
   using PH = Phys<D, C::PDE, T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const T* tab = a.ftab;
@@ -725,8 +728,17 @@ __global__ void __launch_bounds__(128, CW_FLUX_MINB) k_flux(KArgs<C> a, int use_
   const T* wq = tab + C::TABN;
   const T* wt = wq + NQS;
   const T dt = (T)dt_of(a.dt_fixed, a.cfl, a.dtmin, a.cur);
+  const double dtd = dt_of(a.dt_fixed, a.cfl, a.dtmin, a.cur);
   const int64_t N = a.N, F = a.F;
-  for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < F; f += (int64_t)gridDim.x * blockDim.x) {
+  const int part = (int)(threadIdx.x % FP);
+  const int q0 = part * QP;
+  // block-uniform trip count (the group reduction below shuffles over the
+  // whole warp); threads past the last face work on a clamped copy and do
+  // not write
+  for (int64_t g0 = (int64_t)blockIdx.x * blockDim.x; g0 < F * FP; g0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t fg = (g0 + threadIdx.x) / FP;
+    const bool valid = fg < F;
+    const int64_t f = valid ? fg : F - 1;
     const int64_t Lc = a.fL[f];
     const int64_t Rc = a.fR[f];
     const T* tL = tab + (int)a.codeL[f] * (NQT * NQS * C::LP);
@@ -757,81 +769,89 @@ __global__ void __launch_bounds__(128, CW_FLUX_MINB) k_flux(KArgs<C> a, int use_
       for (int m = 0; m < D; ++m) facc[m][v] = T(0);
     }
 #pragma unroll 1
-    for (int t0 = 0; t0 < NQT; t0 += CH) {
-      T trL[CH][NQS][NV], trR[CH][NQS][NV];
+    for (int t = 0; t < NQT; ++t) {
+      T trL[QP][NV], trR[QP][NV];
 #pragma unroll
-      for (int tt = 0; tt < CH; ++tt)
+      for (int j = 0; j < QP; ++j)
 #pragma unroll
-        for (int q = 0; q < NQS; ++q)
-#pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            trL[tt][q][v] = T(0);
-            trR[tt][q][v] = T(0);
-          }
-      face_traces<C>(a.qhat, Lc, N, tL, t0, trL);
+        for (int v = 0; v < NV; ++v) {
+          trL[j][v] = T(0);
+          trR[j][v] = T(0);
+        }
+      face_traces<C>(a.qhat, Lc, N, tL, t, q0, trL);
       if (Rc >= 0) {
-        face_traces<C>(a.qhat, Rc, N, tR, t0, trR);
+        face_traces<C>(a.qhat, Rc, N, tR, t, q0, trR);
       } else {
 #pragma unroll
-        for (int tt = 0; tt < CH; ++tt)
+        for (int j = 0; j < QP; ++j)
 #pragma unroll
-          for (int q = 0; q < NQS; ++q)
-#pragma unroll
-            for (int v = 0; v < NV; ++v) trR[tt][q][v] = trL[tt][q][v];  // transmissive
+          for (int v = 0; v < NV; ++v) trR[j][v] = trL[j][v];  // transmissive
       }
 #pragma unroll
-      for (int tt = 0; tt < CH; ++tt)
+      for (int j = 0; j < QP; ++j) {
+        if (q0 + j >= NQS) continue;
+        // traces = cell average + deviation; a side whose trace is not an
+        // admissible state (density or pressure <= 0) uses its cell average
+        // at this point (positivity safeguard, with the scaling above)
+        T ul[NV], ur[NV];
 #pragma unroll
-        for (int q = 0; q < NQS; ++q) {
-          // traces = cell average + deviation; a side whose trace is not an
-          // admissible state (density or pressure <= 0) uses its cell average
-          // at this point (positivity safeguard, with the scaling above)
-          T ul[NV], ur[NV];
-#pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            ul[v] = qbL[v] + trL[tt][q][v];
-            ur[v] = qbR[v] + trR[tt][q][v];
-          }
-          if (a.pos) {
-            if (!(ul[0] > T(0) && PH::pressure(ul, a.gamma) > T(0)))
-#pragma unroll
-              for (int v = 0; v < NV; ++v) ul[v] = qbL[v];
-            if (!(ur[0] > T(0) && PH::pressure(ur, a.gamma) > T(0)))
-#pragma unroll
-              for (int v = 0; v < NV; ++v) ur[v] = qbR[v];
-          }
-          typename PH::Prim pl = PH::prim(ul, a.gamma);
-          typename PH::Prim pr = PH::prim(ur, a.gamma);
-          T sl = PH::smax(pl, n, a.gamma, a.ch), sr = PH::smax(pr, n, a.gamma, a.ch);
-          const T s = sl > sr ? sl : sr;
-          const T wgt = wq[q] * wt[t0 + tt];
-#pragma unroll
-          for (int m = 0; m < D; ++m) {
-            T em[D];
-#pragma unroll
-            for (int e = 0; e < D; ++e) em[e] = e == m ? T(1) : T(0);
-            T fl[NV], fr[NV];
-            flux_normal<D, C::PDE, T>(ul, pl, em, fl, a.ch);
-            flux_normal<D, C::PDE, T>(ur, pr, em, fr, a.ch);
-#pragma unroll
-            for (int v = 0; v < NV; ++v) facc[m][v] += wgt * (fl[v] + fr[v]);
-          }
-          const T ws = wgt * s;
-#pragma unroll
-          for (int v = 0; v < NV; ++v) dacc[v] += ws * (ur[v] - ul[v]);
+        for (int v = 0; v < NV; ++v) {
+          ul[v] = qbL[v] + trL[j][v];
+          ur[v] = qbR[v] + trR[j][v];
         }
+        if (a.pos) {
+          if (!(ul[0] > T(0) && PH::pressure(ul, a.gamma) > T(0)))
+#pragma unroll
+            for (int v = 0; v < NV; ++v) ul[v] = qbL[v];
+          if (!(ur[0] > T(0) && PH::pressure(ur, a.gamma) > T(0)))
+#pragma unroll
+            for (int v = 0; v < NV; ++v) ur[v] = qbR[v];
+        }
+        typename PH::Prim pl = PH::prim(ul, a.gamma);
+        typename PH::Prim pr = PH::prim(ur, a.gamma);
+        T sl = PH::smax(pl, n, a.gamma, a.ch), sr = PH::smax(pr, n, a.gamma, a.ch);
+        const T s = sl > sr ? sl : sr;
+        const T wgt = wq[q0 + j] * wt[t];
+#pragma unroll
+        for (int m = 0; m < D; ++m) {
+          T em[D];
+#pragma unroll
+          for (int e = 0; e < D; ++e) em[e] = e == m ? T(1) : T(0);
+          T fl[NV], fr[NV];
+          flux_normal<D, C::PDE, T>(ul, pl, em, fl, a.ch);
+          flux_normal<D, C::PDE, T>(ur, pr, em, fr, a.ch);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) facc[m][v] += wgt * (fl[v] + fr[v]);
+        }
+        const T ws = wgt * s;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) dacc[v] += ws * (ur[v] - ul[v]);
+      }
     }
-    const double dtd = dt_of(a.dt_fixed, a.cfl, a.dtmin, a.cur);
-    double fa[D];
+    // sum the partial sums of the FP threads of this face (consecutive lanes)
+    if constexpr (FP > 1) {
 #pragma unroll
-    for (int m = 0; m < D; ++m) fa[m] = a.fa[m * F + f];
-    const double area = a.farea[f];
+      for (int o = FP / 2; o > 0; o >>= 1) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      double g = -area * (double)dacc[v];
+        for (int v = 0; v < NV; ++v) {
+          dacc[v] += __shfl_down_sync(0xffffffffu, dacc[v], o, FP);
 #pragma unroll
-      for (int m = 0; m < D; ++m) g += fa[m] * (double)facc[m][v];
-      a.G[v * F + f] = 0.5 * dtd * g;
+          for (int m = 0; m < D; ++m) facc[m][v] += __shfl_down_sync(0xffffffffu, facc[m][v], o, FP);
+        }
+      }
+    }
+    if (valid && part == 0) {
+      double fa[D];
+#pragma unroll
+      for (int m = 0; m < D; ++m) fa[m] = a.fa[m * F + f];
+      const double area = a.farea[f];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        double g = -area * (double)dacc[v];
+#pragma unroll
+        for (int m = 0; m < D; ++m) g += fa[m] * (double)facc[m][v];
+        a.G[v * F + f] = 0.5 * dtd * g;
+      }
     }
   }
 }
@@ -1087,7 +1107,7 @@ class OpsImpl final : public Ops {
     KArgs<C> a = args(s, ph, dt);
     if (dt.cur < 0) a.cur = 0;
     const size_t smem = use_smem_ ? table_bytes() : 0;
-    unsigned nb = (unsigned)std::min<int64_t>(nblk(s.F, 128), max_blocks_);
+    unsigned nb = (unsigned)std::min<int64_t>(nblk(s.F * C::FP, 128), max_blocks_);
     k_flux<C><<<nb, 128, smem, st>>>(a, use_smem_);
     return cudaGetLastError();
   }
