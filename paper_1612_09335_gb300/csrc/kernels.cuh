@@ -61,7 +61,7 @@ struct Cfg {
 #ifdef CW_FLUX_P
   static constexpr int FP = CW_FLUX_P;
 #else
-  static constexpr int FP = NQS >= 8 ? 4 : NQS >= 4 ? 2 : 1;
+  static constexpr int FP = 1;  // measured: more threads per face multiply the gathers
 #endif
   static constexpr int QP = (NQS + FP - 1) / FP;
   // resident 128-thread blocks per SM requested from the register allocator:
