@@ -35,6 +35,14 @@ constexpr int cmcal(int M, int d) {
                 : d == 3 ? (M + 1) * (M + 2) * (M + 3) / 6 : (M + 1) * (M + 2) * (M + 3) * (M + 4) / 24;
 }
 
+// smallest stride >= base, a multiple of vw elements, whose byte size is
+// 16 mod 128
+constexpr int code_stride(int base, int vw, int esize) {
+  int st = (base + vw - 1) / vw * vw;
+  while ((st * esize) % 128 != 16) st += vw;
+  return st;
+}
+
 template <int D_, int M_, int PDE_, typename T_>
 struct Cfg {
   static constexpr int D = D_, M = M_, PDE = PDE_;
@@ -54,7 +62,11 @@ struct Cfg {
   // is padded to a multiple of one 16-byte vector
   static constexpr int VW = 16 / (int)sizeof(T_);
   static constexpr int LP = (L + VW - 1) / VW * VW;
-  static constexpr int TABN = NCODE * NQT * NQS * LP;
+  // per-code stride padded to 16 bytes past a multiple of 128 bytes, so the
+  // rows of different face codes read by one warp fall into different
+  // shared-memory banks
+  static constexpr int CODE_STRIDE = code_stride(NQT * NQS * LP, VW, (int)sizeof(T_));
+  static constexpr int TABN = NCODE * CODE_STRIDE;
   // time points processed per pass of the face kernel (register budget)
   // threads cooperating on one face: each evaluates both traces and the
   // Rusanov flux at its share of the NQS space points of every time point
@@ -741,8 +753,8 @@ __global__ void __launch_bounds__(128, CW_FLUX_MINB) k_flux(KArgs<C> a, int use_
     const int64_t f = valid ? fg : F - 1;
     const int64_t Lc = a.fL[f];
     const int64_t Rc = a.fR[f];
-    const T* tL = tab + (int)a.codeL[f] * (NQT * NQS * C::LP);
-    const T* tR = tab + (int)a.codeR[f] * (NQT * NQS * C::LP);
+    const T* tL = tab + (int)a.codeL[f] * C::CODE_STRIDE;
+    const T* tR = tab + (int)a.codeR[f] * C::CODE_STRIDE;
     T n[D];
 #pragma unroll
     for (int e = 0; e < D; ++e) n[e] = a.fn[e * F + f];
@@ -1010,8 +1022,11 @@ class OpsImpl final : public Ops {
       for (int k = 0; k < C::L1; ++k)
         for (int l = 0; l < C::L; ++l) tab_.P[e][k][l] = (T)re.P[((size_t)e * C::L1 + k) * C::L + l];
     ftab_.assign(C::TABN + C::NQS + C::NQT, T(0));
-    for (int row = 0; row < C::NCODE * C::NQT * C::NQS; ++row)
-      for (int l = 0; l < C::L; ++l) ftab_[row * C::LP + l] = (T)re.ftab[(size_t)row * C::L + l];
+    for (int code = 0; code < C::NCODE; ++code)
+      for (int row = 0; row < C::NQT * C::NQS; ++row)
+        for (int l = 0; l < C::L; ++l)
+          ftab_[code * C::CODE_STRIDE + row * C::LP + l] =
+              (T)re.ftab[((size_t)code * C::NQT * C::NQS + row) * C::L + l];
     for (int q = 0; q < C::NQS; ++q) ftab_[C::TABN + q] = (T)re.wq[q];
     for (int t = 0; t < C::NQT; ++t) ftab_[C::TABN + C::NQS + t] = (T)re.wt[t];
   }
