@@ -7,7 +7,8 @@
 //               weights, weights2), then the space-time Galerkin predictor
 //               (Eq. CGfinal) with the Picard iteration folded into
 //               q1 = C0 q0 - dt sum_e P_e G_e,  P_e = (K_tau^1)^-1 K_xi_e;
-//               writes the L space-time nodal values.
+//               node loops rolled, working set in shared memory; writes
+//               the L space-time nodal values.
 //   k_flux      one thread per face (persistent grid): the predictor of both
 //               sides at the space-time Gauss points of the face, Rusanov
 //               flux (Eq. rusanov) with s_max per point, integrated with
@@ -76,14 +77,20 @@ struct Cfg {
   static constexpr int FP = 1;  // measured: more threads per face multiply the gathers
 #endif
   static constexpr int QP = (NQS + FP - 1) / FP;
-  // resident 128-thread blocks per SM requested from the register allocator:
-  // three for the FP32 Euler reconstruction + predictor (<= 168 registers);
-  // unconstrained where that would spill (MHD, FP64)
+  // resident 128-thread blocks per SM requested from the register allocator
+  // for the reconstruction + predictor: four in 2D FP32 Euler (<= 128
+  // registers), three in 3D FP32 Euler (<= 168; 128 spills); unconstrained
+  // where a cap would spill (MHD, FP64)
 #ifdef CW_REC_MINB
   static constexpr int REC_MINB = CW_REC_MINB;
 #else
-  static constexpr int REC_MINB = (sizeof(T_) == 4 && NV <= 5) ? 3 : 1;
+  static constexpr int REC_MINB = sizeof(T_) != 4 ? 1 : NV == 4 ? 4 : NV == 5 ? 3 : 1;
 #endif
+  // predictor working set (the fixed part and the current iterate of the L1
+  // unknown space-time nodes) kept in shared memory, one column per thread,
+  // so that the node loops run rolled: a few kilobytes of code instead of a
+  // fully unrolled body that misses the instruction cache
+  static constexpr int PRED_SMEM_BYTES = 2 * L1 * NV * (int)sizeof(T_) * 128;
 };
 
 template <class C>
@@ -91,7 +98,7 @@ struct CellTab {
   using T = typename C::T;
   T E[C::L0][C::MC1];
   T Sig[C::MC1][C::MC1];
-  T C0[C::L1][C::L0];
+  T CE[C::L1][C::MC1];  // C0 E: known part of the unknown nodes, from w directly
   T P[C::D][C::L1][C::L];
 };
 
@@ -386,7 +393,7 @@ __device__ __forceinline__ void store_node(T* __restrict__ p, const T* in) {
 #endif
 
 template <class C, bool REC_ONLY>
-__global__ void __launch_bounds__(128, C::REC_MINB) k_rec_pred(KArgs<C> a, CellTab<C> tb) {
+__global__ void __launch_bounds__(128, C::REC_MINB) k_rec_pred(KArgs<C> a, const __grid_constant__ CellTab<C> tb) {
   using T = typename C::T;
   constexpr int D = C::D, NV = C::NV, MC1 = C::MC1, NE1 = C::NE - 1, NS = C::NS;
   using PH = Phys<D, C::PDE, T>;
@@ -523,7 +530,7 @@ __global__ void __launch_bounds__(128, C::REC_MINB) k_rec_pred(KArgs<C> a, CellT
     for (int v = 0; v < NV; ++v) qb[v] = qi[v] + qlo[v];
     const T rb = qb[0];
     T th = T(1);
-#pragma unroll
+#pragma unroll 1
     for (int n = 0; n < C::L0; ++n) {
       T r = qb[0];
 #pragma unroll
@@ -536,7 +543,7 @@ __global__ void __launch_bounds__(128, C::REC_MINB) k_rec_pred(KArgs<C> a, CellT
     const T pb = PH::pressure(qb, a.gamma);
     T thp = T(1);
     if (pb > T(0)) {
-#pragma unroll
+#pragma unroll 1
       for (int n = 0; n < C::L0; ++n) {
         T q[NV];
 #pragma unroll
@@ -580,14 +587,16 @@ __global__ void __launch_bounds__(128, C::REC_MINB) k_rec_pred(KArgs<C> a, CellT
       }
     return;
   } else {
-    constexpr int L = C::L, L0 = C::L0, L1 = C::L1;
+    constexpr int L0 = C::L0, L1 = C::L1, B = 128;
+    extern __shared__ __align__(16) unsigned char rp_smem[];
+    T* sb = reinterpret_cast<T*>(rp_smem) + threadIdx.x;  // fixed part, [(k NV + v) B]
+    T* sq = sb + L1 * NV * B;                              // current iterate
     const T dt = (T)dt_of(a.dt_fixed, a.cfl, a.dtmin, a.cur);
     T J[D][D];
 #pragma unroll
     for (int e = 0; e < D; ++e)
 #pragma unroll
       for (int m = 0; m < D; ++m) J[e][m] = __ldg(a.Jinv + (e * D + m) * N + i);
-
     // Deviations from the cell average: the Picard update subtracts the flux
     // of the cell average, G_e(q) - G_e(Qbar), which P_e annihilates exactly
     // (it differentiates constants to zero); q_hat is stored as q - Qbar.  The
@@ -602,19 +611,13 @@ __global__ void __launch_bounds__(128, C::REC_MINB) k_rec_pred(KArgs<C> a, CellT
 #pragma unroll
       for (int e = 0; e < D; ++e) flux_normal<D, C::PDE, T>(qb, pr, J[e], Gref[e], a.ch);
     }
-    // known degrees of freedom: w at the tau = 0 nodes (written out at once);
-    // base = C0 dq0 - dt sum_e P_e[:, tau=0 nodes] (G_e(q0) - G_e(Qbar)) is
-    // fixed over the iterations; the initial guess of the unknown nodes is w
-    // at their spatial positions, Qbar + C0 dq0.
-    T base[L1][NV], q1[L1][NV];
+    // flux part of the fixed term, -dt sum_e P_e[:, tau=0 nodes] (G_e(q0) - G_e(Qbar))
+    T S[L1][NV];
 #pragma unroll
     for (int k = 0; k < L1; ++k)
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        base[k][v] = T(0);
-        q1[k][v] = T(0);
-      }
-#pragma unroll
+      for (int v = 0; v < NV; ++v) S[k][v] = T(0);
+#pragma unroll 1
     for (int n = 0; n < L0; ++n) {
       T dq0[NV], q0[NV];
 #pragma unroll
@@ -638,25 +641,36 @@ __global__ void __launch_bounds__(128, C::REC_MINB) k_rec_pred(KArgs<C> a, CellT
       for (int k = 0; k < L1; ++k)
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          T b = base[k][v] + tb.C0[k][n] * dq0[v];
+          T b = S[k][v];
 #pragma unroll
           for (int e = 0; e < D; ++e) b -= tb.P[e][k][n] * Ge[e][v];
-          base[k][v] = b;
-          q1[k][v] += tb.C0[k][n] * dq0[v];
+          S[k][v] = b;
         }
     }
+    // known part C0 dq0 = (C0 E) w; it is also the initial guess (deviation
+    // of the unknown nodes from Qbar)
+#pragma unroll
+    for (int k = 0; k < L1; ++k)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        T c0 = T(0);
+#pragma unroll
+        for (int l = 0; l < MC1; ++l) c0 += tb.CE[k][l] * w[l][v];
+        sq[(k * NV + v) * B] = c0;
+        sb[(k * NV + v) * B] = c0 + S[k][v];
+      }
     // Picard iterations of Eq. (CGfinal), on deviations
     for (int it = 0; it < a.niter; ++it) {
       T nq[L1][NV];
 #pragma unroll
       for (int k = 0; k < L1; ++k)
 #pragma unroll
-        for (int v = 0; v < NV; ++v) nq[k][v] = base[k][v];
-#pragma unroll
+        for (int v = 0; v < NV; ++v) nq[k][v] = sb[(k * NV + v) * B];
+#pragma unroll 1
       for (int l = 0; l < L1; ++l) {
         T ql[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) ql[v] = qb[v] + q1[l][v];
+        for (int v = 0; v < NV; ++v) ql[v] = qb[v] + sq[(l * NV + v) * B];
         typename PH::Prim pr = PH::prim(ql, a.gamma);
         T Ge[D][NV];
 #pragma unroll
@@ -678,10 +692,15 @@ __global__ void __launch_bounds__(128, C::REC_MINB) k_rec_pred(KArgs<C> a, CellT
 #pragma unroll
       for (int k = 0; k < L1; ++k)
 #pragma unroll
-        for (int v = 0; v < NV; ++v) q1[k][v] = nq[k][v];
+        for (int v = 0; v < NV; ++v) sq[(k * NV + v) * B] = nq[k][v];
     }
+#pragma unroll 1
+    for (int k = 0; k < L1; ++k) {
+      T q1[NV];
 #pragma unroll
-    for (int k = 0; k < L1; ++k) store_node<NV, T>(a.qhat + ((int64_t)(L0 + k) * N + i) * NV, q1[k]);
+      for (int v = 0; v < NV; ++v) q1[v] = sq[(k * NV + v) * B];
+      store_node<NV, T>(a.qhat + ((int64_t)(L0 + k) * N + i) * NV, q1);
+    }
   }
 }
 
@@ -1017,7 +1036,11 @@ class OpsImpl final : public Ops {
     for (int l = 0; l < C::MC1; ++l)
       for (int m = 0; m < C::MC1; ++m) tab_.Sig[l][m] = (T)re.Sigma[l * C::MC1 + m];
     for (int k = 0; k < C::L1; ++k)
-      for (int n = 0; n < C::L0; ++n) tab_.C0[k][n] = (T)re.C0[k * C::L0 + n];
+      for (int l = 0; l < C::MC1; ++l) {
+        double s = 0.0;
+        for (int n = 0; n < C::L0; ++n) s += re.C0[k * C::L0 + n] * re.E[n * C::MC1 + l];
+        tab_.CE[k][l] = (T)s;
+      }
     for (int e = 0; e < C::D; ++e)
       for (int k = 0; k < C::L1; ++k)
         for (int l = 0; l < C::L; ++l) tab_.P[e][k][l] = (T)re.P[((size_t)e * C::L1 + k) * C::L + l];
@@ -1089,7 +1112,7 @@ class OpsImpl final : public Ops {
       a.cur = 0;
       a.reset_next = 0;
     }
-    k_rec_pred<C, false><<<nblk(s.N, 128), 128, 0, st>>>(a, tab_);
+    k_rec_pred<C, false><<<nblk(s.N, 128), 128, C::PRED_SMEM_BYTES, st>>>(a, tab_);
     return cudaGetLastError();
   }
   cudaError_t reconstruct(const DevState& s, const PhysParams& ph, double* out, cudaStream_t st) override {
@@ -1102,6 +1125,9 @@ class OpsImpl final : public Ops {
   cudaError_t prepare() override {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_rec_pred<C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             C::PRED_SMEM_BYTES);
     if (e != cudaSuccess) return e;
     const size_t smem = table_bytes();
     use_smem_ = smem <= 100 * 1024 ? 1 : 0;
