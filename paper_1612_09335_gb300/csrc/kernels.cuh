@@ -77,10 +77,18 @@ struct Cfg {
   static constexpr int FP = 1;  // measured: more threads per face multiply the gathers
 #endif
   static constexpr int QP = (NQS + FP - 1) / FP;
-  // resident 128-thread blocks per SM requested from the register allocator
-  // for the reconstruction + predictor: four in 2D FP32 Euler (<= 128
-  // registers), three in 3D FP32 Euler (<= 168; 128 spills); unconstrained
-  // where a cap would spill (MHD, FP64)
+  // Resident 128-thread blocks per SM requested from the register allocator
+  // (measured launch-shape sweeps).  Face kernel: four in 2D FP32 Euler
+  // (<= 128 registers), three in FP32 MHD and 3D FP32 Euler up to P2
+  // (<= 168), unconstrained elsewhere.
+#ifdef CW_FLUX_MINB
+  static constexpr int FLUX_MINB = CW_FLUX_MINB;
+#else
+  static constexpr int FLUX_MINB = sizeof(T_) != 4 ? 1 : (D == 2 && NV == 4) ? 4 : (D == 2 || M <= 2) ? 3 : 1;
+#endif
+  // Reconstruction + predictor: four in 2D FP32 Euler (<= 128 registers),
+  // three in 3D FP32 Euler (<= 168; 128 spills); unconstrained where a cap
+  // would spill (MHD, FP64).
 #ifdef CW_REC_MINB
   static constexpr int REC_MINB = CW_REC_MINB;
 #else
@@ -146,6 +154,24 @@ __device__ __forceinline__ double dt_of(double fixed, double cfl, const unsigned
 // ------------------------------------------------------------------ physics
 // Normal flux F.n for an arbitrary (not necessarily unit) vector n, which is
 // linear in n: used with unit face normals and with rows of d xi / d x.
+// Reciprocal and square root in the arithmetic type.  FP32: the PTX
+// approximate instructions rcp.approx.ftz.f32 and sqrt.approx.ftz.f32
+// (relative error within about 2^-23), which skip the correction sequences
+// of IEEE division and square root; the FP32 path is held to tolerances far
+// above that.  FP64: correctly rounded.
+__device__ __forceinline__ float arcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ double arcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float asqrt(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ double asqrt(double x) { return sqrt(x); }
+
 template <int D, int PDE, typename T>
 struct Phys;
 
@@ -158,7 +184,7 @@ struct Phys<D, 0, T> {  // Euler, Eqs. (eulerTerms), (eos)
   __device__ __forceinline__ static Prim prim(const T* q, T gamma) {
     Prim s;
     s.rho = q[0];
-    s.ir = T(1) / q[0];
+    s.ir = arcp(q[0]);
     T v2 = T(0);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
@@ -184,7 +210,7 @@ struct Phys<D, 0, T> {  // Euler, Eqs. (eulerTerms), (eos)
 #pragma unroll
     for (int a = 0; a < D; ++a) vn += s.v[a] * n[a];
     const T c2 = gamma * s.p * s.ir;
-    return fabs(vn) + sqrt(c2 > T(0) ? c2 : T(0));
+    return fabs(vn) + asqrt(c2 > T(0) ? c2 : T(0));
   }
   // largest |eigenvalue| over all directions
   __device__ __forceinline__ static T speed(const T* q, T gamma, T /*ch*/) {
@@ -193,13 +219,13 @@ struct Phys<D, 0, T> {  // Euler, Eqs. (eulerTerms), (eos)
 #pragma unroll
     for (int a = 0; a < D; ++a) v2 += s.v[a] * s.v[a];
     const T c2 = gamma * s.p * s.ir;
-    return sqrt(v2) + sqrt(c2 > T(0) ? c2 : T(0));
+    return asqrt(v2) + asqrt(c2 > T(0) ? c2 : T(0));
   }
   __device__ __forceinline__ static T pressure(const T* q, T gamma) {
     T m2 = T(0);
 #pragma unroll
     for (int a = 0; a < D; ++a) m2 += q[1 + a] * q[1 + a];
-    return (gamma - T(1)) * (q[D + 1] - T(0.5) * m2 / q[0]);
+    return (gamma - T(1)) * (q[D + 1] - T(0.5) * m2 * arcp(q[0]));
   }
 };
 
@@ -212,7 +238,7 @@ struct Phys<D, 1, T> {  // ideal MHD + GLM, Eqs. (MHDTerms), (MHDeos), Gaussian 
   __device__ __forceinline__ static Prim prim(const T* q, T gamma) {
     Prim s;
     s.rho = q[0];
-    s.ir = T(1) / q[0];
+    s.ir = arcp(q[0]);
     T v2 = T(0), B2 = T(0), vB = T(0);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -260,8 +286,8 @@ struct Phys<D, 1, T> {  // ideal MHD + GLM, Eqs. (MHDTerms), (MHDeos), Gaussian 
     T sum = a2 + b2;
     T disc = sum * sum - T(4) * a2 * bn2;
     disc = disc > T(0) ? disc : T(0);
-    T cf2 = T(0.5) * (sum + sqrt(disc));
-    T cf = sqrt(cf2 > T(0) ? cf2 : T(0));
+    T cf2 = T(0.5) * (sum + asqrt(disc));
+    T cf = asqrt(cf2 > T(0) ? cf2 : T(0));
     T sp = fabs(vn) + cf;
     return sp > ch ? sp : ch;
   }
@@ -275,14 +301,14 @@ struct Phys<D, 1, T> {  // ideal MHD + GLM, Eqs. (MHDTerms), (MHDeos), Gaussian 
       B2 += s.B[a] * s.B[a];
     }
     T f2 = gamma * s.p * s.ir + B2 * i4pi * s.ir;
-    T sp = sqrt(v2) + sqrt(f2 > T(0) ? f2 : T(0));
+    T sp = asqrt(v2) + asqrt(f2 > T(0) ? f2 : T(0));
     return sp > ch ? sp : ch;
   }
   __device__ __forceinline__ static T pressure(const T* q, T gamma) {
     const T i8pi = T(0.039788735772973836);
     T m2 = q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
     T B2 = q[5] * q[5] + q[6] * q[6] + q[7] * q[7];
-    return (gamma - T(1)) * (q[4] - T(0.5) * m2 / q[0] - B2 * i8pi);
+    return (gamma - T(1)) * (q[4] - T(0.5) * m2 * arcp(q[0]) - B2 * i8pi);
   }
 };
 
@@ -386,11 +412,6 @@ __device__ __forceinline__ void store_node(T* __restrict__ p, const T* in) {
 }
 
 // ---------------------------------------------------------- rec + predictor
-// Minimum resident flux blocks per SM requested from the register allocator
-// (launch shape sweeps); 1 leaves the allocation unconstrained.
-#ifndef CW_FLUX_MINB
-#define CW_FLUX_MINB 1
-#endif
 
 template <class C, bool REC_ONLY>
 __global__ void __launch_bounds__(128, C::REC_MINB) k_rec_pred(KArgs<C> a, const __grid_constant__ CellTab<C> tb) {
@@ -453,9 +474,9 @@ __global__ void __launch_bounds__(128, C::REC_MINB) k_rec_pred(KArgs<C> a, const
 
   // ---- linear weights (normalised over kept stencils), P_0, indicators, weights
   const int ns = a.nsec[i];
-  const T lden = T(1) / (a.lam0 + T(ns) * a.lams);
+  const T lden = arcp(a.lam0 + T(ns) * a.lams);
   const T lam0 = a.lam0 * lden, lams = a.lams * lden;
-  const T ilam0 = T(1) / lam0;
+  const T ilam0 = arcp(lam0);
   T w[MC1][NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
@@ -495,15 +516,15 @@ __global__ void __launch_bounds__(128, C::REC_MINB) k_rec_pred(KArgs<C> a, const
     // omega_s proportional to lambda_s / (sigma_s + eps)^4, scaled by
     // (sigma_min + eps)^4 so that nothing overflows in FP32
     const T num = smin + a.eps;
-    T w0 = a.linw ? lam0 : lam0 * pow4(num / (sig0 + a.eps));
+    T w0 = a.linw ? lam0 : lam0 * pow4(num * arcp(sig0 + a.eps));
     T ws[NS];
     T tot = w0;
 #pragma unroll
     for (int sc = 0; sc < NS; ++sc) {
-      ws[sc] = keep[sc] ? (a.linw ? lams : lams * pow4(num / (sig[sc] + a.eps))) : T(0);
+      ws[sc] = keep[sc] ? (a.linw ? lams : lams * pow4(num * arcp(sig[sc] + a.eps))) : T(0);
       tot += ws[sc];
     }
-    const T itot = T(1) / tot;
+    const T itot = arcp(tot);
     w0 *= itot;
 #pragma unroll
     for (int sc = 0; sc < NS; ++sc) ws[sc] *= itot;
@@ -744,7 +765,7 @@ __device__ __forceinline__ void face_traces(const typename C::T* __restrict__ qh
 }
 
 template <class C>
-__global__ void __launch_bounds__(128, CW_FLUX_MINB) k_flux(KArgs<C> a, int use_smem) {
+__global__ void __launch_bounds__(128, C::FLUX_MINB) k_flux(KArgs<C> a, int use_smem) {
   using T = typename C::T;
   constexpr int D = C::D, NV = C::NV, NQS = C::NQS, NQT = C::NQT, FP = C::FP, QP = C::QP;
   using PH = Phys<D, C::PDE, T>;
@@ -830,16 +851,20 @@ __global__ void __launch_bounds__(128, CW_FLUX_MINB) k_flux(KArgs<C> a, int use_
           ul[v] = qbL[v] + trL[j][v];
           ur[v] = qbR[v] + trR[j][v];
         }
-        if (a.pos) {
-          if (!(ul[0] > T(0) && PH::pressure(ul, a.gamma) > T(0)))
-#pragma unroll
-            for (int v = 0; v < NV; ++v) ul[v] = qbL[v];
-          if (!(ur[0] > T(0) && PH::pressure(ur, a.gamma) > T(0)))
-#pragma unroll
-            for (int v = 0; v < NV; ++v) ur[v] = qbR[v];
-        }
         typename PH::Prim pl = PH::prim(ul, a.gamma);
         typename PH::Prim pr = PH::prim(ur, a.gamma);
+        if (a.pos) {
+          if (!(ul[0] > T(0) && pl.p > T(0))) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) ul[v] = qbL[v];
+            pl = PH::prim(ul, a.gamma);
+          }
+          if (!(ur[0] > T(0) && pr.p > T(0))) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) ur[v] = qbR[v];
+            pr = PH::prim(ur, a.gamma);
+          }
+        }
         T sl = PH::smax(pl, n, a.gamma, a.ch), sr = PH::smax(pr, n, a.gamma, a.ch);
         const T s = sl > sr ? sl : sr;
         const T wgt = wq[q0 + j] * wt[t];
@@ -888,25 +913,47 @@ __global__ void __launch_bounds__(128, CW_FLUX_MINB) k_flux(KArgs<C> a, int use_
 }
 
 // ------------------------------------------------------------ block minimum
-__device__ __forceinline__ void block_min_atomic(double val, unsigned long long* target) {
-  __shared__ double red[32];
+// Block minimum of non-negative ratios folded into *target, which holds the
+// bits of a positive double.  Non-negative IEEE values order like their bit
+// patterns, so the reduction runs on the integer bits (no FP64 pipe work in
+// FP32-mixed mode); a NaN (bits above +inf) never wins.
+template <typename T>
+__device__ __forceinline__ void block_min_atomic(T val, unsigned long long* target) {
+  using U = typename std::conditional<sizeof(T) == 4, unsigned, unsigned long long>::type;
+  __shared__ U red[32];
+  U b;
+  if constexpr (sizeof(T) == 4) {
+    b = __reduce_min_sync(0xffffffffu, __float_as_uint(val));
+  } else {
+    b = (U)__double_as_longlong(val);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    double other = __shfl_xor_sync(0xffffffffu, val, o);
-    val = other < val ? other : val;
+    for (int o = 16; o > 0; o >>= 1) {
+      const U other = __shfl_xor_sync(0xffffffffu, b, o);
+      b = other < b ? other : b;
+    }
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) red[warp] = val;
+  if (lane == 0) red[warp] = b;
   __syncthreads();
   if (warp == 0) {
     const int nw = (blockDim.x + 31) >> 5;
-    val = lane < nw ? red[lane] : __longlong_as_double(0x7ff0000000000000ll);
+    const U inf = sizeof(T) == 4 ? (U)0x7f800000u : (U)0x7ff0000000000000ull;
+    b = lane < nw ? red[lane] : inf;
+    if constexpr (sizeof(T) == 4) {
+      b = __reduce_min_sync(0xffffffffu, b);
+    } else {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      double other = __shfl_xor_sync(0xffffffffu, val, o);
-      val = other < val ? other : val;
+      for (int o = 16; o > 0; o >>= 1) {
+        const U other = __shfl_xor_sync(0xffffffffu, b, o);
+        b = other < b ? other : b;
+      }
     }
-    if (lane == 0 && val > 0.0) atomicMin(target, (unsigned long long)__double_as_longlong(val));
+    if (lane == 0) {
+      double v;
+      if constexpr (sizeof(T) == 4) v = (double)__uint_as_float((unsigned)b);
+      else v = __longlong_as_double((long long)b);
+      if (v > 0.0) atomicMin(target, (unsigned long long)__double_as_longlong(v));
+    }
   }
 }
 
@@ -918,7 +965,7 @@ __global__ void __launch_bounds__(256) k_update(KArgs<C> a) {
   using PH = Phys<D, C::PDE, T>;
   const int64_t N = a.N, F = a.F;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double ratio = __longlong_as_double(0x7ff0000000000000ll);
+  T ratio = T(INFINITY);
   if (i < N) {
     double acc[NV];
 #pragma unroll
@@ -927,9 +974,11 @@ __global__ void __launch_bounds__(256) k_update(KArgs<C> a) {
     for (int k = 0; k <= D; ++k) {
       const int cf = a.cellface[k * N + i];
       const int64_t f = cf >> 1;
-      const double sgn = (cf & 1) ? -1.0 : 1.0;
 #pragma unroll
-      for (int v = 0; v < NV; ++v) acc[v] += sgn * a.G[v * F + f];
+      for (int v = 0; v < NV; ++v) {
+        const double g = a.G[v * F + f];
+        acc[v] += (cf & 1) ? -g : g;
+      }
     }
     const double iv = a.invvol[i];
     double q[NV];
@@ -956,7 +1005,7 @@ __global__ void __launch_bounds__(256) k_update(KArgs<C> a) {
     const T pk = PH::pressure(qt, a.gamma);
     if (!(qt[0] > T(0) && pk > T(0) && isfinite(pk))) atomicOr(a.status, 1);
     const T sp = PH::speed(qt, a.gamma, a.ch);
-    ratio = (double)((T)a.hsize[i] / sp);
+    ratio = (T)a.hsize[i] / sp;
   }
   block_min_atomic(ratio, a.dtmin + (1 - a.cur));
   if (blockIdx.x == 0 && threadIdx.x == 0) *a.time += dt_of(a.dt_fixed, a.cfl, a.dtmin, a.cur);
@@ -968,7 +1017,7 @@ __global__ void __launch_bounds__(256) k_stable_dt(KArgs<C> a, int slot) {
   using PH = Phys<C::D, C::PDE, T>;
   const int64_t N = a.N;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double ratio = __longlong_as_double(0x7ff0000000000000ll);
+  T ratio = T(INFINITY);
   if (i < N) {
     T q[C::NV];
 #pragma unroll
@@ -976,7 +1025,7 @@ __global__ void __launch_bounds__(256) k_stable_dt(KArgs<C> a, int slot) {
       if constexpr (std::is_same<T, float>::value) q[v] = a.Qhi[v * N + i];
       else q[v] = a.Q[v * N + i];
     }
-    ratio = (double)((T)a.hsize[i] / PH::speed(q, a.gamma, a.ch));
+    ratio = (T)a.hsize[i] / PH::speed(q, a.gamma, a.ch);
   }
   block_min_atomic(ratio, a.dtmin + slot);
 }
