@@ -68,15 +68,18 @@ struct Cfg {
   // shared-memory banks
   static constexpr int CODE_STRIDE = code_stride(NQT * NQS * LP, VW, (int)sizeof(T_));
   static constexpr int TABN = NCODE * CODE_STRIDE;
-  // time points processed per pass of the face kernel (register budget)
-  // threads cooperating on one face: each evaluates both traces and the
-  // Rusanov flux at its share of the NQS space points of every time point
-#ifdef CW_FLUX_P
-  static constexpr int FP = CW_FLUX_P;
+  // face kernel: two threads per face, each evaluating one side at every
+  // space-time point, where those traces fit the register budget (FP32,
+  // NQT NQS NV <= 64: 2D Euler); otherwise one thread per face, one time
+  // point at a time
+#ifdef CW_FLUX_PAIR
+  static constexpr int PAIR = CW_FLUX_PAIR;
 #else
-  static constexpr int FP = 1;  // measured: more threads per face multiply the gathers
+  static constexpr int PAIR = sizeof(T_) == 4 && NQT * NQS * NV <= 64;
 #endif
-  static constexpr int QP = (NQS + FP - 1) / FP;
+  // prefetch of the next q_hat chunk in the trace loop where the extra
+  // registers are few (measured: faster in 2D Euler, slower for NV >= 5)
+  static constexpr bool TR_PREFETCH = VW * NV <= 16;
   // Resident 128-thread blocks per SM requested from the register allocator
   // (measured launch-shape sweeps).  Face kernel: four in 2D FP32 Euler
   // (<= 128 registers), three in FP32 MHD and 3D FP32 Euler up to P2
@@ -726,32 +729,49 @@ __global__ void __launch_bounds__(128, C::REC_MINB) k_rec_pred(KArgs<C> a, const
 }
 
 // ----------------------------------------------------------------- fluxes
-// Predictor deviations of cell c at the thread's QP space points of time
-// point t: tr[j][v] += theta_l(point) q_hat_l[v], basis values read from the
-// padded table as 16-byte vectors, VW nodes at a time.
 template <class C>
+__device__ __forceinline__ void load_chunk(const typename C::T* __restrict__ qhat, int64_t c, int64_t N, int l4,
+                                           typename C::T (&ql)[C::VW][C::NV]) {
+  using T = typename C::T;
+#pragma unroll
+  for (int j = 0; j < C::VW; ++j) {
+    if (l4 + j < C::L) {
+      load_node<C::NV, T>(qhat + ((int64_t)(l4 + j) * N + c) * C::NV, ql[j]);
+    } else {
+#pragma unroll
+      for (int v = 0; v < C::NV; ++v) ql[j][v] = T(0);
+    }
+  }
+}
+
+// Predictor deviations of cell c at NPT consecutive rows (space-time points)
+// of its face table, starting at row r0: tr[j][v] += theta_l(point) q_hat_l[v].
+// Basis values are read from the padded table as 16-byte vectors, VW nodes
+// at a time; with TR_PREFETCH the next chunk of nodes is in flight while the
+// current one is used.
+template <class C, int NPT>
 __device__ __forceinline__ void face_traces(const typename C::T* __restrict__ qhat, int64_t c, int64_t N,
-                                            const typename C::T* tcode, int t, int q0,
-                                            typename C::T (&tr)[C::QP][C::NV]) {
+                                            const typename C::T* tcode, int r0, typename C::T (&tr)[NPT][C::NV]) {
   using T = typename C::T;
   using V = typename Vec16<T>::V;
-  constexpr int NV = C::NV, L = C::L, LP = C::LP, VW = C::VW, NQS = C::NQS, QP = C::QP;
+  constexpr int NV = C::NV, L = C::L, LP = C::LP, VW = C::VW;
+  T nx[VW][NV];
+  if constexpr (C::TR_PREFETCH) load_chunk<C>(qhat, c, N, 0, nx);
 #pragma unroll 1
   for (int l4 = 0; l4 < LP; l4 += VW) {
     T ql[VW][NV];
+    if constexpr (C::TR_PREFETCH) {
 #pragma unroll
-    for (int j = 0; j < VW; ++j) {
-      if (l4 + j < L) {
-        load_node<NV, T>(qhat + ((int64_t)(l4 + j) * N + c) * NV, ql[j]);
-      } else {
+      for (int j = 0; j < VW; ++j)
 #pragma unroll
-        for (int v = 0; v < NV; ++v) ql[j][v] = T(0);
-      }
+        for (int v = 0; v < NV; ++v) ql[j][v] = nx[j][v];
+      if (l4 + VW < LP) load_chunk<C>(qhat, c, N, l4 + VW, nx);
+    } else {
+      load_chunk<C>(qhat, c, N, l4, ql);
     }
 #pragma unroll
-    for (int jq = 0; jq < QP; ++jq) {
-      const int q = q0 + jq < NQS ? q0 + jq : NQS - 1;
-      const V th = *reinterpret_cast<const V*>(tcode + (t * NQS + q) * LP + l4);
+    for (int jq = 0; jq < NPT; ++jq) {
+      const V th = *reinterpret_cast<const V*>(tcode + (r0 + jq) * LP + l4);
 #pragma unroll
       for (int j = 0; j < VW; ++j) {
         if (l4 + j < L) {
@@ -764,33 +784,108 @@ __device__ __forceinline__ void face_traces(const typename C::T* __restrict__ qh
   }
 }
 
+// Rusanov flux (Eq. rusanov) at one space-time point with quadrature weight
+// wgt, from the traces ul, ur (cell average + deviation) of both sides:
+// facc[m] += wgt (F_m(u-) + F_m(u+)) per direction m, dacc += wgt s (u+ - u-),
+// s the larger of the two sides' maximal signal speeds along n.  A trace that
+// is not an admissible state (density or pressure <= 0) is replaced by its
+// cell average at this point (positivity safeguard, with the scaling of the
+// reconstruction).
+template <class C>
+__device__ __forceinline__ void rusanov_point(const KArgs<C>& a, typename C::T* ul, typename C::T* ur,
+                                              const typename C::T* qbL, const typename C::T* qbR,
+                                              const typename C::T* n, typename C::T wgt,
+                                              typename C::T (&facc)[C::D][C::NV], typename C::T (&dacc)[C::NV]) {
+  using T = typename C::T;
+  constexpr int D = C::D, NV = C::NV;
+  using PH = Phys<D, C::PDE, T>;
+  typename PH::Prim pl = PH::prim(ul, a.gamma);
+  typename PH::Prim pr = PH::prim(ur, a.gamma);
+  if (a.pos) {
+    if (!(ul[0] > T(0) && pl.p > T(0))) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) ul[v] = qbL[v];
+      pl = PH::prim(ul, a.gamma);
+    }
+    if (!(ur[0] > T(0) && pr.p > T(0))) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) ur[v] = qbR[v];
+      pr = PH::prim(ur, a.gamma);
+    }
+  }
+  const T sl = PH::smax(pl, n, a.gamma, a.ch), sr = PH::smax(pr, n, a.gamma, a.ch);
+  const T s = sl > sr ? sl : sr;
+#pragma unroll
+  for (int m = 0; m < D; ++m) {
+    T em[D];
+#pragma unroll
+    for (int e = 0; e < D; ++e) em[e] = e == m ? T(1) : T(0);
+    T fl[NV], fr[NV];
+    flux_normal<D, C::PDE, T>(ul, pl, em, fl, a.ch);
+    flux_normal<D, C::PDE, T>(ur, pr, em, fr, a.ch);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) facc[m][v] += wgt * (fl[v] + fr[v]);
+  }
+  const T ws = wgt * s;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) dacc[v] += ws * (ur[v] - ul[v]);
+}
+
+// G_f = 1/2 dt (sum_m |f| n_m facc[m] - |f| dacc), contracted in FP64 so that
+// a constant state gives bit-identical sums on every face and the update
+// closes
+template <class C>
+__device__ __forceinline__ void store_face_integral(const KArgs<C>& a, int64_t f, double dtd,
+                                                    const typename C::T (&facc)[C::D][C::NV],
+                                                    const typename C::T (&dacc)[C::NV]) {
+  double fa[C::D];
+#pragma unroll
+  for (int m = 0; m < C::D; ++m) fa[m] = a.fa[m * a.F + f];
+  const double area = a.farea[f];
+#pragma unroll
+  for (int v = 0; v < C::NV; ++v) {
+    double g = -area * (double)dacc[v];
+#pragma unroll
+    for (int m = 0; m < C::D; ++m) g += fa[m] * (double)facc[m][v];
+    a.G[v * a.F + f] = 0.5 * dtd * g;
+  }
+}
+
+template <class C>
+__device__ __forceinline__ const typename C::T* face_tables(const KArgs<C>& a, int use_smem, unsigned char* smem_raw) {
+  using T = typename C::T;
+  if (!use_smem) return a.ftab;
+  T* st = reinterpret_cast<T*>(smem_raw);
+  for (int k = threadIdx.x; k < C::TABN + C::NQS + C::NQT; k += blockDim.x) st[k] = a.ftab[k];
+  __syncthreads();
+  return st;
+}
+
+template <class C>
+__device__ __forceinline__ void cell_average(const KArgs<C>& a, int64_t c, typename C::T* qb) {
+#pragma unroll
+  for (int v = 0; v < C::NV; ++v) {
+    if constexpr (std::is_same<typename C::T, double>::value) {
+      qb[v] = a.Q[v * a.N + c];
+    } else {
+      qb[v] = __ldg(a.Qhi + v * a.N + c) + __ldg(a.Qlo + v * a.N + c);
+    }
+  }
+}
+
+// One thread per face, persistent grid: both sides' traces one time point
+// at a time (NQS space points), Rusanov flux, space-time quadrature.
 template <class C>
 __global__ void __launch_bounds__(128, C::FLUX_MINB) k_flux(KArgs<C> a, int use_smem) {
   using T = typename C::T;
-  constexpr int D = C::D, NV = C::NV, NQS = C::NQS, NQT = C::NQT, FP = C::FP, QP = C::QP;
-  using PH = Phys<D, C::PDE, T>;
+  constexpr int D = C::D, NV = C::NV, NQS = C::NQS, NQT = C::NQT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const T* tab = a.ftab;
-  if (use_smem) {
-    T* st = reinterpret_cast<T*>(smem_raw);
-    for (int k = threadIdx.x; k < C::TABN + NQS + NQT; k += blockDim.x) st[k] = a.ftab[k];
-    __syncthreads();
-    tab = st;
-  }
+  const T* tab = face_tables<C>(a, use_smem, smem_raw);
   const T* wq = tab + C::TABN;
   const T* wt = wq + NQS;
-  const T dt = (T)dt_of(a.dt_fixed, a.cfl, a.dtmin, a.cur);
   const double dtd = dt_of(a.dt_fixed, a.cfl, a.dtmin, a.cur);
   const int64_t N = a.N, F = a.F;
-  const int part = (int)(threadIdx.x % FP);
-  const int q0 = part * QP;
-  // block-uniform trip count (the group reduction below shuffles over the
-  // whole warp); threads past the last face work on a clamped copy and do
-  // not write
-  for (int64_t g0 = (int64_t)blockIdx.x * blockDim.x; g0 < F * FP; g0 += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t fg = (g0 + threadIdx.x) / FP;
-    const bool valid = fg < F;
-    const int64_t f = valid ? fg : F - 1;
+  for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < F; f += (int64_t)gridDim.x * blockDim.x) {
     const int64_t Lc = a.fL[f];
     const int64_t Rc = a.fR[f];
     const T* tL = tab + (int)a.codeL[f] * C::CODE_STRIDE;
@@ -800,19 +895,13 @@ __global__ void __launch_bounds__(128, C::FLUX_MINB) k_flux(KArgs<C> a, int use_
     for (int e = 0; e < D; ++e) n[e] = a.fn[e * F + f];
     // cell averages of both sides: q_hat holds deviations from them
     T qbL[NV], qbR[NV];
+    cell_average<C>(a, Lc, qbL);
+    if (Rc >= 0) {
+      cell_average<C>(a, Rc, qbR);
+    } else {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      if constexpr (std::is_same<T, double>::value) {
-        qbL[v] = a.Q[v * N + Lc];
-        qbR[v] = Rc >= 0 ? a.Q[v * N + Rc] : qbL[v];
-      } else {
-        qbL[v] = __ldg(a.Qhi + v * N + Lc) + __ldg(a.Qlo + v * N + Lc);
-        qbR[v] = Rc >= 0 ? __ldg(a.Qhi + v * N + Rc) + __ldg(a.Qlo + v * N + Rc) : qbL[v];
-      }
+      for (int v = 0; v < NV; ++v) qbR[v] = qbL[v];
     }
-    // sum_q w_q (F_m(q-) + F_m(q+)) per direction m, and sum_q w_q s_q (q+ - q-);
-    // the contraction with |f| n is done in FP64 below, so that a constant
-    // state gives bit-identical sums on every face and the update closes
     T facc[D][NV], dacc[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
@@ -822,97 +911,122 @@ __global__ void __launch_bounds__(128, C::FLUX_MINB) k_flux(KArgs<C> a, int use_
     }
 #pragma unroll 1
     for (int t = 0; t < NQT; ++t) {
-      T trL[QP][NV], trR[QP][NV];
+      T trL[NQS][NV], trR[NQS][NV];
 #pragma unroll
-      for (int j = 0; j < QP; ++j)
+      for (int j = 0; j < NQS; ++j)
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           trL[j][v] = T(0);
           trR[j][v] = T(0);
         }
-      face_traces<C>(a.qhat, Lc, N, tL, t, q0, trL);
+      face_traces<C, NQS>(a.qhat, Lc, N, tL, t * NQS, trL);
       if (Rc >= 0) {
-        face_traces<C>(a.qhat, Rc, N, tR, t, q0, trR);
+        face_traces<C, NQS>(a.qhat, Rc, N, tR, t * NQS, trR);
       } else {
 #pragma unroll
-        for (int j = 0; j < QP; ++j)
+        for (int j = 0; j < NQS; ++j)
 #pragma unroll
           for (int v = 0; v < NV; ++v) trR[j][v] = trL[j][v];  // transmissive
       }
 #pragma unroll
-      for (int j = 0; j < QP; ++j) {
-        if (q0 + j >= NQS) continue;
-        // traces = cell average + deviation; a side whose trace is not an
-        // admissible state (density or pressure <= 0) uses its cell average
-        // at this point (positivity safeguard, with the scaling above)
+      for (int j = 0; j < NQS; ++j) {
         T ul[NV], ur[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           ul[v] = qbL[v] + trL[j][v];
           ur[v] = qbR[v] + trR[j][v];
         }
-        typename PH::Prim pl = PH::prim(ul, a.gamma);
-        typename PH::Prim pr = PH::prim(ur, a.gamma);
-        if (a.pos) {
-          if (!(ul[0] > T(0) && pl.p > T(0))) {
-#pragma unroll
-            for (int v = 0; v < NV; ++v) ul[v] = qbL[v];
-            pl = PH::prim(ul, a.gamma);
-          }
-          if (!(ur[0] > T(0) && pr.p > T(0))) {
-#pragma unroll
-            for (int v = 0; v < NV; ++v) ur[v] = qbR[v];
-            pr = PH::prim(ur, a.gamma);
-          }
-        }
-        T sl = PH::smax(pl, n, a.gamma, a.ch), sr = PH::smax(pr, n, a.gamma, a.ch);
-        const T s = sl > sr ? sl : sr;
-        const T wgt = wq[q0 + j] * wt[t];
-#pragma unroll
-        for (int m = 0; m < D; ++m) {
-          T em[D];
-#pragma unroll
-          for (int e = 0; e < D; ++e) em[e] = e == m ? T(1) : T(0);
-          T fl[NV], fr[NV];
-          flux_normal<D, C::PDE, T>(ul, pl, em, fl, a.ch);
-          flux_normal<D, C::PDE, T>(ur, pr, em, fr, a.ch);
-#pragma unroll
-          for (int v = 0; v < NV; ++v) facc[m][v] += wgt * (fl[v] + fr[v]);
-        }
-        const T ws = wgt * s;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) dacc[v] += ws * (ur[v] - ul[v]);
+        rusanov_point<C>(a, ul, ur, qbL, qbR, n, wq[j] * wt[t], facc, dacc);
       }
     }
-    // sum the partial sums of the FP threads of this face (consecutive lanes)
-    if constexpr (FP > 1) {
-#pragma unroll
-      for (int o = FP / 2; o > 0; o >>= 1) {
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          dacc[v] += __shfl_down_sync(0xffffffffu, dacc[v], o, FP);
-#pragma unroll
-          for (int m = 0; m < D; ++m) facc[m][v] += __shfl_down_sync(0xffffffffu, facc[m][v], o, FP);
-        }
-      }
-    }
-    if (valid && part == 0) {
-      double fa[D];
-#pragma unroll
-      for (int m = 0; m < D; ++m) fa[m] = a.fa[m * F + f];
-      const double area = a.farea[f];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        double g = -area * (double)dacc[v];
-#pragma unroll
-        for (int m = 0; m < D; ++m) g += fa[m] * (double)facc[m][v];
-        a.G[v * F + f] = 0.5 * dtd * g;
-      }
-    }
+    store_face_integral<C>(a, f, dtd, facc, dacc);
   }
 }
 
-// ------------------------------------------------------------ block minimum
+// Two threads per face (consecutive lanes), persistent grid: each evaluates
+// the traces of its own side at all NQT x NQS space-time points from one
+// pass over that cell's q_hat; the pair then swaps traces by warp shuffles,
+// each thread takes every other point for the Rusanov flux, and the two
+// partial sums are added.  A boundary face evaluates its inner cell on both
+// threads (transmissive: the outer trace equals the inner one).
+template <class C>
+__global__ void __launch_bounds__(128, C::FLUX_MINB) k_flux_pair(KArgs<C> a, int use_smem) {
+  using T = typename C::T;
+  constexpr int D = C::D, NV = C::NV, NQS = C::NQS, NP = C::NQT * C::NQS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const T* tab = face_tables<C>(a, use_smem, smem_raw);
+  const T* wq = tab + C::TABN;
+  const T* wt = wq + NQS;
+  const double dtd = dt_of(a.dt_fixed, a.cfl, a.dtmin, a.cur);
+  const int64_t N = a.N, F = a.F;
+  const int side = (int)(threadIdx.x & 1);
+  // block-uniform trip count (the pair exchanges shuffle over the whole
+  // warp); a thread past the last face works on a clamped copy, not written
+  for (int64_t g0 = (int64_t)blockIdx.x * blockDim.x; g0 < 2 * F; g0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t fg = (g0 + threadIdx.x) >> 1;
+    const bool valid = fg < F;
+    const int64_t f = valid ? fg : F - 1;
+    const int64_t Lc = a.fL[f];
+    const int64_t Rc = a.fR[f];
+    const bool own_left = side == 0 || Rc < 0;
+    const int64_t c = own_left ? Lc : Rc;
+    const T* tc = tab + (int)(own_left ? a.codeL[f] : a.codeR[f]) * C::CODE_STRIDE;
+    T n[D];
+#pragma unroll
+    for (int e = 0; e < D; ++e) n[e] = a.fn[e * F + f];
+    T qb[NV], qo[NV];
+    cell_average<C>(a, c, qb);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) qo[v] = __shfl_xor_sync(0xffffffffu, qb[v], 1);
+    T tr[NP][NV];
+#pragma unroll
+    for (int p = 0; p < NP; ++p)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) tr[p][v] = T(0);
+    face_traces<C, NP>(a.qhat, c, N, tc, 0, tr);
+    const T* qbL = side == 0 ? qb : qo;
+    const T* qbR = side == 0 ? qo : qb;
+    T facc[D][NV], dacc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      dacc[v] = T(0);
+#pragma unroll
+      for (int m = 0; m < D; ++m) facc[m][v] = T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < (NP + 1) / 2; ++k) {
+      constexpr int LAST = NP - 1;
+      const int p0 = 2 * k, p1 = 2 * k + 1 <= LAST ? 2 * k + 1 : LAST;
+      // thread 0 of the pair takes point p0, thread 1 point p1: each sends
+      // the partner its own trace at the partner's point
+      T mine[NV], other[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const T send = side == 0 ? tr[p1][v] : tr[p0][v];
+        other[v] = __shfl_xor_sync(0xffffffffu, send, 1);
+        mine[v] = side == 0 ? tr[p0][v] : tr[p1][v];
+      }
+      if (side == 0 || 2 * k + 1 <= LAST) {
+        const int p = side == 0 ? p0 : p1;
+        T ul[NV], ur[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          ul[v] = qbL[v] + (side == 0 ? mine[v] : other[v]);
+          ur[v] = qbR[v] + (side == 0 ? other[v] : mine[v]);
+        }
+        rusanov_point<C>(a, ul, ur, qbL, qbR, n, wq[p % NQS] * wt[p / NQS], facc, dacc);
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      dacc[v] += __shfl_xor_sync(0xffffffffu, dacc[v], 1);
+#pragma unroll
+      for (int m = 0; m < D; ++m) facc[m][v] += __shfl_xor_sync(0xffffffffu, facc[m][v], 1);
+    }
+    if (valid && side == 0) store_face_integral<C>(a, f, dtd, facc, dacc);
+  }
+}
+
 // Block minimum of non-negative ratios folded into *target, which holds the
 // bits of a positive double.  Non-negative IEEE values order like their bit
 // patterns, so the reduction runs on the integer bits (no FP64 pipe work in
@@ -1171,6 +1285,11 @@ class OpsImpl final : public Ops {
     k_rec_pred<C, true><<<nblk(s.N, 128), 128, 0, st>>>(a, tab_);
     return cudaGetLastError();
   }
+  using FluxKernel = void (*)(KArgs<C>, int);
+  static FluxKernel flux_kernel() {
+    if constexpr (C::PAIR) return k_flux_pair<C>;
+    else return k_flux<C>;
+  }
   cudaError_t prepare() override {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1181,11 +1300,11 @@ class OpsImpl final : public Ops {
     const size_t smem = table_bytes();
     use_smem_ = smem <= 100 * 1024 ? 1 : 0;
     if (use_smem_) {
-      e = cudaFuncSetAttribute(k_flux<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      e = cudaFuncSetAttribute(flux_kernel(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
     }
     int nb = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_flux<C>, 128, use_smem_ ? smem : 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, flux_kernel(), 128, use_smem_ ? smem : 0);
     if (e != cudaSuccess) return e;
     int nsm = 0;
     e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -1197,8 +1316,8 @@ class OpsImpl final : public Ops {
     KArgs<C> a = args(s, ph, dt);
     if (dt.cur < 0) a.cur = 0;
     const size_t smem = use_smem_ ? table_bytes() : 0;
-    unsigned nb = (unsigned)std::min<int64_t>(nblk(s.F * C::FP, 128), max_blocks_);
-    k_flux<C><<<nb, 128, smem, st>>>(a, use_smem_);
+    unsigned nb = (unsigned)std::min<int64_t>(nblk(s.F * (C::PAIR ? 2 : 1), 128), max_blocks_);
+    flux_kernel()<<<nb, 128, smem, st>>>(a, use_smem_);
     return cudaGetLastError();
   }
   cudaError_t update(const DevState& s, const PhysParams& ph, DtArgs dt, cudaStream_t st) override {
