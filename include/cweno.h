@@ -109,11 +109,11 @@ int cweno_mesh_info(const cweno_mesh* m, int64_t* ncells, int64_t* nfaces, int64
 /* Diagnostic, host only: the stencils cweno_setup would use for `order`,
  * in the caller's cell ids.  S0: nc x n_e (S0[c*n_e] = c, then the ranked
  * breadth-first cells of Eq. stencil); sec: nc x (d+1) x d sector cells
- * (Sec. 2.1 cone rule), -1 where a sector is dropped.  Errors as
- * cweno_setup. */
+ * (Sec. 2.1 cone rule), -1 where a sector is dropped.  `order` 2..5 in
+ * 2D, 2..4 in 3D.  Errors as cweno_setup. */
 int cweno_mesh_stencils(const cweno_mesh* m, int order, int32_t* S0, int32_t* sec);
 
-/* Reconstruction setup for `order` = M + 1 in 2..4 (Sec. 2.1): central
+/* Reconstruction setup for `order` = M + 1 in 2..5 (Sec. 2.1): central
  * stencils S_i^0 of n_e = d * M(M,d) cells (Eq. stencil), d+1 sectorial
  * stencils, the FP64 pseudo-inverses of the constrained least-squares
  * problems (Eq. CWENO:Popt, precomputed as the paper prescribes for fixed
@@ -123,7 +123,9 @@ int cweno_mesh_stencils(const cweno_mesh* m, int order, int32_t* S0, int32_t* se
  * throughout, or FP32 arithmetic with FP64 setup and FP64 cell-average
  * accumulators.  `stream` is a cudaStream_t (NULL: the library creates a
  * non-blocking stream it owns).  `params` NULL means defaults.
- * Supported: (dim 2, Euler or MHD, order 2..4), (dim 3, Euler, order 2..4).
+ * Supported: (dim 2, Euler, order 2..5; order 5 is the paper's fifth-order
+ * scheme of Secs. 4.2.1-4.2.2), (dim 2, MHD, order 2..4), (dim 3, Euler,
+ * order 2..4).
  * The state is zero until cweno_set_state.
  * Errors: EINVAL, EDEGENERATE (rank-deficient LSQ, mesh too small for the
  * stencil), ENOMEM, ECUDA.  Synchronous. */
@@ -227,7 +229,7 @@ typedef struct {
   int64_t nc;
   const int32_t* cells;  /* nc x (dim+1), host */
   const double* period;  /* dim or NULL */
-  int order;             /* 2..4 */
+  int order;             /* as cweno_setup */
   int pde;               /* CWENO_EULER / CWENO_MHD_GLM */
   int precision;         /* CWENO_FP64 / CWENO_FP32_MIXED */
   const double* Q0;      /* nc x nvars, host */

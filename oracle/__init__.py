@@ -58,7 +58,7 @@ def lib():
             L.orc_stencil.argtypes = [P, I64, lp, lp, cp, I]
             L.orc_reconstruct.argtypes = [P, dp, I64, lp, dp, dp, dp, dp, cp, I]
             L.orc_predictor.argtypes = [P, dp, D, I64, lp, dp, cp, I]
-            L.orc_predictor_from_w.argtypes = [P, I64, dp, D, dp]
+            L.orc_predictor_from_w.argtypes = [P, I64, dp, D, C.c_int, dp]
             L.orc_step.argtypes = [P, dp, D, I64, lp, dp, cp, I]
             L.orc_stable_dt.restype = D
             L.orc_stable_dt.argtypes = [P, dp, D]
@@ -208,10 +208,13 @@ class Oracle:
             raise ValueError(err.value.decode())
         return q
 
-    def predictor_from_w(self, cell, wnodal, dt):
+    def predictor_from_w(self, cell, wnodal, dt, galerkin=False):
+        """Predictor of one cell from reconstruction values at the lattice
+        nodes; galerkin=True solves the Galerkin system of Eq. (CGfinal)
+        every iteration instead of using its closed form."""
         w = np.ascontiguousarray(wnodal, dtype=np.float64)
         q = np.zeros((self.L, self.nu))
-        lib().orc_predictor_from_w(self.h, int(cell), _d(w), float(dt), _d(q))
+        lib().orc_predictor_from_w(self.h, int(cell), _d(w), float(dt), int(bool(galerkin)), _d(q))
         return q
 
     def step(self, Q, dt, ids=None):

@@ -742,7 +742,9 @@ struct OSolver {
   std::vector<std::array<int, 4>> mono;  // spatial monomials of P_M
   // predictor
   std::vector<std::array<double, 4>> st_nodes;  // space-time nodes (xi..., tau in slot 3)
-  std::vector<Poly> theta;                      // nodal basis
+  std::vector<std::array<int, 5>> alpha;        // lattice indices of the space-time nodes
+  std::vector<double> Pint;                     // d x (L-L0) x L: int_0^tau_k d theta_l / d xi_e
+  std::vector<Poly> theta;                      // nodal basis as polynomials (Galerkin form)
   std::vector<double> Ktau, Mmat;               // rows: unknown nodes (L-L0) x L columns
   std::vector<std::array<double, 4>> lat;       // spatial lattice (M), same as tau=0 nodes
   std::map<long, CellRec> cache;
@@ -1081,6 +1083,84 @@ bool reconstruct_cell(OSolver& S, const double* Q, long i, RecOut& out, std::str
 }
 
 // --------------------------------------------------------------- predictor
+// Nodal basis of the space-time nodes, evaluated in closed form.  The nodes
+// are the principal lattice of the (d+1)-simplex with barycentric
+// coordinates lambda_0 = 1 - sum(xi) - tau, lambda_{1..d} = xi, lambda_{d+1}
+// = tau; node l has lattice indices alpha_l (summing to M), and its Lagrange
+// polynomial is the product over c and j < alpha_c of (M lambda_c - j)/(j+1):
+// one at node l, zero at every other node of the lattice.  x holds
+// (xi_0, xi_1, xi_2, tau) with tau in slot 3.  th[l]; dth (optional) holds
+// d theta_l / d xi_e at dth[e * L + l] for e < d and d/d tau at e = d.
+void st_basis(const OSolver& S, const double* x, double* th, double* dth) {
+  const int d = S.d, M = S.M, L = S.Lc;
+  double lam[5];
+  lam[0] = 1.0 - x[3];
+  for (int a = 0; a < d; ++a) {
+    lam[1 + a] = x[a];
+    lam[0] -= x[a];
+  }
+  lam[d + 1] = x[3];
+  for (int l = 0; l < L; ++l) {
+    // the M linear factors of theta_l and their barycentric variable
+    double f[8];
+    int var[8], jj[8], nf = 0;
+    for (int c = 0; c <= d + 1; ++c)
+      for (int j = 0; j < S.alpha[l][c]; ++j) {
+        f[nf] = (M * lam[c] - j) / (j + 1);
+        var[nf] = c;
+        jj[nf] = j;
+        ++nf;
+      }
+    double v = 1.0;
+    for (int q = 0; q < nf; ++q) v *= f[q];
+    th[l] = v;
+    if (!dth) continue;
+    // product rule; d lambda_0 / d x_a = -1, d lambda_{1+a} / d xi_a = 1,
+    // d lambda_{d+1} / d tau = 1
+    for (int e = 0; e <= d; ++e) {
+      double g = 0.0;
+      for (int q = 0; q < nf; ++q) {
+        double dl = var[q] == 0 ? -1.0 : (var[q] == e + 1 ? 1.0 : 0.0);
+        if (dl == 0.0) continue;
+        // factor q is (M lambda - j)/(j+1): its derivative is M/(j+1) dlambda
+        double t = dl * M / (jj[q] + 1);
+        for (int r = 0; r < nf; ++r)
+          if (r != q) t *= f[r];
+        g += t;
+      }
+      dth[e * L + l] = g;
+    }
+  }
+}
+
+// Space-time predictor in closed form.  With the nodal flux interpolant
+// F_h in P_M (Eq. PDEterm), q_h(xi, tau) = w(xi) - dt int_0^tau H_h(xi, s) ds
+// is a polynomial of degree M that satisfies d q_h / d tau + dt H_h = 0
+// pointwise and takes the known values at tau = 0, so it makes the residual
+// of Eq. (CGfinal) vanish for every test function: it is the Galerkin
+// solution (K_tau^1 is invertible, reading c6).  Its value at the unknown
+// node k is w(xi_k) - dt sum_e sum_l Pint[e][k][l] G_e,l with
+//   Pint[e][k][l] = int_0^{tau_k} d theta_l / d xi_e (xi_k, s) ds,
+// integrated by Gauss-Legendre (exact: the integrand has degree M-1 in s).
+// This avoids forming (K_tau^1)^-1, whose condition number reaches 1.4e6 at
+// M = 4; the Galerkin form is kept for comparison (predictor_cell_galerkin).
+void init_predictor_integrals(OSolver& S) {
+  const int d = S.d, M = S.M, L = S.Lc, L0 = S.L0, L1 = L - L0;
+  std::vector<double> gx, gw;
+  gauss_legendre01(M + 1, gx, gw);
+  S.Pint.assign((size_t)d * L1 * L, 0.0);
+  std::vector<double> th(L), dth((size_t)(d + 1) * L);
+  for (int k = 0; k < L1; ++k) {
+    const std::array<double, 4>& nk = S.st_nodes[L0 + k];
+    for (size_t q = 0; q < gx.size(); ++q) {
+      double x[4] = {nk[0], nk[1], nk[2], nk[3] * gx[q]};
+      st_basis(S, x, th.data(), dth.data());
+      for (int e = 0; e < d; ++e)
+        for (int l = 0; l < L; ++l) S.Pint[((size_t)e * L1 + k) * L + l] += nk[3] * gw[q] * dth[e * L + l];
+    }
+  }
+}
+
 void init_predictor(OSolver& S) {
   int d = S.d, M = S.M;
   // space-time nodes: time level t (tau = t/M) carries the spatial lattice of
@@ -1096,6 +1176,19 @@ void init_predictor(OSolver& S) {
   S.Lc = (int)S.st_nodes.size();
   S.L0 = S.Mc;
   S.lat = spatial_lattice(d, M, M);
+  S.alpha.clear();
+  for (const auto& nd : S.st_nodes) {
+    std::array<int, 5> al = {0, 0, 0, 0, 0};
+    int sum = 0;
+    for (int a = 0; a < d; ++a) {
+      al[1 + a] = (int)std::lround(nd[a] * M);
+      sum += al[1 + a];
+    }
+    al[d + 1] = (int)std::lround(nd[3] * M);
+    sum += al[d + 1];
+    al[0] = M - sum;
+    S.alpha.push_back(al);
+  }
   // nodal basis: theta_l = sum_k C[k][l] m_k with V[n][k] = m_k(node_n), C = V^{-1}
   std::vector<std::array<int, 4>> stm = monomial_list(d + 1, M);
   for (auto& e : stm)
@@ -1129,11 +1222,58 @@ void init_predictor(OSolver& S) {
       S.Ktau[k * L + l] = integrate_prism(poly_mul(tk, poly_deriv(S.theta[l], 3)), d);
       S.Mmat[k * L + l] = integrate_prism(poly_mul(tk, S.theta[l]), d);
     }
+  init_predictor_integrals(S);
 }
 
 // Space-time predictor of cell i from its reconstruction w (per variable),
-// Eq. (CGfinal).  qhat: L x nu nodal values.
+// Eq. (CGfinal), in the closed form of init_predictor_integrals: M+1 Picard
+// iterations q_k <- w(xi_k) - dt sum_e sum_l Pint[e][k][l] G_e(q_l), with
+// G_e = sum_m (d xi_e / d x_m) F_m (Eq. Hterm, Eulerian), from the initial
+// guess w(xi) at every node.  qhat: L x nu nodal values.
 void predictor_cell(const OSolver& S, long i, const std::vector<Poly>& w, double dt, std::vector<double>& qhat) {
+  int d = S.d, nu = S.nu, L = S.Lc, L0 = S.L0, L1 = L - L0;
+  const OMesh& m = *S.mesh;
+  double J[3][3], Ji[3][3];
+  cell_jacobian(m, i, J);
+  inv3(J, d, Ji);  // Ji[e][m] = d xi_e / d x_m
+  qhat.assign((size_t)L * nu, 0.0);
+  std::vector<double> wk((size_t)L * nu);
+  for (int l = 0; l < L; ++l) {
+    double x[4] = {S.st_nodes[l][0], S.st_nodes[l][1], S.st_nodes[l][2], 0.0};
+    for (int v = 0; v < nu; ++v) wk[l * nu + v] = poly_eval(w[v], x);
+  }
+  qhat = wk;
+  std::vector<double> F((size_t)d * nu), G((size_t)L * d * nu);
+  for (int it = 0; it < S.P.niter; ++it) {
+    for (int l = 0; l < L; ++l) {
+      for (int mm = 0; mm < d; ++mm) flux(S.pde, d, S.P, &qhat[l * nu], mm, &F[mm * nu]);
+      for (int e = 0; e < d; ++e)
+        for (int v = 0; v < nu; ++v) {
+          double g = 0.0;
+          for (int mm = 0; mm < d; ++mm) g += Ji[e][mm] * F[mm * nu + v];
+          G[((size_t)l * d + e) * nu + v] = g;
+        }
+    }
+    std::vector<double> q1((size_t)L1 * nu);
+    for (int k = 0; k < L1; ++k)
+      for (int v = 0; v < nu; ++v) {
+        double s = 0.0;
+        for (int e = 0; e < d; ++e)
+          for (int l = 0; l < L; ++l) s += S.Pint[((size_t)e * L1 + k) * L + l] * G[((size_t)l * d + e) * nu + v];
+        q1[k * nu + v] = wk[(L0 + k) * nu + v] - dt * s;
+      }
+    for (int k = 0; k < L1; ++k)
+      for (int v = 0; v < nu; ++v) qhat[(L0 + k) * nu + v] = q1[k * nu + v];
+  }
+}
+
+// The same predictor through the Galerkin system of Eq. (CGfinal) as
+// written: K_tau^1 q^1 = -dt M H - K_tau^0 q^0 solved every iteration, with
+// the matrices integrated exactly from the nodal basis in monomial form.
+// Used only to check the closed form (their difference is the rounding of
+// the Galerkin solve, which grows with the condition number of K_tau^1).
+void predictor_cell_galerkin(const OSolver& S, long i, const std::vector<Poly>& w, double dt,
+                             std::vector<double>& qhat) {
   int d = S.d, nu = S.nu, L = S.Lc, L0 = S.L0, L1 = L - L0;
   const OMesh& m = *S.mesh;
   double J[3][3], Ji[3][3];
@@ -1192,11 +1332,11 @@ void predictor_cell(const OSolver& S, long i, const std::vector<Poly>& w, double
 
 // Value of the predictor polynomial of a cell at reference point (xi, tau).
 void eval_qh(const OSolver& S, const std::vector<double>& qhat, const double* xt, double* q) {
+  std::vector<double> th(S.Lc);
+  st_basis(S, xt, th.data(), nullptr);
   for (int v = 0; v < S.nu; ++v) q[v] = 0.0;
-  for (int l = 0; l < S.Lc; ++l) {
-    double th = poly_eval(S.theta[l], xt);
-    for (int v = 0; v < S.nu; ++v) q[v] += th * qhat[l * S.nu + v];
-  }
+  for (int l = 0; l < S.Lc; ++l)
+    for (int v = 0; v < S.nu; ++v) q[v] += th[l] * qhat[l * S.nu + v];
 }
 
 // Face quadrature points in physical space for face k of cell i: the face
@@ -1416,8 +1556,10 @@ int orc_predictor(void* p, const double* Q, double dt, int64_t n, const int64_t*
   return 0;
 }
 
-// Predictor from given reconstruction values at the lattice nodes (Mc x nu).
-int orc_predictor_from_w(void* p, int64_t cell, const double* wnodal, double dt, double* qhat) {
+// Predictor from given reconstruction values at the lattice nodes (Mc x nu);
+// galerkin != 0 takes the Galerkin solve of Eq. (CGfinal) instead of the
+// closed form.
+int orc_predictor_from_w(void* p, int64_t cell, const double* wnodal, double dt, int galerkin, double* qhat) {
   OSolver* S = (OSolver*)p;
   int nu = S->nu, Mc = S->Mc, d = S->d;
   // interpolate: monomial coefficients from lattice values
@@ -1438,7 +1580,8 @@ int orc_predictor_from_w(void* p, int64_t cell, const double* wnodal, double dt,
     w[v] = poly_from_coef(*S, c.data());
   }
   std::vector<double> qh;
-  predictor_cell(*S, cell, w, dt, qh);
+  if (galerkin) predictor_cell_galerkin(*S, cell, w, dt, qh);
+  else predictor_cell(*S, cell, w, dt, qh);
   for (size_t k = 0; k < qh.size(); ++k) qhat[k] = qh[k];
   return 0;
 }

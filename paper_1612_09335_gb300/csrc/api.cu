@@ -180,8 +180,8 @@ int cweno_mesh_info(const cweno_mesh* m, int64_t* ncells, int64_t* nfaces, int64
 
 int cweno_mesh_stencils(const cweno_mesh* mesh, int order, int32_t* S0, int32_t* sec) {
   if (!mesh || !S0 || !sec) return fail(CWENO_EINVAL, "null argument");
-  if (order < 2 || order > 4) return fail(CWENO_EINVAL, "order must be 2, 3 or 4");
   const MeshHost& m = mesh->m;
+  if (order < 2 || order > (m.d == 2 ? 5 : 4)) return fail(CWENO_EINVAL, "order must be 2..5 in 2D, 2..4 in 3D");
   const RefElem& re = ref_elem(m.d, order - 1);
   CellSetup cs;
   std::string err;
@@ -228,8 +228,9 @@ int cweno_setup(const cweno_mesh* mesh, int order, int pde, int precision, const
   *out = nullptr;
   if (!mesh) return fail(CWENO_EINVAL, "null mesh");
   const MeshHost& m = mesh->m;
-  if (order < 2 || order > 4) return fail(CWENO_EINVAL, "order must be 2, 3 or 4");
+  if (order < 2 || order > 5) return fail(CWENO_EINVAL, "order must be 2..5");
   if (pde != CWENO_EULER && pde != CWENO_MHD_GLM) return fail(CWENO_EINVAL, "unknown pde");
+  if (order == 5 && !(pde == CWENO_EULER && m.d == 2)) return fail(CWENO_EINVAL, "order 5 is built for 2D Euler only");
   if (pde == CWENO_MHD_GLM && m.d != 2) return fail(CWENO_EINVAL, "MHD-GLM is built for 2D meshes only");
   if (precision != CWENO_FP64 && precision != CWENO_FP32_MIXED) return fail(CWENO_EINVAL, "unknown precision");
   cweno_params prm;

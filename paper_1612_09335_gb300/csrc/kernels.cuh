@@ -81,21 +81,21 @@ struct Cfg {
   // registers are few (measured: faster in 2D Euler, slower for NV >= 5)
   static constexpr bool TR_PREFETCH = VW * NV <= 16;
   // Resident 128-thread blocks per SM requested from the register allocator
-  // (measured launch-shape sweeps).  Face kernel: four in 2D FP32 Euler
-  // (<= 128 registers), three in FP32 MHD and 3D FP32 Euler up to P2
-  // (<= 168), unconstrained elsewhere.
+  // (measured launch-shape sweeps).  Face kernel: four in 2D FP32 Euler up
+  // to P3 (<= 128 registers), three in 2D P4, FP32 MHD and 3D FP32 Euler up
+  // to P2 (<= 168), unconstrained elsewhere.
 #ifdef CW_FLUX_MINB
   static constexpr int FLUX_MINB = CW_FLUX_MINB;
 #else
-  static constexpr int FLUX_MINB = sizeof(T_) != 4 ? 1 : (D == 2 && NV == 4) ? 4 : (D == 2 || M <= 2) ? 3 : 1;
+  static constexpr int FLUX_MINB = sizeof(T_) != 4 ? 1 : (D == 2 && NV == 4 && M <= 3) ? 4 : (D == 2 || M <= 2) ? 3 : 1;
 #endif
-  // Reconstruction + predictor: four in 2D FP32 Euler (<= 128 registers),
-  // three in 3D FP32 Euler (<= 168; 128 spills); unconstrained where a cap
-  // would spill (MHD, FP64).
+  // Reconstruction + predictor: four in 2D FP32 Euler up to P3 (<= 128
+  // registers), three in 3D FP32 Euler (<= 168; 128 spills); unconstrained
+  // where a cap would spill (MHD, FP64, P4).
 #ifdef CW_REC_MINB
   static constexpr int REC_MINB = CW_REC_MINB;
 #else
-  static constexpr int REC_MINB = sizeof(T_) != 4 ? 1 : NV == 4 ? 4 : NV == 5 ? 3 : 1;
+  static constexpr int REC_MINB = (sizeof(T_) != 4 || M >= 4) ? 1 : NV == 4 ? 4 : NV == 5 ? 3 : 1;
 #endif
   // predictor working set (the fixed part and the current iterate of the L1
   // unknown space-time nodes) kept in shared memory, one column per thread,

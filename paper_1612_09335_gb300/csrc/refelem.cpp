@@ -162,11 +162,11 @@ PPoly PPoly::deriv(int var) const {
   return r;
 }
 
-bool lu_solve(int n, std::vector<double> A, std::vector<double>& B, int nrhs) {
-  std::vector<int> piv(n);
+template <typename R>
+static bool lu_solve_t(int n, std::vector<R> A, std::vector<R>& B, int nrhs) {
   for (int k = 0; k < n; ++k) {
     int p = k;
-    double best = std::fabs(A[k * n + k]);
+    R best = std::fabs(A[k * n + k]);
     for (int i = k + 1; i < n; ++i)
       if (std::fabs(A[i * n + k]) > best) {
         best = std::fabs(A[i * n + k]);
@@ -177,9 +177,9 @@ bool lu_solve(int n, std::vector<double> A, std::vector<double>& B, int nrhs) {
       for (int j = 0; j < n; ++j) std::swap(A[k * n + j], A[p * n + j]);
       for (int j = 0; j < nrhs; ++j) std::swap(B[k * nrhs + j], B[p * nrhs + j]);
     }
-    double inv = 1.0 / A[k * n + k];
+    R inv = R(1) / A[k * n + k];
     for (int i = k + 1; i < n; ++i) {
-      double f = A[i * n + k] * inv;
+      R f = A[i * n + k] * inv;
       A[i * n + k] = f;
       for (int j = k + 1; j < n; ++j) A[i * n + j] -= f * A[k * n + j];
       for (int j = 0; j < nrhs; ++j) B[i * nrhs + j] -= f * B[k * nrhs + j];
@@ -187,11 +187,15 @@ bool lu_solve(int n, std::vector<double> A, std::vector<double>& B, int nrhs) {
   }
   for (int j = 0; j < nrhs; ++j)
     for (int k = n - 1; k >= 0; --k) {
-      double s = B[k * nrhs + j];
+      R s = B[k * nrhs + j];
       for (int i = k + 1; i < n; ++i) s -= A[k * n + i] * B[i * nrhs + j];
       B[k * nrhs + j] = s / A[k * n + k];
     }
   return true;
+}
+
+bool lu_solve(int n, std::vector<double> A, std::vector<double>& B, int nrhs) {
+  return lu_solve_t<double>(n, std::move(A), B, nrhs);
 }
 
 // Homogenised Jacobi polynomial s^n P_n^{(alpha,0)}(u/s) by the three-term
@@ -376,81 +380,72 @@ void RefElem::init(int d_, int M_) {
       }
     }
   }
-  // space-time nodal basis: theta_l = sum_k Cinv[k][l] m_k(xi, tau), variables (xi_0..xi_{d-1}, tau)
+  // Space-time nodal basis theta_l = sum_k Cb[k][l] m_k(xi, tau) in
+  // monomials of (xi_0..xi_{d-1}, tau), built and evaluated in extended
+  // precision (long double): the coefficients reach 2.6e2 at M = 4, so
+  // double evaluation would lose about 1e-13.
+  using LD = long double;
   std::vector<std::array<int, 4>> stm = graded_monomials(d + 1, M);
-  std::vector<double> V((size_t)L * L), Cb((size_t)L * L, 0.0);
-  auto stpoint = [&](const std::array<double, 4>& nd, double* x) {
-    for (int a = 0; a < d; ++a) x[a] = nd[a];
-    x[d] = nd[3];
+  std::vector<LD> V((size_t)L * L), Cb((size_t)L * L, 0.0L);
+  auto ipow = [](LD x, int n) {
+    LD r = 1.0L;
+    for (int i = 0; i < n; ++i) r *= x;
+    return r;
   };
   for (int n = 0; n < L; ++n) {
-    double x[4];
-    stpoint(stnode[n], x);
+    LD x[4];
+    for (int a = 0; a < d; ++a) x[a] = (LD)stnode[n][a];
+    x[d] = (LD)stnode[n][3];
     for (int k = 0; k < L; ++k) {
-      double m = 1.0;
-      for (int a = 0; a <= d; ++a) m *= std::pow(x[a], stm[k][a]);
+      LD m = 1.0L;
+      for (int a = 0; a <= d; ++a) m *= ipow(x[a], stm[k][a]);
       V[n * L + k] = m;
     }
   }
-  for (int k = 0; k < L; ++k) Cb[k * L + k] = 1.0;
-  if (!lu_solve(L, V, Cb, L)) throw std::runtime_error("singular space-time Vandermonde");
-  std::vector<PPoly> theta(L);
-  for (int l = 0; l < L; ++l) {
-    theta[l].nvar = d + 1;
-    theta[l].e = stm;
-    theta[l].c.resize(L);
-    for (int k = 0; k < L; ++k) theta[l].c[k] = Cb[k * L + l];
-  }
-  // Galerkin matrices over T_E x [0,1] (rows: unknown nodes), Eq. (cgPDE)
-  {
-    SimplexQuad Q = simplex_quad(d, M + 1);
-    std::vector<double> tx, tw;
-    gauss_jacobi(M + 1, 0.0, 0.0, tx, tw);
-    std::vector<double> Kt((size_t)L1 * L, 0.0), Kx((size_t)d * L1 * L, 0.0);
-    std::vector<PPoly> dtau(L), dxi((size_t)d * L);
-    for (int l = 0; l < L; ++l) {
-      dtau[l] = theta[l].deriv(d);
-      for (int e = 0; e < d; ++e) dxi[e * L + l] = theta[l].deriv(e);
+  for (int k = 0; k < L; ++k) Cb[k * L + k] = 1.0L;
+  if (!lu_solve_t<LD>(L, V, Cb, L)) throw std::runtime_error("singular space-time Vandermonde");
+  // theta_l at (xi, tau), variables x[0..d-1] = xi, x[d] = tau
+  auto theta = [&](int l, const LD* x) {
+    LD s = 0.0L;
+    for (int k = 0; k < L; ++k) {
+      LD m = Cb[k * L + l];
+      for (int a = 0; a <= d; ++a) m *= ipow(x[a], stm[k][a]);
+      s += m;
     }
-    std::vector<double> th(L), dth(L), dx((size_t)d * L);
-    for (size_t g = 0; g < Q.w.size(); ++g)
-      for (int it = 0; it <= M; ++it) {
-        double x[4];
-        for (int a = 0; a < d; ++a) x[a] = Q.x[g][a];
-        x[d] = 0.5 * (1.0 + tx[it]);
-        double wgt = Q.w[g] * 0.5 * tw[it];
-        for (int l = 0; l < L; ++l) {
-          th[l] = theta[l].eval(x);
-          dth[l] = dtau[l].eval(x);
-          for (int e = 0; e < d; ++e) dx[e * L + l] = dxi[e * L + l].eval(x);
+    return s;
+  };
+  // Predictor matrices in closed form.  With the nodal flux interpolant in
+  // P_M, q(xi, tau) = q(xi, 0) - dt int_0^tau H(xi, s) ds is a degree-M
+  // polynomial with d_tau q + dt H = 0 pointwise, so the residual of Eq.
+  // (CGfinal) vanishes for every test function and (K_tau^1 being
+  // invertible) it is the Galerkin solution.  At the unknown node k:
+  //   C0[k][n]   = theta_n(xi_k, 0)  (the tau = 0 data extended in time),
+  //   P_e[k][l]  = int_0^{tau_k} d theta_l / d xi_e (xi_k, s) ds,
+  // the latter integrated exactly monomial by monomial.  This never forms
+  // (K_tau^1)^-1, whose condition number is 1.5e4 at M = 3 and 1.4e6 at M = 4.
+  C0.assign((size_t)L1 * L0, 0.0);
+  P.assign((size_t)d * L1 * L, 0.0);
+  for (int k = 0; k < L1; ++k) {
+    const std::array<double, 4>& nk = stnode[L0 + k];
+    LD x0[4];
+    for (int a = 0; a < d; ++a) x0[a] = (LD)nk[a];
+    x0[d] = 0.0L;
+    for (int n = 0; n < L0; ++n) C0[k * L0 + n] = (double)theta(n, x0);
+    const LD tk = (LD)nk[3];
+    for (int e = 0; e < d; ++e)
+      for (int l = 0; l < L; ++l) {
+        LD s = 0.0L;
+        for (int j = 0; j < L; ++j) {
+          const int pe = stm[j][e];
+          if (pe == 0) continue;
+          LD m = Cb[j * L + l] * pe;
+          for (int a = 0; a < d; ++a) m *= ipow((LD)nk[a], a == e ? stm[j][a] - 1 : stm[j][a]);
+          const int pt = stm[j][d];
+          m *= ipow(tk, pt + 1) / (LD)(pt + 1);
+          s += m;
         }
-        for (int k = 0; k < L1; ++k) {
-          double tk = th[L0 + k] * wgt;
-          for (int l = 0; l < L; ++l) {
-            Kt[k * L + l] += tk * dth[l];
-            for (int e = 0; e < d; ++e) Kx[((size_t)e * L1 + k) * L + l] += tk * dx[e * L + l];
-          }
-        }
+        P[((size_t)e * L1 + k) * L + l] = (double)s;
       }
-    // K1 = Kt[:, L0:]; C0 = -K1^{-1} Kt[:, :L0]; P_e = K1^{-1} Kx_e
-    std::vector<double> K1((size_t)L1 * L1);
-    for (int k = 0; k < L1; ++k)
-      for (int l = 0; l < L1; ++l) K1[k * L1 + l] = Kt[k * L + L0 + l];
-    int nr = L0 + d * L;
-    std::vector<double> RHS((size_t)L1 * nr);
-    for (int k = 0; k < L1; ++k) {
-      for (int l = 0; l < L0; ++l) RHS[k * nr + l] = -Kt[k * L + l];
-      for (int e = 0; e < d; ++e)
-        for (int l = 0; l < L; ++l) RHS[k * nr + L0 + e * L + l] = Kx[((size_t)e * L1 + k) * L + l];
-    }
-    if (!lu_solve(L1, K1, RHS, nr)) throw std::runtime_error("singular K_tau^1");
-    C0.assign((size_t)L1 * L0, 0.0);
-    P.assign((size_t)d * L1 * L, 0.0);
-    for (int k = 0; k < L1; ++k) {
-      for (int l = 0; l < L0; ++l) C0[k * L0 + l] = RHS[k * nr + l];
-      for (int e = 0; e < d; ++e)
-        for (int l = 0; l < L; ++l) P[((size_t)e * L1 + k) * L + l] = RHS[k * nr + L0 + e * L + l];
-    }
   }
   // face quadrature tables
   {
@@ -505,14 +500,15 @@ void RefElem::init(int d_, int M_) {
       if (d == 3) ref_vertex(d, ol[2], vC);
       for (int t = 0; t < nqt; ++t)
         for (int q = 0; q < nqs; ++q) {
-          double x[4];
+          LD x[4];
           for (int a = 0; a < d; ++a) {
-            x[a] = vA[a] + chi[q][0] * (vB[a] - vA[a]);
-            if (d == 3) x[a] += chi[q][1] * (vC[a] - vA[a]);
+            double xa = vA[a] + chi[q][0] * (vB[a] - vA[a]);
+            if (d == 3) xa += chi[q][1] * (vC[a] - vA[a]);
+            x[a] = (LD)xa;
           }
-          x[d] = tq[t];
+          x[d] = (LD)tq[t];
           for (int l = 0; l < L; ++l)
-            ftab[(((size_t)code * nqt + t) * nqs + q) * L + l] = theta[l].eval(x);
+            ftab[(((size_t)code * nqt + t) * nqs + q) * L + l] = (double)theta(l, x);
         }
     }
   }

@@ -4,8 +4,9 @@
 //   * orthonormal Dubiner-type basis psi_l on T_E (Sec. 2.1, Eq. recpolydef),
 //     with psi_0 := 1 so that the cell average is the first coefficient;
 //   * oscillation-indicator matrix Sigma_lm (Sec. 2.1);
-//   * space-time nodal basis theta_l and the Galerkin matrices K_tau, M, K_xi
-//     of Eq. (cgPDE), folded into the Picard update of Eq. (CGfinal);
+//   * space-time nodal basis theta_l and the predictor matrices of the
+//     Picard update of Eq. (CGfinal), in the closed form of its Galerkin
+//     solution (exact time integration of the interpolated flux divergence);
 //   * space-time Gauss quadrature on faces (Sec. 2.4) as basis tables.
 #pragma once
 #include <array>

@@ -67,8 +67,9 @@ def case_inputs(wl, name):
     raise KeyError(name)
 
 
-CASES = [("vortex2d", 2), ("vortex2d", 3), ("vortex2d", 4), ("explosion2d", 3), ("explosion2d", 4),
-         ("wave3d", 2), ("wave3d", 3), ("explosion3d", 3), ("orszag", 3), ("orszag", 4)]
+CASES = [("vortex2d", 2), ("vortex2d", 3), ("vortex2d", 4), ("vortex2d", 5), ("explosion2d", 3),
+         ("explosion2d", 4), ("explosion2d", 5), ("wave3d", 2), ("wave3d", 3), ("explosion3d", 3),
+         ("orszag", 3), ("orszag", 4)]
 
 
 def s_cfl(dim):
@@ -184,7 +185,8 @@ def test_state_roundtrip_and_device_pointers(cw, wl):
     assert torch.equal(out, Qd)
 
 
-@pytest.mark.parametrize("name,order", [("vortex2d", 3), ("explosion2d", 4), ("wave3d", 3), ("orszag", 4)])
+@pytest.mark.parametrize("name,order", [("vortex2d", 3), ("explosion2d", 4), ("explosion2d", 5), ("wave3d", 3),
+                                        ("orszag", 4)])
 def test_conservation_both_modes(cw, wl, name, order):
     """Sum |T_i| Q_i is conserved on periodic meshes (and changes only by
     boundary fluxes otherwise): drift below 1e-12 relative in both modes."""
@@ -207,7 +209,7 @@ def test_conservation_both_modes(cw, wl, name, order):
         assert np.all(np.abs(tot - tot0) <= 1e-12 * scale), (prec, tot - tot0)
 
 
-@pytest.mark.parametrize("dim,pde,order", [(2, EULER, 4), (3, EULER, 3), (2, MHD, 4)])
+@pytest.mark.parametrize("dim,pde,order", [(2, EULER, 4), (2, EULER, 5), (3, EULER, 3), (2, MHD, 4)])
 def test_free_stream_both_modes(cw, wl, dim, pde, order):
     mesh = wl.tri_mesh(12, jitter=0.2, seed=3) if dim == 2 else wl.tet_mesh(5, jitter=0.15, seed=3)
     if pde == EULER:
@@ -233,8 +235,8 @@ def test_free_stream_both_modes(cw, wl, dim, pde, order):
 # MHD-GLM: 3e-5 (psi and B_z come from cancellations in div B and the
 # induction fluxes); discontinuous data: 1e-4 (weights near jumps amplify
 # FP32 rounding of the indicators).
-@pytest.mark.parametrize("name,order,tol", [("vortex2d", 3, 2e-6), ("vortex2d", 4, 2e-6),
-                                            ("explosion2d", 4, 1e-4), ("wave3d", 3, 2e-6),
+@pytest.mark.parametrize("name,order,tol", [("vortex2d", 3, 2e-6), ("vortex2d", 4, 2e-6), ("vortex2d", 5, 2e-6),
+                                            ("explosion2d", 4, 1e-4), ("explosion2d", 5, 1e-4), ("wave3d", 3, 2e-6),
                                             ("orszag", 3, 3e-5), ("orszag", 4, 3e-5)])
 def test_one_step_fp32_mixed_bounds(cw, orc, wl, name, order, tol):
     (mesh, Q), pde = case_inputs(wl, name)

@@ -168,7 +168,7 @@ def test_geometry_3d_insphere(orc, wl):
 
 
 # ---------------------------------------------------------------- stencils
-@pytest.mark.parametrize("dim,order", [(2, 2), (2, 3), (2, 4), (3, 3)])
+@pytest.mark.parametrize("dim,order", [(2, 2), (2, 3), (2, 4), (2, 5), (3, 3)])
 def test_central_stencil_is_ranked_bfs(orc, wl, dim, order):
     mesh = wl.tri_mesh(10, jitter=0.2, seed=11) if dim == 2 else wl.tet_mesh(5, jitter=0.15, seed=11)
     o = orc.Oracle(mesh, order, EULER)
@@ -190,7 +190,7 @@ def test_central_stencil_is_ranked_bfs(orc, wl, dim, order):
         assert set(last[:need]) == set(S0.tolist()) - set(inner)
 
 
-@pytest.mark.parametrize("dim,order", [(2, 3), (2, 4), (3, 3)])
+@pytest.mark.parametrize("dim,order", [(2, 3), (2, 4), (2, 5), (3, 3)])
 def test_sector_cells_lie_in_open_cone(orc, wl, dim, order):
     mesh = wl.tri_mesh(10, jitter=0.2, seed=13) if dim == 2 else wl.tet_mesh(5, jitter=0.15, seed=13)
     o = orc.Oracle(mesh, order, EULER)
@@ -213,7 +213,7 @@ def test_sector_cells_lie_in_open_cone(orc, wl, dim, order):
 
 
 # ------------------------------------------------------- reconstruction pins
-@pytest.mark.parametrize("dim,order", [(2, 2), (2, 3), (2, 4), (3, 2), (3, 3)])
+@pytest.mark.parametrize("dim,order", [(2, 2), (2, 3), (2, 4), (2, 5), (3, 2), (3, 3)])
 def test_popt_reproduces_polynomials(orc, wl, dim, order):
     """p1: P_opt is exact for data that are averages of a degree-M polynomial."""
     M = order - 1
@@ -227,7 +227,7 @@ def test_popt_reproduces_polynomials(orc, wl, dim, order):
     assert np.abs(out["popt"] - ref).max() < 1e-11 * scale
 
 
-@pytest.mark.parametrize("dim,order", [(2, 3), (2, 4), (3, 3)])
+@pytest.mark.parametrize("dim,order", [(2, 3), (2, 4), (2, 5), (3, 3)])
 def test_linear_weights_mode_reproduces_polynomials(orc, wl, dim, order):
     """p1: with omega := lambda the CWENO polynomial equals P_opt (Eq. CWENO:P0)."""
     M = order - 1
@@ -242,7 +242,7 @@ def test_linear_weights_mode_reproduces_polynomials(orc, wl, dim, order):
     assert np.abs(w - ref).max() < 1e-11 * np.abs(ref).max()
 
 
-@pytest.mark.parametrize("dim,order", [(2, 2), (2, 4), (3, 3)])
+@pytest.mark.parametrize("dim,order", [(2, 2), (2, 4), (2, 5), (3, 3)])
 def test_nonlinear_weights_exact_for_linear_data(orc, wl, dim, order):
     """p1: for degree-1 data every candidate equals P_opt, so w is exact."""
     M = order - 1
@@ -266,7 +266,7 @@ def _interp_average(dim, M, vals, wl):
     return gw @ (Vg @ coef)
 
 
-@pytest.mark.parametrize("dim,order", [(2, 2), (2, 3), (2, 4), (3, 3)])
+@pytest.mark.parametrize("dim,order", [(2, 2), (2, 3), (2, 4), (2, 5), (3, 3)])
 def test_reconstruction_preserves_cell_average(orc, wl, dim, order):
     """p2: avg_{T_i} w_i = Q_i for discontinuous data (Eqs. CWENO:Popt, CWENO:Ps)."""
     M = order - 1
@@ -303,7 +303,7 @@ def test_weights_positive_and_normalised(orc, wl):
     assert kept.any()
 
 
-@pytest.mark.parametrize("dim,M", [(2, 1), (2, 2), (2, 3), (3, 2)])
+@pytest.mark.parametrize("dim,M", [(2, 1), (2, 2), (2, 3), (2, 4), (3, 2)])
 def test_oscillation_indicator_matches_sympy(orc, wl, dim, M):
     """p4: sigma = sum_{1<=|a|<=M} int_{T_E} (d^a p)^2, integrated exactly by sympy."""
     sp = pytest.importorskip("sympy")
@@ -460,7 +460,7 @@ def test_mhd_glm_flux_jacobian_eigenvalues(orc):
 
 
 # ----------------------------------------------------------------- predictor
-@pytest.mark.parametrize("dim,order,pde", [(2, 2, EULER), (2, 3, EULER), (2, 4, EULER),
+@pytest.mark.parametrize("dim,order,pde", [(2, 2, EULER), (2, 3, EULER), (2, 4, EULER), (2, 5, EULER),
                                            (3, 2, EULER), (3, 3, EULER), (2, 4, MHD)])
 def test_predictor_exact_for_advected_polynomial(orc, wl, dim, order, pde):
     """p5: constant velocity/pressure (and B) with polynomial density of degree M
@@ -494,6 +494,35 @@ def test_predictor_exact_for_advected_polynomial(orc, wl, dim, order, pde):
         xn = X[c, 0] + nodes[:, :dim] @ (X[c, 1:] - X[c, 0])
         ref = state(xn - dt * nodes[:, 3:4] * vel[None, :])
         assert np.abs(qh - ref).max() < 1e-11 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("dim,order,pde,tol", [(2, 2, EULER, 1e-12), (2, 3, EULER, 1e-12), (2, 4, EULER, 1e-11),
+                                               (3, 2, EULER, 1e-12), (3, 3, EULER, 1e-10), (2, 4, MHD, 1e-11),
+                                               (2, 5, EULER, 1e-7)])
+def test_predictor_closed_form_equals_galerkin_solve(orc, wl, dim, order, pde, tol):
+    """p5b: the predictor's closed form (w - dt int_0^tau H_h at the unknown
+    nodes) equals the Galerkin solve of Eq. (CGfinal) as written, for a
+    nonlinear state (Euler / MHD fluxes, random smooth data) over all M+1
+    Picard iterations.  The difference is the rounding of the Galerkin solve,
+    which scales with the condition number of K_tau^1 (about 5e1, 1.5e4, 1.4e6
+    for 2D M = 2, 3, 4), hence the tolerances."""
+    M = order - 1
+    mesh = wl.tri_mesh(4, periodic=False, jitter=0.2, seed=2) if dim == 2 else \
+        wl.tet_mesh(2, periodic=False, jitter=0.1, seed=2)
+    o = orc.Oracle(mesh, order, pde)
+    rng = np.random.default_rng(21)
+    X = mesh.cell_vertices()
+    nu = 9 if pde == MHD else dim + 2
+    for c in [0, mesh.nc - 1]:
+        xlat = X[c, 0] + lattice(dim, M) @ (X[c, 1:] - X[c, 0])
+        f = poly_field(dim, M, rng, nu, centre=X[c].mean(axis=0))
+        w = f(xlat) * 0.1
+        w[:, 0] += 1.0
+        w[:, dim + 1 if pde == EULER else 4] += 3.0
+        for dt in (0.02, 0.07):
+            a = o.predictor_from_w(c, w, dt)
+            b = o.predictor_from_w(c, w, dt, galerkin=True)
+            assert np.abs(a - b).max() < tol * np.abs(b).max(), (np.abs(a - b).max(), np.abs(b).max())
 
 
 # --------------------------------------------------------------------- step
@@ -588,7 +617,7 @@ def test_face_quadrature_and_closure(orc, wl):
             assert np.abs(tot).max() < 1e-15
 
 
-@pytest.mark.parametrize("order,linear", [(2, False), (2, True), (3, True), (4, True)])
+@pytest.mark.parametrize("order,linear", [(2, False), (2, True), (3, True), (4, True), (5, True)])
 def test_convergence_density_wave_2d(orc, wl, order, linear):
     """p10: design order M+1 on the smooth density wave (exact advection).
 
