@@ -36,6 +36,8 @@ WORKLOADS = {
                              "unit cube, density wave, Euler, P2, CFL 1/3"),
     "orszagtang2d_p3": dict(dim=2, order=4, pde=1, n=724, desc="724x724x2 jittered triangles, periodic "
                             "[0,2pi]^2, Orszag-Tang, MHD-GLM gamma 5/3 c_h 2, P3, CFL 0.5"),
+    "explosion2d_p4": dict(dim=2, order=5, pde=0, n=512, desc="512x512x2 jittered triangles on [-1,1]^2, "
+                           "transmissive, circular explosion, Euler gamma 1.4, P4 (fifth order), CFL 0.5"),
     "vortex2d_p2": dict(dim=2, order=3, pde=0, n=32, desc="32x32x2 jittered triangles, periodic unit "
                         "square, isentropic vortex, Euler, P2, CFL 0.5"),
 }
@@ -46,7 +48,7 @@ def make_inputs(name, n=None):
     from paper_1612_09335_gb300 import workloads as wl
     cfg = WORKLOADS[name]
     n = cfg["n"] if n is None else n
-    if name == "explosion2d_p3":
+    if name in ("explosion2d_p3", "explosion2d_p4"):
         return wl.explosion_2d(n)
     if name == "densitywave3d_p2":
         return wl.density_wave_3d(n)
@@ -495,7 +497,7 @@ def run_ours(args):
         out["serving"] = serving_run(cw, args.serve_requests)
     if not args.no_other:
         out["other_workloads"] = {}
-        for other in ("densitywave3d_p2", "orszagtang2d_p3"):
+        for other in ("densitywave3d_p2", "orszagtang2d_p3", "explosion2d_p4"):
             if other == name:
                 continue
             out["other_workloads"][other] = workload_rate(cw, other, stream, barrier, steps=10)

@@ -51,6 +51,8 @@ enum {
 
 enum { CWENO_EULER = 0, CWENO_MHD_GLM = 1 };
 enum { CWENO_FP64 = 0, CWENO_FP32_MIXED = 1 };
+/* Numerical flux at the space-time face points. */
+enum { CWENO_FLUX_RUSANOV = 0, CWENO_FLUX_OSHER = 1 };
 
 typedef struct cweno_mesh cweno_mesh;
 typedef struct cweno_solver cweno_solver;
@@ -60,7 +62,8 @@ typedef struct cweno_server cweno_server;
  * eps = 1e-14, r = 4, lambda_0 = 1e5, lambda_s = 1 (Sec. 2.1, after Eq.
  * weights2; the lambdas are normalised to sum 1 over the kept stencils),
  * CFL = 1/d (Eq. timestep), gamma = 1.4 (Euler) or 5/3 (MHD), c_h = 2,
- * Picard iterations of Eq. (CGfinal) = M + 1, positivity scaling on. */
+ * Picard iterations of Eq. (CGfinal) = M + 1, positivity scaling on,
+ * Rusanov flux. */
 typedef struct {
   double eps;          /* epsilon of Eq. (weights2) */
   double r;            /* exponent r of Eq. (weights2); must be 4 */
@@ -76,6 +79,11 @@ typedef struct {
                           cell-average values at a lattice node (Zhang & Shu
                           scaling; not part of the paper, inactive wherever the
                           reconstruction is admissible); 0: the paper's scheme */
+  int flux;            /* CWENO_FLUX_RUSANOV (default, Eq. rusanov) or
+                          CWENO_FLUX_OSHER: the Osher-type flux of Eq. (osher),
+                          |A_n| integrated along the straight path between the
+                          two traces by 3-point Gauss-Legendre; Euler only
+                          (EINVAL for MHD) */
 } cweno_params;
 
 /* Fill *p with the paper's defaults for dimension `dim` and `pde`. */

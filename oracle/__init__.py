@@ -65,6 +65,8 @@ def lib():
             L.orc_physical_flux.argtypes = [I, I, dp, dp, I, dp]
             L.orc_max_speed_normal.restype = D
             L.orc_max_speed_normal.argtypes = [I, I, dp, dp, dp]
+            L.orc_numerical_flux.argtypes = [I, I, dp, dp, dp, dp, dp]
+            L.orc_abs_jacobian.argtypes = [I, D, dp, dp, dp]
             L.orc_max_speed.restype = D
             L.orc_max_speed.argtypes = [I, I, dp, dp]
             L.orc_gauss_rule.argtypes = [I, I, dp, dp]
@@ -94,15 +96,16 @@ def _i(a):
 
 def default_params(dim: int = 2, pde: int = EULER, cfl: float | None = None, order: int = 3,
                    gamma: float | None = None, ch: float = 2.0, linear_weights: bool = False,
-                   niter: int | None = None, positivity: bool = True) -> np.ndarray:
-    """[eps, r, lambda0, lambda_s, gamma, c_h, cfl, picard iterations, linear_weights, positivity]."""
+                   niter: int | None = None, positivity: bool = True, flux: int = 0) -> np.ndarray:
+    """[eps, r, lambda0, lambda_s, gamma, c_h, cfl, picard iterations, linear_weights, positivity,
+    flux (0 Rusanov, 1 Osher-type)]."""
     if gamma is None:
         gamma = 1.4 if pde == EULER else 5.0 / 3.0
     if cfl is None:
         cfl = 0.5 if dim == 2 else 1.0 / 3.0
     M = order - 1
     return np.array([1e-14, 4.0, 1e5, 1.0, gamma, ch, cfl, float(M + 1 if niter is None else niter),
-                     1.0 if linear_weights else 0.0, 1.0 if positivity else 0.0])
+                     1.0 if linear_weights else 0.0, 1.0 if positivity else 0.0, float(flux)])
 
 
 class OracleMesh:
@@ -273,6 +276,27 @@ def physical_flux(pde, dim, q, m, params=None):
     f = np.zeros(len(q))
     lib().orc_physical_flux(pde, dim, _d(p), _d(q), int(m), _d(f))
     return f
+
+
+def numerical_flux(pde, dim, qm, qp, n, params=None):
+    """Numerical normal flux at one point, unit normal n: Rusanov, Eq.
+    (rusanov), or the Osher-type flux of Eq. (osher) when params[10] == 1."""
+    p = default_params(dim, pde) if params is None else np.asarray(params, float)
+    qm = np.ascontiguousarray(qm, dtype=np.float64)
+    qp = np.ascontiguousarray(qp, dtype=np.float64)
+    n = np.ascontiguousarray(n, dtype=np.float64)
+    g = np.zeros(len(qm))
+    lib().orc_numerical_flux(pde, dim, _d(p), _d(qm), _d(qp), _d(n), _d(g))
+    return g
+
+
+def abs_jacobian(dim, q, n, gamma=1.4):
+    """|A_n(q)| = R |Lambda| R^-1 of the Euler normal flux Jacobian."""
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    n = np.ascontiguousarray(n, dtype=np.float64)
+    out = np.zeros((len(q), len(q)))
+    lib().orc_abs_jacobian(dim, float(gamma), _d(q), _d(n), _d(out))
+    return out
 
 
 def max_speed_normal(pde, dim, q, n, params=None):

@@ -28,6 +28,7 @@
 //   space-time Galerkin predictor        Sec. 2.2, Eqs. (PDExi2)-(CGfinal)
 //   one-step finite volume update        Sec. 2.4, Eq. (PDEfinal), Eulerian case
 //   Rusanov flux                         Eq. (rusanov)
+//   Osher-type flux (Euler, switchable)  Eq. (osher), |A| = R|Lambda|R^-1
 //   Euler equations / EOS                Eqs. (eulerTerms), (eos)
 //   ideal MHD with GLM cleaning          Eqs. (MHDTerms), (MHDeos)
 //
@@ -43,6 +44,7 @@
 //     {xi >= 0, sum(xi) + tau <= 1} with step 1/M; test functions = nodal
 //     functions of the tau > 0 nodes; M+1 Picard iterations from w(xi);
 //   * Rusanov s_max per quadrature point, max over both sides;
+//   * Osher-type flux: the path integral of |A_n| by 3-point Gauss-Legendre;
 //   * MHD EOS p = (gamma-1)(rho E - rho|v|^2/2 - |B|^2/(8 pi)).
 //   * s_max and the time-step speed take sqrt(max(0, .)) of the sound speed.
 // Addition not in the paper (switchable, on by default): a positivity
@@ -453,6 +455,7 @@ enum { PDE_EULER = 0, PDE_MHD = 1 };
 struct Params {
   double eps, r, lam0, lams, gamma, ch, cfl;
   int niter, linear_weights, positivity;
+  int flux = 0;  // 0 Rusanov, Eq. (rusanov); 1 Osher-type, Eq. (osher) (Euler)
 };
 
 const double PI = 3.14159265358979323846;
@@ -523,6 +526,112 @@ double max_speed_normal(int pde, int d, const Params& P, const double* q, const 
   double bn2 = Bn * Bn / (4.0 * PI * rho);
   double cf2 = 0.5 * (a2 + b2 + std::sqrt(std::max(0.0, (a2 + b2) * (a2 + b2) - 4.0 * a2 * bn2)));
   return std::max(std::fabs(vn) + std::sqrt(std::max(0.0, cf2)), P.ch);
+}
+
+// |A_n(q)| = R |Lambda| R^{-1} for the Euler normal flux Jacobian
+// dF/dq . n at state q (unit normal n): R holds the right eigenvectors
+// (columns) for the eigenvalues vn - c, vn (entropy), vn (shear, d-1
+// tangents), vn + c; R^{-1} is formed numerically.  Out: nu x nu row-major.
+void euler_abs_jacobian(int d, double gamma, const double* q, const double* n, double* out) {
+  const int nu = d + 2;
+  double rho = q[0], v[3] = {0, 0, 0}, v2 = 0.0, vn = 0.0;
+  for (int k = 0; k < d; ++k) {
+    v[k] = q[1 + k] / rho;
+    v2 += v[k] * v[k];
+    vn += v[k] * n[k];
+  }
+  double p = (gamma - 1.0) * (q[d + 1] - 0.5 * rho * v2);
+  double c = std::sqrt(gamma * p / rho);
+  double H = (q[d + 1] + p) / rho;
+  // tangents: 2D (-n_y, n_x); 3D two unit vectors orthogonal to n
+  double t[2][3] = {{0, 0, 0}, {0, 0, 0}};
+  if (d == 2) {
+    t[0][0] = -n[1];
+    t[0][1] = n[0];
+  } else {
+    int a = 0;
+    for (int k = 1; k < 3; ++k)
+      if (std::fabs(n[k]) < std::fabs(n[a])) a = k;
+    double e[3] = {0, 0, 0};
+    e[a] = 1.0;
+    double t0[3] = {n[1] * e[2] - n[2] * e[1], n[2] * e[0] - n[0] * e[2], n[0] * e[1] - n[1] * e[0]};
+    double l0 = std::sqrt(t0[0] * t0[0] + t0[1] * t0[1] + t0[2] * t0[2]);
+    for (int k = 0; k < 3; ++k) t[0][k] = t0[k] / l0;
+    double t1[3] = {n[1] * t[0][2] - n[2] * t[0][1], n[2] * t[0][0] - n[0] * t[0][2], n[0] * t[0][1] - n[1] * t[0][0]};
+    for (int k = 0; k < 3; ++k) t[1][k] = t1[k];
+  }
+  std::vector<double> R((size_t)nu * nu, 0.0), lam(nu);
+  auto col = [&](int j, const std::vector<double>& r) {
+    for (int i = 0; i < nu; ++i) R[i * nu + j] = r[i];
+  };
+  std::vector<double> r(nu);
+  r[0] = 1.0;
+  for (int k = 0; k < d; ++k) r[1 + k] = v[k] - c * n[k];
+  r[d + 1] = H - c * vn;
+  col(0, r);
+  lam[0] = vn - c;
+  r[0] = 1.0;
+  for (int k = 0; k < d; ++k) r[1 + k] = v[k];
+  r[d + 1] = 0.5 * v2;
+  col(1, r);
+  lam[1] = vn;
+  for (int a = 0; a < d - 1; ++a) {
+    r[0] = 0.0;
+    double vt = 0.0;
+    for (int k = 0; k < d; ++k) {
+      r[1 + k] = t[a][k];
+      vt += v[k] * t[a][k];
+    }
+    r[d + 1] = vt;
+    col(2 + a, r);
+    lam[2 + a] = vn;
+  }
+  r[0] = 1.0;
+  for (int k = 0; k < d; ++k) r[1 + k] = v[k] + c * n[k];
+  r[d + 1] = H + c * vn;
+  col(nu - 1, r);
+  lam[nu - 1] = vn + c;
+  // R^{-1} by elimination on the identity
+  std::vector<double> Rinv((size_t)nu * nu, 0.0);
+  for (int i = 0; i < nu; ++i) Rinv[i * nu + i] = 1.0;
+  gauss_solve(nu, R, Rinv, nu);
+  for (int i = 0; i < nu; ++i)
+    for (int j = 0; j < nu; ++j) {
+      double sum = 0.0;
+      for (int k = 0; k < nu; ++k) sum += R[i * nu + k] * std::fabs(lam[k]) * Rinv[k * nu + j];
+      out[i * nu + j] = sum;
+    }
+}
+
+// Numerical normal flux at a face point (unit normal n): Rusanov, Eq.
+// (rusanov), or Osher-type, Eq. (osher), whose dissipation integrates
+// |A_n| along the straight path psi(s) = q- + s (q+ - q-) with 3-point
+// Gauss-Legendre (the paper leaves the rule open).
+void numerical_flux(int pde, int d, const Params& P, const double* qm, const double* qp, const double* n,
+                    double* G) {
+  const int nu = nvars(pde, d);
+  std::vector<double> fm(nu, 0.0), fp(nu, 0.0), fd(nu);
+  for (int mm = 0; mm < d; ++mm) {
+    flux(pde, d, P, qm, mm, fd.data());
+    for (int v = 0; v < nu; ++v) fm[v] += fd[v] * n[mm];
+    flux(pde, d, P, qp, mm, fd.data());
+    for (int v = 0; v < nu; ++v) fp[v] += fd[v] * n[mm];
+  }
+  if (P.flux == 1 && pde == PDE_EULER) {
+    std::vector<double> sx, sw;
+    gauss_legendre01(3, sx, sw);
+    std::vector<double> absA((size_t)nu * nu), psi(nu), dis(nu, 0.0);
+    for (int j = 0; j < 3; ++j) {
+      for (int v = 0; v < nu; ++v) psi[v] = qm[v] + sx[j] * (qp[v] - qm[v]);
+      euler_abs_jacobian(d, P.gamma, psi.data(), n, absA.data());
+      for (int a = 0; a < nu; ++a)
+        for (int b = 0; b < nu; ++b) dis[a] += sw[j] * absA[a * nu + b] * (qp[b] - qm[b]);
+    }
+    for (int v = 0; v < nu; ++v) G[v] = 0.5 * (fm[v] + fp[v]) - 0.5 * dis[v];
+    return;
+  }
+  double smax = std::max(max_speed_normal(pde, d, P, qm, n), max_speed_normal(pde, d, P, qp, n));
+  for (int v = 0; v < nu; ++v) G[v] = 0.5 * (fm[v] + fp[v]) - 0.5 * smax * (qp[v] - qm[v]);
 }
 
 // Largest |eigenvalue| over all directions (for the time step).
@@ -1446,7 +1555,7 @@ int orc_mesh_geometry(void* p, double* vol, double* bary, double* h, int64_t* nb
   return 0;
 }
 
-// params: eps, r, lam0, lams, gamma, ch, cfl, niter, linear_weights, positivity
+// params: eps, r, lam0, lams, gamma, ch, cfl, niter, linear_weights, positivity, flux
 void* orc_solver_new(void* mesh, int M, int pde, const double* prm, char* err, int errlen) {
   OMesh* m = (OMesh*)mesh;
   if (M < 1 || M > 4 || (pde != PDE_EULER && pde != PDE_MHD)) {
@@ -1469,6 +1578,12 @@ void* orc_solver_new(void* mesh, int M, int pde, const double* prm, char* err, i
   S->P.niter = (int)prm[7];
   S->P.linear_weights = (int)prm[8];
   S->P.positivity = (int)prm[9];
+  S->P.flux = (int)prm[10];
+  if (S->P.flux != 0 && pde != PDE_EULER) {
+    delete S;
+    set_err(err, errlen, "the Osher-type flux is built for the Euler equations");
+    return nullptr;
+  }
   S->Mc = Mcal(M, m->d);
   S->ne = m->d * S->Mc;
   S->mono = monomial_list(m->d, M);
@@ -1614,7 +1729,7 @@ int orc_step(void* p, const double* Q, double dt, int64_t n, const int64_t* ids,
   }
   std::vector<double> tx, tw;
   gauss_legendre01(M + 1, tx, tw);
-  std::vector<double> qm(nu), qp(nu), fm(nu), fp(nu), fdir(nu);
+  std::vector<double> qm(nu), qp(nu), fdir(nu);
   for (long c = 0; c < cnt; ++c) {
     long i = ids ? ids[c] : c;
     std::vector<double> acc(nu, 0.0);
@@ -1648,23 +1763,9 @@ int orc_step(void* p, const double* Q, double dt, int64_t n, const int64_t* ids,
             if (!(qp[0] > 0.0 && pressure(S->pde, d, S->P, qp.data()) > 0.0))
               for (int v = 0; v < nu; ++v) qp[v] = j >= 0 ? Q[j * nu + v] : Q[i * nu + v];
           }
-          // Rusanov flux, Eq. (rusanov), Eulerian normal (n |f| dt, 0)
-          for (int v = 0; v < nu; ++v) {
-            fm[v] = 0.0;
-            fp[v] = 0.0;
-          }
-          for (int mm = 0; mm < d; ++mm) {
-            flux(S->pde, d, S->P, qm.data(), mm, fdir.data());
-            for (int v = 0; v < nu; ++v) fm[v] += fdir[v] * nrm[mm];
-            flux(S->pde, d, S->P, qp.data(), mm, fdir.data());
-            for (int v = 0; v < nu; ++v) fp[v] += fdir[v] * nrm[mm];
-          }
-          double smax = std::max(max_speed_normal(S->pde, d, S->P, qm.data(), nrm),
-                                 max_speed_normal(S->pde, d, S->P, qp.data(), nrm));
-          for (int v = 0; v < nu; ++v) {
-            double G = 0.5 * (fm[v] + fp[v]) - 0.5 * smax * (qp[v] - qm[v]);
-            acc[v] += dt * area * wts[q] * tw[t] * G;
-          }
+          // numerical flux, Eq. (rusanov) or (osher), Eulerian normal (n |f| dt, 0)
+          numerical_flux(S->pde, d, S->P, qm.data(), qp.data(), nrm, fdir.data());
+          for (int v = 0; v < nu; ++v) acc[v] += dt * area * wts[q] * tw[t] * fdir[v];
         }
       }
     }
@@ -1699,6 +1800,22 @@ double orc_max_speed_normal(int pde, int d, const double* prm, const double* q, 
   P.gamma = prm[4];
   P.ch = prm[5];
   return max_speed_normal(pde, d, P, q, n);
+}
+
+// Numerical normal flux (prm[10] selects Rusanov / Osher) and |A_n| (Euler).
+int orc_numerical_flux(int pde, int d, const double* prm, const double* qm, const double* qp, const double* n,
+                       double* G) {
+  Params P;
+  P.gamma = prm[4];
+  P.ch = prm[5];
+  P.flux = (int)prm[10];
+  numerical_flux(pde, d, P, qm, qp, n, G);
+  return 0;
+}
+
+int orc_abs_jacobian(int d, double gamma, const double* q, const double* n, double* out) {
+  euler_abs_jacobian(d, gamma, q, n, out);
+  return 0;
 }
 
 double orc_max_speed(int pde, int d, const double* prm, const double* q) {

@@ -17,6 +17,7 @@ from . import _build
 
 EULER, MHD_GLM = 0, 1
 FP64, FP32_MIXED = 0, 1
+FLUX_RUSANOV, FLUX_OSHER = 0, 1
 OK, EINVAL, EDEGENERATE, ENOMEM, EBUSY, ENAN, ETIMEDOUT, ECUDA, ENOTFOUND = 0, -1, -2, -3, -4, -5, -6, -7, -8
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_ERROR = 0, 1, 2, 3
 
@@ -30,7 +31,7 @@ class CwenoError(RuntimeError):
 class cweno_params(C.Structure):
     _fields_ = [("eps", C.c_double), ("r", C.c_double), ("lambda0", C.c_double), ("lambda_s", C.c_double),
                 ("gamma", C.c_double), ("c_h", C.c_double), ("cfl", C.c_double), ("picard_iters", C.c_int),
-                ("linear_weights", C.c_int), ("positivity", C.c_int)]
+                ("linear_weights", C.c_int), ("positivity", C.c_int), ("flux", C.c_int)]
 
 
 class cweno_request(C.Structure):

@@ -150,6 +150,7 @@ void cweno_default_params(cweno_params* p, int dim, int pde) {
   p->picard_iters = 0;
   p->linear_weights = 0;
   p->positivity = 1;
+  p->flux = CWENO_FLUX_RUSANOV;
 }
 
 const char* cweno_last_error(void) { return g_err.c_str(); }
@@ -239,6 +240,9 @@ int cweno_setup(const cweno_mesh* mesh, int order, int pde, int precision, const
   if (prm.r != 4.0) return fail(CWENO_EINVAL, "only r = 4 is built (Eq. weights2)");
   if (!(prm.eps > 0) || !(prm.lambda0 > 0) || !(prm.lambda_s > 0) || !(prm.gamma > 1.0) || !(prm.cfl > 0))
     return fail(CWENO_EINVAL, "bad scheme parameters");
+  if (prm.flux != CWENO_FLUX_RUSANOV && prm.flux != CWENO_FLUX_OSHER) return fail(CWENO_EINVAL, "unknown flux");
+  if (prm.flux == CWENO_FLUX_OSHER && pde != CWENO_EULER)
+    return fail(CWENO_EINVAL, "the Osher-type flux is built for the Euler equations");
   const int M = order - 1;
   std::unique_ptr<cweno_solver> s(new cweno_solver());
   s->dim = m.d;
@@ -256,6 +260,7 @@ int cweno_setup(const cweno_mesh* mesh, int order, int pde, int precision, const
   s->ph.niter = prm.picard_iters > 0 ? prm.picard_iters : M + 1;
   s->ph.linear_weights = prm.linear_weights;
   s->ph.positivity = prm.positivity;
+  s->ph.flux = prm.flux;
   s->nc = m.nc;
   s->nf = m.nf;
   CK(cudaGetDevice(&s->dev));

@@ -145,7 +145,7 @@ struct KArgs {
   int* status;
   double* out;
   T gamma, ch, eps, lam0, lams;
-  int niter, linw, pos;
+  int niter, linw, pos, flux;
   double dt_fixed, cfl;
   int cur, reset_next;
 };
@@ -229,6 +229,69 @@ struct Phys<D, 0, T> {  // Euler, Eqs. (eulerTerms), (eos)
 #pragma unroll
     for (int a = 0; a < D; ++a) m2 += q[1 + a] * q[1 + a];
     return (gamma - T(1)) * (q[D + 1] - T(0.5) * m2 * arcp(q[0]));
+  }
+  // Dissipation of the Osher-type flux, Eq. (osher): out = sum_j w_j
+  // |A_n(psi_j)| (ur - ul) over the 3-point Gauss-Legendre rule on the path
+  // psi(s) = ul + s (ur - ul), unit normal n.  |A_n| dq is formed from the
+  // characteristic decomposition at psi: linearised primitive variations
+  // (drho, du, dp) of dq, wave strengths of the acoustic (vn -+ c), entropy
+  // and shear (vn) waves, each scaled by |eigenvalue| times its right
+  // eigenvector.
+  __device__ __forceinline__ static void osher_dissipation(const T* ul, const T* ur, const T* n, T gamma, T* out) {
+    T dq[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      dq[v] = ur[v] - ul[v];
+      out[v] = T(0);
+    }
+    const T sq = T(0.38729833462074168852);  // sqrt(3/5) / 2
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const T sj = T(0.5) + (j == 0 ? -sq : j == 1 ? T(0) : sq);
+      const T wj = j == 1 ? T(8.0 / 18.0) : T(5.0 / 18.0);
+      T q[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) q[v] = ul[v] + sj * dq[v];
+      const T rho = q[0], ir = arcp(q[0]);
+      T u[D], u2 = T(0), un = T(0), udm = T(0);
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        u[a] = q[1 + a] * ir;
+        u2 += u[a] * u[a];
+        un += u[a] * n[a];
+        udm += u[a] * dq[1 + a];
+      }
+      const T p = (gamma - T(1)) * (q[D + 1] - T(0.5) * rho * u2);
+      const T c2 = gamma * p * ir;
+      const T c = asqrt(c2 > T(0) ? c2 : T(0));
+      const T ic2 = arcp(c2);
+      const T H = (q[D + 1] + p) * ir;
+      // linearised primitive variations at psi
+      const T drho = dq[0];
+      T du[D], dun = T(0);
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        du[a] = (dq[1 + a] - u[a] * drho) * ir;
+        dun += du[a] * n[a];
+      }
+      const T dp = (gamma - T(1)) * (dq[D + 1] - udm + T(0.5) * u2 * drho);
+      // wave strengths
+      const T am = T(0.5) * (dp - rho * c * dun) * ic2;
+      const T ap = T(0.5) * (dp + rho * c * dun) * ic2;
+      const T a0 = drho - dp * ic2;
+      const T lm = fabs(un - c) * wj, lp = fabs(un + c) * wj, l0 = fabs(un) * wj;
+      T dut[D], udut = T(0);
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        dut[a] = du[a] - dun * n[a];
+        udut += u[a] * dut[a];
+      }
+      out[0] += lm * am + lp * ap + l0 * a0;
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+        out[1 + a] += lm * am * (u[a] - c * n[a]) + lp * ap * (u[a] + c * n[a]) + l0 * (a0 * u[a] + rho * dut[a]);
+      out[D + 1] += lm * am * (H - c * un) + lp * ap * (H + c * un) + l0 * (a0 * T(0.5) * u2 + rho * udut);
+    }
   }
 };
 
@@ -784,10 +847,12 @@ __device__ __forceinline__ void face_traces(const typename C::T* __restrict__ qh
   }
 }
 
-// Rusanov flux (Eq. rusanov) at one space-time point with quadrature weight
-// wgt, from the traces ul, ur (cell average + deviation) of both sides:
-// facc[m] += wgt (F_m(u-) + F_m(u+)) per direction m, dacc += wgt s (u+ - u-),
-// s the larger of the two sides' maximal signal speeds along n.  A trace that
+// Numerical flux at one space-time point with quadrature weight wgt, from
+// the traces ul, ur (cell average + deviation) of both sides:
+// facc[m] += wgt (F_m(u-) + F_m(u+)) per direction m, and dacc += wgt s
+// (u+ - u-), s the larger of the two sides' maximal signal speeds along n
+// (Rusanov, Eq. rusanov), or dacc += wgt int_0^1 |A_n(psi)| ds (u+ - u-)
+// (Osher-type, Eq. osher; Euler).  A trace that
 // is not an admissible state (density or pressure <= 0) is replaced by its
 // cell average at this point (positivity safeguard, with the scaling of the
 // reconstruction).
@@ -813,8 +878,6 @@ __device__ __forceinline__ void rusanov_point(const KArgs<C>& a, typename C::T* 
       pr = PH::prim(ur, a.gamma);
     }
   }
-  const T sl = PH::smax(pl, n, a.gamma, a.ch), sr = PH::smax(pr, n, a.gamma, a.ch);
-  const T s = sl > sr ? sl : sr;
 #pragma unroll
   for (int m = 0; m < D; ++m) {
     T em[D];
@@ -826,6 +889,17 @@ __device__ __forceinline__ void rusanov_point(const KArgs<C>& a, typename C::T* 
 #pragma unroll
     for (int v = 0; v < NV; ++v) facc[m][v] += wgt * (fl[v] + fr[v]);
   }
+  if constexpr (C::PDE == 0) {
+    if (a.flux) {  // Osher-type, Eq. (osher)
+      T dis[NV];
+      PH::osher_dissipation(ul, ur, n, a.gamma, dis);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) dacc[v] += wgt * dis[v];
+      return;
+    }
+  }
+  const T sl = PH::smax(pl, n, a.gamma, a.ch), sr = PH::smax(pr, n, a.gamma, a.ch);
+  const T s = sl > sr ? sl : sr;
   const T ws = wgt * s;
 #pragma unroll
   for (int v = 0; v < NV; ++v) dacc[v] += ws * (ur[v] - ul[v]);
@@ -1260,6 +1334,7 @@ class OpsImpl final : public Ops {
     a.niter = ph.niter;
     a.linw = ph.linear_weights;
     a.pos = ph.positivity;
+    a.flux = ph.flux;
     a.dt_fixed = dt.fixed;
     a.cfl = dt.cfl;
     a.cur = dt.cur;

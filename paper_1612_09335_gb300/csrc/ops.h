@@ -47,6 +47,7 @@ struct PhysParams {
   double gamma = 1.4, ch = 2.0;
   double eps = 1e-14, lam0 = 1e5, lams = 1.0;
   int niter = 2, linear_weights = 0, positivity = 1;
+  int flux = 0;  // 0 Rusanov, 1 Osher-type (Euler)
 };
 
 // Time step source: fixed > 0, else cfl * (min h/lambda) read from dtmin[cur].

@@ -43,6 +43,21 @@ def test_default_params_are_the_papers(cw):
     pm = cw.cweno_default_params(2, cw.MHD_GLM)
     assert abs(pm.gamma - 5 / 3) < 1e-15 and pm.c_h == 2.0
     assert cw.cweno_nvars(2, cw.EULER) == 4 and cw.cweno_nvars(3, cw.EULER) == 5 and cw.cweno_nvars(2, cw.MHD_GLM) == 9
+    assert p.flux == cw.FLUX_RUSANOV and p.positivity == 1 and p.linear_weights == 0 and p.picard_iters == 0
+
+
+def test_setup_rejects_unsupported_combinations_before_device_work(cw, wl):
+    """Argument checks run before any device call (so they hold without a
+    GPU): order range, order 5 outside 2D Euler, the Osher flux for MHD, an
+    unknown flux."""
+    m2 = cw.Mesh.from_workload(wl.tri_mesh(6))
+    m3 = cw.Mesh.from_workload(wl.tet_mesh(3))
+    cases = [(m2, 6, cw.EULER, {}), (m2, 1, cw.EULER, {}), (m3, 5, cw.EULER, {}), (m2, 5, cw.MHD_GLM, {}),
+             (m2, 3, cw.MHD_GLM, {"flux": cw.FLUX_OSHER}), (m2, 3, cw.EULER, {"flux": 7})]
+    for mesh, order, pde, kw in cases:
+        with pytest.raises(cw.CwenoError) as e:
+            cw.Solver(mesh, order, pde, **kw)
+        assert e.value.code == cw.EINVAL, (order, pde, kw)
 
 
 def test_mesh_validation_errors(cw, wl):

@@ -8,7 +8,8 @@ averages on 64^2, 128^2, 256^2 x 2 jittered triangles.
   finest pair (this pins reconstruction, predictor, fluxes and update).
 * With the paper's weights (eps = 1e-14, r = 4) the weight of P_0 drops next
   to the vortex's critical points; measured: P2 2.78 -> 3.14, P3 2.74 -> 3.09
-  (and 2.95 at 512^2).  Required: P2 >= 2.7, P3 >= 2.9.
+  (and 2.95 at 512^2), P4 2.55 -> 3.15 (still rising; the linear P4 scheme:
+  4.85 -> 4.88).  Required: P2 >= 2.7, P3 >= 2.9, P4 >= 3.0.
 * FP32-mixed must not lower the order: its rate matches the FP64 rate within
   0.1 on every pair whose finer FP64 error is above 1e-4 (two orders above
   the FP32 floor of about 1e-6 here)."""
@@ -52,7 +53,7 @@ def l1_error(cw, wl, n, order, prec, tf=1.0, linear=0):
     return float(vol @ np.abs(Q[:, 0] - ex[:, 0]))
 
 
-@pytest.mark.parametrize("order", [3, 4])
+@pytest.mark.parametrize("order", [3, 4, 5])
 def test_vortex_design_order_fp64_and_fp32(cw, wl, order):
     ns = (64, 128, 256)
     runs = {(p, lin): [l1_error(cw, wl, n, order, p, linear=lin) for n in ns]
@@ -60,7 +61,7 @@ def test_vortex_design_order_fp64_and_fp32(cw, wl, order):
     rates = {k: [math.log(e[j] / e[j + 1], 2) for j in range(len(ns) - 1)] for k, e in runs.items()}
     print("order", order, "errors", runs, "rates", rates)
     assert rates[(cw.FP64, 1)][-1] > order - 0.3, (runs, rates)
-    assert rates[(cw.FP64, 0)][-1] > {3: 2.7, 4: 2.9}[order], (runs, rates)
+    assert rates[(cw.FP64, 0)][-1] > {3: 2.7, 4: 2.9, 5: 3.0}[order], (runs, rates)
     checked = 0
     for lin in (0, 1):
         for j in range(len(ns) - 1):

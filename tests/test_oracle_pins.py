@@ -682,3 +682,88 @@ def test_explosion_stays_admissible(orc, wl):
     for _ in range(8):
         Q = o.step(Q, o.stable_dt(Q))
     assert np.isfinite(Q).all() and Q[:, 0].min() > 0.12 and _pressure(Q).min() > 0.09
+
+
+# --------------------------------------------------------- Osher-type flux
+def _osher_state(dim, rng, rho=None, vel=None, p=None, gamma=1.4):
+    rho = rng.uniform(0.5, 2.0) if rho is None else rho
+    vel = rng.normal(size=dim) if vel is None else np.asarray(vel, float)
+    p = rng.uniform(0.5, 2.0) if p is None else p
+    return np.concatenate([[rho], rho * vel, [p / (gamma - 1) + 0.5 * rho * vel @ vel]])
+
+
+def _unit(dim, rng):
+    n = rng.normal(size=dim)
+    return n / np.linalg.norm(n)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_abs_jacobian_matches_eigendecomposition(orc, dim):
+    """|A_n| of Eq. (osher): against numpy's eigendecomposition of the normal
+    flux Jacobian taken by central differences of the physical flux."""
+    rng = np.random.default_rng(31 + dim)
+    for _ in range(5):
+        q, n = _osher_state(dim, rng), _unit(dim, rng)
+
+        def fn(x):
+            return sum(orc.physical_flux(EULER, dim, x, m) * n[m] for m in range(dim))
+        J = np.zeros((dim + 2, dim + 2))
+        for b in range(dim + 2):
+            h = 1e-6 * max(1.0, abs(q[b]))
+            e = np.zeros(dim + 2)
+            e[b] = h
+            J[:, b] = (fn(q + e) - fn(q - e)) / (2 * h)
+        lam, R = np.linalg.eig(J)
+        ref = np.real(R @ np.diag(np.abs(lam)) @ np.linalg.inv(R))
+        got = orc.abs_jacobian(dim, q, n)
+        assert np.abs(got - ref).max() < 1e-6 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_osher_flux_consistent_and_conservative(orc, dim):
+    """G(q, q, n) = F(q).n; G(q-, q+, n) = -G(q+, q-, -n) (the 3-point path
+    rule is symmetric, |A_{-n}| = |A_n|)."""
+    rng = np.random.default_rng(41 + dim)
+    prm = orc.default_params(dim, EULER, flux=1)
+    for _ in range(5):
+        qm, qp, n = _osher_state(dim, rng), _osher_state(dim, rng), _unit(dim, rng)
+        fn = sum(orc.physical_flux(EULER, dim, qm, m) * n[m] for m in range(dim))
+        assert np.abs(orc.numerical_flux(EULER, dim, qm, qm, n, prm) - fn).max() < 1e-14 * np.abs(fn).max()
+        a = orc.numerical_flux(EULER, dim, qm, qp, n, prm)
+        b = orc.numerical_flux(EULER, dim, qp, qm, -n, prm)
+        assert np.abs(a + b).max() < 1e-13 * np.abs(a).max()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_osher_flux_upwinds_supersonic_flow(orc, dim):
+    """With every eigenvalue positive along the path |A| = A, and with equal
+    densities the flux along the straight path is a cubic in s, so 3-point
+    Gauss-Legendre integrates A(psi) (q+ - q-) exactly: the Osher flux is the
+    upwind flux F(q-).n.  Rusanov is not."""
+    rng = np.random.default_rng(51 + dim)
+    prm = orc.default_params(dim, EULER, flux=1)
+    for _ in range(4):
+        n = _unit(dim, rng)
+        qm = _osher_state(dim, rng, rho=1.3, vel=4.0 * n + 0.3 * rng.normal(size=dim), p=0.8)
+        qp = _osher_state(dim, rng, rho=1.3, vel=4.5 * n + 0.3 * rng.normal(size=dim), p=1.1)
+        fm = sum(orc.physical_flux(EULER, dim, qm, m) * n[m] for m in range(dim))
+        g = orc.numerical_flux(EULER, dim, qm, qp, n, prm)
+        assert np.abs(g - fm).max() < 1e-13 * np.abs(fm).max()
+        r = orc.numerical_flux(EULER, dim, qm, qp, n, orc.default_params(dim, EULER))
+        assert np.abs(r - fm).max() > 1e-3 * np.abs(fm).max()
+
+
+def test_osher_flux_resolves_stationary_contact(orc):
+    """A contact at rest (equal pressure, zero velocity, density jump): the
+    entropy wave has speed 0, so the Osher flux carries no dissipation and
+    equals the exact flux (0, p n, 0); Rusanov diffuses the density."""
+    rng = np.random.default_rng(61)
+    for dim in (2, 3):
+        n = _unit(dim, rng)
+        qm = _osher_state(dim, rng, rho=1.0, vel=np.zeros(dim), p=0.7)
+        qp = _osher_state(dim, rng, rho=0.125, vel=np.zeros(dim), p=0.7)
+        exact = np.concatenate([[0.0], 0.7 * n, [0.0]])
+        g = orc.numerical_flux(EULER, dim, qm, qp, n, orc.default_params(dim, EULER, flux=1))
+        assert np.abs(g - exact).max() < 1e-14
+        r = orc.numerical_flux(EULER, dim, qm, qp, n, orc.default_params(dim, EULER))
+        assert abs(r[0]) > 0.1
