@@ -300,17 +300,21 @@ def accuracy_run(cw, m, cfg, Q0, nsteps=10):
     return a.get_state(), b.get_state(), dt
 
 
-def workload_rate(cw, name, stream, barrier, steps=10):
-    """Cell-updates/s of another benchmark workload in both precisions (same
-    timing method: CUDA events on the solver stream, device CFL step)."""
+def workload_rate(cw, name, stream, barrier, steps=10, flux=0, precisions=None, inputs=None):
+    """Cell-updates/s of a benchmark workload in both precisions (same
+    timing method: CUDA events on the solver stream, device CFL step);
+    `flux` selects the face flux (0 Rusanov, 1 Osher-type, 2 quadrature-free
+    Rusanov)."""
     import torch
     cfg = WORKLOADS[name]
-    mesh, Q0 = make_inputs(name)
+    mesh, Q0 = make_inputs(name) if inputs is None else inputs
     m = cw.Mesh.from_workload(mesh)
     res = {"cells": mesh.nc, "mesh": cfg["desc"], "order": cfg["order"],
            "pde": "euler" if cfg["pde"] == 0 else "mhd_glm"}
-    for prec, key, k in ((cw.FP32_MIXED, "fp32_mixed", steps), (cw.FP64, "fp64", max(3, steps // 2))):
-        s = cw.Solver(m, cfg["order"], cfg["pde"], prec, stream=stream.cuda_stream)
+    if precisions is None:
+        precisions = ((cw.FP32_MIXED, "fp32_mixed", steps), (cw.FP64, "fp64", max(3, steps // 2)))
+    for prec, key, k in precisions:
+        s = cw.Solver(m, cfg["order"], cfg["pde"], prec, stream=stream.cuda_stream, flux=flux)
         s.set_state(Q0)
         for _ in range(3):
             s.step(0.0)
@@ -501,6 +505,14 @@ def run_ours(args):
             if other == name:
                 continue
             out["other_workloads"][other] = workload_rate(cw, other, stream, barrier, steps=10)
+        # the other face fluxes on the bench workload (FP32-mixed)
+        out["flux_variants"] = {}
+        for key, fl in (("osher", cw.FLUX_OSHER), ("rusanov_quadrature_free", cw.FLUX_RUSANOV_QF)):
+            if fl == cw.FLUX_OSHER and cfg["pde"] != 0:
+                continue
+            r = workload_rate(cw, name, stream, barrier, steps=20, flux=fl, inputs=(mesh, Q0),
+                              precisions=((cw.FP32_MIXED, "fp32_mixed", 20),))
+            out["flux_variants"][key] = r["fp32_mixed"]
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_run(name)
     if rank == 0:

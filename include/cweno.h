@@ -52,7 +52,7 @@ enum {
 enum { CWENO_EULER = 0, CWENO_MHD_GLM = 1 };
 enum { CWENO_FP64 = 0, CWENO_FP32_MIXED = 1 };
 /* Numerical flux at the space-time face points. */
-enum { CWENO_FLUX_RUSANOV = 0, CWENO_FLUX_OSHER = 1 };
+enum { CWENO_FLUX_RUSANOV = 0, CWENO_FLUX_OSHER = 1, CWENO_FLUX_RUSANOV_QF = 2 };
 
 typedef struct cweno_mesh cweno_mesh;
 typedef struct cweno_solver cweno_solver;
@@ -83,7 +83,13 @@ typedef struct {
                           CWENO_FLUX_OSHER: the Osher-type flux of Eq. (osher),
                           |A_n| integrated along the straight path between the
                           two traces by 3-point Gauss-Legendre; Euler only
-                          (EINVAL for MHD) */
+                          (EINVAL for MHD); or CWENO_FLUX_RUSANOV_QF: the
+                          quadrature-free fixed-mesh form described after Eq.
+                          (osher): the nodal predictor fluxes contracted with
+                          precomputed integrals of the nodal basis over face
+                          and time step, Rusanov dissipation with the
+                          signal speed of the two sides' space-time face
+                          averages */
 } cweno_params;
 
 /* Fill *p with the paper's defaults for dimension `dim` and `pde`. */

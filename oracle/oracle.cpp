@@ -29,6 +29,7 @@
 //   one-step finite volume update        Sec. 2.4, Eq. (PDEfinal), Eulerian case
 //   Rusanov flux                         Eq. (rusanov)
 //   Osher-type flux (Euler, switchable)  Eq. (osher), |A| = R|Lambda|R^-1
+//   quadrature-free Rusanov (switchable) fixed-mesh form described after Eq. (osher)
 //   Euler equations / EOS                Eqs. (eulerTerms), (eos)
 //   ideal MHD with GLM cleaning          Eqs. (MHDTerms), (MHDeos)
 //
@@ -455,7 +456,8 @@ enum { PDE_EULER = 0, PDE_MHD = 1 };
 struct Params {
   double eps, r, lam0, lams, gamma, ch, cfl;
   int niter, linear_weights, positivity;
-  int flux = 0;  // 0 Rusanov, Eq. (rusanov); 1 Osher-type, Eq. (osher) (Euler)
+  int flux = 0;  // 0 Rusanov, Eq. (rusanov); 1 Osher-type, Eq. (osher) (Euler);
+                 // 2 quadrature-free Rusanov (fixed-mesh form, after Eq. osher)
 };
 
 const double PI = 3.14159265358979323846;
@@ -1579,9 +1581,9 @@ void* orc_solver_new(void* mesh, int M, int pde, const double* prm, char* err, i
   S->P.linear_weights = (int)prm[8];
   S->P.positivity = (int)prm[9];
   S->P.flux = (int)prm[10];
-  if (S->P.flux != 0 && pde != PDE_EULER) {
+  if (S->P.flux < 0 || S->P.flux > 2 || (S->P.flux == 1 && pde != PDE_EULER)) {
     delete S;
-    set_err(err, errlen, "the Osher-type flux is built for the Euler equations");
+    set_err(err, errlen, "unknown flux, or the Osher-type flux outside the Euler equations");
     return nullptr;
   }
   S->Mc = Mcal(M, m->d);
@@ -1701,6 +1703,78 @@ int orc_predictor_from_w(void* p, int64_t cell, const double* wnodal, double dt,
   return 0;
 }
 
+// Quadrature-free Rusanov flux of one face (the fixed-mesh formulation the
+// paper describes after Eq. osher): with the nodal expansions of the
+// predictor and of its flux (Eq. PDEterm), the face and time integrals
+// reduce to the integrals I_l of each side's nodal basis over the face and
+// [0,1] (normalised by |f|), so the time-averaged normal flux is
+//   1/2 sum_l (I-_l F(q-_l) + I+_l F(q+_l)) . n - 1/2 s (qbar+ - qbar-),
+// qbar = sum_l I_l q_l the space-time face average of a side's predictor and
+// s the larger maximal signal speed along n of the two averages (reading:
+// the paper fixes no constant s for this form).  I_l are computed here by
+// the face and time Gauss rules (exact: the integrand has degree M).  A
+// nodal state that is not admissible contributes its cell average's flux,
+// and an inadmissible face average its cell average's speed (positivity
+// safeguard, as for the quadrature flux).  G: time-averaged flux per |f|.
+void qf_face_flux(const OSolver& S, const double* Q, std::map<long, std::vector<double>>& pred, long i, long j,
+                  const std::vector<std::array<double, 3>>& pts, const std::vector<double>& wts, const double* sj,
+                  const double* nrm, const std::vector<double>& tx, const std::vector<double>& tw, double* G) {
+  const OMesh& m = *S.mesh;
+  const int d = S.d, nu = S.nu, L = S.Lc;
+  std::vector<double> Ii(L, 0.0), Ij(L, 0.0), th(L);
+  for (size_t q = 0; q < pts.size(); ++q) {
+    double xi_i[3], xi_j[3];
+    to_ref(m, i, pts[q].data(), xi_i);
+    if (j >= 0) {
+      double xj[3] = {pts[q][0] - sj[0], pts[q][1] - sj[1], pts[q][2] - sj[2]};
+      to_ref(m, j, xj, xi_j);
+    }
+    for (size_t t = 0; t < tx.size(); ++t) {
+      double xt[4] = {xi_i[0], xi_i[1], xi_i[2], tx[t]};
+      st_basis(S, xt, th.data(), nullptr);
+      for (int l = 0; l < L; ++l) Ii[l] += wts[q] * tw[t] * th[l];
+      if (j >= 0) {
+        double xtj[4] = {xi_j[0], xi_j[1], xi_j[2], tx[t]};
+        st_basis(S, xtj, th.data(), nullptr);
+        for (int l = 0; l < L; ++l) Ij[l] += wts[q] * tw[t] * th[l];
+      }
+    }
+  }
+  // one side: sum_l I_l F_n(q_l) and qbar
+  auto side = [&](long c, const std::vector<double>& I, std::vector<double>& Fn, std::vector<double>& qbar) {
+    const std::vector<double>& qh = pred[c];
+    Fn.assign(nu, 0.0);
+    qbar.assign(nu, 0.0);
+    std::vector<double> f(nu);
+    for (int l = 0; l < L; ++l) {
+      const double* ql = &qh[(size_t)l * nu];
+      const double* qs = ql;
+      if (S.P.positivity && !(ql[0] > 0.0 && pressure(S.pde, d, S.P, ql) > 0.0)) qs = &Q[c * nu];
+      for (int mm = 0; mm < d; ++mm) {
+        flux(S.pde, d, S.P, qs, mm, f.data());
+        for (int v = 0; v < nu; ++v) Fn[v] += I[l] * nrm[mm] * f[v];
+      }
+      for (int v = 0; v < nu; ++v) qbar[v] += I[l] * ql[v];
+    }
+  };
+  std::vector<double> Fi, qi, Fj, qj;
+  side(i, Ii, Fi, qi);
+  if (j >= 0) {
+    side(j, Ij, Fj, qj);
+  } else {  // transmissive boundary: the outer side is the inner one
+    Fj = Fi;
+    qj = qi;
+  }
+  const double* si = qi.data();
+  const double* sjp = qj.data();
+  if (S.P.positivity) {
+    if (!(qi[0] > 0.0 && pressure(S.pde, d, S.P, qi.data()) > 0.0)) si = &Q[i * nu];
+    if (!(qj[0] > 0.0 && pressure(S.pde, d, S.P, qj.data()) > 0.0)) sjp = j >= 0 ? &Q[j * nu] : &Q[i * nu];
+  }
+  double smax = std::max(max_speed_normal(S.pde, d, S.P, si, nrm), max_speed_normal(S.pde, d, S.P, sjp, nrm));
+  for (int v = 0; v < nu; ++v) G[v] = 0.5 * (Fi[v] + Fj[v]) - 0.5 * smax * (qj[v] - qi[v]);
+}
+
 // One ADER-CWENO step, Eq. (PDEfinal) (Eulerian), for cells ids (NULL -> all).
 // Qnew: n x nu.
 int orc_step(void* p, const double* Q, double dt, int64_t n, const int64_t* ids, double* Qnew, char* err,
@@ -1741,6 +1815,11 @@ int orc_step(void* p, const double* Q, double dt, int64_t n, const int64_t* ids,
       face_points(*S, i, k, pts, wts, nrm, area);
       double sj[3] = {0, 0, 0};
       if (j >= 0) min_image_shift(m, i, j, sj);
+      if (S->P.flux == 2) {
+        qf_face_flux(*S, Q, pred, i, j, pts, wts, sj, nrm, tx, tw, fdir.data());
+        for (int v = 0; v < nu; ++v) acc[v] += dt * area * fdir[v];
+        continue;
+      }
       for (size_t q = 0; q < pts.size(); ++q) {
         double xi_i[3], xi_j[3];
         to_ref(m, i, pts[q].data(), xi_i);

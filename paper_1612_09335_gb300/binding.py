@@ -17,7 +17,7 @@ from . import _build
 
 EULER, MHD_GLM = 0, 1
 FP64, FP32_MIXED = 0, 1
-FLUX_RUSANOV, FLUX_OSHER = 0, 1
+FLUX_RUSANOV, FLUX_OSHER, FLUX_RUSANOV_QF = 0, 1, 2
 OK, EINVAL, EDEGENERATE, ENOMEM, EBUSY, ENAN, ETIMEDOUT, ECUDA, ENOTFOUND = 0, -1, -2, -3, -4, -5, -6, -7, -8
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_ERROR = 0, 1, 2, 3
 

@@ -240,7 +240,8 @@ int cweno_setup(const cweno_mesh* mesh, int order, int pde, int precision, const
   if (prm.r != 4.0) return fail(CWENO_EINVAL, "only r = 4 is built (Eq. weights2)");
   if (!(prm.eps > 0) || !(prm.lambda0 > 0) || !(prm.lambda_s > 0) || !(prm.gamma > 1.0) || !(prm.cfl > 0))
     return fail(CWENO_EINVAL, "bad scheme parameters");
-  if (prm.flux != CWENO_FLUX_RUSANOV && prm.flux != CWENO_FLUX_OSHER) return fail(CWENO_EINVAL, "unknown flux");
+  if (prm.flux != CWENO_FLUX_RUSANOV && prm.flux != CWENO_FLUX_OSHER && prm.flux != CWENO_FLUX_RUSANOV_QF)
+    return fail(CWENO_EINVAL, "unknown flux");
   if (prm.flux == CWENO_FLUX_OSHER && pde != CWENO_EULER)
     return fail(CWENO_EINVAL, "the Osher-type flux is built for the Euler equations");
   const int M = order - 1;

@@ -68,6 +68,10 @@ struct Cfg {
   // shared-memory banks
   static constexpr int CODE_STRIDE = code_stride(NQT * NQS * LP, VW, (int)sizeof(T_));
   static constexpr int TABN = NCODE * CODE_STRIDE;
+  // quadrature-free flux: per code, the L integrals of the nodal basis over
+  // the face and [0,1] (rows of LP), after the quadrature weights
+  static constexpr int QF_OFF = (TABN + NQS + NQT + VW - 1) / VW * VW;
+  static constexpr int TAB_TOTAL = QF_OFF + NCODE * LP;
   // face kernel: two threads per face, each evaluating one side at every
   // space-time point, where those traces fit the register budget (FP32,
   // NQT NQS NV <= 64: 2D Euler); otherwise one thread per face, one time
@@ -890,7 +894,7 @@ __device__ __forceinline__ void rusanov_point(const KArgs<C>& a, typename C::T* 
     for (int v = 0; v < NV; ++v) facc[m][v] += wgt * (fl[v] + fr[v]);
   }
   if constexpr (C::PDE == 0) {
-    if (a.flux) {  // Osher-type, Eq. (osher)
+    if (a.flux == 1) {  // Osher-type, Eq. (osher)
       T dis[NV];
       PH::osher_dissipation(ul, ur, n, a.gamma, dis);
 #pragma unroll
@@ -1101,6 +1105,130 @@ __global__ void __launch_bounds__(128, C::FLUX_MINB) k_flux_pair(KArgs<C> a, int
   }
 }
 
+// Quadrature-free Rusanov flux (the fixed-mesh form the paper describes
+// after Eq. osher), one thread per face, persistent grid.  With the nodal
+// expansions of the predictor and its flux (Eq. PDEterm) the face and time
+// integrals reduce to the precomputed integrals I_l of each side's nodal
+// basis (per code), so the time-averaged normal flux per |f| is
+//   1/2 sum_l (I-_l F(q-_l) + I+_l F(q+_l)) . n - 1/2 s (qbar+ - qbar-),
+// qbar = Qbar + sum_l I_l q_hat_l the space-time face average of a side's
+// predictor, s the larger maximal signal speed along n of the two averages.
+// Deviation form: F(Qbar) + sum_l I_l (F(Qbar + q_hat_l) - F(Qbar)) (the I_l
+// sum to one), so a constant state gives identical sums on every face.  A
+// nodal state that is not admissible contributes F(Qbar); an inadmissible
+// face average takes its cell average's speed.
+template <class C>
+__device__ __forceinline__ void qf_side(const KArgs<C>& a, const typename C::T* __restrict__ qhat, int64_t c,
+                                        int64_t N, const typename C::T* Ic, const typename C::T* qb,
+                                        typename C::T (&facc)[C::D][C::NV], typename C::T (&dev)[C::NV]) {
+  using T = typename C::T;
+  using V = typename Vec16<T>::V;
+  constexpr int D = C::D, NV = C::NV, L = C::L, LP = C::LP, VW = C::VW;
+  using PH = Phys<D, C::PDE, T>;
+  T Fb[D][NV];
+  {
+    typename PH::Prim pb = PH::prim(qb, a.gamma);
+#pragma unroll
+    for (int m = 0; m < D; ++m) {
+      T em[D];
+#pragma unroll
+      for (int e = 0; e < D; ++e) em[e] = e == m ? T(1) : T(0);
+      flux_normal<D, C::PDE, T>(qb, pb, em, Fb[m], a.ch);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) facc[m][v] += Fb[m][v];
+    }
+  }
+#pragma unroll 1
+  for (int l4 = 0; l4 < LP; l4 += VW) {
+    T ql[VW][NV];
+    load_chunk<C>(qhat, c, N, l4, ql);
+    const V iv = *reinterpret_cast<const V*>(Ic + l4);
+#pragma unroll
+    for (int j = 0; j < VW; ++j) {
+      if (l4 + j >= L) continue;
+      const T I = Vec16<T>::get(iv, j);
+      T q[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        q[v] = qb[v] + ql[j][v];
+        dev[v] += I * ql[j][v];
+      }
+      typename PH::Prim pq = PH::prim(q, a.gamma);
+      if (a.pos && !(q[0] > T(0) && pq.p > T(0))) continue;
+#pragma unroll
+      for (int m = 0; m < D; ++m) {
+        T em[D];
+#pragma unroll
+        for (int e = 0; e < D; ++e) em[e] = e == m ? T(1) : T(0);
+        T fq[NV];
+        flux_normal<D, C::PDE, T>(q, pq, em, fq, a.ch);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) facc[m][v] += I * (fq[v] - Fb[m][v]);
+      }
+    }
+  }
+}
+
+template <class C>
+__global__ void __launch_bounds__(128) k_flux_qf(KArgs<C> a) {
+  using T = typename C::T;
+  constexpr int D = C::D, NV = C::NV, LP = C::LP;
+  using PH = Phys<D, C::PDE, T>;
+  __shared__ __align__(16) T sI[C::NCODE * LP];
+  for (int k = threadIdx.x; k < C::NCODE * LP; k += blockDim.x) sI[k] = a.ftab[C::QF_OFF + k];
+  __syncthreads();
+  const double dtd = dt_of(a.dt_fixed, a.cfl, a.dtmin, a.cur);
+  const int64_t N = a.N, F = a.F;
+  for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < F; f += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t Lc = a.fL[f];
+    const int64_t Rc = a.fR[f];
+    T n[D];
+#pragma unroll
+    for (int e = 0; e < D; ++e) n[e] = a.fn[e * F + f];
+    T qbL[NV], qbR[NV], devL[NV], devR[NV];
+    T facc[D][NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      devL[v] = T(0);
+      devR[v] = T(0);
+#pragma unroll
+      for (int m = 0; m < D; ++m) facc[m][v] = T(0);
+    }
+    cell_average<C>(a, Lc, qbL);
+    qf_side<C>(a, a.qhat, Lc, N, sI + (int)a.codeL[f] * LP, qbL, facc, devL);
+    if (Rc >= 0) {
+      cell_average<C>(a, Rc, qbR);
+      qf_side<C>(a, a.qhat, Rc, N, sI + (int)a.codeR[f] * LP, qbR, facc, devR);
+    } else {  // transmissive: the outer side repeats the inner one
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        qbR[v] = qbL[v];
+        devR[v] = devL[v];
+#pragma unroll
+        for (int m = 0; m < D; ++m) facc[m][v] *= T(2);
+      }
+    }
+    T uL[NV], uR[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      uL[v] = qbL[v] + devL[v];
+      uR[v] = qbR[v] + devR[v];
+    }
+    typename PH::Prim pl = PH::prim(uL, a.gamma);
+    typename PH::Prim pr = PH::prim(uR, a.gamma);
+    if (a.pos) {
+      if (!(uL[0] > T(0) && pl.p > T(0))) pl = PH::prim(qbL, a.gamma);
+      if (!(uR[0] > T(0) && pr.p > T(0))) pr = PH::prim(qbR, a.gamma);
+    }
+    const T sl = PH::smax(pl, n, a.gamma, a.ch), sr = PH::smax(pr, n, a.gamma, a.ch);
+    const T s = sl > sr ? sl : sr;
+    T dacc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) dacc[v] = s * ((qbR[v] - qbL[v]) + (devR[v] - devL[v]));
+    store_face_integral<C>(a, f, dtd, facc, dacc);
+  }
+}
+
 // Block minimum of non-negative ratios folded into *target, which holds the
 // bits of a positive double.  Non-negative IEEE values order like their bit
 // patterns, so the reduction runs on the integer bits (no FP64 pipe work in
@@ -1281,7 +1409,7 @@ class OpsImpl final : public Ops {
     for (int e = 0; e < C::D; ++e)
       for (int k = 0; k < C::L1; ++k)
         for (int l = 0; l < C::L; ++l) tab_.P[e][k][l] = (T)re.P[((size_t)e * C::L1 + k) * C::L + l];
-    ftab_.assign(C::TABN + C::NQS + C::NQT, T(0));
+    ftab_.assign(C::TAB_TOTAL, T(0));
     for (int code = 0; code < C::NCODE; ++code)
       for (int row = 0; row < C::NQT * C::NQS; ++row)
         for (int l = 0; l < C::L; ++l)
@@ -1289,8 +1417,12 @@ class OpsImpl final : public Ops {
               (T)re.ftab[((size_t)code * C::NQT * C::NQS + row) * C::L + l];
     for (int q = 0; q < C::NQS; ++q) ftab_[C::TABN + q] = (T)re.wq[q];
     for (int t = 0; t < C::NQT; ++t) ftab_[C::TABN + C::NQS + t] = (T)re.wt[t];
+    for (int code = 0; code < C::NCODE; ++code)
+      for (int l = 0; l < C::L; ++l) ftab_[C::QF_OFF + code * C::LP + l] = (T)re.fint[(size_t)code * C::L + l];
   }
   size_t table_bytes() const override { return ftab_.size() * sizeof(T); }
+  // shared-memory bytes of the quadrature flux kernels (tables and weights)
+  static size_t quad_table_bytes() { return (size_t)(C::TABN + C::NQS + C::NQT) * sizeof(T); }
   void pack_tables(void* host) const override { std::memcpy(host, ftab_.data(), table_bytes()); }
   size_t elem_size() const override { return sizeof(T); }
 
@@ -1372,7 +1504,7 @@ class OpsImpl final : public Ops {
     e = cudaFuncSetAttribute(k_rec_pred<C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              C::PRED_SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    const size_t smem = table_bytes();
+    const size_t smem = quad_table_bytes();
     use_smem_ = smem <= 100 * 1024 ? 1 : 0;
     if (use_smem_) {
       e = cudaFuncSetAttribute(flux_kernel(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1385,12 +1517,21 @@ class OpsImpl final : public Ops {
     e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     max_blocks_ = (int64_t)std::max(1, nb) * nsm;
+    int nbq = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nbq, k_flux_qf<C>, 128, 0);
+    if (e != cudaSuccess) return e;
+    max_blocks_qf_ = (int64_t)std::max(1, nbq) * nsm;
     return cudaSuccess;
   }
   cudaError_t flux(const DevState& s, const PhysParams& ph, DtArgs dt, cudaStream_t st) override {
     KArgs<C> a = args(s, ph, dt);
     if (dt.cur < 0) a.cur = 0;
-    const size_t smem = use_smem_ ? table_bytes() : 0;
+    if (ph.flux == 2) {  // quadrature-free Rusanov
+      unsigned nb = (unsigned)std::min<int64_t>(nblk(s.F, 128), max_blocks_qf_);
+      k_flux_qf<C><<<nb, 128, 0, st>>>(a);
+      return cudaGetLastError();
+    }
+    const size_t smem = use_smem_ ? quad_table_bytes() : 0;
     unsigned nb = (unsigned)std::min<int64_t>(nblk(s.F * (C::PAIR ? 2 : 1), 128), max_blocks_);
     flux_kernel()<<<nb, 128, smem, st>>>(a, use_smem_);
     return cudaGetLastError();
@@ -1426,6 +1567,7 @@ class OpsImpl final : public Ops {
   std::vector<T> ftab_;
   int use_smem_ = 0;
   int64_t max_blocks_ = 152;
+  int64_t max_blocks_qf_ = 152;
 };
 
 }  // namespace cw

@@ -480,6 +480,7 @@ void RefElem::init(int d_, int M_) {
     nqs = (int)chi.size();
     ncode = (d == 2) ? 6 : 24;
     ftab.assign((size_t)ncode * nqt * nqs * L, 0.0);
+    std::vector<LD> fi((size_t)ncode * L, 0.0L);
     for (int code = 0; code < ncode; ++code) {
       int lf = (d == 2) ? code / 2 : code / 6;
       int asc[3], n = 0;
@@ -507,10 +508,15 @@ void RefElem::init(int d_, int M_) {
             x[a] = (LD)xa;
           }
           x[d] = (LD)tq[t];
-          for (int l = 0; l < L; ++l)
-            ftab[(((size_t)code * nqt + t) * nqs + q) * L + l] = (double)theta(l, x);
+          for (int l = 0; l < L; ++l) {
+            const LD th = theta(l, x);
+            ftab[(((size_t)code * nqt + t) * nqs + q) * L + l] = (double)th;
+            fi[(size_t)code * L + l] += (LD)wt[t] * (LD)wq[q] * th;
+          }
         }
     }
+    fint.assign((size_t)ncode * L, 0.0);
+    for (size_t k = 0; k < fi.size(); ++k) fint[k] = (double)fi[k];
   }
 }
 

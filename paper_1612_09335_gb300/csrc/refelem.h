@@ -67,6 +67,10 @@ struct RefElem {
   std::vector<double> P;   // d x L1 x L
   // face quadrature: code -> table[t][q][l]; weights normalised to 1
   std::vector<double> ftab;  // ncode x nqt x nqs x L
+  // integrals of the nodal basis over the face (per |f|) and [0,1]:
+  // fint[code][l] = sum_t sum_q wt[t] wq[q] theta_l(point), the tables of
+  // the quadrature-free flux
+  std::vector<double> fint;  // ncode x L
   std::vector<double> wq, wt;
   std::vector<double> tq;    // time points
   void init(int d, int M);

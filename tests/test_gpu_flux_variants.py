@@ -1,13 +1,15 @@
-"""Osher-type flux of Eq. (osher) on the GPU against the FP64 oracle: the
-same one-step parity bounds as the Rusanov path (FP64: 1e-12, or 8x the
-oracle's own response to one-ulp input changes on discontinuous data;
-FP32-mixed: the stated bounds), plus free-stream and conservation
-invariants, and the flux's defining advantage: a stationary contact stays
-sharp (no dissipation on the entropy wave), where Rusanov smears it."""
+"""The other face fluxes on the GPU against the FP64 oracle: the Osher-type
+flux of Eq. (osher) (Euler) and the quadrature-free Rusanov flux of the
+fixed-mesh formulation (Euler and MHD-GLM).  Same one-step parity bounds as
+the quadrature Rusanov path (FP64: 1e-12, or 8x the oracle's own response to
+one-ulp input changes on discontinuous data; FP32-mixed: the stated
+bounds), free-stream and conservation invariants, and the Osher flux's
+defining advantage: a stationary contact stays sharp (no dissipation on the
+entropy wave), where Rusanov smears it."""
 import numpy as np
 import pytest
 
-from test_gpu_parity import EULER, case_inputs, make, relerr, tolerance
+from test_gpu_parity import EULER, MHD, case_inputs, make, relerr, tolerance
 
 pytestmark = pytest.mark.gpu
 
@@ -22,17 +24,21 @@ def cw():
     return binding
 
 
-CASES = [("vortex2d", 3), ("vortex2d", 4), ("vortex2d", 5), ("explosion2d", 4), ("explosion2d", 5),
-         ("wave3d", 2), ("wave3d", 3), ("explosion3d", 3)]
+OSHER, QF = 1, 2
+CASES = [(OSHER, "vortex2d", 3), (OSHER, "vortex2d", 4), (OSHER, "vortex2d", 5), (OSHER, "explosion2d", 4),
+         (OSHER, "explosion2d", 5), (OSHER, "wave3d", 2), (OSHER, "wave3d", 3), (OSHER, "explosion3d", 3),
+         (QF, "vortex2d", 2), (QF, "vortex2d", 3), (QF, "vortex2d", 4), (QF, "vortex2d", 5),
+         (QF, "explosion2d", 4), (QF, "explosion2d", 5), (QF, "wave3d", 2), (QF, "wave3d", 3),
+         (QF, "explosion3d", 3), (QF, "orszag", 3), (QF, "orszag", 4)]
 
 
-@pytest.mark.parametrize("name,order", CASES)
-def test_one_step_osher_fp64_matches_oracle(cw, orc, wl, name, order):
+@pytest.mark.parametrize("flux,name,order", CASES)
+def test_one_step_fp64_matches_oracle(cw, orc, wl, flux, name, order):
     (mesh, Q), pde = case_inputs(wl, name)
-    prm = orc.default_params(mesh.dim, pde, order=order, flux=1)
+    prm = orc.default_params(mesh.dim, pde, order=order, flux=flux)
     o = orc.Oracle(mesh, order, pde, params=prm)
     dt = o.stable_dt(Q)
-    s = make(cw, mesh, order, pde, cw.FP64, flux=cw.FLUX_OSHER)
+    s = make(cw, mesh, order, pde, cw.FP64, flux=flux)
     s.set_state(Q)
     s.step(dt)
     s.sync()
@@ -41,25 +47,27 @@ def test_one_step_osher_fp64_matches_oracle(cw, orc, wl, name, order):
     assert relerr(got, o.step(Q, dt)) < tol
 
 
-@pytest.mark.parametrize("name,order,tol", [("vortex2d", 4, 2e-6), ("vortex2d", 5, 2e-6), ("explosion2d", 4, 1e-4),
-                                            ("wave3d", 3, 2e-6)])
-def test_one_step_osher_fp32_mixed_bounds(cw, orc, wl, name, order, tol):
+@pytest.mark.parametrize("flux,name,order,tol", [(OSHER, "vortex2d", 4, 2e-6), (OSHER, "vortex2d", 5, 2e-6),
+                                                 (OSHER, "explosion2d", 4, 1e-4), (OSHER, "wave3d", 3, 2e-6),
+                                                 (QF, "vortex2d", 4, 2e-6), (QF, "explosion2d", 4, 1e-4),
+                                                 (QF, "wave3d", 3, 2e-6), (QF, "orszag", 4, 3e-5)])
+def test_one_step_fp32_mixed_bounds(cw, orc, wl, flux, name, order, tol):
     (mesh, Q), pde = case_inputs(wl, name)
-    o = orc.Oracle(mesh, order, pde, params=orc.default_params(mesh.dim, pde, order=order, flux=1))
+    o = orc.Oracle(mesh, order, pde, params=orc.default_params(mesh.dim, pde, order=order, flux=flux))
     dt = o.stable_dt(Q)
-    s = make(cw, mesh, order, pde, cw.FP32_MIXED, flux=cw.FLUX_OSHER)
+    s = make(cw, mesh, order, pde, cw.FP32_MIXED, flux=flux)
     s.set_state(Q)
     s.step(dt)
     s.sync()
     assert relerr(s.get_state(), o.step(Q, dt), floor=1e-2) < tol
 
 
-@pytest.mark.parametrize("dim,order", [(2, 4), (3, 3)])
-def test_osher_free_stream_and_conservation(cw, wl, dim, order):
+@pytest.mark.parametrize("flux,dim,order", [(OSHER, 2, 4), (OSHER, 3, 3), (QF, 2, 4), (QF, 3, 3)])
+def test_free_stream_and_conservation(cw, wl, flux, dim, order):
     mesh = wl.tri_mesh(12, jitter=0.2, seed=3) if dim == 2 else wl.tet_mesh(5, jitter=0.15, seed=3)
     q = np.array([1.3, 0.4, -0.2, 0.1][:dim + 1] + [2.5])
     for prec in (cw.FP64, cw.FP32_MIXED):
-        s = make(cw, mesh, order, EULER, prec, flux=cw.FLUX_OSHER)
+        s = make(cw, mesh, order, EULER, prec, flux=flux)
         s.set_state(np.tile(q, (mesh.nc, 1)))
         s.run(3)
         s.sync()
@@ -68,7 +76,7 @@ def test_osher_free_stream_and_conservation(cw, wl, dim, order):
     X = m2.cell_vertices()
     vol = np.abs(np.linalg.det(X[:, 1:] - X[:, :1])) / (2 if dim == 2 else 6)
     for prec in (cw.FP64, cw.FP32_MIXED):
-        s = make(cw, m2, order, EULER, prec, flux=cw.FLUX_OSHER)
+        s = make(cw, m2, order, EULER, prec, flux=flux)
         s.set_state(Q)
         s.run(10)
         s.sync()

@@ -617,8 +617,9 @@ def test_face_quadrature_and_closure(orc, wl):
             assert np.abs(tot).max() < 1e-15
 
 
-@pytest.mark.parametrize("order,linear", [(2, False), (2, True), (3, True), (4, True), (5, True)])
-def test_convergence_density_wave_2d(orc, wl, order, linear):
+@pytest.mark.parametrize("order,linear,flux", [(2, False, 0), (2, True, 0), (3, True, 0), (4, True, 0), (5, True, 0),
+                                              (3, True, 1), (3, True, 2), (4, True, 2)])
+def test_convergence_density_wave_2d(orc, wl, order, linear, flux):
     """p10: design order M+1 on the smooth density wave (exact advection).
 
     With the paper's nonlinear weights (eps = 1e-14, r = 4) the weight of P_0
@@ -626,13 +627,14 @@ def test_convergence_density_wave_2d(orc, wl, order, linear):
     sectorial gradients nearly vanish; at these resolutions that costs the
     third-order scheme about one order.  The linear scheme (omega = lambda)
     carries the whole reconstruction/predictor/flux/update chain and must show
-    the design order; the nonlinear weights are pinned at order 2."""
+    the design order; the nonlinear weights are pinned at order 2.  flux 1:
+    the Osher-type flux, 2: the quadrature-free Rusanov flux."""
     errs, hs = [], []
     tf = 0.04
     # second order is still pre-asymptotic at 12 -> 24 (1.57, then 1.74, 1.90)
     for n in ((24, 48) if order == 2 else (12, 24)):
         mesh, Q = wl.density_wave_2d(n)
-        prm = orc.default_params(2, EULER, order=order, linear_weights=linear)
+        prm = orc.default_params(2, EULER, order=order, linear_weights=linear, flux=flux)
         o = orc.Oracle(mesh, order, params=prm)
         vol = o.mesh.geometry()["vol"]
         dt0 = o.stable_dt(Q)
@@ -767,3 +769,29 @@ def test_osher_flux_resolves_stationary_contact(orc):
         assert np.abs(g - exact).max() < 1e-14
         r = orc.numerical_flux(EULER, dim, qm, qp, n, orc.default_params(dim, EULER))
         assert abs(r[0]) > 0.1
+
+
+# ------------------------------------------------ quadrature-free flux
+@pytest.mark.parametrize("dim,order,pde", [(2, 3, EULER), (2, 4, EULER), (3, 3, EULER), (2, 3, MHD)])
+def test_quadrature_free_flux_free_stream_and_conservation(orc, wl, dim, order, pde):
+    """The quadrature-free flux keeps a constant state (its face integrals
+    I_l of the nodal basis sum to one) and conserves the totals on a
+    periodic mesh (each face's flux is shared by its two cells)."""
+    mesh = wl.tri_mesh(6, jitter=0.2, seed=4) if dim == 2 else wl.tet_mesh(3, jitter=0.12, seed=4)
+    prm = orc.default_params(dim, pde, order=order, flux=2)
+    o = orc.Oracle(mesh, order, pde, params=prm)
+    nu = 9 if pde == MHD else dim + 2
+    q = np.array([1.3, 0.4, -0.2, 0.1][:dim + 1] + [2.5]) if pde == EULER else \
+        np.array([1.2, 0.3, -0.2, 0.1, 3.0, 0.5, -0.7, 0.2, 0.0])
+    Qc = np.tile(q, (mesh.nc, 1))
+    dt = o.stable_dt(Qc)
+    assert np.abs(o.step(Qc, dt) - Qc).max() < 1e-14 * np.abs(q).max()
+    rng = np.random.default_rng(8)
+    Q = Qc * (1 + 0.05 * rng.uniform(-1, 1, size=Qc.shape))
+    Q1 = o.step(Q, o.stable_dt(Q))
+    vol = o.mesh.geometry()["vol"]
+    tot0, tot1 = vol @ Q, vol @ Q1
+    scale = vol @ np.abs(Q)
+    scale = np.maximum(scale, 1e-2 * scale.max())  # psi starts at zero: measured at the state scale
+    assert np.all(np.abs(tot1 - tot0) < 1e-13 * scale), (tot1 - tot0)
+    assert nu == Q.shape[1]
