@@ -682,12 +682,14 @@ __global__ void __launch_bounds__(128, C::REC_MINB) k_rec_pred(KArgs<C> a, const
     extern __shared__ __align__(16) unsigned char rp_smem[];
     T* sb = reinterpret_cast<T*>(rp_smem) + threadIdx.x;  // fixed part, [(k NV + v) B]
     T* sq = sb + L1 * NV * B;                              // current iterate
+    // dt is folded into the inverse Jacobian: G_e = F . (dt d xi_e / d x) is
+    // linear in the direction, so the scaled directions give dt G_e directly
     const T dt = (T)dt_of(a.dt_fixed, a.cfl, a.dtmin, a.cur);
     T J[D][D];
 #pragma unroll
     for (int e = 0; e < D; ++e)
 #pragma unroll
-      for (int m = 0; m < D; ++m) J[e][m] = __ldg(a.Jinv + (e * D + m) * N + i);
+      for (int m = 0; m < D; ++m) J[e][m] = dt * __ldg(a.Jinv + (e * D + m) * N + i);
     // Deviations from the cell average: the Picard update subtracts the flux
     // of the cell average, G_e(q) - G_e(Qbar), which P_e annihilates exactly
     // (it differentiates constants to zero); q_hat is stored as q - Qbar.  The
@@ -702,7 +704,7 @@ __global__ void __launch_bounds__(128, C::REC_MINB) k_rec_pred(KArgs<C> a, const
 #pragma unroll
       for (int e = 0; e < D; ++e) flux_normal<D, C::PDE, T>(qb, pr, J[e], Gref[e], a.ch);
     }
-    // flux part of the fixed term, -dt sum_e P_e[:, tau=0 nodes] (G_e(q0) - G_e(Qbar))
+    // flux part of the fixed term, -sum_e P_e[:, tau=0 nodes] dt (G_e(q0) - G_e(Qbar))
     T S[L1][NV];
 #pragma unroll
     for (int k = 0; k < L1; ++k)
@@ -726,7 +728,7 @@ __global__ void __launch_bounds__(128, C::REC_MINB) k_rec_pred(KArgs<C> a, const
       for (int e = 0; e < D; ++e) {
         flux_normal<D, C::PDE, T>(q0, pr, J[e], Ge[e], a.ch);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) Ge[e][v] = dt * (Ge[e][v] - Gref[e][v]);
+        for (int v = 0; v < NV; ++v) Ge[e][v] -= Gref[e][v];
       }
 #pragma unroll
       for (int k = 0; k < L1; ++k)
@@ -768,7 +770,7 @@ __global__ void __launch_bounds__(128, C::REC_MINB) k_rec_pred(KArgs<C> a, const
         for (int e = 0; e < D; ++e) {
           flux_normal<D, C::PDE, T>(ql, pr, J[e], Ge[e], a.ch);
 #pragma unroll
-          for (int v = 0; v < NV; ++v) Ge[e][v] = dt * (Ge[e][v] - Gref[e][v]);
+          for (int v = 0; v < NV; ++v) Ge[e][v] -= Gref[e][v];
         }
 #pragma unroll
         for (int k = 0; k < L1; ++k)
@@ -860,7 +862,7 @@ __device__ __forceinline__ void face_traces(const typename C::T* __restrict__ qh
 // is not an admissible state (density or pressure <= 0) is replaced by its
 // cell average at this point (positivity safeguard, with the scaling of the
 // reconstruction).
-template <class C>
+template <class C, bool OSHER>
 __device__ __forceinline__ void rusanov_point(const KArgs<C>& a, typename C::T* ul, typename C::T* ur,
                                               const typename C::T* qbL, const typename C::T* qbR,
                                               const typename C::T* n, typename C::T wgt,
@@ -893,14 +895,12 @@ __device__ __forceinline__ void rusanov_point(const KArgs<C>& a, typename C::T* 
 #pragma unroll
     for (int v = 0; v < NV; ++v) facc[m][v] += wgt * (fl[v] + fr[v]);
   }
-  if constexpr (C::PDE == 0) {
-    if (a.flux == 1) {  // Osher-type, Eq. (osher)
-      T dis[NV];
-      PH::osher_dissipation(ul, ur, n, a.gamma, dis);
+  if constexpr (OSHER && C::PDE == 0) {  // Osher-type, Eq. (osher)
+    T dis[NV];
+    PH::osher_dissipation(ul, ur, n, a.gamma, dis);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) dacc[v] += wgt * dis[v];
-      return;
-    }
+    for (int v = 0; v < NV; ++v) dacc[v] += wgt * dis[v];
+    return;
   }
   const T sl = PH::smax(pl, n, a.gamma, a.ch), sr = PH::smax(pr, n, a.gamma, a.ch);
   const T s = sl > sr ? sl : sr;
@@ -953,7 +953,7 @@ __device__ __forceinline__ void cell_average(const KArgs<C>& a, int64_t c, typen
 
 // One thread per face, persistent grid: both sides' traces one time point
 // at a time (NQS space points), Rusanov flux, space-time quadrature.
-template <class C>
+template <class C, bool OSHER>
 __global__ void __launch_bounds__(128, C::FLUX_MINB) k_flux(KArgs<C> a, int use_smem) {
   using T = typename C::T;
   constexpr int D = C::D, NV = C::NV, NQS = C::NQS, NQT = C::NQT;
@@ -1014,7 +1014,7 @@ __global__ void __launch_bounds__(128, C::FLUX_MINB) k_flux(KArgs<C> a, int use_
           ul[v] = qbL[v] + trL[j][v];
           ur[v] = qbR[v] + trR[j][v];
         }
-        rusanov_point<C>(a, ul, ur, qbL, qbR, n, wq[j] * wt[t], facc, dacc);
+        rusanov_point<C, OSHER>(a, ul, ur, qbL, qbR, n, wq[j] * wt[t], facc, dacc);
       }
     }
     store_face_integral<C>(a, f, dtd, facc, dacc);
@@ -1027,7 +1027,7 @@ __global__ void __launch_bounds__(128, C::FLUX_MINB) k_flux(KArgs<C> a, int use_
 // each thread takes every other point for the Rusanov flux, and the two
 // partial sums are added.  A boundary face evaluates its inner cell on both
 // threads (transmissive: the outer trace equals the inner one).
-template <class C>
+template <class C, bool OSHER>
 __global__ void __launch_bounds__(128, C::FLUX_MINB) k_flux_pair(KArgs<C> a, int use_smem) {
   using T = typename C::T;
   constexpr int D = C::D, NV = C::NV, NQS = C::NQS, NP = C::NQT * C::NQS;
@@ -1092,7 +1092,7 @@ __global__ void __launch_bounds__(128, C::FLUX_MINB) k_flux_pair(KArgs<C> a, int
           ul[v] = qbL[v] + (side == 0 ? mine[v] : other[v]);
           ur[v] = qbR[v] + (side == 0 ? other[v] : mine[v]);
         }
-        rusanov_point<C>(a, ul, ur, qbL, qbR, n, wq[p % NQS] * wt[p / NQS], facc, dacc);
+        rusanov_point<C, OSHER>(a, ul, ur, qbL, qbR, n, wq[p % NQS] * wt[p / NQS], facc, dacc);
       }
     }
 #pragma unroll
@@ -1101,7 +1101,35 @@ __global__ void __launch_bounds__(128, C::FLUX_MINB) k_flux_pair(KArgs<C> a, int
 #pragma unroll
       for (int m = 0; m < D; ++m) facc[m][v] += __shfl_xor_sync(0xffffffffu, facc[m][v], 1);
     }
-    if (valid && side == 0) store_face_integral<C>(a, f, dtd, facc, dacc);
+    // FP64 contraction split over the pair: thread 0 takes the first H
+    // variables, thread 1 the rest, so every FP64 instruction runs on all lanes
+    if (valid) {
+      constexpr int H = (NV + 1) / 2;
+      double fa[D];
+#pragma unroll
+      for (int m = 0; m < D; ++m) fa[m] = a.fa[m * F + f];
+      const double area = a.farea[f];
+#pragma unroll
+      for (int j = 0; j < H; ++j) {
+        const int v = side == 0 ? j : H + j;
+        if (v >= NV) break;
+        T dv = dacc[0];
+        T fv[D];
+#pragma unroll
+        for (int m = 0; m < D; ++m) fv[m] = facc[m][0];
+#pragma unroll
+        for (int u = 1; u < NV; ++u)
+          if (u == v) {
+            dv = dacc[u];
+#pragma unroll
+            for (int m = 0; m < D; ++m) fv[m] = facc[m][u];
+          }
+        double g = -area * (double)dv;
+#pragma unroll
+        for (int m = 0; m < D; ++m) g += fa[m] * (double)fv[m];
+        a.G[v * F + f] = 0.5 * dtd * g;
+      }
+    }
   }
 }
 
@@ -1493,9 +1521,16 @@ class OpsImpl final : public Ops {
     return cudaGetLastError();
   }
   using FluxKernel = void (*)(KArgs<C>, int);
-  static FluxKernel flux_kernel() {
-    if constexpr (C::PAIR) return k_flux_pair<C>;
-    else return k_flux<C>;
+  // quadrature flux kernel: Rusanov, or Osher-type (Euler only)
+  static FluxKernel flux_kernel(bool osher = false) {
+    if constexpr (C::PDE == 0) {
+      if (osher) {
+        if constexpr (C::PAIR) return k_flux_pair<C, true>;
+        else return k_flux<C, true>;
+      }
+    }
+    if constexpr (C::PAIR) return k_flux_pair<C, false>;
+    else return k_flux<C, false>;
   }
   cudaError_t prepare() override {
     int dev = 0;
@@ -1507,8 +1542,10 @@ class OpsImpl final : public Ops {
     const size_t smem = quad_table_bytes();
     use_smem_ = smem <= 100 * 1024 ? 1 : 0;
     if (use_smem_) {
-      e = cudaFuncSetAttribute(flux_kernel(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
+      for (int o = 0; o < (C::PDE == 0 ? 2 : 1); ++o) {
+        e = cudaFuncSetAttribute(flux_kernel(o == 1), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+      }
     }
     int nb = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, flux_kernel(), 128, use_smem_ ? smem : 0);
@@ -1533,7 +1570,7 @@ class OpsImpl final : public Ops {
     }
     const size_t smem = use_smem_ ? quad_table_bytes() : 0;
     unsigned nb = (unsigned)std::min<int64_t>(nblk(s.F * (C::PAIR ? 2 : 1), 128), max_blocks_);
-    flux_kernel()<<<nb, 128, smem, st>>>(a, use_smem_);
+    flux_kernel(ph.flux == 1)<<<nb, 128, smem, st>>>(a, use_smem_);
     return cudaGetLastError();
   }
   cudaError_t update(const DevState& s, const PhysParams& ph, DtArgs dt, cudaStream_t st) override {
