@@ -569,8 +569,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--no-other", action="store_true", help="skip the 3D and MHD workloads")
-    ap.add_argument("--serve-requests", type=int, default=128,
+    ap.add_argument("--no-other", action="store_true", help="skip the 3D, MHD and fifth-order workloads and the flux variants")
+    ap.add_argument("--serve-requests", type=int, default=512,
                     help="requests in the serving mix (the full mix has 512)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -234,6 +234,18 @@ static double dubiner_raw(int d, const std::array<int, 3>& id, const double* xi)
 void Dubiner::init(int d_, int M_) {
   d = d_;
   M = M_;
+  // recurrence coefficients for alpha = 0 .. 2M + 2 (the Jacobi weights the
+  // collapsed directions need), the same three-term recurrence as jacobi_h
+  rec.assign((size_t)(2 * M + 3) * (M + 1), {0.0, 0.0, 0.0});
+  for (int al = 0; al <= 2 * M + 2; ++al)
+    for (int k = 2; k <= M; ++k) {
+      const double alpha = al, kk = k, c = 2.0 * kk + alpha;
+      const double a1 = 2.0 * kk * (kk + alpha) * (c - 2.0);
+      const double a2 = (c - 1.0) * (alpha * alpha);
+      const double a3 = (c - 2.0) * (c - 1.0) * c;
+      const double a4 = 2.0 * (kk + alpha - 1.0) * (kk - 1.0) * c;
+      rec[(size_t)al * (M + 1) + k] = {a2 / a1, a3 / a1, a4 / a1};
+    }
   pqr.clear();
   for (int k = 0; k <= M; ++k) {
     if (d == 2) {
@@ -286,8 +298,39 @@ void Dubiner::init(int d_, int M_) {
   }
 }
 
+// p[k] = s^k P_k^(alpha,0)(u/s), k = 0..nmax, by the precomputed recurrence
+void Dubiner::jacobi_seq(int alpha, int nmax, double u, double s, double* p) const {
+  p[0] = 1.0;
+  if (nmax < 1) return;
+  p[1] = 0.5 * ((alpha + 2.0) * u + alpha * s);
+  for (int k = 2; k <= nmax; ++k) {
+    const std::array<double, 3>& r = rec[(size_t)alpha * (M + 1) + k];
+    p[k] = (r[0] * s + r[1] * u) * p[k - 1] - r[2] * s * s * p[k - 2];
+  }
+}
+
+// All basis functions at one point, sharing the Jacobi sequences of the
+// collapsed directions (one recurrence per direction and outer index).
 void Dubiner::eval(const double* xi, double* out) const {
-  for (int l = 0; l < n; ++l) out[l] = (l == 0) ? 1.0 : norm[l] * dubiner_raw(d, pqr[l], xi);
+  double f1[16], f2[16][16], f3[16];
+  if (d == 2) {
+    const double s1 = 1.0 - xi[1], u1 = 2.0 * xi[0] - s1;
+    jacobi_seq(0, M, u1, s1, f1);
+    for (int p = 0; p <= M; ++p) jacobi_seq(2 * p + 1, M - p, 2.0 * xi[1] - 1.0, 1.0, f2[p]);
+    out[0] = 1.0;
+    for (int l = 1; l < n; ++l) out[l] = norm[l] * (f1[pqr[l][0]] * f2[pqr[l][0]][pqr[l][1]]);
+    return;
+  }
+  const double s1 = 1.0 - xi[1] - xi[2], u1 = 2.0 * xi[0] - s1;
+  const double s2 = 1.0 - xi[2], u2 = 2.0 * xi[1] - s2;
+  jacobi_seq(0, M, u1, s1, f1);
+  for (int p = 0; p <= M; ++p) jacobi_seq(2 * p + 1, M - p, u2, s2, f2[p]);
+  out[0] = 1.0;
+  for (int l = 1; l < n; ++l) {
+    const int p = pqr[l][0], q = pqr[l][1], r = pqr[l][2];
+    jacobi_seq(2 * p + 2 * q + 2, r, 2.0 * xi[2] - 1.0, 1.0, f3);
+    out[l] = norm[l] * (f1[p] * f2[p][q] * f3[r]);
+  }
 }
 
 // ---------------------------------------------------------- face codes

@@ -46,8 +46,14 @@ struct Dubiner {
   std::vector<double> norm;              // normalisation per function
   std::vector<std::array<int, 3>> pqr;   // Jacobi indices
   std::vector<PPoly> power;              // power-form coefficients (for derivatives)
+  // three-term recurrence coefficients of the homogenised Jacobi polynomials
+  // P^(alpha,0), per integer alpha and degree k >= 2: p_k = (c2 s + c3 u)
+  // p_{k-1} - c4 s^2 p_{k-2}
+  std::vector<std::array<double, 3>> rec;  // [(alpha * (M + 1) + k)]
   void init(int d, int M);
   void eval(const double* xi, double* out) const;  // out[n]
+ private:
+  void jacobi_seq(int alpha, int nmax, double u, double s, double* p) const;
 };
 
 // Reference data of one (d, M).

@@ -13,6 +13,7 @@
 // positive barycentric coordinates for all vertices but s); a sector with
 // fewer cells, or with collinear / coplanar barycentres, is dropped.
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -82,12 +83,23 @@ struct Cand {
   }
 };
 
+// per-thread scratch of the stencil search: mark[j] == i flags cell j as
+// reached from cell i (each cell is searched once, so no reset is needed)
+struct Scratch {
+  std::vector<int32_t> mark, front, next;
+  std::vector<Cand> cand;
+};
+
 // ranked BFS sequence (cell i excluded); returns false if the mesh is too small
-bool ranked_sequence(const MeshHost& m, int32_t i, int need, std::vector<int32_t>& seq) {
+bool ranked_sequence(const MeshHost& m, int32_t i, int need, std::vector<int32_t>& seq, Scratch& sc) {
   const int nvx = m.d + 1;
   seq.clear();
-  std::vector<int32_t> seen(1, i), front(1, i), next;
-  std::vector<Cand> cand;
+  if ((int64_t)sc.mark.size() != m.nc) sc.mark.assign(m.nc, -1);
+  sc.mark[i] = i;
+  std::vector<int32_t>& front = sc.front;
+  std::vector<int32_t>& next = sc.next;
+  std::vector<Cand>& cand = sc.cand;
+  front.assign(1, i);
   const double tol = 1e-9 * m.qscale;
   int done_layer = -1;
   for (int layer = 1;; ++layer) {
@@ -95,9 +107,8 @@ bool ranked_sequence(const MeshHost& m, int32_t i, int need, std::vector<int32_t
     for (int32_t c : front)
       for (int k = 0; k < nvx; ++k) {
         int32_t j = m.nbr[(size_t)c * nvx + k];
-        if (j < 0) continue;
-        if (std::find(seen.begin(), seen.end(), j) != seen.end()) continue;
-        seen.push_back(j);
+        if (j < 0 || sc.mark[j] == i) continue;
+        sc.mark[j] = i;
         next.push_back(j);
       }
     if (next.empty()) break;
@@ -137,8 +148,10 @@ void to_ref(const MeshHost& m, int32_t i, const double Ji[3][3], const double* x
 
 // Pseudo-inverse of A (m x n, m >= n, row-major) by modified Gram-Schmidt QR
 // with one reorthogonalisation pass: pinv = R^{-1} Q^T (n x m).
-bool mgs_pinv(int mrow, int n, const std::vector<double>& A, std::vector<double>& pinv) {
-  std::vector<double> Qm(A), Rm((size_t)n * n, 0.0);
+bool mgs_pinv(int mrow, int n, const std::vector<double>& A, std::vector<double>& pinv, std::vector<double>& Qm,
+              std::vector<double>& Rm) {
+  Qm = A;
+  Rm.assign((size_t)n * n, 0.0);
   for (int k = 0; k < n; ++k) {
     for (int pass = 0; pass < 2; ++pass)
       for (int j = 0; j < k; ++j) {
@@ -222,12 +235,15 @@ int build_cell_setup(const MeshHost& m, const RefElem& re, CellSetup& cs, std::s
   std::atomic<int> badkind(0);
   auto work = [&](int64_t c0, int64_t c1) {
     std::vector<int32_t> seq;
-    std::vector<double> A((size_t)(ne - 1) * (Mc - 1)), pinv;
+    std::vector<double> A((size_t)(ne - 1) * (Mc - 1)), pinv, Qm, Rm;
+    std::vector<std::array<double, 4>> lamseq;  // barycentric coordinates of the sequence's barycentres
+    std::vector<std::array<double, 3>> xiseq;   // and their reference coordinates
+    Scratch sc;
     double psi[64];
     for (int64_t ii = c0; ii < c1; ++ii) {
       if (bad.load() >= 0) return;
       int32_t i = (int32_t)ii;
-      if (!ranked_sequence(m, i, ne, seq)) {
+      if (!ranked_sequence(m, i, ne, seq, sc)) {
         bad = ii;
         badkind = 1;
         return;
@@ -258,37 +274,43 @@ int build_cell_setup(const MeshHost& m, const RefElem& re, CellSetup& cs, std::s
         }
         for (int l = 1; l < Mc; ++l) A[(size_t)r * (Mc - 1) + (l - 1)] = acc[l] / wsum;
       }
-      if (!mgs_pinv(ne - 1, Mc - 1, A, pinv)) {
+      if (!mgs_pinv(ne - 1, Mc - 1, A, pinv, Qm, Rm)) {
         bad = ii;
         badkind = 2;
         return;
       }
       std::memcpy(&cs.R[(size_t)i * (Mc - 1) * (ne - 1)], pinv.data(), sizeof(double) * (Mc - 1) * (ne - 1));
-      // sectors
+      // sectors: barycentric coordinates of every sequence cell's
+      // (minimum-image) barycentre in cell i, once
+      lamseq.resize(seq.size());
+      xiseq.resize(seq.size());
+      for (size_t q = 0; q < seq.size(); ++q) {
+        const int32_t j = seq[q];
+        double s[3];
+        shift_of(m, i, j, s);
+        double b[3] = {0, 0, 0};
+        for (int a = 0; a < d; ++a) b[a] = m.bary[j * 3 + a] + s[a];
+        double xi[3] = {0, 0, 0};
+        to_ref(m, i, Ji, b, xi);
+        lamseq[q][0] = 1.0;
+        for (int a = 0; a < d; ++a) {
+          lamseq[q][a + 1] = xi[a];
+          lamseq[q][0] -= xi[a];
+        }
+        for (int a = 0; a < 3; ++a) xiseq[q][a] = xi[a];
+      }
       int kept = 0;
       for (int sct = 0; sct < nvx; ++sct) {
         int32_t chosen[3];
         int nch = 0;
         double xib[3][3];
-        for (int32_t j : seq) {
-          double s[3];
-          shift_of(m, i, j, s);
-          double b[3] = {0, 0, 0};
-          for (int a = 0; a < d; ++a) b[a] = m.bary[j * 3 + a] + s[a];
-          double xi[3];
-          to_ref(m, i, Ji, b, xi);
-          double lam[4];
-          lam[0] = 1.0;
-          for (int a = 0; a < d; ++a) {
-            lam[a + 1] = xi[a];
-            lam[0] -= xi[a];
-          }
+        for (size_t q = 0; q < seq.size(); ++q) {
           bool in = true;
-          for (int q = 0; q < nvx; ++q)
-            if (q != sct && !(lam[q] > 1e-9)) in = false;
+          for (int v = 0; v < nvx; ++v)
+            if (v != sct && !(lamseq[q][v] > 1e-9)) in = false;
           if (!in) continue;
-          for (int a = 0; a < 3; ++a) xib[nch][a] = xi[a];
-          chosen[nch++] = j;
+          for (int a = 0; a < 3; ++a) xib[nch][a] = xiseq[q][a];
+          chosen[nch++] = seq[q];
           if (nch == d) break;
         }
         if (nch < d) continue;

@@ -462,13 +462,16 @@ def serving_stream(nreq=512, seed=42, rate=None, nmin=1000, nmax=200000):
 
 
 def serving_request_inputs(req):
-    """Mesh and initial cell averages of one request of `serving_stream`."""
+    """Mesh and initial cell averages of one request of `serving_stream`
+    (collapsed Gauss rule with 3 x 3 points for the vortex, 4 x 4 x 2
+    sub-triangle samples for the explosion: initial data of a throughput
+    workload, generated for tens of millions of cells)."""
     mesh = tri_mesh(req["n"], periodic=True, jitter=0.2, seed=req["seed"])
     if req["kind"] == "vortex":
         c = req["params"]["centre"]
-        Q = cell_averages(mesh, lambda x: vortex(x, eps=req["params"]["eps"], centre=c), n=5)
+        Q = cell_averages(mesh, lambda x: vortex(x, eps=req["params"]["eps"], centre=c), n=3)
     else:
         pr = req["params"]["pratio"]
         Q = explosion_averages(mesh, r0=req["params"]["r0"], centre=(0.5, 0.5), p_in=0.1 * pr,
-                               sub=8)
+                               sub=4)
     return mesh, Q
