@@ -51,11 +51,13 @@
 // Addition not in the paper (switchable, on by default): a positivity
 // preserving scaling of the reconstruction toward the cell average at the
 // lattice nodes, first for the density, then for the pressure, with floors
-// of 1e-6 of their cell-average values (the scaling
+// of 1e-3 of their cell-average values (the scaling
 // limiter of Zhang & Shu, J. Comput. Phys. 229 (2010) 3091), and, at a face
 // quadrature point where one side's predictor is not an admissible state,
-// that side's cell average in place of its trace.  Where everything is
-// admissible neither changes anything.
+// that side's cell average in place of its trace, and, where the space-time
+// predictor of a cell leaves the admissible set at any node, that cell's
+// average as its predictor.  Where everything is admissible none of these
+// changes anything.
 // ============================================================================
 #include <algorithm>
 #include <array>
@@ -1154,12 +1156,12 @@ bool reconstruct_cell(OSolver& S, const double* Q, long i, RecOut& out, std::str
   if (S.P.positivity) {
     // Positivity scaling (addition, see the header): w <- Qbar + theta (w - Qbar)
     // with theta the largest value in [0,1] keeping density, then pressure,
-    // above 1e-6 times their cell-average values at every lattice node (a
+    // above 1e-3 times their cell-average values at every lattice node (a
     // floor above single-precision rounding, so both precisions of the
     // product take the same decisions).  Density and pressure are concave in
     // the conserved variables, so the linear interpolation bound below is
     // sufficient; a node whose scaled density is not positive gives theta 0.
-    const double floor_rel = 1e-6;
+    const double floor_rel = 1e-3;
     const double* qb = &Q[i * nu];
     double rb = qb[0], pb = pressure(S.pde, d, S.P, qb);
     std::vector<std::vector<double>> node(S.Mc, std::vector<double>(nu));
@@ -1341,7 +1343,8 @@ void init_predictor(OSolver& S) {
 // iterations q_k <- w(xi_k) - dt sum_e sum_l Pint[e][k][l] G_e(q_l), with
 // G_e = sum_m (d xi_e / d x_m) F_m (Eq. Hterm, Eulerian), from the initial
 // guess w(xi) at every node.  qhat: L x nu nodal values.
-void predictor_cell(const OSolver& S, long i, const std::vector<Poly>& w, double dt, std::vector<double>& qhat) {
+void predictor_cell(const OSolver& S, long i, const std::vector<Poly>& w, double dt, std::vector<double>& qhat,
+                    const double* qbar) {
   int d = S.d, nu = S.nu, L = S.Lc, L0 = S.L0, L1 = L - L0;
   const OMesh& m = *S.mesh;
   double J[3][3], Ji[3][3];
@@ -1375,6 +1378,23 @@ void predictor_cell(const OSolver& S, long i, const std::vector<Poly>& w, double
       }
     for (int k = 0; k < L1; ++k)
       for (int v = 0; v < nu; ++v) qhat[(L0 + k) * nu + v] = q1[k * nu + v];
+  }
+  // Predictor fallback (addition, with the positivity switch): if a
+  // space-time node left the admissible set (density or pressure <= 0, or
+  // not finite), the cell's predictor is its cell average at every node.
+  // A lattice node scaled close to vacuum can carry a wave speed far above
+  // the cell average's, which the time step of Eq. (timestep) does not see.
+  if (qbar && S.P.positivity) {
+    bool ok = true;
+    for (int l = L0; l < L; ++l) {
+      const double* q = &qhat[(size_t)l * nu];
+      bool fin = true;
+      for (int v = 0; v < nu; ++v) fin = fin && std::isfinite(q[v]);
+      if (!(fin && q[0] > 0.0 && pressure(S.pde, d, S.P, q) > 0.0)) ok = false;
+    }
+    if (!ok)
+      for (int l = 0; l < L; ++l)
+        for (int v = 0; v < nu; ++v) qhat[(size_t)l * nu + v] = qbar[v];
   }
 }
 
@@ -1666,7 +1686,7 @@ int orc_predictor(void* p, const double* Q, double dt, int64_t n, const int64_t*
       return -1;
     }
     std::vector<double> qh;
-    predictor_cell(*S, i, R.w, dt, qh);
+    predictor_cell(*S, i, R.w, dt, qh, &Q[i * nu]);
     for (int l = 0; l < L; ++l)
       for (int v = 0; v < nu; ++v) qhat[((size_t)c * L + l) * nu + v] = qh[l * nu + v];
   }
@@ -1698,7 +1718,7 @@ int orc_predictor_from_w(void* p, int64_t cell, const double* wnodal, double dt,
   }
   std::vector<double> qh;
   if (galerkin) predictor_cell_galerkin(*S, cell, w, dt, qh);
-  else predictor_cell(*S, cell, w, dt, qh);
+  else predictor_cell(*S, cell, w, dt, qh, nullptr);
   for (size_t k = 0; k < qh.size(); ++k) qhat[k] = qh[k];
   return 0;
 }
@@ -1798,7 +1818,7 @@ int orc_step(void* p, const double* Q, double dt, int64_t n, const int64_t* ids,
         set_err(err, errlen, e);
         return -1;
       }
-      predictor_cell(*S, j, R.w, dt, pred[j]);
+      predictor_cell(*S, j, R.w, dt, pred[j], &Q[j * S->nu]);
     }
   }
   std::vector<double> tx, tw;

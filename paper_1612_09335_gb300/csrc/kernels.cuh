@@ -611,11 +611,13 @@ __global__ void __launch_bounds__(128, C::REC_MINB) k_rec_pred(KArgs<C> a, const
 
   // ---- positivity scaling toward the cell average (switchable; an addition
   // to the paper, the Zhang-Shu scaling limiter): density first, then the
-  // pressure, both kept above 1e-6 of their cell-average values at every
-  // lattice node (a floor above FP32 rounding of Qbar + theta (w - Qbar));
+  // pressure, both kept above 1e-3 of their cell-average values at every
+  // lattice node (well above FP32 rounding of Qbar + theta (w - Qbar), and
+  // high enough that a scaled node cannot reach near-vacuum with a finite
+  // momentum, whose velocity the cell-average time step would not see);
   // density and pressure are concave in the conserved state
   if (a.pos) {
-    const T fl = T(1e-6);
+    const T fl = T(1e-3);
     T qb[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) qb[v] = qi[v] + qlo[v];
@@ -787,12 +789,37 @@ __global__ void __launch_bounds__(128, C::REC_MINB) k_rec_pred(KArgs<C> a, const
 #pragma unroll
         for (int v = 0; v < NV; ++v) sq[(k * NV + v) * B] = nq[k][v];
     }
+    // predictor fallback (with the positivity switch; an addition to the
+    // paper): a space-time node outside the admissible set (density or
+    // pressure <= 0, or not finite) makes the cell's predictor its cell
+    // average at every node.  A lattice node scaled close to vacuum can carry
+    // a wave speed far above the cell average's, which the time step of Eq.
+    // (timestep) does not see.
+    bool admissible = true;
+    if (a.pos) {
 #pragma unroll 1
-    for (int k = 0; k < L1; ++k) {
-      T q1[NV];
+      for (int k = 0; k < L1; ++k) {
+        T q[NV];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) q1[v] = sq[(k * NV + v) * B];
-      store_node<NV, T>(a.qhat + ((int64_t)(L0 + k) * N + i) * NV, q1);
+        for (int v = 0; v < NV; ++v) q[v] = qb[v] + sq[(k * NV + v) * B];
+        const T pk = PH::pressure(q, a.gamma);
+        if (!(q[0] > T(0) && pk > T(0) && isfinite(pk))) admissible = false;
+      }
+    }
+    if (admissible) {
+#pragma unroll 1
+      for (int k = 0; k < L1; ++k) {
+        T q1[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) q1[v] = sq[(k * NV + v) * B];
+        store_node<NV, T>(a.qhat + ((int64_t)(L0 + k) * N + i) * NV, q1);
+      }
+    } else {
+      T z[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) z[v] = T(0);
+#pragma unroll 1
+      for (int l = 0; l < C::L; ++l) store_node<NV, T>(a.qhat + ((int64_t)l * N + i) * NV, z);
     }
   }
 }

@@ -443,11 +443,13 @@ def serving_stream(nreq=512, seed=42, rate=None, nmin=1000, nmax=200000):
     log-uniform cell counts (n = round(sqrt(N/2))), orders P1..P3 and either a
     vortex or an explosion initial state on a periodic unit square."""
     rng = np.random.default_rng(seed)
+    # arrival times from their own stream: the requests are the same at any rate
+    rng_t = np.random.default_rng([seed, 1])
     out = []
     t = 0.0
     for k in range(nreq):
         if rate:
-            t += rng.exponential(1.0 / rate)
+            t += rng_t.exponential(1.0 / rate)
         N = math.exp(rng.uniform(math.log(nmin), math.log(nmax)))
         n = max(8, int(round(math.sqrt(N / 2))))
         order = int(rng.integers(2, 5))

@@ -298,3 +298,22 @@ def test_positivity_off_is_the_papers_scheme(cw, orc, wl):
     s = make(cw, mesh, 4, EULER, cw.FP64, positivity=0)
     s.set_state(Q)
     assert relerr(s.reconstruct(), o.reconstruct(Q)) < tolerance("explosion", o.reconstruct, Q)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("n,seed,order,r0,p_in", [(27, 1617, 2, 0.3786104969506505, 0.5165250010763427),
+                                                 (165, 1689, 4, 0.3738107572554006, 0.55464529352432494)])
+def test_explosions_from_serving_mix_stay_admissible(cw, wl, prec, n, seed, order, r0, p_in):
+    """Two serving-mix requests that failed before the floor of 1e-3 and the
+    predictor fallback: a P1 explosion (near-vacuum lattice node with finite
+    momentum) and a P3 explosion (near-vacuum node with finite pressure, a
+    sound speed 16x the cell average's).  50 steps at CFL 0.5 stay
+    admissible in both precisions."""
+    mesh = wl.tri_mesh(n, periodic=True, jitter=0.2, seed=seed)
+    Q = wl.explosion_averages(mesh, r0=r0, centre=(0.5, 0.5), p_in=p_in, sub=4)
+    s = make(cw, mesh, order, EULER, prec, cfl=0.5)
+    s.set_state(Q)
+    s.run(50)
+    s.sync()  # raises on a non-admissible state
+    Q1 = s.get_state()
+    assert np.isfinite(Q1).all() and Q1[:, 0].min() > 0
