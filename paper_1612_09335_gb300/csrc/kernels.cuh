@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "ops.h"
+#include "pred_pattern.h"
 
 namespace cw {
 
@@ -106,6 +107,14 @@ struct Cfg {
   // so that the node loops run rolled: a few kilobytes of code instead of a
   // fully unrolled body that misses the instruction cache
   static constexpr int PRED_SMEM_BYTES = 2 * L1 * NV * (int)sizeof(T_) * 128;
+  // Picard node loop unrolled with the compile-time zero pattern of P_e
+  // where it has at most ten unknown nodes (measured: P2/P3 3-8 % faster;
+  // the 20-node unroll of P4 overflows the instruction cache)
+#ifdef CW_PRED_SPARSE
+  static constexpr bool PRED_SPARSE = CW_PRED_SPARSE;
+#else
+  static constexpr bool PRED_SPARSE = L1 <= 10;
+#endif
 };
 
 template <class C>
@@ -483,6 +492,7 @@ __device__ __forceinline__ void store_node(T* __restrict__ p, const T* in) {
 
 // ---------------------------------------------------------- rec + predictor
 
+
 template <class C, bool REC_ONLY>
 __global__ void __launch_bounds__(128, C::REC_MINB) k_rec_pred(KArgs<C> a, const __grid_constant__ CellTab<C> tb) {
   using T = typename C::T;
@@ -761,7 +771,10 @@ __global__ void __launch_bounds__(128, C::REC_MINB) k_rec_pred(KArgs<C> a, const
       for (int k = 0; k < L1; ++k)
 #pragma unroll
         for (int v = 0; v < NV; ++v) nq[k][v] = sb[(k * NV + v) * B];
-#pragma unroll 1
+      // with PRED_SPARSE the loop is unrolled over the nodes, so the exact
+      // zeros of P_e (half to two thirds of the entries, pred_pattern.h) are
+      // skipped at compile time and the rest are immediate operands
+#pragma unroll(C::PRED_SPARSE ? C::L1 : 1)
       for (int l = 0; l < L1; ++l) {
         T ql[NV];
 #pragma unroll
@@ -780,7 +793,8 @@ __global__ void __launch_bounds__(128, C::REC_MINB) k_rec_pred(KArgs<C> a, const
           for (int v = 0; v < NV; ++v) {
             T s = nq[k][v];
 #pragma unroll
-            for (int e = 0; e < D; ++e) s -= tb.P[e][k][L0 + l] * Ge[e][v];
+            for (int e = 0; e < D; ++e)
+              if (!C::PRED_SPARSE || PredPattern<D, C::M>::nz(e, k, L0 + l)) s -= tb.P[e][k][L0 + l] * Ge[e][v];
             nq[k][v] = s;
           }
       }

@@ -133,3 +133,15 @@ def test_product_path_refuses_without_gpu_or_library(cw, wl):
     with pytest.raises(cw.CwenoError) as e:
         cw.Solver(cw.Mesh.from_workload(m), 3)
     assert e.value.code == cw.ECUDA
+
+
+def test_predictor_zero_pattern_header_is_generated():
+    """pred_pattern.h (the exact zero pattern of the predictor matrices that
+    the kernels skip) is the output of its generator, which computes the
+    entries in exact rational arithmetic."""
+    import subprocess
+    import sys
+    csrc = os.path.join(ROOT, "paper_1612_09335_gb300", "csrc")
+    out = subprocess.run([sys.executable, os.path.join(csrc, "gen_pred_pattern.py")], capture_output=True,
+                         text=True, check=True).stdout
+    assert out == open(os.path.join(csrc, "pred_pattern.h")).read()
