@@ -307,7 +307,7 @@ int serve_create(size_t mem_budget, int max_slots, int nworkers, cweno_server** 
 int serve_submit(cweno_server* S, const cweno_request* q, uint64_t* id) {
   if (!S || !q || !id) return cw::fail(CWENO_EINVAL, "null argument");
   if ((q->dim != 2 && q->dim != 3) || q->nv <= 0 || q->nc <= 0 || !q->xyz || !q->cells || !q->Q0 ||
-      q->order < 2 || q->order > 4 || q->nsteps < 0 || !(q->cfl > 0) ||
+      q->order < 2 || q->order > 5 || q->nsteps < 0 || !(q->cfl > 0) ||
       (q->pde != CWENO_EULER && q->pde != CWENO_MHD_GLM) ||
       (q->precision != CWENO_FP64 && q->precision != CWENO_FP32_MIXED))
     return cw::fail(CWENO_EINVAL, "bad request");

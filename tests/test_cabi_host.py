@@ -145,3 +145,23 @@ def test_predictor_zero_pattern_header_is_generated():
     out = subprocess.run([sys.executable, os.path.join(csrc, "gen_pred_pattern.py")], capture_output=True,
                          text=True, check=True).stdout
     assert out == open(os.path.join(csrc, "pred_pattern.h")).read()
+
+
+def test_edge_case_meshes(cw, wl):
+    """An empty mesh is refused (EINVAL); a mesh too small for the central
+    stencil of the requested order is reported (EDEGENERATE, host setup);
+    the smallest meshes that hold the stencil are accepted (8 bounded cells
+    at second order: every cell has fewer than three neighbours)."""
+    with pytest.raises(cw.CwenoError) as e:
+        cw.Mesh(2, np.zeros((3, 2)), np.zeros((0, 3), np.int32), None)
+    assert e.value.code == cw.EINVAL
+    for n, per, ok_orders in ((3, True, (2, 3)), (3, False, (2, 3)), (2, False, (2,))):
+        m = cw.Mesh.from_workload(wl.tri_mesh(n, periodic=per, jitter=0.0))
+        for order in (2, 3, 4, 5):
+            if order in ok_orders:
+                S0, sec = m.stencils(order)
+                assert S0.shape[0] == m.nc and (S0 >= 0).all()
+            else:
+                with pytest.raises(cw.CwenoError) as e:
+                    m.stencils(order)
+                assert e.value.code == cw.EDEGENERATE

@@ -317,3 +317,24 @@ def test_explosions_from_serving_mix_stay_admissible(cw, wl, prec, n, seed, orde
     s.sync()  # raises on a non-admissible state
     Q1 = s.get_state()
     assert np.isfinite(Q1).all() and Q1[:, 0].min() > 0
+
+
+def test_tiny_mesh_zero_steps_and_one_block(cw, orc, wl):
+    """Edge cases: an 8-cell bounded mesh (second order; less than one thread
+    block, boundary faces only around two cells) matches the oracle in FP64;
+    zero steps leave the state untouched in both modes."""
+    mesh = wl.tri_mesh(2, periodic=False, jitter=0.0)
+    Q = wl.cell_averages(mesh, lambda x: wl.vortex(x, eps=2.0), n=4)
+    o = orc.Oracle(mesh, 2, EULER)
+    dt = o.stable_dt(Q)
+    s = make(cw, mesh, 2, EULER, cw.FP64)
+    s.set_state(Q)
+    s.step(dt)
+    s.sync()
+    assert relerr(s.get_state(), o.step(Q, dt)) < TOL64
+    for prec in (cw.FP64, cw.FP32_MIXED):
+        s = make(cw, mesh, 2, EULER, prec)
+        s.set_state(Q)
+        s.run(0)
+        s.sync()
+        assert np.array_equal(s.get_state(), Q)

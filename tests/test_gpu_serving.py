@@ -112,3 +112,24 @@ def test_requests_overlap_on_device(cw, wl):
         return el
     run(8)  # warm-up (reference tables, kernels)
     assert run(8) < run(1)
+
+
+def test_zero_step_and_fifth_order_requests(cw, wl):
+    """A request of zero steps returns its initial state unchanged; a
+    fifth-order request is served like the others (same result as alone)."""
+    m = wl.tri_mesh(20, seed=401)
+    Q = wl.cell_averages(m, lambda x: wl.vortex(x), n=3)
+    srv = cw.Server(max_slots=4)
+    a = srv.submit(m, Q, 3, 0.5, 0)
+    b = srv.submit(m, Q, 5, 0.5, 10)
+    srv.drain(300)
+    st, Qa, _ = srv.poll(a)
+    assert st == cw.REQ_DONE and np.array_equal(Qa, Q)
+    st, Qb, _ = srv.poll(b)
+    assert st == cw.REQ_DONE, srv.errors
+    srv.close()
+    s = cw.Solver(cw.Mesh.from_workload(m), 5, cw.EULER, cw.FP32_MIXED, cfl=0.5)
+    s.set_state(Q)
+    s.run(10)
+    s.sync()
+    assert np.array_equal(s.get_state(), Qb)
