@@ -19,7 +19,10 @@ LIB = os.path.join(LIBDIR, "libcweno.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["kern_euler2.cu", "kern_euler3.cu", "kern_mhd2.cu", "api.cu", "noalloc.cu"]
+CU_SOURCES = ["kern_euler2.cu", "kern_euler3.cu", "kern_mhd2.cu", "api.cu", "noalloc.cu", "setup_gpu.cu"]
+# per-file flags: the device least-squares setup keeps the host's FP64
+# arithmetic (no FMA contraction)
+CU_FLAGS = {"setup_gpu.cu": ["--fmad=false"]}
 CPP_SOURCES = ["refelem.cpp", "mesh.cpp", "setup.cpp", "serve.cpp"]
 
 
@@ -49,7 +52,7 @@ def _compile(src: str, extra: list[str], objdir: str = OBJ) -> str:
     path = os.path.join(CSRC, src)
     if src.endswith(".cu"):
         cmd = [nvcc, "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
-               "-Xptxas", "-O3", *extra, "-c", path, "-o", obj]
+               "-Xptxas", "-O3", *CU_FLAGS.get(src, []), *extra, "-c", path, "-o", obj]
     else:
         cmd = [nvcc, "-O2", "-std=c++17", "-x", "c++", "-Xcompiler", "-fPIC,-ffp-contract=off",
                *extra, "-c", path, "-o", obj]

@@ -186,7 +186,7 @@ int cweno_mesh_stencils(const cweno_mesh* mesh, int order, int32_t* S0, int32_t*
   const RefElem& re = ref_elem(m.d, order - 1);
   CellSetup cs;
   std::string err;
-  int rc = build_cell_setup(m, re, cs, err, (int)std::max(1u, std::thread::hardware_concurrency()));
+  int rc = build_cell_setup(m, re, cs, err, (int)std::max(1u, std::thread::hardware_concurrency()), false);
   if (rc) return fail(rc, err);
   const int ne = re.ne, d = m.d, nvx = d + 1;
   for (int64_t i = 0; i < m.nc; ++i) {
@@ -274,7 +274,7 @@ int cweno_setup(const cweno_mesh* mesh, int order, int pde, int precision, const
   CellSetup cs;
   std::string err;
   int nth = (int)std::max(1u, std::thread::hardware_concurrency());
-  int rc = build_cell_setup(m, re, cs, err, nth);
+  int rc = build_cell_setup(m, re, cs, err, nth, false);  // R on the device below
   if (rc) return fail(rc, err);
   {
     // keep freed blocks in the device's default pool for reuse (serving)
@@ -319,7 +319,10 @@ int cweno_setup(const cweno_mesh* mesh, int order, int pde, int precision, const
   }
   if ((rc = upload(s.get(), m.perm, (const void**)&ds.perm))) return rc;
   if ((rc = upload(s.get(), soa_i(cs.sten, N, re.ne - 1), (const void**)&ds.sten))) return rc;
-  if ((rc = upload_real(s.get(), cs.R, N, (re.Mc - 1) * (re.ne - 1), &ds.R))) return rc;
+  if ((rc = dev_alloc(s.get(), &p, es * N * (re.Mc - 1) * (re.ne - 1)))) return rc;
+  ds.R = p;
+  if ((rc = lsq_setup_device(m, re, ds.sten, p, precision == CWENO_FP32_MIXED, s->stream, err)))
+    return fail(rc, err);
   if ((rc = upload(s.get(), soa_i(cs.sec, N, nvx * d), (const void**)&ds.sec))) return rc;
   if ((rc = upload_real(s.get(), cs.Binv, N, nvx * d * d, &ds.Binv))) return rc;
   if ((rc = upload(s.get(), cs.nsec, (const void**)&ds.nsec))) return rc;

@@ -48,6 +48,14 @@ struct CellSetup {
   std::vector<double> Jinv;     // nc x d x d, Jinv[e][m] = d xi_e / d x_m
 };
 
-int build_cell_setup(const MeshHost& m, const RefElem& re, CellSetup& cs, std::string& err, int nthreads);
+// with_lsq = false leaves R empty (the device computes it, lsq_setup_device).
+int build_cell_setup(const MeshHost& m, const RefElem& re, CellSetup& cs, std::string& err, int nthreads,
+                     bool with_lsq = true);
+
+// Least-squares pseudo-inverses R on the current device (setup_gpu.cu): d_sten
+// the uploaded SoA stencils, d_R the solver's R buffer (FP32 if fp32, else
+// FP64), stream a cudaStream_t.  Synchronous on that stream.
+int lsq_setup_device(const MeshHost& m, const RefElem& re, const int32_t* d_sten, void* d_R, int fp32,
+                     void* stream, std::string& err);
 
 }  // namespace cw

@@ -214,7 +214,8 @@ double det_small(int d, const double* B) {
 
 }  // namespace
 
-int build_cell_setup(const MeshHost& m, const RefElem& re, CellSetup& cs, std::string& err, int nthreads) {
+int build_cell_setup(const MeshHost& m, const RefElem& re, CellSetup& cs, std::string& err, int nthreads,
+                     bool with_lsq) {
   const int d = m.d, nvx = d + 1, ne = re.ne, Mc = re.Mc, M = re.M;
   const int64_t nc = m.nc;
   cs = CellSetup();
@@ -222,7 +223,7 @@ int build_cell_setup(const MeshHost& m, const RefElem& re, CellSetup& cs, std::s
   cs.Mc = Mc;
   cs.d = d;
   cs.sten.assign((size_t)nc * (ne - 1), -1);
-  cs.R.assign((size_t)nc * (Mc - 1) * (ne - 1), 0.0);
+  if (with_lsq) cs.R.assign((size_t)nc * (Mc - 1) * (ne - 1), 0.0);
   cs.sec.assign((size_t)nc * nvx * d, -1);
   cs.Binv.assign((size_t)nc * nvx * d * d, 0.0);
   cs.nsec.assign(nc, 0);
@@ -254,7 +255,7 @@ int build_cell_setup(const MeshHost& m, const RefElem& re, CellSetup& cs, std::s
         for (int b = 0; b < d; ++b) cs.Jinv[(size_t)i * d * d + a * d + b] = Ji[a][b];
       for (int k = 0; k < ne - 1; ++k) cs.sten[(size_t)i * (ne - 1) + k] = seq[k];
       // least-squares rows: averages of psi_l (l >= 1) over each stencil cell
-      for (int r = 0; r < ne - 1; ++r) {
+      for (int r = 0; r < (with_lsq ? ne - 1 : 0); ++r) {
         int32_t j = seq[r];
         double s[3];
         shift_of(m, i, j, s);
@@ -274,12 +275,13 @@ int build_cell_setup(const MeshHost& m, const RefElem& re, CellSetup& cs, std::s
         }
         for (int l = 1; l < Mc; ++l) A[(size_t)r * (Mc - 1) + (l - 1)] = acc[l] / wsum;
       }
-      if (!mgs_pinv(ne - 1, Mc - 1, A, pinv, Qm, Rm)) {
+      if (with_lsq && !mgs_pinv(ne - 1, Mc - 1, A, pinv, Qm, Rm)) {
         bad = ii;
         badkind = 2;
         return;
       }
-      std::memcpy(&cs.R[(size_t)i * (Mc - 1) * (ne - 1)], pinv.data(), sizeof(double) * (Mc - 1) * (ne - 1));
+      if (with_lsq)
+        std::memcpy(&cs.R[(size_t)i * (Mc - 1) * (ne - 1)], pinv.data(), sizeof(double) * (Mc - 1) * (ne - 1));
       // sectors: barycentric coordinates of every sequence cell's
       // (minimum-image) barycentre in cell i, once
       lamseq.resize(seq.size());
