@@ -256,8 +256,9 @@ enum { CWENO_REQ_QUEUED = 0, CWENO_REQ_RUNNING = 1, CWENO_REQ_DONE = 2, CWENO_RE
 /* mem_budget: device bytes the server may hold for admitted requests
  * (0 -> 80% of free memory); max_slots: concurrently admitted requests, each
  * with its own CUDA stream (<= 0 -> 64); nworkers: host threads preparing
- * admitted requests (mesh, stencils, least-squares inverses; <= 0 -> a
- * quarter of the host cores).  Admission is first come, first served. */
+ * admitted requests (mesh and stencils on the host, least-squares inverses
+ * on the device; <= 0 -> half the host cores).  Admission is first come,
+ * first served. */
 int serve_create(size_t mem_budget, int max_slots, int nworkers, cweno_server** out);
 /* Copies the request; returns its id.  EBUSY if its footprint exceeds the
  * whole budget (it could never be admitted).  Thread-safe. */
