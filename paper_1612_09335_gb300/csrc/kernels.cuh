@@ -107,6 +107,13 @@ struct Cfg {
   // so that the node loops run rolled: a few kilobytes of code instead of a
   // fully unrolled body that misses the instruction cache
   static constexpr int PRED_SMEM_BYTES = 2 * L1 * NV * (int)sizeof(T_) * 128;
+  // stencil neighbours whose gathers are in flight together (measured: 8
+  // beats 4 by ~2 % in FP32 Euler, 2 and 1 are 7-30 % slower)
+#ifdef CW_GATHER_UNROLL
+  static constexpr int GATHER_UNROLL = CW_GATHER_UNROLL;
+#else
+  static constexpr int GATHER_UNROLL = (sizeof(T_) == 4 && NV <= 5) ? 8 : 4;
+#endif
   // Picard node loop unrolled with the compile-time zero pattern of P_e
   // where it has at most ten unknown nodes (measured: P2/P3 3-8 % faster;
   // the 20-node unroll of P4 overflows the instruction cache)
@@ -512,7 +519,7 @@ __global__ void __launch_bounds__(128, C::REC_MINB) k_rec_pred(KArgs<C> a, const
   for (int l = 0; l < MC1; ++l)
 #pragma unroll
     for (int v = 0; v < NV; ++v) c[l][v] = T(0);
-#pragma unroll 4
+#pragma unroll(C::GATHER_UNROLL)
   for (int k = 0; k < NE1; ++k) {
     const int64_t j = __ldg(a.sten + k * N + i);
     T dq[NV];
