@@ -73,26 +73,29 @@ struct Cfg {
   // the face and [0,1] (rows of LP), after the quadrature weights
   static constexpr int QF_OFF = (TABN + NQS + NQT + VW - 1) / VW * VW;
   static constexpr int TAB_TOTAL = QF_OFF + NCODE * LP;
-  // face kernel: two threads per face, each evaluating one side at every
-  // space-time point, where those traces fit the register budget (FP32,
-  // NQT NQS NV <= 64: 2D Euler); otherwise one thread per face, one time
-  // point at a time
+  // face kernel: two threads per face in FP32 (each thread evaluates its
+  // own side's traces, the pair swaps them by shuffles and splits the
+  // Rusanov points); one thread per face in FP64
 #ifdef CW_FLUX_PAIR
   static constexpr int PAIR = CW_FLUX_PAIR;
 #else
-  static constexpr int PAIR = sizeof(T_) == 4 && NQT * NQS * NV <= 64;
+  static constexpr int PAIR = sizeof(T_) == 4;
 #endif
+  // passes of the pair kernel over the time points: one pass holds all
+  // NQT NQS traces where they fit (2D Euler), otherwise one time point per
+  // pass (q_hat re-read per time point, as in the one-thread kernel)
+  static constexpr int PAIR_PASSES = NQT * NQS * NV <= 64 ? 1 : NQT;
   // prefetch of the next q_hat chunk in the trace loop where the extra
   // registers are few (measured: faster in 2D Euler, slower for NV >= 5)
   static constexpr bool TR_PREFETCH = VW * NV <= 16;
   // Resident 128-thread blocks per SM requested from the register allocator
-  // (measured launch-shape sweeps).  Face kernel: four in 2D FP32 Euler up
-  // to P3 (<= 128 registers), three in 2D P4, FP32 MHD and 3D FP32 Euler up
-  // to P2 (<= 168), unconstrained elsewhere.
+  // (measured launch-shape sweeps).  Face kernel (the two-threads-per-face
+  // form in FP32): four in FP32 Euler (<= 128 registers) except 3D P3, three
+  // in FP32 MHD (<= 168), unconstrained elsewhere.
 #ifdef CW_FLUX_MINB
   static constexpr int FLUX_MINB = CW_FLUX_MINB;
 #else
-  static constexpr int FLUX_MINB = sizeof(T_) != 4 ? 1 : (D == 2 && NV == 4 && M <= 3) ? 4 : (D == 2 || M <= 2) ? 3 : 1;
+  static constexpr int FLUX_MINB = sizeof(T_) != 4 ? 1 : PDE == 1 ? 3 : (D == 3 && M >= 3) ? 1 : 4;
 #endif
   // Reconstruction + predictor: four in 2D FP32 Euler up to P3 (<= 128
   // registers), three in 3D FP32 Euler (<= 168; 128 spills); unconstrained
@@ -1104,12 +1107,6 @@ __global__ void __launch_bounds__(128, C::FLUX_MINB) k_flux_pair(KArgs<C> a, int
     cell_average<C>(a, c, qb);
 #pragma unroll
     for (int v = 0; v < NV; ++v) qo[v] = __shfl_xor_sync(0xffffffffu, qb[v], 1);
-    T tr[NP][NV];
-#pragma unroll
-    for (int p = 0; p < NP; ++p)
-#pragma unroll
-      for (int v = 0; v < NV; ++v) tr[p][v] = T(0);
-    face_traces<C, NP>(a.qhat, c, N, tc, 0, tr);
     const T* qbL = side == 0 ? qb : qo;
     const T* qbR = side == 0 ? qo : qb;
     T facc[D][NV], dacc[NV];
@@ -1119,9 +1116,18 @@ __global__ void __launch_bounds__(128, C::FLUX_MINB) k_flux_pair(KArgs<C> a, int
 #pragma unroll
       for (int m = 0; m < D; ++m) facc[m][v] = T(0);
     }
+    constexpr int NPP = NP / C::PAIR_PASSES;
+#pragma unroll 1
+    for (int h = 0; h < C::PAIR_PASSES; ++h) {
+    T tr[NPP][NV];
 #pragma unroll
-    for (int k = 0; k < (NP + 1) / 2; ++k) {
-      constexpr int LAST = NP - 1;
+    for (int p = 0; p < NPP; ++p)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) tr[p][v] = T(0);
+    face_traces<C, NPP>(a.qhat, c, N, tc, h * NPP, tr);
+#pragma unroll
+    for (int k = 0; k < (NPP + 1) / 2; ++k) {
+      constexpr int LAST = NPP - 1;
       const int p0 = 2 * k, p1 = 2 * k + 1 <= LAST ? 2 * k + 1 : LAST;
       // thread 0 of the pair takes point p0, thread 1 point p1: each sends
       // the partner its own trace at the partner's point
@@ -1133,7 +1139,7 @@ __global__ void __launch_bounds__(128, C::FLUX_MINB) k_flux_pair(KArgs<C> a, int
         mine[v] = side == 0 ? tr[p0][v] : tr[p1][v];
       }
       if (side == 0 || 2 * k + 1 <= LAST) {
-        const int p = side == 0 ? p0 : p1;
+        const int p = h * NPP + (side == 0 ? p0 : p1);
         T ul[NV], ur[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
@@ -1142,6 +1148,7 @@ __global__ void __launch_bounds__(128, C::FLUX_MINB) k_flux_pair(KArgs<C> a, int
         }
         rusanov_point<C, OSHER>(a, ul, ur, qbL, qbR, n, wq[p % NQS] * wt[p / NQS], facc, dacc);
       }
+    }
     }
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
