@@ -155,7 +155,14 @@ int cweno_solver_footprint(const cweno_solver* s, size_t* bytes);
 
 /* Cell averages Q (Eq. cellaverage), nc x nvars FP64, copied in / out.
  * set_state also resets the accumulated time and the status word and
- * computes the CFL time-step bound for the next step. */
+ * computes the CFL time-step bound for the next step.
+ * on_device = 0: Q is host memory.  Pageable memory goes through a device
+ * staging buffer.  Page-locked memory that is mapped into the device address
+ * space (cudaHostAlloc, cudaHostRegister, torch pin_memory) is read or
+ * written in place by the state kernel over the CPU-GPU link, with no
+ * staging copy.  In both cases set_state is asynchronous on the solver's
+ * stream for page-locked Q: keep Q unchanged until a later synchronous call
+ * (get_state, reconstruct, ...) or a synchronisation of that stream. */
 int cweno_set_state(cweno_solver* s, const double* Q, int on_device);
 int cweno_get_state(cweno_solver* s, double* Q, int on_device); /* synchronous */
 

@@ -107,6 +107,8 @@ def _check(rc: int):
 
 def _ptr(x):
     """(pointer, on_device) for a numpy array or a CUDA tensor (duck-typed)."""
+    if hasattr(x, "data_ptr") and not x.is_contiguous():
+        raise ValueError("tensor arguments must be contiguous")
     if hasattr(x, "data_ptr") and getattr(x, "is_cuda", False):
         return C.c_void_p(x.data_ptr()), 1
     if hasattr(x, "data_ptr"):

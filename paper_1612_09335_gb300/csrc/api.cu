@@ -318,6 +318,7 @@ int cweno_setup(const cweno_mesh* mesh, int order, int pde, int precision, const
     CK(cudaMemsetAsync(ds.Qlo, 0, sizeof(float) * N * nv, s->stream));
   }
   if ((rc = upload(s.get(), m.perm, (const void**)&ds.perm))) return rc;
+  if ((rc = upload(s.get(), m.iperm, (const void**)&ds.iperm))) return rc;
   if ((rc = upload(s.get(), soa_i(cs.sten, N, re.ne - 1), (const void**)&ds.sten))) return rc;
   if ((rc = dev_alloc(s.get(), &p, es * N * (re.Mc - 1) * (re.ne - 1)))) return rc;
   ds.R = p;
@@ -395,18 +396,32 @@ int cweno_solver_footprint(const cweno_solver* s, size_t* bytes) {
   return CWENO_OK;
 }
 
+// Page-locked host memory that is mapped into the device address space (every
+// cudaHostAlloc/cudaHostRegister allocation under unified addressing): the
+// state kernels then read or write it in place over the CPU-GPU link instead
+// of going through a staging copy. Returns nullptr for pageable memory.
+static void* mapped_host(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 int cweno_set_state(cweno_solver* s, const double* Q, int on_device) {
   if (!s || !Q) return fail(CWENO_EINVAL, "null argument");
   CK(cudaSetDevice(s->dev));
   const double* src = Q;
   if (!on_device) {
-    CK(cudaMemcpyAsync(s->ds.stage, Q, sizeof(double) * s->nc * s->nv, cudaMemcpyHostToDevice, s->stream));
-    src = s->ds.stage;
+    if (const void* dp = mapped_host(Q)) {
+      src = (const double*)dp;
+    } else {
+      CK(cudaMemcpyAsync(s->ds.stage, Q, sizeof(double) * s->nc * s->nv, cudaMemcpyHostToDevice, s->stream));
+      src = s->ds.stage;
+    }
   }
-  CK(s->ops->set_state(s->ds, src, s->stream));
-  static const unsigned long long inf = 0x7ff0000000000000ull;
-  CK(cudaMemcpyAsync(s->ds.dtmin, &inf, sizeof(inf), cudaMemcpyHostToDevice, s->stream));
-  CK(cudaMemsetAsync(s->ds.time, 0, sizeof(double) + 2 * sizeof(int), s->stream));
+  CK(s->ops->set_state(s->ds, src, s->stream));  // also resets dt bound, time, status
   CK(s->ops->stable_dt(s->ds, s->ph, 0, s->stream));
   s->cur = 0;
   return CWENO_OK;
@@ -420,8 +435,12 @@ int cweno_get_state(cweno_solver* s, double* Q, int on_device) {
     CK(cudaStreamSynchronize(s->stream));
     return CWENO_OK;
   }
-  CK(s->ops->get_state(s->ds, s->ds.stage, s->stream));
-  CK(cudaMemcpyAsync(Q, s->ds.stage, sizeof(double) * s->nc * s->nv, cudaMemcpyDeviceToHost, s->stream));
+  if (void* dp = mapped_host(Q)) {
+    CK(s->ops->get_state(s->ds, (double*)dp, s->stream));
+  } else {
+    CK(s->ops->get_state(s->ds, s->ds.stage, s->stream));
+    CK(cudaMemcpyAsync(Q, s->ds.stage, sizeof(double) * s->nc * s->nv, cudaMemcpyDeviceToHost, s->stream));
+  }
   CK(cudaStreamSynchronize(s->stream));
   return CWENO_OK;
 }

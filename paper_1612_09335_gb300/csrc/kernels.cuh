@@ -144,6 +144,7 @@ struct KArgs {
   float* Qhi;
   float* Qlo;
   const int32_t* perm;
+  const int32_t* iperm;
   const int32_t* sten;
   const T* R;
   const int32_t* sec;
@@ -1429,30 +1430,41 @@ __global__ void __launch_bounds__(256) k_stable_dt(KArgs<C> a, int slot) {
   block_min_atomic(ratio, a.dtmin + slot);
 }
 
+// State in the caller's cell order (N x NV, row-major) <-> internal SoA. One
+// thread per caller element, so the caller-side accesses (which may be pinned
+// host memory read or written directly over the CPU-GPU link) are contiguous
+// across a warp; the device side scatters through the user->internal map.
+// set_state also restarts the run: the time-step bound of slot 0 (recomputed
+// by k_stable_dt next), the accumulated time and the status words.
 template <class C>
 __global__ void k_set_state(KArgs<C> a, const double* user) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.N) return;
-  const int64_t u = a.perm[i];
-#pragma unroll
-  for (int v = 0; v < C::NV; ++v) {
-    const double q = user[u * C::NV + v];
-    a.Q[v * a.N + i] = q;
-    if constexpr (std::is_same<typename C::T, float>::value) {
-      const float hi = (float)q;
-      a.Qhi[v * a.N + i] = hi;
-      a.Qlo[v * a.N + i] = (float)(q - (double)hi);
-    }
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e == 0) {
+    a.dtmin[0] = 0x7ff0000000000000ull;
+    *a.time = 0.0;
+    a.status[0] = 0;
+    a.status[1] = 0;
+  }
+  if (e >= a.N * C::NV) return;
+  const int64_t u = e / C::NV;
+  const int v = (int)(e - u * C::NV);
+  const int64_t j = v * a.N + a.iperm[u];
+  const double q = user[e];
+  a.Q[j] = q;
+  if constexpr (std::is_same<typename C::T, float>::value) {
+    const float hi = (float)q;
+    a.Qhi[j] = hi;
+    a.Qlo[j] = (float)(q - (double)hi);
   }
 }
 
 template <class C>
 __global__ void k_get_state(KArgs<C> a, double* user) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.N) return;
-  const int64_t u = a.perm[i];
-#pragma unroll
-  for (int v = 0; v < C::NV; ++v) user[u * C::NV + v] = a.Q[v * a.N + i];
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.N * C::NV) return;
+  const int64_t u = e / C::NV;
+  const int v = (int)(e - u * C::NV);
+  user[e] = a.Q[v * a.N + a.iperm[u]];
 }
 
 template <class C>
@@ -1518,6 +1530,7 @@ class OpsImpl final : public Ops {
     a.Qhi = s.Qhi;
     a.Qlo = s.Qlo;
     a.perm = s.perm;
+    a.iperm = s.iperm;
     a.sten = s.sten;
     a.R = (const T*)s.R;
     a.sec = s.sec;
@@ -1640,12 +1653,12 @@ class OpsImpl final : public Ops {
   }
   cudaError_t set_state(const DevState& s, const double* user, cudaStream_t st) override {
     KArgs<C> a = args(s, PhysParams(), DtArgs());
-    k_set_state<C><<<nblk(s.N, 256), 256, 0, st>>>(a, user);
+    k_set_state<C><<<nblk(s.N * C::NV, 256), 256, 0, st>>>(a, user);
     return cudaGetLastError();
   }
   cudaError_t get_state(const DevState& s, double* user, cudaStream_t st) override {
     KArgs<C> a = args(s, PhysParams(), DtArgs());
-    k_get_state<C><<<nblk(s.N, 256), 256, 0, st>>>(a, user);
+    k_get_state<C><<<nblk(s.N * C::NV, 256), 256, 0, st>>>(a, user);
     return cudaGetLastError();
   }
   cudaError_t qhat_out(const DevState& s, double* user, cudaStream_t st) override {

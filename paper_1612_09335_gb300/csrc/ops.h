@@ -18,6 +18,7 @@ struct DevState {
   float* Qhi = nullptr;         // nv x N (FP32 mode)
   float* Qlo = nullptr;         // nv x N (FP32 mode)
   const int32_t* perm = nullptr;  // internal -> user
+  const int32_t* iperm = nullptr; // user -> internal
   const int32_t* sten = nullptr;  // (ne-1) x N
   const void* R = nullptr;        // (Mc-1)(ne-1) x N
   const int32_t* sec = nullptr;   // (d+1) d x N

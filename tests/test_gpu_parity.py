@@ -185,6 +185,28 @@ def test_state_roundtrip_and_device_pointers(cw, wl):
     assert torch.equal(out, Qd)
 
 
+@pytest.mark.parametrize("name,fp64", [("vortex2d", False), ("wave3d", True), ("orszag", False)])
+def test_state_through_pinned_host_memory(cw, wl, name, fp64):
+    """Page-locked host buffers are read and written in place by the state
+    kernels; the result must equal the staged (pageable) path bit for bit,
+    before and after a step."""
+    import torch
+    (mesh, Q), pde = case_inputs(wl, name)
+    s = make(cw, mesh, 3, pde, cw.FP64 if fp64 else cw.FP32_MIXED)
+    hin = torch.from_numpy(Q.copy()).pin_memory()
+    s.set_state(hin)
+    hout = torch.full(Q.shape, float("nan"), dtype=torch.float64).pin_memory()
+    s.get_state(hout)
+    assert np.array_equal(hout.numpy(), Q)
+    s.step(0.0)
+    a = s.get_state()
+    s.get_state(hout)
+    assert np.array_equal(hout.numpy(), a)
+    s.set_state(Q)
+    s.step(0.0)
+    assert np.array_equal(s.get_state(), a)
+
+
 @pytest.mark.parametrize("name,order", [("vortex2d", 3), ("vortex2d", 5), ("explosion2d", 4), ("wave3d", 3),
                                         ("orszag", 4)])
 def test_conservation_both_modes(cw, wl, name, order):
