@@ -1,4 +1,5 @@
-"""FP64 CPU oracle of the fixed-mesh ADER-CWENO step -- TEST INFRASTRUCTURE.
+"""FP64 CPU oracle of the fixed-mesh and moving-mesh (direct ALE) ADER-CWENO
+steps -- TEST INFRASTRUCTURE.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline / reference
 arm of ``bench.py`` may import this package.  The product path (the CUDA
@@ -78,6 +79,11 @@ def lib():
             L.orc_st_nodes.argtypes = [P, dp]
             L.orc_face_points.argtypes = [P, I64, I, dp, dp, dp, dp]
             L.orc_face_points.restype = I
+            L.orc_ale_step.argtypes = [P, dp, D, I, dp, dp, cp, I]
+            L.orc_ale_predictor.argtypes = [P, dp, D, I, I64, dp, dp, cp, I]
+            L.orc_ale_vertex_weights.argtypes = [P, dp]
+            L.orc_st_normal.argtypes = [dp, dp, dp, dp, D, D, D, dp]
+            L.orc_mesh_xyz.argtypes = [P, dp]
             _lib = L
     return _lib
 
@@ -122,6 +128,12 @@ class OracleMesh:
             raise ValueError(err.value.decode())
         self.nc = cells.shape[0]
         self._keep = (xyz, cells, per)
+
+    def xyz(self):
+        """Current vertex positions (they change under ALE steps)."""
+        out = np.zeros(self._keep[0].shape)
+        lib().orc_mesh_xyz(self.h, _d(out))
+        return out
 
     def geometry(self):
         L = lib()
@@ -245,6 +257,44 @@ class Oracle:
             t += h
         return Q, t
 
+    # ---- moving meshes (direct ALE, Secs. 2.2-2.4; 2D Euler, Rusanov)
+    ALE_LAGRANGE, ALE_STILL = 1, 2
+
+    def ale_step(self, Q, dt, mode=1):
+        """One direct ALE step; returns (Q_new, xyz_new) and moves the
+        oracle's mesh (stencils fixed)."""
+        Q = np.ascontiguousarray(Q, dtype=np.float64)
+        out = np.zeros((self.nc, self.nu))
+        xyz = np.zeros(self.mesh._keep[0].shape)
+        err = C.create_string_buffer(256)
+        if lib().orc_ale_step(self.h, _d(Q), float(dt), int(mode), _d(out), _d(xyz), err, 256) != 0:
+            raise ValueError(err.value.decode())
+        return out, xyz
+
+    def ale_run(self, Q, nsteps, dt=None, mode=1, cfl=None):
+        """nsteps ALE steps; dt None -> CFL time step on the current mesh."""
+        Q = np.array(Q, dtype=np.float64)
+        t = 0.0
+        for _ in range(nsteps):
+            h = self.stable_dt(Q, cfl) if dt is None else dt
+            Q, _ = self.ale_step(Q, h, mode)
+            t += h
+        return Q, t
+
+    def ale_predictor(self, Q, dt, cell, mode=1):
+        Q = np.ascontiguousarray(Q, dtype=np.float64)
+        q = np.zeros((self.L, self.nu))
+        V = np.zeros((self.L, self.dim))
+        err = C.create_string_buffer(256)
+        if lib().orc_ale_predictor(self.h, _d(Q), float(dt), int(mode), int(cell), _d(q), _d(V), err, 256) != 0:
+            raise ValueError(err.value.decode())
+        return q, V
+
+    def ale_vertex_weights(self):
+        W = np.zeros((self.dim + 1, self.L))
+        lib().orc_ale_vertex_weights(self.h, _d(W))
+        return W
+
     def sigma(self, coef):
         c = np.ascontiguousarray(coef, dtype=np.float64)
         return lib().orc_sigma(self.h, _d(c))
@@ -322,3 +372,11 @@ def gauss_rule(kind, n):
 def simplex_integral(dim, e):
     a = np.ascontiguousarray(list(e) + [0] * (4 - len(e)), dtype=np.int32)
     return lib().orc_simplex_integral(dim, _i(a))
+
+
+def st_normal(XA0, XB0, XA1, XB1, chi, tau, dt):
+    """Space-time normal (x, y, t) of a moving 2D face at (chi, tau), Eq. (detChi)."""
+    a = [np.ascontiguousarray(x, dtype=np.float64) for x in (XA0, XB0, XA1, XB1)]
+    n = np.zeros(3)
+    lib().orc_st_normal(_d(a[0]), _d(a[1]), _d(a[2]), _d(a[3]), float(chi), float(tau), float(dt), _d(n))
+    return n

@@ -1,8 +1,9 @@
 // ============================================================================
 // ORACLE -- test infrastructure only.
 //
-// A plain, slow, FP64 CPU implementation of the fixed-mesh (Eulerian)
-// ADER-CWENO finite-volume step of Dumbser, Boscheri, Semplice & Russo,
+// A plain, slow, FP64 CPU implementation of the fixed-mesh (Eulerian) and
+// the moving-mesh (direct ALE, two dimensions, Euler, Rusanov)
+// ADER-CWENO finite-volume steps of Dumbser, Boscheri, Semplice & Russo,
 // "Central WENO schemes on unstructured meshes" (arXiv 1612.09335).
 // It is used only by tests/, by the smoke check and by the CPU-baseline /
 // reference arm of bench.py.  The product (the CUDA path) never calls it,
@@ -32,6 +33,11 @@
 //   quadrature-free Rusanov (switchable) fixed-mesh form described after Eq. (osher)
 //   Euler equations / EOS                Eqs. (eulerTerms), (eos)
 //   ideal MHD with GLM cleaning          Eqs. (MHDTerms), (MHDeos)
+//   moving meshes: predictor on a moving Sec. 2.2, Eqs. (PDExi2), (Hterm),
+//     element with the trajectory eq.    (CGfinal), (ODEfinal), (xh_vh)
+//   nodal solver and new vertices        Sec. 2.3, Eqs. (NScs)-(newX)
+//   space-time control volumes, normals  Sec. 2.4, Eqs. (dCi)-(detChi)
+//   ALE update and Rusanov flux          Eqs. (PDEfinal), (rusanov) with A_n^V
 //
 // Readings where the paper is silent (documented in the design notes):
 //   * stencil fill = face-neighbour BFS by layers, candidates of a layer ranked
@@ -47,6 +53,12 @@
 //   * Rusanov s_max per quadrature point, max over both sides;
 //   * Osher-type flux: the path integral of |A_n| by 3-point Gauss-Legendre;
 //   * MHD EOS p = (gamma-1)(rho E - rho|v|^2/2 - |B|^2/(8 pi)).
+//   * moving meshes: mesh velocity V = v (Sec. 3) or V = 0; stencils and
+//     sectors fixed on the initial mesh, their matrices rebuilt each step;
+//     M+1 coupled Picard iterations; a lateral face point (chi, tau) is
+//     evaluated at the reference point at parameter chi on the cell's own
+//     reference edge; Gauss-Legendre with M+1 points in chi and tau; the
+//     vertex velocity uses the mesh velocity of the final predictor states.
 //   * s_max and the time-step speed take sqrt(max(0, .)) of the sound speed.
 // Addition not in the paper (switchable, on by default): a positivity
 // preserving scaling of the reconstruction toward the cell average at the
@@ -717,7 +729,10 @@ void to_ref(const OMesh& m, long c, const double* x, double* xi) {
     for (int b = 0; b < m.d; ++b) xi[a] += Ji[a][b] * (x[b] - vx(m, c, 0, b));
 }
 
-bool build_mesh(OMesh& m, std::string& err) {
+// Geometry of every cell from the vertex coordinates m.xyz: unwrapped vertex
+// coordinates (periodic images nearest the cell's first vertex), |T_i| and the
+// barycentre.  Called at construction and again after every mesh motion.
+bool mesh_geometry(OMesh& m, std::string& err) {
   int d = m.d;
   m.X.assign((size_t)m.nc * (d + 1) * 3, 0.0);
   m.vol.assign(m.nc, 0.0);
@@ -760,6 +775,12 @@ bool build_mesh(OMesh& m, std::string& err) {
       m.bary[c * 3 + a] = s / (d + 1);
     }
   }
+  return true;
+}
+
+bool build_mesh(OMesh& m, std::string& err) {
+  int d = m.d;
+  if (!mesh_geometry(m, err)) return false;
   // face matching by sorted global vertex ids
   struct FaceKey {
     long v[3];
@@ -946,6 +967,8 @@ void bary_in_ref(const OMesh& m, long i, long j, double* xi) {
   to_ref(m, i, b, xi);
 }
 
+void cell_matrices(OSolver& S, long i, CellRec& R);
+
 bool prepare_cell(OSolver& S, long i, std::string& err) {
   CellRec& R = S.cache[i];
   if (R.ready) return true;
@@ -988,6 +1011,30 @@ bool prepare_cell(OSolver& S, long i, std::string& err) {
       for (int a = 0; a < d; ++a) Bm[k][a] = B[k * d + a];
     if (std::fabs(det3(Bm, d)) < 1e-8) continue;  // degenerate sector: dropped
     R.st.sector[s] = chosen;
+  }
+  cell_matrices(S, i, R);
+  R.ready = true;
+  return true;
+}
+
+// Geometry-dependent data of cell i for its (fixed) stencils, from the current
+// vertex positions: the sector rows xi(b_j) - xi_bary of Eq. (CWENO:Ps) and
+// the least-squares rows of Eq. (CWENO:Popt).  On a moving mesh the stencils
+// stay those chosen on the initial mesh (the topology never changes) and
+// only these matrices are rebuilt every step (Sec. 2.1).
+void cell_matrices(OSolver& S, long i, CellRec& R) {
+  const OMesh& m = *S.mesh;
+  int d = m.d;
+  double xb = 1.0 / (d + 1);
+  R.Bsec.assign(d + 1, std::vector<double>());
+  for (int s = 0; s <= d; ++s) {
+    if (R.st.sector[s].empty()) continue;
+    std::vector<double> B((size_t)d * d);
+    for (int k = 0; k < d; ++k) {
+      double xi[3];
+      bary_in_ref(m, i, R.st.sector[s][k], xi);
+      for (int a = 0; a < d; ++a) B[k * d + a] = xi[a] - xb;
+    }
     R.Bsec[s] = B;
   }
   // --- least-squares rows, Eq. (CWENO:Popt): averages of the monomials over
@@ -1024,8 +1071,6 @@ bool prepare_cell(OSolver& S, long i, std::string& err) {
       R.Ared[(size_t)r * (nmono - 1) + (e - 1)] = avg - R.ai[e];
     }
   }
-  R.ready = true;
-  return true;
 }
 
 // Polynomial in the spatial monomials from coefficients (index = mono order).
@@ -1526,6 +1571,327 @@ void face_points(const OSolver& S, long i, int k, std::vector<std::array<double,
   for (int a = 0; a < 3; ++a) nrm[a] = dot > 0 ? out[a] : -out[a];
 }
 
+// ============================================================================
+// Moving meshes: the direct ALE step (Secs. 2.2-2.4), two space dimensions,
+// Euler equations, Rusanov flux with the ALE Jacobian of Eq. (rusanov)
+// ============================================================================
+
+// Mesh-velocity choice of Sec. 2.3: ALE_LAGRANGE takes V = v, the local
+// fluid velocity (the choice of every moving-mesh test of Sec. 3); ALE_STILL
+// takes V = 0, the ALE machinery on a mesh that does not move (it reduces to
+// the Eulerian scheme).
+enum { ALE_LAGRANGE = 1, ALE_STILL = 2 };
+
+void mesh_velocity(int mode, int d, const double* q, double* V) {
+  for (int a = 0; a < d; ++a) V[a] = mode == ALE_LAGRANGE ? q[1 + a] / q[0] : 0.0;
+}
+
+double ipow_d(double x, int n) {
+  double r = 1.0;
+  for (int k = 0; k < n; ++k) r *= x;
+  return r;
+}
+
+// Space-time predictor on a moving element, Eqs. (PDExi2)-(ODEfinal).  The
+// state DOFs q_hat and the geometry DOFs x_hat of the isoparametric map
+// (Eq. xh_vh) are iterated together.  Each iteration takes the nodal fluxes
+// F_hat and mesh velocities V_hat, the term H of Eq. (Hterm) at every node
+// from the xi-derivatives of the nodal interpolants, with d xi / d x the
+// inverse of d x_h / d xi at that node and d xi / d t = -(d xi / d x) V, and
+// then solves, as written,
+//   K_tau^1 q^1 = -dt M H - K_tau^0 q^0        (Eq. CGfinal)
+//   K_tau^1 x^1 =  dt M V - K_tau^0 x^0        (Eq. ODEfinal)
+// by Gaussian elimination.  Initial guess: w(xi) and the affine map of T_i^n
+// at every node; niter (= M+1) iterations.  Vhat: L x d mesh velocities of
+// the final nodal states.  With the positivity switch, a cell whose
+// predictor leaves the admissible set at a tau > 0 node falls back to its
+// cell average at every node (as on fixed meshes).
+void ale_predictor_cell(const OSolver& S, long i, const std::vector<Poly>& w, double dt, int mode,
+                        std::vector<double>& qhat, std::vector<double>& Vhat, const double* qbar) {
+  int d = S.d, nu = S.nu, L = S.Lc, L0 = S.L0, L1 = L - L0;
+  const OMesh& m = *S.mesh;
+  qhat.assign((size_t)L * nu, 0.0);
+  std::vector<double> xh((size_t)L * d);
+  for (int l = 0; l < L; ++l) {
+    double x[4] = {S.st_nodes[l][0], S.st_nodes[l][1], S.st_nodes[l][2], 0.0};
+    for (int v = 0; v < nu; ++v) qhat[l * nu + v] = poly_eval(w[v], x);
+    for (int a = 0; a < d; ++a) {
+      double xa = vx(m, i, 0, a);
+      for (int e = 0; e < d; ++e) xa += (vx(m, i, e + 1, a) - vx(m, i, 0, a)) * S.st_nodes[l][e];
+      xh[l * d + a] = xa;
+    }
+  }
+  // dth[e][n][l] = d theta_l / d xi_e at node n
+  std::vector<double> dth((size_t)d * L * L);
+  for (int e = 0; e < d; ++e)
+    for (int l = 0; l < L; ++l) {
+      Poly dp = poly_deriv(S.theta[l], e);
+      for (int n = 0; n < L; ++n) {
+        double x[4] = {S.st_nodes[n][0], S.st_nodes[n][1], S.st_nodes[n][2], S.st_nodes[n][3]};
+        dth[((size_t)e * L + n) * L + l] = poly_eval(dp, x);
+      }
+    }
+  std::vector<double> K1((size_t)L1 * L1);
+  for (int k = 0; k < L1; ++k)
+    for (int l = 0; l < L1; ++l) K1[k * L1 + l] = S.Ktau[k * L + L0 + l];
+  std::vector<double> F((size_t)L * d * nu), H((size_t)L * nu), V((size_t)L * d);
+  const int nr = nu + d;
+  for (int it = 0; it < S.P.niter; ++it) {
+    for (int l = 0; l < L; ++l) {
+      for (int mm = 0; mm < d; ++mm) flux(S.pde, d, S.P, &qhat[l * nu], mm, &F[((size_t)l * d + mm) * nu]);
+      mesh_velocity(mode, d, &qhat[l * nu], &V[l * d]);
+    }
+    for (int n = 0; n < L; ++n) {
+      // Jx[a][e] = d x_a / d xi_e of the isoparametric map at node n
+      double Jx[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, Ji[3][3];
+      for (int a = 0; a < d; ++a)
+        for (int e = 0; e < d; ++e) {
+          double s = 0.0;
+          for (int l = 0; l < L; ++l) s += dth[((size_t)e * L + n) * L + l] * xh[l * d + a];
+          Jx[a][e] = s;
+        }
+      inv3(Jx, d, Ji);  // Ji[e][a] = d xi_e / d x_a
+      for (int v = 0; v < nu; ++v) {
+        double h = 0.0;
+        for (int e = 0; e < d; ++e) {
+          double dq = 0.0;
+          for (int l = 0; l < L; ++l) dq += dth[((size_t)e * L + n) * L + l] * qhat[l * nu + v];
+          double dxidt = 0.0;
+          for (int a = 0; a < d; ++a) dxidt -= Ji[e][a] * V[n * d + a];
+          h += dq * dxidt;
+          for (int mm = 0; mm < d; ++mm) {
+            double dF = 0.0;
+            for (int l = 0; l < L; ++l) dF += dth[((size_t)e * L + n) * L + l] * F[((size_t)l * d + mm) * nu + v];
+            h += Ji[e][mm] * dF;
+          }
+        }
+        H[n * nu + v] = h;
+      }
+    }
+    std::vector<double> rhs((size_t)L1 * nr, 0.0);
+    for (int k = 0; k < L1; ++k) {
+      for (int v = 0; v < nu; ++v) {
+        double s = 0.0;
+        for (int l = 0; l < L; ++l) s -= dt * S.Mmat[k * L + l] * H[l * nu + v];
+        for (int l = 0; l < L0; ++l) s -= S.Ktau[k * L + l] * qhat[l * nu + v];
+        rhs[k * nr + v] = s;
+      }
+      for (int a = 0; a < d; ++a) {
+        double s = 0.0;
+        for (int l = 0; l < L; ++l) s += dt * S.Mmat[k * L + l] * V[l * d + a];
+        for (int l = 0; l < L0; ++l) s -= S.Ktau[k * L + l] * xh[l * d + a];
+        rhs[k * nr + nu + a] = s;
+      }
+    }
+    gauss_solve(L1, K1, rhs, nr);
+    for (int k = 0; k < L1; ++k) {
+      for (int v = 0; v < nu; ++v) qhat[(L0 + k) * nu + v] = rhs[k * nr + v];
+      for (int a = 0; a < d; ++a) xh[(L0 + k) * d + a] = rhs[k * nr + nu + a];
+    }
+  }
+  if (qbar && S.P.positivity) {
+    bool ok = true;
+    for (int l = L0; l < L; ++l) {
+      const double* q = &qhat[(size_t)l * nu];
+      bool fin = true;
+      for (int v = 0; v < nu; ++v) fin = fin && std::isfinite(q[v]);
+      if (!(fin && q[0] > 0.0 && pressure(S.pde, d, S.P, q) > 0.0)) ok = false;
+    }
+    if (!ok)
+      for (int l = 0; l < L; ++l)
+        for (int v = 0; v < nu; ++v) qhat[(size_t)l * nu + v] = qbar[v];
+  }
+  Vhat.assign((size_t)L * d, 0.0);
+  for (int l = 0; l < L; ++l) mesh_velocity(mode, d, &qhat[l * nu], &Vhat[l * d]);
+}
+
+// Time integrals of the nodal basis at the reference vertices, the weights
+// of Eq. (NodesVel): W[v][l] = int_0^1 theta_l(xi_v, tau) dtau with xi_0 = 0
+// and xi_v the v-th unit vector, integrated monomial by monomial.
+std::vector<double> ale_vertex_weights(const OSolver& S) {
+  int d = S.d, L = S.Lc;
+  std::vector<double> W((size_t)(d + 1) * L, 0.0);
+  for (int v = 0; v <= d; ++v) {
+    double xv[3] = {0, 0, 0};
+    if (v > 0) xv[v - 1] = 1.0;
+    for (int l = 0; l < L; ++l) {
+      double s = 0.0;
+      for (const Term& t : S.theta[l])
+        s += t.c * ipow_d(xv[0], t.e[0]) * ipow_d(xv[1], t.e[1]) * ipow_d(xv[2], t.e[2]) / (t.e[3] + 1);
+      W[(size_t)v * L + l] = s;
+    }
+  }
+  return W;
+}
+
+// Space-time normal of a lateral face, Eqs. (SurfPar)-(detChi), d = 2.  The
+// face is the segment A-B at t^n (XA0, XB0) moving on straight lines to
+// (XA1, XB1) at t^{n+1}; x(chi, tau) is the bilinear map of Eq. (SurfPar)
+// and t = t^n + tau dt.  The rows of the matrix of Eq. (ChiTransf) below the
+// unit vectors are (dx/dchi, dt/dchi = 0) and (dx/dtau, dt/dtau = dt); the
+// normal is the cofactor expansion along the first row, (x, y, t) order.
+void st_normal(const double* XA0, const double* XB0, const double* XA1, const double* XB1, double chi, double tau,
+               double dt, double* n) {
+  double r1[3], r2[3];
+  for (int a = 0; a < 2; ++a) {
+    r1[a] = (1.0 - tau) * (XB0[a] - XA0[a]) + tau * (XB1[a] - XA1[a]);
+    r2[a] = (1.0 - chi) * (XA1[a] - XA0[a]) + chi * (XB1[a] - XB0[a]);
+  }
+  r1[2] = 0.0;
+  r2[2] = dt;
+  // (-1)^(1+p) times the minor that deletes column p
+  n[0] = r1[1] * r2[2] - r1[2] * r2[1];
+  n[1] = -(r1[0] * r2[2] - r1[2] * r2[0]);
+  n[2] = r1[0] * r2[1] - r1[1] * r2[0];
+}
+
+// Reference coordinates in cell c of the point at parameter chi on the
+// segment from global vertex ga to global vertex gb of that cell: the
+// lateral face (chi, tau) sits at the same reference point at every tau.
+void ref_on_edge(const OMesh& m, long c, long ga, long gb, double chi, double* xi) {
+  int d = m.d;
+  double pa[3] = {0, 0, 0}, pb[3] = {0, 0, 0};
+  for (int k = 0; k <= d; ++k) {
+    long g = m.cells[c * (d + 1) + k];
+    if (k > 0 && g == ga) pa[k - 1] = 1.0;
+    if (k > 0 && g == gb) pb[k - 1] = 1.0;
+  }
+  for (int a = 0; a < 3; ++a) xi[a] = pa[a] + chi * (pb[a] - pa[a]);
+}
+
+// One direct ALE ADER-CWENO step on the solver's current mesh:
+//   1. reconstruction (fixed stencils, matrices of the current geometry) and
+//      the moving-element predictor of every cell;
+//   2. nodal solver, Eqs. (NScs), (NScs.weights), (NodesVel): the velocity
+//      of vertex k is the mass-weighted mean over its cells j of the time
+//      integral of the predictor's mesh velocity at that vertex, with masses
+//      rho_j^n |T_j^n| and cells visited in increasing index; new positions
+//      by Eq. (newX);
+//   3. the space-time control volumes of Eq. (dCi): bottom T_i^n, top
+//      T_i^{n+1}, lateral faces (SurfPar) with normals (detChi);
+//   4. Eq. (PDEfinal): |T_i^{n+1}| Q_i^{n+1} = |T_i^n| Q_i^n minus the
+//      lateral-face integrals of the Rusanov flux of Eq. (rusanov),
+//      (F~(q+) + F~(q-)) . n~ / 2 - s_max (q+ - q-) / 2 with
+//      F~ = (f, g, Q), s_max = |n~_x| max over both sides of |v.n - V.n| + c
+//      (the largest eigenvalue of the ALE Jacobian A_n^V), V.n = -n~_t/|n~_x|
+//      the face's own normal velocity; Gauss-Legendre with M+1 points in chi
+//      and in tau.  Transmissive boundary: q+ = q-.
+// Qnew: nc x nu; xyz_new: nv x d.  The mesh is not moved (ale_move does).
+bool ale_step(OSolver& S, const double* Q, double dt, int mode, double* Qnew, double* xyz_new, std::string& err) {
+  OMesh& m = *S.mesh;
+  int d = m.d, nu = S.nu, L = S.Lc, M = S.M;
+  if (d != 2 || S.pde != PDE_EULER || S.P.flux != 0) {
+    err = "moving meshes: two dimensions, Euler equations, Rusanov flux";
+    return false;
+  }
+  std::vector<std::vector<double>> pred(m.nc), Vh(m.nc);
+  for (long c = 0; c < m.nc; ++c) {
+    RecOut R;
+    if (!reconstruct_cell(S, Q, c, R, err)) return false;
+    ale_predictor_cell(S, c, R.w, dt, mode, pred[c], Vh[c], &Q[c * nu]);
+  }
+  // nodal solver
+  std::vector<double> W = ale_vertex_weights(S);
+  std::vector<double> acc((size_t)m.nv * d, 0.0), mu(m.nv, 0.0);
+  for (long c = 0; c < m.nc; ++c) {
+    double mass = Q[c * nu] * m.vol[c];
+    for (int k = 0; k <= d; ++k) {
+      long g = m.cells[c * (d + 1) + k];
+      for (int a = 0; a < d; ++a) {
+        double vkj = 0.0;
+        for (int l = 0; l < L; ++l) vkj += W[(size_t)k * L + l] * Vh[c][(size_t)l * d + a];
+        acc[g * d + a] += mass * vkj;
+      }
+      mu[g] += mass;
+    }
+  }
+  for (long g = 0; g < m.nv; ++g)
+    for (int a = 0; a < d; ++a) xyz_new[g * d + a] = m.xyz[g * d + a] + dt * (acc[g * d + a] / mu[g]);
+  // geometry at t^{n+1}
+  OMesh m1 = m;
+  m1.xyz.assign(xyz_new, xyz_new + m.nv * d);
+  if (!mesh_geometry(m1, err)) {
+    err = "moving mesh: " + err;
+    return false;
+  }
+  std::vector<double> gx, gw;
+  gauss_legendre01(M + 1, gx, gw);
+  std::vector<double> qm(nu), qp(nu), f(nu), g(nu);
+  for (long i = 0; i < m.nc; ++i) {
+    std::vector<double> accq(nu, 0.0);
+    for (int k = 0; k <= d; ++k) {
+      long j = m.nbr[i * (d + 1) + k];
+      // face vertices (local a, b of cell i), A the lower global id
+      int la = (k + 1) % 3, lb = (k + 2) % 3;
+      long ga = m.cells[i * (d + 1) + la], gb = m.cells[i * (d + 1) + lb];
+      if (ga > gb) {
+        std::swap(ga, gb);
+        std::swap(la, lb);
+      }
+      const double XA0[2] = {vx(m, i, la, 0), vx(m, i, la, 1)}, XB0[2] = {vx(m, i, lb, 0), vx(m, i, lb, 1)};
+      const double XA1[2] = {vx(m1, i, la, 0), vx(m1, i, la, 1)}, XB1[2] = {vx(m1, i, lb, 0), vx(m1, i, lb, 1)};
+      // outward orientation from cell i at t^n
+      double n0[3];
+      st_normal(XA0, XB0, XA1, XB1, 0.0, 0.0, dt, n0);
+      double sgn = n0[0] * (XA0[0] - m.bary[i * 3]) + n0[1] * (XA0[1] - m.bary[i * 3 + 1]) > 0 ? 1.0 : -1.0;
+      for (int q = 0; q <= M; ++q) {
+        double xi_i[3], xi_j[3];
+        ref_on_edge(m, i, ga, gb, gx[q], xi_i);
+        if (j >= 0) ref_on_edge(m, j, ga, gb, gx[q], xi_j);
+        for (int t = 0; t <= M; ++t) {
+          double nt[3];
+          st_normal(XA0, XB0, XA1, XB1, gx[q], gx[t], dt, nt);
+          for (int a = 0; a < 3; ++a) nt[a] *= sgn;
+          double xt[4] = {xi_i[0], xi_i[1], xi_i[2], gx[t]};
+          eval_qh(S, pred[i], xt, qm.data());
+          if (j >= 0) {
+            double xtj[4] = {xi_j[0], xi_j[1], xi_j[2], gx[t]};
+            eval_qh(S, pred[j], xtj, qp.data());
+          } else {
+            qp = qm;
+          }
+          if (S.P.positivity) {
+            if (!(qm[0] > 0.0 && pressure(S.pde, d, S.P, qm.data()) > 0.0))
+              for (int v = 0; v < nu; ++v) qm[v] = Q[i * nu + v];
+            if (!(qp[0] > 0.0 && pressure(S.pde, d, S.P, qp.data()) > 0.0))
+              for (int v = 0; v < nu; ++v) qp[v] = j >= 0 ? Q[j * nu + v] : Q[i * nu + v];
+          }
+          double nx = std::sqrt(nt[0] * nt[0] + nt[1] * nt[1]);
+          double un[2] = {nt[0] / nx, nt[1] / nx};
+          double Vn = -nt[2] / nx;
+          double sm = 0.0;
+          for (const double* qs : {qm.data(), qp.data()}) {
+            double vn = (qs[1] * un[0] + qs[2] * un[1]) / qs[0];
+            double c = max_speed_normal(S.pde, d, S.P, qs, un) - std::fabs(vn);  // sound speed
+            sm = std::max(sm, std::fabs(vn - Vn) + c);
+          }
+          sm *= nx;
+          std::vector<double> G(nu, 0.0);
+          for (int mm = 0; mm < d; ++mm) {
+            flux(S.pde, d, S.P, qm.data(), mm, f.data());
+            flux(S.pde, d, S.P, qp.data(), mm, g.data());
+            for (int v = 0; v < nu; ++v) G[v] += 0.5 * (f[v] + g[v]) * nt[mm];
+          }
+          for (int v = 0; v < nu; ++v) G[v] += 0.5 * (qm[v] + qp[v]) * nt[2] - 0.5 * sm * (qp[v] - qm[v]);
+          for (int v = 0; v < nu; ++v) accq[v] += gw[q] * gw[t] * G[v];
+        }
+      }
+    }
+    for (int v = 0; v < nu; ++v) Qnew[i * nu + v] = (m.vol[i] * Q[i * nu + v] - accq[v]) / m1.vol[i];
+  }
+  return true;
+}
+
+// Move the mesh to new vertex positions (same topology) and rebuild every
+// cell's geometry-dependent matrices for its fixed stencils.
+bool ale_move(OSolver& S, const double* xyz, std::string& err) {
+  OMesh& m = *S.mesh;
+  m.xyz.assign(xyz, xyz + m.nv * m.d);
+  if (!mesh_geometry(m, err)) return false;
+  for (auto& kv : S.cache) cell_matrices(S, kv.first, kv.second);
+  return true;
+}
+
 }  // namespace
 
 // ============================================================================
@@ -1972,6 +2338,64 @@ int orc_face_points(void* p, int64_t cell, int k, double* pts, double* wts, doub
     wts[q] = W[q];
   }
   return (int)P.size();
+}
+
+
+// Direct ALE step (two dimensions, Euler, Rusanov): Qnew (nc x nu) and the
+// new vertex positions xyz_new (nv x d); the oracle's mesh is then moved to
+// them (stencils fixed, matrices rebuilt).  mode: 1 V = v, 2 V = 0.
+int orc_ale_step(void* p, const double* Q, double dt, int mode, double* Qnew, double* xyz_new, char* err,
+                 int errlen) {
+  OSolver* S = (OSolver*)p;
+  std::string e;
+  if (mode != ALE_LAGRANGE && mode != ALE_STILL) {
+    set_err(err, errlen, "unknown mesh-velocity mode");
+    return -1;
+  }
+  if (!ale_step(*S, Q, dt, mode, Qnew, xyz_new, e) || !ale_move(*S, xyz_new, e)) {
+    set_err(err, errlen, e);
+    return -1;
+  }
+  return 0;
+}
+
+// Moving-element predictor of one cell from its reconstruction: qhat (L x nu)
+// and the nodal mesh velocities Vhat (L x d).
+int orc_ale_predictor(void* p, const double* Q, double dt, int mode, int64_t cell, double* qhat, double* Vhat,
+                      char* err, int errlen) {
+  OSolver* S = (OSolver*)p;
+  RecOut R;
+  std::string e;
+  if (!reconstruct_cell(*S, Q, cell, R, e)) {
+    set_err(err, errlen, e);
+    return -1;
+  }
+  std::vector<double> qh, vh;
+  ale_predictor_cell(*S, cell, R.w, dt, mode, qh, vh, &Q[cell * S->nu]);
+  std::memcpy(qhat, qh.data(), sizeof(double) * qh.size());
+  std::memcpy(Vhat, vh.data(), sizeof(double) * vh.size());
+  return 0;
+}
+
+// W[(d+1) x L], Eq. (NodesVel)
+int orc_ale_vertex_weights(void* p, double* W) {
+  std::vector<double> w = ale_vertex_weights(*(OSolver*)p);
+  std::memcpy(W, w.data(), sizeof(double) * w.size());
+  return 0;
+}
+
+// Space-time normal of a lateral face, Eq. (detChi), d = 2: n[3] = (x, y, t).
+int orc_st_normal(const double* XA0, const double* XB0, const double* XA1, const double* XB1, double chi,
+                  double tau, double dt, double* n) {
+  st_normal(XA0, XB0, XA1, XB1, chi, tau, dt, n);
+  return 0;
+}
+
+// Current vertex positions of the oracle's mesh (nv x d).
+int orc_mesh_xyz(void* p, double* xyz) {
+  OMesh* m = (OMesh*)p;
+  std::memcpy(xyz, m->xyz.data(), sizeof(double) * m->xyz.size());
+  return 0;
 }
 
 }  // extern "C"
