@@ -53,6 +53,14 @@ enum { CWENO_EULER = 0, CWENO_MHD_GLM = 1 };
 enum { CWENO_FP64 = 0, CWENO_FP32_MIXED = 1 };
 /* Numerical flux at the space-time face points. */
 enum { CWENO_FLUX_RUSANOV = 0, CWENO_FLUX_OSHER = 1, CWENO_FLUX_RUSANOV_QF = 2 };
+/* Mesh motion (Secs. 2.3-2.4).  FIXED: the Eulerian scheme on the given
+ * mesh.  LAGRANGE: the direct ALE scheme with mesh velocity V = v, the local
+ * fluid velocity (the paper's choice for its moving-mesh tests): predictor on
+ * the moving element (Eqs. CGfinal, ODEfinal), nodal solver (Eqs. NScs to
+ * newX), space-time control volumes (Eqs. dCi to detChi), update of Eq.
+ * (PDEfinal).  STILL: the same ALE machinery with V = 0 (it reduces to the
+ * Eulerian scheme; a check of the moving-mesh path). */
+enum { CWENO_MOTION_FIXED = 0, CWENO_MOTION_LAGRANGE = 1, CWENO_MOTION_STILL = 2 };
 
 typedef struct cweno_mesh cweno_mesh;
 typedef struct cweno_solver cweno_solver;
@@ -75,7 +83,7 @@ typedef struct {
   int picard_iters;    /* iterations of Eq. (CGfinal); <= 0 -> M + 1 */
   int linear_weights;  /* test mode: omega := lambda (no indicators) */
   int positivity;      /* 1 (default): scale w toward the cell average where
-                          density or pressure would fall below 1e-6 of their
+                          density or pressure would fall below 1e-3 of their
                           cell-average values at a lattice node (Zhang & Shu
                           scaling; not part of the paper, inactive wherever the
                           reconstruction is admissible); 0: the paper's scheme */
@@ -90,6 +98,12 @@ typedef struct {
                           and time step, Rusanov dissipation with the
                           signal speed of the two sides' space-time face
                           averages */
+  int mesh_motion;     /* CWENO_MOTION_FIXED (default), _LAGRANGE or _STILL.
+                          Moving meshes: dim 2, Euler, FP64, order 2..4,
+                          Rusanov flux (EINVAL otherwise); the stencils are
+                          chosen on the initial mesh and kept (the topology
+                          never changes), their least-squares and sector
+                          matrices are rebuilt on the device every step */
 } cweno_params;
 
 /* Fill *p with the paper's defaults for dimension `dim` and `pde`. */
@@ -126,6 +140,12 @@ int cweno_mesh_info(const cweno_mesh* m, int64_t* ncells, int64_t* nfaces, int64
  * (Sec. 2.1 cone rule), -1 where a sector is dropped.  `order` 2..5 in
  * 2D, 2..4 in 3D.  Errors as cweno_setup. */
 int cweno_mesh_stencils(const cweno_mesh* m, int order, int32_t* S0, int32_t* sec);
+
+/* Current vertex positions, nv x dim FP64 in the caller's vertex order
+ * (they move under CWENO_MOTION_LAGRANGE; otherwise the mesh's own).
+ * on_device selects a device or host destination.  EINVAL for a solver of
+ * a fixed mesh.  Synchronous. */
+int cweno_get_vertices(cweno_solver* s, double* xyz, int on_device);
 
 /* Reconstruction setup for `order` = M + 1 in 2..5 (Sec. 2.1): central
  * stencils S_i^0 of n_e = d * M(M,d) cells (Eq. stencil), d+1 sectorial
@@ -176,7 +196,8 @@ int cweno_reconstruct(cweno_solver* s, double* w_nodal, int on_device);
 /* Space-time predictor of the current state for time step dt (Eq. CGfinal),
  * nodal values at the L space-time nodes (principal lattice of the
  * (d+1)-simplex, step 1/M, time level tau = t/M outermost), written as
- * qhat[(c * L + node) * nvars + v].  Diagnostic; synchronous. */
+ * qhat[(c * L + node) * nvars + v].  Diagnostic; synchronous.  EINVAL on
+ * a moving mesh (its predictor is internal to the ALE step). */
 int cweno_predictor(cweno_solver* s, double dt, double* qhat, int on_device);
 
 /* Global time step of Eq. (timestep) for the current state:
@@ -187,15 +208,20 @@ int cweno_stable_dt(cweno_solver* s, double cfl, double* dt);
 /* One ADER-CWENO step of length dt (Eq. PDEfinal, Eulerian).  dt <= 0 uses
  * the CFL bound of the current state, computed on the device (no host
  * round trip; the bound for the following step is produced by the update).
- * Asynchronous. */
+ * On a moving mesh (mesh_motion != FIXED) one direct ALE step: geometry and
+ * reconstruction matrices of the current mesh, moving-element predictor,
+ * nodal solver and new vertices, space-time face fluxes, volume-weighted
+ * update; dt <= 0 takes the CFL bound on the current mesh.  Asynchronous. */
 int ader_cweno_step(cweno_solver* s, double dt);
 
 /* `nsteps` steps as above; the sequence is captured once into a CUDA graph
- * per solver and replayed.  Asynchronous. */
+ * per solver and replayed (moving meshes: plain launches).  Asynchronous. */
 int ader_cweno_run(cweno_solver* s, int nsteps, double dt);
 
 /* Wait for the solver's stream.  Returns ENAN if any step since the last
- * set_state produced NaN or non-positive density / pressure. */
+ * set_state produced NaN or non-positive density / pressure (on a moving
+ * mesh also a cell of non-positive area), EDEGENERATE if a moving mesh made
+ * a least-squares or sector system singular. */
 int cweno_sync(cweno_solver* s);
 /* Simulated time accumulated since set_state (synchronous). */
 int cweno_get_time(cweno_solver* s, double* t);

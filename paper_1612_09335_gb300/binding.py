@@ -18,6 +18,7 @@ from . import _build
 EULER, MHD_GLM = 0, 1
 FP64, FP32_MIXED = 0, 1
 FLUX_RUSANOV, FLUX_OSHER, FLUX_RUSANOV_QF = 0, 1, 2
+MOTION_FIXED, MOTION_LAGRANGE, MOTION_STILL = 0, 1, 2
 OK, EINVAL, EDEGENERATE, ENOMEM, EBUSY, ENAN, ETIMEDOUT, ECUDA, ENOTFOUND = 0, -1, -2, -3, -4, -5, -6, -7, -8
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_ERROR = 0, 1, 2, 3
 
@@ -31,7 +32,8 @@ class CwenoError(RuntimeError):
 class cweno_params(C.Structure):
     _fields_ = [("eps", C.c_double), ("r", C.c_double), ("lambda0", C.c_double), ("lambda_s", C.c_double),
                 ("gamma", C.c_double), ("c_h", C.c_double), ("cfl", C.c_double), ("picard_iters", C.c_int),
-                ("linear_weights", C.c_int), ("positivity", C.c_int), ("flux", C.c_int)]
+                ("linear_weights", C.c_int), ("positivity", C.c_int), ("flux", C.c_int),
+                ("mesh_motion", C.c_int)]
 
 
 class cweno_request(C.Structure):
@@ -69,6 +71,7 @@ SIGNATURES = [
     ("ader_cweno_run", _I, [_P, _I, _D]),
     ("cweno_sync", _I, [_P]),
     ("cweno_get_time", _I, [_P, _DP]),
+    ("cweno_get_vertices", _I, [_P, _P, _I]),
     ("cweno_stream", _P, [_P]),
     ("cweno_profile_enable", _I, [_P, _I]),
     ("cweno_profile_read", _I, [_P, _DP, _I64P]),
@@ -164,6 +167,7 @@ class Mesh:
         self.dim = dim
         self.h = cweno_mesh_create(dim, xyz, cells, period)
         self.nc = int(np.asarray(cells).shape[0])
+        self.nv = int(np.asarray(xyz).shape[0])
 
     @classmethod
     def from_workload(cls, m):
@@ -264,6 +268,14 @@ class Solver:
         t = C.c_double()
         _check(lib().cweno_get_time(self.h, C.byref(t)))
         return t.value
+
+    def get_vertices(self, out=None):
+        """Current vertex positions (moving meshes), nv x dim."""
+        if out is None:
+            out = np.zeros((self.mesh.nv, self.mesh.dim))
+        p, dev = _ptr(out)
+        _check(lib().cweno_get_vertices(self.h, p, dev))
+        return out
 
     def stream(self) -> int:
         return lib().cweno_stream(self.h) or 0

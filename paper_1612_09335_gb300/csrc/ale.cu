@@ -1,0 +1,630 @@
+// Moving meshes: the direct ALE ADER-CWENO step (Secs. 2.2-2.4) on 2D
+// triangle meshes, Euler equations, FP64, Rusanov flux with the ALE
+// Jacobian.  Mesh velocity V = v (the local fluid velocity, the choice of the
+// paper's moving-mesh tests) or V = 0 (the same machinery on a mesh that does
+// not move).  One step:
+//   k_ale_geom      cell geometry of the current vertices (unwrapped
+//                   vertices, |T|, barycentre, h, 1/|T|);
+//   matrices        least-squares pseudo-inverses and sector inverses for
+//                   the fixed stencils, rebuilt on the device every step
+//                   (Sec. 2.1: on moving meshes they change with the mesh);
+//   reconstruction  the fixed-mesh CWENO kernel (rows a2-a6), values at the
+//                   lattice nodes;
+//   k_ale_pred      space-time predictor on the moving element: state and
+//                   geometry DOFs iterated together (Eqs. CGfinal, ODEfinal)
+//                   with H of Eq. (Hterm) from the nodal derivatives;
+//   k_ale_nodes     nodal solver, Eqs. (NScs)-(newX), one thread per vertex
+//                   over a fixed incidence list (increasing cell order, so
+//                   the sums are deterministic);
+//   k_ale_flux      lateral space-time faces, normals of Eq. (detChi),
+//                   Rusanov flux of Eq. (rusanov) with s_max of A_n^V;
+//   k_ale_update    Eq. (PDEfinal): |T^{n+1}| Q^{n+1} = |T^n| Q^n - sum.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/cweno.h"
+#include "ale.h"
+
+namespace cw {
+
+constexpr int kLmax = 20, kL0max = 10, kL1max = 10, kNQ = 4;
+
+// Reference tables of one M (2D), passed as a kernel parameter.
+struct AleTab {
+  double Dxi[2][kLmax][kLmax];  // d theta_l / d xi_e at node n: [e][n][l]
+  double Gal[kL1max][kLmax];    // (K_tau^1)^-1 M^1
+  double C0[kL1max][kL0max];    // theta_n(xi_k, 0): constant extension in time
+  double Wv[3][kLmax];          // int_0^1 theta_l(vertex v, tau) dtau
+  double node[kLmax][3];        // xi, eta, tau
+  double chi[kNQ], wq[kNQ], wt[kNQ], tq[kNQ];
+  double gamma;
+  int mode;  // CWENO_MOTION_LAGRANGE or CWENO_MOTION_STILL
+  int pos;   // positivity switch (fallbacks as on fixed meshes)
+};
+
+namespace {
+
+__host__ __device__ constexpr int lcal2(int M) { return (M + 1) * (M + 2) * (M + 3) / 6; }
+__host__ __device__ constexpr int mcal2(int M) { return (M + 1) * (M + 2) / 2; }
+
+__device__ __forceinline__ double step_dt(double dt_fixed, double cfl, const unsigned long long* dtmin) {
+  return dt_fixed > 0.0 ? dt_fixed : cfl * __longlong_as_double((long long)dtmin[0]);
+}
+
+__device__ __forceinline__ double pressure(const double* q, double g) {
+  return (g - 1.0) * (q[3] - 0.5 * (q[1] * q[1] + q[2] * q[2]) / q[0]);
+}
+
+__device__ __forceinline__ bool admissible(const double* q, double g) {
+  bool fin = isfinite(q[0]) && isfinite(q[1]) && isfinite(q[2]) && isfinite(q[3]);
+  return fin && q[0] > 0.0 && pressure(q, g) > 0.0;
+}
+
+// ---------------------------------------------------------------- geometry
+// Per cell: vertices Xv[g] + the cell's periodic image shift, |T|, the
+// barycentre, h = 4|T| / perimeter (incircle diameter, Eq. timestep), 1/|T|.
+__global__ void __launch_bounds__(256) k_ale_geom(const double* __restrict__ Xv, const int32_t* __restrict__ gv,
+                                                  const double* __restrict__ shift, int64_t N, double* __restrict__ X,
+                                                  double* __restrict__ bary, double* __restrict__ vol,
+                                                  double* __restrict__ hsize, double* __restrict__ invvol) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double P[3][2];
+  for (int k = 0; k < 3; ++k) {
+    const int64_t g = gv[k * N + i];
+    for (int a = 0; a < 2; ++a) {
+      P[k][a] = Xv[g * 2 + a] + shift[(k * 2 + a) * N + i];
+      X[i * 9 + k * 3 + a] = P[k][a];
+    }
+    X[i * 9 + k * 3 + 2] = 0.0;
+  }
+  const double det = (P[1][0] - P[0][0]) * (P[2][1] - P[0][1]) - (P[2][0] - P[0][0]) * (P[1][1] - P[0][1]);
+  const double v = det / 2.0;
+  double per = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    const int a = k == 0 ? 1 : 0, b = k == 2 ? 1 : 2;
+    per += hypot(P[b][0] - P[a][0], P[b][1] - P[a][1]);
+  }
+  vol[i] = v;
+  hsize[i] = 4.0 * v / per;
+  invvol[i] = 1.0 / v;
+  for (int a = 0; a < 2; ++a) bary[i * 3 + a] = (P[0][a] + P[1][a] + P[2][a]) / 3.0;
+  bary[i * 3 + 2] = 0.0;
+}
+
+// Reset of the time-step bound of slot 0 before it is recomputed.
+__global__ void k_ale_dt_reset(unsigned long long* dtmin) { dtmin[0] = 0x7ff0000000000000ull; }
+
+// ---------------------------------------------------------------- predictor
+// One thread per cell.  w: reconstruction values at the lattice nodes
+// (N x L0 x 4); X: unwrapped vertices of T_i^n.  Writes q_hat (N x L x 4) and,
+// per vertex k of the cell, (mu V_kj, mu) with mu = rho_j |T_j| and V_kj the
+// time integral of the predictor's mesh velocity at that vertex.
+template <int M>
+__global__ void __launch_bounds__(128) k_ale_pred(const __grid_constant__ AleTab t, const double* __restrict__ w,
+                                                  const double* __restrict__ Q, const double* __restrict__ X,
+                                                  const double* __restrict__ vol, int64_t N, int niter,
+                                                  double dt_fixed, double cfl, const unsigned long long* dtmin,
+                                                  double* __restrict__ qhat, double* __restrict__ vcon) {
+  constexpr int L = lcal2(M), L0 = mcal2(M), L1 = L - L0;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double dt = step_dt(dt_fixed, cfl, dtmin);
+  double q[L][4], x[L][2];
+  for (int n = 0; n < L0; ++n)
+    for (int v = 0; v < 4; ++v) q[n][v] = w[(i * L0 + n) * 4 + v];
+  for (int k = 0; k < L1; ++k)
+    for (int v = 0; v < 4; ++v) {
+      double s = 0.0;
+      for (int n = 0; n < L0; ++n) s += t.C0[k][n] * q[n][v];
+      q[L0 + k][v] = s;
+    }
+  const double* Xi = X + i * 9;
+  for (int l = 0; l < L; ++l)
+    for (int a = 0; a < 2; ++a)
+      x[l][a] = Xi[a] + (Xi[3 + a] - Xi[a]) * t.node[l][0] + (Xi[6 + a] - Xi[a]) * t.node[l][1];
+  double V[L][2];
+  for (int it = 0; it < niter; ++it) {
+    double F[L][2][4];
+    for (int l = 0; l < L; ++l) {
+      const double r = q[l][0], u = q[l][1] / r, vv = q[l][2] / r;
+      const double p = pressure(q[l], t.gamma);
+      F[l][0][0] = q[l][1];
+      F[l][0][1] = q[l][1] * u + p;
+      F[l][0][2] = q[l][2] * u;
+      F[l][0][3] = u * (q[l][3] + p);
+      F[l][1][0] = q[l][2];
+      F[l][1][1] = q[l][1] * vv;
+      F[l][1][2] = q[l][2] * vv + p;
+      F[l][1][3] = vv * (q[l][3] + p);
+      V[l][0] = t.mode == CWENO_MOTION_LAGRANGE ? u : 0.0;
+      V[l][1] = t.mode == CWENO_MOTION_LAGRANGE ? vv : 0.0;
+    }
+    double H[L][4];
+    for (int n = 0; n < L; ++n) {
+      // d x / d xi of the isoparametric map at node n, and its inverse
+      double J[2][2];
+      for (int a = 0; a < 2; ++a)
+        for (int e = 0; e < 2; ++e) {
+          double s = 0.0;
+          for (int l = 0; l < L; ++l) s += t.Dxi[e][n][l] * x[l][a];
+          J[a][e] = s;
+        }
+      const double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+      const double Ji[2][2] = {{J[1][1] / det, -J[0][1] / det}, {-J[1][0] / det, J[0][0] / det}};
+      double dxidt[2];
+      for (int e = 0; e < 2; ++e) dxidt[e] = -(Ji[e][0] * V[n][0] + Ji[e][1] * V[n][1]);
+      for (int v = 0; v < 4; ++v) {
+        double h = 0.0;
+        for (int e = 0; e < 2; ++e) {
+          double dq = 0.0, df0 = 0.0, df1 = 0.0;
+          for (int l = 0; l < L; ++l) {
+            const double dd = t.Dxi[e][n][l];
+            dq += dd * q[l][v];
+            df0 += dd * F[l][0][v];
+            df1 += dd * F[l][1][v];
+          }
+          h += dq * dxidt[e] + Ji[e][0] * df0 + Ji[e][1] * df1;
+        }
+        H[n][v] = h;
+      }
+    }
+    for (int k = 0; k < L1; ++k) {
+      double qn[4], xn[2];
+      for (int v = 0; v < 4; ++v) {
+        double s = 0.0, g = 0.0;
+        for (int n = 0; n < L0; ++n) s += t.C0[k][n] * q[n][v];
+        for (int l = 0; l < L; ++l) g += t.Gal[k][l] * H[l][v];
+        qn[v] = s - dt * g;
+      }
+      for (int a = 0; a < 2; ++a) {
+        double s = 0.0, g = 0.0;
+        for (int n = 0; n < L0; ++n) s += t.C0[k][n] * x[n][a];
+        for (int l = 0; l < L; ++l) g += t.Gal[k][l] * V[l][a];
+        xn[a] = s + dt * g;
+      }
+      // the right-hand sides read only tau = 0 nodes and H, V: update in place
+      for (int v = 0; v < 4; ++v) q[L0 + k][v] = qn[v];
+      for (int a = 0; a < 2; ++a) x[L0 + k][a] = xn[a];
+    }
+  }
+  double qb[4];
+  for (int v = 0; v < 4; ++v) qb[v] = Q[v * N + i];
+  if (t.pos) {
+    bool ok = true;
+    for (int l = L0; l < L; ++l) ok = ok && admissible(q[l], t.gamma);
+    if (!ok)
+      for (int l = 0; l < L; ++l)
+        for (int v = 0; v < 4; ++v) q[l][v] = qb[v];
+  }
+  for (int l = 0; l < L; ++l) {
+    for (int v = 0; v < 4; ++v) qhat[(i * L + l) * 4 + v] = q[l][v];
+    V[l][0] = t.mode == CWENO_MOTION_LAGRANGE ? q[l][1] / q[l][0] : 0.0;
+    V[l][1] = t.mode == CWENO_MOTION_LAGRANGE ? q[l][2] / q[l][0] : 0.0;
+  }
+  const double mu = qb[0] * vol[i];
+  for (int k = 0; k < 3; ++k) {
+    for (int a = 0; a < 2; ++a) {
+      double s = 0.0;
+      for (int l = 0; l < L; ++l) s += t.Wv[k][l] * V[l][a];
+      vcon[(i * 3 + k) * 3 + a] = mu * s;
+    }
+    vcon[(i * 3 + k) * 3 + 2] = mu;
+  }
+}
+
+// ------------------------------------------------------------- nodal solver
+// One thread per vertex: V_k = sum mu V_kj / sum mu over the incident cells
+// (entries ent[start[g] .. start[g+1]) = cell * 3 + local vertex, in
+// increasing caller cell order), X^{n+1} = X^n + dt V_k.
+__global__ void __launch_bounds__(256) k_ale_nodes(const int32_t* __restrict__ start, const int32_t* __restrict__ ent,
+                                                   const double* __restrict__ vcon, const double* __restrict__ Xv,
+                                                   int64_t nvert, double dt_fixed, double cfl,
+                                                   const unsigned long long* dtmin, double* __restrict__ Xv1) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= nvert) return;
+  const double dt = step_dt(dt_fixed, cfl, dtmin);
+  double ax = 0.0, ay = 0.0, mu = 0.0;
+  for (int32_t e = start[g]; e < start[g + 1]; ++e) {
+    const double* c = vcon + (int64_t)ent[e] * 3;
+    ax += c[0];
+    ay += c[1];
+    mu += c[2];
+  }
+  Xv1[g * 2] = mu > 0.0 ? Xv[g * 2] + dt * (ax / mu) : Xv[g * 2];
+  Xv1[g * 2 + 1] = mu > 0.0 ? Xv[g * 2 + 1] + dt * (ay / mu) : Xv[g * 2 + 1];
+}
+
+// -------------------------------------------------------------------- faces
+struct FaceGeo {
+  double A0[2], B0[2], A1[2], B1[2];
+};
+
+// Space-time normal (x, y, t) at (chi, tau) of the face moving on straight
+// lines from A0-B0 to A1-B1 over dt: cross product of d x/d chi = (e, 0) and
+// d x/d tau = (w, dt), the cofactor expansion of Eq. (detChi).
+__device__ __forceinline__ void st_normal(const FaceGeo& f, double chi, double tau, double dt, double* n) {
+  double e[2], w[2];
+  for (int a = 0; a < 2; ++a) {
+    e[a] = (1.0 - tau) * (f.B0[a] - f.A0[a]) + tau * (f.B1[a] - f.A1[a]);
+    w[a] = (1.0 - chi) * (f.A1[a] - f.A0[a]) + chi * (f.B1[a] - f.B0[a]);
+  }
+  n[0] = e[1] * dt;
+  n[1] = -(e[0] * dt);
+  n[2] = e[0] * w[1] - e[1] * w[0];
+}
+
+// One thread per face: the integral over the lateral space-time face of the
+// Rusanov flux, (F~(q+) + F~(q-)).n~/2 - s_max (q+ - q-)/2 with F~ = (f, g, Q)
+// and s_max = |n~_x| max(|v.n - V.n| + c) over both sides, V.n = -n~_t/|n~_x|;
+// Gauss-Legendre in chi and tau.  Traces from the face basis table of each
+// side's face code (points ordered from the lower to the higher global
+// vertex id).  Transmissive boundary: q+ = q-.  Positivity switch: an
+// inadmissible trace is replaced by that side's cell average.
+template <int M>
+__global__ void __launch_bounds__(128) k_ale_flux(const __grid_constant__ AleTab t, const double* __restrict__ ftab,
+                                                  const int32_t* __restrict__ fL, const int32_t* __restrict__ fR,
+                                                  const uint8_t* __restrict__ codeL, const uint8_t* __restrict__ codeR,
+                                                  const int32_t* __restrict__ gv, const double* __restrict__ shift,
+                                                  const double* __restrict__ Xv, const double* __restrict__ Xv1,
+                                                  const double* __restrict__ bary, const double* __restrict__ qhat,
+                                                  const double* __restrict__ Q, int64_t N, int64_t F,
+                                                  double dt_fixed, double cfl, const unsigned long long* dtmin,
+                                                  double* __restrict__ G) {
+  constexpr int L = lcal2(M), NQ = M + 1;
+  const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= F) return;
+  const double dt = step_dt(dt_fixed, cfl, dtmin);
+  const int64_t cl = fL[f], cr = fR[f];
+  const int kL = codeL[f], kR = cr >= 0 ? codeR[f] : 0;
+  const int lf = kL / 2;
+  int la = (lf + 1) % 3, lb = (lf + 2) % 3;
+  int64_t ga = gv[la * N + cl], gb = gv[lb * N + cl];
+  if (ga > gb) {
+    const int64_t tg = ga;
+    ga = gb;
+    gb = tg;
+    const int tl = la;
+    la = lb;
+    lb = tl;
+  }
+  FaceGeo fg;
+  for (int a = 0; a < 2; ++a) {
+    const double sa = shift[(la * 2 + a) * N + cl], sb = shift[(lb * 2 + a) * N + cl];
+    fg.A0[a] = Xv[ga * 2 + a] + sa;
+    fg.B0[a] = Xv[gb * 2 + a] + sb;
+    fg.A1[a] = Xv1[ga * 2 + a] + sa;
+    fg.B1[a] = Xv1[gb * 2 + a] + sb;
+  }
+  double n0[3];
+  st_normal(fg, 0.0, 0.0, dt, n0);
+  const double sgn =
+      n0[0] * (fg.A0[0] - bary[cl * 3]) + n0[1] * (fg.A0[1] - bary[cl * 3 + 1]) > 0.0 ? 1.0 : -1.0;
+  double qbL[4], qbR[4];
+  for (int v = 0; v < 4; ++v) {
+    qbL[v] = Q[v * N + cl];
+    qbR[v] = cr >= 0 ? Q[v * N + cr] : qbL[v];
+  }
+  const double* qL = qhat + cl * L * 4;
+  const double* qR = qhat + (cr >= 0 ? cr : cl) * L * 4;
+  double acc[4] = {0, 0, 0, 0};
+  for (int qp = 0; qp < NQ; ++qp)
+    for (int tt = 0; tt < NQ; ++tt) {
+      const double* bL = ftab + ((int64_t)(kL * NQ + tt) * NQ + qp) * L;
+      const double* bR = ftab + ((int64_t)(kR * NQ + tt) * NQ + qp) * L;
+      double qm[4] = {0, 0, 0, 0}, qq[4] = {0, 0, 0, 0};
+      for (int l = 0; l < L; ++l)
+        for (int v = 0; v < 4; ++v) {
+          qm[v] += bL[l] * qL[l * 4 + v];
+          qq[v] += bR[l] * qR[l * 4 + v];
+        }
+      if (cr < 0)
+        for (int v = 0; v < 4; ++v) qq[v] = qm[v];
+      if (t.pos) {
+        if (!admissible(qm, t.gamma))
+          for (int v = 0; v < 4; ++v) qm[v] = qbL[v];
+        if (!admissible(qq, t.gamma))
+          for (int v = 0; v < 4; ++v) qq[v] = qbR[v];
+      }
+      double n[3];
+      st_normal(fg, t.chi[qp], t.tq[tt], dt, n);
+      for (int a = 0; a < 3; ++a) n[a] *= sgn;
+      const double nx = sqrt(n[0] * n[0] + n[1] * n[1]);
+      const double un[2] = {n[0] / nx, n[1] / nx};
+      const double Vn = -n[2] / nx;
+      double sm = 0.0, fsum[4];
+      const double* sides[2] = {qm, qq};
+      for (int v = 0; v < 4; ++v) fsum[v] = 0.0;
+      for (int s = 0; s < 2; ++s) {
+        const double* z = sides[s];
+        const double r = z[0], u = z[1] / r, vv = z[2] / r, p = pressure(z, t.gamma);
+        const double c = sqrt(fmax(0.0, t.gamma * p / r));
+        const double vn = u * un[0] + vv * un[1];
+        sm = fmax(sm, fabs(vn - Vn) + c);
+        fsum[0] += z[1] * n[0] + z[2] * n[1];
+        fsum[1] += (z[1] * u + p) * n[0] + z[1] * vv * n[1];
+        fsum[2] += z[2] * u * n[0] + (z[2] * vv + p) * n[1];
+        fsum[3] += u * (z[3] + p) * n[0] + vv * (z[3] + p) * n[1];
+      }
+      sm *= nx;
+      const double wgt = t.wq[qp] * t.wt[tt];
+      for (int v = 0; v < 4; ++v)
+        acc[v] += wgt * (0.5 * fsum[v] + 0.5 * (qm[v] + qq[v]) * n[2] - 0.5 * sm * (qq[v] - qm[v]));
+    }
+  for (int v = 0; v < 4; ++v) G[v * F + f] = acc[v];
+}
+
+// ------------------------------------------------------------------- update
+// Eq. (PDEfinal) with the face integrals (outward from fL), new volume from
+// the new vertices; status bit on an inadmissible result or a tangled cell.
+__global__ void __launch_bounds__(256) k_ale_update(const int32_t* __restrict__ cellface, const double* __restrict__ G,
+                                                    const int32_t* __restrict__ gv, const double* __restrict__ shift,
+                                                    const double* __restrict__ Xv1, const double* __restrict__ vol0,
+                                                    int64_t N, int64_t F, double gamma, double dt_fixed, double cfl,
+                                                    const unsigned long long* dtmin, double* __restrict__ Q,
+                                                    double* time, int* status) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) *time += step_dt(dt_fixed, cfl, dtmin);
+  if (i >= N) return;
+  double acc[4] = {0, 0, 0, 0};
+  for (int k = 0; k < 3; ++k) {
+    const int32_t cf = cellface[k * N + i];
+    const int64_t f = cf >> 1;
+    const double s = (cf & 1) ? -1.0 : 1.0;
+    for (int v = 0; v < 4; ++v) acc[v] += s * G[v * F + f];
+  }
+  double P[3][2];
+  for (int k = 0; k < 3; ++k) {
+    const int64_t g = gv[k * N + i];
+    for (int a = 0; a < 2; ++a) P[k][a] = Xv1[g * 2 + a] + shift[(k * 2 + a) * N + i];
+  }
+  const double det = (P[1][0] - P[0][0]) * (P[2][1] - P[0][1]) - (P[2][0] - P[0][0]) * (P[1][1] - P[0][1]);
+  const double v1 = det / 2.0, v0 = vol0[i];
+  double q[4];
+  for (int v = 0; v < 4; ++v) {
+    q[v] = (v0 * Q[v * N + i] - acc[v]) / v1;
+    Q[v * N + i] = q[v];
+  }
+  if (!(v1 > 0.0) || !admissible(q, gamma)) atomicOr(status, 1);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+struct Ale {
+  int M = 1;
+  MeshHost slim;  // d, nc, periodicity: what the device matrices refresh reads
+  int64_t nvert = 0;
+  AleTab tab;
+  double *Xv = nullptr, *Xv1 = nullptr, *shift = nullptr, *X = nullptr, *bary = nullptr, *vol = nullptr;
+  double *w = nullptr, *qhat = nullptr, *vcon = nullptr, *G = nullptr, *ftab = nullptr;
+  int32_t *gv = nullptr, *start = nullptr, *ent = nullptr, *ident = nullptr;
+  int* bad = nullptr;
+  bool fresh = false;
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  ~Ale() {
+    for (void* p : allocs) cudaFree(p);
+  }
+  template <typename T>
+  cudaError_t alloc(T** p, size_t n, cudaStream_t st) {
+    void* q = nullptr;
+    cudaError_t e = cudaMallocAsync(&q, sizeof(T) * std::max<size_t>(n, 1), st);
+    if (e != cudaSuccess) return e;
+    allocs.push_back(q);
+    bytes += sizeof(T) * n;
+    *p = (T*)q;
+    return cudaSuccess;
+  }
+  template <typename T>
+  cudaError_t put(T** p, const std::vector<T>& h, cudaStream_t st) {
+    cudaError_t e = alloc(p, h.size(), st);
+    if (e != cudaSuccess || h.empty()) return e;
+    e = cudaMemcpyAsync(*p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(st);  // h is a host temporary
+  }
+};
+
+namespace {
+
+#define ACK(x)                                               \
+  do {                                                       \
+    cudaError_t e_ = (x);                                    \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #x);         \
+  } while (0)
+
+unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+template <int M>
+cudaError_t launch_pred(Ale& A, cweno_solver* s, double dtf, cudaStream_t st) {
+  const DevState& ds = s->ds;
+  k_ale_pred<M><<<nblk(ds.N, 128), 128, 0, st>>>(A.tab, A.w, ds.Q, A.X, A.vol, ds.N, s->ph.niter, dtf,
+                                                  s->prm.cfl, ds.dtmin, A.qhat, A.vcon);
+  return cudaGetLastError();
+}
+
+template <int M>
+cudaError_t launch_flux(Ale& A, cweno_solver* s, double dtf, cudaStream_t st) {
+  const DevState& ds = s->ds;
+  k_ale_flux<M><<<nblk(ds.F, 128), 128, 0, st>>>(A.tab, A.ftab, ds.fL, ds.fR, ds.codeL, ds.codeR, A.gv, A.shift,
+                                                  A.Xv, A.Xv1, A.bary, A.qhat, ds.Q, ds.N, ds.F, dtf, s->prm.cfl,
+                                                  ds.dtmin, A.G);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int ale_create(cweno_solver* s, const MeshHost& m, std::string& err) {
+  const RefElem& re = *s->re;
+  if (m.d != 2 || s->pde != CWENO_EULER || s->prec != CWENO_FP64 || re.M > 3 ||
+      s->prm.flux != CWENO_FLUX_RUSANOV) {
+    err = "moving meshes are built for 2D Euler, FP64, order 2..4, Rusanov flux";
+    return CWENO_EINVAL;
+  }
+  auto A = std::make_shared<Ale>();
+  cudaStream_t st = s->stream;
+  const int64_t N = m.nc, nv = m.nv;
+  const int L = re.L, L0 = re.L0, L1 = re.L1;
+  A->M = re.M;
+  A->nvert = nv;
+  A->slim.d = 2;
+  A->slim.nc = N;
+  for (int a = 0; a < 3; ++a) {
+    A->slim.per[a] = m.per[a];
+    A->slim.Lper[a] = m.Lper[a];
+  }
+  // reference tables
+  AleTab& t = A->tab;
+  std::memset(&t, 0, sizeof(t));
+  for (int e = 0; e < 2; ++e)
+    for (int n = 0; n < L; ++n)
+      for (int l = 0; l < L; ++l) t.Dxi[e][n][l] = re.Dxi[((size_t)e * L + n) * L + l];
+  for (int k = 0; k < L1; ++k) {
+    for (int l = 0; l < L; ++l) t.Gal[k][l] = re.Gal[(size_t)k * L + l];
+    for (int n = 0; n < L0; ++n) t.C0[k][n] = re.C0[(size_t)k * L0 + n];
+  }
+  for (int v = 0; v < 3; ++v)
+    for (int l = 0; l < L; ++l) t.Wv[v][l] = re.Wv[(size_t)v * L + l];
+  for (int l = 0; l < L; ++l) {
+    t.node[l][0] = re.stnode[l][0];
+    t.node[l][1] = re.stnode[l][1];
+    t.node[l][2] = re.stnode[l][3];
+  }
+  for (int q = 0; q <= re.M; ++q) {
+    t.chi[q] = re.chi[q];
+    t.wq[q] = re.wq[q];
+    t.wt[q] = re.wt[q];
+    t.tq[q] = re.tq[q];
+  }
+  t.gamma = s->prm.gamma;
+  t.mode = s->prm.mesh_motion;
+  t.pos = s->prm.positivity;
+  // per-cell global vertices and periodic image shifts (the unwrapping of
+  // the mesh: image nearest the cell's first vertex), SoA
+  std::vector<int32_t> gv((size_t)3 * N);
+  std::vector<double> sh((size_t)6 * N, 0.0);
+  for (int64_t i = 0; i < N; ++i) {
+    const int64_t g0 = m.gv[i * 3];
+    for (int k = 0; k < 3; ++k) {
+      const int64_t g = m.gv[i * 3 + k];
+      gv[(size_t)k * N + i] = (int32_t)g;
+      for (int a = 0; a < 2; ++a)
+        if (m.per[a] && k > 0)
+          sh[(size_t)(k * 2 + a) * N + i] = m.Lper[a] * std::nearbyint((m.xyz[g0 * 2 + a] - m.xyz[g * 2 + a]) / m.Lper[a]);
+    }
+  }
+  // vertex -> (cell, local vertex) incidence, cells in increasing caller order
+  std::vector<int32_t> start(nv + 1, 0), ent((size_t)3 * N);
+  for (int64_t i = 0; i < N; ++i)
+    for (int k = 0; k < 3; ++k) ++start[m.gv[i * 3 + k] + 1];
+  for (int64_t g = 0; g < nv; ++g) start[g + 1] += start[g];
+  {
+    std::vector<int32_t> fill(start.begin(), start.end() - 1);
+    for (int64_t u = 0; u < N; ++u) {
+      const int64_t i = m.iperm[u];
+      for (int k = 0; k < 3; ++k) ent[fill[m.gv[i * 3 + k]]++] = (int32_t)(i * 3 + k);
+    }
+  }
+  std::vector<int32_t> ident(N);
+  std::iota(ident.begin(), ident.end(), 0);
+  ACK(A->put(&A->gv, gv, st));
+  ACK(A->put(&A->shift, sh, st));
+  ACK(A->put(&A->start, start, st));
+  ACK(A->put(&A->ent, ent, st));
+  ACK(A->put(&A->ident, ident, st));
+  ACK(A->put(&A->Xv, m.xyz, st));
+  ACK(A->put(&A->ftab, re.ftab, st));
+  ACK(A->alloc(&A->Xv1, (size_t)nv * 2, st));
+  ACK(A->alloc(&A->X, (size_t)N * 9, st));
+  ACK(A->alloc(&A->bary, (size_t)N * 3, st));
+  ACK(A->alloc(&A->vol, (size_t)N, st));
+  ACK(A->alloc(&A->w, (size_t)N * L0 * 4, st));
+  ACK(A->alloc(&A->qhat, (size_t)N * L * 4, st));
+  ACK(A->alloc(&A->vcon, (size_t)N * 9, st));
+  ACK(A->alloc(&A->G, (size_t)4 * m.nf, st));
+  ACK(A->alloc(&A->bad, 1, st));
+  const int big = 0x7fffffff;
+  ACK(cudaMemcpyAsync(A->bad, &big, sizeof(int), cudaMemcpyHostToDevice, st));
+  ACK(cudaStreamSynchronize(st));
+  s->bytes += A->bytes;
+  s->ale = A;
+  return CWENO_OK;
+}
+
+int ale_refresh(cweno_solver* s) {
+  Ale& A = *s->ale;
+  if (A.fresh) return CWENO_OK;
+  DevState& ds = s->ds;
+  cudaStream_t st = s->stream;
+  k_ale_geom<<<nblk(ds.N, 256), 256, 0, st>>>(A.Xv, A.gv, A.shift, ds.N, A.X, A.bary, A.vol,
+                                               const_cast<double*>(ds.hsize), const_cast<double*>(ds.invvol));
+  ACK(cudaGetLastError());
+  int rc = ale_matrices_device(A.slim, *s->re, A.X, A.bary, ds.sten, ds.sec, (double*)const_cast<void*>(ds.R),
+                               (double*)const_cast<void*>(ds.Binv), A.bad, st);
+  if (rc) return fail(rc, "moving-mesh matrices");
+  A.fresh = true;
+  return CWENO_OK;
+}
+
+int ale_step(cweno_solver* s, double dt) {
+  Ale& A = *s->ale;
+  int rc = ale_refresh(s);
+  if (rc) return rc;
+  DevState& ds = s->ds;
+  cudaStream_t st = s->stream;
+  const double dtf = dt > 0 ? dt : 0.0;
+  if (dtf == 0.0) {  // CFL bound of the current state on the current mesh
+    k_ale_dt_reset<<<1, 1, 0, st>>>(ds.dtmin);
+    ACK(cudaGetLastError());
+    ACK(s->ops->stable_dt(ds, s->ph, 0, st));
+  }
+  DevState d2 = ds;
+  d2.perm = A.ident;  // reconstruction values in internal cell order
+  ACK(s->ops->reconstruct(d2, s->ph, A.w, st));
+  switch (A.M) {
+    case 1: ACK(launch_pred<1>(A, s, dtf, st)); break;
+    case 2: ACK(launch_pred<2>(A, s, dtf, st)); break;
+    default: ACK(launch_pred<3>(A, s, dtf, st)); break;
+  }
+  k_ale_nodes<<<nblk(A.nvert, 256), 256, 0, st>>>(A.start, A.ent, A.vcon, A.Xv, A.nvert, dtf, s->prm.cfl, ds.dtmin,
+                                                   A.Xv1);
+  ACK(cudaGetLastError());
+  switch (A.M) {
+    case 1: ACK(launch_flux<1>(A, s, dtf, st)); break;
+    case 2: ACK(launch_flux<2>(A, s, dtf, st)); break;
+    default: ACK(launch_flux<3>(A, s, dtf, st)); break;
+  }
+  k_ale_update<<<nblk(ds.N, 256), 256, 0, st>>>(ds.cellface, A.G, A.gv, A.shift, A.Xv1, A.vol, ds.N, ds.F,
+                                                 s->prm.gamma, dtf, s->prm.cfl, ds.dtmin, ds.Q, ds.time, ds.status);
+  ACK(cudaGetLastError());
+  std::swap(A.Xv, A.Xv1);
+  A.fresh = false;
+  return CWENO_OK;
+}
+
+int ale_vertices(cweno_solver* s, double* xyz, int on_device) {
+  Ale& A = *s->ale;
+  ACK(cudaMemcpyAsync(xyz, A.Xv, sizeof(double) * A.nvert * 2,
+                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream));
+  ACK(cudaStreamSynchronize(s->stream));
+  return CWENO_OK;
+}
+
+int ale_degenerate(cweno_solver* s, int* cell) {
+  Ale& A = *s->ale;
+  int b = 0;
+  ACK(cudaMemcpyAsync(&b, A.bad, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  ACK(cudaStreamSynchronize(s->stream));
+  *cell = b == 0x7fffffff ? -1 : b;  // internal cell index
+  return CWENO_OK;
+}
+
+}  // namespace cw

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "../../include/cweno.h"
+#include "ale.h"
 #include "api_internal.h"
 #include "host.h"
 #include "ops.h"
@@ -151,6 +152,7 @@ void cweno_default_params(cweno_params* p, int dim, int pde) {
   p->linear_weights = 0;
   p->positivity = 1;
   p->flux = CWENO_FLUX_RUSANOV;
+  p->mesh_motion = CWENO_MOTION_FIXED;
 }
 
 const char* cweno_last_error(void) { return g_err.c_str(); }
@@ -207,6 +209,7 @@ void cweno_solver_destroy(cweno_solver* s) {
   cudaGetDevice(&cur);
   cudaSetDevice(s->dev);
   cudaStreamSynchronize(s->stream);
+  s->ale.reset();
   for (auto& kv : s->graphs)
     if (kv.second) cudaGraphExecDestroy(kv.second);
   for (auto& u : s->ev_used) {
@@ -244,6 +247,12 @@ int cweno_setup(const cweno_mesh* mesh, int order, int pde, int precision, const
     return fail(CWENO_EINVAL, "unknown flux");
   if (prm.flux == CWENO_FLUX_OSHER && pde != CWENO_EULER)
     return fail(CWENO_EINVAL, "the Osher-type flux is built for the Euler equations");
+  if (prm.mesh_motion != CWENO_MOTION_FIXED && prm.mesh_motion != CWENO_MOTION_LAGRANGE &&
+      prm.mesh_motion != CWENO_MOTION_STILL)
+    return fail(CWENO_EINVAL, "unknown mesh motion");
+  if (prm.mesh_motion != CWENO_MOTION_FIXED &&
+      (m.d != 2 || pde != CWENO_EULER || precision != CWENO_FP64 || order > 4 || prm.flux != CWENO_FLUX_RUSANOV))
+    return fail(CWENO_EINVAL, "moving meshes are built for 2D Euler, FP64, order 2..4, Rusanov flux");
   const int M = order - 1;
   std::unique_ptr<cweno_solver> s(new cweno_solver());
   s->dim = m.d;
@@ -373,6 +382,7 @@ int cweno_setup(const cweno_mesh* mesh, int order, int pde, int precision, const
   if ((rc = dev_alloc(s.get(), &p, sizeof(double) * N * nv))) return rc;
   ds.stage = (double*)p;
   CK(s->ops->prepare());
+  if (prm.mesh_motion != CWENO_MOTION_FIXED && (rc = ale_create(s.get(), m, err))) return fail(rc, err);
   CK(cudaStreamSynchronize(s->stream));
   *out = s.release();
   return CWENO_OK;
@@ -422,6 +432,10 @@ int cweno_set_state(cweno_solver* s, const double* Q, int on_device) {
     }
   }
   CK(s->ops->set_state(s->ds, src, s->stream));  // also resets dt bound, time, status
+  if (s->ale) {
+    int rc = ale_refresh(s);  // h of the current mesh for the bound below
+    if (rc) return rc;
+  }
   CK(s->ops->stable_dt(s->ds, s->ph, 0, s->stream));
   s->cur = 0;
   return CWENO_OK;
@@ -465,6 +479,10 @@ int cweno_reconstruct(cweno_solver* s, double* w, int on_device) {
     if (rc) return rc;
     dst = s->outbuf;
   }
+  if (s->ale) {
+    int rc = ale_refresh(s);
+    if (rc) return rc;
+  }
   CK(s->ops->reconstruct(s->ds, s->ph, dst, s->stream));
   if (!on_device) CK(cudaMemcpyAsync(w, dst, bytes, cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
@@ -473,6 +491,7 @@ int cweno_reconstruct(cweno_solver* s, double* w, int on_device) {
 
 int cweno_predictor(cweno_solver* s, double dt, double* qhat, int on_device) {
   if (!s || !qhat || !(dt > 0)) return fail(CWENO_EINVAL, "bad argument");
+  if (s->ale) return fail(CWENO_EINVAL, "the predictor of a moving mesh is internal to its step");
   CK(cudaSetDevice(s->dev));
   size_t bytes = sizeof(double) * s->nc * s->re->L * s->nv;
   double* dst = qhat;
@@ -494,6 +513,10 @@ int cweno_predictor(cweno_solver* s, double dt, double* qhat, int on_device) {
 int cweno_stable_dt(cweno_solver* s, double cfl, double* dt) {
   if (!s || !dt || !(cfl > 0)) return fail(CWENO_EINVAL, "bad argument");
   CK(cudaSetDevice(s->dev));
+  if (s->ale) {
+    int rc = ale_refresh(s);
+    if (rc) return rc;
+  }
   static const unsigned long long inf = 0x7ff0000000000000ull;
   CK(cudaMemcpyAsync(s->ds.dtmin + 2, &inf, sizeof(inf), cudaMemcpyHostToDevice, s->stream));
   CK(s->ops->stable_dt(s->ds, s->ph, 2, s->stream));
@@ -547,6 +570,7 @@ extern "C" {
 int ader_cweno_step(cweno_solver* s, double dt) {
   if (!s) return fail(CWENO_EINVAL, "null solver");
   CK(cudaSetDevice(s->dev));
+  if (s->ale) return ale_step(s, dt);
   int rc = enqueue_step(s, dt, s->cur);
   if (rc) return rc;
   s->cur ^= 1;
@@ -556,6 +580,13 @@ int ader_cweno_step(cweno_solver* s, double dt) {
 int ader_cweno_run(cweno_solver* s, int nsteps, double dt) {
   if (!s || nsteps < 0) return fail(CWENO_EINVAL, "bad argument");
   CK(cudaSetDevice(s->dev));
+  if (s->ale) {
+    for (int k = 0; k < nsteps; ++k) {
+      int rc = ale_step(s, dt);
+      if (rc) return rc;
+    }
+    return CWENO_OK;
+  }
   for (int k = 0; k < nsteps; ++k) {
     // one graph per (time-step slot, dt): captured on first use, then replayed
     std::pair<int, double> gk(s->cur, dt > 0 ? dt : 0.0);
@@ -586,8 +617,23 @@ int cweno_sync(cweno_solver* s) {
   int st = 0;
   CK(cudaMemcpyAsync(&st, s->ds.status, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
+  if (s->ale) {
+    int bad = -1;
+    int rc = ale_degenerate(s, &bad);
+    if (rc) return rc;
+    if (bad >= 0)
+      return fail(CWENO_EDEGENERATE, "the moving mesh made a least-squares or sector system singular (cell " +
+                                         std::to_string(s->ds.N > bad ? bad : -1) + ", internal order)");
+  }
   if (st) return fail(CWENO_ENAN, "a step produced NaN or non-positive density / pressure");
   return CWENO_OK;
+}
+
+int cweno_get_vertices(cweno_solver* s, double* xyz, int on_device) {
+  if (!s || !xyz) return fail(CWENO_EINVAL, "null argument");
+  if (!s->ale) return fail(CWENO_EINVAL, "the solver's mesh is fixed");
+  CK(cudaSetDevice(s->dev));
+  return ale_vertices(s, xyz, on_device);
 }
 
 int cweno_get_time(cweno_solver* s, double* t) {

@@ -12,6 +12,10 @@
 #include "ops.h"
 #include "refelem.h"
 
+namespace cw {
+struct Ale;
+}
+
 struct cweno_solver {
   int dim = 2, order = 2, M = 1, pde = 0, prec = 0, nv = 4;
   cweno_params prm;
@@ -33,6 +37,8 @@ struct cweno_solver {
   bool profile = false;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<std::pair<cudaEvent_t, cudaEvent_t>, int>> ev_used;
+  // moving mesh (mesh_motion != CWENO_MOTION_FIXED), else empty
+  std::shared_ptr<cw::Ale> ale;
 };
 
 namespace cw {

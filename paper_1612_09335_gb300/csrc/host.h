@@ -58,4 +58,15 @@ int build_cell_setup(const MeshHost& m, const RefElem& re, CellSetup& cs, std::s
 int lsq_setup_device(const MeshHost& m, const RefElem& re, const int32_t* d_sten, void* d_R, int fp32,
                      void* stream, std::string& err);
 
+// Moving meshes (setup_gpu.cu, two dimensions, FP64): rebuild on the device
+// the least-squares pseudo-inverses R and the sector inverses Binv of every
+// cell from the unwrapped cell vertices d_X (nc x (d+1) x 3, internal order)
+// and barycentres d_bary (nc x 3) of the current mesh, for the fixed
+// stencils d_sten and sector cells d_sec (SoA, as uploaded by the setup).
+// *d_bad receives the smallest cell index whose system is degenerate.
+// Asynchronous on stream (a cudaStream_t).
+int ale_matrices_device(const MeshHost& m, const RefElem& re, const double* d_X, const double* d_bary,
+                        const int32_t* d_sten, const int32_t* d_sec, double* d_R, double* d_Binv, int* d_bad,
+                        void* stream);
+
 }  // namespace cw

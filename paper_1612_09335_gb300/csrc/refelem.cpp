@@ -490,6 +490,68 @@ void RefElem::init(int d_, int M_) {
         P[((size_t)e * L1 + k) * L + l] = (double)s;
       }
   }
+  // Moving-mesh predictor tables.  K_tau and M (rows: test functions of the
+  // tau > 0 nodes) by the collapsed Gauss rule on T_E times Gauss-Legendre
+  // on [0, 1], exact for their degree 2M; Gal = (K_tau^1)^-1 M^1 solved in
+  // extended precision (K_tau^1 has condition number 1.5e4 at M = 3).  In
+  // exact arithmetic -(K_tau^1)^-1 K_tau^0 is the constant extension C0 above,
+  // so only Gal is new.
+  {
+    auto dtheta = [&](int l, int e, const LD* x) {
+      LD s = 0.0L;
+      for (int k = 0; k < L; ++k) {
+        const int pe = stm[k][e];
+        if (pe == 0) continue;
+        LD m = Cb[k * L + l] * (LD)pe;
+        for (int a = 0; a <= d; ++a) m *= ipow(x[a], a == e ? stm[k][a] - 1 : stm[k][a]);
+        s += m;
+      }
+      return s;
+    };
+    Dxi.assign((size_t)d * L * L, 0.0);
+    for (int e = 0; e < d; ++e)
+      for (int n = 0; n < L; ++n) {
+        LD x[4];
+        for (int a = 0; a < d; ++a) x[a] = (LD)stnode[n][a];
+        x[d] = (LD)stnode[n][3];
+        for (int l = 0; l < L; ++l) Dxi[((size_t)e * L + n) * L + l] = (double)dtheta(l, e, x);
+      }
+    SimplexQuad Qs = simplex_quad(d, M + 1);
+    std::vector<double> gx, gw;
+    gauss_jacobi(M + 1, 0.0, 0.0, gx, gw);
+    std::vector<LD> Kt((size_t)L1 * L, 0.0L), Mm((size_t)L1 * L, 0.0L);
+    std::vector<LD> th(L), dtt(L);
+    for (size_t g = 0; g < Qs.w.size(); ++g)
+      for (int t = 0; t <= M; ++t) {
+        LD x[4];
+        for (int a = 0; a < d; ++a) x[a] = (LD)Qs.x[g][a];
+        x[d] = 0.5L * (1.0L + (LD)gx[t]);
+        const LD w = (LD)Qs.w[g] * 0.5L * (LD)gw[t];
+        for (int l = 0; l < L; ++l) {
+          th[l] = theta(l, x);
+          dtt[l] = dtheta(l, d, x);
+        }
+        for (int k = 0; k < L1; ++k)
+          for (int l = 0; l < L; ++l) {
+            Kt[(size_t)k * L + l] += w * th[L0 + k] * dtt[l];
+            Mm[(size_t)k * L + l] += w * th[L0 + k] * th[l];
+          }
+      }
+    std::vector<LD> K1((size_t)L1 * L1);
+    for (int k = 0; k < L1; ++k)
+      for (int l = 0; l < L1; ++l) K1[(size_t)k * L1 + l] = Kt[(size_t)k * L + L0 + l];
+    if (!lu_solve_t<LD>(L1, K1, Mm, L)) throw std::runtime_error("singular K_tau^1");
+    Gal.assign((size_t)L1 * L, 0.0);
+    for (size_t k = 0; k < Mm.size(); ++k) Gal[k] = (double)Mm[k];
+    Wv.assign((size_t)(d + 1) * L, 0.0);
+    for (int v = 0; v <= d; ++v)
+      for (int t = 0; t <= M; ++t) {
+        LD x[4] = {0.0L, 0.0L, 0.0L, 0.0L};
+        if (v > 0) x[v - 1] = 1.0L;
+        x[d] = 0.5L * (1.0L + (LD)gx[t]);
+        for (int l = 0; l < L; ++l) Wv[(size_t)v * L + l] += (double)(0.5L * (LD)gw[t] * theta(l, x));
+      }
+  }
   // face quadrature tables
   {
     std::vector<double> gx, gw, jx, jw;
@@ -521,6 +583,9 @@ void RefElem::init(int d_, int M_) {
       for (double& w : wq) w /= sw;
     }
     nqs = (int)chi.size();
+    this->chi.clear();
+    if (d == 2)
+      for (const auto& c : chi) this->chi.push_back(c[0]);
     ncode = (d == 2) ? 6 : 24;
     ftab.assign((size_t)ncode * nqt * nqs * L, 0.0);
     std::vector<LD> fi((size_t)ncode * L, 0.0L);

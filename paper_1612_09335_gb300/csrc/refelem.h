@@ -79,6 +79,13 @@ struct RefElem {
   std::vector<double> fint;  // ncode x L
   std::vector<double> wq, wt;
   std::vector<double> tq;    // time points
+  std::vector<double> chi;   // face points (d = 2: parameter along the edge)
+  // moving-mesh predictor (Secs. 2.2-2.3):
+  //   Dxi[(e L + n) L + l] = d theta_l / d xi_e at node n;
+  //   Gal = (K_tau^1)^-1 M^1, L1 x L, the Galerkin operator of Eqs. (CGfinal)
+  //     and (ODEfinal) (q^1 = C0 q^0 - dt Gal H, x^1 = C0 x^0 + dt Gal V);
+  //   Wv[v L + l] = int_0^1 theta_l(reference vertex v, tau) dtau (Eq. NodesVel).
+  std::vector<double> Dxi, Gal, Wv;
   void init(int d, int M);
 };
 

@@ -190,6 +190,70 @@ __global__ void __launch_bounds__(128) k_lsq(const double* __restrict__ X, const
   }
 }
 
+// Moving meshes: the sector inverses of Eq. (CWENO:Ps) for the fixed sector
+// cells on the current geometry, B[k][l] = psi_{1+l}(xi_i(b_jk)) (b_jk the
+// minimum-image barycentre of the k-th cell of sector s, xi_i the reference
+// coordinates of cell i) and Binv[((s D + e) D + k) N + i] = (B^-1)[e][k],
+// the layout the reconstruction kernel reads.  Dropped sectors (first id
+// < 0) are skipped.  bad: smallest cell index with a singular B.
+template <int D, int M>
+__global__ void __launch_bounds__(128) k_sectors(const double* __restrict__ X, const double* __restrict__ bary,
+                                                 const int32_t* __restrict__ sec, int64_t N, const LsqTab tab,
+                                                 double* __restrict__ Binv, int* bad) {
+  constexpr int MC = cmc(M, D), NX = (D + 1) * 3;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double* Xi = X + i * NX;
+  double Ji[3][3];
+  jac_inv<D>(Xi, Ji);
+  double psi[MC];
+  for (int s = 0; s <= D; ++s) {
+    if (sec[(int64_t)(s * D) * N + i] < 0) continue;
+    double B[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int k = 0; k < D; ++k) {
+      const int64_t j = sec[(int64_t)(s * D + k) * N + i];
+      double xi[3] = {0, 0, 0};
+      for (int a = 0; a < D; ++a) {
+        double sh = 0.0;
+        if (tab.per[a]) sh = tab.Lper[a] * nearbyint((bary[i * 3 + a] - bary[j * 3 + a]) / tab.Lper[a]);
+        const double db = bary[j * 3 + a] + sh - Xi[a];
+        for (int b = 0; b < D; ++b) xi[b] += Ji[b][a] * db;
+      }
+      dubiner<D, M>(tab, xi, psi);
+      for (int l = 0; l < D; ++l) B[k][l] = psi[1 + l];
+    }
+    double Bi[3][3];
+    double det;
+    if (D == 2) {
+      det = B[0][0] * B[1][1] - B[0][1] * B[1][0];
+      Bi[0][0] = B[1][1] / det;
+      Bi[0][1] = -B[0][1] / det;
+      Bi[1][0] = -B[1][0] / det;
+      Bi[1][1] = B[0][0] / det;
+    } else {
+      const double c00 = B[1][1] * B[2][2] - B[1][2] * B[2][1];
+      const double c01 = B[1][2] * B[2][0] - B[1][0] * B[2][2];
+      const double c02 = B[1][0] * B[2][1] - B[1][1] * B[2][0];
+      det = B[0][0] * c00 + B[0][1] * c01 + B[0][2] * c02;
+      Bi[0][0] = c00 / det;
+      Bi[1][0] = c01 / det;
+      Bi[2][0] = c02 / det;
+      Bi[0][1] = (B[0][2] * B[2][1] - B[0][1] * B[2][2]) / det;
+      Bi[1][1] = (B[0][0] * B[2][2] - B[0][2] * B[2][0]) / det;
+      Bi[2][1] = (B[0][1] * B[2][0] - B[0][0] * B[2][1]) / det;
+      Bi[0][2] = (B[0][1] * B[1][2] - B[0][2] * B[1][1]) / det;
+      Bi[1][2] = (B[0][2] * B[1][0] - B[0][0] * B[1][2]) / det;
+      Bi[2][2] = (B[0][0] * B[1][1] - B[0][1] * B[1][0]) / det;
+    }
+    if (!(det != 0.0) || !isfinite(det)) {
+      atomicMin(bad, (int)i);
+      continue;
+    }
+    for (int e = 0; e < D; ++e)
+      for (int k = 0; k < D; ++k) Binv[(int64_t)((s * D + e) * D + k) * N + i] = Bi[e][k];
+  }
+}
+
 template <int D, int M, typename T>
 cudaError_t launch(const double* X, const double* bary, const int32_t* sten, int64_t N, const LsqTab& tab, void* R,
                    int* bad, cudaStream_t st) {
@@ -220,16 +284,14 @@ cudaError_t dispatch(int d, int M, const double* X, const double* bary, const in
 
 }  // namespace
 
-int lsq_setup_device(const MeshHost& m, const RefElem& re, const int32_t* d_sten, void* d_R, int fp32,
-                     void* stream, std::string& err) {
-  cudaStream_t st = (cudaStream_t)stream;
+namespace {
+
+bool make_tab(const MeshHost& m, const RefElem& re, LsqTab& tab, std::string& err) {
   const int d = m.d, M = re.M;
-  const int64_t N = m.nc;
-  LsqTab tab;
   SimplexQuad Q = simplex_quad(d, (M + 2) / 2);
   if ((int)Q.w.size() > kMaxQ || re.psi.n > kMaxB || (2 * M + 3) * (M + 1) > kMaxRec) {
     err = "least-squares tables exceed the device setup limits";
-    return CWENO_EINVAL;
+    return false;
   }
   tab.nq = (int)Q.w.size();
   tab.wsum = 0.0;
@@ -249,6 +311,46 @@ int lsq_setup_device(const MeshHost& m, const RefElem& re, const int32_t* d_sten
     tab.per[a] = m.per[a] ? 1 : 0;
     tab.Lper[a] = m.Lper[a];
   }
+  return true;
+}
+
+template <int D, int M>
+cudaError_t launch_sectors(const double* X, const double* bary, const int32_t* sec, int64_t N, const LsqTab& tab,
+                           double* Binv, int* bad, cudaStream_t st) {
+  k_sectors<D, M><<<(unsigned)((N + 127) / 128), 128, 0, st>>>(X, bary, sec, N, tab, Binv, bad);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int ale_matrices_device(const MeshHost& m, const RefElem& re, const double* d_X, const double* d_bary,
+                        const int32_t* d_sten, const int32_t* d_sec, double* d_R, double* d_Binv, int* d_bad,
+                        void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  LsqTab tab;
+  std::string err;
+  if (!make_tab(m, re, tab, err)) return CWENO_EINVAL;
+  cudaError_t e = dispatch<double>(m.d, re.M, d_X, d_bary, d_sten, m.nc, tab, d_R, d_bad, st);
+  if (e == cudaSuccess && m.d == 2) {
+    switch (re.M) {
+      case 1: e = launch_sectors<2, 1>(d_X, d_bary, d_sec, m.nc, tab, d_Binv, d_bad, st); break;
+      case 2: e = launch_sectors<2, 2>(d_X, d_bary, d_sec, m.nc, tab, d_Binv, d_bad, st); break;
+      case 3: e = launch_sectors<2, 3>(d_X, d_bary, d_sec, m.nc, tab, d_Binv, d_bad, st); break;
+      default: e = cudaErrorInvalidValue;
+    }
+  } else if (e == cudaSuccess) {
+    e = cudaErrorInvalidValue;
+  }
+  return e == cudaSuccess ? CWENO_OK : CWENO_ECUDA;
+}
+
+int lsq_setup_device(const MeshHost& m, const RefElem& re, const int32_t* d_sten, void* d_R, int fp32,
+                     void* stream, std::string& err) {
+  cudaStream_t st = (cudaStream_t)stream;
+  const int d = m.d, M = re.M;
+  const int64_t N = m.nc;
+  LsqTab tab;
+  if (!make_tab(m, re, tab, err)) return CWENO_EINVAL;
   double* dX = nullptr;
   double* dB = nullptr;
   int* dbad = nullptr;
