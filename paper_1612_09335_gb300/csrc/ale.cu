@@ -38,7 +38,11 @@ constexpr int kLmax = 20, kL0max = 10, kL1max = 10, kNQ = 4;
 
 // Reference tables of one M (2D), passed as a kernel parameter.
 struct AleTab {
-  double Dxi[2][kLmax][kLmax];  // d theta_l / d xi_e at node n: [e][n][l]
+  // d theta_l / d xi_e at node n, nonzero entries only (about a third of
+  // them are nonzero): for (e, n) the first nnz[e][n] pairs (col, val)
+  double val[2][kLmax][kLmax];
+  uint8_t col[2][kLmax][kLmax];
+  int nnz[2][kLmax];
   double Gal[kL1max][kLmax];    // (K_tau^1)^-1 M^1
   double C0[kL1max][kL0max];    // theta_n(xi_k, 0): constant extension in time
   double Wv[3][kLmax];          // int_0^1 theta_l(vertex v, tau) dtau
@@ -149,30 +153,32 @@ __global__ void __launch_bounds__(128) k_ale_pred(const __grid_constant__ AleTab
     }
     double H[L][4];
     for (int n = 0; n < L; ++n) {
-      // d x / d xi of the isoparametric map at node n, and its inverse
-      double J[2][2];
-      for (int a = 0; a < 2; ++a)
-        for (int e = 0; e < 2; ++e) {
-          double s = 0.0;
-          for (int l = 0; l < L; ++l) s += t.Dxi[e][n][l] * x[l][a];
-          J[a][e] = s;
+      // xi-derivatives at node n of the interpolants of x, q and F (one pass
+      // over the nonzero entries per direction)
+      double dx[2][2], dq[2][4], df[2][2][4];
+      for (int e = 0; e < 2; ++e) {
+        for (int a = 0; a < 2; ++a) dx[e][a] = 0.0;
+        for (int v = 0; v < 4; ++v) dq[e][v] = df[e][0][v] = df[e][1][v] = 0.0;
+        const int cnt = t.nnz[e][n];
+        for (int j = 0; j < cnt; ++j) {
+          const int l = t.col[e][n][j];
+          const double dd = t.val[e][n][j];
+          for (int a = 0; a < 2; ++a) dx[e][a] += dd * x[l][a];
+          for (int v = 0; v < 4; ++v) {
+            dq[e][v] += dd * q[l][v];
+            df[e][0][v] += dd * F[l][0][v];
+            df[e][1][v] += dd * F[l][1][v];
+          }
         }
-      const double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
-      const double Ji[2][2] = {{J[1][1] / det, -J[0][1] / det}, {-J[1][0] / det, J[0][0] / det}};
+      }
+      // d x / d xi of the isoparametric map at node n (J[a][e] = dx[e][a]) and its inverse
+      const double det = dx[0][0] * dx[1][1] - dx[1][0] * dx[0][1];
+      const double Ji[2][2] = {{dx[1][1] / det, -dx[1][0] / det}, {-dx[0][1] / det, dx[0][0] / det}};
       double dxidt[2];
       for (int e = 0; e < 2; ++e) dxidt[e] = -(Ji[e][0] * V[n][0] + Ji[e][1] * V[n][1]);
       for (int v = 0; v < 4; ++v) {
         double h = 0.0;
-        for (int e = 0; e < 2; ++e) {
-          double dq = 0.0, df0 = 0.0, df1 = 0.0;
-          for (int l = 0; l < L; ++l) {
-            const double dd = t.Dxi[e][n][l];
-            dq += dd * q[l][v];
-            df0 += dd * F[l][0][v];
-            df1 += dd * F[l][1][v];
-          }
-          h += dq * dxidt[e] + Ji[e][0] * df0 + Ji[e][1] * df1;
-        }
+        for (int e = 0; e < 2; ++e) h += dq[e][v] * dxidt[e] + Ji[e][0] * df[e][0][v] + Ji[e][1] * df[e][1][v];
         H[n][v] = h;
       }
     }
@@ -484,9 +490,22 @@ int ale_create(cweno_solver* s, const MeshHost& m, std::string& err) {
   // reference tables
   AleTab& t = A->tab;
   std::memset(&t, 0, sizeof(t));
-  for (int e = 0; e < 2; ++e)
-    for (int n = 0; n < L; ++n)
-      for (int l = 0; l < L; ++l) t.Dxi[e][n][l] = re.Dxi[((size_t)e * L + n) * L + l];
+  {
+    double dmax = 0.0;
+    for (double v : re.Dxi) dmax = std::max(dmax, std::fabs(v));
+    for (int e = 0; e < 2; ++e)
+      for (int n = 0; n < L; ++n) {
+        int c = 0;
+        for (int l = 0; l < L; ++l) {
+          const double v = re.Dxi[((size_t)e * L + n) * L + l];
+          if (std::fabs(v) <= 1e-12 * dmax) continue;  // exact zeros, rounded in extended precision
+          t.val[e][n][c] = v;
+          t.col[e][n][c] = (uint8_t)l;
+          ++c;
+        }
+        t.nnz[e][n] = c;
+      }
+  }
   for (int k = 0; k < L1; ++k) {
     for (int l = 0; l < L; ++l) t.Gal[k][l] = re.Gal[(size_t)k * L + l];
     for (int n = 0; n < L0; ++n) t.C0[k][n] = re.C0[(size_t)k * L0 + n];
