@@ -391,6 +391,25 @@ def workload_rate(cw, name, stream, barrier, steps=10, flux=0, precisions=None, 
     return res
 
 
+def ale_oracle_rate(n=40, steps=3):
+    """The FP64 oracle's direct ALE step timed on the host (one thread) on a
+    bounded sample of the same workload family: n x n x 2 triangles (3,200 at
+    n = 40, the size of the paper's 2D Sedov mesh), one untimed step first."""
+    import oracle
+    from paper_1612_09335_gb300 import workloads as wl
+    mesh = wl.tri_mesh(n, lo=(-1.0, -1.0), hi=(1.0, 1.0), periodic=False, jitter=0.2, seed=1234)
+    Q = wl.explosion_averages(mesh, sub=4)
+    o = oracle.Oracle(mesh, 4)
+    Q, _ = o.ale_step(Q, o.stable_dt(Q))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        Q, _ = o.ale_step(Q, o.stable_dt(Q))
+    el = time.perf_counter() - t0
+    return {"value": mesh.nc * steps / el, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"{mesh.nc} triangles ({n}x{n}x2, same family), {steps} ALE steps after one untimed step, "
+                      "single host thread"}
+
+
 def ale_rate(cw, stream, barrier, n=256, steps=10, warm=3):
     """Moving mesh: direct ALE steps (mesh velocity = fluid velocity) of the
     2D explosion (Sec. 3.2's ALE explosion, Table efficiency), fourth order
@@ -611,6 +630,8 @@ def run_ours(args):
             out["flux_variants"][key] = r["fp32_mixed"]
         # moving mesh (direct ALE), rank 0's GPU
         out["ale_explosion2d_p3"] = ale_rate(cw, stream, barrier)
+        if rank == 0 and not args.no_cpu_baseline:
+            out["ale_explosion2d_p3"]["cpu_baseline"] = ale_oracle_rate()
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_run(name)
     if rank == 0:

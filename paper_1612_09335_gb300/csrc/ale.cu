@@ -31,6 +31,7 @@
 
 #include "../../include/cweno.h"
 #include "ale.h"
+#include "lsq_kernels.cuh"
 
 namespace cw {
 
@@ -43,6 +44,7 @@ struct AleTab {
   double val[2][kLmax][kLmax];
   uint8_t col[2][kLmax][kLmax];
   int nnz[2][kLmax];
+  int nnz0[2][kLmax];  // of which on tau = 0 nodes (listed first)
   double Gal[kL1max][kLmax];    // (K_tau^1)^-1 M^1
   double C0[kL1max][kL0max];    // theta_n(xi_k, 0): constant extension in time
   double Wv[3][kLmax];          // int_0^1 theta_l(vertex v, tau) dtau
@@ -107,6 +109,22 @@ __global__ void __launch_bounds__(256) k_ale_geom(const double* __restrict__ Xv,
 __global__ void k_ale_dt_reset(unsigned long long* dtmin) { dtmin[0] = 0x7ff0000000000000ull; }
 
 // ---------------------------------------------------------------- predictor
+// Euler fluxes (x and y) and the mesh velocity of one nodal state.
+__device__ __forceinline__ void ale_flux(const double* q, double gamma, int mode, double F[2][4], double V[2]) {
+  const double ir = 1.0 / q[0], u = q[1] * ir, vv = q[2] * ir;
+  const double p = (gamma - 1.0) * (q[3] - 0.5 * (q[1] * u + q[2] * vv));
+  F[0][0] = q[1];
+  F[0][1] = q[1] * u + p;
+  F[0][2] = q[2] * u;
+  F[0][3] = u * (q[3] + p);
+  F[1][0] = q[2];
+  F[1][1] = q[1] * vv;
+  F[1][2] = q[2] * vv + p;
+  F[1][3] = vv * (q[3] + p);
+  V[0] = mode == CWENO_MOTION_LAGRANGE ? u : 0.0;
+  V[1] = mode == CWENO_MOTION_LAGRANGE ? vv : 0.0;
+}
+
 // One thread per cell.  w: reconstruction values at the lattice nodes
 // (N x L0 x 4); X: unwrapped vertices of T_i^n.  Writes q_hat (N x L x 4) and,
 // per vertex k of the cell, (mu V_kj, mu) with mu = rho_j |T_j| and V_kj the
@@ -134,46 +152,66 @@ __global__ void __launch_bounds__(128) k_ale_pred(const __grid_constant__ AleTab
   for (int l = 0; l < L; ++l)
     for (int a = 0; a < 2; ++a)
       x[l][a] = Xi[a] + (Xi[3 + a] - Xi[a]) * t.node[l][0] + (Xi[6 + a] - Xi[a]) * t.node[l][1];
-  double V[L][2];
-  for (int it = 0; it < niter; ++it) {
-    double F[L][2][4];
-    for (int l = 0; l < L; ++l) {
-      const double r = q[l][0], u = q[l][1] / r, vv = q[l][2] / r;
-      const double p = pressure(q[l], t.gamma);
-      F[l][0][0] = q[l][1];
-      F[l][0][1] = q[l][1] * u + p;
-      F[l][0][2] = q[l][2] * u;
-      F[l][0][3] = u * (q[l][3] + p);
-      F[l][1][0] = q[l][2];
-      F[l][1][1] = q[l][1] * vv;
-      F[l][1][2] = q[l][2] * vv + p;
-      F[l][1][3] = vv * (q[l][3] + p);
-      V[l][0] = t.mode == CWENO_MOTION_LAGRANGE ? u : 0.0;
-      V[l][1] = t.mode == CWENO_MOTION_LAGRANGE ? vv : 0.0;
-    }
-    double H[L][4];
-    for (int n = 0; n < L; ++n) {
-      // xi-derivatives at node n of the interpolants of x, q and F (one pass
-      // over the nonzero entries per direction)
-      double dx[2][2], dq[2][4], df[2][2][4];
+  // The tau = 0 nodes never change: their fluxes and mesh velocities, their
+  // part of every xi-derivative (200 of the 284 nonzero entries at M = 3)
+  // and the constant extensions C0 q^0, C0 x^0 (the initial tau > 0 values)
+  // are formed once.
+  double qe[L1][4], xe[L1][2], V[L][2];
+  for (int k = 0; k < L1; ++k) {
+    for (int v = 0; v < 4; ++v) qe[k][v] = q[L0 + k][v];
+    for (int a = 0; a < 2; ++a) xe[k][a] = x[L0 + k][a];
+  }
+  double c0[L][2][14];  // per node and direction: d x (2), d q (4), d F (2 x 4) over tau = 0 nodes
+  {
+    double F0[L0][2][4];
+    for (int l = 0; l < L0; ++l) ale_flux(q[l], t.gamma, t.mode, F0[l], V[l]);
+    for (int n = 0; n < L; ++n)
       for (int e = 0; e < 2; ++e) {
-        for (int a = 0; a < 2; ++a) dx[e][a] = 0.0;
-        for (int v = 0; v < 4; ++v) dq[e][v] = df[e][0][v] = df[e][1][v] = 0.0;
-        const int cnt = t.nnz[e][n];
-        for (int j = 0; j < cnt; ++j) {
+        double* c = c0[n][e];
+        for (int m = 0; m < 14; ++m) c[m] = 0.0;
+        for (int j = 0; j < t.nnz0[e][n]; ++j) {
           const int l = t.col[e][n][j];
           const double dd = t.val[e][n][j];
-          for (int a = 0; a < 2; ++a) dx[e][a] += dd * x[l][a];
+          for (int a2 = 0; a2 < 2; ++a2) c[a2] += dd * x[l][a2];
+          for (int v = 0; v < 4; ++v) {
+            c[2 + v] += dd * q[l][v];
+            c[6 + v] += dd * F0[l][0][v];
+            c[10 + v] += dd * F0[l][1][v];
+          }
+        }
+      }
+  }
+  for (int it = 0; it < niter; ++it) {
+    double F[L1][2][4];
+    for (int l = L0; l < L; ++l) ale_flux(q[l], t.gamma, t.mode, F[l - L0], V[l]);
+    double H[L][4];
+    for (int n = 0; n < L; ++n) {
+      // xi-derivatives at node n of the interpolants of x, q and F: the cached
+      // tau = 0 part plus one pass over the remaining nonzero entries
+      double dx[2][2], dq[2][4], df[2][2][4];
+      for (int e = 0; e < 2; ++e) {
+        const double* c = c0[n][e];
+        for (int a2 = 0; a2 < 2; ++a2) dx[e][a2] = c[a2];
+        for (int v = 0; v < 4; ++v) {
+          dq[e][v] = c[2 + v];
+          df[e][0][v] = c[6 + v];
+          df[e][1][v] = c[10 + v];
+        }
+        const int cnt = t.nnz[e][n];
+        for (int j = t.nnz0[e][n]; j < cnt; ++j) {
+          const int l = t.col[e][n][j];
+          const double dd = t.val[e][n][j];
+          for (int a2 = 0; a2 < 2; ++a2) dx[e][a2] += dd * x[l][a2];
           for (int v = 0; v < 4; ++v) {
             dq[e][v] += dd * q[l][v];
-            df[e][0][v] += dd * F[l][0][v];
-            df[e][1][v] += dd * F[l][1][v];
+            df[e][0][v] += dd * F[l - L0][0][v];
+            df[e][1][v] += dd * F[l - L0][1][v];
           }
         }
       }
       // d x / d xi of the isoparametric map at node n (J[a][e] = dx[e][a]) and its inverse
-      const double det = dx[0][0] * dx[1][1] - dx[1][0] * dx[0][1];
-      const double Ji[2][2] = {{dx[1][1] / det, -dx[1][0] / det}, {-dx[0][1] / det, dx[0][0] / det}};
+      const double idet = 1.0 / (dx[0][0] * dx[1][1] - dx[1][0] * dx[0][1]);
+      const double Ji[2][2] = {{dx[1][1] * idet, -dx[1][0] * idet}, {-dx[0][1] * idet, dx[0][0] * idet}};
       double dxidt[2];
       for (int e = 0; e < 2; ++e) dxidt[e] = -(Ji[e][0] * V[n][0] + Ji[e][1] * V[n][1]);
       for (int v = 0; v < 4; ++v) {
@@ -183,22 +221,16 @@ __global__ void __launch_bounds__(128) k_ale_pred(const __grid_constant__ AleTab
       }
     }
     for (int k = 0; k < L1; ++k) {
-      double qn[4], xn[2];
       for (int v = 0; v < 4; ++v) {
-        double s = 0.0, g = 0.0;
-        for (int n = 0; n < L0; ++n) s += t.C0[k][n] * q[n][v];
+        double g = 0.0;
         for (int l = 0; l < L; ++l) g += t.Gal[k][l] * H[l][v];
-        qn[v] = s - dt * g;
+        q[L0 + k][v] = qe[k][v] - dt * g;
       }
-      for (int a = 0; a < 2; ++a) {
-        double s = 0.0, g = 0.0;
-        for (int n = 0; n < L0; ++n) s += t.C0[k][n] * x[n][a];
-        for (int l = 0; l < L; ++l) g += t.Gal[k][l] * V[l][a];
-        xn[a] = s + dt * g;
+      for (int a2 = 0; a2 < 2; ++a2) {
+        double g = 0.0;
+        for (int l = 0; l < L; ++l) g += t.Gal[k][l] * V[l][a2];
+        x[L0 + k][a2] = xe[k][a2] + dt * g;
       }
-      // the right-hand sides read only tau = 0 nodes and H, V: update in place
-      for (int v = 0; v < 4; ++v) q[L0 + k][v] = qn[v];
-      for (int a = 0; a < 2; ++a) x[L0 + k][a] = xn[a];
     }
   }
   double qb[4];
@@ -212,8 +244,9 @@ __global__ void __launch_bounds__(128) k_ale_pred(const __grid_constant__ AleTab
   }
   for (int l = 0; l < L; ++l) {
     for (int v = 0; v < 4; ++v) qhat[(i * L + l) * 4 + v] = q[l][v];
-    V[l][0] = t.mode == CWENO_MOTION_LAGRANGE ? q[l][1] / q[l][0] : 0.0;
-    V[l][1] = t.mode == CWENO_MOTION_LAGRANGE ? q[l][2] / q[l][0] : 0.0;
+    const double ir = 1.0 / q[l][0];
+    V[l][0] = t.mode == CWENO_MOTION_LAGRANGE ? q[l][1] * ir : 0.0;
+    V[l][1] = t.mode == CWENO_MOTION_LAGRANGE ? q[l][2] * ir : 0.0;
   }
   const double mu = qb[0] * vol[i];
   for (int k = 0; k < 3; ++k) {
@@ -342,16 +375,17 @@ __global__ void __launch_bounds__(128) k_ale_flux(const __grid_constant__ AleTab
       double n[3];
       st_normal(fg, t.chi[qp], t.tq[tt], dt, n);
       for (int a = 0; a < 3; ++a) n[a] *= sgn;
-      const double nx = sqrt(n[0] * n[0] + n[1] * n[1]);
-      const double un[2] = {n[0] / nx, n[1] / nx};
-      const double Vn = -n[2] / nx;
+      const double nx = sqrt(n[0] * n[0] + n[1] * n[1]), inx = 1.0 / nx;
+      const double un[2] = {n[0] * inx, n[1] * inx};
+      const double Vn = -n[2] * inx;
       double sm = 0.0, fsum[4];
       const double* sides[2] = {qm, qq};
       for (int v = 0; v < 4; ++v) fsum[v] = 0.0;
       for (int s = 0; s < 2; ++s) {
         const double* z = sides[s];
-        const double r = z[0], u = z[1] / r, vv = z[2] / r, p = pressure(z, t.gamma);
-        const double c = sqrt(fmax(0.0, t.gamma * p / r));
+        const double ir = 1.0 / z[0], u = z[1] * ir, vv = z[2] * ir;
+        const double p = (t.gamma - 1.0) * (z[3] - 0.5 * (z[1] * u + z[2] * vv));
+        const double c = sqrt(fmax(0.0, t.gamma * p * ir));
         const double vn = u * un[0] + vv * un[1];
         sm = fmax(sm, fabs(vn - Vn) + c);
         fsum[0] += z[1] * n[0] + z[2] * n[1];
@@ -468,6 +502,29 @@ cudaError_t launch_flux(Ale& A, cweno_solver* s, double dtf, cudaStream_t st) {
 
 }  // namespace
 
+// Per-step rebuild for a moving mesh: this unit keeps FMA contraction (the
+// matrices change every step; the host setup's exact arithmetic is not needed).
+int ale_matrices_device(const MeshHost& m, const RefElem& re, const double* d_X, const double* d_bary,
+                        const int32_t* d_sten, const int32_t* d_sec, double* d_R, double* d_Binv, int* d_bad,
+                        void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  LsqTab tab;
+  std::string err;
+  if (!make_tab(m, re, tab, err)) return CWENO_EINVAL;
+  cudaError_t e = dispatch<double>(m.d, re.M, d_X, d_bary, d_sten, m.nc, tab, d_R, d_bad, st);
+  if (e == cudaSuccess && m.d == 2) {
+    switch (re.M) {
+      case 1: e = launch_sectors<2, 1>(d_X, d_bary, d_sec, m.nc, tab, d_Binv, d_bad, st); break;
+      case 2: e = launch_sectors<2, 2>(d_X, d_bary, d_sec, m.nc, tab, d_Binv, d_bad, st); break;
+      case 3: e = launch_sectors<2, 3>(d_X, d_bary, d_sec, m.nc, tab, d_Binv, d_bad, st); break;
+      default: e = cudaErrorInvalidValue;
+    }
+  } else if (e == cudaSuccess) {
+    e = cudaErrorInvalidValue;
+  }
+  return e == cudaSuccess ? CWENO_OK : CWENO_ECUDA;
+}
+
 int ale_create(cweno_solver* s, const MeshHost& m, std::string& err) {
   const RefElem& re = *s->re;
   if (m.d != 2 || s->pde != CWENO_EULER || s->prec != CWENO_FP64 || re.M > 3 ||
@@ -502,6 +559,7 @@ int ale_create(cweno_solver* s, const MeshHost& m, std::string& err) {
           t.val[e][n][c] = v;
           t.col[e][n][c] = (uint8_t)l;
           ++c;
+          if (l < L0) t.nnz0[e][n] = c;  // columns ascend: tau = 0 nodes first
         }
         t.nnz[e][n] = c;
       }

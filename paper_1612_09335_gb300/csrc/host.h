@@ -58,7 +58,7 @@ int build_cell_setup(const MeshHost& m, const RefElem& re, CellSetup& cs, std::s
 int lsq_setup_device(const MeshHost& m, const RefElem& re, const int32_t* d_sten, void* d_R, int fp32,
                      void* stream, std::string& err);
 
-// Moving meshes (setup_gpu.cu, two dimensions, FP64): rebuild on the device
+// Moving meshes (ale.cu, two dimensions, FP64): rebuild on the device
 // the least-squares pseudo-inverses R and the sector inverses Binv of every
 // cell from the unwrapped cell vertices d_X (nc x (d+1) x 3, internal order)
 // and barycentres d_bary (nc x 3) of the current mesh, for the fixed

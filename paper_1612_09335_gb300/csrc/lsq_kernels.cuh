@@ -1,0 +1,329 @@
+// Least-squares reconstruction matrices on the device (Sec. 2.1, Eq.
+// CWENO:Popt), shared by the fixed-mesh setup (setup_gpu.cu, compiled without
+// FMA contraction, the host setup's arithmetic) and the per-step rebuild on
+// moving meshes (ale.cu): for every cell, the averages of the Dubiner basis
+// functions psi_1..psi_{Mc-1} of its reference frame over the cells of its
+// central stencil (the constrained problem with the constant part removed),
+// the pseudo-inverse R_i of that (n_e - 1) x (Mc - 1) matrix by modified
+// Gram-Schmidt with one reorthogonalisation pass, written in the SoA layout
+// the reconstruction kernel reads; and the sector inverses of Eq. (CWENO:Ps).
+// FP64 throughout, one thread per cell.  Each including translation unit gets
+// its own copy (unnamed namespace).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "../../include/cweno.h"
+#include "host.h"
+
+namespace cw {
+
+namespace {
+
+constexpr int kMaxQ = 27, kMaxB = 35, kMaxRec = 11 * 5;
+
+// reference data of one (d, M) as a kernel parameter
+struct LsqTab {
+  int nq;
+  double qx[kMaxQ][3];
+  double qw[kMaxQ];
+  double wsum;
+  int nb;
+  int pqr[kMaxB][3];
+  double norm[kMaxB];
+  double rec[kMaxRec][3];  // [(alpha * (M + 1) + k)]
+  double Lper[3];
+  int per[3];
+};
+
+__host__ __device__ constexpr int cmc(int M, int d) {
+  return d == 2 ? (M + 1) * (M + 2) / 2 : (M + 1) * (M + 2) * (M + 3) / 6;
+}
+
+template <int M>
+__device__ void jacobi_seq(const LsqTab& t, int alpha, int nmax, double u, double s, double* p) {
+  p[0] = 1.0;
+  if (nmax < 1) return;
+  p[1] = 0.5 * ((alpha + 2.0) * u + alpha * s);
+  for (int k = 2; k <= nmax; ++k) {
+    const double* r = t.rec[alpha * (M + 1) + k];
+    p[k] = (r[0] * s + r[1] * u) * p[k - 1] - r[2] * s * s * p[k - 2];
+  }
+}
+
+// all Dubiner basis functions at xi (psi_0 = 1), shared Jacobi sequences
+template <int D, int M>
+__device__ void dubiner(const LsqTab& t, const double* xi, double* out) {
+  double f1[M + 1], f2[M + 1][M + 1], f3[M + 1];
+  if (D == 2) {
+    const double s1 = 1.0 - xi[1], u1 = 2.0 * xi[0] - s1;
+    jacobi_seq<M>(t, 0, M, u1, s1, f1);
+    for (int p = 0; p <= M; ++p) jacobi_seq<M>(t, 2 * p + 1, M - p, 2.0 * xi[1] - 1.0, 1.0, f2[p]);
+    out[0] = 1.0;
+    for (int l = 1; l < t.nb; ++l) out[l] = t.norm[l] * (f1[t.pqr[l][0]] * f2[t.pqr[l][0]][t.pqr[l][1]]);
+    return;
+  }
+  const double s1 = 1.0 - xi[1] - xi[2], u1 = 2.0 * xi[0] - s1;
+  const double s2 = 1.0 - xi[2], u2 = 2.0 * xi[1] - s2;
+  jacobi_seq<M>(t, 0, M, u1, s1, f1);
+  for (int p = 0; p <= M; ++p) jacobi_seq<M>(t, 2 * p + 1, M - p, u2, s2, f2[p]);
+  out[0] = 1.0;
+  for (int l = 1; l < t.nb; ++l) {
+    const int p = t.pqr[l][0], q = t.pqr[l][1], r = t.pqr[l][2];
+    jacobi_seq<M>(t, 2 * p + 2 * q + 2, r, 2.0 * xi[2] - 1.0, 1.0, f3);
+    out[l] = t.norm[l] * (f1[p] * f2[p][q] * f3[r]);
+  }
+}
+
+template <int D>
+__device__ void jac_inv(const double* X, double Ji[3][3]) {
+  double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  for (int a = 0; a < D; ++a)
+    for (int k = 0; k < D; ++k) J[a][k] = X[(k + 1) * 3 + a] - X[a];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) Ji[a][b] = 0.0;
+  if (D == 2) {
+    const double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    Ji[0][0] = J[1][1] / det;
+    Ji[0][1] = -J[0][1] / det;
+    Ji[1][0] = -J[1][0] / det;
+    Ji[1][1] = J[0][0] / det;
+    return;
+  }
+  const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+  const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+  const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+  const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+  Ji[0][0] = c00 / det;
+  Ji[1][0] = c01 / det;
+  Ji[2][0] = c02 / det;
+  Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+  Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+  Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+  Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+  Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+  Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+}
+
+// X: nc x (D+1) x 3 unwrapped vertices, bary: nc x 3, sten: SoA [k N + i].
+// bad: smallest internal index of a cell whose system is rank deficient.
+template <int D, int M, typename T>
+__global__ void __launch_bounds__(128) k_lsq(const double* __restrict__ X, const double* __restrict__ bary,
+                                             const int32_t* __restrict__ sten, int64_t N, const LsqTab tab,
+                                             T* __restrict__ R, int* bad) {
+  constexpr int MC = cmc(M, D), NE1 = D * MC - 1, MC1 = MC - 1, NX = (D + 1) * 3;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double* Xi = X + i * NX;
+  double Ji[3][3];
+  jac_inv<D>(Xi, Ji);
+  double Qm[NE1][MC1];
+  double psi[MC];
+  for (int r = 0; r < NE1; ++r) {
+    const int64_t j = sten[(int64_t)r * N + i];
+    const double* Xj = X + j * NX;
+    double s[3];
+    for (int a = 0; a < 3; ++a) {
+      s[a] = 0.0;
+      if (a < D && tab.per[a])
+        s[a] = tab.Lper[a] * nearbyint((bary[i * 3 + a] - bary[j * 3 + a]) / tab.Lper[a]);
+    }
+    double acc[MC];
+    for (int l = 0; l < MC; ++l) acc[l] = 0.0;
+    for (int g = 0; g < tab.nq; ++g) {
+      double x[3] = {0, 0, 0};
+      for (int a = 0; a < D; ++a) {
+        x[a] = Xj[a] + s[a];
+        for (int k = 0; k < D; ++k) x[a] += tab.qx[g][k] * (Xj[(k + 1) * 3 + a] - Xj[a]);
+      }
+      double xi[3] = {0, 0, 0};
+      for (int a = 0; a < D; ++a)
+        for (int b = 0; b < D; ++b) xi[a] += Ji[a][b] * (x[b] - Xi[b]);
+      dubiner<D, M>(tab, xi, psi);
+      for (int l = 1; l < MC; ++l) acc[l] += tab.qw[g] * psi[l];
+    }
+    for (int l = 1; l < MC; ++l) Qm[r][l - 1] = acc[l] / tab.wsum;
+  }
+  // modified Gram-Schmidt with one reorthogonalisation pass: A = Q Rm
+  double Rm[MC1][MC1];
+  for (int a = 0; a < MC1; ++a)
+    for (int b = 0; b < MC1; ++b) Rm[a][b] = 0.0;
+  bool ok = true;
+  for (int k = 0; k < MC1; ++k) {
+    for (int pass = 0; pass < 2; ++pass)
+      for (int j = 0; j < k; ++j) {
+        double sdot = 0.0;
+        for (int r = 0; r < NE1; ++r) sdot += Qm[r][j] * Qm[r][k];
+        Rm[j][k] += sdot;
+        for (int r = 0; r < NE1; ++r) Qm[r][k] -= sdot * Qm[r][j];
+      }
+    double nn = 0.0;
+    for (int r = 0; r < NE1; ++r) nn += Qm[r][k] * Qm[r][k];
+    nn = sqrt(nn);
+    Rm[k][k] = nn;
+    if (nn == 0.0) {
+      ok = false;
+      break;
+    }
+    for (int r = 0; r < NE1; ++r) Qm[r][k] /= nn;
+  }
+  if (ok) {
+    double dmax = 0.0;
+    for (int k = 0; k < MC1; ++k) dmax = fmax(dmax, fabs(Rm[k][k]));
+    for (int k = 0; k < MC1; ++k)
+      if (fabs(Rm[k][k]) <= 1e-13 * dmax) ok = false;
+  }
+  if (!ok) {
+    atomicMin(bad, (int)i);
+    return;
+  }
+  // pinv = Rm^{-1} Q^T, column by column of Q^T, written as R[(l NE1 + r) N + i]
+  for (int r = 0; r < NE1; ++r) {
+    double col[MC1];
+    for (int k = MC1 - 1; k >= 0; --k) {
+      double sv = Qm[r][k];
+      for (int j = k + 1; j < MC1; ++j) sv -= Rm[k][j] * col[j];
+      col[k] = sv / Rm[k][k];
+    }
+    for (int k = 0; k < MC1; ++k) R[((int64_t)k * NE1 + r) * N + i] = (T)col[k];
+  }
+}
+
+// Moving meshes: the sector inverses of Eq. (CWENO:Ps) for the fixed sector
+// cells on the current geometry, B[k][l] = psi_{1+l}(xi_i(b_jk)) (b_jk the
+// minimum-image barycentre of the k-th cell of sector s, xi_i the reference
+// coordinates of cell i) and Binv[((s D + e) D + k) N + i] = (B^-1)[e][k],
+// the layout the reconstruction kernel reads.  Dropped sectors (first id
+// < 0) are skipped.  bad: smallest cell index with a singular B.
+template <int D, int M>
+__global__ void __launch_bounds__(128) k_sectors(const double* __restrict__ X, const double* __restrict__ bary,
+                                                 const int32_t* __restrict__ sec, int64_t N, const LsqTab tab,
+                                                 double* __restrict__ Binv, int* bad) {
+  constexpr int MC = cmc(M, D), NX = (D + 1) * 3;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double* Xi = X + i * NX;
+  double Ji[3][3];
+  jac_inv<D>(Xi, Ji);
+  double psi[MC];
+  for (int s = 0; s <= D; ++s) {
+    if (sec[(int64_t)(s * D) * N + i] < 0) continue;
+    double B[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int k = 0; k < D; ++k) {
+      const int64_t j = sec[(int64_t)(s * D + k) * N + i];
+      double xi[3] = {0, 0, 0};
+      for (int a = 0; a < D; ++a) {
+        double sh = 0.0;
+        if (tab.per[a]) sh = tab.Lper[a] * nearbyint((bary[i * 3 + a] - bary[j * 3 + a]) / tab.Lper[a]);
+        const double db = bary[j * 3 + a] + sh - Xi[a];
+        for (int b = 0; b < D; ++b) xi[b] += Ji[b][a] * db;
+      }
+      dubiner<D, M>(tab, xi, psi);
+      for (int l = 0; l < D; ++l) B[k][l] = psi[1 + l];
+    }
+    double Bi[3][3];
+    double det;
+    if (D == 2) {
+      det = B[0][0] * B[1][1] - B[0][1] * B[1][0];
+      Bi[0][0] = B[1][1] / det;
+      Bi[0][1] = -B[0][1] / det;
+      Bi[1][0] = -B[1][0] / det;
+      Bi[1][1] = B[0][0] / det;
+    } else {
+      const double c00 = B[1][1] * B[2][2] - B[1][2] * B[2][1];
+      const double c01 = B[1][2] * B[2][0] - B[1][0] * B[2][2];
+      const double c02 = B[1][0] * B[2][1] - B[1][1] * B[2][0];
+      det = B[0][0] * c00 + B[0][1] * c01 + B[0][2] * c02;
+      Bi[0][0] = c00 / det;
+      Bi[1][0] = c01 / det;
+      Bi[2][0] = c02 / det;
+      Bi[0][1] = (B[0][2] * B[2][1] - B[0][1] * B[2][2]) / det;
+      Bi[1][1] = (B[0][0] * B[2][2] - B[0][2] * B[2][0]) / det;
+      Bi[2][1] = (B[0][1] * B[2][0] - B[0][0] * B[2][1]) / det;
+      Bi[0][2] = (B[0][1] * B[1][2] - B[0][2] * B[1][1]) / det;
+      Bi[1][2] = (B[0][2] * B[1][0] - B[0][0] * B[1][2]) / det;
+      Bi[2][2] = (B[0][0] * B[1][1] - B[0][1] * B[1][0]) / det;
+    }
+    if (!(det != 0.0) || !isfinite(det)) {
+      atomicMin(bad, (int)i);
+      continue;
+    }
+    for (int e = 0; e < D; ++e)
+      for (int k = 0; k < D; ++k) Binv[(int64_t)((s * D + e) * D + k) * N + i] = Bi[e][k];
+  }
+}
+
+template <int D, int M, typename T>
+cudaError_t launch(const double* X, const double* bary, const int32_t* sten, int64_t N, const LsqTab& tab, void* R,
+                   int* bad, cudaStream_t st) {
+  const unsigned nb = (unsigned)((N + 127) / 128);
+  k_lsq<D, M, T><<<nb, 128, 0, st>>>(X, bary, sten, N, tab, (T*)R, bad);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t dispatch(int d, int M, const double* X, const double* bary, const int32_t* sten, int64_t N,
+                     const LsqTab& tab, void* R, int* bad, cudaStream_t st) {
+  if (d == 2) {
+    switch (M) {
+      case 1: return launch<2, 1, T>(X, bary, sten, N, tab, R, bad, st);
+      case 2: return launch<2, 2, T>(X, bary, sten, N, tab, R, bad, st);
+      case 3: return launch<2, 3, T>(X, bary, sten, N, tab, R, bad, st);
+      case 4: return launch<2, 4, T>(X, bary, sten, N, tab, R, bad, st);
+    }
+  } else {
+    switch (M) {
+      case 1: return launch<3, 1, T>(X, bary, sten, N, tab, R, bad, st);
+      case 2: return launch<3, 2, T>(X, bary, sten, N, tab, R, bad, st);
+      case 3: return launch<3, 3, T>(X, bary, sten, N, tab, R, bad, st);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+namespace {
+
+bool make_tab(const MeshHost& m, const RefElem& re, LsqTab& tab, std::string& err) {
+  const int d = m.d, M = re.M;
+  SimplexQuad Q = simplex_quad(d, (M + 2) / 2);
+  if ((int)Q.w.size() > kMaxQ || re.psi.n > kMaxB || (2 * M + 3) * (M + 1) > kMaxRec) {
+    err = "least-squares tables exceed the device setup limits";
+    return false;
+  }
+  tab.nq = (int)Q.w.size();
+  tab.wsum = 0.0;
+  for (int g = 0; g < tab.nq; ++g) {
+    for (int a = 0; a < 3; ++a) tab.qx[g][a] = Q.x[g][a];
+    tab.qw[g] = Q.w[g];
+    tab.wsum += Q.w[g];
+  }
+  tab.nb = re.psi.n;
+  for (int l = 0; l < tab.nb; ++l) {
+    for (int a = 0; a < 3; ++a) tab.pqr[l][a] = re.psi.pqr[l][a];
+    tab.norm[l] = re.psi.norm[l];
+  }
+  for (size_t k = 0; k < re.psi.rec.size(); ++k)
+    for (int a = 0; a < 3; ++a) tab.rec[k][a] = re.psi.rec[k][a];
+  for (int a = 0; a < 3; ++a) {
+    tab.per[a] = m.per[a] ? 1 : 0;
+    tab.Lper[a] = m.Lper[a];
+  }
+  return true;
+}
+
+template <int D, int M>
+cudaError_t launch_sectors(const double* X, const double* bary, const int32_t* sec, int64_t N, const LsqTab& tab,
+                           double* Binv, int* bad, cudaStream_t st) {
+  k_sectors<D, M><<<(unsigned)((N + 127) / 128), 128, 0, st>>>(X, bary, sec, N, tab, Binv, bad);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+}  // namespace cw
