@@ -1805,8 +1805,9 @@ bool ale_step(OSolver& S, const double* Q, double dt, int mode, double* Qnew, do
       mu[g] += mass;
     }
   }
-  for (long g = 0; g < m.nv; ++g)
-    for (int a = 0; a < d; ++a) xyz_new[g * d + a] = m.xyz[g * d + a] + dt * (acc[g * d + a] / mu[g]);
+  for (long g = 0; g < m.nv; ++g)  // a vertex of no cell keeps its position
+    for (int a = 0; a < d; ++a)
+      xyz_new[g * d + a] = mu[g] > 0.0 ? m.xyz[g * d + a] + dt * (acc[g * d + a] / mu[g]) : m.xyz[g * d + a];
   // geometry at t^{n+1}
   OMesh m1 = m;
   m1.xyz.assign(xyz_new, xyz_new + m.nv * d);
