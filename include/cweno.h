@@ -6,7 +6,9 @@
  * WENO schemes on unstructured meshes" (arXiv 1612.09335).  One time step
  * is: CWENO reconstruction (Sec. 2.1), local space-time Galerkin predictor
  * (Sec. 2.2), space-time-quadrature Rusanov face fluxes and the conservative
- * one-step update (Sec. 2.4, Eq. PDEfinal with zero mesh velocity).
+ * one-step update (Sec. 2.4, Eq. PDEfinal with zero mesh velocity).  On 2D
+ * triangle meshes the same step also runs on a moving mesh (direct ALE,
+ * Secs. 2.2-2.4: cweno_params.mesh_motion, cweno_get_vertices).
  *
  * Conventions for every call:
  *   - Return value: CWENO_OK (0) or a negative CWENO_E* code.  A message

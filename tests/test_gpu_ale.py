@@ -178,3 +178,27 @@ def test_moving_mesh_rejects_the_fixed_mesh_diagnostics(cw, wl):
     f = cw.Solver(cw.Mesh.from_workload(mesh), 3, EULER, cw.FP64)
     with pytest.raises(cw.CwenoError):
         f.get_vertices()
+
+
+def test_run_equals_step_loop_and_isolated_vertex(cw, orc, wl):
+    """ader_cweno_run on a moving mesh is the step loop, bit for bit; a vertex
+    that belongs to no cell keeps its position (as in the oracle)."""
+    import dataclasses
+    mesh, Q = inputs(wl, "vortex")
+    m2 = dataclasses.replace(mesh, xyz=np.vstack([mesh.xyz, [[0.5, 0.5]]]))
+    a, b = solver(cw, m2, 3), solver(cw, m2, 3)
+    a.set_state(Q)
+    b.set_state(Q)
+    a.run(3, 0.0)
+    for _ in range(3):
+        b.step(0.0)
+    assert np.array_equal(a.get_state(), b.get_state())
+    xa = a.get_vertices()
+    assert np.array_equal(xa, b.get_vertices())
+    assert np.array_equal(xa[-1], [0.5, 0.5])
+    o = orc.Oracle(m2, 3)
+    Qo = Q.copy()
+    for _ in range(3):
+        Qo, xo = o.ale_step(Qo, o.stable_dt(Qo))
+    assert np.abs(xa - xo).max() < 1e-12
+    assert relerr(a.get_state(), Qo) < 1e-11
