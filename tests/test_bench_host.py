@@ -22,3 +22,12 @@ def test_oracle_parallel_run_uses_worker_processes():
     import bench
     v, cores, cells, sec = bench.oracle_parallel_run("vortex2d_p2", 10, steps=1, warmup=1, nproc=2)
     assert cores == 2 and cells == 200 and v > 0 and math.isfinite(v) and sec > 0
+
+
+def test_moving_mesh_oracle_baseline_line():
+    """The oracle's ALE step timed beside the moving-mesh bench line: a
+    bounded sample, one host thread, the baseline keys of the contract."""
+    import bench
+    r = bench.ale_oracle_rate(n=6, steps=1)
+    assert r["kind"] == "oracle" and r["cores"] == 1 and r["unit"] == "cell-updates/s"
+    assert r["value"] > 0 and math.isfinite(r["value"]) and "72 triangles" in r["sample"]
