@@ -232,7 +232,7 @@ void* cweno_stream(cweno_solver* s);
 
 /* Measurement: with profiling on, ader_cweno_step brackets each of its three
  * kernels (reconstruction + predictor, face fluxes, update) with CUDA events
- * on the solver's stream.  cweno_profile_read waits for the stream and
+ * on the solver's stream (fixed meshes; a moving-mesh step records none).  cweno_profile_read waits for the stream and
  * returns the summed device milliseconds per kernel (ms[0..2]) and the
  * number of launches per kernel since the last read, then clears them. */
 int cweno_profile_enable(cweno_solver* s, int on);
