@@ -183,6 +183,26 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x: float) -> float:
+    """The largest x over the ranks of the default process group (a timed
+    region's duration: the job is as slow as its slowest replica); x itself
+    without a group.  NCCL reduces a device tensor, other backends a host one."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(ws: int, units_per_rank: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput of ws replicas (weak scaling): all units processed
+    by all ranks over the slowest rank's time."""
+    return ws * units_per_rank * steps / seconds
+
+
 def cpu_baseline_run(name, seconds_budget=20.0, cells_hint=None):
     """Time the FP64 oracle (single host thread, as it stands) on a bounded
     sample of the workload: the same scheme on a coarser mesh of the same
@@ -503,11 +523,8 @@ def run_ours(args):
     s.profile(False)
     s.sync()
     sim_time = s.time()
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * N * args.steps / (ms / 1e3)
+    ms = max_over_ranks(ms)
+    value = replica_rate(ws, N, args.steps, ms / 1e3)
     out = {"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic"}
@@ -589,12 +606,8 @@ def run_ours(args):
             s.get_state(hout)
         barrier()
         tb = time.perf_counter()
-        el = tb - ta
-        if ws > 1:
-            t = torch.tensor([el], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            el = float(t.item())
-        out["e2e"] = {"value": ws * N * ke / el, "unit": "cell-updates/s", "h2d_bytes_per_step": N * nv * 8,
+        el = max_over_ranks(tb - ta)
+        out["e2e"] = {"value": replica_rate(ws, N, ke, el), "unit": "cell-updates/s", "h2d_bytes_per_step": N * nv * 8,
                       "d2h_bytes_per_step": N * nv * 8, "steps": ke,
                       "path": "cweno_set_state(pinned host) + ader_cweno_step + cweno_get_state(pinned host)"}
     # accuracy of the FP32-mixed mode against the FP64 mode, and conservation
