@@ -8,7 +8,8 @@
 //   matrices        least-squares pseudo-inverses and sector inverses for
 //                   the fixed stencils, rebuilt on the device every step
 //                   (Sec. 2.1: on moving meshes they change with the mesh);
-//   reconstruction  the fixed-mesh CWENO kernel (rows a2-a6), values at the
+//   reconstruction  the fixed-mesh CWENO kernel (gather, P_opt, sectors,
+//                   indicators, weights), values at the
 //                   lattice nodes;
 //   k_ale_pred      space-time predictor on the moving element: state and
 //                   geometry DOFs iterated together (Eqs. CGfinal, ODEfinal)
