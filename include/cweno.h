@@ -249,12 +249,17 @@ int cweno_profile_read(cweno_solver* s, double* ms, int64_t* launches);
  *          insphere diameters, Eq. timestep)
  *   dt     device, one FP64, receives the bound
  *   stream cudaStream_t (NULL: the legacy default stream); asynchronous.
+ * dim 2 or 3 with pde CWENO_EULER, or dim 2 with CWENO_MHD_GLM (EINVAL
+ * otherwise, as cweno_setup).
  * Scratch is a file-scope device array of one partial minimum per 256 cells
  * (512 KiB), held by every GPU that loads the library until the process
  * exits, so ncells must not exceed CWENO_NOALLOC_MAX_CELLS (EINVAL
  * otherwise).  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  Calls that overlap on the GPU share the
+ * call before any stream capture.  The address is kept for the life of the
+ * process: after cudaDeviceReset (or any other teardown of the device's
+ * primary context) the array lives at a new address, so do not call this
+ * entry point again in that process.  Calls that overlap on the GPU share the
  * scratch and race; serialise them (one stream, or events).  Nothing is
  * allocated and nothing is freed. */
 #define CWENO_NOALLOC_MAX_CELLS (65536 * 256)

@@ -149,12 +149,43 @@ def cweno_mesh_create(dim: int, xyz, cells, period=None):
 NOALLOC_MAX_CELLS = 65536 * 256
 
 
+def _noalloc_check(dim: int, pde: int, Q_dev, h_dev, dt_dev) -> int:
+    """The buffers cweno_stable_dt_noalloc reads and writes, checked before
+    the call (the kernel reads ncells x nvars FP64 values of Q and ncells of
+    h and writes one FP64 value to dt): CUDA, FP64, contiguous, of the right
+    shape.  Returns ncells; raises CwenoError(EINVAL) otherwise."""
+    import torch
+    if dim not in (2, 3) or pde not in (EULER, MHD_GLM) or (dim == 3 and pde == MHD_GLM):
+        raise CwenoError(EINVAL, "dim must be 2 or 3, pde EULER or MHD_GLM (MHD-GLM on 2D meshes only)")
+    for name, t in (("Q", Q_dev), ("h", h_dev), ("dt", dt_dev)):
+        if t.dtype != torch.float64:
+            raise CwenoError(EINVAL, f"{name} must be float64, got {t.dtype}")
+        if not t.is_cuda:
+            raise CwenoError(EINVAL, f"{name} must be a CUDA tensor")
+        if not t.is_contiguous():
+            raise CwenoError(EINVAL, f"{name} must be contiguous")
+    nv = cweno_nvars(dim, pde)
+    if len(Q_dev.shape) != 2 or int(Q_dev.shape[1]) != nv:
+        raise CwenoError(EINVAL, f"Q must have shape (ncells, {nv}), got {tuple(Q_dev.shape)}")
+    n = int(Q_dev.shape[0])
+    if h_dev.numel() < n:
+        raise CwenoError(EINVAL, f"h has {h_dev.numel()} elements, fewer than the {n} cells of Q")
+    if dt_dev.numel() < 1:
+        raise CwenoError(EINVAL, "dt must hold one element")
+    devs = {Q_dev.device, h_dev.device, dt_dev.device}
+    if len(devs) != 1:
+        raise CwenoError(EINVAL, "Q, h and dt must be on one device")
+    return n
+
+
 def cweno_stable_dt_noalloc(dim: int, pde: int, Q_dev, h_dev, gamma: float, c_h: float, cfl: float, dt_dev,
                             stream: int = 0):
     """CFL bound of a state held in the caller's device buffers, allocating
     nothing (Q_dev: ncells x nvars FP64 CUDA tensor, h_dev: ncells FP64, dt_dev:
-    one FP64 element receiving the bound; asynchronous on `stream`)."""
-    n = int(Q_dev.shape[0])
+    one FP64 element receiving the bound; asynchronous on `stream`).  The
+    buffers are checked first (CwenoError EINVAL on a wrong dtype, device,
+    layout or size), so the kernel never reads past them."""
+    n = _noalloc_check(dim, pde, Q_dev, h_dev, dt_dev)
     _check(lib().cweno_stable_dt_noalloc(dim, pde, n, C.c_void_p(Q_dev.data_ptr()), C.c_void_p(h_dev.data_ptr()),
                                          float(gamma), float(c_h), float(cfl), C.c_void_p(dt_dev.data_ptr()),
                                          C.c_void_p(stream) if stream else None))

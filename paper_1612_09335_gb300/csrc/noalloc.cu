@@ -85,6 +85,7 @@ extern "C" int cweno_stable_dt_noalloc(int dim, int pde, int64_t ncells, const d
   using namespace cw;
   if (dim != 2 && dim != 3) return fail(CWENO_EINVAL, "dim must be 2 or 3");
   if (pde != CWENO_EULER && pde != CWENO_MHD_GLM) return fail(CWENO_EINVAL, "unknown pde");
+  if (dim == 3 && pde == CWENO_MHD_GLM) return fail(CWENO_EINVAL, "MHD-GLM is built for 2D meshes only");
   if (!Q || !h || !dt) return fail(CWENO_EINVAL, "null pointer");
   if (!(gamma > 1.0) || !(cfl > 0.0)) return fail(CWENO_EINVAL, "bad gamma or cfl");
   if (ncells <= 0) return fail(CWENO_EINVAL, "no cells");
@@ -114,8 +115,7 @@ extern "C" int cweno_stable_dt_noalloc(int dim, int pde, int64_t ncells, const d
   double* part = (double*)scratch;
   if (dim == 2 && pde == CWENO_EULER) k_dt_partial<2, 0><<<nb, kThreads, 0, st>>>(Q, h, ncells, gamma, c_h, part);
   else if (dim == 3 && pde == CWENO_EULER) k_dt_partial<3, 0><<<nb, kThreads, 0, st>>>(Q, h, ncells, gamma, c_h, part);
-  else if (dim == 2) k_dt_partial<2, 1><<<nb, kThreads, 0, st>>>(Q, h, ncells, gamma, c_h, part);
-  else k_dt_partial<3, 1><<<nb, kThreads, 0, st>>>(Q, h, ncells, gamma, c_h, part);
+  else k_dt_partial<2, 1><<<nb, kThreads, 0, st>>>(Q, h, ncells, gamma, c_h, part);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "k_dt_partial launch");
   k_dt_final<<<1, kThreads, 0, st>>>(part, nb, cfl, dt);

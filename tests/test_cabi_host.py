@@ -183,3 +183,70 @@ def test_edge_case_meshes(cw, wl):
                 with pytest.raises(cw.CwenoError) as e:
                     m.stencils(order)
                 assert e.value.code == cw.EDEGENERATE
+
+
+class _FakeTensor:
+    """Stands in for a tensor in the buffer checks of the allocation-free
+    time-step call: the checks read only attributes, never memory."""
+
+    def __init__(self, shape, dtype=None, is_cuda=True, contiguous=True, device="cuda:0"):
+        import torch
+        self.shape = tuple(shape)
+        self.dtype = torch.float64 if dtype is None else dtype
+        self.is_cuda = is_cuda
+        self._contig = contiguous
+        self.device = device
+
+    def is_contiguous(self):
+        return self._contig
+
+    def numel(self):
+        return int(np.prod(self.shape)) if self.shape else 1
+
+    def data_ptr(self):
+        raise AssertionError("the library must not be called when a buffer check fails")
+
+
+def test_noalloc_binding_rejects_bad_buffers(cw):
+    """The binding of cweno_stable_dt_noalloc checks every buffer before the
+    call, so the kernel (which reads ncells x nvars FP64 values of Q and
+    ncells of h) can never read past a caller's buffer: one rejection per
+    check, and 3D MHD-GLM (not built) is refused like in cweno_setup."""
+    import torch
+    F = _FakeTensor
+    good = dict(Q=F((100, 4)), h=F((100,)), dt=F((1,)))
+    assert cw._noalloc_check(2, cw.EULER, good["Q"], good["h"], good["dt"]) == 100
+    bad_cases = [
+        (2, cw.EULER, F((100, 4), dtype=torch.float32), good["h"], good["dt"], "float64"),
+        (2, cw.EULER, good["Q"], F((100,), dtype=torch.float32), good["dt"], "float64"),
+        (2, cw.EULER, good["Q"], good["h"], F((1,), dtype=torch.float32), "float64"),
+        (2, cw.EULER, F((100, 4), is_cuda=False), good["h"], good["dt"], "CUDA"),
+        (2, cw.EULER, good["Q"], F((100,), is_cuda=False), good["dt"], "CUDA"),
+        (2, cw.EULER, F((100, 4), contiguous=False), good["h"], good["dt"], "contiguous"),
+        (2, cw.EULER, F((100, 3)), good["h"], good["dt"], "shape"),
+        (3, cw.EULER, F((100, 4)), good["h"], good["dt"], "shape"),
+        (2, cw.MHD_GLM, F((100, 4)), good["h"], good["dt"], "shape"),
+        (2, cw.EULER, F((400,)), good["h"], good["dt"], "shape"),
+        (2, cw.EULER, good["Q"], F((99,)), good["dt"], "fewer"),
+        (2, cw.EULER, good["Q"], good["h"], F((0,)), "one element"),
+        (2, cw.EULER, good["Q"], F((100,), device="cuda:1"), good["dt"], "one device"),
+        (3, cw.MHD_GLM, F((100, 9)), good["h"], good["dt"], "2D meshes only"),
+        (4, cw.EULER, F((100, 6)), good["h"], good["dt"], "dim"),
+    ]
+    for dim, pde, Q, h, dt, msg in bad_cases:
+        with pytest.raises(cw.CwenoError) as e:
+            cw.cweno_stable_dt_noalloc(dim, pde, Q, h, 1.4, 2.0, 0.5, dt)
+        assert e.value.code == cw.EINVAL and msg in str(e.value), (dim, pde, msg, str(e.value))
+
+
+def test_noalloc_entry_point_rejects_before_device_access(cw):
+    """The C entry point itself refuses, before touching any pointer, the
+    sizes beyond its static scratch and the pairings the solver does not
+    build (3D MHD-GLM); no GPU is needed for either."""
+    import ctypes as C
+    L = cw.lib()
+    fake = C.c_void_p(16)
+    rc = L.cweno_stable_dt_noalloc(2, cw.EULER, cw.NOALLOC_MAX_CELLS + 1, fake, fake, 1.4, 2.0, 0.5, fake, None)
+    assert rc == cw.EINVAL and "CWENO_NOALLOC_MAX_CELLS" in L.cweno_last_error().decode()
+    rc = L.cweno_stable_dt_noalloc(3, cw.MHD_GLM, 1000, fake, fake, 5.0 / 3.0, 2.0, 0.5, fake, None)
+    assert rc == cw.EINVAL and "2D meshes only" in L.cweno_last_error().decode()

@@ -56,16 +56,17 @@ def test_noalloc_dt_matches_allocating_entry_point_twice():
 
 
 def test_noalloc_rejects_sizes_beyond_scratch():
+    """Through the C ABI on a GPU process: sizes beyond the static scratch and
+    3D MHD-GLM are refused before any device access (the pointers are never
+    read)."""
+    import ctypes as C
     import torch
     from paper_1612_09335_gb300 import binding as cw
 
-    class Fake:  # shape check happens before any device access
-        shape = (cw.NOALLOC_MAX_CELLS + 1, 4)
-
-        def data_ptr(self):
-            return 16
-
-    d = torch.zeros(1, dtype=torch.float64, device="cuda")
-    with pytest.raises(cw.CwenoError) as e:
-        cw.cweno_stable_dt_noalloc(2, cw.EULER, Fake(), d, 1.4, 2.0, 0.5, d)
-    assert e.value.code == cw.EINVAL and "CWENO_NOALLOC_MAX_CELLS" in str(e.value)
+    assert torch.cuda.is_available()
+    L = cw.lib()
+    fake = C.c_void_p(16)
+    rc = L.cweno_stable_dt_noalloc(2, cw.EULER, cw.NOALLOC_MAX_CELLS + 1, fake, fake, 1.4, 2.0, 0.5, fake, None)
+    assert rc == cw.EINVAL and "CWENO_NOALLOC_MAX_CELLS" in L.cweno_last_error().decode()
+    rc = L.cweno_stable_dt_noalloc(3, cw.MHD_GLM, 1000, fake, fake, 5.0 / 3.0, 2.0, 0.5, fake, None)
+    assert rc == cw.EINVAL and "2D meshes only" in L.cweno_last_error().decode()
