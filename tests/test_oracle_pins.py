@@ -829,3 +829,98 @@ def test_predictor_falls_back_to_cell_average_when_it_leaves_the_admissible_set(
     off = orc.Oracle(mesh, 4, EULER, params=orc.default_params(2, EULER, order=4, cfl=0.5, positivity=False))
     qo = off.predictor(Q, dt, ids=[c])[0]
     assert (qo[:, 0] <= 0).any() or (_pressure(qo) <= 0).any() or not np.isfinite(qo).all()
+
+
+def _ref_simplex_monomial_integral(a, b):
+    """int_{T_E} xi^a eta^b = a! b! / (a + b + 2)! (the Dirichlet integral)."""
+    return math.factorial(a) * math.factorial(b) / math.factorial(a + b + 2)
+
+
+def _ref_sigma(poly_xi, xi, eta, M):
+    """sum over multi-indices 1 <= |alpha| <= M (each once) of int_{T_E}
+    (d^alpha p)^2 on the reference triangle, by exact monomial integration."""
+    sp = pytest.importorskip("sympy")
+    tot = 0.0
+    for a in range(M + 1):
+        for b in range(M + 1 - a):
+            if a + b == 0:
+                continue
+            d = sp.diff(poly_xi, xi, a, eta, b)
+            pd = sp.Poly(sp.expand(d * d), xi, eta)
+            tot += sum(float(c) * _ref_simplex_monomial_integral(int(i), int(j))
+                       for (i, j), c in zip(pd.monoms(), pd.coeffs()))
+    return tot
+
+
+@pytest.mark.parametrize("order", [3, 4])
+def test_nonlinear_weights_follow_eq_weights2(orc, wl, order):
+    """The map sigma -> omega of Eqs. (weights), (weights2): omega_k proportional
+    to lambda_k / (sigma_k + eps)^r with r = 4, eps = 1e-14 inside the power,
+    lambda normalised (lambda_0 = 1e5, lambda_s = 1).
+
+    Data: exact cell averages of a random degree-M polynomial p.  Then P_opt = p
+    (pinned separately), the sectorial polynomial P_s is the plane through the
+    barycentre values (b_i, Q_i), (b_j, Q_j) of its cells, and P_0 =
+    (p - sum lambda_s P_s) / lambda_0.  The test builds all three itself (numpy
+    and sympy, nothing from the oracle but the stencil's cell ids), integrates
+    their indicators exactly in reference coordinates and compares the weights
+    with the oracle's, once at O(1) data and once scaled so that sigma is near
+    eps.  It also checks it could tell r = 2 from r = 4, and eps outside the
+    power from eps inside it."""
+    sp = pytest.importorskip("sympy")
+    M = order - 1
+    mesh = wl.tri_mesh(8, lo=(-1, -1), hi=(1, 1), periodic=False, jitter=0.2, seed=11)
+    X = mesh.cell_vertices()
+    bary = X.mean(axis=1)
+    rng = np.random.default_rng(7 + order)
+    x, y, xi, eta = sp.symbols("x y xi eta")
+    exps = [(a, b) for a in range(M + 1) for b in range(M + 1 - a)]
+    coef = rng.normal(size=len(exps))
+    p = sum(float(c) * x ** a * y ** b for c, (a, b) in zip(coef, exps))
+
+    def in_ref(expr, c):
+        X0, J = X[c, 0], (X[c, 1:] - X[c, :1]).T  # x = X0 + J (xi, eta)
+        return sp.expand(expr.subs({x: X0[0] + J[0, 0] * xi + J[0, 1] * eta,
+                                    y: X0[1] + J[1, 0] * xi + J[1, 1] * eta}, simultaneous=True))
+
+    avg = np.zeros(mesh.nc)
+    for c in range(mesh.nc):
+        pr = sp.Poly(in_ref(p, c), xi, eta)
+        avg[c] = 2.0 * sum(float(k) * _ref_simplex_monomial_integral(int(i), int(j))
+                           for (i, j), k in zip(pr.monoms(), pr.coeffs()))
+    o = orc.Oracle(mesh, order, EULER)
+    eps, lam0r, lamsr = 1e-14, 1e5, 1.0
+    cells = [c for c in range(mesh.nc) if (o.stencil(c)[1] >= 0).all()][::3][:8]
+    assert len(cells) >= 5
+    for scale in (1.0, None):
+        for c in cells:
+            sec = o.stencil(c)[1]
+            planes = []
+            for s in range(3):
+                pts = np.vstack([bary[c], bary[sec[s]]])
+                A = np.hstack([np.ones((3, 1)), pts])
+                planes.append(np.linalg.solve(A, np.concatenate([[avg[c]], avg[sec[s]]])))
+            ns = 3
+            lam0, lams = lam0r / (lam0r + ns * lamsr), lamsr / (lam0r + ns * lamsr)
+            P0 = (p - lams * sum(a0 + a1 * x + a2 * y for a0, a1, a2 in planes)) / lam0
+            sig = np.array([_ref_sigma(in_ref(P0, c), xi, eta, M)]
+                           + [_ref_sigma(in_ref(a0 + a1 * x + a2 * y, c), xi, eta, M) for a0, a1, a2 in planes])
+            f = scale if scale is not None else math.sqrt(eps / sig[0])  # sigma_0 of the scaled data = eps
+            sig = sig * f * f
+            Q = np.zeros((mesh.nc, 4))
+            Q[:, 0] = 1.0
+            Q[:, 1] = f * avg
+            Q[:, 3] = 10.0
+            om = o.reconstruct(Q, ids=[c], want_weights=True)["omega"][0, :, 1]
+            lam = np.array([lam0] + [lams] * 3)
+
+            def weights(r, eps_inside=True):
+                wt = lam / (sig + eps) ** r if eps_inside else lam / (sig ** r + eps)
+                return wt / wt.sum()
+
+            want = weights(4)
+            assert np.allclose(om, want, rtol=1e-8, atol=0), (c, scale, om, want)
+            # the check separates the plausible mistakes
+            assert np.max(np.abs(weights(2) / want - 1)) > 1e-3
+            if scale is None:
+                assert np.max(np.abs(weights(4, eps_inside=False) / want - 1)) > 1e-3
