@@ -62,45 +62,163 @@ def mcal(M, d):
     return math.comb(M + d, d)
 
 
-def algorithmic(dim, order, pde, fp32=True):
+def pred_nonzeros(d, M):
+    """(nonzeros of P_e in the tau = 0 columns, nonzeros in the unknown-node
+    columns), summed over the d directions, from the exact zero pattern of the
+    closed-form predictor matrices (csrc/pred_pattern.h, generated in exact
+    rational arithmetic).  Zeros of P_e are structural, not the method's work."""
+    import re
+    txt = open(os.path.join(ROOT, "paper_1612_09335_gb300", "csrc", "pred_pattern.h")).read()
+    m = re.search(r"struct PredPattern<%d, %d> \{.*?return \((.*?)\)\[" % (d, M), txt, re.S)
+    bits = "".join(re.findall(r'"([01]+)"', m.group(1)))
+    L, L0 = mcal(M, d + 1), mcal(M, d)
+    L1 = L - L0
+    nz0 = nz1 = 0
+    for e in range(d):
+        for k in range(L1):
+            row = bits[(e * L1 + k) * L:(e * L1 + k + 1) * L]
+            nz0 += row[:L0].count("1")
+            nz1 += row[L0:].count("1")
+    return nz0, nz1
+
+
+def phys_flops(d, pde):
+    """Flops of the pointwise physics (an FMA counts 2, a division, reciprocal
+    or square root 1): primitive variables from a state, the normal flux
+    along a general direction, the flux along a coordinate axis, the largest
+    signal speed along a unit normal and over all directions, the pressure."""
+    if pde == 0:
+        return dict(prim=3 * d + 3, fluxn=5 * d + 2, axis=d + 4, smax=2 * d + 4, speed=2 * d + 4,
+                    pressure=2 * d + 4)
+    return dict(prim=26, fluxn=42, axis=30, smax=25, speed=20, pressure=14)
+
+
+def algorithmic(dim, order, pde, fp32=True, flux=0):
     """Algorithmic bytes and flops per unit of each kernel (a unit is a cell
-    for the reconstruction/predictor and update kernels, a face for the flux
-    kernel).  Bytes count each datum the method must move once; flops count
-    the method's arithmetic (an FMA is 2 flops)."""
+    for the reconstruction + predictor and the update kernels, a face for the
+    flux kernel).  Bytes count each datum the method must move once (stencil
+    neighbours' states are the same data as their own, read once); flops
+    count the method's arithmetic, 2 per FMA, with the exact zeros of the
+    predictor matrices skipped (they are structural in the closed form of the
+    Galerkin predictor), the positivity safeguard included (on by default and
+    timed).  `flux`: 0 quadrature Rusanov, 1 Osher-type, 2 quadrature-free."""
     d, M = dim, order - 1
     nv = 9 if pde == 1 else d + 2
     Mc, L = mcal(M, d), mcal(M, d + 1)
-    ne, L0 = d * Mc, mcal(M, d)
+    ne1, MC1, NS = d * Mc - 1, Mc - 1, d + 1
+    L0 = Mc
     L1 = L - L0
     r = 4 if fp32 else 8
     nqs = (M + 1) ** (d - 1)
     nqt = M + 1
     niter = M + 1
-    fl_flux = 3 * d * nv + 10 if pde == 0 else 60 + 4 * nv      # one normal flux incl. primitives
-    rec_bytes = (4 * (ne - 1) + r * (Mc - 1) * (ne - 1) + 4 * (d + 1) * d + r * (d + 1) * d * d + 1 + r * d * d
-                 + (8 if fp32 else 8) * nv + r * L * nv)
-    rec_flops = (3 * (ne - 1) * nv + 2 * (Mc - 1) * (ne - 1) * nv + (2 * d * d + 3 * d) * (d + 1) * nv
-                 + nv * (2 * (Mc - 1) ** 2 + (d + 1) * 2 * d * d + 4 * (Mc - 1) + 40)
-                 + L0 * nv * 2 * (Mc - 1) + L0 * (d * fl_flux + 2 * L1 * nv * (d + 2))
-                 + niter * L1 * (d * fl_flux + 2 * L1 * nv * (d + 1)))
-    flux_bytes_face = (2 / (d + 1)) * r * L * nv + 4 + 4 + 2 + r * d + r + r * nv
-    flux_flops_face = nqt * nqs * (2 * 2 * L * nv + 2 * fl_flux + 2 * 25 + 5 * nv)
-    upd_bytes = 4 * (d + 1) + (2 * r * nv) + 8 * nv * 2 + (8 * nv if fp32 else 0) + 16
-    upd_flops = (d + 1) * nv * 2 + 2 * nv + 30
+    ph = phys_flops(d, pde)
+    nz0, nz1 = pred_nonzeros(d, M)
+    rec_bytes = (4 * ne1 + r * MC1 * ne1 + 4 * NS * d + r * NS * d * d + 1 + r * d * d + 8 * nv + r * L * nv)
+    node_flux = nv + ph["prim"] + d * (ph["fluxn"] + nv)      # q = Qbar + dev, G_e - G_e(Qbar) per direction
+    rec_flops = ((ne1 + NS * d) * nv                           # stencil differences
+                 + 2 * MC1 * ne1 * nv                          # P_opt = R dQ (Eq. CWENO:Popt)
+                 + 2 * NS * d * d * nv                         # sectorial gradients (Eq. CWENO:Ps)
+                 + nv * (2 * d * NS + MC1)                     # P_0 (Eq. CWENO:P0)
+                 + nv * (2 * MC1 * MC1 + 2 * MC1 + NS * (2 * d * d + 2 * d))  # indicators (Eq. Sigma_lm)
+                 + nv * (8 * (NS + 1) + 1)                     # nonlinear weights (Eq. weights2)
+                 + nv * (MC1 + 2 * d * NS)                     # w = sum omega P
+                 + L0 * nv * 2 * MC1                           # w at the tau = 0 nodes
+                 + L0 * (ph["pressure"] + 6)                   # positivity checks at the lattice nodes
+                 + ph["prim"] + d * ph["fluxn"]                # G_e(Qbar)
+                 + L0 * node_flux + 2 * nz0 * nv               # fixed part: -sum_e P_e[:, tau=0] G_e
+                 + L1 * nv * (2 * MC1 + 1)                     # known part (C0 E) w
+                 + niter * (L1 * node_flux + 2 * nz1 * nv)     # Picard iterations (Eq. CGfinal)
+                 + L1 * (nv + ph["pressure"] + 3))             # predictor admissibility
+    # per face: both sides' predictors and cell averages (each cell's read
+    # once over its d + 1 faces), the two cell ids and codes, the unit normal,
+    # |f| n and |f| (FP64), the face integral (FP64)
+    flux_bytes_face = (2 / (d + 1)) * (r * L * nv + 8 * nv) + 4 + 4 + 2 + r * d + 8 * d + 8 + 8 * nv
+    npts = nqt * nqs
+    point = (2 * nv + 2 * ph["prim"] + 4 + 2 * d * ph["axis"] + 3 * d * nv)  # traces + averages, both fluxes
+    if flux == 1:  # Osher-type: 3-point path rule of |A_n| dq
+        point += 3 * (nv + 4 * d + 45 + 4 * nv) + 3 * nv
+    else:
+        point += 2 * ph["smax"] + 2 + 3 * nv
+    if flux == 2:  # quadrature-free: one pass over each side's L nodes
+        flux_flops_face = (2 * L * (nv + ph["prim"] + d * ph["axis"] + d * nv * 3 + 2 * nv)
+                           + 2 * ph["prim"] + 2 * ph["smax"] + 4 * nv + nv * (2 * d + 3))
+    else:
+        flux_flops_face = 2 * npts * L * nv * 2 + npts * point + nv * (2 * d + 3)
+    # face ids, face integrals (each read by its two cells: once per face),
+    # Q read and written (FP64), the FP32 hi/lo copies written, 1/|T| and h
+    upd_bytes = 4 * (d + 1) + (d + 1) / 2 * 8 * nv + 16 * nv + (8 * nv if fp32 else 0) + 16
+    upd_flops = (d + 1) * nv + 2 * nv + nv + ph["pressure"] + ph["speed"] + 4
     return dict(rec=(rec_bytes, rec_flops), flux=(flux_bytes_face, flux_flops_face), update=(upd_bytes, upd_flops))
 
 
-def peaks():
-    p = {"hbm_gbs": 6800.0, "src": "fallback"}
+def peaks(fma=None):
+    """Roofline denominators: the measured HBM copy bandwidth
+    (MEASURED_PEAKS.json, else the fallback 6800 GB/s) and the FP32 / FP64 FMA
+    rates measured on this device by cweno_measure_fma_peak (`fma`), else
+    derived from the SM count, 128 FP32 lanes per SM, 2 flops per FMA and the
+    maximum SM clock (FP64: 1/64 of that)."""
+    p = {"hbm_gbs": 6800.0, "hbm_src": "fallback"}
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         mp = json.load(open(path))
-        p = {"hbm_gbs": float(mp["hbm_gbs"]), "src": "measured", "sm_max_mhz": float(mp.get("sm_max_mhz", 2070))}
+        p = {"hbm_gbs": float(mp["hbm_gbs"]), "hbm_src": "measured (MEASURED_PEAKS.json copy bandwidth)",
+             "sm_max_mhz": float(mp.get("sm_max_mhz", 2070))}
     p.setdefault("sm_max_mhz", 2070.0)
-    # FP32 FMA pipe: 152 SMs x 128 lanes x 2 flops x max SM clock (nominal units, max clock)
-    p["fp32_tflops"] = 152 * 128 * 2 * p["sm_max_mhz"] * 1e6 / 1e12
-    p["fp64_tflops"] = 1.25  # GB300 nominal FP64
+    nsm = 152
+    try:
+        import torch
+        if torch.cuda.is_available():
+            nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    except Exception:
+        pass
+    p["sm_count"] = nsm
+    derived = nsm * 128 * 2 * p["sm_max_mhz"] * 1e6 / 1e12
+    if fma:
+        p["fp32_tflops"], p["fp64_tflops"] = fma["fp32_tflops"], fma["fp64_tflops"]
+        p["alu_src"] = (f"measured: FMA-chain kernel on {nsm} SMs at a median {fma.get('sm_mhz')} MHz "
+                        f"(derived FP32 at the max clock: {derived:.1f} TFLOP/s)")
+    else:
+        p["fp32_tflops"], p["fp64_tflops"] = derived, derived / 64
+        p["alu_src"] = f"derived: {nsm} SM x 128 FP32 lanes x 2 x {p['sm_max_mhz']:.0f} MHz (FP64 1/64)"
     return p
+
+
+def kernel_rooflines(kernel_ms, units, alg, pk, fp32=True):
+    """Per kernel: algorithmic GB/s and TFLOP/s from its average launch time,
+    the HBM and pipe fractions, and which roof binds by arithmetic intensity
+    against the ridge of the measured peaks.  Returns (kernels, dominant)."""
+    alu_peak = pk["fp32_tflops"] if fp32 else pk["fp64_tflops"]
+    ridge = alu_peak * 1e12 / (pk["hbm_gbs"] * 1e9)
+    out = {}
+    tot = sum(kernel_ms.values())
+    for name, ms in kernel_ms.items():
+        key = {"k_rec_pred": "rec", "k_flux": "flux", "k_update": "update"}[name]
+        b, f = alg[key]
+        dur = ms / 1e3
+        gbs = b * units[key] / dur / 1e9
+        tf = f * units[key] / dur / 1e12
+        inten = f / b
+        bound = "alu" if inten > ridge else "hbm"
+        out[name] = {"ms": ms, "share": ms / tot if tot else None, "bytes_per_unit": b, "flops_per_unit": f,
+                     "units": units[key], "intensity_flop_per_byte": inten, "GB/s": gbs, "TFLOP/s": tf,
+                     "hbm_frac": gbs / pk["hbm_gbs"], ("fp32_frac" if fp32 else "fp64_frac"): tf / alu_peak,
+                     "bound": bound}
+    dom = max(out, key=lambda k: out[k]["ms"])
+    return out, dom
+
+
+def roofline_line(kern, dom, pk, fp32, traffic):
+    k = kern[dom]
+    fr = "fp32_frac" if fp32 else "fp64_frac"
+    if k["bound"] == "hbm":
+        return {"bound": "hbm", "achieved": k["GB/s"], "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": k["hbm_frac"],
+                "traffic": traffic, "kernel": dom, "peak_src": pk["hbm_src"], fr: k[fr],
+                "intensity_flop_per_byte": k["intensity_flop_per_byte"]}
+    return {"bound": "alu", "achieved": k["TFLOP/s"], "peak": pk["fp32_tflops"] if fp32 else pk["fp64_tflops"],
+            "unit": "TFLOP/s", "frac": k[fr], "traffic": traffic, "kernel": dom,
+            "peak_src": pk["alu_src"] + (" (FP32 FMA)" if fp32 else " (FP64 FMA)"), "hbm_frac": k["hbm_frac"],
+            "intensity_flop_per_byte": k["intensity_flop_per_byte"]}
 
 
 def kernel_source_hash():
@@ -357,13 +475,30 @@ def serving_run(cw, nreq, steps=50, seed=42, max_slots=64, seq_sample=16):
             "note": "wall clock includes host setup (mesh, stencils, FP64 least-squares inverses)"}
 
 
-def accuracy_run(cw, m, cfg, Q0, nsteps=10):
-    """FP32-mixed against the FP64 mode (itself parity-tested against the
-    oracle) after nsteps steps with one fixed time step; per-variable L1
-    (volume weighted, relative to the variable's L1 norm) and L_inf errors,
-    and the drift of sum |T_i| Q_i in the FP32-mixed run."""
-    a = cw.Solver(m, cfg["order"], cfg["pde"], cw.FP32_MIXED)
-    b = cw.Solver(m, cfg["order"], cfg["pde"], cw.FP64)
+def accuracy_metrics(mesh, Q0, qa, qb):
+    """Per-variable L1 (volume weighted, relative to the variable's L1 norm)
+    and L_inf (relative to its max) errors of qa against qb, and the drift
+    of sum |T_i| Q_i in qa relative to the larger of the totals and the L1
+    norms (floored at 1e-6 of the largest, so identically zero variables are
+    measured at the state's scale)."""
+    import numpy as np
+    Xv = mesh.cell_vertices()
+    vol = np.abs(np.linalg.det(Xv[:, 1:] - Xv[:, :1])) / math.factorial(mesh.dim)
+    l1 = (vol @ np.abs(qa - qb)) / np.maximum(vol @ np.abs(qb), 1e-300)
+    linf = np.abs(qa - qb).max(axis=0) / np.maximum(np.abs(qb).max(axis=0), 1e-300)
+    tot0 = vol @ Q0
+    scale = np.maximum(np.maximum(np.abs(tot0), vol @ np.abs(Q0)), vol @ np.abs(qa))
+    scale = np.maximum(scale, 1e-6 * scale.max())
+    drift = np.abs(vol @ qa - tot0) / scale
+    return {"L1_rel": [float(x) for x in l1], "Linf_rel": [float(x) for x in linf],
+            "conservation_drift_rel": [float(x) for x in drift]}
+
+
+def accuracy_pair(solvers, mesh, Q0, nsteps=10):
+    """FP32-mixed against the FP64 mode after nsteps steps with one fixed
+    time step (the FP64 CFL bound of the initial state); `solvers` maps
+    "fp32_mixed" / "fp64" to live solvers of the same mesh and scheme."""
+    a, b = solvers["fp32_mixed"], solvers["fp64"]
     a.set_state(Q0)
     b.set_state(Q0)
     dt = b.stable_dt()
@@ -372,41 +507,64 @@ def accuracy_run(cw, m, cfg, Q0, nsteps=10):
         b.step(dt)
     a.sync()
     b.sync()
-    return a.get_state(), b.get_state(), dt
+    out = accuracy_metrics(mesh, Q0, a.get_state(), b.get_state())
+    out.update({"reference": "FP64 mode of the same solver (itself parity-tested against the FP64 oracle to "
+                             "1e-12, one step at full size on sampled cells)", "steps": nsteps, "dt": dt})
+    return out
 
 
-def workload_rate(cw, name, stream, barrier, steps=10, flux=0, precisions=None, inputs=None):
-    """Cell-updates/s of a benchmark workload in both precisions (same
-    timing method: CUDA events on the solver stream, device CFL step);
-    `flux` selects the face flux (0 Rusanov, 1 Osher-type, 2 quadrature-free
-    Rusanov)."""
+def time_solver(s, stream, barrier, Q0, k, warm=3):
+    """k steps with the device CFL bound after `warm` untimed ones, CUDA events
+    on the solver's stream; returns (ms per step, per-kernel mean ms)."""
     import torch
+    s.set_state(Q0)
+    for _ in range(warm):
+        s.step(0.0)
+    s.sync()
+    s.set_state(Q0)
+    s.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(k):
+        s.step(0.0)
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    kms, kn = s.profile_read()
+    s.profile(False)
+    s.sync()
+    names = ("k_rec_pred", "k_flux", "k_update")
+    return ms / k, {names[q]: kms[q] / kn[q] for q in range(3) if kn[q]}, int(sum(kn))
+
+
+def workload_rate(cw, name, stream, barrier, pk, steps=10, flux=0, precisions=None, inputs=None):
+    """Cell-updates/s of a benchmark workload in both precisions (same
+    timing method: CUDA events on the solver stream, device CFL step), the
+    per-kernel rooflines of each, and the accuracy of the FP32-mixed mode
+    against the FP64 mode; `flux` selects the face flux (0 Rusanov, 1
+    Osher-type, 2 quadrature-free Rusanov)."""
     cfg = WORKLOADS[name]
     mesh, Q0 = make_inputs(name) if inputs is None else inputs
     m = cw.Mesh.from_workload(mesh)
     res = {"cells": mesh.nc, "mesh": cfg["desc"], "order": cfg["order"],
-           "pde": "euler" if cfg["pde"] == 0 else "mhd_glm"}
+           "pde": "euler" if cfg["pde"] == 0 else "mhd_glm",
+           "flux": {0: "rusanov", 1: "osher", 2: "rusanov_quadrature_free"}[flux]}
     if precisions is None:
         precisions = ((cw.FP32_MIXED, "fp32_mixed", steps), (cw.FP64, "fp64", max(3, steps // 2)))
+    solvers = {}
     for prec, key, k in precisions:
         s = cw.Solver(m, cfg["order"], cfg["pde"], prec, stream=stream.cuda_stream, flux=flux)
-        s.set_state(Q0)
-        for _ in range(3):
-            s.step(0.0)
-        s.sync()
-        s.profile(True)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        barrier()
-        e0.record(stream)
-        for _ in range(k):
-            s.step(0.0)
-        e1.record(stream)
-        barrier()
-        ms = e0.elapsed_time(e1)
-        kms, kn = s.profile_read()
-        s.sync()
-        res[key] = {"value": mesh.nc * k / (ms / 1e3), "ms_per_step": ms / k, "steps": k,
-                    "kernel_ms": {"k_rec_pred": kms[0] / kn[0], "k_flux": kms[1] / kn[1], "k_update": kms[2] / kn[2]}}
+        ms, kern_ms, _ = time_solver(s, stream, barrier, Q0, k)
+        fp32 = prec == cw.FP32_MIXED
+        alg = algorithmic(cfg["dim"], cfg["order"], cfg["pde"], fp32=fp32, flux=flux)
+        kern, dom = kernel_rooflines(kern_ms, {"rec": mesh.nc, "flux": s.nf, "update": mesh.nc}, alg, pk, fp32)
+        res[key] = {"value": mesh.nc / (ms / 1e3), "unit": "cell-updates/s", "ms_per_step": ms, "steps": k,
+                    "kernels": kern, "roofline": roofline_line(kern, dom, pk, fp32, None)}
+        solvers[key] = s
+    if "fp32_mixed" in solvers and "fp64" in solvers:
+        res["accuracy"] = accuracy_pair(solvers, mesh, Q0)
+    for s in solvers.values():
         s.close()
     return res
 
@@ -536,58 +694,46 @@ def run_ours(args):
                      "time_step": "CFL bound computed on the device every step",
                      "l2": f"inputs larger than L2 (reconstruction matrices {r_bytes / 1e6:.0f} MB)",
                      "parallelism": f"replicas x{ws}", "simulated_time": sim_time}
-    # per-kernel roofline
-    pk = peaks()
+    out["config"]["scheme"] = ("the paper's fixed-mesh ADER-CWENO step plus the positivity safeguard "
+                               "(scaling limiter, face-point and predictor fallbacks; inactive on smooth data)")
+    # measured FMA peaks of this device (FP32, FP64), clocks sampled meanwhile
+    clk2 = ClockSampler(local)
+    time.sleep(0.2)
+    tp0 = time.perf_counter()
+    fma32 = max(cw.cweno_measure_fma_peak(False)[0] for _ in range(3))
+    fma64 = max(cw.cweno_measure_fma_peak(True)[0] for _ in range(3))
+    tp1 = time.perf_counter()
+    clk2.stop()
+    pclk = clk2.summary(tp0, tp1)
+    pk = peaks({"fp32_tflops": fma32, "fp64_tflops": fma64, "sm_mhz": pclk["sm_mhz"]})
+    out["peaks"] = {"hbm_gbs": pk["hbm_gbs"], "hbm_src": pk["hbm_src"], "fp32_fma_tflops": fma32,
+                    "fp64_fma_tflops": fma64, "sm_count": pk["sm_count"], "clocks": pclk,
+                    "how": "cweno_measure_fma_peak: 16 independent FMA chains per thread, all SMs filled, "
+                           "CUDA events, best of 3"}
+    # per-kernel rooflines of the timed region
+    names = ("k_rec_pred", "k_flux", "k_update")
+    kern_ms = {names[q]: kms[q] / kn[q] for q in range(3) if kn[q]}
     alg = algorithmic(cfg["dim"], cfg["order"], cfg["pde"], fp32=True)
-    units = {"rec": N, "flux": s.nf, "update": N}
-    kern = {"rec": "k_rec_pred", "flux": "k_flux", "update": "k_update"}
-    kernels = {}
-    tot = sum(kms)
-    for k, key in enumerate(("rec", "flux", "update")):
-        if kn[k] == 0:
-            continue
-        dur = kms[k] / kn[k] / 1e3
-        b, f = alg[key]
-        ach_gbs = b * units[key] / dur / 1e9
-        ach_tf = f * units[key] / dur / 1e12
-        kernels[kern[key]] = {"ms": kms[k] / kn[k], "share": kms[k] / tot, "GB/s": ach_gbs, "TFLOP/s": ach_tf,
-                              "hbm_frac": ach_gbs / pk["hbm_gbs"], "fp32_frac": ach_tf / pk["fp32_tflops"]}
-    dom = max(kernels, key=lambda k: kernels[k]["share"])
-    kd = kernels[dom]
-    key = {v: k for k, v in kern.items()}[dom]
-    b, f = alg[key]
-    intensity = f / b
-    ridge = pk["fp32_tflops"] * 1e12 / (pk["hbm_gbs"] * 1e9)
-    traffic = measured_traffic(dom, name)
-    if intensity > ridge:
-        out["roofline"] = {"bound": "alu", "achieved": kd["TFLOP/s"], "peak": pk["fp32_tflops"], "unit": "TFLOP/s",
-                           "frac": kd["fp32_frac"], "traffic": traffic, "kernel": dom,
-                           "peak_src": f"derived: 152 SM x 128 FP32 lanes x 2 x {pk['sm_max_mhz']:.0f} MHz",
-                           "hbm_frac": kd["hbm_frac"]}
-    else:
-        out["roofline"] = {"bound": "hbm", "achieved": kd["GB/s"], "peak": pk["hbm_gbs"], "unit": "GB/s",
-                           "frac": kd["hbm_frac"], "traffic": traffic, "kernel": dom,
-                           "peak_src": pk["src"], "fp32_frac": kd["fp32_frac"]}
+    kernels, dom = kernel_rooflines(kern_ms, {"rec": N, "flux": s.nf, "update": N}, alg, pk, True)
+    out["roofline"] = roofline_line(kernels, dom, pk, True, measured_traffic(dom, name))
+    step_bytes = sum(kernels[k]["bytes_per_unit"] * kernels[k]["units"] for k in kernels)
+    out["step_hbm_frac"] = step_bytes / (ms / args.steps / 1e3) / 1e9 / pk["hbm_gbs"]
     out["kernels"] = kernels
     out["gpu_launches"] = int(sum(kn))
     out["clocks"] = clk.summary(t0, t1)
+    solvers = {"fp32_mixed": s}
     # FP64 mode, same workload (the other precision of the metric)
     if not args.no_fp64:
         s64 = cw.Solver(m, cfg["order"], cfg["pde"], cw.FP64, stream=stream.cuda_stream)
-        s64.set_state(Q0)
-        s64.step(0.0)
-        s64.sync()
         k64 = max(3, min(args.steps, 20))
-        barrier()
-        e0.record(stream)
-        for _ in range(k64):
-            s64.step(0.0)
-        e1.record(stream)
-        barrier()
-        ms64 = e0.elapsed_time(e1)
-        out["fp64"] = {"value": ws * N * k64 / (ms64 / 1e3), "unit": "cell-updates/s", "steps": k64,
-                       "ms_per_step": ms64 / k64}
-        s64.close()
+        ms64, kern64_ms, _ = time_solver(s64, stream, barrier, Q0, k64, warm=1)
+        alg64 = algorithmic(cfg["dim"], cfg["order"], cfg["pde"], fp32=False)
+        kern64, dom64 = kernel_rooflines(kern64_ms, {"rec": N, "flux": s64.nf, "update": N}, alg64, pk, False)
+        ms64 = max_over_ranks(ms64)
+        out["fp64"] = {"value": ws * N / (ms64 / 1e3), "unit": "cell-updates/s", "steps": k64,
+                       "ms_per_step": ms64, "kernels": kern64,
+                       "roofline": roofline_line(kern64, dom64, pk, False, None)}
+        solvers["fp64"] = s64
     # end to end through the C ABI with pinned host buffers
     if not args.no_e2e:
         nv = s.nv
@@ -611,20 +757,10 @@ def run_ours(args):
                       "d2h_bytes_per_step": N * nv * 8, "steps": ke,
                       "path": "cweno_set_state(pinned host) + ader_cweno_step + cweno_get_state(pinned host)"}
     # accuracy of the FP32-mixed mode against the FP64 mode, and conservation
-    if not args.no_accuracy:
-        import numpy as np
-        qa, qb, dtf = accuracy_run(cw, m, cfg, Q0)
-        Xv = mesh.cell_vertices()
-        vol = np.abs(np.linalg.det(Xv[:, 1:] - Xv[:, :1])) / math.factorial(mesh.dim)
-        l1 = (vol @ np.abs(qa - qb)) / np.maximum(vol @ np.abs(qb), 1e-300)
-        linf = np.abs(qa - qb).max(axis=0) / np.maximum(np.abs(qb).max(axis=0), 1e-300)
-        tot0 = vol @ Q0
-        scale = np.maximum(np.maximum(np.abs(tot0), vol @ np.abs(Q0)), vol @ np.abs(qa))
-        scale = np.maximum(scale, 1e-6 * scale.max())
-        drift = np.abs(vol @ qa - tot0) / scale
-        out["accuracy"] = {"reference": "FP64 mode (parity-tested against the FP64 oracle)", "steps": 10,
-                           "dt": dtf, "L1_rel": [float(x) for x in l1], "Linf_rel": [float(x) for x in linf],
-                           "conservation_drift_rel": [float(x) for x in drift]}
+    if not args.no_accuracy and "fp64" in solvers:
+        out["accuracy"] = accuracy_pair(solvers, mesh, Q0)
+    for sv in solvers.values():
+        sv.close()
     if rank == 0 and not args.no_serve:
         out["serving"] = serving_run(cw, args.serve_requests)
     if not args.no_other:
@@ -632,15 +768,14 @@ def run_ours(args):
         for other in ("densitywave3d_p2", "orszagtang2d_p3", "explosion2d_p4"):
             if other == name:
                 continue
-            out["other_workloads"][other] = workload_rate(cw, other, stream, barrier, steps=10)
-        # the other face fluxes on the bench workload (FP32-mixed)
+            out["other_workloads"][other] = workload_rate(cw, other, stream, barrier, pk, steps=10)
+        # the other face fluxes on the bench workload
         out["flux_variants"] = {}
         for key, fl in (("osher", cw.FLUX_OSHER), ("rusanov_quadrature_free", cw.FLUX_RUSANOV_QF)):
             if fl == cw.FLUX_OSHER and cfg["pde"] != 0:
                 continue
-            r = workload_rate(cw, name, stream, barrier, steps=20, flux=fl, inputs=(mesh, Q0),
-                              precisions=((cw.FP32_MIXED, "fp32_mixed", 20),))
-            out["flux_variants"][key] = r["fp32_mixed"]
+            out["flux_variants"][key] = workload_rate(cw, name, stream, barrier, pk, steps=20, flux=fl,
+                                                      inputs=(mesh, Q0))
         # moving mesh (direct ALE), rank 0's GPU
         out["ale_explosion2d_p3"] = ale_rate(cw, stream, barrier)
         if rank == 0 and not args.no_cpu_baseline:

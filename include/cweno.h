@@ -238,6 +238,16 @@ void* cweno_stream(cweno_solver* s);
 int cweno_profile_enable(cweno_solver* s, int on);
 int cweno_profile_read(cweno_solver* s, double* ms, int64_t* launches);
 
+/* Measured FMA rate of the current device (the paper has no counterpart: it
+ * is the denominator of the FP32 / FP64 pipe fractions a benchmark reports).
+ * fp64 = 0 measures FP32 fused multiply-adds, otherwise FP64.  Every thread
+ * runs 16 independent FMA chains, in enough blocks to fill every SM; one
+ * untimed launch, then one launch timed with CUDA events on a private
+ * stream (about 10 ms).  Synchronous.  *tflops receives 2 flops per FMA per
+ * second / 1e12, *ms (nullable) the timed launch's milliseconds.  Allocates
+ * no device memory. */
+int cweno_measure_fma_peak(int fp64, double* tflops, double* ms);
+
 /* CFL time-step bound without any allocation.  The paper has no counterpart:
  * this is for callers that cannot call cudaMalloc (work inside a captured
  * CUDA graph, inside another framework's memory pool, or in a process whose

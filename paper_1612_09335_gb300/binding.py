@@ -75,6 +75,7 @@ SIGNATURES = [
     ("cweno_stream", _P, [_P]),
     ("cweno_profile_enable", _I, [_P, _I]),
     ("cweno_profile_read", _I, [_P, _DP, _I64P]),
+    ("cweno_measure_fma_peak", _I, [_I, _DP, _DP]),
     ("cweno_stable_dt_noalloc", _I, [_I, _I, _I64, _P, _P, _D, _D, _D, _P, _P]),
     ("serve_create", _I, [_SZ, _I, _I, C.POINTER(_P)]),
     ("serve_submit", _I, [_P, C.POINTER(cweno_request), _U64P]),
@@ -144,6 +145,14 @@ def cweno_mesh_create(dim: int, xyz, cells, period=None):
                                    cells.ctypes.data_as(_I32P),
                                    per.ctypes.data_as(_DP) if per is not None else None, C.byref(h)))
     return h
+
+
+def cweno_measure_fma_peak(fp64: bool) -> tuple[float, float]:
+    """(TFLOP/s, ms) of the current device's FP32 (or FP64) FMA pipe, measured
+    by an FMA-chain kernel timed with CUDA events (synchronous)."""
+    t, ms = C.c_double(), C.c_double()
+    _check(lib().cweno_measure_fma_peak(int(bool(fp64)), C.byref(t), C.byref(ms)))
+    return t.value, ms.value
 
 
 NOALLOC_MAX_CELLS = 65536 * 256

@@ -14,6 +14,11 @@ def test_algorithmic_model_counts():
     b, f = a["rec"]
     assert b == 4 * 19 + 4 * 9 * 19 + 4 * 3 * 2 + 4 * 3 * 4 + 1 + 4 * 4 + 8 * 4 + 4 * 20 * 4
     assert f > 0 and a["flux"][0] > 0 and a["update"][0] > 0
+    # the matvec R dQ alone is 2 (Mc - 1)(n_e - 1) nu flops; the Picard loop
+    # counts 2 nu per nonzero of P_e (116 in the unknown-node columns at 2D P3)
+    assert f > 2 * 9 * 19 * 4 + 4 * 2 * 116 * 4
+    # recounted without the structural zeros of P_e: below the dense count
+    assert f < 2 * 9 * 19 * 4 + 4 * (2 * 10 * 20 * 4 * 2) + 20000
     # FP64 doubles the floating-point terms
     assert bench.algorithmic(2, 4, 0, fp32=False)["rec"][0] > b
 
@@ -31,3 +36,52 @@ def test_moving_mesh_oracle_baseline_line():
     r = bench.ale_oracle_rate(n=6, steps=1)
     assert r["kind"] == "oracle" and r["cores"] == 1 and r["unit"] == "cell-updates/s"
     assert r["value"] > 0 and math.isfinite(r["value"]) and "72 triangles" in r["sample"]
+
+
+@pytest.mark.parametrize("d,M", [(2, 2), (2, 3), (3, 2)])
+def test_predictor_nonzero_counts_match_exact_generator(d, M):
+    """The flop model counts only the nonzeros of P_e; its counts (parsed from
+    the generated header) equal a direct evaluation of the entries in exact
+    rational arithmetic."""
+    import importlib.util
+    import os
+    import bench
+    spec = importlib.util.spec_from_file_location(
+        "gen_pred_pattern", os.path.join(bench.ROOT, "paper_1612_09335_gb300", "csrc", "gen_pred_pattern.py"))
+    g = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(g)
+    nodes = g.st_nodes(d, M)
+    L0 = math.comb(M + d, d)
+    nz0 = nz1 = 0
+    for e in range(d):
+        for k in range(len(nodes) - L0):
+            for l in range(len(nodes)):
+                if g.entry(d, M, nodes[L0 + k], nodes[l], e) != 0:
+                    if l < L0:
+                        nz0 += 1
+                    else:
+                        nz1 += 1
+    assert bench.pred_nonzeros(d, M) == (nz0, nz1)
+
+
+def test_roofline_picks_the_binding_roof():
+    """A kernel whose intensity is below the ridge (peak flops / peak bytes)
+    is reported against HBM, above it against the ALU peak; fractions are
+    achieved / peak with achieved = algorithmic units / measured time."""
+    import bench
+    pk = {"hbm_gbs": 1000.0, "hbm_src": "t", "fp32_tflops": 10.0, "fp64_tflops": 1.0, "alu_src": "t"}
+    alg = {"rec": (100.0, 500.0), "flux": (100.0, 5000.0), "update": (100.0, 10.0)}
+    kern, dom = bench.kernel_rooflines({"k_rec_pred": 1.0, "k_flux": 2.0, "k_update": 0.5},
+                                       {"rec": 1e6, "flux": 1e6, "update": 1e6}, alg, pk, fp32=True)
+    assert dom == "k_flux"
+    assert kern["k_rec_pred"]["bound"] == "hbm"        # 5 flop/B < ridge 10
+    assert kern["k_flux"]["bound"] == "alu"            # 50 flop/B > 10
+    line = bench.roofline_line(kern, dom, pk, True, None)
+    assert line["bound"] == "alu" and line["unit"] == "TFLOP/s"
+    assert abs(line["achieved"] - 5000.0 * 1e6 / 2e-3 / 1e12) < 1e-9
+    assert abs(line["frac"] - line["achieved"] / 10.0) < 1e-12
+    rec = bench.roofline_line(kern, "k_rec_pred", pk, True, None)
+    assert rec["bound"] == "hbm" and abs(rec["achieved"] - 100.0 * 1e6 / 1e-3 / 1e9) < 1e-9
+    # FP64: the same intensities against the FP64 ridge (1 flop/B) are ALU-bound
+    k64, _ = bench.kernel_rooflines({"k_rec_pred": 1.0}, {"rec": 1e6}, alg, pk, fp32=False)
+    assert k64["k_rec_pred"]["bound"] == "alu" and "fp64_frac" in k64["k_rec_pred"]
