@@ -15,6 +15,7 @@
 #include "../../include/cweno.h"
 #include "ale.h"
 #include "api_internal.h"
+#include "layout.h"
 #include "host.h"
 #include "ops.h"
 #include "refelem.h"
@@ -66,8 +67,9 @@ size_t footprint_estimate(int d, int64_t nc, int64_t nf, int order, int pde, int
   const size_t es = precision == CWENO_FP32_MIXED ? 4 : 8;
   size_t b = 0;
   b += 8 * nc * nv * 2;                                     // Q, staging
-  if (precision == CWENO_FP32_MIXED) b += 8 * nc * nv;      // hi, lo
-  b += 4 * nc + 4 * nc * (ne - 1) + es * nc * (Mc - 1) * (ne - 1);
+  if (precision == CWENO_FP32_MIXED) b += 8 * nc * ((nv + 1) & ~1);  // hi, lo pairs
+  b += 4 * nc + 4 * nc * (ne - 1) + 16 * nc * ((ne + 2) / 4);        // ids, ids in vectors
+  b += 16 * nc * (((ne - 1) * (Mc - 1) * es + 15) / 16);             // R_i in vectors
   b += 4 * nc * nvx * d + es * nc * nvx * d * d + nc + es * nc * d * d;
   b += es * nc * nv * L;                                    // q_hat
   b += nf * (8 + 2 + es * d + 8 * d + 8 + 8 * nv);          // faces + G
@@ -319,17 +321,31 @@ int cweno_setup(const cweno_mesh* mesh, int order, int pde, int precision, const
   ds.Q = (double*)p;
   CK(cudaMemsetAsync(ds.Q, 0, sizeof(double) * N * nv, s->stream));
   if (precision == CWENO_FP32_MIXED) {
-    if ((rc = dev_alloc(s.get(), &p, sizeof(float) * N * nv))) return rc;
-    ds.Qhi = (float*)p;
-    if ((rc = dev_alloc(s.get(), &p, sizeof(float) * N * nv))) return rc;
-    ds.Qlo = (float*)p;
-    CK(cudaMemsetAsync(ds.Qhi, 0, sizeof(float) * N * nv, s->stream));
-    CK(cudaMemsetAsync(ds.Qlo, 0, sizeof(float) * N * nv, s->stream));
+    const size_t pb = sizeof(float) * 2 * N * cw::pair_vars(nv);
+    if ((rc = dev_alloc(s.get(), &p, pb))) return rc;
+    ds.Qp = (float*)p;
+    CK(cudaMemsetAsync(ds.Qp, 0, pb, s->stream));
   }
   if ((rc = upload(s.get(), m.perm, (const void**)&ds.perm))) return rc;
   if ((rc = upload(s.get(), m.iperm, (const void**)&ds.iperm))) return rc;
   if ((rc = upload(s.get(), soa_i(cs.sten, N, re.ne - 1), (const void**)&ds.sten))) return rc;
-  if ((rc = dev_alloc(s.get(), &p, es * N * (re.Mc - 1) * (re.ne - 1)))) return rc;
+  {
+    // central stencil ids four per vector, the spare slots of the last one
+    // holding the cell itself (layout.h)
+    const int ne1 = re.ne - 1, nsv = cw::sten_vectors(ne1);
+    std::vector<int32_t> s4((size_t)nsv * N * 4);
+    for (int64_t i = 0; i < N; ++i)
+      for (int r = 0; r < nsv * 4; ++r)
+        s4[((size_t)(r / 4) * N + i) * 4 + r % 4] = r < ne1 ? cs.sten[(size_t)i * ne1 + r] : (int32_t)i;
+    if ((rc = upload(s.get(), s4, (const void**)&ds.sten4))) return rc;
+  }
+  {
+    // R_i in 16-byte vectors (layout.h); the padding of the last vector is zero
+    const int vw = (int)(16 / es);
+    const size_t rb = es * (size_t)N * vw * cw::r_vectors(re.ne - 1, re.Mc - 1, vw);
+    if ((rc = dev_alloc(s.get(), &p, rb))) return rc;
+    CK(cudaMemsetAsync(p, 0, rb, s->stream));
+  }
   ds.R = p;
   if ((rc = lsq_setup_device(m, re, ds.sten, p, precision == CWENO_FP32_MIXED, s->stream, err)))
     return fail(rc, err);

@@ -27,6 +27,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "layout.h"
 #include "ops.h"
 #include "pred_pattern.h"
 
@@ -60,6 +61,10 @@ struct Cfg {
   static constexpr int NQS = D == 2 ? M + 1 : (M + 1) * (M + 1);
   static constexpr int NQT = M + 1;
   static constexpr int NCODE = D == 2 ? 6 : 24;
+  // FP32 pairs per cell (layout.h) and the 16-byte vectors of R_i
+  static constexpr int NVP = pair_vars(NV);
+  static constexpr int NE1 = NE - 1;
+  static constexpr int RV = r_vectors(NE1, MC - 1, 16 / (int)sizeof(T_));
   // face tables: each (code, time point, space point) row of L basis values
   // is padded to a multiple of one 16-byte vector
   static constexpr int VW = 16 / (int)sizeof(T_);
@@ -110,12 +115,11 @@ struct Cfg {
   // so that the node loops run rolled: a few kilobytes of code instead of a
   // fully unrolled body that misses the instruction cache
   static constexpr int PRED_SMEM_BYTES = 2 * L1 * NV * (int)sizeof(T_) * 128;
-  // stencil neighbours whose gathers are in flight together (measured: 8
-  // beats 4 by ~2 % in FP32 Euler, 2 and 1 are 7-30 % slower)
-#ifdef CW_GATHER_UNROLL
-  static constexpr int GATHER_UNROLL = CW_GATHER_UNROLL;
+  // chunks of four stencil neighbours unrolled together in the gather
+#ifdef CW_GATHER_CHUNKS
+  static constexpr int GATHER_CHUNKS = CW_GATHER_CHUNKS;
 #else
-  static constexpr int GATHER_UNROLL = (sizeof(T_) == 4 && NV <= 5) ? 8 : 4;
+  static constexpr int GATHER_CHUNKS = 2;
 #endif
   // Picard node loop unrolled with the compile-time zero pattern of P_e
   // where it has at most ten unknown nodes (measured: P2/P3 3-8 % faster;
@@ -141,11 +145,10 @@ struct KArgs {
   using T = typename C::T;
   int64_t N, F;
   double* Q;
-  float* Qhi;
-  float* Qlo;
+  float* Qp;  // FP32 pairs (hi, lo) per cell and variable, layout.h
   const int32_t* perm;
   const int32_t* iperm;
-  const int32_t* sten;
+  const int32_t* sten4;  // central stencil ids, four per vector, layout.h
   const T* R;
   const int32_t* sec;
   const T* Binv;
@@ -413,19 +416,62 @@ __device__ __forceinline__ void flux_normal(const T* q, const typename Phys<D, P
 }
 
 // --------------------------------------------------- state access helpers
+// FP32 pair (hi, lo) of an FP64 value q: hi is q truncated to 24 significant
+// bits, lo = q - hi (exact in FP64) rounded to FP32, so hi + lo equals q to
+// about 2^-47 relative.  Built from the bits of q with integer operations,
+// off the FP64 pipe (1/64 of the FP32 rate on this part; the conversions of
+// the plain form (float)q, (float)(q - (double)hi) ran on it).  Exponents
+// outside the range where hi and lo are normal FP32 numbers take that plain
+// form; zero (and FP64 subnormals) give (0, 0) with the sign of q.
+__device__ __forceinline__ void split_hilo(double q, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(q);
+  const unsigned hw = (unsigned)(b >> 32);
+  const int e = (int)((hw >> 20) & 0x7ffu);
+  const unsigned sign = hw & 0x80000000u;
+  if (e >= 950 && e <= 1150) {
+    // hi: sign, exponent rebased from 1023 to 127, top 23 mantissa bits
+    hi = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | (unsigned)((b >> 29) & 0x7fffffu));
+    // lo: the 29 dropped mantissa bits times 2^(e - 1075), rounded once
+    const unsigned rem = (unsigned)(b & 0x1fffffffu);
+    const float scale = __uint_as_float((unsigned)(e - 1075 + 127) << 23);
+    lo = __uint_as_float(__float_as_uint(__uint2float_rn(rem) * scale) | sign);
+  } else if (e == 0) {
+    hi = __uint_as_float(sign);
+    lo = hi;
+  } else {
+    hi = (float)q;
+    lo = (float)(q - (double)hi);
+  }
+}
+
+// The FP32 pairs (hi, lo) of cell j, NVP / 2 16-byte vectors (layout.h)
+template <class C>
+__device__ __forceinline__ void load_pairs(const float* __restrict__ Qp, int64_t j, float* hi, float* lo) {
+  const float4* p = reinterpret_cast<const float4*>(Qp) + j * (C::NVP / 2);
+#pragma unroll
+  for (int m = 0; m < C::NVP / 2; ++m) {
+    const float4 x = __ldg(p + m);
+    hi[2 * m] = x.x;
+    lo[2 * m] = x.y;
+    if (2 * m + 1 < C::NV) {
+      hi[2 * m + 1] = x.z;
+      lo[2 * m + 1] = x.w;
+    }
+  }
+}
+
 template <class C>
 __device__ __forceinline__ void load_state(const KArgs<C>& a, int64_t i, typename C::T* q,
                                            typename C::T* lo) {
   using T = typename C::T;
+  if constexpr (std::is_same<T, double>::value) {
 #pragma unroll
-  for (int v = 0; v < C::NV; ++v) {
-    if constexpr (std::is_same<T, double>::value) {
+    for (int v = 0; v < C::NV; ++v) {
       q[v] = a.Q[v * a.N + i];
       lo[v] = 0.0;
-    } else {
-      q[v] = a.Qhi[v * a.N + i];
-      lo[v] = a.Qlo[v * a.N + i];
     }
+  } else {
+    load_pairs<C>(a.Qp, i, q, lo);
   }
 }
 
@@ -435,13 +481,14 @@ template <class C>
 __device__ __forceinline__ void load_diff(const KArgs<C>& a, int64_t j, const typename C::T* qi,
                                           const typename C::T* qilo, typename C::T* dq) {
   using T = typename C::T;
+  if constexpr (std::is_same<T, double>::value) {
 #pragma unroll
-  for (int v = 0; v < C::NV; ++v) {
-    if constexpr (std::is_same<T, double>::value) {
-      dq[v] = a.Q[v * a.N + j] - qi[v];
-    } else {
-      dq[v] = (__ldg(a.Qhi + v * a.N + j) - qi[v]) + (__ldg(a.Qlo + v * a.N + j) - qilo[v]);
-    }
+    for (int v = 0; v < C::NV; ++v) dq[v] = a.Q[v * a.N + j] - qi[v];
+  } else {
+    float hj[C::NV], lj[C::NV];
+    load_pairs<C>(a.Qp, j, hj, lj);
+#pragma unroll
+    for (int v = 0; v < C::NV; ++v) dq[v] = (hj[v] - qi[v]) + (lj[v] - qilo[v]);
   }
 }
 
@@ -502,38 +549,56 @@ __device__ __forceinline__ void store_node(T* __restrict__ p, const T* in) {
 }
 
 // ---------------------------------------------------------- rec + predictor
-
-
+// One cell: reconstruction, then (unless REC_ONLY) the predictor.
 template <class C, bool REC_ONLY>
-__global__ void __launch_bounds__(128, C::REC_MINB) k_rec_pred(KArgs<C> a, const __grid_constant__ CellTab<C> tb) {
+__device__ __forceinline__ void rec_pred_cell(const KArgs<C>& a, const CellTab<C>& tb, int64_t i) {
   using T = typename C::T;
   constexpr int D = C::D, NV = C::NV, MC1 = C::MC1, NE1 = C::NE - 1, NS = C::NS;
   using PH = Phys<D, C::PDE, T>;
   const int64_t N = a.N;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (!REC_ONLY && a.reset_next && blockIdx.x == 0 && threadIdx.x == 0) a.dtmin[1 - a.cur] = 0x7ff0000000000000ull;
   if (i >= N) return;
 
   T qi[NV], qlo[NV];
   load_state<C>(a, i, qi, qlo);
 
-  // ---- P_opt: c = R dQ over the central stencil (constant part is Q_i)
+  // ---- P_opt: c = R dQ over the central stencil (constant part is Q_i).
+  // Neighbours in chunks of four: one 16-byte vector of ids, whole 16-byte
+  // vectors of R (layout.h), four neighbours' differences, then the FMAs.
   T c[MC1][NV];
 #pragma unroll
   for (int l = 0; l < MC1; ++l)
 #pragma unroll
     for (int v = 0; v < NV; ++v) c[l][v] = T(0);
-#pragma unroll(C::GATHER_UNROLL)
-  for (int k = 0; k < NE1; ++k) {
-    const int64_t j = __ldg(a.sten + k * N + i);
-    T dq[NV];
-    load_diff<C>(a, j, qi, qlo, dq);
+  {
+    using V = typename Vec16<T>::V;
+    constexpr int VW = C::VW, NFULL = NE1 / 4, TAIL = NE1 % 4, GPC = 4 * MC1 / VW;
+    const V* Rv = reinterpret_cast<const V*>(a.R);
+    const int4* S4 = reinterpret_cast<const int4*>(a.sten4);
+    auto chunk = [&](int ch, auto nn) {
+      constexpr int NN = decltype(nn)::value;
+      constexpr int NG = (NN * MC1 + VW - 1) / VW;
+      const int4 id = __ldg(S4 + (int64_t)ch * N + i);
+      const int ids[4] = {id.x, id.y, id.z, id.w};
+      T dq[NN][NV];
 #pragma unroll
-    for (int l = 0; l < MC1; ++l) {
-      const T r = __ldg(a.R + (int64_t)(l * NE1 + k) * N + i);
+      for (int rr = 0; rr < NN; ++rr) load_diff<C>(a, ids[rr], qi, qlo, dq[rr]);
+      T r[NG * VW];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) c[l][v] += r * dq[v];
-    }
+      for (int g = 0; g < NG; ++g) {
+        const V x = __ldg(Rv + (int64_t)(ch * GPC + g) * N + i);
+#pragma unroll
+        for (int j = 0; j < VW; ++j) r[g * VW + j] = Vec16<T>::get(x, j);
+      }
+#pragma unroll
+      for (int rr = 0; rr < NN; ++rr)
+#pragma unroll
+        for (int l = 0; l < MC1; ++l)
+#pragma unroll
+          for (int v = 0; v < NV; ++v) c[l][v] += r[rr * MC1 + l] * dq[rr][v];
+    };
+#pragma unroll(C::GATHER_CHUNKS)
+    for (int ch = 0; ch < NFULL; ++ch) chunk(ch, std::integral_constant<int, 4>());
+    if constexpr (TAIL > 0) chunk(NFULL, std::integral_constant<int, TAIL>());
   }
 
   // ---- sectorial polynomials: g_s = B_s^{-1} dQ_sector
@@ -849,6 +914,13 @@ __global__ void __launch_bounds__(128, C::REC_MINB) k_rec_pred(KArgs<C> a, const
   }
 }
 
+// One thread per cell, one block per tile of 128 consecutive cells.
+template <class C, bool REC_ONLY>
+__global__ void __launch_bounds__(128, C::REC_MINB) k_rec_pred(KArgs<C> a, const __grid_constant__ CellTab<C> tb) {
+  if (!REC_ONLY && a.reset_next && blockIdx.x == 0 && threadIdx.x == 0) a.dtmin[1 - a.cur] = 0x7ff0000000000000ull;
+  rec_pred_cell<C, REC_ONLY>(a, tb, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 // ----------------------------------------------------------------- fluxes
 template <class C>
 __device__ __forceinline__ void load_chunk(const typename C::T* __restrict__ qhat, int64_t c, int64_t N, int l4,
@@ -993,13 +1065,14 @@ __device__ __forceinline__ const typename C::T* face_tables(const KArgs<C>& a, i
 
 template <class C>
 __device__ __forceinline__ void cell_average(const KArgs<C>& a, int64_t c, typename C::T* qb) {
+  if constexpr (std::is_same<typename C::T, double>::value) {
 #pragma unroll
-  for (int v = 0; v < C::NV; ++v) {
-    if constexpr (std::is_same<typename C::T, double>::value) {
-      qb[v] = a.Q[v * a.N + c];
-    } else {
-      qb[v] = __ldg(a.Qhi + v * a.N + c) + __ldg(a.Qlo + v * a.N + c);
-    }
+    for (int v = 0; v < C::NV; ++v) qb[v] = a.Q[v * a.N + c];
+  } else {
+    float hi[C::NV], lo[C::NV];
+    load_pairs<C>(a.Qp, c, hi, lo);
+#pragma unroll
+    for (int v = 0; v < C::NV; ++v) qb[v] = hi[v] + lo[v];
   }
 }
 
@@ -1367,35 +1440,41 @@ __global__ void __launch_bounds__(256) k_update(KArgs<C> a) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   T ratio = T(INFINITY);
   if (i < N) {
+    // sum_f +-G_f: the sign of a face's integral is flipped on the bits (no
+    // FP64 instruction), the first face starts the sum
     double acc[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) acc[v] = 0.0;
 #pragma unroll
     for (int k = 0; k <= D; ++k) {
       const int cf = a.cellface[k * N + i];
       const int64_t f = cf >> 1;
+      const long long flip = (long long)(cf & 1) << 63;
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        const double g = a.G[v * F + f];
-        acc[v] += (cf & 1) ? -g : g;
+        const double g = __longlong_as_double(__double_as_longlong(a.G[v * F + f]) ^ flip);
+        acc[v] = k == 0 ? g : acc[v] + g;
       }
     }
     const double iv = a.invvol[i];
     double q[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      q[v] = a.Q[v * N + i] - iv * acc[v];
+      q[v] = fma(-iv, acc[v], a.Q[v * N + i]);
       a.Q[v * N + i] = q[v];
     }
     T qt[NV];
     if constexpr (std::is_same<T, float>::value) {
+      float pr[2 * C::NVP];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        const float hi = (float)q[v];
-        a.Qhi[v * N + i] = hi;
-        a.Qlo[v * N + i] = (float)(q[v] - (double)hi);
-        qt[v] = hi;
+      for (int v = 0; v < C::NVP; ++v) {
+        float hi = 0.f, lo = 0.f;
+        if (v < NV) split_hilo(q[v], hi, lo);
+        pr[2 * v] = hi;
+        pr[2 * v + 1] = lo;
+        if (v < NV) qt[v] = hi;
       }
+      float4* dst = reinterpret_cast<float4*>(a.Qp) + i * (C::NVP / 2);
+#pragma unroll
+      for (int m = 0; m < C::NVP / 2; ++m) dst[m] = make_float4(pr[4 * m], pr[4 * m + 1], pr[4 * m + 2], pr[4 * m + 3]);
     } else {
 #pragma unroll
       for (int v = 0; v < NV; ++v) qt[v] = q[v];
@@ -1420,10 +1499,12 @@ __global__ void __launch_bounds__(256) k_stable_dt(KArgs<C> a, int slot) {
   T ratio = T(INFINITY);
   if (i < N) {
     T q[C::NV];
+    if constexpr (std::is_same<T, float>::value) {
+      float lo[C::NV];
+      load_pairs<C>(a.Qp, i, q, lo);
+    } else {
 #pragma unroll
-    for (int v = 0; v < C::NV; ++v) {
-      if constexpr (std::is_same<T, float>::value) q[v] = a.Qhi[v * N + i];
-      else q[v] = a.Q[v * N + i];
+      for (int v = 0; v < C::NV; ++v) q[v] = a.Q[v * N + i];
     }
     ratio = (T)a.hsize[i] / PH::speed(q, a.gamma, a.ch);
   }
@@ -1448,13 +1529,13 @@ __global__ void k_set_state(KArgs<C> a, const double* user) {
   if (e >= a.N * C::NV) return;
   const int64_t u = e / C::NV;
   const int v = (int)(e - u * C::NV);
-  const int64_t j = v * a.N + a.iperm[u];
+  const int64_t c = a.iperm[u];
   const double q = user[e];
-  a.Q[j] = q;
+  a.Q[v * a.N + c] = q;
   if constexpr (std::is_same<typename C::T, float>::value) {
-    const float hi = (float)q;
-    a.Qhi[j] = hi;
-    a.Qlo[j] = (float)(q - (double)hi);
+    float hi, lo;
+    split_hilo(q, hi, lo);
+    reinterpret_cast<float2*>(a.Qp)[c * C::NVP + v] = make_float2(hi, lo);
   }
 }
 
@@ -1477,7 +1558,7 @@ __global__ void k_qhat_out(KArgs<C> a, double* user) {
     for (int v = 0; v < C::NV; ++v) {
       double qbar;
       if constexpr (std::is_same<typename C::T, float>::value)
-        qbar = (double)a.Qhi[v * a.N + i] + (double)a.Qlo[v * a.N + i];
+        qbar = (double)a.Qp[(i * C::NVP + v) * 2] + (double)a.Qp[(i * C::NVP + v) * 2 + 1];
       else
         qbar = a.Q[v * a.N + i];
       user[(u * C::L + l) * C::NV + v] = qbar + (double)a.qhat[((int64_t)l * a.N + i) * C::NV + v];
@@ -1527,11 +1608,10 @@ class OpsImpl final : public Ops {
     a.N = s.N;
     a.F = s.F;
     a.Q = s.Q;
-    a.Qhi = s.Qhi;
-    a.Qlo = s.Qlo;
+    a.Qp = s.Qp;
     a.perm = s.perm;
     a.iperm = s.iperm;
-    a.sten = s.sten;
+    a.sten4 = s.sten4;
     a.R = (const T*)s.R;
     a.sec = s.sec;
     a.Binv = (const T*)s.Binv;

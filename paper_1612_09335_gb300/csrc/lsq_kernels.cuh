@@ -5,8 +5,8 @@
 // functions psi_1..psi_{Mc-1} of its reference frame over the cells of its
 // central stencil (the constrained problem with the constant part removed),
 // the pseudo-inverse R_i of that (n_e - 1) x (Mc - 1) matrix by modified
-// Gram-Schmidt with one reorthogonalisation pass, written in the SoA layout
-// the reconstruction kernel reads; and the sector inverses of Eq. (CWENO:Ps).
+// Gram-Schmidt with one reorthogonalisation pass, written in the vector layout
+// the reconstruction kernel reads (layout.h); and the sector inverses of Eq. (CWENO:Ps).
 // FP64 throughout, one thread per cell.  Each including translation unit gets
 // its own copy (unnamed namespace).
 #pragma once
@@ -19,6 +19,7 @@
 
 #include "../../include/cweno.h"
 #include "host.h"
+#include "layout.h"
 
 namespace cw {
 
@@ -181,7 +182,8 @@ __global__ void __launch_bounds__(128) k_lsq(const double* __restrict__ X, const
     atomicMin(bad, (int)i);
     return;
   }
-  // pinv = Rm^{-1} Q^T, column by column of Q^T, written as R[(l NE1 + r) N + i]
+  // pinv = Rm^{-1} Q^T, column by column of Q^T, in the vector layout of
+  // layout.h (r_index)
   for (int r = 0; r < NE1; ++r) {
     double col[MC1];
     for (int k = MC1 - 1; k >= 0; --k) {
@@ -189,7 +191,7 @@ __global__ void __launch_bounds__(128) k_lsq(const double* __restrict__ X, const
       for (int j = k + 1; j < MC1; ++j) sv -= Rm[k][j] * col[j];
       col[k] = sv / Rm[k][k];
     }
-    for (int k = 0; k < MC1; ++k) R[((int64_t)k * NE1 + r) * N + i] = (T)col[k];
+    for (int k = 0; k < MC1; ++k) R[r_index<T>(r, k, MC1, i, N)] = (T)col[k];
   }
 }
 

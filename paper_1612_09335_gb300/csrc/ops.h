@@ -15,12 +15,12 @@ struct DevState {
   int64_t N = 0, F = 0;
   int nv = 0;
   double* Q = nullptr;          // nv x N (FP64 always)
-  float* Qhi = nullptr;         // nv x N (FP32 mode)
-  float* Qlo = nullptr;         // nv x N (FP32 mode)
+  float* Qp = nullptr;          // N x NVP x 2 FP32 pairs (FP32 mode), layout.h
   const int32_t* perm = nullptr;  // internal -> user
   const int32_t* iperm = nullptr; // user -> internal
   const int32_t* sten = nullptr;  // (ne-1) x N
-  const void* R = nullptr;        // (Mc-1)(ne-1) x N
+  const int32_t* sten4 = nullptr; // (ne-1)/4 rounded up x N x 4, layout.h
+  const void* R = nullptr;        // vectors of R_i, layout.h
   const int32_t* sec = nullptr;   // (d+1) d x N
   const void* Binv = nullptr;     // (d+1) d d x N
   const uint8_t* nsec = nullptr;  // N

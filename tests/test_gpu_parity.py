@@ -415,3 +415,31 @@ def test_tiny_mesh_zero_steps_and_one_block(cw, orc, wl):
         s.run(0)
         s.sync()
         assert np.array_equal(s.get_state(), Q)
+
+
+def test_fp32_pair_split_of_the_state(cw, wl):
+    """FP32-mixed mode keeps each FP64 cell average as an FP32 pair (hi, lo).
+    For a constant state the predictor is exactly the cell average at every
+    node, returned as (double)hi + (double)lo, which must equal the FP64 value
+    to 2^-46 relative (hi: 24 leading bits, lo: the rest rounded to FP32);
+    exponents outside the integer-built range take the plain conversion."""
+    mesh = wl.tri_mesh(8, jitter=0.2, seed=3)
+    states = [
+        [1.0, 0.0, -0.0, 2.5],
+        [0.7, 1e-30, -2.5e-20, 3.3e15],
+        [1.3, 1e-45, -7.77e30, 1e36],
+        [2.0, 123456.789012345, -9.87654321e-7, 1.0 / 3.0],
+        [1e-3, 1e-300, 5e-310, 2.0 ** -126],
+    ]
+    for q in states:
+        q = np.array(q)
+        Q = np.tile(q, (mesh.nc, 1))
+        s = make(cw, mesh, 3, EULER, cw.FP32_MIXED)
+        s.set_state(Q)
+        out = s.predictor(1e-4)
+        for v in range(4):
+            got = out[..., v]
+            assert np.all(got == got.flat[0]), (q[v], np.unique(got))
+            g = float(got.flat[0])
+            assert abs(g - q[v]) <= 2.0 ** -46 * abs(q[v]) + 1e-44, (q[v], g)
+        s.close()
