@@ -20,6 +20,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 #include <algorithm>
 #include <cstring>
@@ -89,7 +90,11 @@ struct Cfg {
   // passes of the pair kernel over the time points: one pass holds all
   // NQT NQS traces where they fit (2D Euler), otherwise one time point per
   // pass (q_hat re-read per time point, as in the one-thread kernel)
+#ifdef CW_PAIR_PASSES
+  static constexpr int PAIR_PASSES = CW_PAIR_PASSES;
+#else
   static constexpr int PAIR_PASSES = NQT * NQS * NV <= 64 ? 1 : NQT;
+#endif
   // prefetch of the next q_hat chunk in the trace loop where the extra
   // registers are few (measured: faster in 2D Euler, slower for NV >= 5)
   static constexpr bool TR_PREFETCH = VW * NV <= 16;
@@ -115,11 +120,22 @@ struct Cfg {
   // so that the node loops run rolled: a few kilobytes of code instead of a
   // fully unrolled body that misses the instruction cache
   static constexpr int PRED_SMEM_BYTES = 2 * L1 * NV * (int)sizeof(T_) * 128;
+  // reconstruction at the lattice nodes kept in the predictor's working set
+  // (where it fits: L0 NV <= 2 L1 NV)
+  static constexpr bool STASH = L0 <= 2 * L1;
+  // tau = 0 node loop of the predictor unrolled with the zero pattern of P_e
+  // (measured: 4 % slower at 2D P3 FP32, the unrolled body costs more in
+  // instruction fetch than the skipped FMAs save)
+#ifdef CW_TAU0_SPARSE
+  static constexpr bool TAU0_SPARSE = CW_TAU0_SPARSE;
+#else
+  static constexpr bool TAU0_SPARSE = false;
+#endif
   // chunks of four stencil neighbours unrolled together in the gather
 #ifdef CW_GATHER_CHUNKS
   static constexpr int GATHER_CHUNKS = CW_GATHER_CHUNKS;
 #else
-  static constexpr int GATHER_CHUNKS = 2;
+  static constexpr int GATHER_CHUNKS = 1;
 #endif
   // Picard node loop unrolled with the compile-time zero pattern of P_e
   // where it has at most ten unknown nodes (measured: P2/P3 3-8 % faster;
@@ -137,6 +153,7 @@ struct CellTab {
   T E[C::L0][C::MC1];
   T Sig[C::MC1][C::MC1];
   T CE[C::L1][C::MC1];  // C0 E: known part of the unknown nodes, from w directly
+  int sel[C::L1];       // tau = 0 lattice node below each unknown node
   T P[C::D][C::L1][C::L];
 };
 
@@ -549,6 +566,53 @@ __device__ __forceinline__ void store_node(T* __restrict__ p, const T* in) {
 }
 
 // ---------------------------------------------------------- rec + predictor
+// Positivity scaling toward the cell average (switchable; an addition to the
+// paper, the Zhang-Shu scaling limiter): density first, then the pressure,
+// both kept above 1e-3 of their cell-average values at every lattice node
+// (well above FP32 rounding of Qbar + theta (w - Qbar), and high enough that
+// a scaled node cannot reach near-vacuum with a finite momentum, whose
+// velocity the cell-average time step would not see); density and pressure
+// are concave in the conserved state.  dev(n, v) is the reconstruction's
+// deviation from the cell average qb at lattice node n; returns the factor
+// theta in (0, 1] that scales it.
+template <class C, class Dev>
+__device__ __forceinline__ typename C::T positivity_theta(const KArgs<C>& a, const typename C::T* qb, Dev dev) {
+  using T = typename C::T;
+  constexpr int NV = C::NV;
+  using PH = Phys<C::D, C::PDE, T>;
+  const T fl = T(1e-3);
+  const T rb = qb[0];
+  T th = T(1);
+#pragma unroll 1
+  for (int n = 0; n < C::L0; ++n) {
+    const T r = qb[0] + dev(n, 0);
+    if (r < fl * rb) {
+      const T t = (rb - fl * rb) / (rb - r);
+      th = t < th ? t : th;
+    }
+  }
+  const T pb = PH::pressure(qb, a.gamma);
+  T thp = T(1);
+  if (pb > T(0)) {
+#pragma unroll 1
+    for (int n = 0; n < C::L0; ++n) {
+      T q[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) q[v] = qb[v] + th * dev(n, v);
+      if (!(q[0] > T(0))) {
+        thp = T(0);
+        continue;
+      }
+      const T pk = PH::pressure(q, a.gamma);
+      if (pk < fl * pb) {
+        const T t = (pb - fl * pb) / (pb - pk);
+        thp = t < thp ? t : thp;
+      }
+    }
+  }
+  return th * thp;
+}
+
 // One cell: reconstruction, then (unless REC_ONLY) the predictor.
 template <class C, bool REC_ONLY>
 __device__ __forceinline__ void rec_pred_cell(const KArgs<C>& a, const CellTab<C>& tb, int64_t i) {
@@ -695,71 +759,31 @@ __device__ __forceinline__ void rec_pred_cell(const KArgs<C>& a, const CellTab<C
     }
   }
 
-  // ---- positivity scaling toward the cell average (switchable; an addition
-  // to the paper, the Zhang-Shu scaling limiter): density first, then the
-  // pressure, both kept above 1e-3 of their cell-average values at every
-  // lattice node (well above FP32 rounding of Qbar + theta (w - Qbar), and
-  // high enough that a scaled node cannot reach near-vacuum with a finite
-  // momentum, whose velocity the cell-average time step would not see);
-  // density and pressure are concave in the conserved state
-  if (a.pos) {
-    const T fl = T(1e-3);
-    T qb[NV];
+  T qbar[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) qb[v] = qi[v] + qlo[v];
-    const T rb = qb[0];
-    T th = T(1);
-#pragma unroll 1
-    for (int n = 0; n < C::L0; ++n) {
-      T r = qb[0];
-#pragma unroll
-      for (int l = 0; l < MC1; ++l) r += tb.E[n][l] * w[l][0];
-      if (r < fl * rb) {
-        const T t = (rb - fl * rb) / (rb - r);
-        th = t < th ? t : th;
-      }
-    }
-    const T pb = PH::pressure(qb, a.gamma);
-    T thp = T(1);
-    if (pb > T(0)) {
-#pragma unroll 1
-      for (int n = 0; n < C::L0; ++n) {
-        T q[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          T s = T(0);
-#pragma unroll
-          for (int l = 0; l < MC1; ++l) s += tb.E[n][l] * w[l][v];
-          q[v] = qb[v] + th * s;
-        }
-        if (!(q[0] > T(0))) {
-          thp = T(0);
-          continue;
-        }
-        const T pk = PH::pressure(q, a.gamma);
-        if (pk < fl * pb) {
-          const T t = (pb - fl * pb) / (pb - pk);
-          thp = t < thp ? t : thp;
-        }
-      }
-    }
-    const T theta = th * thp;
-    if (theta < T(1)) {
-#pragma unroll
-      for (int l = 0; l < MC1; ++l)
-#pragma unroll
-        for (int v = 0; v < NV; ++v) w[l][v] *= theta;
-    }
-  }
-
+  for (int v = 0; v < NV; ++v) qbar[v] = qi[v] + qlo[v];
   if constexpr (REC_ONLY) {
+    if (a.pos) {
+      const T theta = positivity_theta<C>(a, qbar, [&](int n, int v) {
+        T s = T(0);
+#pragma unroll
+        for (int l = 0; l < MC1; ++l) s += tb.E[n][l] * w[l][v];
+        return s;
+      });
+      if (theta < T(1)) {
+#pragma unroll
+        for (int l = 0; l < MC1; ++l)
+#pragma unroll
+          for (int v = 0; v < NV; ++v) w[l][v] *= theta;
+      }
+    }
     // reconstruction values at the lattice nodes, caller's cell order
     const int64_t u = a.perm[i];
 #pragma unroll
     for (int n = 0; n < C::L0; ++n)
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        T s = qi[v] + qlo[v];
+        T s = qbar[v];
 #pragma unroll
         for (int l = 0; l < MC1; ++l) s += tb.E[n][l] * w[l][v];
         a.out[(u * C::MC + n) * NV + v] = (double)s;
@@ -770,6 +794,40 @@ __device__ __forceinline__ void rec_pred_cell(const KArgs<C>& a, const CellTab<C
     extern __shared__ __align__(16) unsigned char rp_smem[];
     T* sb = reinterpret_cast<T*>(rp_smem) + threadIdx.x;  // fixed part, [(k NV + v) B]
     T* sq = sb + L1 * NV * B;                              // current iterate
+    // With STASH, the reconstruction at the L0 lattice nodes (E w, deviation
+    // from the cell average) is formed once into the working set: the
+    // positivity scaling, the tau = 0 nodes of the predictor and its known
+    // part read it.  The known part C0 q0 needs no arithmetic: on the
+    // principal lattice every unknown node lies above a tau = 0 node
+    // (tb.sel), where C0 = theta_n(xi_k, 0) is 1, and 0 elsewhere.
+    constexpr bool STASH = C::STASH;
+    T* sw = sb;  // [(n NV + v) B], n < L0
+    T theta = T(1);
+    if constexpr (STASH) {
+#pragma unroll 1
+      for (int n = 0; n < L0; ++n)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          T s = T(0);
+#pragma unroll
+          for (int l = 0; l < MC1; ++l) s += tb.E[n][l] * w[l][v];
+          sw[(n * NV + v) * B] = s;
+        }
+      if (a.pos) theta = positivity_theta<C>(a, qbar, [&](int n, int v) { return sw[(n * NV + v) * B]; });
+    } else if (a.pos) {
+      theta = positivity_theta<C>(a, qbar, [&](int n, int v) {
+        T s = T(0);
+#pragma unroll
+        for (int l = 0; l < MC1; ++l) s += tb.E[n][l] * w[l][v];
+        return s;
+      });
+      if (theta < T(1)) {
+#pragma unroll
+        for (int l = 0; l < MC1; ++l)
+#pragma unroll
+          for (int v = 0; v < NV; ++v) w[l][v] *= theta;
+      }
+    }
     // dt is folded into the inverse Jacobian: G_e = F . (dt d xi_e / d x) is
     // linear in the direction, so the scaled directions give dt G_e directly
     const T dt = (T)dt_of(a.dt_fixed, a.cfl, a.dtmin, a.cur);
@@ -783,29 +841,34 @@ __device__ __forceinline__ void rec_pred_cell(const KArgs<C>& a, const CellTab<C
     // (it differentiates constants to zero); q_hat is stored as q - Qbar.  The
     // arithmetic is identical in exact arithmetic, and constant states stay
     // exactly constant in FP32.
-    T qb[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) qb[v] = qi[v] + qlo[v];
+    const T* qb = qbar;
     T Gref[D][NV];
     {
       typename PH::Prim pr = PH::prim(qb, a.gamma);
 #pragma unroll
       for (int e = 0; e < D; ++e) flux_normal<D, C::PDE, T>(qb, pr, J[e], Gref[e], a.ch);
     }
-    // flux part of the fixed term, -sum_e P_e[:, tau=0 nodes] dt (G_e(q0) - G_e(Qbar))
+    // flux part of the fixed term, -sum_e P_e[:, tau=0 nodes] dt (G_e(q0) - G_e(Qbar));
+    // with TAU0_SPARSE the node loop is unrolled and the exact zeros of P_e
+    // in the tau = 0 columns are skipped at compile time
     T S[L1][NV];
 #pragma unroll
     for (int k = 0; k < L1; ++k)
 #pragma unroll
       for (int v = 0; v < NV; ++v) S[k][v] = T(0);
-#pragma unroll 1
+#pragma unroll(C::TAU0_SPARSE ? C::L0 : 1)
     for (int n = 0; n < L0; ++n) {
       T dq0[NV], q0[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        T s = T(0);
+        T s;
+        if constexpr (STASH) {
+          s = theta * sw[(n * NV + v) * B];
+        } else {
+          s = T(0);
 #pragma unroll
-        for (int l = 0; l < MC1; ++l) s += tb.E[n][l] * w[l][v];
+          for (int l = 0; l < MC1; ++l) s += tb.E[n][l] * w[l][v];
+        }
         dq0[v] = s;
         q0[v] = qb[v] + s;
       }
@@ -824,22 +887,39 @@ __device__ __forceinline__ void rec_pred_cell(const KArgs<C>& a, const CellTab<C
         for (int v = 0; v < NV; ++v) {
           T b = S[k][v];
 #pragma unroll
-          for (int e = 0; e < D; ++e) b -= tb.P[e][k][n] * Ge[e][v];
+          for (int e = 0; e < D; ++e)
+            if (!C::TAU0_SPARSE || PredPattern<D, C::M>::nz(e, k, n)) b -= tb.P[e][k][n] * Ge[e][v];
           S[k][v] = b;
         }
     }
-    // known part C0 dq0 = (C0 E) w; it is also the initial guess (deviation
-    // of the unknown nodes from Qbar)
+    // known part C0 q0, also the initial guess (deviation of the unknown
+    // nodes from Qbar); with STASH read from the stash into registers before
+    // the working set is overwritten
+    if constexpr (STASH) {
+      T c0[L1][NV];
 #pragma unroll
-    for (int k = 0; k < L1; ++k)
+      for (int k = 0; k < L1; ++k)
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        T c0 = T(0);
+        for (int v = 0; v < NV; ++v) c0[k][v] = theta * sw[(tb.sel[k] * NV + v) * B];
 #pragma unroll
-        for (int l = 0; l < MC1; ++l) c0 += tb.CE[k][l] * w[l][v];
-        sq[(k * NV + v) * B] = c0;
-        sb[(k * NV + v) * B] = c0 + S[k][v];
-      }
+      for (int k = 0; k < L1; ++k)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          sq[(k * NV + v) * B] = c0[k][v];
+          sb[(k * NV + v) * B] = c0[k][v] + S[k][v];
+        }
+    } else {
+#pragma unroll
+      for (int k = 0; k < L1; ++k)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          T c0 = T(0);
+#pragma unroll
+          for (int l = 0; l < MC1; ++l) c0 += tb.CE[k][l] * w[l][v];
+          sq[(k * NV + v) * B] = c0;
+          sb[(k * NV + v) * B] = c0 + S[k][v];
+        }
+    }
     // Picard iterations of Eq. (CGfinal), on deviations
     for (int it = 0; it < a.niter; ++it) {
       T nq[L1][NV];
@@ -1585,6 +1665,23 @@ class OpsImpl final : public Ops {
     for (int e = 0; e < C::D; ++e)
       for (int k = 0; k < C::L1; ++k)
         for (int l = 0; l < C::L; ++l) tab_.P[e][k][l] = (T)re.P[((size_t)e * C::L1 + k) * C::L + l];
+    // the tau = 0 node below each unknown node (same spatial coordinates);
+    // C0 must be that selection (it is, on the principal lattice: C0[k][n] =
+    // theta_n(xi_k, 0) with xi_k a lattice node), else prepare() refuses
+    for (int k = 0; k < C::L1; ++k) {
+      tab_.sel[k] = -1;
+      for (int n = 0; n < C::L0 && tab_.sel[k] < 0; ++n) {
+        bool same = true;
+        for (int a = 0; a < C::D; ++a) same = same && re.stnode[n][a] == re.stnode[C::L0 + k][a];
+        if (same) tab_.sel[k] = n;
+      }
+      if (tab_.sel[k] < 0) {
+        sel_ok_ = false;
+        tab_.sel[k] = 0;
+      }
+      for (int n = 0; n < C::L0; ++n)
+        if (std::fabs(re.C0[k * C::L0 + n] - (n == tab_.sel[k] ? 1.0 : 0.0)) > 1e-12) sel_ok_ = false;
+    }
     ftab_.assign(C::TAB_TOTAL, T(0));
     for (int code = 0; code < C::NCODE; ++code)
       for (int row = 0; row < C::NQT * C::NQS; ++row)
@@ -1681,6 +1778,7 @@ class OpsImpl final : public Ops {
     else return k_flux<C, false>;
   }
   cudaError_t prepare() override {
+    if (C::STASH && !sel_ok_) return cudaErrorInvalidValue;  // C0 is not the lattice selection
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -1751,6 +1849,7 @@ class OpsImpl final : public Ops {
   CellTab<C> tab_;
   std::vector<T> ftab_;
   int use_smem_ = 0;
+  bool sel_ok_ = true;
   int64_t max_blocks_ = 152;
   int64_t max_blocks_qf_ = 152;
 };
