@@ -95,6 +95,14 @@ struct Cfg {
 #else
   static constexpr int PAIR_PASSES = NQT * NQS * NV <= 64 ? 1 : NQT;
 #endif
+  // groups of space-time points per face side in the pair kernel (threads
+  // per face = 2 FLUX_SPLIT)
+#ifdef CW_FLUX_SPLIT
+  static constexpr int FLUX_SPLIT_REQ = CW_FLUX_SPLIT;
+#else
+  static constexpr int FLUX_SPLIT_REQ = 1;
+#endif
+  static constexpr int FLUX_SPLIT = (NQT * NQS) % (FLUX_SPLIT_REQ * PAIR_PASSES) == 0 ? FLUX_SPLIT_REQ : 1;
   // prefetch of the next q_hat chunk in the trace loop where the extra
   // registers are few (measured: faster in 2D Euler, slower for NV >= 5)
   static constexpr bool TR_PREFETCH = VW * NV <= 16;
@@ -130,6 +138,11 @@ struct Cfg {
   static constexpr bool TAU0_SPARSE = CW_TAU0_SPARSE;
 #else
   static constexpr bool TAU0_SPARSE = false;
+#endif
+#ifdef CW_IDS_AHEAD
+  static constexpr bool IDS_AHEAD = CW_IDS_AHEAD;
+#else
+  static constexpr bool IDS_AHEAD = true;
 #endif
   // chunks of four stencil neighbours unrolled together in the gather
 #ifdef CW_GATHER_CHUNKS
@@ -638,10 +651,19 @@ __device__ __forceinline__ void rec_pred_cell(const KArgs<C>& a, const CellTab<C
     constexpr int VW = C::VW, NFULL = NE1 / 4, TAIL = NE1 % 4, GPC = 4 * MC1 / VW;
     const V* Rv = reinterpret_cast<const V*>(a.R);
     const int4* S4 = reinterpret_cast<const int4*>(a.sten4);
+    // with IDS_AHEAD the id vector of the next chunk is loaded while the
+    // current one is in use, so a chunk's gathers wait one round trip, not two
+    int4 idn = __ldg(S4 + i);
     auto chunk = [&](int ch, auto nn) {
       constexpr int NN = decltype(nn)::value;
       constexpr int NG = (NN * MC1 + VW - 1) / VW;
-      const int4 id = __ldg(S4 + (int64_t)ch * N + i);
+      int4 id;
+      if constexpr (C::IDS_AHEAD) {
+        id = idn;
+        if (ch + 1 < sten_vectors(NE1)) idn = __ldg(S4 + (int64_t)(ch + 1) * N + i);
+      } else {
+        id = __ldg(S4 + (int64_t)ch * N + i);
+      }
       const int ids[4] = {id.x, id.y, id.z, id.w};
       T dq[NN][NV];
 #pragma unroll
@@ -1226,16 +1248,21 @@ __global__ void __launch_bounds__(128, C::FLUX_MINB) k_flux(KArgs<C> a, int use_
   }
 }
 
-// Two threads per face (consecutive lanes), persistent grid: each evaluates
-// the traces of its own side at all NQT x NQS space-time points from one
-// pass over that cell's q_hat; the pair then swaps traces by warp shuffles,
-// each thread takes every other point for the Rusanov flux, and the two
-// partial sums are added.  A boundary face evaluates its inner cell on both
-// threads (transmissive: the outer trace equals the inner one).
+// 2 SPLIT threads per face (consecutive lanes), persistent grid.  Lane bit 0
+// is the side; the higher bits pick one of SPLIT groups of the NQT x NQS
+// space-time points (in time order).  Each thread evaluates its own side's
+// traces at its group's points from one pass over that cell's q_hat (or
+// PAIR_PASSES passes); the two sides of a group swap traces by warp
+// shuffles, each thread takes every other point for the numerical flux, and
+// the partial sums of the face's threads are added.  A boundary face
+// evaluates its inner cell on both sides (transmissive: the outer trace
+// equals the inner one).
 template <class C, bool OSHER>
 __global__ void __launch_bounds__(128, C::FLUX_MINB) k_flux_pair(KArgs<C> a, int use_smem) {
   using T = typename C::T;
   constexpr int D = C::D, NV = C::NV, NQS = C::NQS, NP = C::NQT * C::NQS;
+  constexpr int SPLIT = C::FLUX_SPLIT, TPF = 2 * SPLIT;
+  static_assert(NP % (SPLIT * C::PAIR_PASSES) == 0, "points must divide over the groups and passes");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const T* tab = face_tables<C>(a, use_smem, smem_raw);
   const T* wq = tab + C::TABN;
@@ -1243,10 +1270,11 @@ __global__ void __launch_bounds__(128, C::FLUX_MINB) k_flux_pair(KArgs<C> a, int
   const double dtd = dt_of(a.dt_fixed, a.cfl, a.dtmin, a.cur);
   const int64_t N = a.N, F = a.F;
   const int side = (int)(threadIdx.x & 1);
-  // block-uniform trip count (the pair exchanges shuffle over the whole
-  // warp); a thread past the last face works on a clamped copy, not written
-  for (int64_t g0 = (int64_t)blockIdx.x * blockDim.x; g0 < 2 * F; g0 += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t fg = (g0 + threadIdx.x) >> 1;
+  const int grp = (int)(threadIdx.x >> 1) & (SPLIT - 1);
+  // block-uniform trip count (the exchanges shuffle over the whole warp); a
+  // thread past the last face works on a clamped copy, not written
+  for (int64_t g0 = (int64_t)blockIdx.x * blockDim.x; g0 < TPF * F; g0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t fg = (g0 + threadIdx.x) / TPF;
     const bool valid = fg < F;
     const int64_t f = valid ? fg : F - 1;
     const int64_t Lc = a.fL[f];
@@ -1270,57 +1298,60 @@ __global__ void __launch_bounds__(128, C::FLUX_MINB) k_flux_pair(KArgs<C> a, int
 #pragma unroll
       for (int m = 0; m < D; ++m) facc[m][v] = T(0);
     }
-    constexpr int NPP = NP / C::PAIR_PASSES;
+    constexpr int NPP = NP / (SPLIT * C::PAIR_PASSES);
 #pragma unroll 1
     for (int h = 0; h < C::PAIR_PASSES; ++h) {
-    T tr[NPP][NV];
+      const int p00 = (grp * C::PAIR_PASSES + h) * NPP;  // first point of this pass
+      T tr[NPP][NV];
 #pragma unroll
-    for (int p = 0; p < NPP; ++p)
+      for (int p = 0; p < NPP; ++p)
 #pragma unroll
-      for (int v = 0; v < NV; ++v) tr[p][v] = T(0);
-    face_traces<C, NPP>(a.qhat, c, N, tc, h * NPP, tr);
+        for (int v = 0; v < NV; ++v) tr[p][v] = T(0);
+      face_traces<C, NPP>(a.qhat, c, N, tc, p00, tr);
 #pragma unroll
-    for (int k = 0; k < (NPP + 1) / 2; ++k) {
-      constexpr int LAST = NPP - 1;
-      const int p0 = 2 * k, p1 = 2 * k + 1 <= LAST ? 2 * k + 1 : LAST;
-      // thread 0 of the pair takes point p0, thread 1 point p1: each sends
-      // the partner its own trace at the partner's point
-      T mine[NV], other[NV];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        const T send = side == 0 ? tr[p1][v] : tr[p0][v];
-        other[v] = __shfl_xor_sync(0xffffffffu, send, 1);
-        mine[v] = side == 0 ? tr[p0][v] : tr[p1][v];
-      }
-      if (side == 0 || 2 * k + 1 <= LAST) {
-        const int p = h * NPP + (side == 0 ? p0 : p1);
-        T ul[NV], ur[NV];
+      for (int k = 0; k < (NPP + 1) / 2; ++k) {
+        constexpr int LAST = NPP - 1;
+        const int p0 = 2 * k, p1 = 2 * k + 1 <= LAST ? 2 * k + 1 : LAST;
+        // side 0 takes point p0, side 1 point p1: each sends the partner its
+        // own trace at the partner's point
+        T mine[NV], other[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          ul[v] = qbL[v] + (side == 0 ? mine[v] : other[v]);
-          ur[v] = qbR[v] + (side == 0 ? other[v] : mine[v]);
+          const T send = side == 0 ? tr[p1][v] : tr[p0][v];
+          other[v] = __shfl_xor_sync(0xffffffffu, send, 1);
+          mine[v] = side == 0 ? tr[p0][v] : tr[p1][v];
         }
-        rusanov_point<C, OSHER>(a, ul, ur, qbL, qbR, n, wq[p % NQS] * wt[p / NQS], facc, dacc);
+        if (side == 0 || 2 * k + 1 <= LAST) {
+          const int p = p00 + (side == 0 ? p0 : p1);
+          T ul[NV], ur[NV];
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            ul[v] = qbL[v] + (side == 0 ? mine[v] : other[v]);
+            ur[v] = qbR[v] + (side == 0 ? other[v] : mine[v]);
+          }
+          rusanov_point<C, OSHER>(a, ul, ur, qbL, qbR, n, wq[p % NQS] * wt[p / NQS], facc, dacc);
+        }
       }
     }
-    }
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      dacc[v] += __shfl_xor_sync(0xffffffffu, dacc[v], 1);
+    for (int o = 1; o < TPF; o <<= 1)
 #pragma unroll
-      for (int m = 0; m < D; ++m) facc[m][v] += __shfl_xor_sync(0xffffffffu, facc[m][v], 1);
-    }
-    // FP64 contraction split over the pair: thread 0 takes the first H
-    // variables, thread 1 the rest, so every FP64 instruction runs on all lanes
+      for (int v = 0; v < NV; ++v) {
+        dacc[v] += __shfl_xor_sync(0xffffffffu, dacc[v], o);
+#pragma unroll
+        for (int m = 0; m < D; ++m) facc[m][v] += __shfl_xor_sync(0xffffffffu, facc[m][v], o);
+      }
+    // FP64 contraction split over the face's threads (thread q takes the
+    // variables q, q + TPF, ...), so every FP64 instruction runs on all lanes
     if (valid) {
-      constexpr int H = (NV + 1) / 2;
+      const int q = (int)(threadIdx.x % TPF);
       double fa[D];
 #pragma unroll
       for (int m = 0; m < D; ++m) fa[m] = a.fa[m * F + f];
       const double area = a.farea[f];
 #pragma unroll
-      for (int j = 0; j < H; ++j) {
-        const int v = side == 0 ? j : H + j;
+      for (int j = 0; j < (NV + TPF - 1) / TPF; ++j) {
+        const int v = q + j * TPF;
         if (v >= NV) break;
         T dv = dacc[0];
         T fv[D];
@@ -1815,7 +1846,7 @@ class OpsImpl final : public Ops {
       return cudaGetLastError();
     }
     const size_t smem = use_smem_ ? quad_table_bytes() : 0;
-    unsigned nb = (unsigned)std::min<int64_t>(nblk(s.F * (C::PAIR ? 2 : 1), 128), max_blocks_);
+    unsigned nb = (unsigned)std::min<int64_t>(nblk(s.F * (C::PAIR ? 2 * C::FLUX_SPLIT : 1), 128), max_blocks_);
     flux_kernel(ph.flux == 1)<<<nb, 128, smem, st>>>(a, use_smem_);
     return cudaGetLastError();
   }
