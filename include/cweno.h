@@ -280,11 +280,16 @@ int cweno_stable_dt_noalloc(int dim, int pde, int64_t ncells, const double* Q, c
  * Serving: continuous batching of independent solves on one GPU.
  * A request owns a mesh (copied), order, initial state, CFL and step count.
  * The server admits requests while their measured device footprint fits the
- * memory budget and a slot is free, runs the ready time steps of all
- * admitted requests concurrently on its worker streams (each request's
- * steps are replayed from a captured CUDA graph), retires finished ones and
- * admits waiting ones as slots and memory free up.  Results are identical
- * to running the same request alone (no cross-request reductions).
+ * memory budget and a slot is free, sets each one up on a host worker, and
+ * groups the admitted requests by configuration (dimension, order, PDE,
+ * precision, flux).  Each group advances all of its members by one time step
+ * per tick: one captured CUDA graph of batched kernels over a table of the
+ * members (the reconstruction + predictor, flux and update of every member's
+ * cells and faces in the same three launches), replayed every tick with the
+ * table rewritten in place as members join and leave.  Groups tick
+ * concurrently; finished requests are retired and waiting ones admitted as
+ * slots and memory free up.  Results are identical to running the same
+ * request alone (same per-cell arithmetic, no cross-request reductions).
  * ------------------------------------------------------------------------- */
 typedef struct {
   int dim;
@@ -305,7 +310,8 @@ enum { CWENO_REQ_QUEUED = 0, CWENO_REQ_RUNNING = 1, CWENO_REQ_DONE = 2, CWENO_RE
 
 /* mem_budget: device bytes the server may hold for admitted requests
  * (0 -> 80% of free memory); max_slots: concurrently admitted requests, each
- * with its own CUDA stream (<= 0 -> 64); nworkers: host threads preparing
+ * with its own CUDA stream for its setup (<= 0 or > 64 -> 64, the capacity of
+ * a group's batch table); nworkers: host threads preparing
  * admitted requests (mesh and stencils on the host, least-squares inverses
  * on the device; <= 0 -> half the host cores).  Admission is first come,
  * first served. */
@@ -324,6 +330,10 @@ int serve_drain(cweno_server* s, double timeout_s);
  * cell-updates completed. */
 int serve_stats(cweno_server* s, uint64_t* submitted, uint64_t* admitted, uint64_t* completed,
                 uint64_t* peak_running, double* cell_updates);
+/* Batching counters: ticks completed (one batched time step of one group)
+ * and the member time steps they carried (member_steps / ticks = requests
+ * advanced per launch sequence). */
+int serve_batch_stats(cweno_server* s, uint64_t* ticks, uint64_t* member_steps);
 void serve_destroy(cweno_server* s);
 
 #ifdef __cplusplus

@@ -82,6 +82,7 @@ SIGNATURES = [
     ("serve_poll", _I, [_P, C.c_uint64, _IP, _DP, _DP]),
     ("serve_drain", _I, [_P, _D]),
     ("serve_stats", _I, [_P, _U64P, _U64P, _U64P, _U64P, _DP]),
+    ("serve_batch_stats", _I, [_P, _U64P, _U64P]),
     ("serve_destroy", None, [_P]),
 ]
 
@@ -387,8 +388,10 @@ class Server:
         a, b, c, d = C.c_uint64(), C.c_uint64(), C.c_uint64(), C.c_uint64()
         cu = C.c_double()
         _check(lib().serve_stats(self.h, C.byref(a), C.byref(b), C.byref(c), C.byref(d), C.byref(cu)))
+        t, ms = C.c_uint64(), C.c_uint64()
+        _check(lib().serve_batch_stats(self.h, C.byref(t), C.byref(ms)))
         return dict(submitted=a.value, admitted=b.value, completed=c.value, peak_running=d.value,
-                    cell_updates=cu.value)
+                    cell_updates=cu.value, ticks=t.value, member_steps=ms.value)
 
     def close(self):
         if getattr(self, "h", None):

@@ -1178,19 +1178,17 @@ __device__ __forceinline__ void cell_average(const KArgs<C>& a, int64_t c, typen
   }
 }
 
-// One thread per face, persistent grid: both sides' traces one time point
-// at a time (NQS space points), Rusanov flux, space-time quadrature.
+// One face, one thread: both sides' traces one time point at a time (NQS
+// space points), Rusanov flux, space-time quadrature.  `tab` holds the face
+// tables, then the space and time quadrature weights.
 template <class C, bool OSHER>
-__global__ void __launch_bounds__(128, C::FLUX_MINB) k_flux(KArgs<C> a, int use_smem) {
+__device__ __forceinline__ void flux_one_face(const KArgs<C>& a, const typename C::T* tab, int64_t f, double dtd) {
   using T = typename C::T;
   constexpr int D = C::D, NV = C::NV, NQS = C::NQS, NQT = C::NQT;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const T* tab = face_tables<C>(a, use_smem, smem_raw);
   const T* wq = tab + C::TABN;
   const T* wt = wq + NQS;
-  const double dtd = dt_of(a.dt_fixed, a.cfl, a.dtmin, a.cur);
   const int64_t N = a.N, F = a.F;
-  for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < F; f += (int64_t)gridDim.x * blockDim.x) {
+  {
     const int64_t Lc = a.fL[f];
     const int64_t Rc = a.fR[f];
     const T* tL = tab + (int)a.codeL[f] * C::CODE_STRIDE;
@@ -1248,6 +1246,16 @@ __global__ void __launch_bounds__(128, C::FLUX_MINB) k_flux(KArgs<C> a, int use_
   }
 }
 
+// One thread per face, persistent grid.
+template <class C, bool OSHER>
+__global__ void __launch_bounds__(128, C::FLUX_MINB) k_flux(KArgs<C> a, int use_smem) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const typename C::T* tab = face_tables<C>(a, use_smem, smem_raw);
+  const double dtd = dt_of(a.dt_fixed, a.cfl, a.dtmin, a.cur);
+  for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < a.F; f += (int64_t)gridDim.x * blockDim.x)
+    flux_one_face<C, OSHER>(a, tab, f, dtd);
+}
+
 // 2 SPLIT threads per face (consecutive lanes), persistent grid.  Lane bit 0
 // is the side; the higher bits pick one of SPLIT groups of the NQT x NQS
 // space-time points (in time order).  Each thread evaluates its own side's
@@ -1257,23 +1265,21 @@ __global__ void __launch_bounds__(128, C::FLUX_MINB) k_flux(KArgs<C> a, int use_
 // the partial sums of the face's threads are added.  A boundary face
 // evaluates its inner cell on both sides (transmissive: the outer trace
 // equals the inner one).
+// One block iteration of the pair kernel: the 128 threads starting at
+// thread index g0 of the face space (TPF threads per face).  `tab` holds the
+// face tables, then the space and time quadrature weights.
 template <class C, bool OSHER>
-__global__ void __launch_bounds__(128, C::FLUX_MINB) k_flux_pair(KArgs<C> a, int use_smem) {
+__device__ __forceinline__ void flux_pair_iter(const KArgs<C>& a, const typename C::T* tab, int64_t g0, double dtd) {
   using T = typename C::T;
   constexpr int D = C::D, NV = C::NV, NQS = C::NQS, NP = C::NQT * C::NQS;
   constexpr int SPLIT = C::FLUX_SPLIT, TPF = 2 * SPLIT;
   static_assert(NP % (SPLIT * C::PAIR_PASSES) == 0, "points must divide over the groups and passes");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const T* tab = face_tables<C>(a, use_smem, smem_raw);
   const T* wq = tab + C::TABN;
   const T* wt = wq + NQS;
-  const double dtd = dt_of(a.dt_fixed, a.cfl, a.dtmin, a.cur);
   const int64_t N = a.N, F = a.F;
   const int side = (int)(threadIdx.x & 1);
   const int grp = (int)(threadIdx.x >> 1) & (SPLIT - 1);
-  // block-uniform trip count (the exchanges shuffle over the whole warp); a
-  // thread past the last face works on a clamped copy, not written
-  for (int64_t g0 = (int64_t)blockIdx.x * blockDim.x; g0 < TPF * F; g0 += (int64_t)gridDim.x * blockDim.x) {
+  {
     const int64_t fg = (g0 + threadIdx.x) / TPF;
     const bool valid = fg < F;
     const int64_t f = valid ? fg : F - 1;
@@ -1371,6 +1377,18 @@ __global__ void __launch_bounds__(128, C::FLUX_MINB) k_flux_pair(KArgs<C> a, int
       }
     }
   }
+}
+
+template <class C, bool OSHER>
+__global__ void __launch_bounds__(128, C::FLUX_MINB) k_flux_pair(KArgs<C> a, int use_smem) {
+  constexpr int TPF = 2 * C::FLUX_SPLIT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const typename C::T* tab = face_tables<C>(a, use_smem, smem_raw);
+  const double dtd = dt_of(a.dt_fixed, a.cfl, a.dtmin, a.cur);
+  // block-uniform trip count (the exchanges shuffle over the whole warp); a
+  // thread past the last face works on a clamped copy, not written
+  for (int64_t g0 = (int64_t)blockIdx.x * blockDim.x; g0 < TPF * a.F; g0 += (int64_t)gridDim.x * blockDim.x)
+    flux_pair_iter<C, OSHER>(a, tab, g0, dtd);
 }
 
 // Quadrature-free Rusanov flux (the fixed-mesh form the paper describes
@@ -1542,13 +1560,14 @@ __device__ __forceinline__ void block_min_atomic(T val, unsigned long long* targ
 }
 
 // ------------------------------------------------------------------ update
+// One cell of the update; returns its ratio h_i / |lambda_max| for the CFL
+// bound of the next step (+inf past the last cell).
 template <class C>
-__global__ void __launch_bounds__(256) k_update(KArgs<C> a) {
+__device__ __forceinline__ typename C::T update_cell(const KArgs<C>& a, int64_t i) {
   using T = typename C::T;
   constexpr int D = C::D, NV = C::NV;
   using PH = Phys<D, C::PDE, T>;
   const int64_t N = a.N, F = a.F;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   T ratio = T(INFINITY);
   if (i < N) {
     // sum_f +-G_f: the sign of a face's integral is flipped on the bits (no
@@ -1597,8 +1616,105 @@ __global__ void __launch_bounds__(256) k_update(KArgs<C> a) {
     const T sp = PH::speed(qt, a.gamma, a.ch);
     ratio = (T)a.hsize[i] / sp;
   }
+  return ratio;
+}
+
+template <class C>
+__global__ void __launch_bounds__(256) k_update(KArgs<C> a) {
+  const typename C::T ratio = update_cell<C>(a, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
   block_min_atomic(ratio, a.dtmin + (1 - a.cur));
   if (blockIdx.x == 0 && threadIdx.x == 0) *a.time += dt_of(a.dt_fixed, a.cfl, a.dtmin, a.cur);
+}
+
+// ------------------------------------------------- batched steps (serving)
+// One time step of many solvers of one configuration in each launch.  A
+// table in device memory lists the solvers (their kernel arguments) and,
+// per kernel, the prefix sums of their work chunks: 128 cells for the
+// reconstruction + predictor, 128 threads of the face space for the fluxes,
+// 256 cells for the update.  The grids are persistent (sized to the
+// resident blocks) and loop over the chunks; a block stages the arguments of
+// its chunk's solver in shared memory.  Every cell and face of a solver gets
+// the arithmetic of the single-solver kernels (the same device functions),
+// and the CFL minimum reduces within a solver's own blocks, so each result
+// equals the solver stepped alone.
+constexpr int kBatchMaxSeg = 64;
+struct BatchHdr {
+  int nseg;
+  int pad;
+  int pref[3][kBatchMaxSeg + 1];
+};
+template <class C>
+struct BatchTab {
+  BatchHdr h;
+  KArgs<C> a[kBatchMaxSeg];
+};
+
+// index of the solver whose chunk range holds chunk c (pref ascending)
+__device__ __forceinline__ int batch_seg(const int* pref, int nseg, int c) {
+  int lo = 0, hi = nseg - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pref[mid] <= c) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// stage the arguments of chunk c's solver into sa; returns the chunk's index
+// within that solver
+template <class C>
+__device__ __forceinline__ int batch_stage(const BatchTab<C>* bt, int kernel, int c, KArgs<C>& sa) {
+  const int seg = batch_seg(bt->h.pref[kernel], bt->h.nseg, c);
+  __syncthreads();
+  const int* src = reinterpret_cast<const int*>(&bt->a[seg]);
+  int* dst = reinterpret_cast<int*>(&sa);
+  for (int k = threadIdx.x; k < (int)(sizeof(KArgs<C>) / 4); k += blockDim.x) dst[k] = src[k];
+  __syncthreads();
+  return c - bt->h.pref[kernel][seg];
+}
+
+template <class C>
+__global__ void __launch_bounds__(128, C::REC_MINB) k_rec_pred_batch(const BatchTab<C>* bt,
+                                                                     const __grid_constant__ CellTab<C> tb) {
+  __shared__ __align__(16) KArgs<C> sa;
+  const int total = bt->h.pref[0][bt->h.nseg];
+  for (int c = blockIdx.x; c < total; c += gridDim.x) {
+    const int lc = batch_stage(bt, 0, c, sa);
+    if (lc == 0 && threadIdx.x == 0 && sa.reset_next) sa.dtmin[1 - sa.cur] = 0x7ff0000000000000ull;
+    rec_pred_cell<C, false>(sa, tb, (int64_t)lc * 128 + threadIdx.x);
+  }
+}
+
+template <class C, bool OSHER>
+__global__ void __launch_bounds__(128, C::FLUX_MINB) k_flux_batch(const BatchTab<C>* bt, int use_smem) {
+  using T = typename C::T;
+  __shared__ __align__(16) KArgs<C> sa;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // the face tables depend on the configuration only: any solver's copy
+  const T* tab = face_tables<C>(bt->a[0], use_smem, smem_raw);
+  const int total = bt->h.pref[1][bt->h.nseg];
+  for (int c = blockIdx.x; c < total; c += gridDim.x) {
+    const int lc = batch_stage(bt, 1, c, sa);
+    const double dtd = dt_of(sa.dt_fixed, sa.cfl, sa.dtmin, sa.cur);
+    if constexpr (C::PAIR) {
+      flux_pair_iter<C, OSHER>(sa, tab, (int64_t)lc * 128, dtd);
+    } else {
+      const int64_t f = (int64_t)lc * 128 + threadIdx.x;
+      if (f < sa.F) flux_one_face<C, OSHER>(sa, tab, f, dtd);
+    }
+  }
+}
+
+template <class C>
+__global__ void __launch_bounds__(256) k_update_batch(const BatchTab<C>* bt) {
+  __shared__ __align__(16) KArgs<C> sa;
+  const int total = bt->h.pref[2][bt->h.nseg];
+  for (int c = blockIdx.x; c < total; c += gridDim.x) {
+    const int lc = batch_stage(bt, 2, c, sa);
+    const typename C::T ratio = update_cell<C>(sa, (int64_t)lc * 256 + threadIdx.x);
+    block_min_atomic(ratio, sa.dtmin + (1 - sa.cur));
+    if (lc == 0 && threadIdx.x == 0) *sa.time += dt_of(sa.dt_fixed, sa.cfl, sa.dtmin, sa.cur);
+  }
 }
 
 template <class C>
@@ -1835,6 +1951,26 @@ class OpsImpl final : public Ops {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nbq, k_flux_qf<C>, 128, 0);
     if (e != cudaSuccess) return e;
     max_blocks_qf_ = (int64_t)std::max(1, nbq) * nsm;
+    // batched kernels (serving): resident grids
+    e = cudaFuncSetAttribute(k_rec_pred_batch<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::PRED_SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    int nb1 = 0, nb2 = 0, nb3 = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb1, k_rec_pred_batch<C>, 128, C::PRED_SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    if (use_smem_) {
+      for (int o = 0; o < (C::PDE == 0 ? 2 : 1); ++o) {
+        e = cudaFuncSetAttribute(o ? (const void*)k_flux_batch<C, true> : (const void*)k_flux_batch<C, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+      }
+    }
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k_flux_batch<C, false>, 128, use_smem_ ? smem : 0);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb3, k_update_batch<C>, 256, 0);
+    if (e != cudaSuccess) return e;
+    max_blocks_rec_b_ = (int64_t)std::max(1, nb1) * nsm;
+    max_blocks_flux_b_ = (int64_t)std::max(1, nb2) * nsm;
+    max_blocks_upd_b_ = (int64_t)std::max(1, nb3) * nsm;
     return cudaSuccess;
   }
   cudaError_t flux(const DevState& s, const PhysParams& ph, DtArgs dt, cudaStream_t st) override {
@@ -1870,6 +2006,33 @@ class OpsImpl final : public Ops {
     k_get_state<C><<<nblk(s.N * C::NV, 256), 256, 0, st>>>(a, user);
     return cudaGetLastError();
   }
+  size_t batch_bytes() const override { return sizeof(BatchTab<C>); }
+  int batch_max() const override { return kBatchMaxSeg; }
+  void batch_fill(void* host_tab, int nseg, const DevState* const* ds, const PhysParams* const* ph,
+                  const DtArgs* dt) const override {
+    BatchTab<C>* bt = reinterpret_cast<BatchTab<C>*>(host_tab);
+    std::memset(&bt->h, 0, sizeof(bt->h));
+    bt->h.nseg = nseg;
+    const int64_t tpf = C::PAIR ? 2 * C::FLUX_SPLIT : 1;
+    for (int k = 0; k < nseg; ++k) {
+      bt->a[k] = args(*ds[k], *ph[k], dt[k]);
+      bt->h.pref[0][k + 1] = bt->h.pref[0][k] + (int)nblk(ds[k]->N, 128);
+      bt->h.pref[1][k + 1] = bt->h.pref[1][k] + (int)nblk(ds[k]->F * tpf, 128);
+      bt->h.pref[2][k + 1] = bt->h.pref[2][k] + (int)nblk(ds[k]->N, 256);
+    }
+  }
+  cudaError_t step_batch(const void* dev_tab, int flux, cudaStream_t st) override {
+    const BatchTab<C>* bt = reinterpret_cast<const BatchTab<C>*>(dev_tab);
+    k_rec_pred_batch<C><<<(unsigned)max_blocks_rec_b_, 128, C::PRED_SMEM_BYTES, st>>>(bt, tab_);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t smem = use_smem_ ? quad_table_bytes() : 0;
+    if (flux == 1 && C::PDE == 0) k_flux_batch<C, true><<<(unsigned)max_blocks_flux_b_, 128, smem, st>>>(bt, use_smem_);
+    else k_flux_batch<C, false><<<(unsigned)max_blocks_flux_b_, 128, smem, st>>>(bt, use_smem_);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_update_batch<C><<<(unsigned)max_blocks_upd_b_, 256, 0, st>>>(bt);
+    return cudaGetLastError();
+  }
   cudaError_t qhat_out(const DevState& s, double* user, cudaStream_t st) override {
     KArgs<C> a = args(s, PhysParams(), DtArgs());
     k_qhat_out<C><<<nblk(s.N, 256), 256, 0, st>>>(a, user);
@@ -1883,6 +2046,7 @@ class OpsImpl final : public Ops {
   bool sel_ok_ = true;
   int64_t max_blocks_ = 152;
   int64_t max_blocks_qf_ = 152;
+  int64_t max_blocks_rec_b_ = 152, max_blocks_flux_b_ = 152, max_blocks_upd_b_ = 152;
 };
 
 }  // namespace cw

@@ -75,6 +75,14 @@ class Ops {
   virtual cudaError_t set_state(const DevState& s, const double* user_dev, cudaStream_t st) = 0;
   virtual cudaError_t get_state(const DevState& s, double* user_dev, cudaStream_t st) = 0;
   virtual cudaError_t qhat_out(const DevState& s, double* user_dev, cudaStream_t st) = 0;
+  // Batched time steps of many solvers of this configuration (serving): the
+  // table's size, its host image for nseg solvers (at most batch_max()), and
+  // one step of all of them from the device copy of that image.
+  virtual size_t batch_bytes() const = 0;
+  virtual int batch_max() const = 0;
+  virtual void batch_fill(void* host_tab, int nseg, const DevState* const* ds, const PhysParams* const* ph,
+                          const DtArgs* dt) const = 0;
+  virtual cudaError_t step_batch(const void* dev_tab, int flux, cudaStream_t st) = 0;
 };
 
 // Factories (one per translation unit); nullptr if (M, precision) is not built.

@@ -3,13 +3,23 @@
 //
 // submit -> FIFO queue -> admission (a free slot and the request's device
 // footprint within the budget) -> host setup worker (mesh, stencils, FP64
-// least-squares inverses, uploads on the slot's stream) -> the request's whole
-// run (set_state, nsteps steps captured once as one CUDA graph, state copied
-// to pinned host memory) is launched on its slot stream -> a completion event
-// -> the scheduler retires it (stream-ordered frees), and admits the next.
-// Different requests overlap on the device through their streams; host setup
-// of waiting requests overlaps with the device work of running ones.  No
-// reduction spans requests, so every result equals the same solve run alone.
+// least-squares inverses on the device, initial state and CFL bound, on the
+// slot's stream) -> the request joins the group of its configuration
+// (dimension, order, PDE, precision, flux).
+//
+// Each group advances all of its members by one time step per tick: one
+// captured CUDA graph (the group's batch table copied from pinned host
+// memory, then the batched reconstruction + predictor, flux and update
+// kernels over all members' cells and faces), replayed every tick on the
+// group's stream.  Between ticks the scheduler rewrites the table in place
+// (members that joined or left, each member's time-step slot), so changes of
+// membership need no new capture.  A member's last tick also copies its
+// final state to pinned host memory; the scheduler retires it when that
+// tick's event completes and admits waiting requests as slots and memory
+// free up.  Groups tick concurrently on their own streams, and host setup of
+// waiting requests overlaps with the ticks.  Every cell and face of a member
+// gets the arithmetic of the single-solver kernels and no reduction spans
+// members, so every result equals the same solve run alone.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -23,6 +33,7 @@
 #include <mutex>
 #include <string>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "../../include/cweno.h"
@@ -31,6 +42,8 @@
 namespace {
 
 using Clock = std::chrono::steady_clock;
+
+struct Group;
 
 struct Req {
   uint64_t id = 0;
@@ -46,12 +59,30 @@ struct Req {
   cweno_mesh* mesh = nullptr;
   cweno_solver* solver = nullptr;
   int slot = -1;
-  cudaEvent_t done = nullptr;
-  cudaGraphExec_t graph = nullptr;
+  int steps_done = 0;
   double* hout = nullptr;  // pinned: nc * nvars
   int* hstatus = nullptr;  // pinned
   std::vector<double> Qout;
   std::string err;
+};
+
+// One configuration's batch: its members, the pinned and device images of
+// the batch table, the captured tick graph and the tick in flight.
+struct Group {
+  std::tuple<int, int, int, int, int> key;  // dim, order, pde, precision, flux
+  int flux = 0;
+  std::unique_ptr<cw::Ops> ops;
+  cudaStream_t stream = nullptr;
+  void* htab = nullptr;
+  void* dtab = nullptr;
+  size_t tab_bytes = 0;
+  cudaGraphExec_t graph = nullptr;
+  cudaEvent_t done = nullptr;
+  bool in_flight = false;
+  std::vector<Req*> members;    // stepping
+  std::vector<Req*> ticking;    // members of the tick in flight
+  std::vector<Req*> finishing;  // members whose final state that tick copies
+  uint64_t ticks = 0;
 };
 
 }  // namespace
@@ -64,12 +95,13 @@ struct cweno_server {
   std::vector<int> free_slots;
   std::mutex mu;
   std::condition_variable cv;
-  std::deque<Req*> queue;     // submitted, waiting for admission
-  std::deque<Req*> setup_q;   // admitted, waiting for a setup worker
-  std::vector<Req*> inflight; // launched on the device
+  std::deque<Req*> queue;    // submitted, waiting for admission
+  std::deque<Req*> setup_q;  // admitted, waiting for a setup worker
+  std::vector<Req*> ready;   // set up, waiting to join their group
   std::map<uint64_t, Req*> all;
-  int active = 0;             // admitted and not retired
-  uint64_t next_id = 1, n_sub = 0, n_adm = 0, n_done = 0, peak = 0;
+  std::vector<std::unique_ptr<Group>> groups;  // scheduler thread only
+  int active = 0;                              // admitted and not retired
+  uint64_t next_id = 1, n_sub = 0, n_adm = 0, n_done = 0, peak = 0, ticks = 0, member_steps = 0;
   double cell_updates = 0.0;
   bool stop = false;
   std::thread sched;
@@ -117,14 +149,10 @@ void release_slot(cweno_server* S, Req* r) {  // caller holds S->mu
 }
 
 void teardown(cweno_server* S, Req* r) {
-  if (r->graph) cudaGraphExecDestroy(r->graph);
-  r->graph = nullptr;
   if (r->solver) cweno_solver_destroy(r->solver);
   r->solver = nullptr;
   if (r->mesh) cweno_mesh_destroy(r->mesh);
   r->mesh = nullptr;
-  if (r->done) cudaEventDestroy(r->done);
-  r->done = nullptr;
   pin_put(S, r->hout);
   r->hout = nullptr;
   pin_put(S, r->hstatus);
@@ -134,8 +162,9 @@ void teardown(cweno_server* S, Req* r) {
   std::vector<double>().swap(r->Q0);
 }
 
-// Host setup and launch of one admitted request (worker thread).
-int prepare_and_launch(cweno_server* S, Req* r, std::string& err) {
+// Host setup of one admitted request (worker thread): mesh, solver, initial
+// state and CFL bound on the slot's stream, complete when this returns.
+int prepare(cweno_server* S, Req* r, std::string& err) {
   cudaStream_t st = S->streams[r->slot];
   int rc = cweno_mesh_create(r->dim, r->nverts, r->xyz.data(), r->nc, r->cells.data(),
                              r->has_period ? r->period.data() : nullptr, &r->mesh);
@@ -158,34 +187,10 @@ int prepare_and_launch(cweno_server* S, Req* r, std::string& err) {
     err = "pinned host allocation failed";
     return CWENO_ENOMEM;
   }
-  rc = cweno_set_state(r->solver, r->Q0.data(), 0);
+  rc = cweno_set_state(r->solver, r->Q0.data(), 0);  // also the CFL bound of the first step
   if (rc) return err = cweno_last_error(), rc;
-  // the whole run as one graph: nsteps x (rec+predictor, fluxes, update)
-  cweno_solver* s = r->solver;
-  cudaGraph_t g;
-  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-    err = "stream capture failed to start";
-    return CWENO_ECUDA;
-  }
-  int erc = CWENO_OK;
-  for (int k = 0; k < r->nsteps && erc == CWENO_OK; ++k) {
-    erc = cw::enqueue_step(s, 0.0, s->cur);
-    s->cur ^= 1;
-  }
-  if (erc == CWENO_OK) erc = s->ops->get_state(s->ds, s->ds.stage, st) == cudaSuccess ? CWENO_OK : CWENO_ECUDA;
-  cudaError_t e = cudaStreamEndCapture(st, &g);
-  if (erc) return err = "step capture failed", erc;
-  if (e != cudaSuccess) return err = std::string("capture: ") + cudaGetErrorString(e), CWENO_ECUDA;
-  e = cudaGraphInstantiate(&r->graph, g, 0);
-  cudaGraphDestroy(g);
-  if (e != cudaSuccess) return err = std::string("instantiate: ") + cudaGetErrorString(e), CWENO_ECUDA;
-  if ((e = cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming)) != cudaSuccess ||
-      (e = cudaGraphLaunch(r->graph, st)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(r->hout, s->ds.stage, sizeof(double) * r->nc * r->nvars, cudaMemcpyDeviceToHost, st)) !=
-          cudaSuccess ||
-      (e = cudaMemcpyAsync(r->hstatus, s->ds.status, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-      (e = cudaEventRecord(r->done, st)) != cudaSuccess)
-    return err = std::string("launch: ") + cudaGetErrorString(e), CWENO_ECUDA;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return err = std::string("setup: ") + cudaGetErrorString(e), CWENO_ECUDA;
   return CWENO_OK;
 }
 
@@ -202,7 +207,7 @@ void worker_main(cweno_server* S) {
       S->setup_q.pop_front();
     }
     std::string err;
-    int rc = prepare_and_launch(S, r, err);
+    int rc = prepare(S, r, err);
     std::lock_guard<std::mutex> lk(S->mu);
     if (rc) {
       r->status = CWENO_REQ_ERROR;
@@ -214,16 +219,114 @@ void worker_main(cweno_server* S) {
       S->n_done++;
     } else {
       r->status = CWENO_REQ_RUNNING;
-      S->inflight.push_back(r);
+      S->ready.push_back(r);
     }
     S->cv.notify_all();
   }
 }
 
+// The group of r's configuration, created (with its tick graph) on first use.
+Group* group_of(cweno_server* S, Req* r, std::string& err) {
+  const int flux = r->solver->prm.flux;
+  auto key = std::make_tuple(r->dim, r->order, r->pde, r->prec, flux);
+  for (auto& g : S->groups)
+    if (g->key == key) return g.get();
+  std::unique_ptr<Group> g(new Group());
+  g->key = key;
+  g->flux = flux;
+  const int M = r->order - 1, fp32 = r->prec == CWENO_FP32_MIXED;
+  const cw::RefElem& re = cw::ref_elem(r->dim, M);
+  if (r->pde == CWENO_EULER && r->dim == 2) g->ops = cw::make_ops_euler2(M, fp32, re);
+  else if (r->pde == CWENO_EULER && r->dim == 3) g->ops = cw::make_ops_euler3(M, fp32, re);
+  else g->ops = cw::make_ops_mhd2(M, fp32, re);
+  if (!g->ops) return err = "configuration not built", nullptr;
+  cudaError_t e = g->ops->prepare();
+  g->tab_bytes = g->ops->batch_bytes();
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMallocHost(&g->htab, g->tab_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&g->dtab, g->tab_bytes);
+  if (e == cudaSuccess) {
+    std::memset(g->htab, 0, g->tab_bytes);
+    cudaGraph_t graph;
+    e = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e1 = cudaMemcpyAsync(g->dtab, g->htab, g->tab_bytes, cudaMemcpyHostToDevice, g->stream);
+      cudaError_t e2 = e1 == cudaSuccess ? g->ops->step_batch(g->dtab, flux, g->stream) : e1;
+      e = cudaStreamEndCapture(g->stream, &graph);
+      if (e == cudaSuccess && e2 != cudaSuccess) e = e2;
+      if (e == cudaSuccess) {
+        e = cudaGraphInstantiate(&g->graph, graph, 0);
+        cudaGraphDestroy(graph);
+      }
+    }
+  }
+  if (e != cudaSuccess) {
+    err = std::string("batch setup: ") + cudaGetErrorString(e);
+    if (g->graph) cudaGraphExecDestroy(g->graph);
+    if (g->dtab) cudaFree(g->dtab);
+    if (g->htab) cudaFreeHost(g->htab);
+    if (g->done) cudaEventDestroy(g->done);
+    if (g->stream) cudaStreamDestroy(g->stream);
+    return nullptr;
+  }
+  S->groups.push_back(std::move(g));
+  return S->groups.back().get();
+}
+
+// One tick of g: table of the members, graph launch, final-state copies of
+// the members that reach their last step, completion event.
+cudaError_t launch_tick(Group* g) {
+  const int n = (int)g->members.size();
+  std::vector<const cw::DevState*> ds(n);
+  std::vector<const cw::PhysParams*> ph(n);
+  std::vector<cw::DtArgs> dt(n);
+  for (int k = 0; k < n; ++k) {
+    cweno_solver* s = g->members[k]->solver;
+    ds[k] = &s->ds;
+    ph[k] = &s->ph;
+    dt[k].fixed = 0.0;  // the CFL bound computed on the device
+    dt[k].cfl = s->prm.cfl;
+    dt[k].cur = s->cur;
+  }
+  g->ops->batch_fill(g->htab, n, ds.data(), ph.data(), dt.data());
+  cudaError_t e = cudaGraphLaunch(g->graph, g->stream);
+  if (e != cudaSuccess) return e;
+  g->ticking = g->members;
+  g->finishing.clear();
+  for (Req* r : g->members) {
+    if (r->steps_done + 1 < r->nsteps) continue;
+    cweno_solver* s = r->solver;
+    if ((e = s->ops->get_state(s->ds, s->ds.stage, g->stream)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(r->hout, s->ds.stage, sizeof(double) * r->nc * r->nvars, cudaMemcpyDeviceToHost,
+                             g->stream)) != cudaSuccess)
+      return e;
+    if ((e = cudaMemcpyAsync(r->hstatus, s->ds.status, sizeof(int), cudaMemcpyDeviceToHost, g->stream)) !=
+        cudaSuccess)
+      return e;
+    g->finishing.push_back(r);
+  }
+  if ((e = cudaEventRecord(g->done, g->stream)) != cudaSuccess) return e;
+  g->in_flight = true;
+  g->ticks++;
+  return cudaSuccess;
+}
+
+void retire(cweno_server* S, Req* r, int status, const std::string& err) {
+  teardown(S, r);
+  std::lock_guard<std::mutex> lk(S->mu);
+  r->status = status;
+  if (status == CWENO_REQ_ERROR) r->err = err;
+  release_slot(S, r);
+  S->n_done++;
+  if (status == CWENO_REQ_DONE) S->cell_updates += (double)r->nc * r->nsteps;
+  S->cv.notify_all();
+}
+
 void scheduler_main(cweno_server* S) {
   cudaSetDevice(S->dev);
   for (;;) {
-    std::vector<Req*> finished;
+    std::vector<Req*> joining;
     {
       std::unique_lock<std::mutex> lk(S->mu);
       if (S->stop) return;
@@ -240,34 +343,78 @@ void scheduler_main(cweno_server* S) {
         S->setup_q.push_back(r);
         S->cv.notify_all();
       }
-      // completion
-      for (size_t k = 0; k < S->inflight.size();) {
-        Req* r = S->inflight[k];
-        if (cudaEventQuery(r->done) == cudaSuccess) {
-          finished.push_back(r);
-          S->inflight[k] = S->inflight.back();
-          S->inflight.pop_back();
-        } else {
-          ++k;
+      joining.swap(S->ready);
+    }
+    bool progress = !joining.empty();
+    for (Req* r : joining) {
+      if (r->nsteps == 0) {  // nothing to step: the initial state is the result
+        r->t_done = Clock::now();
+        r->Qout = r->Q0;
+        retire(S, r, CWENO_REQ_DONE, "");
+        continue;
+      }
+      std::string err;
+      Group* g = group_of(S, r, err);
+      if (!g) {
+        r->t_done = Clock::now();
+        retire(S, r, CWENO_REQ_ERROR, err);
+        continue;
+      }
+      g->members.push_back(r);
+    }
+    for (auto& gp : S->groups) {
+      Group* g = gp.get();
+      if (g->in_flight) {
+        const cudaError_t q = cudaEventQuery(g->done);
+        if (q == cudaErrorNotReady) continue;
+        g->in_flight = false;
+        progress = true;
+        if (q != cudaSuccess) {  // a failed tick fails every member of the group
+          for (Req* r : g->members) {
+            r->t_done = Clock::now();
+            retire(S, r, CWENO_REQ_ERROR, std::string("tick: ") + cudaGetErrorString(q));
+          }
+          g->members.clear();
+          g->ticking.clear();
+          g->finishing.clear();
+          continue;
+        }
+        for (Req* r : g->ticking) {
+          r->steps_done++;
+          r->solver->cur ^= 1;
+        }
+        for (Req* r : g->finishing) {
+          g->members.erase(std::find(g->members.begin(), g->members.end(), r));
+          r->t_done = Clock::now();
+          r->Qout.assign(r->hout, r->hout + r->nc * r->nvars);
+          const int st = *r->hstatus;
+          retire(S, r, st ? CWENO_REQ_ERROR : CWENO_REQ_DONE,
+                 "the solve produced NaN or non-positive density / pressure");
+        }
+        {
+          std::lock_guard<std::mutex> lk(S->mu);
+          S->ticks++;
+          S->member_steps += g->ticking.size();
+        }
+        g->ticking.clear();
+        g->finishing.clear();
+      }
+      if (!g->in_flight && !g->members.empty()) {
+        const cudaError_t e = launch_tick(g);
+        progress = true;
+        if (e != cudaSuccess) {  // the whole group fails
+          for (Req* r : g->members) {
+            r->t_done = Clock::now();
+            retire(S, r, CWENO_REQ_ERROR, std::string("tick launch: ") + cudaGetErrorString(e));
+          }
+          g->members.clear();
+          g->in_flight = false;
         }
       }
     }
-    for (Req* r : finished) {
-      r->t_done = Clock::now();
-      r->Qout.assign(r->hout, r->hout + r->nc * r->nvars);
-      int st = *r->hstatus;
-      teardown(S, r);
-      std::lock_guard<std::mutex> lk(S->mu);
-      r->status = st ? CWENO_REQ_ERROR : CWENO_REQ_DONE;
-      if (st) r->err = "the solve produced NaN or non-positive density / pressure";
-      release_slot(S, r);
-      S->n_done++;
-      S->cell_updates += (double)r->nc * r->nsteps;
-      S->cv.notify_all();
-    }
-    if (finished.empty()) {
+    if (!progress) {
       std::unique_lock<std::mutex> lk(S->mu);
-      S->cv.wait_for(lk, std::chrono::microseconds(100));
+      S->cv.wait_for(lk, std::chrono::microseconds(50));
     }
   }
 }
@@ -287,7 +434,9 @@ int serve_create(size_t mem_budget, int max_slots, int nworkers, cweno_server** 
     mem_budget = (size_t)(0.8 * (double)fr);
   }
   S->budget = mem_budget;
-  S->max_slots = max_slots > 0 ? max_slots : 64;
+  // a group's batch table holds at most 64 members (Ops::batch_max), and
+  // every admitted request may belong to one group
+  S->max_slots = std::min(max_slots > 0 ? max_slots : 64, 64);
   unsigned hc = std::max(1u, std::thread::hardware_concurrency());
   // measured on the serving mix (16 host cores): 8 workers 3.40 s, 16 workers
   // 3.39 s, 4 workers 4.17 s for 512 requests; each worker builds one
@@ -389,6 +538,14 @@ int serve_stats(cweno_server* S, uint64_t* submitted, uint64_t* admitted, uint64
   return CWENO_OK;
 }
 
+int serve_batch_stats(cweno_server* S, uint64_t* ticks, uint64_t* member_steps) {
+  if (!S) return cw::fail(CWENO_EINVAL, "null server");
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (ticks) *ticks = S->ticks;
+  if (member_steps) *member_steps = S->member_steps;
+  return CWENO_OK;
+}
+
 void serve_destroy(cweno_server* S) {
   if (!S) return;
   {
@@ -399,6 +556,15 @@ void serve_destroy(cweno_server* S) {
   for (auto& t : S->workers) t.join();
   if (S->sched.joinable()) S->sched.join();
   cudaSetDevice(S->dev);
+  for (auto& g : S->groups) {
+    cudaStreamSynchronize(g->stream);
+    if (g->graph) cudaGraphExecDestroy(g->graph);
+    if (g->dtab) cudaFree(g->dtab);
+    if (g->htab) cudaFreeHost(g->htab);
+    if (g->done) cudaEventDestroy(g->done);
+    if (g->stream) cudaStreamDestroy(g->stream);
+  }
+  S->groups.clear();
   for (auto& kv : S->all) {
     Req* r = kv.second;
     if (r->slot >= 0) cudaStreamSynchronize(S->streams[r->slot]);

@@ -133,3 +133,35 @@ def test_zero_step_and_fifth_order_requests(cw, wl):
     s.run(10)
     s.sync()
     assert np.array_equal(s.get_state(), Qb)
+
+
+def test_mixed_orders_submitted_mid_run_are_batched_and_equal_alone(cw, wl):
+    """Requests of three orders, half submitted while the first half is
+    already stepping: every result equals the same solve run alone through
+    the solver API, bit for bit, and the steps were packed (each batched
+    launch sequence advanced several requests on average)."""
+    first = mix(wl, nreq=8, seed=11)
+    second = mix(wl, nreq=8, seed=12)
+    srv = cw.Server(max_slots=16)
+    ids = [srv.submit(m, Q, order, 0.5, 30) for m, Q, order in first]
+    t0 = time.perf_counter()
+    while srv.stats()["ticks"] == 0 and time.perf_counter() - t0 < 120:
+        time.sleep(0.002)
+    assert srv.stats()["ticks"] > 0
+    ids += [srv.submit(m, Q, order, 0.5, 20) for m, Q, order in second]
+    srv.drain(300)
+    got = []
+    for rid in ids:
+        st, Q, _ = srv.poll(rid)
+        assert st == cw.REQ_DONE, srv.errors
+        got.append(Q)
+    stats = srv.stats()
+    srv.close()
+    assert stats["member_steps"] == 8 * 30 + 8 * 20
+    assert stats["member_steps"] >= 2 * stats["ticks"]
+    for (m, Q0, order), steps, Qs in zip(first + second, [30] * 8 + [20] * 8, got):
+        s = cw.Solver(cw.Mesh.from_workload(m), order, cw.EULER, cw.FP32_MIXED, cfl=0.5)
+        s.set_state(Q0)
+        s.run(steps)
+        s.sync()
+        assert np.array_equal(s.get_state(), Qs)
