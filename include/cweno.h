@@ -142,6 +142,11 @@ int cweno_mesh_info(const cweno_mesh* m, int64_t* ncells, int64_t* nfaces, int64
  * (Sec. 2.1 cone rule), -1 where a sector is dropped.  `order` 2..5 in
  * 2D, 2..4 in 3D.  Errors as cweno_setup. */
 int cweno_mesh_stencils(const cweno_mesh* m, int order, int32_t* S0, int32_t* sec);
+/* Diagnostic: the stencils a solver actually uses (found on the device by
+ * cweno_setup, or by the host search when a stencil outgrows the device
+ * search's capacity), in the layout and caller ids of cweno_mesh_stencils.
+ * S0: nc x n_e, sec: nc x (d+1) x d, host.  Synchronous. */
+int cweno_solver_stencils(cweno_solver* s, int32_t* S0, int32_t* sec);
 
 /* Current vertex positions, nv x dim FP64 in the caller's vertex order
  * (they move under CWENO_MOTION_LAGRANGE; otherwise the mesh's own).
@@ -312,8 +317,8 @@ enum { CWENO_REQ_QUEUED = 0, CWENO_REQ_RUNNING = 1, CWENO_REQ_DONE = 2, CWENO_RE
  * (0 -> 80% of free memory); max_slots: concurrently admitted requests, each
  * with its own CUDA stream for its setup (<= 0 or > 64 -> 64, the capacity of
  * a group's batch table); nworkers: host threads preparing
- * admitted requests (mesh and stencils on the host, least-squares inverses
- * on the device; <= 0 -> half the host cores).  Admission is first come,
+ * admitted requests (mesh on the host; stencils, sectors and least-squares
+ * inverses on the device; <= 0 -> one per host core).  Admission is first come,
  * first served. */
 int serve_create(size_t mem_budget, int max_slots, int nworkers, cweno_server** out);
 /* Copies the request; returns its id.  EBUSY if its footprint exceeds the

@@ -58,6 +58,7 @@ SIGNATURES = [
     ("cweno_mesh_destroy", None, [_P]),
     ("cweno_mesh_info", _I, [_P, _I64P, _I64P, _I64P]),
     ("cweno_mesh_stencils", _I, [_P, _I, _I32P, _I32P]),
+    ("cweno_solver_stencils", _I, [_P, _I32P, _I32P]),
     ("cweno_setup", _I, [_P, _I, _I, _I, C.POINTER(cweno_params), _P, C.POINTER(_P)]),
     ("cweno_solver_destroy", None, [_P]),
     ("cweno_solver_info", _I, [_P, _IP, _IP, _IP, _IP, _I64P, _I64P]),
@@ -263,6 +264,14 @@ class Solver:
         b = C.c_size_t()
         _check(lib().cweno_solver_footprint(self.h, C.byref(b)))
         return b.value
+
+    def stencils(self):
+        """(S0 nc x n_e, sec nc x (d+1) x d): the stencils this solver uses."""
+        S0 = np.zeros((self.nc, self.ne), dtype=np.int32)
+        d = self.mesh.dim
+        sec = np.zeros((self.nc, d + 1, d), dtype=np.int32)
+        _check(lib().cweno_solver_stencils(self.h, S0.ctypes.data_as(_I32P), sec.ctypes.data_as(_I32P)))
+        return S0, sec
 
     def set_state(self, Q):
         if not (hasattr(Q, "data_ptr") and getattr(Q, "is_cuda", False)):

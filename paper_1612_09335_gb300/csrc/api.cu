@@ -205,6 +205,28 @@ int cweno_mesh_stencils(const cweno_mesh* mesh, int order, int32_t* S0, int32_t*
   return CWENO_OK;
 }
 
+int cweno_solver_stencils(cweno_solver* s, int32_t* S0, int32_t* sec) {
+  if (!s || !S0 || !sec) return fail(CWENO_EINVAL, "null argument");
+  CK(cudaSetDevice(s->dev));
+  const int64_t N = s->nc;
+  const int ne = s->re->ne, d = s->dim, nvx = d + 1;
+  std::vector<int32_t> st((size_t)N * (ne - 1)), sc((size_t)N * nvx * d), perm(N);
+  CK(cudaMemcpyAsync(st.data(), s->ds.sten, sizeof(int32_t) * st.size(), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(sc.data(), s->ds.sec, sizeof(int32_t) * sc.size(), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(perm.data(), s->ds.perm, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  for (int64_t i = 0; i < N; ++i) {  // SoA, internal order -> caller's cells
+    const int64_t u = perm[i];
+    S0[u * ne] = (int32_t)u;
+    for (int k = 0; k < ne - 1; ++k) S0[u * ne + 1 + k] = perm[st[(size_t)k * N + i]];
+    for (int q = 0; q < nvx * d; ++q) {
+      const int32_t c = sc[(size_t)q * N + i];
+      sec[u * nvx * d + q] = c < 0 ? -1 : perm[c];
+    }
+  }
+  return CWENO_OK;
+}
+
 void cweno_solver_destroy(cweno_solver* s) {
   if (!s) return;
   int cur = -1;
@@ -282,11 +304,8 @@ int cweno_setup(const cweno_mesh* mesh, int order, int pde, int precision, const
   else if (pde == CWENO_EULER && m.d == 3) s->ops = make_ops_euler3(M, precision == CWENO_FP32_MIXED, re);
   else s->ops = make_ops_mhd2(M, precision == CWENO_FP32_MIXED, re);
   if (!s->ops) return fail(CWENO_EINVAL, "configuration not built");
-  CellSetup cs;
   std::string err;
-  int nth = (int)std::max(1u, std::thread::hardware_concurrency());
-  int rc = build_cell_setup(m, re, cs, err, nth, false);  // R on the device below
-  if (rc) return fail(rc, err);
+  int rc = CWENO_OK;
   {
     // keep freed blocks in the device's default pool for reuse (serving)
     static std::mutex mu;
@@ -328,31 +347,61 @@ int cweno_setup(const cweno_mesh* mesh, int order, int pde, int precision, const
   }
   if ((rc = upload(s.get(), m.perm, (const void**)&ds.perm))) return rc;
   if ((rc = upload(s.get(), m.iperm, (const void**)&ds.iperm))) return rc;
-  if ((rc = upload(s.get(), soa_i(cs.sten, N, re.ne - 1), (const void**)&ds.sten))) return rc;
   {
-    // central stencil ids four per vector, the spare slots of the last one
-    // holding the cell itself (layout.h)
+    // Per-cell reconstruction data: stencils, sectors, inverse Jacobians and
+    // sector inverses by the device search, then the least-squares inverses
+    // R_i; the host search where the device one runs out of its per-thread
+    // capacity.  Buffers in the kernels' layouts (layout.h, SoA).
     const int ne1 = re.ne - 1, nsv = cw::sten_vectors(ne1);
-    std::vector<int32_t> s4((size_t)nsv * N * 4);
-    for (int64_t i = 0; i < N; ++i)
-      for (int r = 0; r < nsv * 4; ++r)
-        s4[((size_t)(r / 4) * N + i) * 4 + r % 4] = r < ne1 ? cs.sten[(size_t)i * ne1 + r] : (int32_t)i;
-    if ((rc = upload(s.get(), s4, (const void**)&ds.sten4))) return rc;
-  }
-  {
-    // R_i in 16-byte vectors (layout.h); the padding of the last vector is zero
+    void *bs = nullptr, *bs4 = nullptr, *bsec = nullptr, *bB = nullptr, *bns = nullptr, *bJ = nullptr, *bR = nullptr;
     const int vw = (int)(16 / es);
-    const size_t rb = es * (size_t)N * vw * cw::r_vectors(re.ne - 1, re.Mc - 1, vw);
-    if ((rc = dev_alloc(s.get(), &p, rb))) return rc;
-    CK(cudaMemsetAsync(p, 0, rb, s->stream));
+    const size_t rb = es * (size_t)N * vw * cw::r_vectors(ne1, re.Mc - 1, vw);
+    if ((rc = dev_alloc(s.get(), &bs, sizeof(int32_t) * N * ne1))) return rc;
+    if ((rc = dev_alloc(s.get(), &bs4, sizeof(int32_t) * N * nsv * 4))) return rc;
+    if ((rc = dev_alloc(s.get(), &bsec, sizeof(int32_t) * N * nvx * d))) return rc;
+    if ((rc = dev_alloc(s.get(), &bB, es * N * nvx * d * d))) return rc;
+    if ((rc = dev_alloc(s.get(), &bns, N))) return rc;
+    if ((rc = dev_alloc(s.get(), &bJ, es * N * d * d))) return rc;
+    if ((rc = dev_alloc(s.get(), &bR, rb))) return rc;
+    CK(cudaMemsetAsync(bsec, 0xff, sizeof(int32_t) * N * nvx * d, s->stream));
+    CK(cudaMemsetAsync(bB, 0, es * N * nvx * d * d, s->stream));
+    CK(cudaMemsetAsync(bns, 0, N, s->stream));
+    CK(cudaMemsetAsync(bR, 0, rb, s->stream));  // the padding of the last R vector is zero
+    ds.sten = (const int32_t*)bs;
+    ds.sten4 = (const int32_t*)bs4;
+    ds.sec = (const int32_t*)bsec;
+    ds.Binv = bB;
+    ds.nsec = (const uint8_t*)bns;
+    ds.Jinv = bJ;
+    ds.R = bR;
+    rc = cell_setup_device(m, re, precision == CWENO_FP32_MIXED, s->stream, (int32_t*)bs, (int32_t*)bs4,
+                           (int32_t*)bsec, bB, (uint8_t*)bns, bJ, bR, err);
+    if (rc == kCellSetupOnHost) {
+      CellSetup cs;
+      const int nth = cw::g_setup_threads > 0 ? cw::g_setup_threads : (int)std::max(1u, std::thread::hardware_concurrency());
+      if ((rc = build_cell_setup(m, re, cs, err, nth, false))) return fail(rc, err);
+      std::vector<int32_t> s4((size_t)nsv * N * 4);
+      for (int64_t i = 0; i < N; ++i)
+        for (int r = 0; r < nsv * 4; ++r)
+          s4[((size_t)(r / 4) * N + i) * 4 + r % 4] = r < ne1 ? cs.sten[(size_t)i * ne1 + r] : (int32_t)i;
+      std::vector<int32_t> st = soa_i(cs.sten, N, ne1), sc = soa_i(cs.sec, N, nvx * d);
+      CK(cudaMemcpyAsync(bs, st.data(), sizeof(int32_t) * st.size(), cudaMemcpyHostToDevice, s->stream));
+      CK(cudaMemcpyAsync(bs4, s4.data(), sizeof(int32_t) * s4.size(), cudaMemcpyHostToDevice, s->stream));
+      CK(cudaMemcpyAsync(bsec, sc.data(), sizeof(int32_t) * sc.size(), cudaMemcpyHostToDevice, s->stream));
+      CK(cudaMemcpyAsync(bns, cs.nsec.data(), N, cudaMemcpyHostToDevice, s->stream));
+      if (precision == CWENO_FP32_MIXED) {
+        std::vector<float> b = soa<float>(cs.Binv, N, nvx * d * d), j = soa<float>(cs.Jinv, N, d * d);
+        CK(cudaMemcpyAsync(bB, b.data(), sizeof(float) * b.size(), cudaMemcpyHostToDevice, s->stream));
+        CK(cudaMemcpyAsync(bJ, j.data(), sizeof(float) * j.size(), cudaMemcpyHostToDevice, s->stream));
+      } else {
+        std::vector<double> b = soa<double>(cs.Binv, N, nvx * d * d), j = soa<double>(cs.Jinv, N, d * d);
+        CK(cudaMemcpyAsync(bB, b.data(), sizeof(double) * b.size(), cudaMemcpyHostToDevice, s->stream));
+        CK(cudaMemcpyAsync(bJ, j.data(), sizeof(double) * j.size(), cudaMemcpyHostToDevice, s->stream));
+      }
+      rc = lsq_setup_device(m, re, (const int32_t*)bs, bR, precision == CWENO_FP32_MIXED, s->stream, err);
+    }
+    if (rc) return fail(rc, err);
   }
-  ds.R = p;
-  if ((rc = lsq_setup_device(m, re, ds.sten, p, precision == CWENO_FP32_MIXED, s->stream, err)))
-    return fail(rc, err);
-  if ((rc = upload(s.get(), soa_i(cs.sec, N, nvx * d), (const void**)&ds.sec))) return rc;
-  if ((rc = upload_real(s.get(), cs.Binv, N, nvx * d * d, &ds.Binv))) return rc;
-  if ((rc = upload(s.get(), cs.nsec, (const void**)&ds.nsec))) return rc;
-  if ((rc = upload_real(s.get(), cs.Jinv, N, d * d, &ds.Jinv))) return rc;
   if ((rc = dev_alloc(s.get(), &p, es * N * nv * re.L))) return rc;
   ds.qhat = p;
   if ((rc = upload(s.get(), m.fL, (const void**)&ds.fL))) return rc;

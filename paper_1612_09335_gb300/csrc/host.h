@@ -57,6 +57,14 @@ int build_cell_setup(const MeshHost& m, const RefElem& re, CellSetup& cs, std::s
 // FP64), stream a cudaStream_t.  Synchronous on that stream.
 int lsq_setup_device(const MeshHost& m, const RefElem& re, const int32_t* d_sten, void* d_R, int fp32,
                      void* stream, std::string& err);
+// Stencils, sectors, inverse Jacobians, sector inverses and R_i of every
+// cell on the device (setup_gpu.cu), into caller-allocated buffers in the
+// kernels' layouts; returns kCellSetupOnHost when a stencil search outgrows
+// the device kernel's per-thread capacity (the caller then runs the host
+// search), else 0 or a CWENO_E* code with a message in err.
+constexpr int kCellSetupOnHost = 1;
+int cell_setup_device(const MeshHost& m, const RefElem& re, int fp32, void* stream, int32_t* d_sten, int32_t* d_sten4,
+                      int32_t* d_sec, void* d_Binv, uint8_t* d_nsec, void* d_Jinv, void* d_R, std::string& err);
 
 // Moving meshes (ale.cu, two dimensions, FP64): rebuild on the device
 // the least-squares pseudo-inverses R and the sector inverses Binv of every

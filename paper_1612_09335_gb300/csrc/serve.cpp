@@ -438,10 +438,10 @@ int serve_create(size_t mem_budget, int max_slots, int nworkers, cweno_server** 
   // every admitted request may belong to one group
   S->max_slots = std::min(max_slots > 0 ? max_slots : 64, 64);
   unsigned hc = std::max(1u, std::thread::hardware_concurrency());
-  // measured on the serving mix (16 host cores): 8 workers 3.40 s, 16 workers
-  // 3.39 s, 4 workers 4.17 s for 512 requests; each worker builds one
-  // request's mesh (single-threaded) while the others compute
-  S->nworkers = nworkers > 0 ? nworkers : (int)std::max(2u, hc / 2);
+  // one setup worker per host core by default: a worker builds one request's
+  // mesh (host, single-threaded) and runs its stencil search and
+  // least-squares setup on the device, so workers scale with the cores
+  S->nworkers = nworkers > 0 ? nworkers : (int)std::max(2u, hc);
   S->threads_per_setup = (int)std::max(1u, hc / (unsigned)S->nworkers);
   S->streams.resize(S->max_slots);
   for (int k = 0; k < S->max_slots; ++k) {

@@ -443,3 +443,31 @@ def test_fp32_pair_split_of_the_state(cw, wl):
             g = float(got.flat[0])
             assert abs(g - q[v]) <= 2.0 ** -46 * abs(q[v]) + 1e-44, (q[v], g)
         s.close()
+
+
+@pytest.mark.parametrize("kind,orders", [("tri_periodic", (2, 3, 4, 5)), ("tri_bounded", (2, 3, 4, 5)),
+                                         ("tri_ties", (3, 4)), ("tet_periodic", (2, 3, 4)),
+                                         ("tet_bounded", (2, 3))])
+def test_device_stencil_search_equals_host_search(cw, wl, kind, orders):
+    """cweno_setup finds the central stencils and sectors on the device; they
+    must be the host search's (the rule the oracle's stencils are pinned to)
+    cell for cell: jittered and unjittered (tie-breaking) meshes, periodic and
+    bounded (dropped sectors), triangles and tetrahedra."""
+    if kind == "tri_periodic":
+        mesh = wl.tri_mesh(23, jitter=0.2, seed=17)
+    elif kind == "tri_bounded":
+        mesh = wl.tri_mesh(19, lo=(-1, -1), hi=(1, 1), periodic=False, jitter=0.2, seed=18)
+    elif kind == "tri_ties":
+        mesh = wl.tri_mesh(16, jitter=0.0)
+    elif kind == "tet_periodic":
+        mesh = wl.tet_mesh(6, jitter=0.15, seed=19)
+    else:
+        mesh = wl.tet_mesh(6, lo=(-1, -1, -1), hi=(1, 1, 1), periodic=False, jitter=0.12, seed=20)
+    m = cw.Mesh.from_workload(mesh)
+    for order in orders:
+        S0h, sech = m.stencils(order)
+        s = cw.Solver(m, order, cw.EULER, cw.FP32_MIXED)
+        S0d, secd = s.stencils()
+        s.close()
+        assert np.array_equal(S0h, S0d), (kind, order)
+        assert np.array_equal(sech, secd), (kind, order)
