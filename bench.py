@@ -443,13 +443,20 @@ def serving_run(cw, nreq, steps=50, seed=42, max_slots=64, seq_sample=16):
         ids.append(srv.submit(m, Q, r["order"], 0.5, steps))
     srv.drain(3600)
     t_open = time.perf_counter() - t0
-    lat = []
-    for i in ids:
+    lat, lat_nc = [], []
+    for i, (m, _) in zip(ids, inputs):
         st, _, l = srv.poll(i)
         if st == cw.REQ_DONE:
             lat.append(l)
+            lat_nc.append(m.nc)
     stats = srv.stats()
     srv.close()
+    bands = {}
+    for lo, hi, key in ((0, 16384, "below_16k_cells"), (16384, 1 << 62, "from_16k_cells")):
+        sel = [l for l, n in zip(lat, lat_nc) if lo <= n < hi]
+        if sel:
+            bands[key] = {"requests": len(sel), "p50_latency_s": float(np.percentile(sel, 50)),
+                          "p99_latency_s": float(np.percentile(sel, 99))}
     # sequential FP64 per-solve baseline on a sample of the same requests
     k = min(seq_sample, nreq)
     seq_cells = 0
@@ -469,6 +476,8 @@ def serving_run(cw, nreq, steps=50, seed=42, max_slots=64, seq_sample=16):
             "p50_latency_s": float(np.percentile(lat, 50)) if len(lat) else None,
             "p99_latency_s": float(np.percentile(lat, 99)) if len(lat) else None,
             "open_cell_updates_per_s": stats["cell_updates"] / t_open, "completed_open": len(lat),
+            "latency_by_size": bands,
+            "member_steps_per_tick": stats["member_steps"] / max(1, stats["ticks"]),
             "peak_running": int(max(peak1, stats["peak_running"])), "max_slots": max_slots,
             "sequential_fp64_cell_updates_per_s": seq_cells * steps / t_seq,
             "sequential_sample_requests": k,

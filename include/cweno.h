@@ -287,7 +287,9 @@ int cweno_stable_dt_noalloc(int dim, int pde, int64_t ncells, const double* Q, c
  * The server admits requests while their measured device footprint fits the
  * memory budget and a slot is free, sets each one up on a host worker, and
  * groups the admitted requests by configuration (dimension, order, PDE,
- * precision, flux).  Each group advances all of its members by one time step
+ * precision, flux) and size class (cells below 4096, 16384, 65536, above:
+ * a tick lasts as long as its members' steps together, so small requests do
+ * not wait for large ones).  Each group advances all of its members by one time step
  * per tick: one captured CUDA graph of batched kernels over a table of the
  * members (the reconstruction + predictor, flux and update of every member's
  * cells and faces in the same three launches), replayed every tick with the

@@ -7,7 +7,9 @@
 // slot's stream) -> the request joins the group of its configuration
 // (dimension, order, PDE, precision, flux).
 //
-// Each group advances all of its members by one time step per tick: one
+// Groups are per configuration and size class (a tick lasts as long as its
+// members' steps together).  Each group advances all of its members by one
+// time step per tick: one
 // captured CUDA graph (the group's batch table copied from pinned host
 // memory, then the batched reconstruction + predictor, flux and update
 // kernels over all members' cells and faces), replayed every tick on the
@@ -69,7 +71,7 @@ struct Req {
 // One configuration's batch: its members, the pinned and device images of
 // the batch table, the captured tick graph and the tick in flight.
 struct Group {
-  std::tuple<int, int, int, int, int> key;  // dim, order, pde, precision, flux
+  std::tuple<int, int, int, int, int, int> key;  // dim, order, pde, precision, flux, size class
   int flux = 0;
   std::unique_ptr<cw::Ops> ops;
   cudaStream_t stream = nullptr;
@@ -98,13 +100,14 @@ struct cweno_server {
   std::deque<Req*> queue;    // submitted, waiting for admission
   std::deque<Req*> setup_q;  // admitted, waiting for a setup worker
   std::vector<Req*> ready;   // set up, waiting to join their group
+  std::deque<std::pair<Req*, int>> retire_q;  // finished ticks: (request, its status word or -1 on failure)
   std::map<uint64_t, Req*> all;
   std::vector<std::unique_ptr<Group>> groups;  // scheduler thread only
   int active = 0;                              // admitted and not retired
   uint64_t next_id = 1, n_sub = 0, n_adm = 0, n_done = 0, peak = 0, ticks = 0, member_steps = 0;
   double cell_updates = 0.0;
   bool stop = false;
-  std::thread sched;
+  std::thread sched, retirer;
   std::vector<std::thread> workers;
   // pinned host buffers are pooled: freeing pinned memory can synchronise the
   // whole device, which would stall the other requests
@@ -225,10 +228,21 @@ void worker_main(cweno_server* S) {
   }
 }
 
-// The group of r's configuration, created (with its tick graph) on first use.
+// Size class of a request: cells below 4096, 16384, 65536 or above.  A tick
+// lasts as long as its group's members take together, so requests of very
+// different sizes tick in different groups (concurrently): a small request
+// does not wait for the steps of large ones.
+int size_class(int64_t nc) {
+  int c = 0;
+  for (int64_t lim = 4096; c < 3 && nc >= lim; lim *= 4) ++c;
+  return c;
+}
+
+// The group of r's configuration and size class, created (with its tick
+// graph) on first use.
 Group* group_of(cweno_server* S, Req* r, std::string& err) {
   const int flux = r->solver->prm.flux;
-  auto key = std::make_tuple(r->dim, r->order, r->pde, r->prec, flux);
+  auto key = std::make_tuple(r->dim, r->order, r->pde, r->prec, flux, size_class(r->nc));
   for (auto& g : S->groups)
     if (g->key == key) return g.get();
   std::unique_ptr<Group> g(new Group());
@@ -323,6 +337,31 @@ void retire(cweno_server* S, Req* r, int status, const std::string& err) {
   S->cv.notify_all();
 }
 
+// Retirement off the scheduler's path (copying a final state out of pinned
+// memory and freeing a solver take milliseconds, during which no group
+// would get its next tick): results, teardown, slot release.
+void retirer_main(cweno_server* S) {
+  cudaSetDevice(S->dev);
+  for (;;) {
+    std::pair<Req*, int> job;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->cv.wait(lk, [&] { return S->stop || !S->retire_q.empty(); });
+      if (S->retire_q.empty()) return;  // stop with nothing left
+      job = S->retire_q.front();
+      S->retire_q.pop_front();
+    }
+    Req* r = job.first;
+    if (job.second < 0) {
+      retire(S, r, CWENO_REQ_ERROR, r->err);
+      continue;
+    }
+    r->Qout.assign(r->hout, r->hout + r->nc * r->nvars);
+    retire(S, r, job.second ? CWENO_REQ_ERROR : CWENO_REQ_DONE,
+           "the solve produced NaN or non-positive density / pressure");
+  }
+}
+
 void scheduler_main(cweno_server* S) {
   cudaSetDevice(S->dev);
   for (;;) {
@@ -386,10 +425,9 @@ void scheduler_main(cweno_server* S) {
         for (Req* r : g->finishing) {
           g->members.erase(std::find(g->members.begin(), g->members.end(), r));
           r->t_done = Clock::now();
-          r->Qout.assign(r->hout, r->hout + r->nc * r->nvars);
-          const int st = *r->hstatus;
-          retire(S, r, st ? CWENO_REQ_ERROR : CWENO_REQ_DONE,
-                 "the solve produced NaN or non-positive density / pressure");
+          std::lock_guard<std::mutex> lk(S->mu);
+          S->retire_q.push_back({r, *r->hstatus});
+          S->cv.notify_all();
         }
         {
           std::lock_guard<std::mutex> lk(S->mu);
@@ -452,6 +490,7 @@ int serve_create(size_t mem_budget, int max_slots, int nworkers, cweno_server** 
   cweno_server* raw = S.get();
   for (int k = 0; k < S->nworkers; ++k) S->workers.emplace_back(worker_main, raw);
   S->sched = std::thread(scheduler_main, raw);
+  S->retirer = std::thread(retirer_main, raw);
   *out = S.release();
   return CWENO_OK;
 }
@@ -555,6 +594,7 @@ void serve_destroy(cweno_server* S) {
   }
   for (auto& t : S->workers) t.join();
   if (S->sched.joinable()) S->sched.join();
+  if (S->retirer.joinable()) S->retirer.join();
   cudaSetDevice(S->dev);
   for (auto& g : S->groups) {
     cudaStreamSynchronize(g->stream);
