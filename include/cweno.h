@@ -101,11 +101,15 @@ typedef struct {
                           signal speed of the two sides' space-time face
                           averages */
   int mesh_motion;     /* CWENO_MOTION_FIXED (default), _LAGRANGE or _STILL.
-                          Moving meshes: dim 2, Euler, FP64, order 2..4,
-                          Rusanov flux (EINVAL otherwise); the stencils are
-                          chosen on the initial mesh and kept (the topology
-                          never changes), their least-squares and sector
-                          matrices are rebuilt on the device every step */
+                          Moving meshes: dim 2, Euler, order 2..4, Rusanov
+                          flux, FP64 or FP32-mixed (EINVAL otherwise); the
+                          stencils are chosen on the initial mesh and kept
+                          (the topology never changes), their least-squares
+                          and sector matrices are rebuilt on the device every
+                          step in FP64.  FP32-mixed: predictor and face
+                          traces in FP32 on deviations from the cell
+                          averages, the averages' part of the face
+                          integrals, nodal solver and update in FP64 */
 } cweno_params;
 
 /* Fill *p with the paper's defaults for dimension `dim` and `pde`. */

@@ -1,6 +1,7 @@
 // Moving meshes: the direct ALE ADER-CWENO step (Secs. 2.2-2.4) on 2D
-// triangle meshes, Euler equations, FP64, Rusanov flux with the ALE
-// Jacobian.  Mesh velocity V = v (the local fluid velocity, the choice of the
+// triangle meshes, Euler equations, FP64 or FP32-mixed (k_ale_pred32,
+// k_ale_flux32: FP32 deviations, FP64 least squares, averages' face part,
+// nodal solver and update), Rusanov flux with the ALE Jacobian.  Mesh velocity V = v (the local fluid velocity, the choice of the
 // paper's moving-mesh tests) or V = 0 (the same machinery on a mesh that does
 // not move).  One step:
 //   k_ale_geom      cell geometry of the current vertices (unwrapped
@@ -38,23 +39,60 @@ namespace cw {
 
 constexpr int kLmax = 20, kL0max = 10, kL1max = 10, kNQ = 4;
 
-// Reference tables of one M (2D), passed as a kernel parameter.
-struct AleTab {
+// Reference tables of one M (2D) in the arithmetic type T, passed as a
+// kernel parameter.
+template <typename T>
+struct AleTabT {
   // d theta_l / d xi_e at node n, nonzero entries only (about a third of
   // them are nonzero): for (e, n) the first nnz[e][n] pairs (col, val)
-  double val[2][kLmax][kLmax];
+  T val[2][kLmax][kLmax];
   uint8_t col[2][kLmax][kLmax];
   int nnz[2][kLmax];
   int nnz0[2][kLmax];  // of which on tau = 0 nodes (listed first)
-  double Gal[kL1max][kLmax];    // (K_tau^1)^-1 M^1
-  double C0[kL1max][kL0max];    // theta_n(xi_k, 0): constant extension in time
-  double Wv[3][kLmax];          // int_0^1 theta_l(vertex v, tau) dtau
-  double node[kLmax][3];        // xi, eta, tau
-  double chi[kNQ], wq[kNQ], wt[kNQ], tq[kNQ];
-  double gamma;
+  T Gal[kL1max][kLmax];    // (K_tau^1)^-1 M^1
+  T C0[kL1max][kL0max];    // theta_n(xi_k, 0): constant extension in time
+  T Wv[3][kLmax];          // int_0^1 theta_l(vertex v, tau) dtau
+  T node[kLmax][3];        // xi, eta, tau
+  T chi[kNQ], wq[kNQ], wt[kNQ], tq[kNQ];
+  T gamma;
   int mode;  // CWENO_MOTION_LAGRANGE or CWENO_MOTION_STILL
   int pos;   // positivity switch (fallbacks as on fixed meshes)
 };
+using AleTab = AleTabT<double>;
+using AleTab32 = AleTabT<float>;
+
+template <typename T>
+AleTabT<T> ale_tab_cast(const AleTab& t) {
+  AleTabT<T> o;
+  std::memset(&o, 0, sizeof(o));
+  for (int e = 0; e < 2; ++e)
+    for (int n = 0; n < kLmax; ++n) {
+      for (int l = 0; l < kLmax; ++l) {
+        o.val[e][n][l] = (T)t.val[e][n][l];
+        o.col[e][n][l] = t.col[e][n][l];
+      }
+      o.nnz[e][n] = t.nnz[e][n];
+      o.nnz0[e][n] = t.nnz0[e][n];
+    }
+  for (int k = 0; k < kL1max; ++k) {
+    for (int l = 0; l < kLmax; ++l) o.Gal[k][l] = (T)t.Gal[k][l];
+    for (int n = 0; n < kL0max; ++n) o.C0[k][n] = (T)t.C0[k][n];
+  }
+  for (int v = 0; v < 3; ++v)
+    for (int l = 0; l < kLmax; ++l) o.Wv[v][l] = (T)t.Wv[v][l];
+  for (int l = 0; l < kLmax; ++l)
+    for (int a = 0; a < 3; ++a) o.node[l][a] = (T)t.node[l][a];
+  for (int q = 0; q < kNQ; ++q) {
+    o.chi[q] = (T)t.chi[q];
+    o.wq[q] = (T)t.wq[q];
+    o.wt[q] = (T)t.wt[q];
+    o.tq[q] = (T)t.tq[q];
+  }
+  o.gamma = (T)t.gamma;
+  o.mode = t.mode;
+  o.pos = t.pos;
+  return o;
+}
 
 namespace {
 
@@ -260,6 +298,178 @@ __global__ void __launch_bounds__(128) k_ale_pred(const __grid_constant__ AleTab
   }
 }
 
+// FP32-mixed form of k_ale_pred: the same iteration in single precision on
+// deviations — of the state from the cell average Q_i, of the node positions
+// from the cell's first vertex, of the nodal fluxes from the flux of the
+// cell average (rounded once to FP32) — so that the xi-derivatives of a
+// constant state are exactly zero and positions keep FP32 accuracy relative
+// to the cell.  The mesh velocity uses the absolute nodal state.  Writes the
+// state deviations q_hat - Q_i (N x L x 4, FP32) and, per vertex of the
+// cell, (mu V_kj, mu) in FP64.
+__device__ __forceinline__ void ale_flux32(const float* q, float gamma, int mode, float F[2][4], float V[2]) {
+  const float ir = 1.0f / q[0], u = q[1] * ir, vv = q[2] * ir;
+  const float p = (gamma - 1.0f) * (q[3] - 0.5f * (q[1] * u + q[2] * vv));
+  F[0][0] = q[1];
+  F[0][1] = q[1] * u + p;
+  F[0][2] = q[2] * u;
+  F[0][3] = u * (q[3] + p);
+  F[1][0] = q[2];
+  F[1][1] = q[1] * vv;
+  F[1][2] = q[2] * vv + p;
+  F[1][3] = vv * (q[3] + p);
+  V[0] = mode == CWENO_MOTION_LAGRANGE ? u : 0.0f;
+  V[1] = mode == CWENO_MOTION_LAGRANGE ? vv : 0.0f;
+}
+
+__device__ __forceinline__ bool admissible32(const float* q, float g) {
+  bool fin = isfinite(q[0]) && isfinite(q[1]) && isfinite(q[2]) && isfinite(q[3]);
+  return fin && q[0] > 0.0f && (g - 1.0f) * (q[3] - 0.5f * (q[1] * q[1] + q[2] * q[2]) / q[0]) > 0.0f;
+}
+
+template <int M>
+__global__ void __launch_bounds__(128) k_ale_pred32(const __grid_constant__ AleTab32 t, const double* __restrict__ w,
+                                                    const double* __restrict__ Q, const double* __restrict__ X,
+                                                    const double* __restrict__ vol, int64_t N, int niter,
+                                                    double dt_fixed, double cfl, const unsigned long long* dtmin,
+                                                    float* __restrict__ qhat, double* __restrict__ vcon) {
+  constexpr int L = lcal2(M), L0 = mcal2(M), L1 = L - L0;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const float dt = (float)step_dt(dt_fixed, cfl, dtmin);
+  double Qd[4];
+  float qb[4];
+  for (int v = 0; v < 4; ++v) {
+    Qd[v] = Q[v * N + i];
+    qb[v] = (float)Qd[v];
+  }
+  float q[L][4], x[L][2];
+  for (int n = 0; n < L0; ++n)
+    for (int v = 0; v < 4; ++v) q[n][v] = (float)(w[(i * L0 + n) * 4 + v] - Qd[v]);
+  for (int k = 0; k < L1; ++k)
+    for (int v = 0; v < 4; ++v) {
+      float s = 0.0f;
+      for (int n = 0; n < L0; ++n) s += t.C0[k][n] * q[n][v];
+      q[L0 + k][v] = s;
+    }
+  const double* Xi = X + i * 9;
+  float E[2][2];  // edge vectors X1 - X0, X2 - X0
+  for (int a = 0; a < 2; ++a) {
+    E[0][a] = (float)(Xi[3 + a] - Xi[a]);
+    E[1][a] = (float)(Xi[6 + a] - Xi[a]);
+  }
+  for (int l = 0; l < L; ++l)
+    for (int a = 0; a < 2; ++a) x[l][a] = E[0][a] * t.node[l][0] + E[1][a] * t.node[l][1];
+  float Fb[2][4], Vb[2];
+  ale_flux32(qb, t.gamma, t.mode, Fb, Vb);
+  float qe[L1][4], xe[L1][2], V[L][2];
+  for (int k = 0; k < L1; ++k) {
+    for (int v = 0; v < 4; ++v) qe[k][v] = q[L0 + k][v];
+    for (int a = 0; a < 2; ++a) xe[k][a] = x[L0 + k][a];
+  }
+  auto nodal_flux = [&](const float* dq, float F[2][4], float* Vn) {
+    float qa[4];
+    for (int v = 0; v < 4; ++v) qa[v] = qb[v] + dq[v];
+    ale_flux32(qa, t.gamma, t.mode, F, Vn);
+    for (int e = 0; e < 2; ++e)
+      for (int v = 0; v < 4; ++v) F[e][v] -= Fb[e][v];
+  };
+  float c0[L][2][14];  // per node and direction: d x (2), d q (4), d F (2 x 4) over tau = 0 nodes
+  {
+    float F0[L0][2][4];
+    for (int l = 0; l < L0; ++l) nodal_flux(q[l], F0[l], V[l]);
+    for (int n = 0; n < L; ++n)
+      for (int e = 0; e < 2; ++e) {
+        float* c = c0[n][e];
+        for (int m = 0; m < 14; ++m) c[m] = 0.0f;
+        for (int j = 0; j < t.nnz0[e][n]; ++j) {
+          const int l = t.col[e][n][j];
+          const float dd = t.val[e][n][j];
+          for (int a2 = 0; a2 < 2; ++a2) c[a2] += dd * x[l][a2];
+          for (int v = 0; v < 4; ++v) {
+            c[2 + v] += dd * q[l][v];
+            c[6 + v] += dd * F0[l][0][v];
+            c[10 + v] += dd * F0[l][1][v];
+          }
+        }
+      }
+  }
+  for (int it = 0; it < niter; ++it) {
+    float F[L1][2][4];
+    for (int l = L0; l < L; ++l) nodal_flux(q[l], F[l - L0], V[l]);
+    float H[L][4];
+    for (int n = 0; n < L; ++n) {
+      float dx[2][2], dq[2][4], df[2][2][4];
+      for (int e = 0; e < 2; ++e) {
+        const float* c = c0[n][e];
+        for (int a2 = 0; a2 < 2; ++a2) dx[e][a2] = c[a2];
+        for (int v = 0; v < 4; ++v) {
+          dq[e][v] = c[2 + v];
+          df[e][0][v] = c[6 + v];
+          df[e][1][v] = c[10 + v];
+        }
+        const int cnt = t.nnz[e][n];
+        for (int j = t.nnz0[e][n]; j < cnt; ++j) {
+          const int l = t.col[e][n][j];
+          const float dd = t.val[e][n][j];
+          for (int a2 = 0; a2 < 2; ++a2) dx[e][a2] += dd * x[l][a2];
+          for (int v = 0; v < 4; ++v) {
+            dq[e][v] += dd * q[l][v];
+            df[e][0][v] += dd * F[l - L0][0][v];
+            df[e][1][v] += dd * F[l - L0][1][v];
+          }
+        }
+      }
+      const float idet = 1.0f / (dx[0][0] * dx[1][1] - dx[1][0] * dx[0][1]);
+      const float Ji[2][2] = {{dx[1][1] * idet, -dx[1][0] * idet}, {-dx[0][1] * idet, dx[0][0] * idet}};
+      float dxidt[2];
+      for (int e = 0; e < 2; ++e) dxidt[e] = -(Ji[e][0] * V[n][0] + Ji[e][1] * V[n][1]);
+      for (int v = 0; v < 4; ++v) {
+        float h = 0.0f;
+        for (int e = 0; e < 2; ++e) h += dq[e][v] * dxidt[e] + Ji[e][0] * df[e][0][v] + Ji[e][1] * df[e][1][v];
+        H[n][v] = h;
+      }
+    }
+    for (int k = 0; k < L1; ++k) {
+      for (int v = 0; v < 4; ++v) {
+        float g = 0.0f;
+        for (int l = 0; l < L; ++l) g += t.Gal[k][l] * H[l][v];
+        q[L0 + k][v] = qe[k][v] - dt * g;
+      }
+      for (int a2 = 0; a2 < 2; ++a2) {
+        float g = 0.0f;
+        for (int l = 0; l < L; ++l) g += t.Gal[k][l] * V[l][a2];
+        x[L0 + k][a2] = xe[k][a2] + dt * g;
+      }
+    }
+  }
+  if (t.pos) {
+    bool ok = true;
+    for (int l = L0; l < L; ++l) {
+      float qa[4];
+      for (int v = 0; v < 4; ++v) qa[v] = qb[v] + q[l][v];
+      ok = ok && admissible32(qa, t.gamma);
+    }
+    if (!ok)
+      for (int l = 0; l < L; ++l)
+        for (int v = 0; v < 4; ++v) q[l][v] = 0.0f;
+  }
+  for (int l = 0; l < L; ++l) {
+    for (int v = 0; v < 4; ++v) qhat[(i * L + l) * 4 + v] = q[l][v];
+    const float ir = 1.0f / (qb[0] + q[l][0]);
+    V[l][0] = t.mode == CWENO_MOTION_LAGRANGE ? (qb[1] + q[l][1]) * ir : 0.0f;
+    V[l][1] = t.mode == CWENO_MOTION_LAGRANGE ? (qb[2] + q[l][2]) * ir : 0.0f;
+  }
+  const double mu = Qd[0] * vol[i];
+  for (int k = 0; k < 3; ++k) {
+    for (int a = 0; a < 2; ++a) {
+      float s = 0.0f;
+      for (int l = 0; l < L; ++l) s += t.Wv[k][l] * V[l][a];
+      vcon[(i * 3 + k) * 3 + a] = mu * (double)s;
+    }
+    vcon[(i * 3 + k) * 3 + 2] = mu;
+  }
+}
+
 // ------------------------------------------------------------- nodal solver
 // One thread per vertex: V_k = sum mu V_kj / sum mu over the incident cells
 // (entries ent[start[g] .. start[g+1]) = cell * 3 + local vertex, in
@@ -402,6 +612,160 @@ __global__ void __launch_bounds__(128) k_ale_flux(const __grid_constant__ AleTab
   for (int v = 0; v < 4; ++v) G[v * F + f] = acc[v];
 }
 
+// FP32-mixed form of k_ale_flux.  Each side's trace is a deviation from its
+// cell average (q_hat in deviations, FP32); the flux, the mesh-motion term
+// and the dissipation of the deviations are integrated in FP32 with the
+// point normals in FP32.  The cell averages' part, 1/2 (F(Q-) + F(Q+)) . n +
+// 1/2 (Q- + Q+) n_t, is integrated exactly in FP64 once per face: the
+// space-time normal is bilinear in (chi, tau), so its integral over the
+// tensor Gauss rule is its value at (1/2, 1/2).  A constant state therefore
+// gives the FP64 face integrals of the FP64 path's geometry, and the
+// geometric conservation law closes to FP64 rounding.
+__device__ __forceinline__ void euler_xy64(const double* z, double g, double F[2][4]) {
+  const double ir = 1.0 / z[0], u = z[1] * ir, vv = z[2] * ir;
+  const double p = (g - 1.0) * (z[3] - 0.5 * (z[1] * u + z[2] * vv));
+  F[0][0] = z[1];
+  F[0][1] = z[1] * u + p;
+  F[0][2] = z[2] * u;
+  F[0][3] = u * (z[3] + p);
+  F[1][0] = z[2];
+  F[1][1] = z[1] * vv;
+  F[1][2] = z[2] * vv + p;
+  F[1][3] = vv * (z[3] + p);
+}
+
+template <int M>
+__global__ void __launch_bounds__(128) k_ale_flux32(const __grid_constant__ AleTab32 t, double gamma64,
+                                                    const float* __restrict__ ftab, const int32_t* __restrict__ fL,
+                                                    const int32_t* __restrict__ fR, const uint8_t* __restrict__ codeL,
+                                                    const uint8_t* __restrict__ codeR, const int32_t* __restrict__ gv,
+                                                    const double* __restrict__ shift, const double* __restrict__ Xv,
+                                                    const double* __restrict__ Xv1, const double* __restrict__ bary,
+                                                    const float* __restrict__ qhat, const double* __restrict__ Q,
+                                                    int64_t N, int64_t F, double dt_fixed, double cfl,
+                                                    const unsigned long long* dtmin, double* __restrict__ G) {
+  constexpr int L = lcal2(M), NQ = M + 1;
+  const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= F) return;
+  const double dt = step_dt(dt_fixed, cfl, dtmin);
+  const int64_t cl = fL[f], cr = fR[f];
+  const int kL = codeL[f], kR = cr >= 0 ? codeR[f] : 0;
+  const int lf = kL / 2;
+  int la = (lf + 1) % 3, lb = (lf + 2) % 3;
+  int64_t ga = gv[la * N + cl], gb = gv[lb * N + cl];
+  if (ga > gb) {
+    const int64_t tg = ga;
+    ga = gb;
+    gb = tg;
+    const int tl = la;
+    la = lb;
+    lb = tl;
+  }
+  FaceGeo fg;
+  for (int a = 0; a < 2; ++a) {
+    const double sa = shift[(la * 2 + a) * N + cl], sb = shift[(lb * 2 + a) * N + cl];
+    fg.A0[a] = Xv[ga * 2 + a] + sa;
+    fg.B0[a] = Xv[gb * 2 + a] + sb;
+    fg.A1[a] = Xv1[ga * 2 + a] + sa;
+    fg.B1[a] = Xv1[gb * 2 + a] + sb;
+  }
+  double n0[3], nbar[3];
+  st_normal(fg, 0.0, 0.0, dt, n0);
+  const double sgn =
+      n0[0] * (fg.A0[0] - bary[cl * 3]) + n0[1] * (fg.A0[1] - bary[cl * 3 + 1]) > 0.0 ? 1.0 : -1.0;
+  st_normal(fg, 0.5, 0.5, dt, nbar);
+  // edge and displacement vectors of the moving face in FP32 (differences in FP64)
+  float eA[2], eB[2], wA[2], wB[2];
+  for (int a = 0; a < 2; ++a) {
+    eA[a] = (float)(fg.B0[a] - fg.A0[a]);
+    eB[a] = (float)(fg.B1[a] - fg.A1[a]);
+    wA[a] = (float)(fg.A1[a] - fg.A0[a]);
+    wB[a] = (float)(fg.B1[a] - fg.B0[a]);
+  }
+  const float sg = (float)sgn, dt32 = (float)dt;
+  double QL[4], QR[4];
+  float qbL[4], qbR[4], dQ[4];
+  for (int v = 0; v < 4; ++v) {
+    QL[v] = Q[v * N + cl];
+    QR[v] = cr >= 0 ? Q[v * N + cr] : QL[v];
+    qbL[v] = (float)QL[v];
+    qbR[v] = (float)QR[v];
+    dQ[v] = (float)(QR[v] - QL[v]);
+  }
+  float FbL[2][4], FbR[2][4], Vd[2];
+  ale_flux32(qbL, t.gamma, CWENO_MOTION_FIXED, FbL, Vd);
+  ale_flux32(qbR, t.gamma, CWENO_MOTION_FIXED, FbR, Vd);
+  const float* qL = qhat + cl * L * 4;
+  const float* qR = qhat + (cr >= 0 ? cr : cl) * L * 4;
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int qp = 0; qp < NQ; ++qp)
+    for (int tt = 0; tt < NQ; ++tt) {
+      const float* bL = ftab + ((int64_t)(kL * NQ + tt) * NQ + qp) * L;
+      const float* bR = ftab + ((int64_t)(kR * NQ + tt) * NQ + qp) * L;
+      float dm[4] = {0.f, 0.f, 0.f, 0.f}, dp[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int l = 0; l < L; ++l)
+        for (int v = 0; v < 4; ++v) {
+          dm[v] += bL[l] * qL[l * 4 + v];
+          dp[v] += bR[l] * qR[l * 4 + v];
+        }
+      if (cr < 0)
+        for (int v = 0; v < 4; ++v) dp[v] = dm[v];
+      float qm[4], qq[4];
+      for (int v = 0; v < 4; ++v) {
+        qm[v] = qbL[v] + dm[v];
+        qq[v] = qbR[v] + dp[v];
+      }
+      if (t.pos) {
+        if (!admissible32(qm, t.gamma))
+          for (int v = 0; v < 4; ++v) {
+            qm[v] = qbL[v];
+            dm[v] = 0.f;
+          }
+        if (!admissible32(qq, t.gamma))
+          for (int v = 0; v < 4; ++v) {
+            qq[v] = qbR[v];
+            dp[v] = 0.f;
+          }
+      }
+      // space-time normal at (chi, tau), Eq. (detChi), in FP32
+      const float chi = t.chi[qp], tau = t.tq[tt];
+      float e[2], wv[2];
+      for (int a = 0; a < 2; ++a) {
+        e[a] = (1.0f - tau) * eA[a] + tau * eB[a];
+        wv[a] = (1.0f - chi) * wA[a] + chi * wB[a];
+      }
+      const float n[3] = {sg * e[1] * dt32, -sg * e[0] * dt32, sg * (e[0] * wv[1] - e[1] * wv[0])};
+      const float nx = sqrtf(n[0] * n[0] + n[1] * n[1]), inx = 1.0f / nx;
+      const float un[2] = {n[0] * inx, n[1] * inx};
+      const float Vn = -n[2] * inx;
+      float sm = 0.0f, dfs[4] = {0.f, 0.f, 0.f, 0.f};
+      const float* sides[2] = {qm, qq};
+      for (int s = 0; s < 2; ++s) {
+        const float* z = sides[s];
+        float Fz[2][4], Vz[2];
+        ale_flux32(z, t.gamma, CWENO_MOTION_FIXED, Fz, Vz);
+        const float ir = 1.0f / z[0], u = z[1] * ir, vv = z[2] * ir;
+        const float p = (t.gamma - 1.0f) * (z[3] - 0.5f * (z[1] * u + z[2] * vv));
+        const float c = sqrtf(fmaxf(0.0f, t.gamma * p * ir));
+        sm = fmaxf(sm, fabsf(u * un[0] + vv * un[1] - Vn) + c);
+        const float(*Fb)[4] = s == 0 ? FbL : FbR;
+        for (int v = 0; v < 4; ++v) dfs[v] += (Fz[0][v] - Fb[0][v]) * n[0] + (Fz[1][v] - Fb[1][v]) * n[1];
+      }
+      sm *= nx;
+      const float wgt = t.wq[qp] * t.wt[tt];
+      for (int v = 0; v < 4; ++v)
+        acc[v] += wgt * (0.5f * dfs[v] + 0.5f * (dm[v] + dp[v]) * n[2] - 0.5f * sm * (dQ[v] + dp[v] - dm[v]));
+    }
+  // the cell averages' part, in FP64 with the integrated normal
+  double FL[2][4], FR[2][4];
+  euler_xy64(QL, gamma64, FL);
+  euler_xy64(QR, gamma64, FR);
+  for (int a = 0; a < 3; ++a) nbar[a] *= sgn;
+  for (int v = 0; v < 4; ++v)
+    G[v * F + f] = (double)acc[v] + 0.5 * ((FL[0][v] + FR[0][v]) * nbar[0] + (FL[1][v] + FR[1][v]) * nbar[1]) +
+                   0.5 * (QL[v] + QR[v]) * nbar[2];
+}
+
 // ------------------------------------------------------------------- update
 // Eq. (PDEfinal) with the face integrals (outward from fL), new volume from
 // the new vertices; status bit on an inadmissible result or a tangled cell.
@@ -410,7 +774,7 @@ __global__ void __launch_bounds__(256) k_ale_update(const int32_t* __restrict__ 
                                                     const double* __restrict__ Xv1, const double* __restrict__ vol0,
                                                     int64_t N, int64_t F, double gamma, double dt_fixed, double cfl,
                                                     const unsigned long long* dtmin, double* __restrict__ Q,
-                                                    double* time, int* status) {
+                                                    float* __restrict__ Qp, double* time, int* status) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) *time += step_dt(dt_fixed, cfl, dtmin);
   if (i >= N) return;
@@ -433,6 +797,13 @@ __global__ void __launch_bounds__(256) k_ale_update(const int32_t* __restrict__ 
     q[v] = (v0 * Q[v * N + i] - acc[v]) / v1;
     Q[v * N + i] = q[v];
   }
+  if (Qp) {  // FP32-mixed: the state's FP32 pairs for the reconstruction (layout.h)
+    float pr[8];
+    for (int v = 0; v < 4; ++v) split_hilo(q[v], pr[2 * v], pr[2 * v + 1]);
+    float4* dst = reinterpret_cast<float4*>(Qp) + i * 2;
+    dst[0] = make_float4(pr[0], pr[1], pr[2], pr[3]);
+    dst[1] = make_float4(pr[4], pr[5], pr[6], pr[7]);
+  }
   if (!(v1 > 0.0) || !admissible(q, gamma)) atomicOr(status, 1);
 }
 
@@ -446,6 +817,10 @@ struct Ale {
   AleTab tab;
   double *Xv = nullptr, *Xv1 = nullptr, *shift = nullptr, *X = nullptr, *bary = nullptr, *vol = nullptr;
   double *w = nullptr, *qhat = nullptr, *vcon = nullptr, *G = nullptr, *ftab = nullptr;
+  // FP32-mixed: tables, face basis and predictor deviations in FP32
+  bool fp32 = false;
+  AleTab32 tab32;
+  float *ftab32 = nullptr, *qhat32 = nullptr;
   int32_t *gv = nullptr, *start = nullptr, *ent = nullptr, *ident = nullptr;
   int* bad = nullptr;
   bool fresh = false;
@@ -487,14 +862,24 @@ unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 template <int M>
 cudaError_t launch_pred(Ale& A, cweno_solver* s, double dtf, cudaStream_t st) {
   const DevState& ds = s->ds;
-  k_ale_pred<M><<<nblk(ds.N, 128), 128, 0, st>>>(A.tab, A.w, ds.Q, A.X, A.vol, ds.N, s->ph.niter, dtf,
-                                                  s->prm.cfl, ds.dtmin, A.qhat, A.vcon);
+  if (A.fp32)
+    k_ale_pred32<M><<<nblk(ds.N, 128), 128, 0, st>>>(A.tab32, A.w, ds.Q, A.X, A.vol, ds.N, s->ph.niter, dtf,
+                                                      s->prm.cfl, ds.dtmin, A.qhat32, A.vcon);
+  else
+    k_ale_pred<M><<<nblk(ds.N, 128), 128, 0, st>>>(A.tab, A.w, ds.Q, A.X, A.vol, ds.N, s->ph.niter, dtf,
+                                                    s->prm.cfl, ds.dtmin, A.qhat, A.vcon);
   return cudaGetLastError();
 }
 
 template <int M>
 cudaError_t launch_flux(Ale& A, cweno_solver* s, double dtf, cudaStream_t st) {
   const DevState& ds = s->ds;
+  if (A.fp32) {
+    k_ale_flux32<M><<<nblk(ds.F, 128), 128, 0, st>>>(A.tab32, s->prm.gamma, A.ftab32, ds.fL, ds.fR, ds.codeL,
+                                                      ds.codeR, A.gv, A.shift, A.Xv, A.Xv1, A.bary, A.qhat32, ds.Q,
+                                                      ds.N, ds.F, dtf, s->prm.cfl, ds.dtmin, A.G);
+    return cudaGetLastError();
+  }
   k_ale_flux<M><<<nblk(ds.F, 128), 128, 0, st>>>(A.tab, A.ftab, ds.fL, ds.fR, ds.codeL, ds.codeR, A.gv, A.shift,
                                                   A.Xv, A.Xv1, A.bary, A.qhat, ds.Q, ds.N, ds.F, dtf, s->prm.cfl,
                                                   ds.dtmin, A.G);
@@ -506,18 +891,25 @@ cudaError_t launch_flux(Ale& A, cweno_solver* s, double dtf, cudaStream_t st) {
 // Per-step rebuild for a moving mesh: this unit keeps FMA contraction (the
 // matrices change every step; the host setup's exact arithmetic is not needed).
 int ale_matrices_device(const MeshHost& m, const RefElem& re, const double* d_X, const double* d_bary,
-                        const int32_t* d_sten, const int32_t* d_sec, double* d_R, double* d_Binv, int* d_bad,
+                        const int32_t* d_sten, const int32_t* d_sec, void* d_R, void* d_Binv, int fp32, int* d_bad,
                         void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   LsqTab tab;
   std::string err;
   if (!make_tab(m, re, tab, err)) return CWENO_EINVAL;
-  cudaError_t e = dispatch<double>(m.d, re.M, d_X, d_bary, d_sten, m.nc, tab, d_R, d_bad, st);
+  cudaError_t e = fp32 ? dispatch<float>(m.d, re.M, d_X, d_bary, d_sten, m.nc, tab, d_R, d_bad, st)
+                       : dispatch<double>(m.d, re.M, d_X, d_bary, d_sten, m.nc, tab, d_R, d_bad, st);
   if (e == cudaSuccess && m.d == 2) {
     switch (re.M) {
-      case 1: e = launch_sectors<2, 1>(d_X, d_bary, d_sec, m.nc, tab, d_Binv, d_bad, st); break;
-      case 2: e = launch_sectors<2, 2>(d_X, d_bary, d_sec, m.nc, tab, d_Binv, d_bad, st); break;
-      case 3: e = launch_sectors<2, 3>(d_X, d_bary, d_sec, m.nc, tab, d_Binv, d_bad, st); break;
+      case 1: e = fp32 ? launch_sectors<2, 1, float>(d_X, d_bary, d_sec, m.nc, tab, (float*)d_Binv, d_bad, st)
+                       : launch_sectors<2, 1, double>(d_X, d_bary, d_sec, m.nc, tab, (double*)d_Binv, d_bad, st);
+        break;
+      case 2: e = fp32 ? launch_sectors<2, 2, float>(d_X, d_bary, d_sec, m.nc, tab, (float*)d_Binv, d_bad, st)
+                       : launch_sectors<2, 2, double>(d_X, d_bary, d_sec, m.nc, tab, (double*)d_Binv, d_bad, st);
+        break;
+      case 3: e = fp32 ? launch_sectors<2, 3, float>(d_X, d_bary, d_sec, m.nc, tab, (float*)d_Binv, d_bad, st)
+                       : launch_sectors<2, 3, double>(d_X, d_bary, d_sec, m.nc, tab, (double*)d_Binv, d_bad, st);
+        break;
       default: e = cudaErrorInvalidValue;
     }
   } else if (e == cudaSuccess) {
@@ -528,9 +920,8 @@ int ale_matrices_device(const MeshHost& m, const RefElem& re, const double* d_X,
 
 int ale_create(cweno_solver* s, const MeshHost& m, std::string& err) {
   const RefElem& re = *s->re;
-  if (m.d != 2 || s->pde != CWENO_EULER || s->prec != CWENO_FP64 || re.M > 3 ||
-      s->prm.flux != CWENO_FLUX_RUSANOV) {
-    err = "moving meshes are built for 2D Euler, FP64, order 2..4, Rusanov flux";
+  if (m.d != 2 || s->pde != CWENO_EULER || re.M > 3 || s->prm.flux != CWENO_FLUX_RUSANOV) {
+    err = "moving meshes are built for 2D Euler, order 2..4, Rusanov flux";
     return CWENO_EINVAL;
   }
   auto A = std::make_shared<Ale>();
@@ -629,6 +1020,13 @@ int ale_create(cweno_solver* s, const MeshHost& m, std::string& err) {
   ACK(A->alloc(&A->vcon, (size_t)N * 9, st));
   ACK(A->alloc(&A->G, (size_t)4 * m.nf, st));
   ACK(A->alloc(&A->bad, 1, st));
+  if (s->prec == CWENO_FP32_MIXED) {
+    A->fp32 = true;
+    A->tab32 = ale_tab_cast<float>(t);
+    std::vector<float> f32(re.ftab.begin(), re.ftab.end());
+    ACK(A->put(&A->ftab32, f32, st));
+    ACK(A->alloc(&A->qhat32, (size_t)N * L * 4, st));
+  }
   const int big = 0x7fffffff;
   ACK(cudaMemcpyAsync(A->bad, &big, sizeof(int), cudaMemcpyHostToDevice, st));
   ACK(cudaStreamSynchronize(st));
@@ -645,8 +1043,8 @@ int ale_refresh(cweno_solver* s) {
   k_ale_geom<<<nblk(ds.N, 256), 256, 0, st>>>(A.Xv, A.gv, A.shift, ds.N, A.X, A.bary, A.vol,
                                                const_cast<double*>(ds.hsize), const_cast<double*>(ds.invvol));
   ACK(cudaGetLastError());
-  int rc = ale_matrices_device(A.slim, *s->re, A.X, A.bary, ds.sten, ds.sec, (double*)const_cast<void*>(ds.R),
-                               (double*)const_cast<void*>(ds.Binv), A.bad, st);
+  int rc = ale_matrices_device(A.slim, *s->re, A.X, A.bary, ds.sten, ds.sec, const_cast<void*>(ds.R),
+                               const_cast<void*>(ds.Binv), A.fp32, A.bad, st);
   if (rc) return fail(rc, "moving-mesh matrices");
   A.fresh = true;
   return CWENO_OK;
@@ -681,7 +1079,8 @@ int ale_step(cweno_solver* s, double dt) {
     default: ACK(launch_flux<3>(A, s, dtf, st)); break;
   }
   k_ale_update<<<nblk(ds.N, 256), 256, 0, st>>>(ds.cellface, A.G, A.gv, A.shift, A.Xv1, A.vol, ds.N, ds.F,
-                                                 s->prm.gamma, dtf, s->prm.cfl, ds.dtmin, ds.Q, ds.time, ds.status);
+                                                 s->prm.gamma, dtf, s->prm.cfl, ds.dtmin, ds.Q, ds.Qp, ds.time,
+                                                 ds.status);
   ACK(cudaGetLastError());
   std::swap(A.Xv, A.Xv1);
   A.fresh = false;

@@ -71,10 +71,11 @@ int cell_setup_device(const MeshHost& m, const RefElem& re, int fp32, void* stre
 // cell from the unwrapped cell vertices d_X (nc x (d+1) x 3, internal order)
 // and barycentres d_bary (nc x 3) of the current mesh, for the fixed
 // stencils d_sten and sector cells d_sec (SoA, as uploaded by the setup).
+// R and Binv are written as FP32 when fp32 (FP32-mixed solvers), else FP64.
 // *d_bad receives the smallest cell index whose system is degenerate.
 // Asynchronous on stream (a cudaStream_t).
 int ale_matrices_device(const MeshHost& m, const RefElem& re, const double* d_X, const double* d_bary,
-                        const int32_t* d_sten, const int32_t* d_sec, double* d_R, double* d_Binv, int* d_bad,
+                        const int32_t* d_sten, const int32_t* d_sec, void* d_R, void* d_Binv, int fp32, int* d_bad,
                         void* stream);
 
 }  // namespace cw

@@ -446,34 +446,6 @@ __device__ __forceinline__ void flux_normal(const T* q, const typename Phys<D, P
 }
 
 // --------------------------------------------------- state access helpers
-// FP32 pair (hi, lo) of an FP64 value q: hi is q truncated to 24 significant
-// bits, lo = q - hi (exact in FP64) rounded to FP32, so hi + lo equals q to
-// about 2^-47 relative.  Built from the bits of q with integer operations,
-// off the FP64 pipe (1/64 of the FP32 rate on this part; the conversions of
-// the plain form (float)q, (float)(q - (double)hi) ran on it).  Exponents
-// outside the range where hi and lo are normal FP32 numbers take that plain
-// form; zero (and FP64 subnormals) give (0, 0) with the sign of q.
-__device__ __forceinline__ void split_hilo(double q, float& hi, float& lo) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(q);
-  const unsigned hw = (unsigned)(b >> 32);
-  const int e = (int)((hw >> 20) & 0x7ffu);
-  const unsigned sign = hw & 0x80000000u;
-  if (e >= 950 && e <= 1150) {
-    // hi: sign, exponent rebased from 1023 to 127, top 23 mantissa bits
-    hi = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | (unsigned)((b >> 29) & 0x7fffffu));
-    // lo: the 29 dropped mantissa bits times 2^(e - 1075), rounded once
-    const unsigned rem = (unsigned)(b & 0x1fffffffu);
-    const float scale = __uint_as_float((unsigned)(e - 1075 + 127) << 23);
-    lo = __uint_as_float(__float_as_uint(__uint2float_rn(rem) * scale) | sign);
-  } else if (e == 0) {
-    hi = __uint_as_float(sign);
-    lo = hi;
-  } else {
-    hi = (float)q;
-    lo = (float)(q - (double)hi);
-  }
-}
-
 // The FP32 pairs (hi, lo) of cell j, NVP / 2 16-byte vectors (layout.h)
 template <class C>
 __device__ __forceinline__ void load_pairs(const float* __restrict__ Qp, int64_t j, float* hi, float* lo) {
@@ -799,16 +771,25 @@ __device__ __forceinline__ void rec_pred_cell(const KArgs<C>& a, const CellTab<C
           for (int v = 0; v < NV; ++v) w[l][v] *= theta;
       }
     }
-    // reconstruction values at the lattice nodes, caller's cell order
+    // reconstruction values at the lattice nodes, caller's cell order; in
+    // FP32-mixed mode the FP32 deviation is added to the FP64 cell average
+    // (hi + lo in FP64), so the deviation stays recoverable to FP32 accuracy
     const int64_t u = a.perm[i];
 #pragma unroll
     for (int n = 0; n < C::L0; ++n)
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        T s = qbar[v];
+        if constexpr (std::is_same<T, float>::value) {
+          T s = T(0);
 #pragma unroll
-        for (int l = 0; l < MC1; ++l) s += tb.E[n][l] * w[l][v];
-        a.out[(u * C::MC + n) * NV + v] = (double)s;
+          for (int l = 0; l < MC1; ++l) s += tb.E[n][l] * w[l][v];
+          a.out[(u * C::MC + n) * NV + v] = ((double)qi[v] + (double)qlo[v]) + (double)s;
+        } else {
+          T s = qbar[v];
+#pragma unroll
+          for (int l = 0; l < MC1; ++l) s += tb.E[n][l] * w[l][v];
+          a.out[(u * C::MC + n) * NV + v] = (double)s;
+        }
       }
     return;
   } else {

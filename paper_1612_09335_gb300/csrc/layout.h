@@ -17,6 +17,9 @@
 //   rounded up to even, so one cell's pairs are NVP / 2 16-byte vectors.
 #pragma once
 #include <cstdint>
+#ifdef __CUDACC__
+#include <cuda_runtime.h>
+#endif
 
 namespace cw {
 
@@ -33,5 +36,36 @@ __host__ __device__ inline int64_t r_index(int r, int k, int mc1, int64_t i, int
 }
 __host__ __device__ constexpr int sten_vectors(int ne1) { return (ne1 + 3) / 4; }
 __host__ __device__ constexpr int pair_vars(int nv) { return (nv + 1) & ~1; }
+
+#ifdef __CUDACC__
+// FP32 pair (hi, lo) of an FP64 value q: hi is q truncated to 24 significant
+// bits, lo = q - hi (exact in FP64) rounded to FP32, so hi + lo equals q to
+// about 2^-47 relative.  Built from the bits of q with integer operations,
+// off the FP64 pipe (1/64 of the FP32 rate on this part; the conversions of
+// the plain form (float)q, (float)(q - (double)hi) ran on it).  Exponents
+// outside the range where hi and lo are normal FP32 numbers take that plain
+// form; zero (and FP64 subnormals) give (0, 0) with the sign of q.
+__device__ __forceinline__ void split_hilo(double q, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(q);
+  const unsigned hw = (unsigned)(b >> 32);
+  const int e = (int)((hw >> 20) & 0x7ffu);
+  const unsigned sign = hw & 0x80000000u;
+  if (e >= 950 && e <= 1150) {
+    // hi: sign, exponent rebased from 1023 to 127, top 23 mantissa bits
+    hi = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | (unsigned)((b >> 29) & 0x7fffffu));
+    // lo: the 29 dropped mantissa bits times 2^(e - 1075), rounded once
+    const unsigned rem = (unsigned)(b & 0x1fffffffu);
+    const float scale = __uint_as_float((unsigned)(e - 1075 + 127) << 23);
+    lo = __uint_as_float(__float_as_uint(__uint2float_rn(rem) * scale) | sign);
+  } else if (e == 0) {
+    hi = __uint_as_float(sign);
+    lo = hi;
+  } else {
+    hi = (float)q;
+    lo = (float)(q - (double)hi);
+  }
+}
+
+#endif
 
 }  // namespace cw

@@ -201,10 +201,10 @@ __global__ void __launch_bounds__(128) k_lsq(const double* __restrict__ X, const
 // coordinates of cell i) and Binv[((s D + e) D + k) N + i] = (B^-1)[e][k],
 // the layout the reconstruction kernel reads.  Dropped sectors (first id
 // < 0) are skipped.  bad: smallest cell index with a singular B.
-template <int D, int M>
+template <int D, int M, typename T>
 __global__ void __launch_bounds__(128) k_sectors(const double* __restrict__ X, const double* __restrict__ bary,
                                                  const int32_t* __restrict__ sec, int64_t N, const LsqTab tab,
-                                                 double* __restrict__ Binv, int* bad) {
+                                                 T* __restrict__ Binv, int* bad) {
   constexpr int MC = cmc(M, D), NX = (D + 1) * 3;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(128) k_sectors(const double* __restrict__ X, c
       continue;
     }
     for (int e = 0; e < D; ++e)
-      for (int k = 0; k < D; ++k) Binv[(int64_t)((s * D + e) * D + k) * N + i] = Bi[e][k];
+      for (int k = 0; k < D; ++k) Binv[(int64_t)((s * D + e) * D + k) * N + i] = (T)Bi[e][k];
   }
 }
 
@@ -319,10 +319,10 @@ bool make_tab(const MeshHost& m, const RefElem& re, LsqTab& tab, std::string& er
   return true;
 }
 
-template <int D, int M>
+template <int D, int M, typename T>
 cudaError_t launch_sectors(const double* X, const double* bary, const int32_t* sec, int64_t N, const LsqTab& tab,
-                           double* Binv, int* bad, cudaStream_t st) {
-  k_sectors<D, M><<<(unsigned)((N + 127) / 128), 128, 0, st>>>(X, bary, sec, N, tab, Binv, bad);
+                           T* Binv, int* bad, cudaStream_t st) {
+  k_sectors<D, M, T><<<(unsigned)((N + 127) / 128), 128, 0, st>>>(X, bary, sec, N, tab, Binv, bad);
   return cudaGetLastError();
 }
 

@@ -61,14 +61,15 @@ def test_setup_rejects_unsupported_combinations_before_device_work(cw, wl):
 
 
 def test_moving_mesh_setup_rejects_unbuilt_combinations(cw, wl):
-    """Moving meshes are built for 2D Euler, FP64, order 2..4 and the Rusanov
-    flux; everything else is EINVAL before any device call."""
+    """Moving meshes are built for 2D Euler, order 2..4 and the Rusanov flux
+    (FP64 and FP32-mixed); everything else is EINVAL before any device call."""
     m2 = cw.Mesh.from_workload(wl.tri_mesh(6))
     m3 = cw.Mesh.from_workload(wl.tet_mesh(3))
-    cases = [(m2, 3, cw.EULER, cw.FP32_MIXED, {}), (m3, 3, cw.EULER, cw.FP64, {}),
+    cases = [(m3, 3, cw.EULER, cw.FP64, {}), (m3, 3, cw.EULER, cw.FP32_MIXED, {}),
              (m2, 3, cw.MHD_GLM, cw.FP64, {}), (m2, 5, cw.EULER, cw.FP64, {}),
+             (m2, 5, cw.EULER, cw.FP32_MIXED, {}),
              (m2, 3, cw.EULER, cw.FP64, {"flux": cw.FLUX_OSHER}),
-             (m2, 3, cw.EULER, cw.FP64, {"flux": cw.FLUX_RUSANOV_QF})]
+             (m2, 3, cw.EULER, cw.FP32_MIXED, {"flux": cw.FLUX_RUSANOV_QF})]
     for mesh, order, pde, prec, kw in cases:
         with pytest.raises(cw.CwenoError) as e:
             cw.Solver(mesh, order, pde, prec, mesh_motion=cw.MOTION_LAGRANGE, **kw)

@@ -202,3 +202,94 @@ def test_run_equals_step_loop_and_isolated_vertex(cw, orc, wl):
         Qo, xo = o.ale_step(Qo, o.stable_dt(Qo))
     assert np.abs(xa - xo).max() < 1e-12
     assert relerr(a.get_state(), Qo) < 1e-11
+
+
+# ---------------------------------------------------------------- FP32-mixed
+# The moving-mesh step in FP32-mixed precision: per-step least squares, nodal
+# solver, the cell averages' part of the face integrals and the update in
+# FP64; predictor and face traces in FP32 on deviations.  Bounds as on fixed
+# meshes (variables below 1 % of the state's scale measured at that scale):
+# smooth 2e-6, discontinuous 1e-4; vertices move with the FP32 predictor's
+# mesh velocity: 1e-7 of the domain size.
+def solver32(cw, mesh, order, motion=LAGRANGE):
+    return cw.Solver(cw.Mesh.from_workload(mesh), order, EULER, cw.FP32_MIXED, mesh_motion=motion)
+
+
+@pytest.mark.parametrize("name", ["vortex", "explosion"])
+@pytest.mark.parametrize("order", [2, 3, 4])
+def test_fp32_mixed_ale_step_within_bounds(cw, orc, wl, name, order):
+    mesh, Q = inputs(wl, name)
+    o = orc.Oracle(mesh, order)
+    dt = o.stable_dt(Q)
+    Qo, xo = o.ale_step(Q, dt)
+    s = solver32(cw, mesh, order)
+    s.set_state(Q)
+    s.step(dt)
+    s.sync()
+    scale = np.abs(mesh.xyz).max()
+    assert np.abs(s.get_vertices() - xo).max() < 1e-7 * scale
+    assert relerr(s.get_state(), Qo, floor=1e-2) < (2e-6 if name == "vortex" else 1e-4)
+
+
+def test_fp32_mixed_ale_five_steps_device_cfl(cw, orc, wl):
+    """Five steps with the device CFL step on the moving mesh against the
+    oracle's own CFL steps on its moved mesh."""
+    mesh, Q = inputs(wl, "vortex")
+    o = orc.Oracle(mesh, 3)
+    s = solver32(cw, mesh, 3)
+    s.set_state(Q)
+    Qo = Q.copy()
+    t = 0.0
+    for _ in range(5):
+        dt = o.stable_dt(Qo)
+        Qo, xo = o.ale_step(Qo, dt)
+        t += dt
+        s.step(0.0)
+    assert abs(s.time() / t - 1) < 1e-6
+    assert np.abs(s.get_vertices() - xo).max() < 1e-7
+    assert relerr(s.get_state(), Qo, floor=1e-2) < 1e-5
+
+
+def test_fp32_mixed_ale_constant_state_and_conservation(cw, wl):
+    """A constant state stays constant to FP64 rounding while the mesh
+    translates with it (the cell averages' part of the face integrals is FP64
+    and the geometric conservation law closes); on a deforming periodic mesh
+    sum |T| Q is conserved to 1e-12."""
+    import dataclasses
+    mesh, _ = wl.vortex_2d(16)
+    q = np.array([1.3, 0.39, -0.26, 3.1])
+    s = solver32(cw, mesh, 4)
+    s.set_state(np.tile(q, (mesh.nc, 1)))
+    for _ in range(3):
+        s.step(0.01)
+    assert np.abs(s.get_state() - q).max() < 5e-13
+    assert np.abs(s.get_vertices() - mesh.xyz - 0.03 * q[1:3] / q[0]).max() < 1e-8
+    mesh, Q = wl.vortex_2d(24)
+    s = solver32(cw, mesh, 3)
+    s.set_state(Q)
+
+    def vol(xyz):
+        X = dataclasses.replace(mesh, xyz=xyz).cell_vertices()
+        E = X[:, 1:, :] - X[:, :1, :]
+        return 0.5 * (E[:, 0, 0] * E[:, 1, 1] - E[:, 0, 1] * E[:, 1, 0])
+
+    tot0 = vol(mesh.xyz) @ Q
+    for _ in range(6):
+        s.step(0.0)
+    v1 = vol(s.get_vertices())
+    assert np.std(v1 / vol(mesh.xyz)) > 1e-5
+    assert np.abs(v1 @ s.get_state() - tot0).max() / np.abs(tot0).max() < 1e-12
+
+
+def test_fp32_mixed_still_mesh_near_fixed_mesh_fp32(cw, wl):
+    """V = 0 in FP32-mixed: the moving-mesh machinery on a mesh that does not
+    move stays within the FP32 bound of the fixed-mesh FP32-mixed path."""
+    mesh, Q = inputs(wl, "vortex")
+    a = solver32(cw, mesh, 3, STILL)
+    b = cw.Solver(cw.Mesh.from_workload(mesh), 3, EULER, cw.FP32_MIXED)
+    for s in (a, b):
+        s.set_state(Q)
+        for _ in range(3):
+            s.step(0.0)
+    assert np.array_equal(a.get_vertices(), mesh.xyz)
+    assert relerr(a.get_state(), b.get_state(), floor=1e-2) < 2e-6
