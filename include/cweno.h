@@ -321,8 +321,9 @@ enum { CWENO_REQ_QUEUED = 0, CWENO_REQ_RUNNING = 1, CWENO_REQ_DONE = 2, CWENO_RE
 
 /* mem_budget: device bytes the server may hold for admitted requests
  * (0 -> 80% of free memory); max_slots: concurrently admitted requests, each
- * with its own CUDA stream for its setup (<= 0 or > 64 -> 64, the capacity of
- * a group's batch table); nworkers: host threads preparing
+ * with its own CUDA stream for its setup (<= 0 -> 256, at most 256; a
+ * group's batch table holds 64 members, further requests of a configuration
+ * wait to join it); nworkers: host threads preparing
  * admitted requests (mesh on the host; stencils, sectors and least-squares
  * inverses on the device; <= 0 -> one per host core).  Admission is first come,
  * first served. */

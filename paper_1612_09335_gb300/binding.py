@@ -354,7 +354,7 @@ class Solver:
 class Server:
     """Owned cweno_server handle (serve_create / serve_submit / serve_poll)."""
 
-    def __init__(self, mem_budget: int = 0, max_slots: int = 64, nworkers: int = 0):
+    def __init__(self, mem_budget: int = 0, max_slots: int = 0, nworkers: int = 0):
         h = C.c_void_p()
         _check(lib().serve_create(int(mem_budget), int(max_slots), int(nworkers), C.byref(h)))
         self.h = h

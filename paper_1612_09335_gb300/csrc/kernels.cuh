@@ -139,6 +139,11 @@ struct Cfg {
 #else
   static constexpr bool TAU0_SPARSE = false;
 #endif
+#ifdef CW_SIDE_AHEAD
+  static constexpr bool SIDE_AHEAD = CW_SIDE_AHEAD;
+#else
+  static constexpr bool SIDE_AHEAD = true;
+#endif
 #ifdef CW_IDS_AHEAD
   static constexpr bool IDS_AHEAD = CW_IDS_AHEAD;
 #else
@@ -1249,8 +1254,24 @@ __global__ void __launch_bounds__(128, C::FLUX_MINB) k_flux(KArgs<C> a, int use_
 // One block iteration of the pair kernel: the 128 threads starting at
 // thread index g0 of the face space (TPF threads per face).  `tab` holds the
 // face tables, then the space and time quadrature weights.
+// The cell and face code a thread of the pair kernel works on at thread base
+// g0 (its own side; a boundary face evaluates its inner cell on both sides)
+struct PairSide {
+  int32_t c, code;
+};
+template <class C>
+__device__ __forceinline__ PairSide pair_side(const KArgs<C>& a, int64_t g0) {
+  constexpr int TPF = 2 * C::FLUX_SPLIT;
+  const int64_t fg = (g0 + threadIdx.x) / TPF;
+  const int64_t f = fg < a.F ? fg : a.F - 1;
+  const int32_t Lc = a.fL[f], Rc = a.fR[f];
+  const bool own_left = (threadIdx.x & 1) == 0 || Rc < 0;
+  return PairSide{own_left ? Lc : Rc, (int32_t)(own_left ? a.codeL[f] : a.codeR[f])};
+}
+
 template <class C, bool OSHER>
-__device__ __forceinline__ void flux_pair_iter(const KArgs<C>& a, const typename C::T* tab, int64_t g0, double dtd) {
+__device__ __forceinline__ void flux_pair_iter(const KArgs<C>& a, const typename C::T* tab, int64_t g0, double dtd,
+                                               PairSide ps) {
   using T = typename C::T;
   constexpr int D = C::D, NV = C::NV, NQS = C::NQS, NP = C::NQT * C::NQS;
   constexpr int SPLIT = C::FLUX_SPLIT, TPF = 2 * SPLIT;
@@ -1264,11 +1285,8 @@ __device__ __forceinline__ void flux_pair_iter(const KArgs<C>& a, const typename
     const int64_t fg = (g0 + threadIdx.x) / TPF;
     const bool valid = fg < F;
     const int64_t f = valid ? fg : F - 1;
-    const int64_t Lc = a.fL[f];
-    const int64_t Rc = a.fR[f];
-    const bool own_left = side == 0 || Rc < 0;
-    const int64_t c = own_left ? Lc : Rc;
-    const T* tc = tab + (int)(own_left ? a.codeL[f] : a.codeR[f]) * C::CODE_STRIDE;
+    const int64_t c = ps.c;
+    const T* tc = tab + ps.code * C::CODE_STRIDE;
     T n[D];
 #pragma unroll
     for (int e = 0; e < D; ++e) n[e] = a.fn[e * F + f];
@@ -1368,8 +1386,17 @@ __global__ void __launch_bounds__(128, C::FLUX_MINB) k_flux_pair(KArgs<C> a, int
   const double dtd = dt_of(a.dt_fixed, a.cfl, a.dtmin, a.cur);
   // block-uniform trip count (the exchanges shuffle over the whole warp); a
   // thread past the last face works on a clamped copy, not written
-  for (int64_t g0 = (int64_t)blockIdx.x * blockDim.x; g0 < TPF * a.F; g0 += (int64_t)gridDim.x * blockDim.x)
-    flux_pair_iter<C, OSHER>(a, tab, g0, dtd);
+  // with SIDE_AHEAD the next iteration's cell and code are loaded while the
+  // current face is integrated
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t g0 = (int64_t)blockIdx.x * blockDim.x;
+  PairSide ps = pair_side<C>(a, g0);
+  for (; g0 < TPF * a.F; g0 += stride) {
+    PairSide nx = ps;
+    if (C::SIDE_AHEAD && g0 + stride < TPF * a.F) nx = pair_side<C>(a, g0 + stride);
+    flux_pair_iter<C, OSHER>(a, tab, g0, dtd, ps);
+    ps = C::SIDE_AHEAD ? nx : pair_side<C>(a, g0 + stride);
+  }
 }
 
 // Quadrature-free Rusanov flux (the fixed-mesh form the paper describes
@@ -1678,7 +1705,7 @@ __global__ void __launch_bounds__(128, C::FLUX_MINB) k_flux_batch(const BatchTab
     const int lc = batch_stage(bt, 1, c, sa);
     const double dtd = dt_of(sa.dt_fixed, sa.cfl, sa.dtmin, sa.cur);
     if constexpr (C::PAIR) {
-      flux_pair_iter<C, OSHER>(sa, tab, (int64_t)lc * 128, dtd);
+      flux_pair_iter<C, OSHER>(sa, tab, (int64_t)lc * 128, dtd, pair_side<C>(sa, (int64_t)lc * 128));
     } else {
       const int64_t f = (int64_t)lc * 128 + threadIdx.x;
       if (f < sa.F) flux_one_face<C, OSHER>(sa, tab, f, dtd);

@@ -384,7 +384,8 @@ void scheduler_main(cweno_server* S) {
       }
       joining.swap(S->ready);
     }
-    bool progress = !joining.empty();
+    bool progress = false;
+    std::vector<Req*> waiting;  // their group's table is full: join at a later tick
     for (Req* r : joining) {
       if (r->nsteps == 0) {  // nothing to step: the initial state is the result
         r->t_done = Clock::now();
@@ -399,7 +400,16 @@ void scheduler_main(cweno_server* S) {
         retire(S, r, CWENO_REQ_ERROR, err);
         continue;
       }
+      if ((int)g->members.size() >= g->ops->batch_max()) {
+        waiting.push_back(r);
+        continue;
+      }
       g->members.push_back(r);
+      progress = true;
+    }
+    if (!waiting.empty()) {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->ready.insert(S->ready.begin(), waiting.begin(), waiting.end());
     }
     for (auto& gp : S->groups) {
       Group* g = gp.get();
@@ -472,9 +482,10 @@ int serve_create(size_t mem_budget, int max_slots, int nworkers, cweno_server** 
     mem_budget = (size_t)(0.8 * (double)fr);
   }
   S->budget = mem_budget;
-  // a group's batch table holds at most 64 members (Ops::batch_max), and
-  // every admitted request may belong to one group
-  S->max_slots = std::min(max_slots > 0 ? max_slots : 64, 64);
+  // admitted requests (each with a stream for its setup); a group's batch
+  // table holds at most 64 members (Ops::batch_max), requests beyond that
+  // wait to join their group
+  S->max_slots = std::min(max_slots > 0 ? max_slots : 256, 256);
   unsigned hc = std::max(1u, std::thread::hardware_concurrency());
   // one setup worker per host core by default: a worker builds one request's
   // mesh (host, single-threaded) and runs its stencil search and
