@@ -52,11 +52,16 @@ struct CellSetup {
 int build_cell_setup(const MeshHost& m, const RefElem& re, CellSetup& cs, std::string& err, int nthreads,
                      bool with_lsq = true);
 
-// Least-squares pseudo-inverses R on the current device (setup_gpu.cu): d_sten
+// Least-squares pseudo-inverses R on the current device (lsq_gpu.cu): d_sten
 // the uploaded SoA stencils, d_R the solver's R buffer (FP32 if fp32, else
 // FP64), stream a cudaStream_t.  Synchronous on that stream.
 int lsq_setup_device(const MeshHost& m, const RefElem& re, const int32_t* d_sten, void* d_R, int fp32,
                      void* stream, std::string& err);
+// The same kernel on caller-uploaded vertices d_X (nc x (d+1) x 3) and
+// barycentres d_bary (nc x 3); asynchronous on stream, *d_bad receives the
+// smallest rank-deficient cell index (atomicMin, caller-initialised).
+int lsq_launch_device(const MeshHost& m, const RefElem& re, const double* d_X, const double* d_bary,
+                      const int32_t* d_sten, void* d_R, int fp32, int* d_bad, void* stream, std::string& err);
 // Stencils, sectors, inverse Jacobians, sector inverses and R_i of every
 // cell on the device (setup_gpu.cu), into caller-allocated buffers in the
 // kernels' layouts; returns kCellSetupOnHost when a stencil search outgrows

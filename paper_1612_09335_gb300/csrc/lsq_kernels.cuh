@@ -1,11 +1,12 @@
 // Least-squares reconstruction matrices on the device (Sec. 2.1, Eq.
-// CWENO:Popt), shared by the fixed-mesh setup (setup_gpu.cu, compiled without
-// FMA contraction, the host setup's arithmetic) and the per-step rebuild on
-// moving meshes (ale.cu): for every cell, the averages of the Dubiner basis
+// CWENO:Popt), shared by the fixed-mesh setup (lsq_gpu.cu; setup_gpu.cu uses
+// the tables and the Dubiner evaluation for its sector inverses) and the
+// per-step rebuild on moving meshes (ale.cu): for every cell, the averages of the Dubiner basis
 // functions psi_1..psi_{Mc-1} of its reference frame over the cells of its
 // central stencil (the constrained problem with the constant part removed),
 // the pseudo-inverse R_i of that (n_e - 1) x (Mc - 1) matrix by modified
-// Gram-Schmidt with one reorthogonalisation pass, written in the vector layout
+// Gram-Schmidt with one reorthogonalisation pass (FMA, reciprocals instead of
+// per-entry divisions), written in the vector layout
 // the reconstruction kernel reads (layout.h); and the sector inverses of Eq. (CWENO:Ps).
 // FP64 throughout, one thread per cell.  Each including translation unit gets
 // its own copy (unnamed namespace).
@@ -46,38 +47,56 @@ __host__ __device__ constexpr int cmc(int M, int d) {
 }
 
 template <int M>
-__device__ void jacobi_seq(const LsqTab& t, int alpha, int nmax, double u, double s, double* p) {
+__device__ __forceinline__ void jacobi_seq(const LsqTab& t, int alpha, int nmax, double u, double s, double* p) {
   p[0] = 1.0;
   if (nmax < 1) return;
   p[1] = 0.5 * ((alpha + 2.0) * u + alpha * s);
+#pragma unroll
   for (int k = 2; k <= nmax; ++k) {
     const double* r = t.rec[alpha * (M + 1) + k];
     p[k] = (r[0] * s + r[1] * u) * p[k - 1] - r[2] * s * s * p[k - 2];
   }
 }
 
-// all Dubiner basis functions at xi (psi_0 = 1), shared Jacobi sequences
+// all Dubiner basis functions at xi (psi_0 = 1), shared Jacobi sequences.
+// The basis order is the reference element's (by total degree k, then r,
+// then q; make_tab checks it), unrolled at compile time so that every index
+// is static and the sequences stay in registers.  The third-direction
+// sequence depends on (p + q, r) only: one per p + q, a prefix of which
+// serves every r.
 template <int D, int M>
-__device__ void dubiner(const LsqTab& t, const double* xi, double* out) {
-  double f1[M + 1], f2[M + 1][M + 1], f3[M + 1];
+__device__ __forceinline__ void dubiner(const LsqTab& t, const double* xi, double* out) {
+  double f1[M + 1], f2[M + 1][M + 1];
+  out[0] = 1.0;
   if (D == 2) {
     const double s1 = 1.0 - xi[1], u1 = 2.0 * xi[0] - s1;
     jacobi_seq<M>(t, 0, M, u1, s1, f1);
+#pragma unroll
     for (int p = 0; p <= M; ++p) jacobi_seq<M>(t, 2 * p + 1, M - p, 2.0 * xi[1] - 1.0, 1.0, f2[p]);
-    out[0] = 1.0;
-    for (int l = 1; l < t.nb; ++l) out[l] = t.norm[l] * (f1[t.pqr[l][0]] * f2[t.pqr[l][0]][t.pqr[l][1]]);
+    int l = 0;
+#pragma unroll
+    for (int k = 0; k <= M; ++k)
+#pragma unroll
+      for (int q = 0; q <= k; ++q, ++l)
+        if (l > 0) out[l] = t.norm[l] * (f1[k - q] * f2[k - q][q]);
     return;
   }
+  double f3[M + 1][M + 1];
   const double s1 = 1.0 - xi[1] - xi[2], u1 = 2.0 * xi[0] - s1;
   const double s2 = 1.0 - xi[2], u2 = 2.0 * xi[1] - s2;
   jacobi_seq<M>(t, 0, M, u1, s1, f1);
+#pragma unroll
   for (int p = 0; p <= M; ++p) jacobi_seq<M>(t, 2 * p + 1, M - p, u2, s2, f2[p]);
-  out[0] = 1.0;
-  for (int l = 1; l < t.nb; ++l) {
-    const int p = t.pqr[l][0], q = t.pqr[l][1], r = t.pqr[l][2];
-    jacobi_seq<M>(t, 2 * p + 2 * q + 2, r, 2.0 * xi[2] - 1.0, 1.0, f3);
-    out[l] = t.norm[l] * (f1[p] * f2[p][q] * f3[r]);
-  }
+#pragma unroll
+  for (int pq = 0; pq <= M; ++pq) jacobi_seq<M>(t, 2 * pq + 2, M - pq, 2.0 * xi[2] - 1.0, 1.0, f3[pq]);
+  int l = 0;
+#pragma unroll
+  for (int k = 0; k <= M; ++k)
+#pragma unroll
+    for (int r = 0; r <= k; ++r)
+#pragma unroll
+      for (int q = 0; q <= k - r; ++q, ++l)
+        if (l > 0) out[l] = t.norm[l] * (f1[k - q - r] * f2[k - q - r][q] * f3[k - r][r]);
 }
 
 template <int D>
@@ -122,7 +141,10 @@ __global__ void __launch_bounds__(128) k_lsq(const double* __restrict__ X, const
   const double* Xi = X + i * NX;
   double Ji[3][3];
   jac_inv<D>(Xi, Ji);
-  double Qm[NE1][MC1];
+  // FP64 divisions are long instruction sequences: reciprocals once, then
+  // products; explicit fma() in the inner loops
+  const double iwsum = 1.0 / tab.wsum;
+  double Qc[MC1][NE1];  // A by columns, then Q
   double psi[MC];
   for (int r = 0; r < NE1; ++r) {
     const int64_t j = sten[(int64_t)r * N + i];
@@ -139,38 +161,51 @@ __global__ void __launch_bounds__(128) k_lsq(const double* __restrict__ X, const
       double x[3] = {0, 0, 0};
       for (int a = 0; a < D; ++a) {
         x[a] = Xj[a] + s[a];
-        for (int k = 0; k < D; ++k) x[a] += tab.qx[g][k] * (Xj[(k + 1) * 3 + a] - Xj[a]);
+        for (int k = 0; k < D; ++k) x[a] = fma(tab.qx[g][k], Xj[(k + 1) * 3 + a] - Xj[a], x[a]);
       }
       double xi[3] = {0, 0, 0};
       for (int a = 0; a < D; ++a)
-        for (int b = 0; b < D; ++b) xi[a] += Ji[a][b] * (x[b] - Xi[b]);
+        for (int b = 0; b < D; ++b) xi[a] = fma(Ji[a][b], x[b] - Xi[b], xi[a]);
       dubiner<D, M>(tab, xi, psi);
-      for (int l = 1; l < MC; ++l) acc[l] += tab.qw[g] * psi[l];
+#pragma unroll
+      for (int l = 1; l < MC; ++l) acc[l] = fma(tab.qw[g], psi[l], acc[l]);
     }
-    for (int l = 1; l < MC; ++l) Qm[r][l - 1] = acc[l] / tab.wsum;
+#pragma unroll
+    for (int l = 1; l < MC; ++l) Qc[l - 1][r] = acc[l] * iwsum;
   }
   // modified Gram-Schmidt with one reorthogonalisation pass: A = Q Rm
   double Rm[MC1][MC1];
   for (int a = 0; a < MC1; ++a)
     for (int b = 0; b < MC1; ++b) Rm[a][b] = 0.0;
   bool ok = true;
+  // column k in registers while the earlier columns are projected out, where
+  // a column fits (n_e - 1 <= 32); longer columns stay in local memory
+  constexpr int UR = NE1 <= 32 ? NE1 : 1;
   for (int k = 0; k < MC1; ++k) {
+    double v[NE1];
+#pragma unroll UR
+    for (int r = 0; r < NE1; ++r) v[r] = Qc[k][r];
     for (int pass = 0; pass < 2; ++pass)
       for (int j = 0; j < k; ++j) {
         double sdot = 0.0;
-        for (int r = 0; r < NE1; ++r) sdot += Qm[r][j] * Qm[r][k];
+#pragma unroll UR
+        for (int r = 0; r < NE1; ++r) sdot = fma(Qc[j][r], v[r], sdot);
         Rm[j][k] += sdot;
-        for (int r = 0; r < NE1; ++r) Qm[r][k] -= sdot * Qm[r][j];
+#pragma unroll UR
+        for (int r = 0; r < NE1; ++r) v[r] = fma(-sdot, Qc[j][r], v[r]);
       }
     double nn = 0.0;
-    for (int r = 0; r < NE1; ++r) nn += Qm[r][k] * Qm[r][k];
+#pragma unroll UR
+    for (int r = 0; r < NE1; ++r) nn = fma(v[r], v[r], nn);
     nn = sqrt(nn);
     Rm[k][k] = nn;
     if (nn == 0.0) {
       ok = false;
       break;
     }
-    for (int r = 0; r < NE1; ++r) Qm[r][k] /= nn;
+    const double inn = 1.0 / nn;
+#pragma unroll UR
+    for (int r = 0; r < NE1; ++r) Qc[k][r] = v[r] * inn;
   }
   if (ok) {
     double dmax = 0.0;
@@ -184,13 +219,18 @@ __global__ void __launch_bounds__(128) k_lsq(const double* __restrict__ X, const
   }
   // pinv = Rm^{-1} Q^T, column by column of Q^T, in the vector layout of
   // layout.h (r_index)
+  double iR[MC1];
+  for (int k = 0; k < MC1; ++k) iR[k] = 1.0 / Rm[k][k];
   for (int r = 0; r < NE1; ++r) {
     double col[MC1];
+#pragma unroll
     for (int k = MC1 - 1; k >= 0; --k) {
-      double sv = Qm[r][k];
-      for (int j = k + 1; j < MC1; ++j) sv -= Rm[k][j] * col[j];
-      col[k] = sv / Rm[k][k];
+      double sv = Qc[k][r];
+#pragma unroll
+      for (int j = k + 1; j < MC1; ++j) sv = fma(-Rm[k][j], col[j], sv);
+      col[k] = sv * iR[k];
     }
+#pragma unroll
     for (int k = 0; k < MC1; ++k) R[r_index<T>(r, k, MC1, i, N)] = (T)col[k];
   }
 }
@@ -306,6 +346,20 @@ bool make_tab(const MeshHost& m, const RefElem& re, LsqTab& tab, std::string& er
     tab.wsum += Q.w[g];
   }
   tab.nb = re.psi.n;
+  // the device Dubiner evaluation unrolls this order (total degree, then r, then q)
+  {
+    int l = 0;
+    bool same = true;
+    for (int k = 0; k <= M; ++k)
+      for (int r = 0; r <= (d == 3 ? k : 0); ++r)
+        for (int q = 0; q <= k - r; ++q, ++l)
+          if (l >= tab.nb || re.psi.pqr[l][0] != k - q - r || re.psi.pqr[l][1] != q || re.psi.pqr[l][2] != r)
+            same = false;
+    if (!same || l != tab.nb) {
+      err = "Dubiner basis order differs from the device evaluation";
+      return false;
+    }
+  }
   for (int l = 0; l < tab.nb; ++l) {
     for (int a = 0; a < 3; ++a) tab.pqr[l][a] = re.psi.pqr[l][a];
     tab.norm[l] = re.psi.norm[l];

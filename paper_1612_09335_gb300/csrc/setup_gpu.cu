@@ -1,10 +1,11 @@
 // Per-cell reconstruction data of a fixed mesh on the device, once at setup
 // (Sec. 2.1: precomputed for fixed meshes): the ranked stencil search, the
-// sectors and their inverses, the inverse Jacobians, and the least-squares
-// matrices with the kernels of lsq_kernels.cuh.  This unit is compiled
+// sectors and their inverses and the inverse Jacobians; the least-squares
+// matrices follow with the kernel of lsq_gpu.cu.  This unit is compiled
 // without FMA contraction, the same arithmetic as the host setup (which
 // remains for cweno_mesh_stencils and for searches beyond the device
-// kernel's per-thread capacity).
+// kernel's per-thread capacity), so that the quantised distance keys and the
+// cone tests pick the host's cells.
 #include "lsq_kernels.cuh"
 
 namespace cw {
@@ -273,9 +274,17 @@ int cell_setup_device(const MeshHost& m, const RefElem& re, int fp32, void* stre
   if (e == cudaSuccess) e = cudaMemcpyAsync(hflags, flags, sizeof(hflags), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   const bool search_ok = e == cudaSuccess && hflags[0] == INT_MAX && hflags[1] == 0;
-  if (search_ok)
-    e = fp32 ? dispatch<float>(d, M, dX, dB, d_sten, N, tab, d_R, flags + 2, st)
-             : dispatch<double>(d, M, dX, dB, d_sten, N, tab, d_R, flags + 2, st);
+  if (search_ok) {
+    const int rc = lsq_launch_device(m, re, dX, dB, d_sten, d_R, fp32, flags + 2, st, err);
+    if (rc != CWENO_OK) {
+      cudaFreeAsync(dX, st);
+      cudaFreeAsync(dB, st);
+      cudaFreeAsync(dN, st);
+      cudaFreeAsync(dP, st);
+      cudaFreeAsync(flags, st);
+      return rc;
+    }
+  }
   if (search_ok && e == cudaSuccess) e = cudaMemcpyAsync(hflags + 2, flags + 2, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (search_ok && e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (dX) cudaFreeAsync(dX, st);
@@ -294,44 +303,6 @@ int cell_setup_device(const MeshHost& m, const RefElem& re, int fp32, void* stre
   }
   if (hflags[2] != INT_MAX) {
     err = "rank-deficient least-squares system at cell " + std::to_string(m.perm[hflags[2]]);
-    return CWENO_EDEGENERATE;
-  }
-  return CWENO_OK;
-}
-
-int lsq_setup_device(const MeshHost& m, const RefElem& re, const int32_t* d_sten, void* d_R, int fp32,
-                     void* stream, std::string& err) {
-  cudaStream_t st = (cudaStream_t)stream;
-  const int d = m.d, M = re.M;
-  const int64_t N = m.nc;
-  LsqTab tab;
-  if (!make_tab(m, re, tab, err)) return CWENO_EINVAL;
-  double* dX = nullptr;
-  double* dB = nullptr;
-  int* dbad = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&dX, sizeof(double) * m.X.size(), st);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&dB, sizeof(double) * m.bary.size(), st);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&dbad, sizeof(int), st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(dX, m.X.data(), sizeof(double) * m.X.size(), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(dB, m.bary.data(), sizeof(double) * m.bary.size(), cudaMemcpyHostToDevice, st);
-  const int big = INT_MAX;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(dbad, &big, sizeof(int), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
-    e = fp32 ? dispatch<float>(d, M, dX, dB, d_sten, N, tab, d_R, dbad, st)
-             : dispatch<double>(d, M, dX, dB, d_sten, N, tab, d_R, dbad, st);
-  int hbad = INT_MAX;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, dbad, sizeof(int), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (dX) cudaFreeAsync(dX, st);
-  if (dB) cudaFreeAsync(dB, st);
-  if (dbad) cudaFreeAsync(dbad, st);
-  if (e != cudaSuccess) {
-    err = std::string("device least-squares setup: ") + cudaGetErrorString(e);
-    return CWENO_ECUDA;
-  }
-  if (hbad != INT_MAX) {
-    err = "rank-deficient least-squares system at cell " + std::to_string(m.perm[hbad]);
     return CWENO_EDEGENERATE;
   }
   return CWENO_OK;

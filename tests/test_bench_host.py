@@ -85,3 +85,45 @@ def test_roofline_picks_the_binding_roof():
     # FP64: the same intensities against the FP64 ridge (1 flop/B) are ALU-bound
     k64, _ = bench.kernel_rooflines({"k_rec_pred": 1.0}, {"rec": 1e6}, alg, pk, fp32=False)
     assert k64["k_rec_pred"]["bound"] == "alu" and "fp64_frac" in k64["k_rec_pred"]
+
+
+class _FakeSolver:
+    """Host stand-in for a solver: forward Euler on dQ/dt = -Q with a CFL
+    step that grows with time, so a step fixed at t = 0 would differ."""
+
+    def __init__(self, noise=0.0):
+        self.noise, self.t, self.Q, self.dts = noise, 0.0, None, []
+
+    def set_state(self, Q):
+        self.Q, self.t = Q.copy(), 0.0
+
+    def step(self, dt):
+        if dt == 0.0:
+            dt = 1e-3 * (1.0 + self.t)
+        self.dts.append(dt)
+        self.Q = self.Q - dt * self.Q * (1.0 + self.noise)
+        self.t += dt
+
+    def time(self):
+        return self.t
+
+    def sync(self):
+        pass
+
+    def get_state(self):
+        return self.Q.copy()
+
+
+def test_accuracy_pair_follows_the_fp64_cfl_steps():
+    import numpy as np
+
+    import bench
+    from paper_1612_09335_gb300 import workloads as wl
+    mesh = wl.tri_mesh(4, jitter=0.1, seed=3)
+    Q0 = np.tile(np.array([1.0, 0.1, -0.2, 2.5]), (mesh.nc, 1))
+    a, b = _FakeSolver(noise=1e-7), _FakeSolver()
+    out = bench.accuracy_pair({"fp32_mixed": a, "fp64": b}, mesh, Q0, nsteps=5)
+    assert a.dts == pytest.approx(b.dts, rel=1e-12) and len(b.dts) == 5 and b.dts[-1] > b.dts[0]
+    assert out["steps"] == 5 and out["dt_mean"] == pytest.approx(np.mean(b.dts))
+    assert max(out["Linf_rel"]) < 1e-8 and max(out["L1_rel"]) < 1e-8
+    assert len(out["conservation_drift_rel"]) == 4
