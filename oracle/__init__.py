@@ -83,6 +83,7 @@ def lib():
             L.orc_ale_predictor.argtypes = [P, dp, D, I, I64, dp, dp, cp, I]
             L.orc_ale_vertex_weights.argtypes = [P, dp]
             L.orc_st_normal.argtypes = [dp, dp, dp, dp, D, D, D, dp]
+            L.orc_st_normal3.argtypes = [dp, dp, dp, dp, dp, dp, D, D, D, D, dp]
             L.orc_mesh_xyz.argtypes = [P, dp]
             _lib = L
     return _lib
@@ -379,4 +380,12 @@ def st_normal(XA0, XB0, XA1, XB1, chi, tau, dt):
     a = [np.ascontiguousarray(x, dtype=np.float64) for x in (XA0, XB0, XA1, XB1)]
     n = np.zeros(3)
     lib().orc_st_normal(_d(a[0]), _d(a[1]), _d(a[2]), _d(a[3]), float(chi), float(tau), float(dt), _d(n))
+    return n
+
+
+def st_normal3(A0, B0, C0, A1, B1, C1, chi1, chi2, tau, dt):
+    """Space-time normal (x, y, z, t) of a moving triangle at (chi1, chi2, tau), Eq. (detChi)."""
+    a = [np.ascontiguousarray(x, dtype=np.float64) for x in (A0, B0, C0, A1, B1, C1)]
+    n = np.zeros(4)
+    lib().orc_st_normal3(*[_d(x) for x in a], float(chi1), float(chi2), float(tau), float(dt), _d(n))
     return n

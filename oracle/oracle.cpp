@@ -2,7 +2,7 @@
 // ORACLE -- test infrastructure only.
 //
 // A plain, slow, FP64 CPU implementation of the fixed-mesh (Eulerian) and
-// the moving-mesh (direct ALE, two dimensions, Euler, Rusanov)
+// the moving-mesh (direct ALE, triangles and tetrahedra, Euler, Rusanov)
 // ADER-CWENO finite-volume steps of Dumbser, Boscheri, Semplice & Russo,
 // "Central WENO schemes on unstructured meshes" (arXiv 1612.09335).
 // It is used only by tests/, by the smoke check and by the CPU-baseline /
@@ -1572,7 +1572,7 @@ void face_points(const OSolver& S, long i, int k, std::vector<std::array<double,
 }
 
 // ============================================================================
-// Moving meshes: the direct ALE step (Secs. 2.2-2.4), two space dimensions,
+// Moving meshes: the direct ALE step (Secs. 2.2-2.4), two and three space dimensions,
 // Euler equations, Rusanov flux with the ALE Jacobian of Eq. (rusanov)
 // ============================================================================
 
@@ -1745,6 +1745,35 @@ void st_normal(const double* XA0, const double* XB0, const double* XA1, const do
   n[2] = r1[0] * r2[1] - r1[1] * r2[0];
 }
 
+// Space-time normal of a lateral face in three space dimensions, Eqs.
+// (BetaBaseFunc)-(detChi): the triangle (A, B, C) at t^n moving on straight
+// lines to (A1, B1, C1) at t^{n+1}, x(chi1, chi2, tau) the map of Eq.
+// (SurfPar) with the bilinear basis beta_1..beta_6 and t = t^n + tau dt.  The
+// rows of the matrix of Eq. (ChiTransf) below the unit vectors are
+// (dx/dchi1, 0), (dx/dchi2, 0) and (dx/dtau, dt); component p of the normal is
+// (-1)^(1+p) times the 3 x 3 minor that deletes column p, (x, y, z, t) order.
+void st_normal3(const double* A0, const double* B0, const double* C0, const double* A1, const double* B1,
+                const double* C1, double c1, double c2, double tau, double dt, double* n) {
+  double r[3][4];
+  for (int a = 0; a < 3; ++a) {
+    r[0][a] = (1.0 - tau) * (B0[a] - A0[a]) + tau * (B1[a] - A1[a]);
+    r[1][a] = (1.0 - tau) * (C0[a] - A0[a]) + tau * (C1[a] - A1[a]);
+    r[2][a] = (1.0 - c1 - c2) * (A1[a] - A0[a]) + c1 * (B1[a] - B0[a]) + c2 * (C1[a] - C0[a]);
+  }
+  r[0][3] = 0.0;
+  r[1][3] = 0.0;
+  r[2][3] = dt;
+  for (int p = 0; p < 4; ++p) {
+    int c[3], k = 0;
+    for (int q = 0; q < 4; ++q)
+      if (q != p) c[k++] = q;
+    const double det = r[0][c[0]] * (r[1][c[1]] * r[2][c[2]] - r[1][c[2]] * r[2][c[1]]) -
+                       r[0][c[1]] * (r[1][c[0]] * r[2][c[2]] - r[1][c[2]] * r[2][c[0]]) +
+                       r[0][c[2]] * (r[1][c[0]] * r[2][c[1]] - r[1][c[1]] * r[2][c[0]]);
+    n[p] = (p % 2 == 0) ? det : -det;
+  }
+}
+
 // Reference coordinates in cell c of the point at parameter chi on the
 // segment from global vertex ga to global vertex gb of that cell: the
 // lateral face (chi, tau) sits at the same reference point at every tau.
@@ -1757,6 +1786,19 @@ void ref_on_edge(const OMesh& m, long c, long ga, long gb, double chi, double* x
     if (k > 0 && g == gb) pb[k - 1] = 1.0;
   }
   for (int a = 0; a < 3; ++a) xi[a] = pa[a] + chi * (pb[a] - pa[a]);
+}
+
+// The same on a triangular face (global vertices ga, gb, gc of cell c) at
+// parameters (chi1, chi2): A + chi1 (B - A) + chi2 (C - A) in cell c's frame.
+void ref_on_face(const OMesh& m, long c, const long* g, double c1, double c2, double* xi) {
+  int d = m.d;
+  double p[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  for (int k = 1; k <= d; ++k) {
+    long gk = m.cells[c * (d + 1) + k];
+    for (int r = 0; r < 3; ++r)
+      if (gk == g[r]) p[r][k - 1] = 1.0;
+  }
+  for (int a = 0; a < 3; ++a) xi[a] = p[0][a] + c1 * (p[1][a] - p[0][a]) + c2 * (p[2][a] - p[0][a]);
 }
 
 // One direct ALE ADER-CWENO step on the solver's current mesh:
@@ -1780,8 +1822,8 @@ void ref_on_edge(const OMesh& m, long c, long ga, long gb, double chi, double* x
 bool ale_step(OSolver& S, const double* Q, double dt, int mode, double* Qnew, double* xyz_new, std::string& err) {
   OMesh& m = *S.mesh;
   int d = m.d, nu = S.nu, L = S.Lc, M = S.M;
-  if (d != 2 || S.pde != PDE_EULER || S.P.flux != 0) {
-    err = "moving meshes: two dimensions, Euler equations, Rusanov flux";
+  if (S.pde != PDE_EULER || S.P.flux != 0) {
+    err = "moving meshes: Euler equations, Rusanov flux";
     return false;
   }
   std::vector<std::vector<double>> pred(m.nc), Vh(m.nc);
@@ -1815,34 +1857,70 @@ bool ale_step(OSolver& S, const double* Q, double dt, int mode, double* Qnew, do
     err = "moving mesh: " + err;
     return false;
   }
+  // lateral-face rule in (chi) or (chi1, chi2): Gauss-Legendre with M + 1
+  // points on the segment; on the triangle the collapsed product chi1 =
+  // s (1 - r), chi2 = r of M + 1 Gauss-Legendre points s and M + 1
+  // Gauss-Jacobi points r (weight 1 - r), weights times 1/2, the area of the
+  // reference triangle (exact to degree 2M + 1); Gauss-Legendre in tau.
   std::vector<double> gx, gw;
   gauss_legendre01(M + 1, gx, gw);
+  std::vector<std::array<double, 2>> fchi;
+  std::vector<double> fw;
+  if (d == 2) {
+    for (int q = 0; q <= M; ++q) {
+      fchi.push_back({gx[q], 0.0});
+      fw.push_back(gw[q]);
+    }
+  } else {
+    std::vector<double> jx, jw;
+    gauss_jacobi10_01(M + 1, jx, jw);
+    for (int a = 0; a <= M; ++a)
+      for (int b = 0; b <= M; ++b) {
+        fchi.push_back({gx[a] * (1.0 - jx[b]), jx[b]});
+        fw.push_back(0.5 * gw[a] * jw[b]);
+      }
+  }
   std::vector<double> qm(nu), qp(nu), f(nu), g(nu);
   for (long i = 0; i < m.nc; ++i) {
     std::vector<double> accq(nu, 0.0);
     for (int k = 0; k <= d; ++k) {
       long j = m.nbr[i * (d + 1) + k];
-      // face vertices (local a, b of cell i), A the lower global id
-      int la = (k + 1) % 3, lb = (k + 2) % 3;
-      long ga = m.cells[i * (d + 1) + la], gb = m.cells[i * (d + 1) + lb];
-      if (ga > gb) {
-        std::swap(ga, gb);
-        std::swap(la, lb);
-      }
-      const double XA0[2] = {vx(m, i, la, 0), vx(m, i, la, 1)}, XB0[2] = {vx(m, i, lb, 0), vx(m, i, lb, 1)};
-      const double XA1[2] = {vx(m1, i, la, 0), vx(m1, i, la, 1)}, XB1[2] = {vx(m1, i, lb, 0), vx(m1, i, lb, 1)};
+      // face vertices: the cell's local vertices other than k, ordered by
+      // global id so that both sides parametrise the face alike
+      std::vector<std::pair<long, int>> fv;
+      for (int q = 0; q <= d; ++q)
+        if (q != k) fv.push_back({m.cells[i * (d + 1) + q], q});
+      std::sort(fv.begin(), fv.end());
+      long gf[3] = {fv[0].first, fv[1].first, d == 3 ? fv[2].first : -1};
+      double P0[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, P1[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+      for (int r = 0; r < d; ++r)
+        for (int a = 0; a < d; ++a) {
+          P0[r][a] = vx(m, i, fv[r].second, a);
+          P1[r][a] = vx(m1, i, fv[r].second, a);
+        }
+      auto normal = [&](double c1, double c2, double tau, double* n) {
+        if (d == 2) st_normal(P0[0], P0[1], P1[0], P1[1], c1, tau, dt, n);
+        else st_normal3(P0[0], P0[1], P0[2], P1[0], P1[1], P1[2], c1, c2, tau, dt, n);
+      };
       // outward orientation from cell i at t^n
-      double n0[3];
-      st_normal(XA0, XB0, XA1, XB1, 0.0, 0.0, dt, n0);
-      double sgn = n0[0] * (XA0[0] - m.bary[i * 3]) + n0[1] * (XA0[1] - m.bary[i * 3 + 1]) > 0 ? 1.0 : -1.0;
-      for (int q = 0; q <= M; ++q) {
+      double n0[4];
+      normal(0.0, 0.0, 0.0, n0);
+      double dot = 0.0;
+      for (int a = 0; a < d; ++a) dot += n0[a] * (P0[0][a] - m.bary[i * 3 + a]);
+      const double sgn = dot > 0 ? 1.0 : -1.0;
+      for (size_t q = 0; q < fchi.size(); ++q) {
         double xi_i[3], xi_j[3];
-        ref_on_edge(m, i, ga, gb, gx[q], xi_i);
-        if (j >= 0) ref_on_edge(m, j, ga, gb, gx[q], xi_j);
+        if (d == 2) {
+          ref_on_edge(m, i, gf[0], gf[1], fchi[q][0], xi_i);
+          if (j >= 0) ref_on_edge(m, j, gf[0], gf[1], fchi[q][0], xi_j);
+        } else {
+          ref_on_face(m, i, gf, fchi[q][0], fchi[q][1], xi_i);
+          if (j >= 0) ref_on_face(m, j, gf, fchi[q][0], fchi[q][1], xi_j);
+        }
         for (int t = 0; t <= M; ++t) {
-          double nt[3];
-          st_normal(XA0, XB0, XA1, XB1, gx[q], gx[t], dt, nt);
-          for (int a = 0; a < 3; ++a) nt[a] *= sgn;
+          double nt[4];
+          normal(fchi[q][0], fchi[q][1], gx[t], nt);
+          for (int a = 0; a <= d; ++a) nt[a] *= sgn;
           double xt[4] = {xi_i[0], xi_i[1], xi_i[2], gx[t]};
           eval_qh(S, pred[i], xt, qm.data());
           if (j >= 0) {
@@ -1857,12 +1935,17 @@ bool ale_step(OSolver& S, const double* Q, double dt, int mode, double* Qnew, do
             if (!(qp[0] > 0.0 && pressure(S.pde, d, S.P, qp.data()) > 0.0))
               for (int v = 0; v < nu; ++v) qp[v] = j >= 0 ? Q[j * nu + v] : Q[i * nu + v];
           }
-          double nx = std::sqrt(nt[0] * nt[0] + nt[1] * nt[1]);
-          double un[2] = {nt[0] / nx, nt[1] / nx};
-          double Vn = -nt[2] / nx;
+          double nx = 0.0;
+          for (int a = 0; a < d; ++a) nx += nt[a] * nt[a];
+          nx = std::sqrt(nx);
+          double un[3] = {0, 0, 0};
+          for (int a = 0; a < d; ++a) un[a] = nt[a] / nx;
+          double Vn = -nt[d] / nx;
           double sm = 0.0;
           for (const double* qs : {qm.data(), qp.data()}) {
-            double vn = (qs[1] * un[0] + qs[2] * un[1]) / qs[0];
+            double vn = 0.0;
+            for (int a = 0; a < d; ++a) vn += qs[1 + a] * un[a];
+            vn /= qs[0];
             double c = max_speed_normal(S.pde, d, S.P, qs, un) - std::fabs(vn);  // sound speed
             sm = std::max(sm, std::fabs(vn - Vn) + c);
           }
@@ -1873,8 +1956,8 @@ bool ale_step(OSolver& S, const double* Q, double dt, int mode, double* Qnew, do
             flux(S.pde, d, S.P, qp.data(), mm, g.data());
             for (int v = 0; v < nu; ++v) G[v] += 0.5 * (f[v] + g[v]) * nt[mm];
           }
-          for (int v = 0; v < nu; ++v) G[v] += 0.5 * (qm[v] + qp[v]) * nt[2] - 0.5 * sm * (qp[v] - qm[v]);
-          for (int v = 0; v < nu; ++v) accq[v] += gw[q] * gw[t] * G[v];
+          for (int v = 0; v < nu; ++v) G[v] += 0.5 * (qm[v] + qp[v]) * nt[d] - 0.5 * sm * (qp[v] - qm[v]);
+          for (int v = 0; v < nu; ++v) accq[v] += fw[q] * gw[t] * G[v];
         }
       }
     }
@@ -2342,7 +2425,7 @@ int orc_face_points(void* p, int64_t cell, int k, double* pts, double* wts, doub
 }
 
 
-// Direct ALE step (two dimensions, Euler, Rusanov): Qnew (nc x nu) and the
+// Direct ALE step (Euler, Rusanov): Qnew (nc x nu) and the
 // new vertex positions xyz_new (nv x d); the oracle's mesh is then moved to
 // them (stencils fixed, matrices rebuilt).  mode: 1 V = v, 2 V = 0.
 int orc_ale_step(void* p, const double* Q, double dt, int mode, double* Qnew, double* xyz_new, char* err,
@@ -2389,6 +2472,13 @@ int orc_ale_vertex_weights(void* p, double* W) {
 int orc_st_normal(const double* XA0, const double* XB0, const double* XA1, const double* XB1, double chi,
                   double tau, double dt, double* n) {
   st_normal(XA0, XB0, XA1, XB1, chi, tau, dt, n);
+  return 0;
+}
+
+// Space-time normal (x, y, z, t) of a moving triangle, Eq. (detChi), d = 3.
+int orc_st_normal3(const double* A0, const double* B0, const double* C0, const double* A1, const double* B1,
+                   const double* C1, double c1, double c2, double tau, double dt, double* n) {
+  st_normal3(A0, B0, C0, A1, B1, C1, c1, c2, tau, dt, n);
   return 0;
 }
 
