@@ -1,5 +1,5 @@
 // Moving meshes: the direct ALE ADER-CWENO step (Secs. 2.2-2.4) on 2D
-// triangle meshes, Euler equations, FP64 or FP32-mixed (k_ale_pred32,
+// triangle meshes (tetrahedra: ale3.cuh, FP64), Euler equations, FP64 or FP32-mixed (k_ale_pred32,
 // k_ale_flux32: FP32 deviations, FP64 least squares, averages' face part,
 // nodal solver and update), Rusanov flux with the ALE Jacobian.  Mesh velocity V = v (the local fluid velocity, the choice of the
 // paper's moving-mesh tests) or V = 0 (the same machinery on a mesh that does
@@ -809,12 +809,16 @@ __global__ void __launch_bounds__(256) k_ale_update(const int32_t* __restrict__ 
 
 }  // namespace
 
+#include "ale3.cuh"
+
 // ---------------------------------------------------------------- host side
 struct Ale {
+  int d = 2;
   int M = 1;
   MeshHost slim;  // d, nc, periodicity: what the device matrices refresh reads
   int64_t nvert = 0;
   AleTab tab;
+  AleTab3 tab3;  // tetrahedra
   double *Xv = nullptr, *Xv1 = nullptr, *shift = nullptr, *X = nullptr, *bary = nullptr, *vol = nullptr;
   double *w = nullptr, *qhat = nullptr, *vcon = nullptr, *G = nullptr, *ftab = nullptr;
   // FP32-mixed: tables, face basis and predictor deviations in FP32
@@ -912,13 +916,26 @@ int ale_matrices_device(const MeshHost& m, const RefElem& re, const double* d_X,
         break;
       default: e = cudaErrorInvalidValue;
     }
+  } else if (e == cudaSuccess && m.d == 3) {
+    switch (re.M) {
+      case 1: e = fp32 ? launch_sectors<3, 1, float>(d_X, d_bary, d_sec, m.nc, tab, (float*)d_Binv, d_bad, st)
+                       : launch_sectors<3, 1, double>(d_X, d_bary, d_sec, m.nc, tab, (double*)d_Binv, d_bad, st);
+        break;
+      case 2: e = fp32 ? launch_sectors<3, 2, float>(d_X, d_bary, d_sec, m.nc, tab, (float*)d_Binv, d_bad, st)
+                       : launch_sectors<3, 2, double>(d_X, d_bary, d_sec, m.nc, tab, (double*)d_Binv, d_bad, st);
+        break;
+      default: e = cudaErrorInvalidValue;
+    }
   } else if (e == cudaSuccess) {
     e = cudaErrorInvalidValue;
   }
   return e == cudaSuccess ? CWENO_OK : CWENO_ECUDA;
 }
 
+int ale_create3(cweno_solver* s, const MeshHost& m, std::string& err);
+
 int ale_create(cweno_solver* s, const MeshHost& m, std::string& err) {
+  if (m.d == 3) return ale_create3(s, m, err);
   const RefElem& re = *s->re;
   if (m.d != 2 || s->pde != CWENO_EULER || re.M > 3 || s->prm.flux != CWENO_FLUX_RUSANOV) {
     err = "moving meshes are built for 2D Euler, order 2..4, Rusanov flux";
@@ -1035,13 +1052,137 @@ int ale_create(cweno_solver* s, const MeshHost& m, std::string& err) {
   return CWENO_OK;
 }
 
+// Tetrahedra (FP64, M = 1, 2): tables, vertex incidence, periodic shifts and
+// scratch of the moving mesh.
+int ale_create3(cweno_solver* s, const MeshHost& m, std::string& err) {
+  const RefElem& re = *s->re;
+  if (s->pde != CWENO_EULER || re.M < 1 || re.M > 2 || s->prm.flux != CWENO_FLUX_RUSANOV) {
+    err = "moving tetrahedral meshes are built for Euler, order 2..3, Rusanov flux";
+    return CWENO_EINVAL;
+  }
+  if (s->prec != CWENO_FP64) {
+    err = "moving tetrahedral meshes run in FP64";
+    return CWENO_EINVAL;
+  }
+  auto A = std::make_shared<Ale>();
+  cudaStream_t st = s->stream;
+  const int64_t N = m.nc, nv = m.nv;
+  const int L = re.L, L0 = re.L0, L1 = re.L1;
+  if (L > kL3 || L0 > kL03 || L1 > kL13 || re.nqs > kNQS3 || re.nqt > kNQT3) {
+    err = "moving tetrahedral mesh tables exceed their fixed sizes";
+    return CWENO_EINVAL;
+  }
+  A->d = 3;
+  A->M = re.M;
+  A->nvert = nv;
+  A->slim.d = 3;
+  A->slim.nc = N;
+  for (int a = 0; a < 3; ++a) {
+    A->slim.per[a] = m.per[a];
+    A->slim.Lper[a] = m.Lper[a];
+  }
+  AleTab3& t = A->tab3;
+  std::memset(&t, 0, sizeof(t));
+  {
+    double dmax = 0.0;
+    for (double v : re.Dxi) dmax = std::max(dmax, std::fabs(v));
+    for (int e = 0; e < 3; ++e)
+      for (int n = 0; n < L; ++n) {
+        int c = 0;
+        for (int l = 0; l < L; ++l) {
+          const double v = re.Dxi[((size_t)e * L + n) * L + l];
+          if (std::fabs(v) <= 1e-12 * dmax) continue;  // exact zeros, rounded in extended precision
+          t.val[e][n][c] = v;
+          t.col[e][n][c] = (uint8_t)l;
+          ++c;
+          if (l < L0) t.nnz0[e][n] = c;  // columns ascend: tau = 0 nodes first
+        }
+        t.nnz[e][n] = c;
+      }
+  }
+  for (int k = 0; k < L1; ++k) {
+    for (int l = 0; l < L; ++l) t.Gal[k][l] = re.Gal[(size_t)k * L + l];
+    for (int n = 0; n < L0; ++n) t.C0[k][n] = re.C0[(size_t)k * L0 + n];
+  }
+  for (int v = 0; v < 4; ++v)
+    for (int l = 0; l < L; ++l) t.Wv[v][l] = re.Wv[(size_t)v * L + l];
+  for (int l = 0; l < L; ++l)
+    for (int a = 0; a < 4; ++a) t.node[l][a] = re.stnode[l][a];
+  for (int q = 0; q < re.nqs; ++q) {
+    t.chi[q][0] = re.chi3[2 * q];
+    t.chi[q][1] = re.chi3[2 * q + 1];
+    t.wq[q] = re.wq[q];
+  }
+  for (int q = 0; q < re.nqt; ++q) {
+    t.wt[q] = re.wt[q];
+    t.tq[q] = re.tq[q];
+  }
+  t.gamma = s->prm.gamma;
+  t.mode = s->prm.mesh_motion;
+  t.pos = s->prm.positivity;
+  // per-cell global vertices and periodic image shifts (image nearest the
+  // cell's first vertex), SoA
+  std::vector<int32_t> gv((size_t)4 * N);
+  std::vector<double> sh((size_t)12 * N, 0.0);
+  for (int64_t i = 0; i < N; ++i) {
+    const int64_t g0 = m.gv[i * 4];
+    for (int k = 0; k < 4; ++k) {
+      const int64_t g = m.gv[i * 4 + k];
+      gv[(size_t)k * N + i] = (int32_t)g;
+      for (int a = 0; a < 3; ++a)
+        if (m.per[a] && k > 0)
+          sh[(size_t)(k * 3 + a) * N + i] = m.Lper[a] * std::nearbyint((m.xyz[g0 * 3 + a] - m.xyz[g * 3 + a]) / m.Lper[a]);
+    }
+  }
+  // vertex -> (cell, local vertex) incidence, cells in increasing caller order
+  std::vector<int32_t> start(nv + 1, 0), ent((size_t)4 * N);
+  for (int64_t i = 0; i < N; ++i)
+    for (int k = 0; k < 4; ++k) ++start[m.gv[i * 4 + k] + 1];
+  for (int64_t g = 0; g < nv; ++g) start[g + 1] += start[g];
+  {
+    std::vector<int32_t> fill(start.begin(), start.end() - 1);
+    for (int64_t u = 0; u < N; ++u) {
+      const int64_t i = m.iperm[u];
+      for (int k = 0; k < 4; ++k) ent[fill[m.gv[i * 4 + k]]++] = (int32_t)(i * 4 + k);
+    }
+  }
+  std::vector<int32_t> ident(N);
+  std::iota(ident.begin(), ident.end(), 0);
+  ACK(A->put(&A->gv, gv, st));
+  ACK(A->put(&A->shift, sh, st));
+  ACK(A->put(&A->start, start, st));
+  ACK(A->put(&A->ent, ent, st));
+  ACK(A->put(&A->ident, ident, st));
+  ACK(A->put(&A->Xv, m.xyz, st));
+  ACK(A->put(&A->ftab, re.ftab, st));
+  ACK(A->alloc(&A->Xv1, (size_t)nv * 3, st));
+  ACK(A->alloc(&A->X, (size_t)N * 12, st));
+  ACK(A->alloc(&A->bary, (size_t)N * 3, st));
+  ACK(A->alloc(&A->vol, (size_t)N, st));
+  ACK(A->alloc(&A->w, (size_t)N * L0 * 5, st));
+  ACK(A->alloc(&A->qhat, (size_t)N * L * 5, st));
+  ACK(A->alloc(&A->vcon, (size_t)N * 16, st));
+  ACK(A->alloc(&A->G, (size_t)5 * m.nf, st));
+  ACK(A->alloc(&A->bad, 1, st));
+  const int big = 0x7fffffff;
+  ACK(cudaMemcpyAsync(A->bad, &big, sizeof(int), cudaMemcpyHostToDevice, st));
+  ACK(cudaStreamSynchronize(st));
+  s->bytes += A->bytes;
+  s->ale = A;
+  return CWENO_OK;
+}
+
 int ale_refresh(cweno_solver* s) {
   Ale& A = *s->ale;
   if (A.fresh) return CWENO_OK;
   DevState& ds = s->ds;
   cudaStream_t st = s->stream;
-  k_ale_geom<<<nblk(ds.N, 256), 256, 0, st>>>(A.Xv, A.gv, A.shift, ds.N, A.X, A.bary, A.vol,
-                                               const_cast<double*>(ds.hsize), const_cast<double*>(ds.invvol));
+  if (A.d == 3)
+    k_ale_geom3<<<nblk(ds.N, 256), 256, 0, st>>>(A.Xv, A.gv, A.shift, ds.N, A.X, A.bary, A.vol,
+                                                  const_cast<double*>(ds.hsize), const_cast<double*>(ds.invvol));
+  else
+    k_ale_geom<<<nblk(ds.N, 256), 256, 0, st>>>(A.Xv, A.gv, A.shift, ds.N, A.X, A.bary, A.vol,
+                                                 const_cast<double*>(ds.hsize), const_cast<double*>(ds.invvol));
   ACK(cudaGetLastError());
   int rc = ale_matrices_device(A.slim, *s->re, A.X, A.bary, ds.sten, ds.sec, const_cast<void*>(ds.R),
                                const_cast<void*>(ds.Binv), A.fp32, A.bad, st);
@@ -1065,6 +1206,34 @@ int ale_step(cweno_solver* s, double dt) {
   DevState d2 = ds;
   d2.perm = A.ident;  // reconstruction values in internal cell order
   ACK(s->ops->reconstruct(d2, s->ph, A.w, st));
+  if (A.d == 3) {
+    if (A.M == 1)
+      k_ale_pred3<1><<<nblk(ds.N, 128), 128, 0, st>>>(A.tab3, A.w, ds.Q, A.X, A.vol, ds.N, s->ph.niter, dtf,
+                                                       s->prm.cfl, ds.dtmin, A.qhat, A.vcon);
+    else
+      k_ale_pred3<2><<<nblk(ds.N, 128), 128, 0, st>>>(A.tab3, A.w, ds.Q, A.X, A.vol, ds.N, s->ph.niter, dtf,
+                                                       s->prm.cfl, ds.dtmin, A.qhat, A.vcon);
+    ACK(cudaGetLastError());
+    k_ale_nodes3<<<nblk(A.nvert, 256), 256, 0, st>>>(A.start, A.ent, A.vcon, A.Xv, A.nvert, dtf, s->prm.cfl,
+                                                      ds.dtmin, A.Xv1);
+    ACK(cudaGetLastError());
+    if (A.M == 1)
+      k_ale_flux3<1><<<nblk(ds.F, 128), 128, 0, st>>>(A.tab3, A.ftab, ds.fL, ds.fR, ds.codeL, ds.codeR, A.gv,
+                                                       A.shift, A.Xv, A.Xv1, A.bary, A.qhat, ds.Q, ds.N, ds.F, dtf,
+                                                       s->prm.cfl, ds.dtmin, A.G);
+    else
+      k_ale_flux3<2><<<nblk(ds.F, 128), 128, 0, st>>>(A.tab3, A.ftab, ds.fL, ds.fR, ds.codeL, ds.codeR, A.gv,
+                                                       A.shift, A.Xv, A.Xv1, A.bary, A.qhat, ds.Q, ds.N, ds.F, dtf,
+                                                       s->prm.cfl, ds.dtmin, A.G);
+    ACK(cudaGetLastError());
+    k_ale_update3<<<nblk(ds.N, 256), 256, 0, st>>>(ds.cellface, A.G, A.gv, A.shift, A.Xv1, A.vol, ds.N, ds.F,
+                                                    s->prm.gamma, dtf, s->prm.cfl, ds.dtmin, ds.Q, ds.time,
+                                                    ds.status);
+    ACK(cudaGetLastError());
+    std::swap(A.Xv, A.Xv1);
+    A.fresh = false;
+    return CWENO_OK;
+  }
   switch (A.M) {
     case 1: ACK(launch_pred<1>(A, s, dtf, st)); break;
     case 2: ACK(launch_pred<2>(A, s, dtf, st)); break;
@@ -1089,7 +1258,7 @@ int ale_step(cweno_solver* s, double dt) {
 
 int ale_vertices(cweno_solver* s, double* xyz, int on_device) {
   Ale& A = *s->ale;
-  ACK(cudaMemcpyAsync(xyz, A.Xv, sizeof(double) * A.nvert * 2,
+  ACK(cudaMemcpyAsync(xyz, A.Xv, sizeof(double) * A.nvert * A.d,
                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream));
   ACK(cudaStreamSynchronize(s->stream));
   return CWENO_OK;

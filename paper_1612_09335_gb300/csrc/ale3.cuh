@@ -1,0 +1,439 @@
+// Moving meshes in three space dimensions: the direct ALE step (Secs.
+// 2.2-2.4) on tetrahedra, Euler equations, FP64, orders 2 and 3 (M = 1, 2),
+// Rusanov flux with the ALE Jacobian.  The same step as the triangle path of
+// ale.cu, kernel for kernel:
+//   k_ale_geom3    unwrapped vertices, |T|, barycentre, h = 6|T| / surface
+//                  (insphere diameter, Eq. timestep), 1/|T|;
+//   k_ale_pred3    space-time predictor of the moving tetrahedron: state and
+//                  geometry DOFs iterated together (Eqs. CGfinal, ODEfinal),
+//                  H of Eq. (Hterm) from the nodal xi-derivatives with the
+//                  3 x 3 inverse of d x / d xi at every node;
+//   k_ale_nodes3   nodal solver, Eqs. (NScs)-(newX);
+//   k_ale_flux3    lateral space-time faces: a triangle (A, B, C) moving on
+//                  straight lines, x(chi1, chi2, tau) of Eq. (SurfPar) with
+//                  the bilinear basis of Eq. (BetaBaseFunc), its normal the
+//                  cofactors of the 4 x 4 matrix of Eq. (ChiTransf) (Eq.
+//                  detChi); the face rule of the fixed-mesh kernels (collapsed
+//                  Gauss on the triangle, weights normalised to 1, times the
+//                  reference area 1/2) and Gauss-Legendre in tau;
+//   k_ale_update3  Eq. (PDEfinal) with the new volume of the moved vertices.
+// Included by ale.cu (shares its unnamed-namespace helpers).
+
+constexpr int kL3 = 15, kL03 = 10, kL13 = 5, kNQS3 = 9, kNQT3 = 3;
+
+// Reference tables of one M (tetrahedra), a kernel parameter.
+struct AleTab3 {
+  // d theta_l / d xi_e at node n, nonzero entries only, tau = 0 columns first
+  double val[3][kL3][kL3];
+  uint8_t col[3][kL3][kL3];
+  int nnz[3][kL3];
+  int nnz0[3][kL3];
+  double Gal[kL13][kL3];  // (K_tau^1)^-1 M^1
+  double C0[kL13][kL03];  // constant extension in time
+  double Wv[4][kL3];      // int_0^1 theta_l(vertex v, tau) dtau
+  double node[kL3][4];    // xi, eta, zeta, tau
+  double chi[kNQS3][2], wq[kNQS3], wt[kNQT3], tq[kNQT3];
+  double gamma;
+  int mode;
+  int pos;
+};
+
+namespace {
+
+__host__ __device__ constexpr int lcal3(int M) { return (M + 1) * (M + 2) * (M + 3) * (M + 4) / 24; }
+__host__ __device__ constexpr int mcal3(int M) { return (M + 1) * (M + 2) * (M + 3) / 6; }
+
+__device__ __forceinline__ double pressure3(const double* q, double g) {
+  return (g - 1.0) * (q[4] - 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / q[0]);
+}
+
+__device__ __forceinline__ bool admissible3(const double* q, double g) {
+  bool fin = true;
+  for (int v = 0; v < 5; ++v) fin = fin && isfinite(q[v]);
+  return fin && q[0] > 0.0 && pressure3(q, g) > 0.0;
+}
+
+__device__ __forceinline__ double det3(const double* a, const double* b, const double* c) {
+  return a[0] * (b[1] * c[2] - b[2] * c[1]) - a[1] * (b[0] * c[2] - b[2] * c[0]) + a[2] * (b[0] * c[1] - b[1] * c[0]);
+}
+
+// ---------------------------------------------------------------- geometry
+__global__ void __launch_bounds__(256) k_ale_geom3(const double* __restrict__ Xv, const int32_t* __restrict__ gv,
+                                                   const double* __restrict__ shift, int64_t N, double* __restrict__ X,
+                                                   double* __restrict__ bary, double* __restrict__ vol,
+                                                   double* __restrict__ hsize, double* __restrict__ invvol) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double P[4][3];
+  for (int k = 0; k < 4; ++k) {
+    const int64_t g = gv[k * N + i];
+    for (int a = 0; a < 3; ++a) {
+      P[k][a] = Xv[g * 3 + a] + shift[(k * 3 + a) * N + i];
+      X[i * 12 + k * 3 + a] = P[k][a];
+    }
+  }
+  double e[3][3];
+  for (int k = 0; k < 3; ++k)
+    for (int a = 0; a < 3; ++a) e[k][a] = P[k + 1][a] - P[0][a];
+  const double v = det3(e[0], e[1], e[2]) / 6.0;
+  double surf = 0.0;
+  for (int k = 0; k < 4; ++k) {
+    int o[3], n = 0;
+    for (int q = 0; q < 4; ++q)
+      if (q != k) o[n++] = q;
+    double u[3], w[3];
+    for (int a = 0; a < 3; ++a) {
+      u[a] = P[o[1]][a] - P[o[0]][a];
+      w[a] = P[o[2]][a] - P[o[0]][a];
+    }
+    const double cx = u[1] * w[2] - u[2] * w[1], cy = u[2] * w[0] - u[0] * w[2], cz = u[0] * w[1] - u[1] * w[0];
+    surf += 0.5 * sqrt(cx * cx + cy * cy + cz * cz);
+  }
+  vol[i] = v;
+  hsize[i] = 6.0 * v / surf;
+  invvol[i] = 1.0 / v;
+  for (int a = 0; a < 3; ++a) bary[i * 3 + a] = (P[0][a] + P[1][a] + P[2][a] + P[3][a]) / 4.0;
+}
+
+// ---------------------------------------------------------------- predictor
+// Euler fluxes (x, y, z) and the mesh velocity of one nodal state.
+__device__ __forceinline__ void ale_flux3(const double* q, double gamma, int mode, double F[3][5], double V[3]) {
+  const double ir = 1.0 / q[0];
+  const double u[3] = {q[1] * ir, q[2] * ir, q[3] * ir};
+  const double p = (gamma - 1.0) * (q[4] - 0.5 * (q[1] * u[0] + q[2] * u[1] + q[3] * u[2]));
+  for (int m = 0; m < 3; ++m) {
+    F[m][0] = q[1 + m];
+    for (int b = 0; b < 3; ++b) F[m][1 + b] = q[1 + b] * u[m] + (b == m ? p : 0.0);
+    F[m][4] = u[m] * (q[4] + p);
+    V[m] = mode == CWENO_MOTION_LAGRANGE ? u[m] : 0.0;
+  }
+}
+
+// One thread per cell.  w: reconstruction values at the lattice nodes
+// (N x L0 x 5); X: unwrapped vertices of T_i^n (N x 4 x 3).  Writes q_hat
+// (N x L x 5) and, per vertex k of the cell, (mu V_kj, mu) with mu =
+// rho_j |T_j| (N x 4 x 4).
+template <int M>
+__global__ void __launch_bounds__(128) k_ale_pred3(const __grid_constant__ AleTab3 t, const double* __restrict__ w,
+                                                   const double* __restrict__ Q, const double* __restrict__ X,
+                                                   const double* __restrict__ vol, int64_t N, int niter,
+                                                   double dt_fixed, double cfl, const unsigned long long* dtmin,
+                                                   double* __restrict__ qhat, double* __restrict__ vcon) {
+  constexpr int L = lcal3(M), L0 = mcal3(M), L1 = L - L0, NC = 3 + 5 + 15;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double dt = step_dt(dt_fixed, cfl, dtmin);
+  double q[L][5], x[L][3], V[L][3];
+  for (int n = 0; n < L0; ++n)
+    for (int v = 0; v < 5; ++v) q[n][v] = w[(i * L0 + n) * 5 + v];
+  for (int k = 0; k < L1; ++k)
+    for (int v = 0; v < 5; ++v) {
+      double s = 0.0;
+      for (int n = 0; n < L0; ++n) s += t.C0[k][n] * q[n][v];
+      q[L0 + k][v] = s;
+    }
+  const double* Xi = X + i * 12;
+  for (int l = 0; l < L; ++l)
+    for (int a = 0; a < 3; ++a)
+      x[l][a] = Xi[a] + (Xi[3 + a] - Xi[a]) * t.node[l][0] + (Xi[6 + a] - Xi[a]) * t.node[l][1] +
+                (Xi[9 + a] - Xi[a]) * t.node[l][2];
+  double qe[L1][5], xe[L1][3];
+  for (int k = 0; k < L1; ++k) {
+    for (int v = 0; v < 5; ++v) qe[k][v] = q[L0 + k][v];
+    for (int a = 0; a < 3; ++a) xe[k][a] = x[L0 + k][a];
+  }
+  // the tau = 0 nodes never change: their part of every xi-derivative of x,
+  // q and F is formed once (per node and direction: 3 + 5 + 3 x 5 sums)
+  double c0[L][3][NC];
+  {
+    double F0[L0][3][5];
+    for (int l = 0; l < L0; ++l) ale_flux3(q[l], t.gamma, t.mode, F0[l], V[l]);
+    for (int n = 0; n < L; ++n)
+      for (int e = 0; e < 3; ++e) {
+        double* c = c0[n][e];
+        for (int m = 0; m < NC; ++m) c[m] = 0.0;
+        for (int j = 0; j < t.nnz0[e][n]; ++j) {
+          const int l = t.col[e][n][j];
+          const double dd = t.val[e][n][j];
+          for (int a = 0; a < 3; ++a) c[a] += dd * x[l][a];
+          for (int v = 0; v < 5; ++v) {
+            c[3 + v] += dd * q[l][v];
+            for (int m = 0; m < 3; ++m) c[8 + m * 5 + v] += dd * F0[l][m][v];
+          }
+        }
+      }
+  }
+  for (int it = 0; it < niter; ++it) {
+    double F[L1][3][5];
+    for (int l = L0; l < L; ++l) ale_flux3(q[l], t.gamma, t.mode, F[l - L0], V[l]);
+    double H[L][5];
+    for (int n = 0; n < L; ++n) {
+      double dx[3][3], dq[3][5], df[3][3][5];
+      for (int e = 0; e < 3; ++e) {
+        const double* c = c0[n][e];
+        for (int a = 0; a < 3; ++a) dx[e][a] = c[a];
+        for (int v = 0; v < 5; ++v) {
+          dq[e][v] = c[3 + v];
+          for (int m = 0; m < 3; ++m) df[e][m][v] = c[8 + m * 5 + v];
+        }
+        const int cnt = t.nnz[e][n];
+        for (int j = t.nnz0[e][n]; j < cnt; ++j) {
+          const int l = t.col[e][n][j];
+          const double dd = t.val[e][n][j];
+          for (int a = 0; a < 3; ++a) dx[e][a] += dd * x[l][a];
+          for (int v = 0; v < 5; ++v) {
+            dq[e][v] += dd * q[l][v];
+            for (int m = 0; m < 3; ++m) df[e][m][v] += dd * F[l - L0][m][v];
+          }
+        }
+      }
+      // J[a][e] = d x_a / d xi_e = dx[e][a]; Ji[e][a] = d xi_e / d x_a by
+      // cofactors: row e of J^-1 is (dx[e+1] x dx[e+2]) / det
+      const double det = det3(dx[0], dx[1], dx[2]), idet = 1.0 / det;
+      double Ji[3][3];
+      for (int e = 0; e < 3; ++e) {
+        const double* p = dx[(e + 1) % 3];
+        const double* r = dx[(e + 2) % 3];
+        Ji[e][0] = (p[1] * r[2] - p[2] * r[1]) * idet;
+        Ji[e][1] = (p[2] * r[0] - p[0] * r[2]) * idet;
+        Ji[e][2] = (p[0] * r[1] - p[1] * r[0]) * idet;
+      }
+      double dxidt[3];
+      for (int e = 0; e < 3; ++e) dxidt[e] = -(Ji[e][0] * V[n][0] + Ji[e][1] * V[n][1] + Ji[e][2] * V[n][2]);
+      for (int v = 0; v < 5; ++v) {
+        double h = 0.0;
+        for (int e = 0; e < 3; ++e)
+          h += dq[e][v] * dxidt[e] + Ji[e][0] * df[e][0][v] + Ji[e][1] * df[e][1][v] + Ji[e][2] * df[e][2][v];
+        H[n][v] = h;
+      }
+    }
+    for (int k = 0; k < L1; ++k) {
+      for (int v = 0; v < 5; ++v) {
+        double g = 0.0;
+        for (int l = 0; l < L; ++l) g += t.Gal[k][l] * H[l][v];
+        q[L0 + k][v] = qe[k][v] - dt * g;
+      }
+      for (int a = 0; a < 3; ++a) {
+        double g = 0.0;
+        for (int l = 0; l < L; ++l) g += t.Gal[k][l] * V[l][a];
+        x[L0 + k][a] = xe[k][a] + dt * g;
+      }
+    }
+  }
+  double qb[5];
+  for (int v = 0; v < 5; ++v) qb[v] = Q[v * N + i];
+  if (t.pos) {
+    bool ok = true;
+    for (int l = L0; l < L; ++l) ok = ok && admissible3(q[l], t.gamma);
+    if (!ok)
+      for (int l = 0; l < L; ++l)
+        for (int v = 0; v < 5; ++v) q[l][v] = qb[v];
+  }
+  for (int l = 0; l < L; ++l) {
+    for (int v = 0; v < 5; ++v) qhat[(i * L + l) * 5 + v] = q[l][v];
+    const double ir = 1.0 / q[l][0];
+    for (int a = 0; a < 3; ++a) V[l][a] = t.mode == CWENO_MOTION_LAGRANGE ? q[l][1 + a] * ir : 0.0;
+  }
+  const double mu = qb[0] * vol[i];
+  for (int k = 0; k < 4; ++k) {
+    for (int a = 0; a < 3; ++a) {
+      double s = 0.0;
+      for (int l = 0; l < L; ++l) s += t.Wv[k][l] * V[l][a];
+      vcon[(i * 4 + k) * 4 + a] = mu * s;
+    }
+    vcon[(i * 4 + k) * 4 + 3] = mu;
+  }
+}
+
+// ------------------------------------------------------------- nodal solver
+// One thread per vertex over the incidence list (cell * 4 + local vertex, in
+// increasing caller cell order): V_k = sum mu V_kj / sum mu, X^{n+1} = X^n +
+// dt V_k.
+__global__ void __launch_bounds__(256) k_ale_nodes3(const int32_t* __restrict__ start, const int32_t* __restrict__ ent,
+                                                    const double* __restrict__ vcon, const double* __restrict__ Xv,
+                                                    int64_t nvert, double dt_fixed, double cfl,
+                                                    const unsigned long long* dtmin, double* __restrict__ Xv1) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= nvert) return;
+  const double dt = step_dt(dt_fixed, cfl, dtmin);
+  double ax = 0.0, ay = 0.0, az = 0.0, mu = 0.0;
+  for (int32_t e = start[g]; e < start[g + 1]; ++e) {
+    const double* c = vcon + (int64_t)ent[e] * 4;
+    ax += c[0];
+    ay += c[1];
+    az += c[2];
+    mu += c[3];
+  }
+  Xv1[g * 3] = mu > 0.0 ? Xv[g * 3] + dt * (ax / mu) : Xv[g * 3];
+  Xv1[g * 3 + 1] = mu > 0.0 ? Xv[g * 3 + 1] + dt * (ay / mu) : Xv[g * 3 + 1];
+  Xv1[g * 3 + 2] = mu > 0.0 ? Xv[g * 3 + 2] + dt * (az / mu) : Xv[g * 3 + 2];
+}
+
+// -------------------------------------------------------------------- faces
+struct FaceGeo3 {
+  double A0[3], B0[3], C0[3], A1[3], B1[3], C1[3];
+};
+
+// Space-time normal (x, y, z, t) at (chi1, chi2, tau): component p is
+// (-1)^(1+p) times the minor of the rows (dx/dchi1, 0), (dx/dchi2, 0),
+// (dx/dtau, dt) that deletes column p (Eq. detChi).
+__device__ __forceinline__ void st_normal3(const FaceGeo3& f, double c1, double c2, double tau, double dt, double* n) {
+  double r1[3], r2[3], r3[3];
+  for (int a = 0; a < 3; ++a) {
+    r1[a] = (1.0 - tau) * (f.B0[a] - f.A0[a]) + tau * (f.B1[a] - f.A1[a]);
+    r2[a] = (1.0 - tau) * (f.C0[a] - f.A0[a]) + tau * (f.C1[a] - f.A1[a]);
+    r3[a] = (1.0 - c1 - c2) * (f.A1[a] - f.A0[a]) + c1 * (f.B1[a] - f.B0[a]) + c2 * (f.C1[a] - f.C0[a]);
+  }
+  // the t-column is (0, 0, dt): the spatial components expand along it
+  n[0] = dt * (r1[1] * r2[2] - r1[2] * r2[1]);
+  n[1] = dt * (r1[2] * r2[0] - r1[0] * r2[2]);
+  n[2] = dt * (r1[0] * r2[1] - r1[1] * r2[0]);
+  n[3] = -det3(r1, r2, r3);
+}
+
+// One thread per face: the integral over the lateral space-time face of the
+// Rusanov flux (F~(q+) + F~(q-)).n~/2 - s_max (q+ - q-)/2, F~ = (f, g, h, Q),
+// s_max = |n~_x| max(|v.n - V.n| + c) over both sides, V.n = -n~_t/|n~_x|.
+// Face vertices in ascending global id (the order of the face tables of
+// both sides' codes).  Transmissive boundary: q+ = q-.  Positivity switch:
+// an inadmissible trace is replaced by that side's cell average.
+template <int M>
+__global__ void __launch_bounds__(128) k_ale_flux3(const __grid_constant__ AleTab3 t, const double* __restrict__ ftab,
+                                                   const int32_t* __restrict__ fL, const int32_t* __restrict__ fR,
+                                                   const uint8_t* __restrict__ codeL, const uint8_t* __restrict__ codeR,
+                                                   const int32_t* __restrict__ gv, const double* __restrict__ shift,
+                                                   const double* __restrict__ Xv, const double* __restrict__ Xv1,
+                                                   const double* __restrict__ bary, const double* __restrict__ qhat,
+                                                   const double* __restrict__ Q, int64_t N, int64_t F,
+                                                   double dt_fixed, double cfl, const unsigned long long* dtmin,
+                                                   double* __restrict__ G) {
+  constexpr int L = lcal3(M), NQT = M + 1, NQS = (M + 1) * (M + 1);
+  const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= F) return;
+  const double dt = step_dt(dt_fixed, cfl, dtmin);
+  const int64_t cl = fL[f], cr = fR[f];
+  const int kL = codeL[f], kR = cr >= 0 ? codeR[f] : 0;
+  const int lf = kL / 6;
+  int lv[3], n3 = 0;
+  for (int q = 0; q < 4; ++q)
+    if (q != lf) lv[n3++] = q;
+  int64_t gg[3];
+  for (int r = 0; r < 3; ++r) gg[r] = gv[lv[r] * N + cl];
+  // ascending global id (insertion sort of three)
+  for (int r = 1; r < 3; ++r)
+    for (int s = r; s > 0 && gg[s] < gg[s - 1]; --s) {
+      const int64_t tg = gg[s];
+      gg[s] = gg[s - 1];
+      gg[s - 1] = tg;
+      const int tl = lv[s];
+      lv[s] = lv[s - 1];
+      lv[s - 1] = tl;
+    }
+  FaceGeo3 fg;
+  for (int a = 0; a < 3; ++a) {
+    const double sa = shift[(lv[0] * 3 + a) * N + cl], sb = shift[(lv[1] * 3 + a) * N + cl],
+                 sc = shift[(lv[2] * 3 + a) * N + cl];
+    fg.A0[a] = Xv[gg[0] * 3 + a] + sa;
+    fg.B0[a] = Xv[gg[1] * 3 + a] + sb;
+    fg.C0[a] = Xv[gg[2] * 3 + a] + sc;
+    fg.A1[a] = Xv1[gg[0] * 3 + a] + sa;
+    fg.B1[a] = Xv1[gg[1] * 3 + a] + sb;
+    fg.C1[a] = Xv1[gg[2] * 3 + a] + sc;
+  }
+  double n0[4];
+  st_normal3(fg, 0.0, 0.0, 0.0, dt, n0);
+  const double sgn = n0[0] * (fg.A0[0] - bary[cl * 3]) + n0[1] * (fg.A0[1] - bary[cl * 3 + 1]) +
+                             n0[2] * (fg.A0[2] - bary[cl * 3 + 2]) >
+                             0.0
+                         ? 1.0
+                         : -1.0;
+  double qbL[5], qbR[5];
+  for (int v = 0; v < 5; ++v) {
+    qbL[v] = Q[v * N + cl];
+    qbR[v] = cr >= 0 ? Q[v * N + cr] : qbL[v];
+  }
+  const double* qL = qhat + cl * L * 5;
+  const double* qR = qhat + (cr >= 0 ? cr : cl) * L * 5;
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (int qp = 0; qp < NQS; ++qp)
+    for (int tt = 0; tt < NQT; ++tt) {
+      const double* bL = ftab + ((int64_t)(kL * NQT + tt) * NQS + qp) * L;
+      const double* bR = ftab + ((int64_t)(kR * NQT + tt) * NQS + qp) * L;
+      double qm[5] = {0, 0, 0, 0, 0}, qq[5] = {0, 0, 0, 0, 0};
+      for (int l = 0; l < L; ++l)
+        for (int v = 0; v < 5; ++v) {
+          qm[v] += bL[l] * qL[l * 5 + v];
+          qq[v] += bR[l] * qR[l * 5 + v];
+        }
+      if (cr < 0)
+        for (int v = 0; v < 5; ++v) qq[v] = qm[v];
+      if (t.pos) {
+        if (!admissible3(qm, t.gamma))
+          for (int v = 0; v < 5; ++v) qm[v] = qbL[v];
+        if (!admissible3(qq, t.gamma))
+          for (int v = 0; v < 5; ++v) qq[v] = qbR[v];
+      }
+      double n[4];
+      st_normal3(fg, t.chi[qp][0], t.chi[qp][1], t.tq[tt], dt, n);
+      for (int a = 0; a < 4; ++a) n[a] *= sgn;
+      const double nx = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]), inx = 1.0 / nx;
+      const double un[3] = {n[0] * inx, n[1] * inx, n[2] * inx};
+      const double Vn = -n[3] * inx;
+      double sm = 0.0, fsum[5] = {0, 0, 0, 0, 0};
+      const double* sides[2] = {qm, qq};
+      for (int s = 0; s < 2; ++s) {
+        const double* z = sides[s];
+        const double ir = 1.0 / z[0];
+        const double u[3] = {z[1] * ir, z[2] * ir, z[3] * ir};
+        const double p = (t.gamma - 1.0) * (z[4] - 0.5 * (z[1] * u[0] + z[2] * u[1] + z[3] * u[2]));
+        const double c = sqrt(fmax(0.0, t.gamma * p * ir));
+        const double vn = u[0] * un[0] + u[1] * un[1] + u[2] * un[2];
+        sm = fmax(sm, fabs(vn - Vn) + c);
+        const double un_n = u[0] * n[0] + u[1] * n[1] + u[2] * n[2];  // v . n~_x
+        fsum[0] += z[1] * n[0] + z[2] * n[1] + z[3] * n[2];
+        for (int b = 0; b < 3; ++b) fsum[1 + b] += z[1 + b] * un_n + p * n[b];
+        fsum[4] += (z[4] + p) * un_n;
+      }
+      sm *= nx;
+      const double wgt = 0.5 * t.wq[qp] * t.wt[tt];  // reference triangle area 1/2
+      for (int v = 0; v < 5; ++v)
+        acc[v] += wgt * (0.5 * fsum[v] + 0.5 * (qm[v] + qq[v]) * n[3] - 0.5 * sm * (qq[v] - qm[v]));
+    }
+  for (int v = 0; v < 5; ++v) G[v * F + f] = acc[v];
+}
+
+// ------------------------------------------------------------------- update
+__global__ void __launch_bounds__(256) k_ale_update3(const int32_t* __restrict__ cellface, const double* __restrict__ G,
+                                                     const int32_t* __restrict__ gv, const double* __restrict__ shift,
+                                                     const double* __restrict__ Xv1, const double* __restrict__ vol0,
+                                                     int64_t N, int64_t F, double gamma, double dt_fixed, double cfl,
+                                                     const unsigned long long* dtmin, double* __restrict__ Q,
+                                                     double* time, int* status) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) *time += step_dt(dt_fixed, cfl, dtmin);
+  if (i >= N) return;
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (int k = 0; k < 4; ++k) {
+    const int32_t cf = cellface[k * N + i];
+    const int64_t f = cf >> 1;
+    const double s = (cf & 1) ? -1.0 : 1.0;
+    for (int v = 0; v < 5; ++v) acc[v] += s * G[v * F + f];
+  }
+  double P[4][3];
+  for (int k = 0; k < 4; ++k) {
+    const int64_t g = gv[k * N + i];
+    for (int a = 0; a < 3; ++a) P[k][a] = Xv1[g * 3 + a] + shift[(k * 3 + a) * N + i];
+  }
+  double e[3][3];
+  for (int k = 0; k < 3; ++k)
+    for (int a = 0; a < 3; ++a) e[k][a] = P[k + 1][a] - P[0][a];
+  const double v1 = det3(e[0], e[1], e[2]) / 6.0, v0 = vol0[i];
+  double q[5];
+  for (int v = 0; v < 5; ++v) {
+    q[v] = (v0 * Q[v * N + i] - acc[v]) / v1;
+    Q[v * N + i] = q[v];
+  }
+  if (!(v1 > 0.0) || !admissible3(q, gamma)) atomicOr(status, 1);
+}
+
+}  // namespace

@@ -586,6 +586,12 @@ void RefElem::init(int d_, int M_) {
     this->chi.clear();
     if (d == 2)
       for (const auto& c : chi) this->chi.push_back(c[0]);
+    chi3.clear();
+    if (d == 3)
+      for (const auto& c : chi) {
+        chi3.push_back(c[0]);
+        chi3.push_back(c[1]);
+      }
     ncode = (d == 2) ? 6 : 24;
     ftab.assign((size_t)ncode * nqt * nqs * L, 0.0);
     std::vector<LD> fi((size_t)ncode * L, 0.0L);

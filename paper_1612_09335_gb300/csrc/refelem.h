@@ -80,6 +80,7 @@ struct RefElem {
   std::vector<double> wq, wt;
   std::vector<double> tq;    // time points
   std::vector<double> chi;   // face points (d = 2: parameter along the edge)
+  std::vector<double> chi3;  // face points (d = 3: (chi1, chi2) pairs on the triangle)
   // moving-mesh predictor (Secs. 2.2-2.3):
   //   Dxi[(e L + n) L + l] = d theta_l / d xi_e at node n;
   //   Gal = (K_tau^1)^-1 M^1, L1 x L, the Galerkin operator of Eqs. (CGfinal)

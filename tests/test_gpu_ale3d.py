@@ -1,0 +1,160 @@
+"""Moving tetrahedral meshes (direct ALE in three space dimensions, Secs.
+2.2-2.4) through the C ABI against the FP64 oracle's ALE step on the same
+seeded inputs: cell averages and vertex positions after one and after
+several steps (the same dt given to both), orders 2 and 3, a periodic
+deforming flow and a transmissive explosion on meshes of 750 tetrahedra (five
+128-cell blocks and a ragged tail).
+
+Bound: 1e-12 relative per variable (as on fixed meshes), or for the
+discontinuous data 8x the oracle's own response to one-ulp input
+perturbations; vertices to 1e-13 of the domain size."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+EULER = 0
+LAGRANGE, STILL = 1, 2
+
+
+@pytest.fixture(scope="module")
+def cw():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_1612_09335_gb300 as pkg
+    pkg.build()
+    from paper_1612_09335_gb300 import binding
+    return binding
+
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+    return oracle
+
+
+@pytest.fixture(scope="module")
+def wl():
+    from paper_1612_09335_gb300 import workloads
+    return workloads
+
+
+def relerr(a, b, floor=1e-6):
+    num = np.abs(a - b).max(axis=0)
+    mag = np.abs(b).max(axis=0)
+    den = np.maximum(np.maximum(mag, floor * mag.max()), 1e-300)
+    return float((num / den).max())
+
+
+def shear_flow(wl, x):
+    rho = 1.0 + 0.2 * np.sin(2 * np.pi * x[:, 0])
+    vel = 0.3 * np.stack([np.sin(2 * np.pi * x[:, 1]), np.sin(2 * np.pi * x[:, 2]), np.sin(2 * np.pi * x[:, 0])])
+    return wl.euler_conserved(rho, vel, np.ones_like(rho), 1.4)
+
+
+def inputs(wl, name):
+    if name == "shear":
+        m = wl.tet_mesh(5, jitter=0.15, seed=31)                   # 750 cells, periodic
+        return m, wl.cell_averages(m, lambda x: shear_flow(wl, x), n=4)
+    m = wl.tet_mesh(5, lo=(-1, -1, -1), hi=(1, 1, 1), periodic=False, jitter=0.12, seed=32)
+    return m, wl.explosion_averages(m, sub=4)                      # transmissive, discontinuous
+
+
+def solver(cw, mesh, order, motion=LAGRANGE):
+    return cw.Solver(cw.Mesh.from_workload(mesh), order, EULER, cw.FP64, mesh_motion=motion)
+
+
+def bound(orc, mesh, order, Q, dt, name):
+    if name == "shear":
+        return 1e-12
+    ref = orc.Oracle(mesh, order).ale_step(Q, dt)[0]
+    rng = np.random.default_rng(3)
+    worst = 0.0
+    for _ in range(2):
+        Qp = Q * (1.0 + 2.0 ** -52 * rng.choice([-1.0, 1.0], size=Q.shape))
+        worst = max(worst, relerr(orc.Oracle(mesh, order).ale_step(Qp, dt)[0], ref))
+    return max(1e-12, 8.0 * worst)
+
+
+@pytest.mark.parametrize("name", ["shear", "explosion"])
+@pytest.mark.parametrize("order", [2, 3])
+def test_one_ale3d_step_matches_oracle(cw, orc, wl, name, order):
+    mesh, Q = inputs(wl, name)
+    o = orc.Oracle(mesh, order)
+    dt = o.stable_dt(Q)
+    Qo, xo = o.ale_step(Q, dt)
+    s = solver(cw, mesh, order)
+    s.set_state(Q)
+    s.step(dt)
+    s.sync()
+    xg = s.get_vertices()
+    scale = np.abs(mesh.xyz).max()
+    assert np.abs(xg - xo).max() < 1e-13 * scale
+    assert np.abs(xg - mesh.xyz).max() > 1e-4  # the mesh did move
+    assert relerr(s.get_state(), Qo) < bound(orc, mesh, order, Q, dt, name)
+
+
+@pytest.mark.parametrize("order", [2, 3])
+def test_five_ale3d_steps_match_oracle(cw, orc, wl, order):
+    mesh, Q = inputs(wl, "shear")
+    o = orc.Oracle(mesh, order)
+    s = solver(cw, mesh, order)
+    s.set_state(Q)
+    Qo = Q.copy()
+    for _ in range(5):
+        dt = o.stable_dt(Qo)
+        Qo, xo = o.ale_step(Qo, dt)
+        s.step(dt)
+    assert np.abs(s.get_vertices() - xo).max() < 1e-12
+    assert np.abs(s.get_vertices() - mesh.xyz).max() > 1e-3
+    assert relerr(s.get_state(), Qo) < 1e-11
+
+
+@pytest.mark.parametrize("order", [2, 3])
+def test_still_tetrahedral_mesh_equals_fixed_mesh_path(cw, wl, order):
+    mesh, Q = inputs(wl, "shear")
+    a = solver(cw, mesh, order, STILL)
+    b = cw.Solver(cw.Mesh.from_workload(mesh), order, EULER, cw.FP64)
+    for s in (a, b):
+        s.set_state(Q)
+        for _ in range(3):
+            s.step(0.0)
+    assert np.array_equal(a.get_vertices(), mesh.xyz)
+    assert relerr(a.get_state(), b.get_state()) < 1e-12
+    assert abs(a.time() - b.time()) < 1e-14 * b.time()
+
+
+def test_ale3d_constant_state_translates_the_mesh(cw, wl):
+    mesh = wl.tet_mesh(4, jitter=0.15, seed=33)
+    q = np.array([1.3, 0.39, -0.26, 0.13, 3.1])
+    s = solver(cw, mesh, 3)
+    s.set_state(np.tile(q, (mesh.nc, 1)))
+    for _ in range(2):
+        s.step(0.01)
+    assert np.abs(s.get_state() - q).max() < 1e-13
+    assert np.abs(s.get_vertices() - mesh.xyz - 0.02 * q[1:4] / q[0]).max() < 1e-14
+
+
+def test_ale3d_conservation_on_the_deforming_periodic_mesh(cw, wl):
+    import dataclasses
+    mesh, Q = inputs(wl, "shear")
+    s = solver(cw, mesh, 3)
+    s.set_state(Q)
+    for _ in range(10):
+        s.step(0.0)
+    X0 = mesh.cell_vertices()
+    v0 = np.abs(np.linalg.det(X0[:, 1:] - X0[:, :1])) / 6.0
+    X1 = dataclasses.replace(mesh, xyz=s.get_vertices()).cell_vertices()
+    v1 = np.abs(np.linalg.det(X1[:, 1:] - X1[:, :1])) / 6.0
+    assert np.std(v1 / v0) > 1e-4                          # the cells deformed
+    assert abs(v1.sum() - v0.sum()) < 1e-13                # the periodic box keeps its volume
+    tot0 = v0 @ Q
+    assert np.abs(v1 @ s.get_state() - tot0).max() / np.abs(tot0).max() < 1e-13
+
+
+def test_ale3d_rejects_what_it_does_not_build(cw, wl):
+    m = cw.Mesh.from_workload(wl.tet_mesh(3))
+    with pytest.raises(cw.CwenoError):
+        cw.Solver(m, 4, EULER, cw.FP64, mesh_motion=LAGRANGE)      # order 4 on tetrahedra
+    with pytest.raises(cw.CwenoError):
+        cw.Solver(m, 3, EULER, cw.FP32_MIXED, mesh_motion=LAGRANGE)
