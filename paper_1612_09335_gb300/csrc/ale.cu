@@ -1,5 +1,5 @@
 // Moving meshes: the direct ALE ADER-CWENO step (Secs. 2.2-2.4) on 2D
-// triangle meshes (tetrahedra: ale3.cuh, FP64), Euler equations, FP64 or FP32-mixed (k_ale_pred32,
+// triangle meshes (tetrahedra: ale3.cuh), Euler equations, FP64 or FP32-mixed (k_ale_pred32,
 // k_ale_flux32: FP32 deviations, FP64 least squares, averages' face part,
 // nodal solver and update), Rusanov flux with the ALE Jacobian.  Mesh velocity V = v (the local fluid velocity, the choice of the
 // paper's moving-mesh tests) or V = 0 (the same machinery on a mesh that does
@@ -819,6 +819,7 @@ struct Ale {
   int64_t nvert = 0;
   AleTab tab;
   AleTab3 tab3;  // tetrahedra
+  AleTab3f tab3f;
   double *Xv = nullptr, *Xv1 = nullptr, *shift = nullptr, *X = nullptr, *bary = nullptr, *vol = nullptr;
   double *w = nullptr, *qhat = nullptr, *vcon = nullptr, *G = nullptr, *ftab = nullptr;
   // FP32-mixed: tables, face basis and predictor deviations in FP32
@@ -1052,16 +1053,12 @@ int ale_create(cweno_solver* s, const MeshHost& m, std::string& err) {
   return CWENO_OK;
 }
 
-// Tetrahedra (FP64, M = 1, 2): tables, vertex incidence, periodic shifts and
-// scratch of the moving mesh.
+// Tetrahedra (M = 1, 2; FP64 or FP32-mixed): tables, vertex incidence,
+// periodic shifts and scratch of the moving mesh.
 int ale_create3(cweno_solver* s, const MeshHost& m, std::string& err) {
   const RefElem& re = *s->re;
   if (s->pde != CWENO_EULER || re.M < 1 || re.M > 2 || s->prm.flux != CWENO_FLUX_RUSANOV) {
     err = "moving tetrahedral meshes are built for Euler, order 2..3, Rusanov flux";
-    return CWENO_EINVAL;
-  }
-  if (s->prec != CWENO_FP64) {
-    err = "moving tetrahedral meshes run in FP64";
     return CWENO_EINVAL;
   }
   auto A = std::make_shared<Ale>();
@@ -1164,6 +1161,13 @@ int ale_create3(cweno_solver* s, const MeshHost& m, std::string& err) {
   ACK(A->alloc(&A->vcon, (size_t)N * 16, st));
   ACK(A->alloc(&A->G, (size_t)5 * m.nf, st));
   ACK(A->alloc(&A->bad, 1, st));
+  if (s->prec == CWENO_FP32_MIXED) {
+    A->fp32 = true;
+    A->tab3f = ale_tab3_float(t);
+    std::vector<float> f32(re.ftab.begin(), re.ftab.end());
+    ACK(A->put(&A->ftab32, f32, st));
+    ACK(A->alloc(&A->qhat32, (size_t)N * L * 5, st));
+  }
   const int big = 0x7fffffff;
   ACK(cudaMemcpyAsync(A->bad, &big, sizeof(int), cudaMemcpyHostToDevice, st));
   ACK(cudaStreamSynchronize(st));
@@ -1207,7 +1211,13 @@ int ale_step(cweno_solver* s, double dt) {
   d2.perm = A.ident;  // reconstruction values in internal cell order
   ACK(s->ops->reconstruct(d2, s->ph, A.w, st));
   if (A.d == 3) {
-    if (A.M == 1)
+    if (A.fp32 && A.M == 1)
+      k_ale_pred3_32<1><<<nblk(ds.N, 128), 128, 0, st>>>(A.tab3f, A.w, ds.Q, A.X, A.vol, ds.N, s->ph.niter, dtf,
+                                                          s->prm.cfl, ds.dtmin, A.qhat32, A.vcon);
+    else if (A.fp32)
+      k_ale_pred3_32<2><<<nblk(ds.N, 128), 128, 0, st>>>(A.tab3f, A.w, ds.Q, A.X, A.vol, ds.N, s->ph.niter, dtf,
+                                                          s->prm.cfl, ds.dtmin, A.qhat32, A.vcon);
+    else if (A.M == 1)
       k_ale_pred3<1><<<nblk(ds.N, 128), 128, 0, st>>>(A.tab3, A.w, ds.Q, A.X, A.vol, ds.N, s->ph.niter, dtf,
                                                        s->prm.cfl, ds.dtmin, A.qhat, A.vcon);
     else
@@ -1217,7 +1227,15 @@ int ale_step(cweno_solver* s, double dt) {
     k_ale_nodes3<<<nblk(A.nvert, 256), 256, 0, st>>>(A.start, A.ent, A.vcon, A.Xv, A.nvert, dtf, s->prm.cfl,
                                                       ds.dtmin, A.Xv1);
     ACK(cudaGetLastError());
-    if (A.M == 1)
+    if (A.fp32 && A.M == 1)
+      k_ale_flux3_32<1><<<nblk(ds.F, 128), 128, 0, st>>>(A.tab3f, s->prm.gamma, A.ftab32, ds.fL, ds.fR, ds.codeL,
+                                                          ds.codeR, A.gv, A.shift, A.Xv, A.Xv1, A.bary, A.qhat32,
+                                                          ds.Q, ds.N, ds.F, dtf, s->prm.cfl, ds.dtmin, A.G);
+    else if (A.fp32)
+      k_ale_flux3_32<2><<<nblk(ds.F, 128), 128, 0, st>>>(A.tab3f, s->prm.gamma, A.ftab32, ds.fL, ds.fR, ds.codeL,
+                                                          ds.codeR, A.gv, A.shift, A.Xv, A.Xv1, A.bary, A.qhat32,
+                                                          ds.Q, ds.N, ds.F, dtf, s->prm.cfl, ds.dtmin, A.G);
+    else if (A.M == 1)
       k_ale_flux3<1><<<nblk(ds.F, 128), 128, 0, st>>>(A.tab3, A.ftab, ds.fL, ds.fR, ds.codeL, ds.codeR, A.gv,
                                                        A.shift, A.Xv, A.Xv1, A.bary, A.qhat, ds.Q, ds.N, ds.F, dtf,
                                                        s->prm.cfl, ds.dtmin, A.G);
@@ -1227,7 +1245,7 @@ int ale_step(cweno_solver* s, double dt) {
                                                        s->prm.cfl, ds.dtmin, A.G);
     ACK(cudaGetLastError());
     k_ale_update3<<<nblk(ds.N, 256), 256, 0, st>>>(ds.cellface, A.G, A.gv, A.shift, A.Xv1, A.vol, ds.N, ds.F,
-                                                    s->prm.gamma, dtf, s->prm.cfl, ds.dtmin, ds.Q, ds.time,
+                                                    s->prm.gamma, dtf, s->prm.cfl, ds.dtmin, ds.Q, ds.Qp, ds.time,
                                                     ds.status);
     ACK(cudaGetLastError());
     std::swap(A.Xv, A.Xv1);

@@ -277,8 +277,6 @@ int cweno_setup(const cweno_mesh* mesh, int order, int pde, int precision, const
   if (prm.mesh_motion != CWENO_MOTION_FIXED &&
       (pde != CWENO_EULER || order > (m.d == 2 ? 4 : 3) || prm.flux != CWENO_FLUX_RUSANOV))
     return fail(CWENO_EINVAL, "moving meshes are built for Euler, Rusanov flux, order 2..4 (2D) or 2..3 (3D)");
-  if (prm.mesh_motion != CWENO_MOTION_FIXED && m.d == 3 && precision != CWENO_FP64)
-    return fail(CWENO_EINVAL, "moving tetrahedral meshes run in FP64");
   const int M = order - 1;
   std::unique_ptr<cweno_solver> s(new cweno_solver());
   s->dim = m.d;
