@@ -595,29 +595,62 @@ def workload_rate(cw, name, stream, barrier, pk, steps=10, flux=0, precisions=No
     return res
 
 
-def ale_oracle_rate(n=40, steps=3):
+def ale_mesh(wl, dim, n):
+    """The ALE explosion's mesh: [-1, 1]^d, transmissive, n x n x 2 jittered
+    triangles (2D) or n^3 x 6 jittered tetrahedra (3D)."""
+    if dim == 2:
+        return wl.tri_mesh(n, lo=(-1.0, -1.0), hi=(1.0, 1.0), periodic=False, jitter=0.2, seed=1234)
+    return wl.tet_mesh(n, lo=(-1.0, -1.0, -1.0), hi=(1.0, 1.0, 1.0), periodic=False, jitter=0.15, seed=1234)
+
+
+ALE_ORDER = {2: 4, 3: 3}
+
+
+def ale_oracle_rate(dim=2, n=None, steps=3):
     """The FP64 oracle's direct ALE step timed on the host (one thread) on a
-    bounded sample of the same workload family: n x n x 2 triangles (3,200 at
-    n = 40, the size of the paper's 2D Sedov mesh), one untimed step first."""
+    bounded sample of the same workload family: 40 x 40 x 2 triangles (3,200,
+    the size of the paper's 2D Sedov mesh) or 6^3 x 6 tetrahedra (1,296), one
+    untimed step first."""
     import oracle
     from paper_1612_09335_gb300 import workloads as wl
-    mesh = wl.tri_mesh(n, lo=(-1.0, -1.0), hi=(1.0, 1.0), periodic=False, jitter=0.2, seed=1234)
+    n = n or (40 if dim == 2 else 6)
+    mesh = ale_mesh(wl, dim, n)
     Q = wl.explosion_averages(mesh, sub=4)
-    o = oracle.Oracle(mesh, 4)
+    o = oracle.Oracle(mesh, ALE_ORDER[dim])
     Q, _ = o.ale_step(Q, o.stable_dt(Q))
     t0 = time.perf_counter()
     for _ in range(steps):
         Q, _ = o.ale_step(Q, o.stable_dt(Q))
     el = time.perf_counter() - t0
+    shape = f"{n}x{n}x2 triangles" if dim == 2 else f"{n}^3x6 tetrahedra"
     return {"value": mesh.nc * steps / el, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
-            "sample": f"{mesh.nc} triangles ({n}x{n}x2, same family), {steps} ALE steps after one untimed step, "
+            "sample": f"{mesh.nc} cells ({shape}, same family), {steps} ALE steps after one untimed step, "
                       "single host thread"}
 
 
-def ale_rate(cw, stream, barrier, n=256, steps=10, warm=3):
+ALE_STAGES = ("geometry_and_least_squares", "reconstruction", "predictor", "nodal_solver", "faces", "update",
+              "cfl_bound")
+
+
+def ale_stages(s, steps):
+    """Per-stage device time of `steps` further moving-mesh steps (CUDA events
+    around each stage on the solver's stream, a pass of its own so that the
+    timed steps carry no events): mean ms per step and share of the stages'
+    sum."""
+    s.profile(True)
+    for _ in range(steps):
+        s.step(0.0)
+    ms, n = s.profile_read_stages(len(ALE_STAGES))
+    s.profile(False)
+    tot = sum(ms) or 1.0
+    return {k: {"ms": ms[q] / max(1, n[q]), "share": ms[q] / tot} for q, k in enumerate(ALE_STAGES) if n[q]}
+
+
+def ale_rate(cw, stream, barrier, dim=2, n=None, steps=None, warm=3):
     """Moving mesh: direct ALE steps (mesh velocity = fluid velocity) of the
-    2D explosion (Sec. 3.2's ALE explosion, Table efficiency), fourth order
-    (M = 3), Rusanov, on an n x n x 2 transmissive mesh of [-1, 1]^2, FP64 and
+    explosion (Sec. 3.2's ALE explosion, Table efficiency), Rusanov, on a
+    transmissive mesh of [-1, 1]^d: 2D fourth order (M = 3) on n x n x 2
+    triangles, 3D third order (M = 2) on n^3 x 6 tetrahedra; FP64 and
     FP32-mixed; CUDA events on the solver stream, device CFL step.  Accuracy
     of FP32-mixed against FP64 after `steps` steps of the FP64 solver's CFL
     step sizes (state and vertices), and its drift of sum |T| Q."""
@@ -625,16 +658,22 @@ def ale_rate(cw, stream, barrier, n=256, steps=10, warm=3):
     import numpy as np
     import torch
     from paper_1612_09335_gb300 import workloads as wl
-    mesh = wl.tri_mesh(n, lo=(-1.0, -1.0), hi=(1.0, 1.0), periodic=False, jitter=0.2, seed=1234)
+    n = n or (256 if dim == 2 else 63)
+    steps = steps or (10 if dim == 2 else 4)
+    order = ALE_ORDER[dim]
+    mesh = ale_mesh(wl, dim, n)
     Q0 = wl.explosion_averages(mesh, sub=4)
     m = cw.Mesh.from_workload(mesh)
-    out = {"cells": mesh.nc, "mesh": f"[-1,1]^2, {n}x{n}x2 triangles, jitter 20 %, transmissive, moving with the flow",
-           "order": 4,
-           "note": "the paper's ALE explosion (2D, 17,340 triangles, P3) reports tau_E = 6.6e-4 s per "
-                   "element update on its CPU (Table efficiency): context, not a target"}
+    shape = f"{n}x{n}x2 triangles, jitter 20 %" if dim == 2 else f"{n}^3x6 tetrahedra, jitter 15 %"
+    paper = ("2D, 17,340 triangles, reports tau_E = 6.6e-4 s" if dim == 2 else
+             "3D, 1,469,472 tetrahedra, reports tau_E = 1.9e-2 s")
+    out = {"cells": mesh.nc, "mesh": f"[-1,1]^{dim}, {shape}, transmissive, moving with the flow",
+           "order": order,
+           "note": f"the paper's ALE explosion ({paper} per element update on its CPU, Table efficiency): "
+                   "context, not a target"}
     solvers = {}
     for prec, key in ((cw.FP32_MIXED, "fp32_mixed"), (cw.FP64, "fp64")):
-        s = cw.Solver(m, 4, 0, prec, stream=stream.cuda_stream, mesh_motion=cw.MOTION_LAGRANGE)
+        s = cw.Solver(m, order, 0, prec, stream=stream.cuda_stream, mesh_motion=cw.MOTION_LAGRANGE)
         s.set_state(Q0)
         for _ in range(warm):
             s.step(0.0)
@@ -651,13 +690,14 @@ def ale_rate(cw, stream, barrier, n=256, steps=10, warm=3):
         moved = float(abs(s.get_vertices() - mesh.xyz).max())
         v = mesh.nc * steps / (ms / 1e3)
         out[key] = {"value": v, "unit": "cell-updates/s", "ms_per_step": ms / steps, "steps": steps,
-                    "max_vertex_displacement": moved, "tau_E_s": 1.0 / v}
+                    "max_vertex_displacement": moved, "tau_E_s": 1.0 / v,
+                    "stages": ale_stages(s, steps)}
         solvers[key] = s
     for sv in solvers.values():
         sv.close()
     # accuracy on fresh solvers (the timed ones moved their meshes)
-    a = cw.Solver(m, 4, 0, cw.FP32_MIXED, stream=stream.cuda_stream, mesh_motion=cw.MOTION_LAGRANGE)
-    b = cw.Solver(m, 4, 0, cw.FP64, stream=stream.cuda_stream, mesh_motion=cw.MOTION_LAGRANGE)
+    a = cw.Solver(m, order, 0, cw.FP32_MIXED, stream=stream.cuda_stream, mesh_motion=cw.MOTION_LAGRANGE)
+    b = cw.Solver(m, order, 0, cw.FP64, stream=stream.cuda_stream, mesh_motion=cw.MOTION_LAGRANGE)
     a.set_state(Q0)
     b.set_state(Q0)
     # the FP64 solver takes its device CFL step (the flow accelerates, so a
@@ -674,9 +714,9 @@ def ale_rate(cw, stream, barrier, n=256, steps=10, warm=3):
     xa, xb = a.get_vertices(), b.get_vertices()
     acc = accuracy_metrics(dataclasses.replace(mesh, xyz=xb), Q0, qa, qb)
     X0 = mesh.cell_vertices()
-    v0 = np.abs(np.linalg.det(X0[:, 1:] - X0[:, :1])) / 2.0
+    v0 = np.abs(np.linalg.det(X0[:, 1:] - X0[:, :1])) / math.factorial(dim)
     Xa = dataclasses.replace(mesh, xyz=xa).cell_vertices()
-    va = np.abs(np.linalg.det(Xa[:, 1:] - Xa[:, :1])) / 2.0
+    va = np.abs(np.linalg.det(Xa[:, 1:] - Xa[:, :1])) / math.factorial(dim)
     tot0 = v0 @ Q0
     scale = np.maximum(np.maximum(np.abs(tot0), v0 @ np.abs(Q0)), 1e-300)
     acc["conservation_drift_rel"] = [float(x) for x in np.abs(va @ qa - tot0) / np.maximum(scale, 1e-6 * scale.max())]
@@ -685,6 +725,7 @@ def ale_rate(cw, stream, barrier, n=256, steps=10, warm=3):
     out["accuracy"] = acc
     a.close()
     b.close()
+    m.close()
     return out
 
 
@@ -704,7 +745,7 @@ def run_ours(args):
     if args.only_ale:
         st = torch.cuda.Stream()
         torch.cuda.set_stream(st)
-        print(json.dumps({"ale": ale_rate(cw, st, torch.cuda.synchronize, n=args.n or 256,
+        print(json.dumps({"ale": ale_rate(cw, st, torch.cuda.synchronize, dim=args.ale_dim, n=args.n,
                                           steps=args.steps, warm=args.warmup)}))
         return
     name = args.workload
@@ -843,8 +884,10 @@ def run_ours(args):
                                                       inputs=(mesh, Q0))
         # moving mesh (direct ALE), rank 0's GPU
         out["ale_explosion2d_p3"] = ale_rate(cw, stream, barrier)
+        out["ale_explosion3d_p2"] = ale_rate(cw, stream, barrier, dim=3)
         if rank == 0 and not args.no_cpu_baseline:
             out["ale_explosion2d_p3"]["cpu_baseline"] = ale_oracle_rate()
+            out["ale_explosion3d_p2"]["cpu_baseline"] = ale_oracle_rate(dim=3, steps=2)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_run(name)
     if rank == 0:
@@ -896,6 +939,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-other", action="store_true",
                     help="skip the 3D, MHD and fifth-order workloads, the flux variants and the moving mesh")
+    ap.add_argument("--ale-dim", type=int, default=2, choices=[2, 3], help="with --only-ale: 2D or 3D explosion")
     ap.add_argument("--only-ale", action="store_true",
                     help="time only the moving-mesh (direct ALE) explosion; --n sets its resolution")
     ap.add_argument("--serve-requests", type=int, default=512,

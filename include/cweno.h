@@ -246,6 +246,13 @@ void* cweno_stream(cweno_solver* s);
  * number of launches per kernel since the last read, then clears them. */
 int cweno_profile_enable(cweno_solver* s, int on);
 int cweno_profile_read(cweno_solver* s, double* ms, int64_t* launches);
+/* The same per stage for moving meshes (the paper has no counterpart: it is
+ * instrumentation).  ms[k], launches[k] for k < nstages (1..8): on a moving
+ * mesh 0 geometry + least squares + sector inverses, 1 reconstruction, 2
+ * predictor, 3 nodal solver, 4 lateral space-time faces, 5 update, 6 CFL
+ * bound; on a fixed mesh the three kernels of cweno_profile_read.  Waits for
+ * the stream and clears the record, like cweno_profile_read. */
+int cweno_profile_read_stages(cweno_solver* s, double* ms, int64_t* launches, int nstages);
 
 /* Measured FMA rate of the current device (the paper has no counterpart: it
  * is the denominator of the FP32 / FP64 pipe fractions a benchmark reports).

@@ -1690,12 +1690,28 @@ void ale_predictor_cell(const OSolver& S, long i, const std::vector<Poly>& w, do
     }
   }
   if (qbar && S.P.positivity) {
+    // The fallback takes a tau > 0 node that is inadmissible or whose density
+    // or pressure leaves [1/2 min, 2 max] of the tau = 0 nodes' values (a
+    // relaxed discrete maximum principle: with V = v the Picard iteration of
+    // a cell cut by a strong discontinuity can stop on large, positive
+    // oscillations instead of converging).
+    double r0 = HUGE_VAL, r1 = -HUGE_VAL, p0 = HUGE_VAL, p1 = -HUGE_VAL;
+    for (int l = 0; l < L0; ++l) {
+      const double* q = &qhat[(size_t)l * nu];
+      const double pl = pressure(S.pde, d, S.P, q);
+      r0 = std::min(r0, q[0]);
+      r1 = std::max(r1, q[0]);
+      p0 = std::min(p0, pl);
+      p1 = std::max(p1, pl);
+    }
     bool ok = true;
     for (int l = L0; l < L; ++l) {
       const double* q = &qhat[(size_t)l * nu];
       bool fin = true;
       for (int v = 0; v < nu; ++v) fin = fin && std::isfinite(q[v]);
-      if (!(fin && q[0] > 0.0 && pressure(S.pde, d, S.P, q) > 0.0)) ok = false;
+      const double pl = pressure(S.pde, d, S.P, q);
+      if (!(fin && q[0] > 0.0 && pl > 0.0)) ok = false;
+      if (!(q[0] >= 0.5 * r0 && q[0] <= 2.0 * r1 && pl >= 0.5 * p0 && pl <= 2.0 * p1)) ok = false;
     }
     if (!ok)
       for (int l = 0; l < L; ++l)

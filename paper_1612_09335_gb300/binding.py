@@ -76,6 +76,7 @@ SIGNATURES = [
     ("cweno_stream", _P, [_P]),
     ("cweno_profile_enable", _I, [_P, _I]),
     ("cweno_profile_read", _I, [_P, _DP, _I64P]),
+    ("cweno_profile_read_stages", _I, [_P, _DP, _I64P, _I]),
     ("cweno_measure_fma_peak", _I, [_I, _DP, _DP]),
     ("cweno_stable_dt_noalloc", _I, [_I, _I, _I64, _P, _P, _D, _D, _D, _P, _P]),
     ("serve_create", _I, [_SZ, _I, _I, C.POINTER(_P)]),
@@ -337,6 +338,15 @@ class Solver:
         ms = (C.c_double * 3)()
         n = (C.c_int64 * 3)()
         _check(lib().cweno_profile_read(self.h, ms, n))
+        return list(ms), list(n)
+
+    def profile_read_stages(self, nstages: int = 7):
+        """Summed device ms and launch counts per stage since the last read
+        (moving meshes: geometry + least squares, reconstruction, predictor,
+        nodal solver, faces, update, CFL bound)."""
+        ms = (C.c_double * nstages)()
+        n = (C.c_int64 * nstages)()
+        _check(lib().cweno_profile_read_stages(self.h, ms, n, int(nstages)))
         return list(ms), list(n)
 
     def close(self):

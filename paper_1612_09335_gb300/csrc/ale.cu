@@ -275,8 +275,23 @@ __global__ void __launch_bounds__(128) k_ale_pred(const __grid_constant__ AleTab
   double qb[4];
   for (int v = 0; v < 4; ++v) qb[v] = Q[v * N + i];
   if (t.pos) {
+    // fallback: a tau > 0 node inadmissible or outside [1/2 min, 2 max] of
+    // the tau = 0 nodes' density and pressure (a Picard iteration with V = v
+    // can stop on large positive oscillations in a cell cut by a shock)
+    double r0 = 1e300, r1 = -1e300, p0 = 1e300, p1 = -1e300;
+    for (int l = 0; l < L0; ++l) {
+      const double pl = pressure(q[l], t.gamma);
+      r0 = fmin(r0, q[l][0]);
+      r1 = fmax(r1, q[l][0]);
+      p0 = fmin(p0, pl);
+      p1 = fmax(p1, pl);
+    }
     bool ok = true;
-    for (int l = L0; l < L; ++l) ok = ok && admissible(q[l], t.gamma);
+    for (int l = L0; l < L; ++l) {
+      const double pl = pressure(q[l], t.gamma);
+      ok = ok && admissible(q[l], t.gamma) && q[l][0] >= 0.5 * r0 && q[l][0] <= 2.0 * r1 && pl >= 0.5 * p0 &&
+           pl <= 2.0 * p1;
+    }
     if (!ok)
       for (int l = 0; l < L; ++l)
         for (int v = 0; v < 4; ++v) q[l][v] = qb[v];
@@ -442,12 +457,27 @@ __global__ void __launch_bounds__(128) k_ale_pred32(const __grid_constant__ AleT
       }
     }
   }
-  if (t.pos) {
+  if (t.pos) {  // the fallback rule of k_ale_pred, on absolute states
+    auto pres = [&](const float* qa) {
+      return (t.gamma - 1.0f) * (qa[3] - 0.5f * (qa[1] * qa[1] + qa[2] * qa[2]) / qa[0]);
+    };
+    float r0 = 3e38f, r1 = -3e38f, p0 = 3e38f, p1 = -3e38f;
+    for (int l = 0; l < L0; ++l) {
+      float qa[4];
+      for (int v = 0; v < 4; ++v) qa[v] = qb[v] + q[l][v];
+      const float pl = pres(qa);
+      r0 = fminf(r0, qa[0]);
+      r1 = fmaxf(r1, qa[0]);
+      p0 = fminf(p0, pl);
+      p1 = fmaxf(p1, pl);
+    }
     bool ok = true;
     for (int l = L0; l < L; ++l) {
       float qa[4];
       for (int v = 0; v < 4; ++v) qa[v] = qb[v] + q[l][v];
-      ok = ok && admissible32(qa, t.gamma);
+      const float pl = pres(qa);
+      ok = ok && admissible32(qa, t.gamma) && qa[0] >= 0.5f * r0 && qa[0] <= 2.0f * r1 && pl >= 0.5f * p0 &&
+           pl <= 2.0f * p1;
     }
     if (!ok)
       for (int l = 0; l < L; ++l)
@@ -1197,19 +1227,28 @@ int ale_refresh(cweno_solver* s) {
 
 int ale_step(cweno_solver* s, double dt) {
   Ale& A = *s->ale;
+  // stages timed when profiling is on (cweno_profile_read_stages)
+  cudaEvent_t ev = nullptr;
+  ACK(prof_begin(s, &ev));
   int rc = ale_refresh(s);
   if (rc) return rc;
+  ACK(prof_end(s, ev, 0));
   DevState& ds = s->ds;
   cudaStream_t st = s->stream;
   const double dtf = dt > 0 ? dt : 0.0;
   if (dtf == 0.0) {  // CFL bound of the current state on the current mesh
+    ACK(prof_begin(s, &ev));
     k_ale_dt_reset<<<1, 1, 0, st>>>(ds.dtmin);
     ACK(cudaGetLastError());
     ACK(s->ops->stable_dt(ds, s->ph, 0, st));
+    ACK(prof_end(s, ev, 6));
   }
   DevState d2 = ds;
   d2.perm = A.ident;  // reconstruction values in internal cell order
+  ACK(prof_begin(s, &ev));
   ACK(s->ops->reconstruct(d2, s->ph, A.w, st));
+  ACK(prof_end(s, ev, 1));
+  ACK(prof_begin(s, &ev));
   if (A.d == 3) {
     if (A.fp32 && A.M == 1)
       k_ale_pred3_32<1><<<nblk(ds.N, 128), 128, 0, st>>>(A.tab3f, A.w, ds.Q, A.X, A.vol, ds.N, s->ph.niter, dtf,
@@ -1224,9 +1263,13 @@ int ale_step(cweno_solver* s, double dt) {
       k_ale_pred3<2><<<nblk(ds.N, 128), 128, 0, st>>>(A.tab3, A.w, ds.Q, A.X, A.vol, ds.N, s->ph.niter, dtf,
                                                        s->prm.cfl, ds.dtmin, A.qhat, A.vcon);
     ACK(cudaGetLastError());
+    ACK(prof_end(s, ev, 2));
+    ACK(prof_begin(s, &ev));
     k_ale_nodes3<<<nblk(A.nvert, 256), 256, 0, st>>>(A.start, A.ent, A.vcon, A.Xv, A.nvert, dtf, s->prm.cfl,
                                                       ds.dtmin, A.Xv1);
     ACK(cudaGetLastError());
+    ACK(prof_end(s, ev, 3));
+    ACK(prof_begin(s, &ev));
     if (A.fp32 && A.M == 1)
       k_ale_flux3_32<1><<<nblk(ds.F, 128), 128, 0, st>>>(A.tab3f, s->prm.gamma, A.ftab32, ds.fL, ds.fR, ds.codeL,
                                                           ds.codeR, A.gv, A.shift, A.Xv, A.Xv1, A.bary, A.qhat32,
@@ -1244,10 +1287,13 @@ int ale_step(cweno_solver* s, double dt) {
                                                        A.shift, A.Xv, A.Xv1, A.bary, A.qhat, ds.Q, ds.N, ds.F, dtf,
                                                        s->prm.cfl, ds.dtmin, A.G);
     ACK(cudaGetLastError());
+    ACK(prof_end(s, ev, 4));
+    ACK(prof_begin(s, &ev));
     k_ale_update3<<<nblk(ds.N, 256), 256, 0, st>>>(ds.cellface, A.G, A.gv, A.shift, A.Xv1, A.vol, ds.N, ds.F,
                                                     s->prm.gamma, dtf, s->prm.cfl, ds.dtmin, ds.Q, ds.Qp, ds.time,
                                                     ds.status);
     ACK(cudaGetLastError());
+    ACK(prof_end(s, ev, 5));
     std::swap(A.Xv, A.Xv1);
     A.fresh = false;
     return CWENO_OK;
@@ -1257,18 +1303,25 @@ int ale_step(cweno_solver* s, double dt) {
     case 2: ACK(launch_pred<2>(A, s, dtf, st)); break;
     default: ACK(launch_pred<3>(A, s, dtf, st)); break;
   }
+  ACK(prof_end(s, ev, 2));
+  ACK(prof_begin(s, &ev));
   k_ale_nodes<<<nblk(A.nvert, 256), 256, 0, st>>>(A.start, A.ent, A.vcon, A.Xv, A.nvert, dtf, s->prm.cfl, ds.dtmin,
                                                    A.Xv1);
   ACK(cudaGetLastError());
+  ACK(prof_end(s, ev, 3));
+  ACK(prof_begin(s, &ev));
   switch (A.M) {
     case 1: ACK(launch_flux<1>(A, s, dtf, st)); break;
     case 2: ACK(launch_flux<2>(A, s, dtf, st)); break;
     default: ACK(launch_flux<3>(A, s, dtf, st)); break;
   }
+  ACK(prof_end(s, ev, 4));
+  ACK(prof_begin(s, &ev));
   k_ale_update<<<nblk(ds.N, 256), 256, 0, st>>>(ds.cellface, A.G, A.gv, A.shift, A.Xv1, A.vol, ds.N, ds.F,
                                                  s->prm.gamma, dtf, s->prm.cfl, ds.dtmin, ds.Q, ds.Qp, ds.time,
                                                  ds.status);
   ACK(cudaGetLastError());
+  ACK(prof_end(s, ev, 5));
   std::swap(A.Xv, A.Xv1);
   A.fresh = false;
   return CWENO_OK;

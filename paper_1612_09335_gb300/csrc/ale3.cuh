@@ -263,8 +263,22 @@ __global__ void __launch_bounds__(128) k_ale_pred3(const __grid_constant__ AleTa
   double qb[5];
   for (int v = 0; v < 5; ++v) qb[v] = Q[v * N + i];
   if (t.pos) {
+    // fallback: a tau > 0 node inadmissible or outside [1/2 min, 2 max] of
+    // the tau = 0 nodes' density and pressure (the triangle path's rule)
+    double r0 = 1e300, r1 = -1e300, p0 = 1e300, p1 = -1e300;
+    for (int l = 0; l < L0; ++l) {
+      const double pl = pressure3(q[l], t.gamma);
+      r0 = fmin(r0, q[l][0]);
+      r1 = fmax(r1, q[l][0]);
+      p0 = fmin(p0, pl);
+      p1 = fmax(p1, pl);
+    }
     bool ok = true;
-    for (int l = L0; l < L; ++l) ok = ok && admissible3(q[l], t.gamma);
+    for (int l = L0; l < L; ++l) {
+      const double pl = pressure3(q[l], t.gamma);
+      ok = ok && admissible3(q[l], t.gamma) && q[l][0] >= 0.5 * r0 && q[l][0] <= 2.0 * r1 && pl >= 0.5 * p0 &&
+           pl <= 2.0 * p1;
+    }
     if (!ok)
       for (int l = 0; l < L; ++l)
         for (int v = 0; v < 5; ++v) q[l][v] = qb[v];
@@ -593,12 +607,27 @@ __global__ void __launch_bounds__(128) k_ale_pred3_32(const __grid_constant__ Al
       }
     }
   }
-  if (t.pos) {
+  if (t.pos) {  // the fallback rule of k_ale_pred3, on absolute states
+    auto pres = [&](const float* qa) {
+      return (t.gamma - 1.0f) * (qa[4] - 0.5f * (qa[1] * qa[1] + qa[2] * qa[2] + qa[3] * qa[3]) / qa[0]);
+    };
+    float r0 = 3e38f, r1 = -3e38f, p0 = 3e38f, p1 = -3e38f;
+    for (int l = 0; l < L0; ++l) {
+      float qa[5];
+      for (int v = 0; v < 5; ++v) qa[v] = qb[v] + q[l][v];
+      const float pl = pres(qa);
+      r0 = fminf(r0, qa[0]);
+      r1 = fmaxf(r1, qa[0]);
+      p0 = fminf(p0, pl);
+      p1 = fmaxf(p1, pl);
+    }
     bool ok = true;
     for (int l = L0; l < L; ++l) {
       float qa[5];
       for (int v = 0; v < 5; ++v) qa[v] = qb[v] + q[l][v];
-      ok = ok && admissible3f(qa, t.gamma);
+      const float pl = pres(qa);
+      ok = ok && admissible3f(qa, t.gamma) && qa[0] >= 0.5f * r0 && qa[0] <= 2.0f * r1 && pl >= 0.5f * p0 &&
+           pl <= 2.0f * p1;
     }
     if (!ok)
       for (int l = 0; l < L; ++l)

@@ -606,6 +606,22 @@ static cudaError_t take_event(cweno_solver* s, cudaEvent_t* e) {
   return cudaEventCreate(e);
 }
 
+cudaError_t prof_begin(cweno_solver* s, cudaEvent_t* e0) {
+  *e0 = nullptr;
+  if (!s->profile) return cudaSuccess;
+  cudaError_t e = take_event(s, e0);
+  return e == cudaSuccess ? cudaEventRecord(*e0, s->stream) : e;
+}
+
+cudaError_t prof_end(cweno_solver* s, cudaEvent_t e0, int k) {
+  if (!s->profile || !e0) return cudaSuccess;
+  cudaEvent_t e1 = nullptr;
+  cudaError_t e = take_event(s, &e1);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, s->stream);
+  if (e == cudaSuccess) s->ev_used.push_back({{e0, e1}, k});
+  return e;
+}
+
 int enqueue_step(cweno_solver* s, double dt, int cur) {
   DtArgs a;
   a.fixed = dt > 0 ? dt : 0.0;
@@ -718,18 +734,25 @@ int cweno_profile_enable(cweno_solver* s, int on) {
 }
 
 int cweno_profile_read(cweno_solver* s, double* ms, int64_t* launches) {
+  return cweno_profile_read_stages(s, ms, launches, 3);
+}
+
+int cweno_profile_read_stages(cweno_solver* s, double* ms, int64_t* launches, int nstages) {
   if (!s || !ms || !launches) return fail(CWENO_EINVAL, "null argument");
+  if (nstages < 1 || nstages > 8) return fail(CWENO_EINVAL, "nstages must be 1..8");
   CK(cudaSetDevice(s->dev));
   CK(cudaStreamSynchronize(s->stream));
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < nstages; ++k) {
     ms[k] = 0.0;
     launches[k] = 0;
   }
   for (auto& u : s->ev_used) {
     float t = 0.f;
     CK(cudaEventElapsedTime(&t, u.first.first, u.first.second));
-    ms[u.second] += t;
-    launches[u.second] += 1;
+    if (u.second < nstages) {
+      ms[u.second] += t;
+      launches[u.second] += 1;
+    }
     s->ev_pool.push_back(u.first.first);
     s->ev_pool.push_back(u.first.second);
   }

@@ -45,6 +45,10 @@ namespace cw {
 int fail(int code, const std::string& msg);
 int cuda_fail(cudaError_t e, const char* where);
 int enqueue_step(cweno_solver* s, double dt, int cur);
+// Profiling of one stage on the solver's stream, a no-op unless profiling is
+// on: prof_begin records the start event, prof_end the stop event of stage k.
+cudaError_t prof_begin(cweno_solver* s, cudaEvent_t* e0);
+cudaError_t prof_end(cweno_solver* s, cudaEvent_t e0, int k);
 const RefElem& ref_elem(int d, int M);
 size_t footprint_estimate(int d, int64_t nc, int64_t nf, int order, int pde, int precision);
 extern thread_local int g_setup_threads;

@@ -333,7 +333,17 @@ namespace {
 
 bool make_tab(const MeshHost& m, const RefElem& re, LsqTab& tab, std::string& err) {
   const int d = m.d, M = re.M;
+  // averages of degree-M polynomials: a rule exact to degree M.  The
+  // collapsed Gauss rule with (M + 2) / 2 points per direction is; for
+  // tetrahedra at M = 2 the four-point degree-2 rule of Hammer, Marlowe and
+  // Stroud (barycentric permutations of (a, b, b, b), a = (5 + 3 sqrt 5) / 20,
+  // b = (5 - sqrt 5) / 20, equal weights) is too, with half the points.
   SimplexQuad Q = simplex_quad(d, (M + 2) / 2);
+  if (d == 3 && M == 2) {
+    const double a = (5.0 + 3.0 * std::sqrt(5.0)) / 20.0, b = (5.0 - std::sqrt(5.0)) / 20.0;
+    Q.x = {{b, b, b}, {a, b, b}, {b, a, b}, {b, b, a}};
+    Q.w = {0.25, 0.25, 0.25, 0.25};
+  }
   if ((int)Q.w.size() > kMaxQ || re.psi.n > kMaxB || (2 * M + 3) * (M + 1) > kMaxRec) {
     err = "least-squares tables exceed the device setup limits";
     return false;

@@ -33,9 +33,10 @@ def test_moving_mesh_oracle_baseline_line():
     """The oracle's ALE step timed beside the moving-mesh bench line: a
     bounded sample, one host thread, the baseline keys of the contract."""
     import bench
-    r = bench.ale_oracle_rate(n=6, steps=1)
-    assert r["kind"] == "oracle" and r["cores"] == 1 and r["unit"] == "cell-updates/s"
-    assert r["value"] > 0 and math.isfinite(r["value"]) and "72 triangles" in r["sample"]
+    for dim, n, shape in ((2, 6, "72 cells (6x6x2 triangles"), (3, 3, "162 cells (3^3x6 tetrahedra")):
+        r = bench.ale_oracle_rate(dim=dim, n=n, steps=1)
+        assert r["kind"] == "oracle" and r["cores"] == 1 and r["unit"] == "cell-updates/s"
+        assert r["value"] > 0 and math.isfinite(r["value"]) and shape in r["sample"], r["sample"]
 
 
 @pytest.mark.parametrize("d,M", [(2, 2), (2, 3), (3, 2)])
