@@ -54,6 +54,9 @@ def shear_flow(wl, x):
 
 
 def inputs(wl, name):
+    if name == "explosion6":  # a cell of it takes the predictor's range fallback
+        m = wl.tet_mesh(6, lo=(-1, -1, -1), hi=(1, 1, 1), periodic=False, jitter=0.15, seed=1234)
+        return m, wl.explosion_averages(m, sub=4)
     if name == "shear":
         m = wl.tet_mesh(5, jitter=0.15, seed=31)                   # 750 cells, periodic
         return m, wl.cell_averages(m, lambda x: shear_flow(wl, x), n=4)
@@ -77,7 +80,7 @@ def bound(orc, mesh, order, Q, dt, name):
     return max(1e-12, 8.0 * worst)
 
 
-@pytest.mark.parametrize("name", ["shear", "explosion"])
+@pytest.mark.parametrize("name", ["shear", "explosion", "explosion6"])
 @pytest.mark.parametrize("order", [2, 3])
 def test_one_ale3d_step_matches_oracle(cw, orc, wl, name, order):
     mesh, Q = inputs(wl, name)
@@ -170,7 +173,7 @@ def solver32(cw, mesh, order, motion=LAGRANGE):
     return cw.Solver(cw.Mesh.from_workload(mesh), order, EULER, cw.FP32_MIXED, mesh_motion=motion)
 
 
-@pytest.mark.parametrize("name", ["shear", "explosion"])
+@pytest.mark.parametrize("name", ["shear", "explosion", "explosion6"])
 @pytest.mark.parametrize("order", [2, 3])
 def test_fp32_mixed_ale3d_step_within_bounds(cw, orc, wl, name, order):
     mesh, Q = inputs(wl, name)

@@ -181,3 +181,25 @@ def test_ale3d_conservation_on_a_deforming_periodic_mesh(orc, wl):
     assert np.std(vol1 / vol0) > 1e-5                              # ... and deformed
     assert abs(vol1.sum() - vol0.sum()) < 1e-13                    # a periodic domain keeps its volume
     assert np.abs(vol1 @ Q - tot0).max() / np.abs(tot0).max() < 1e-13
+
+
+def test_lagrangian_predictor_fallback_on_the_relaxed_range(orc, wl):
+    """The positivity safeguard's predictor fallback on moving meshes: a cell
+    cut by the explosion's sphere whose Lagrangian Picard iteration ends on
+    admissible values outside [1/2 min, 2 max] of its tau = 0 nodes' density
+    or pressure (checked with the safeguard off) is sent to its cell average
+    at every node (safeguard on)."""
+    mesh = wl.tet_mesh(6, lo=(-1, -1, -1), hi=(1, 1, 1), periodic=False, jitter=0.15, seed=1234)
+    Q0 = wl.explosion_averages(mesh, sub=4)
+    cell = 343
+    raw = orc.Oracle(mesh, 3, params=orc.default_params(3, EULER, order=3, positivity=False))
+    dt = raw.stable_dt(Q0)
+    q, _ = raw.ale_predictor(Q0, dt, cell, mode=1)
+    L0 = raw.Mc
+    p = 0.4 * (q[:, 4] - 0.5 * (q[:, 1] ** 2 + q[:, 2] ** 2 + q[:, 3] ** 2) / q[:, 0])
+    assert (q[L0:, 0] > 0).all() and (p[L0:] > 0).all()            # admissible ...
+    out = ((q[L0:, 0] < 0.5 * q[:L0, 0].min()) | (q[L0:, 0] > 2 * q[:L0, 0].max()) |
+           (p[L0:] < 0.5 * p[:L0].min()) | (p[L0:] > 2 * p[:L0].max()))
+    assert out.any()                                                # ... but out of range
+    qs, _ = orc.Oracle(mesh, 3).ale_predictor(Q0, dt, cell, mode=1)
+    assert np.array_equal(qs, np.tile(Q0[cell], (len(qs), 1)))
