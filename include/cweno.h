@@ -6,9 +6,10 @@
  * WENO schemes on unstructured meshes" (arXiv 1612.09335).  One time step
  * is: CWENO reconstruction (Sec. 2.1), local space-time Galerkin predictor
  * (Sec. 2.2), space-time-quadrature Rusanov face fluxes and the conservative
- * one-step update (Sec. 2.4, Eq. PDEfinal with zero mesh velocity).  On 2D
- * triangle meshes the same step also runs on a moving mesh (direct ALE,
- * Secs. 2.2-2.4: cweno_params.mesh_motion, cweno_get_vertices).
+ * one-step update (Sec. 2.4, Eq. PDEfinal with zero mesh velocity).  For
+ * the Euler equations the same step also runs on a moving mesh (direct ALE,
+ * Secs. 2.2-2.4: cweno_params.mesh_motion, cweno_get_vertices): triangles at
+ * orders 2..4, tetrahedra at orders 2..3.
  *
  * Conventions for every call:
  *   - Return value: CWENO_OK (0) or a negative CWENO_E* code.  A message
@@ -101,8 +102,9 @@ typedef struct {
                           signal speed of the two sides' space-time face
                           averages */
   int mesh_motion;     /* CWENO_MOTION_FIXED (default), _LAGRANGE or _STILL.
-                          Moving meshes: dim 2, Euler, order 2..4, Rusanov
-                          flux, FP64 or FP32-mixed (EINVAL otherwise); the
+                          Moving meshes: Euler, Rusanov flux, FP64 or
+                          FP32-mixed, order 2..4 on triangles and 2..3 on
+                          tetrahedra (EINVAL otherwise); the
                           stencils are chosen on the initial mesh and kept
                           (the topology never changes), their least-squares
                           and sector matrices are rebuilt on the device every
@@ -241,7 +243,8 @@ void* cweno_stream(cweno_solver* s);
 
 /* Measurement: with profiling on, ader_cweno_step brackets each of its three
  * kernels (reconstruction + predictor, face fluxes, update) with CUDA events
- * on the solver's stream (fixed meshes; a moving-mesh step records none).  cweno_profile_read waits for the stream and
+ * on the solver's stream (fixed meshes; a moving-mesh step records its
+ * stages instead, cweno_profile_read_stages).  cweno_profile_read waits for the stream and
  * returns the summed device milliseconds per kernel (ms[0..2]) and the
  * number of launches per kernel since the last read, then clears them. */
 int cweno_profile_enable(cweno_solver* s, int on);

@@ -1,6 +1,6 @@
 """GB300 ADER-CWENO: the fixed-mesh ADER-CWENO finite-volume step of
-arXiv 1612.09335, and its direct ALE step on moving 2D meshes, as hand-written
-sm_103a CUDA behind a C ABI (include/cweno.h).
+arXiv 1612.09335, and its direct ALE step on moving triangle and tetrahedron
+meshes, as hand-written sm_103a CUDA behind a C ABI (include/cweno.h).
 
     from paper_1612_09335_gb300 import binding as cw, workloads as wl
     mesh, Q = wl.vortex_2d(64)
