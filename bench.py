@@ -606,7 +606,7 @@ def ale_mesh(wl, dim, n):
 ALE_ORDER = {2: 4, 3: 3}
 
 
-def ale_oracle_rate(dim=2, n=None, steps=3):
+def ale_oracle_rate(dim=2, n=None, steps=3, order=None):
     """The FP64 oracle's direct ALE step timed on the host (one thread) on a
     bounded sample of the same workload family: 40 x 40 x 2 triangles (3,200,
     the size of the paper's 2D Sedov mesh) or 6^3 x 6 tetrahedra (1,296), one
@@ -616,7 +616,7 @@ def ale_oracle_rate(dim=2, n=None, steps=3):
     n = n or (40 if dim == 2 else 6)
     mesh = ale_mesh(wl, dim, n)
     Q = wl.explosion_averages(mesh, sub=4)
-    o = oracle.Oracle(mesh, ALE_ORDER[dim])
+    o = oracle.Oracle(mesh, order or ALE_ORDER[dim])
     Q, _ = o.ale_step(Q, o.stable_dt(Q))
     t0 = time.perf_counter()
     for _ in range(steps):
@@ -646,7 +646,7 @@ def ale_stages(s, steps):
     return {k: {"ms": ms[q] / max(1, n[q]), "share": ms[q] / tot} for q, k in enumerate(ALE_STAGES) if n[q]}
 
 
-def ale_rate(cw, stream, barrier, dim=2, n=None, steps=None, warm=3):
+def ale_rate(cw, stream, barrier, dim=2, n=None, steps=None, warm=3, order=None):
     """Moving mesh: direct ALE steps (mesh velocity = fluid velocity) of the
     explosion (Sec. 3.2's ALE explosion, Table efficiency), Rusanov, on a
     transmissive mesh of [-1, 1]^d: 2D fourth order (M = 3) on n x n x 2
@@ -660,7 +660,7 @@ def ale_rate(cw, stream, barrier, dim=2, n=None, steps=None, warm=3):
     from paper_1612_09335_gb300 import workloads as wl
     n = n or (256 if dim == 2 else 63)
     steps = steps or (10 if dim == 2 else 4)
-    order = ALE_ORDER[dim]
+    order = order or ALE_ORDER[dim]
     mesh = ale_mesh(wl, dim, n)
     Q0 = wl.explosion_averages(mesh, sub=4)
     m = cw.Mesh.from_workload(mesh)
@@ -746,7 +746,7 @@ def run_ours(args):
         st = torch.cuda.Stream()
         torch.cuda.set_stream(st)
         print(json.dumps({"ale": ale_rate(cw, st, torch.cuda.synchronize, dim=args.ale_dim, n=args.n,
-                                          steps=args.steps, warm=args.warmup)}))
+                                          steps=args.steps, warm=args.warmup, order=args.ale_order)}))
         return
     name = args.workload
     cfg = WORKLOADS[name]
@@ -885,9 +885,12 @@ def run_ours(args):
         # moving mesh (direct ALE), rank 0's GPU
         out["ale_explosion2d_p3"] = ale_rate(cw, stream, barrier)
         out["ale_explosion3d_p2"] = ale_rate(cw, stream, barrier, dim=3)
+        # the paper's order for its moving-mesh tests (M = 3)
+        out["ale_explosion3d_p3"] = ale_rate(cw, stream, barrier, dim=3, order=4, steps=3, warm=2)
         if rank == 0 and not args.no_cpu_baseline:
             out["ale_explosion2d_p3"]["cpu_baseline"] = ale_oracle_rate()
             out["ale_explosion3d_p2"]["cpu_baseline"] = ale_oracle_rate(dim=3, steps=2)
+            out["ale_explosion3d_p3"]["cpu_baseline"] = ale_oracle_rate(dim=3, steps=1, order=4)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_run(name)
     if rank == 0:
@@ -940,6 +943,7 @@ def main():
     ap.add_argument("--no-other", action="store_true",
                     help="skip the 3D, MHD and fifth-order workloads, the flux variants and the moving mesh")
     ap.add_argument("--ale-dim", type=int, default=2, choices=[2, 3], help="with --only-ale: 2D or 3D explosion")
+    ap.add_argument("--ale-order", type=int, default=None, choices=[2, 3, 4], help="with --only-ale: order")
     ap.add_argument("--only-ale", action="store_true",
                     help="time only the moving-mesh (direct ALE) explosion; --n sets its resolution")
     ap.add_argument("--serve-requests", type=int, default=512,

@@ -8,8 +8,8 @@
  * (Sec. 2.2), space-time-quadrature Rusanov face fluxes and the conservative
  * one-step update (Sec. 2.4, Eq. PDEfinal with zero mesh velocity).  For
  * the Euler equations the same step also runs on a moving mesh (direct ALE,
- * Secs. 2.2-2.4: cweno_params.mesh_motion, cweno_get_vertices): triangles at
- * orders 2..4, tetrahedra at orders 2..3.
+ * Secs. 2.2-2.4: cweno_params.mesh_motion, cweno_get_vertices), orders
+ * 2..4.
  *
  * Conventions for every call:
  *   - Return value: CWENO_OK (0) or a negative CWENO_E* code.  A message
@@ -103,7 +103,7 @@ typedef struct {
                           averages */
   int mesh_motion;     /* CWENO_MOTION_FIXED (default), _LAGRANGE or _STILL.
                           Moving meshes: Euler, Rusanov flux, FP64 or
-                          FP32-mixed, order 2..4 on triangles and 2..3 on
+                          FP32-mixed, order 2..4 on triangles and
                           tetrahedra (EINVAL otherwise); the
                           stencils are chosen on the initial mesh and kept
                           (the topology never changes), their least-squares

@@ -850,6 +850,8 @@ struct Ale {
   AleTab tab;
   AleTab3 tab3;  // tetrahedra
   AleTab3f tab3f;
+  AleDer3* der3 = nullptr;  // device copies of the nodal derivative tables
+  AleDer3f* der3f = nullptr;
   double *Xv = nullptr, *Xv1 = nullptr, *shift = nullptr, *X = nullptr, *bary = nullptr, *vol = nullptr;
   double *w = nullptr, *qhat = nullptr, *vcon = nullptr, *G = nullptr, *ftab = nullptr;
   // FP32-mixed: tables, face basis and predictor deviations in FP32
@@ -921,6 +923,32 @@ cudaError_t launch_flux(Ale& A, cweno_solver* s, double dtf, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <int M>
+cudaError_t launch_pred3(Ale& A, cweno_solver* s, double dtf, cudaStream_t st) {
+  const DevState& ds = s->ds;
+  if (A.fp32)
+    k_ale_pred3_32<M><<<nblk(ds.N, 128), 128, 0, st>>>(A.tab3f, A.der3f, A.w, ds.Q, A.X, A.vol, ds.N, s->ph.niter,
+                                                        dtf, s->prm.cfl, ds.dtmin, A.qhat32, A.vcon);
+  else
+    k_ale_pred3<M><<<nblk(ds.N, 128), 128, 0, st>>>(A.tab3, A.der3, A.w, ds.Q, A.X, A.vol, ds.N, s->ph.niter, dtf,
+                                                     s->prm.cfl, ds.dtmin, A.qhat, A.vcon);
+  return cudaGetLastError();
+}
+
+template <int M>
+cudaError_t launch_flux3(Ale& A, cweno_solver* s, double dtf, cudaStream_t st) {
+  const DevState& ds = s->ds;
+  if (A.fp32)
+    k_ale_flux3_32<M><<<nblk(ds.F, 128), 128, 0, st>>>(A.tab3f, s->prm.gamma, A.ftab32, ds.fL, ds.fR, ds.codeL,
+                                                        ds.codeR, A.gv, A.shift, A.Xv, A.Xv1, A.bary, A.qhat32, ds.Q,
+                                                        ds.N, ds.F, dtf, s->prm.cfl, ds.dtmin, A.G);
+  else
+    k_ale_flux3<M><<<nblk(ds.F, 128), 128, 0, st>>>(A.tab3, A.ftab, ds.fL, ds.fR, ds.codeL, ds.codeR, A.gv, A.shift,
+                                                     A.Xv, A.Xv1, A.bary, A.qhat, ds.Q, ds.N, ds.F, dtf, s->prm.cfl,
+                                                     ds.dtmin, A.G);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 // Per-step rebuild for a moving mesh: this unit keeps FMA contraction (the
@@ -954,6 +982,9 @@ int ale_matrices_device(const MeshHost& m, const RefElem& re, const double* d_X,
         break;
       case 2: e = fp32 ? launch_sectors<3, 2, float>(d_X, d_bary, d_sec, m.nc, tab, (float*)d_Binv, d_bad, st)
                        : launch_sectors<3, 2, double>(d_X, d_bary, d_sec, m.nc, tab, (double*)d_Binv, d_bad, st);
+        break;
+      case 3: e = fp32 ? launch_sectors<3, 3, float>(d_X, d_bary, d_sec, m.nc, tab, (float*)d_Binv, d_bad, st)
+                       : launch_sectors<3, 3, double>(d_X, d_bary, d_sec, m.nc, tab, (double*)d_Binv, d_bad, st);
         break;
       default: e = cudaErrorInvalidValue;
     }
@@ -1087,8 +1118,8 @@ int ale_create(cweno_solver* s, const MeshHost& m, std::string& err) {
 // periodic shifts and scratch of the moving mesh.
 int ale_create3(cweno_solver* s, const MeshHost& m, std::string& err) {
   const RefElem& re = *s->re;
-  if (s->pde != CWENO_EULER || re.M < 1 || re.M > 2 || s->prm.flux != CWENO_FLUX_RUSANOV) {
-    err = "moving tetrahedral meshes are built for Euler, order 2..3, Rusanov flux";
+  if (s->pde != CWENO_EULER || re.M < 1 || re.M > 3 || s->prm.flux != CWENO_FLUX_RUSANOV) {
+    err = "moving tetrahedral meshes are built for Euler, order 2..4, Rusanov flux";
     return CWENO_EINVAL;
   }
   auto A = std::make_shared<Ale>();
@@ -1110,7 +1141,10 @@ int ale_create3(cweno_solver* s, const MeshHost& m, std::string& err) {
   }
   AleTab3& t = A->tab3;
   std::memset(&t, 0, sizeof(t));
+  std::vector<AleDer3> hd(1);
   {
+    AleDer3& dd = hd[0];
+    std::memset(&dd, 0, sizeof(dd));
     double dmax = 0.0;
     for (double v : re.Dxi) dmax = std::max(dmax, std::fabs(v));
     for (int e = 0; e < 3; ++e)
@@ -1119,12 +1153,12 @@ int ale_create3(cweno_solver* s, const MeshHost& m, std::string& err) {
         for (int l = 0; l < L; ++l) {
           const double v = re.Dxi[((size_t)e * L + n) * L + l];
           if (std::fabs(v) <= 1e-12 * dmax) continue;  // exact zeros, rounded in extended precision
-          t.val[e][n][c] = v;
-          t.col[e][n][c] = (uint8_t)l;
+          dd.val[e][n][c] = v;
+          dd.col[e][n][c] = (uint8_t)l;
           ++c;
-          if (l < L0) t.nnz0[e][n] = c;  // columns ascend: tau = 0 nodes first
+          if (l < L0) dd.nnz0[e][n] = c;  // columns ascend: tau = 0 nodes first
         }
-        t.nnz[e][n] = c;
+        dd.nnz[e][n] = c;
       }
   }
   for (int k = 0; k < L1; ++k) {
@@ -1182,6 +1216,7 @@ int ale_create3(cweno_solver* s, const MeshHost& m, std::string& err) {
   ACK(A->put(&A->ident, ident, st));
   ACK(A->put(&A->Xv, m.xyz, st));
   ACK(A->put(&A->ftab, re.ftab, st));
+  ACK(A->put(&A->der3, hd, st));
   ACK(A->alloc(&A->Xv1, (size_t)nv * 3, st));
   ACK(A->alloc(&A->X, (size_t)N * 12, st));
   ACK(A->alloc(&A->bary, (size_t)N * 3, st));
@@ -1194,6 +1229,9 @@ int ale_create3(cweno_solver* s, const MeshHost& m, std::string& err) {
   if (s->prec == CWENO_FP32_MIXED) {
     A->fp32 = true;
     A->tab3f = ale_tab3_float(t);
+    std::vector<AleDer3f> hdf(1);
+    ale_der3_float(hd[0], hdf[0]);
+    ACK(A->put(&A->der3f, hdf, st));
     std::vector<float> f32(re.ftab.begin(), re.ftab.end());
     ACK(A->put(&A->ftab32, f32, st));
     ACK(A->alloc(&A->qhat32, (size_t)N * L * 5, st));
@@ -1250,19 +1288,11 @@ int ale_step(cweno_solver* s, double dt) {
   ACK(prof_end(s, ev, 1));
   ACK(prof_begin(s, &ev));
   if (A.d == 3) {
-    if (A.fp32 && A.M == 1)
-      k_ale_pred3_32<1><<<nblk(ds.N, 128), 128, 0, st>>>(A.tab3f, A.w, ds.Q, A.X, A.vol, ds.N, s->ph.niter, dtf,
-                                                          s->prm.cfl, ds.dtmin, A.qhat32, A.vcon);
-    else if (A.fp32)
-      k_ale_pred3_32<2><<<nblk(ds.N, 128), 128, 0, st>>>(A.tab3f, A.w, ds.Q, A.X, A.vol, ds.N, s->ph.niter, dtf,
-                                                          s->prm.cfl, ds.dtmin, A.qhat32, A.vcon);
-    else if (A.M == 1)
-      k_ale_pred3<1><<<nblk(ds.N, 128), 128, 0, st>>>(A.tab3, A.w, ds.Q, A.X, A.vol, ds.N, s->ph.niter, dtf,
-                                                       s->prm.cfl, ds.dtmin, A.qhat, A.vcon);
-    else
-      k_ale_pred3<2><<<nblk(ds.N, 128), 128, 0, st>>>(A.tab3, A.w, ds.Q, A.X, A.vol, ds.N, s->ph.niter, dtf,
-                                                       s->prm.cfl, ds.dtmin, A.qhat, A.vcon);
-    ACK(cudaGetLastError());
+    switch (A.M) {
+      case 1: ACK(launch_pred3<1>(A, s, dtf, st)); break;
+      case 2: ACK(launch_pred3<2>(A, s, dtf, st)); break;
+      default: ACK(launch_pred3<3>(A, s, dtf, st)); break;
+    }
     ACK(prof_end(s, ev, 2));
     ACK(prof_begin(s, &ev));
     k_ale_nodes3<<<nblk(A.nvert, 256), 256, 0, st>>>(A.start, A.ent, A.vcon, A.Xv, A.nvert, dtf, s->prm.cfl,
@@ -1270,23 +1300,11 @@ int ale_step(cweno_solver* s, double dt) {
     ACK(cudaGetLastError());
     ACK(prof_end(s, ev, 3));
     ACK(prof_begin(s, &ev));
-    if (A.fp32 && A.M == 1)
-      k_ale_flux3_32<1><<<nblk(ds.F, 128), 128, 0, st>>>(A.tab3f, s->prm.gamma, A.ftab32, ds.fL, ds.fR, ds.codeL,
-                                                          ds.codeR, A.gv, A.shift, A.Xv, A.Xv1, A.bary, A.qhat32,
-                                                          ds.Q, ds.N, ds.F, dtf, s->prm.cfl, ds.dtmin, A.G);
-    else if (A.fp32)
-      k_ale_flux3_32<2><<<nblk(ds.F, 128), 128, 0, st>>>(A.tab3f, s->prm.gamma, A.ftab32, ds.fL, ds.fR, ds.codeL,
-                                                          ds.codeR, A.gv, A.shift, A.Xv, A.Xv1, A.bary, A.qhat32,
-                                                          ds.Q, ds.N, ds.F, dtf, s->prm.cfl, ds.dtmin, A.G);
-    else if (A.M == 1)
-      k_ale_flux3<1><<<nblk(ds.F, 128), 128, 0, st>>>(A.tab3, A.ftab, ds.fL, ds.fR, ds.codeL, ds.codeR, A.gv,
-                                                       A.shift, A.Xv, A.Xv1, A.bary, A.qhat, ds.Q, ds.N, ds.F, dtf,
-                                                       s->prm.cfl, ds.dtmin, A.G);
-    else
-      k_ale_flux3<2><<<nblk(ds.F, 128), 128, 0, st>>>(A.tab3, A.ftab, ds.fL, ds.fR, ds.codeL, ds.codeR, A.gv,
-                                                       A.shift, A.Xv, A.Xv1, A.bary, A.qhat, ds.Q, ds.N, ds.F, dtf,
-                                                       s->prm.cfl, ds.dtmin, A.G);
-    ACK(cudaGetLastError());
+    switch (A.M) {
+      case 1: ACK(launch_flux3<1>(A, s, dtf, st)); break;
+      case 2: ACK(launch_flux3<2>(A, s, dtf, st)); break;
+      default: ACK(launch_flux3<3>(A, s, dtf, st)); break;
+    }
     ACK(prof_end(s, ev, 4));
     ACK(prof_begin(s, &ev));
     k_ale_update3<<<nblk(ds.N, 256), 256, 0, st>>>(ds.cellface, A.G, A.gv, A.shift, A.Xv1, A.vol, ds.N, ds.F,

@@ -1,6 +1,6 @@
 // Moving meshes in three space dimensions: the direct ALE step (Secs.
-// 2.2-2.4) on tetrahedra, Euler equations, FP64 or FP32-mixed, orders 2 and 3
-// (M = 1, 2),
+// 2.2-2.4) on tetrahedra, Euler equations, FP64 or FP32-mixed, orders 2 to 4
+// (M = 1..3),
 // Rusanov flux with the ALE Jacobian.  The same step as the triangle path of
 // ale.cu, kernel for kernel:
 //   k_ale_geom3    unwrapped vertices, |T|, barycentre, h = 6|T| / surface
@@ -20,17 +20,24 @@
 //   k_ale_update3  Eq. (PDEfinal) with the new volume of the moved vertices.
 // Included by ale.cu (shares its unnamed-namespace helpers).
 
-constexpr int kL3 = 15, kL03 = 10, kL13 = 5, kNQS3 = 9, kNQT3 = 3;
+constexpr int kL3 = 35, kL03 = 20, kL13 = 15, kNQS3 = 16, kNQT3 = 4;
 
-// Reference tables of one M (tetrahedra) in the arithmetic type T, a kernel
-// parameter.
+// Nodal derivative tables of one M (tetrahedra) in the arithmetic type T, in
+// device memory (at M = 3 they outgrow the kernel-parameter space): d theta_l
+// / d xi_e at node n, nonzero entries only, tau = 0 columns first.
 template <typename T>
-struct AleTab3T {
-  // d theta_l / d xi_e at node n, nonzero entries only, tau = 0 columns first
+struct AleDer3T {
   T val[3][kL3][kL3];
   uint8_t col[3][kL3][kL3];
   int nnz[3][kL3];
   int nnz0[3][kL3];
+};
+using AleDer3 = AleDer3T<double>;
+using AleDer3f = AleDer3T<float>;
+
+// The other reference tables of one M, a kernel parameter.
+template <typename T>
+struct AleTab3T {
   T Gal[kL13][kL3];  // (K_tau^1)^-1 M^1
   T C0[kL13][kL03];  // constant extension in time
   T Wv[4][kL3];      // int_0^1 theta_l(vertex v, tau) dtau
@@ -43,8 +50,7 @@ struct AleTab3T {
 using AleTab3 = AleTab3T<double>;
 using AleTab3f = AleTab3T<float>;
 
-inline AleTab3f ale_tab3_float(const AleTab3& t) {
-  AleTab3f o;
+inline void ale_der3_float(const AleDer3& t, AleDer3f& o) {
   std::memset(&o, 0, sizeof(o));
   for (int e = 0; e < 3; ++e)
     for (int n = 0; n < kL3; ++n) {
@@ -55,6 +61,11 @@ inline AleTab3f ale_tab3_float(const AleTab3& t) {
       o.nnz[e][n] = t.nnz[e][n];
       o.nnz0[e][n] = t.nnz0[e][n];
     }
+}
+
+inline AleTab3f ale_tab3_float(const AleTab3& t) {
+  AleTab3f o;
+  std::memset(&o, 0, sizeof(o));
   for (int k = 0; k < kL13; ++k) {
     for (int l = 0; l < kL3; ++l) o.Gal[k][l] = (float)t.Gal[k][l];
     for (int n = 0; n < kL03; ++n) o.C0[k][n] = (float)t.C0[k][n];
@@ -154,7 +165,8 @@ __device__ __forceinline__ void ale_flux3(const double* q, double gamma, int mod
 // (N x L x 5) and, per vertex k of the cell, (mu V_kj, mu) with mu =
 // rho_j |T_j| (N x 4 x 4).
 template <int M>
-__global__ void __launch_bounds__(128) k_ale_pred3(const __grid_constant__ AleTab3 t, const double* __restrict__ w,
+__global__ void __launch_bounds__(128) k_ale_pred3(const __grid_constant__ AleTab3 t,
+                                                   const AleDer3* __restrict__ dr, const double* __restrict__ w,
                                                    const double* __restrict__ Q, const double* __restrict__ X,
                                                    const double* __restrict__ vol, int64_t N, int niter,
                                                    double dt_fixed, double cfl, const unsigned long long* dtmin,
@@ -192,9 +204,9 @@ __global__ void __launch_bounds__(128) k_ale_pred3(const __grid_constant__ AleTa
       for (int e = 0; e < 3; ++e) {
         double* c = c0[n][e];
         for (int m = 0; m < NC; ++m) c[m] = 0.0;
-        for (int j = 0; j < t.nnz0[e][n]; ++j) {
-          const int l = t.col[e][n][j];
-          const double dd = t.val[e][n][j];
+        for (int j = 0; j < dr->nnz0[e][n]; ++j) {
+          const int l = dr->col[e][n][j];
+          const double dd = dr->val[e][n][j];
           for (int a = 0; a < 3; ++a) c[a] += dd * x[l][a];
           for (int v = 0; v < 5; ++v) {
             c[3 + v] += dd * q[l][v];
@@ -216,10 +228,10 @@ __global__ void __launch_bounds__(128) k_ale_pred3(const __grid_constant__ AleTa
           dq[e][v] = c[3 + v];
           for (int m = 0; m < 3; ++m) df[e][m][v] = c[8 + m * 5 + v];
         }
-        const int cnt = t.nnz[e][n];
-        for (int j = t.nnz0[e][n]; j < cnt; ++j) {
-          const int l = t.col[e][n][j];
-          const double dd = t.val[e][n][j];
+        const int cnt = dr->nnz[e][n];
+        for (int j = dr->nnz0[e][n]; j < cnt; ++j) {
+          const int l = dr->col[e][n][j];
+          const double dd = dr->val[e][n][j];
           for (int a = 0; a < 3; ++a) dx[e][a] += dd * x[l][a];
           for (int v = 0; v < 5; ++v) {
             dq[e][v] += dd * q[l][v];
@@ -484,7 +496,8 @@ __device__ __forceinline__ bool admissible3f(const float* q, float g) {
 // Writes the state deviations q_hat - Q_i (N x L x 5, FP32) and (mu V_kj, mu)
 // per vertex of the cell in FP64.
 template <int M>
-__global__ void __launch_bounds__(128) k_ale_pred3_32(const __grid_constant__ AleTab3f t, const double* __restrict__ w,
+__global__ void __launch_bounds__(128) k_ale_pred3_32(const __grid_constant__ AleTab3f t,
+                                                      const AleDer3f* __restrict__ dr, const double* __restrict__ w,
                                                       const double* __restrict__ Q, const double* __restrict__ X,
                                                       const double* __restrict__ vol, int64_t N, int niter,
                                                       double dt_fixed, double cfl, const unsigned long long* dtmin,
@@ -536,9 +549,9 @@ __global__ void __launch_bounds__(128) k_ale_pred3_32(const __grid_constant__ Al
       for (int e = 0; e < 3; ++e) {
         float* c = c0[n][e];
         for (int m = 0; m < NC; ++m) c[m] = 0.0f;
-        for (int j = 0; j < t.nnz0[e][n]; ++j) {
-          const int l = t.col[e][n][j];
-          const float dd = t.val[e][n][j];
+        for (int j = 0; j < dr->nnz0[e][n]; ++j) {
+          const int l = dr->col[e][n][j];
+          const float dd = dr->val[e][n][j];
           for (int a = 0; a < 3; ++a) c[a] += dd * x[l][a];
           for (int v = 0; v < 5; ++v) {
             c[3 + v] += dd * q[l][v];
@@ -560,10 +573,10 @@ __global__ void __launch_bounds__(128) k_ale_pred3_32(const __grid_constant__ Al
           dq[e][v] = c[3 + v];
           for (int m = 0; m < 3; ++m) df[e][m][v] = c[8 + m * 5 + v];
         }
-        const int cnt = t.nnz[e][n];
-        for (int j = t.nnz0[e][n]; j < cnt; ++j) {
-          const int l = t.col[e][n][j];
-          const float dd = t.val[e][n][j];
+        const int cnt = dr->nnz[e][n];
+        for (int j = dr->nnz0[e][n]; j < cnt; ++j) {
+          const int l = dr->col[e][n][j];
+          const float dd = dr->val[e][n][j];
           for (int a = 0; a < 3; ++a) dx[e][a] += dd * x[l][a];
           for (int v = 0; v < 5; ++v) {
             dq[e][v] += dd * q[l][v];

@@ -275,8 +275,8 @@ int cweno_setup(const cweno_mesh* mesh, int order, int pde, int precision, const
       prm.mesh_motion != CWENO_MOTION_STILL)
     return fail(CWENO_EINVAL, "unknown mesh motion");
   if (prm.mesh_motion != CWENO_MOTION_FIXED &&
-      (pde != CWENO_EULER || order > (m.d == 2 ? 4 : 3) || prm.flux != CWENO_FLUX_RUSANOV))
-    return fail(CWENO_EINVAL, "moving meshes are built for Euler, Rusanov flux, order 2..4 (2D) or 2..3 (3D)");
+      (pde != CWENO_EULER || order > 4 || prm.flux != CWENO_FLUX_RUSANOV))
+    return fail(CWENO_EINVAL, "moving meshes are built for Euler, Rusanov flux, order 2..4");
   const int M = order - 1;
   std::unique_ptr<cweno_solver> s(new cweno_solver());
   s->dim = m.d;

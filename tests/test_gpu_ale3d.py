@@ -1,12 +1,13 @@
 """Moving tetrahedral meshes (direct ALE in three space dimensions, Secs.
 2.2-2.4) through the C ABI against the FP64 oracle's ALE step on the same
 seeded inputs: cell averages and vertex positions after one and after
-several steps (the same dt given to both), orders 2 and 3, FP64 and
+several steps (the same dt given to both), orders 2 to 4, FP64 and
 FP32-mixed, a periodic
 deforming flow and a transmissive explosion on meshes of 750 tetrahedra (five
 128-cell blocks and a ragged tail).
 
-Bound: 1e-12 relative per variable (as on fixed meshes), or for the
+Bound: 1e-12 relative per variable (as on fixed meshes; 1e-11 at order 4,
+where the oracle's FP64 Galerkin solve rounds at about 1e-12), or for the
 discontinuous data 8x the oracle's own response to one-ulp input
 perturbations; vertices to 1e-13 of the domain size."""
 import numpy as np
@@ -69,19 +70,23 @@ def solver(cw, mesh, order, motion=LAGRANGE):
 
 
 def bound(orc, mesh, order, Q, dt, name):
+    # order 4: the oracle solves the Galerkin system of Eq. (CGfinal) in FP64
+    # every iteration (condition number ~1e4) while the CUDA path applies
+    # (K_tau^1)^-1 M^1 formed in extended precision
+    base = 1e-12 if order < 4 else 1e-11
     if name == "shear":
-        return 1e-12
+        return base
     ref = orc.Oracle(mesh, order).ale_step(Q, dt)[0]
     rng = np.random.default_rng(3)
     worst = 0.0
     for _ in range(2):
         Qp = Q * (1.0 + 2.0 ** -52 * rng.choice([-1.0, 1.0], size=Q.shape))
         worst = max(worst, relerr(orc.Oracle(mesh, order).ale_step(Qp, dt)[0], ref))
-    return max(1e-12, 8.0 * worst)
+    return max(base, 8.0 * worst)
 
 
-@pytest.mark.parametrize("name", ["shear", "explosion", "explosion6"])
-@pytest.mark.parametrize("order", [2, 3])
+@pytest.mark.parametrize("name,order", [(n, o) for n in ("shear", "explosion", "explosion6") for o in (2, 3)] +
+                         [("shear", 4), ("explosion", 4)])
 def test_one_ale3d_step_matches_oracle(cw, orc, wl, name, order):
     mesh, Q = inputs(wl, name)
     o = orc.Oracle(mesh, order)
@@ -114,7 +119,7 @@ def test_five_ale3d_steps_match_oracle(cw, orc, wl, order):
     assert relerr(s.get_state(), Qo) < 1e-11
 
 
-@pytest.mark.parametrize("order", [2, 3])
+@pytest.mark.parametrize("order", [2, 3, 4])
 def test_still_tetrahedral_mesh_equals_fixed_mesh_path(cw, wl, order):
     mesh, Q = inputs(wl, "shear")
     a = solver(cw, mesh, order, STILL)
@@ -160,7 +165,7 @@ def test_ale3d_rejects_what_it_does_not_build(cw, wl):
     m = cw.Mesh.from_workload(wl.tet_mesh(3))
     for prec in (cw.FP64, cw.FP32_MIXED):
         with pytest.raises(cw.CwenoError):
-            cw.Solver(m, 4, EULER, prec, mesh_motion=LAGRANGE)     # order 4 on tetrahedra
+            cw.Solver(m, 4, EULER, prec, mesh_motion=LAGRANGE, flux=cw.FLUX_OSHER)
 
 
 # ---------------------------------------------------------------- FP32-mixed
@@ -173,8 +178,8 @@ def solver32(cw, mesh, order, motion=LAGRANGE):
     return cw.Solver(cw.Mesh.from_workload(mesh), order, EULER, cw.FP32_MIXED, mesh_motion=motion)
 
 
-@pytest.mark.parametrize("name", ["shear", "explosion", "explosion6"])
-@pytest.mark.parametrize("order", [2, 3])
+@pytest.mark.parametrize("name,order", [(n, o) for n in ("shear", "explosion", "explosion6") for o in (2, 3)] +
+                         [("shear", 4), ("explosion", 4)])
 def test_fp32_mixed_ale3d_step_within_bounds(cw, orc, wl, name, order):
     mesh, Q = inputs(wl, name)
     o = orc.Oracle(mesh, order)

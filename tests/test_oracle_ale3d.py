@@ -84,7 +84,7 @@ def test_space_time_normal3_still_and_translating_face(orc):
     assert abs(n[3] + dt * (V @ cr)) < 1e-15  # n~_t = -|n~_x| V.n
 
 
-@pytest.mark.parametrize("order", [2, 3])
+@pytest.mark.parametrize("order", [2, 3, 4])
 def test_ale3d_still_mesh_is_the_eulerian_step(orc, wl, order):
     mesh, Q = wl.density_wave_3d(5)
     dt = orc.Oracle(mesh, order).stable_dt(Q)
@@ -109,7 +109,7 @@ def test_ale3d_galilean_invariance(orc, wl, order):
     assert np.abs(a[:, 0] - Qm[:, 0]).max() > 1e-4  # the step did change the densities
 
 
-@pytest.mark.parametrize("order", [2, 3])
+@pytest.mark.parametrize("order", [2, 3, 4])
 def test_ale3d_constant_state_and_translation(orc, wl, order):
     mesh = wl.tet_mesh(4, jitter=0.15, seed=22)
     q = np.array([1.3, 0.39, -0.26, 0.13, 3.1])
@@ -118,11 +118,12 @@ def test_ale3d_constant_state_and_translation(orc, wl, order):
     x0 = mesh.xyz.copy()
     for _ in range(2):
         Q, xyz = o.ale_step(Q, 0.01, mode=1)
-    assert np.abs(Q - q).max() < 1e-13
+    # order 4: the Galerkin solve of Eq. (CGfinal) rounds the nodal states at ~1e-13
+    assert np.abs(Q - q).max() < (1e-13 if order < 4 else 5e-13)
     assert np.abs(xyz - x0 - 0.02 * q[1:4] / q[0]).max() < 1e-14
 
 
-@pytest.mark.parametrize("order", [2, 3])
+@pytest.mark.parametrize("order", [2, 3, 4])
 def test_vertex_velocity_weights_integrate_in_time_3d(orc, wl, order):
     o = orc.Oracle(wl.tet_mesh(3), order)
     W = o.ale_vertex_weights()
