@@ -321,10 +321,13 @@ def replica_rate(ws: int, units_per_rank: int, steps: int, seconds: float) -> fl
     return ws * units_per_rank * steps / seconds
 
 
-def cpu_baseline_run(name, seconds_budget=20.0, cells_hint=None):
+def cpu_baseline_run(name, seconds_budget=20.0, cells_hint=None, cw=None):
     """Time the FP64 oracle (single host thread, as it stands) on a bounded
     sample of the workload: the same scheme on a coarser mesh of the same
-    family, one untimed warm step (lazy per-cell setup), then timed steps."""
+    family, one untimed warm step (lazy per-cell setup), then timed steps.
+    With `cw` (the binding) the CUDA path in both precisions runs the same
+    steps from the same data and its per-variable errors against the
+    oracle's result are returned under "vs_oracle"."""
     import oracle
     from paper_1612_09335_gb300 import workloads as wl
     cfg = WORKLOADS[name]
@@ -336,6 +339,7 @@ def cpu_baseline_run(name, seconds_budget=20.0, cells_hint=None):
     else:
         n = max(4, int(round((target / 6) ** (1 / 3))))
     mesh, Q = make_inputs(name, n)
+    Q0 = Q.copy()
     o = oracle.Oracle(mesh, cfg["order"], cfg["pde"])
     dt = o.stable_dt(Q)
     Q = o.step(Q, dt)
@@ -350,6 +354,20 @@ def cpu_baseline_run(name, seconds_budget=20.0, cells_hint=None):
     out = dict(value=mesh.nc * steps / el, unit="cell-updates/s", cores=1, kind="oracle",
                sample=f"{mesh.nc} cells ({n}-cell grid of the same workload family), {steps} steps after one "
                       f"untimed warm step, single host thread")
+    if cw is not None:
+        vs = {"cells": mesh.nc, "steps": steps + 1, "dt": dt,
+              "reference": "the FP64 oracle's result on this sample (same mesh, initial data and time step)"}
+        m = cw.Mesh.from_workload(mesh)
+        for prec, key in ((cw.FP64, "fp64"), (cw.FP32_MIXED, "fp32_mixed")):
+            sv = cw.Solver(m, cfg["order"], cfg["pde"], prec)
+            sv.set_state(Q0)
+            for _ in range(steps + 1):
+                sv.step(dt)
+            acc = accuracy_metrics(mesh, Q0, sv.get_state(), Q)
+            vs[key] = {"L1_rel": acc["L1_rel"], "Linf_rel": acc["Linf_rel"]}
+            sv.close()
+        m.close()
+        out["vs_oracle"] = vs
     # the same oracle on all host cores (worker processes), a 4x larger sample
     n4 = 2 * n if cfg["dim"] == 2 else int(round(n * 4 ** (1 / 3)))
     v, cores, cells, sec = oracle_parallel_run(name, n4, steps=3)
@@ -892,7 +910,8 @@ def run_ours(args):
             out["ale_explosion3d_p2"]["cpu_baseline"] = ale_oracle_rate(dim=3, steps=2)
             out["ale_explosion3d_p3"]["cpu_baseline"] = ale_oracle_rate(dim=3, steps=1, order=4)
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline_run(name)
+        out["cpu_baseline"] = cpu_baseline_run(name, cw=cw)
+        out["accuracy_vs_oracle"] = out["cpu_baseline"].pop("vs_oracle")
     if rank == 0:
         print(json.dumps(out))
     if ws > 1:
