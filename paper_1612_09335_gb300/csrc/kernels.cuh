@@ -169,7 +169,7 @@ template <class C>
 struct CellTab {
   using T = typename C::T;
   T E[C::L0][C::MC1];
-  T Sig[C::MC1][C::MC1];
+  T Sig[C::MC1][C::MC1];  // Sigma's diagonal and its upper triangle doubled (symmetric form)
   T CE[C::L1][C::MC1];  // C0 E: known part of the unknown nodes, from w directly
   int sel[C::L1];       // tau = 0 lattice node below each unknown node
   T P[C::D][C::L1][C::L];
@@ -709,12 +709,14 @@ __device__ __forceinline__ void rec_pred_cell(const KArgs<C>& a, const CellTab<C
       }
       p0[l] = s * ilam0;
     }
+    // sigma = p^T Sigma p in the symmetric form: sum over l of p_l (Sigma_ll
+    // p_l + sum over m > l of 2 Sigma_lm p_m)
     T sig0 = T(0);
 #pragma unroll
     for (int l = 0; l < MC1; ++l) {
-      T t = T(0);
+      T t = tb.Sig[l][l] * p0[l];
 #pragma unroll
-      for (int m = 0; m < MC1; ++m) t += tb.Sig[l][m] * p0[m];
+      for (int m = l + 1; m < MC1; ++m) t += tb.Sig[l][m] * p0[m];
       sig0 += p0[l] * t;
     }
     T sig[NS];
@@ -724,9 +726,9 @@ __device__ __forceinline__ void rec_pred_cell(const KArgs<C>& a, const CellTab<C
       T s = T(0);
 #pragma unroll
       for (int l = 0; l < D; ++l) {
-        T t = T(0);
+        T t = tb.Sig[l][l] * g[sc][l][v];
 #pragma unroll
-        for (int m = 0; m < D; ++m) t += tb.Sig[l][m] * g[sc][m][v];
+        for (int m = l + 1; m < D; ++m) t += tb.Sig[l][m] * g[sc][m][v];
         s += g[sc][l][v] * t;
       }
       sig[sc] = s;
@@ -1810,7 +1812,8 @@ class OpsImpl final : public Ops {
     for (int n = 0; n < C::L0; ++n)
       for (int l = 0; l < C::MC1; ++l) tab_.E[n][l] = (T)re.E[n * C::MC1 + l];
     for (int l = 0; l < C::MC1; ++l)
-      for (int m = 0; m < C::MC1; ++m) tab_.Sig[l][m] = (T)re.Sigma[l * C::MC1 + m];
+      for (int m = 0; m < C::MC1; ++m)
+        tab_.Sig[l][m] = m == l ? (T)re.Sigma[l * C::MC1 + m] : m > l ? (T)(2.0 * re.Sigma[l * C::MC1 + m]) : T(0);
     for (int k = 0; k < C::L1; ++k)
       for (int l = 0; l < C::MC1; ++l) {
         double s = 0.0;
