@@ -104,6 +104,15 @@ __device__ __forceinline__ bool admissible3(const double* q, double g) {
   return fin && q[0] > 0.0 && pressure3(q, g) > 0.0;
 }
 
+// Face points per chunk of the face kernels: the largest divisor of np not
+// above cap.  The traces of a chunk's points are formed in one pass over
+// both sides' q_hat (read once per chunk instead of once per point).
+__host__ __device__ constexpr int point_chunk(int np, int cap) {
+  int c = cap;
+  while (c > 1 && np % c != 0) --c;
+  return c;
+}
+
 __device__ __forceinline__ double det3(const double* a, const double* b, const double* c) {
   return a[0] * (b[1] * c[2] - b[2] * c[1]) - a[1] * (b[0] * c[2] - b[2] * c[0]) + a[2] * (b[0] * c[1] - b[1] * c[0]);
 }
@@ -421,16 +430,45 @@ __global__ void __launch_bounds__(128) k_ale_flux3(const __grid_constant__ AleTa
   const double* qL = qhat + cl * L * 5;
   const double* qR = qhat + (cr >= 0 ? cr : cl) * L * 5;
   double acc[5] = {0, 0, 0, 0, 0};
-  for (int qp = 0; qp < NQS; ++qp)
-    for (int tt = 0; tt < NQT; ++tt) {
-      const double* bL = ftab + ((int64_t)(kL * NQT + tt) * NQS + qp) * L;
-      const double* bR = ftab + ((int64_t)(kR * NQT + tt) * NQS + qp) * L;
-      double qm[5] = {0, 0, 0, 0, 0}, qq[5] = {0, 0, 0, 0, 0};
-      for (int l = 0; l < L; ++l)
+  constexpr int NP = NQS * NQT, PC = point_chunk(NP, 4);
+  for (int p0 = 0; p0 < NP; p0 += PC) {
+    // traces of the chunk's points (point p = qp NQT + tt), q_hat read once
+    double qmc[PC][5], qqc[PC][5];
+#pragma unroll
+    for (int j = 0; j < PC; ++j)
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        qmc[j][v] = 0.0;
+        qqc[j][v] = 0.0;
+      }
+    for (int l = 0; l < L; ++l) {
+      double xa[5], xb[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        xa[v] = qL[l * 5 + v];
+        xb[v] = qR[l * 5 + v];
+      }
+#pragma unroll
+      for (int j = 0; j < PC; ++j) {
+        const int pj = p0 + j, qj = pj / NQT, tj = pj % NQT;
+        const double wl = ftab[((int64_t)(kL * NQT + tj) * NQS + qj) * L + l];
+        const double wr = ftab[((int64_t)(kR * NQT + tj) * NQS + qj) * L + l];
+#pragma unroll
         for (int v = 0; v < 5; ++v) {
-          qm[v] += bL[l] * qL[l * 5 + v];
-          qq[v] += bR[l] * qR[l * 5 + v];
+          qmc[j][v] += wl * xa[v];
+          qqc[j][v] += wr * xb[v];
         }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < PC; ++j) {
+      const int qp = (p0 + j) / NQT, tt = (p0 + j) % NQT;
+      double qm[5], qq[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        qm[v] = qmc[j][v];
+        qq[v] = qqc[j][v];
+      }
       if (cr < 0)
         for (int v = 0; v < 5; ++v) qq[v] = qm[v];
       if (t.pos) {
@@ -465,6 +503,7 @@ __global__ void __launch_bounds__(128) k_ale_flux3(const __grid_constant__ AleTa
       for (int v = 0; v < 5; ++v)
         acc[v] += wgt * (0.5 * fsum[v] + 0.5 * (qm[v] + qq[v]) * n[3] - 0.5 * sm * (qq[v] - qm[v]));
     }
+  }
   for (int v = 0; v < 5; ++v) G[v * F + f] = acc[v];
 }
 
@@ -765,16 +804,44 @@ __global__ void __launch_bounds__(128) k_ale_flux3_32(const __grid_constant__ Al
   const float* qL = qhat + cl * L * 5;
   const float* qR = qhat + (cr >= 0 ? cr : cl) * L * 5;
   float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-  for (int qp = 0; qp < NQS; ++qp)
-    for (int tt = 0; tt < NQT; ++tt) {
-      const float* bL = ftab + ((int64_t)(kL * NQT + tt) * NQS + qp) * L;
-      const float* bR = ftab + ((int64_t)(kR * NQT + tt) * NQS + qp) * L;
-      float dm[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, dp[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-      for (int l = 0; l < L; ++l)
+  constexpr int NP = NQS * NQT, PC = point_chunk(NP, 9);
+  for (int p0 = 0; p0 < NP; p0 += PC) {
+    float dmc[PC][5], dpc[PC][5];
+#pragma unroll
+    for (int j = 0; j < PC; ++j)
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        dmc[j][v] = 0.f;
+        dpc[j][v] = 0.f;
+      }
+    for (int l = 0; l < L; ++l) {
+      float xa[5], xb[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        xa[v] = qL[l * 5 + v];
+        xb[v] = qR[l * 5 + v];
+      }
+#pragma unroll
+      for (int j = 0; j < PC; ++j) {
+        const int pj = p0 + j, qj = pj / NQT, tj = pj % NQT;
+        const float wl = ftab[((int64_t)(kL * NQT + tj) * NQS + qj) * L + l];
+        const float wr = ftab[((int64_t)(kR * NQT + tj) * NQS + qj) * L + l];
+#pragma unroll
         for (int v = 0; v < 5; ++v) {
-          dm[v] += bL[l] * qL[l * 5 + v];
-          dp[v] += bR[l] * qR[l * 5 + v];
+          dmc[j][v] += wl * xa[v];
+          dpc[j][v] += wr * xb[v];
         }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < PC; ++j) {
+      const int qp = (p0 + j) / NQT, tt = (p0 + j) % NQT;
+      float dm[5], dp[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        dm[v] = dmc[j][v];
+        dp[v] = dpc[j][v];
+      }
       if (cr < 0)
         for (int v = 0; v < 5; ++v) dp[v] = dm[v];
       float qm[5], qq[5];
@@ -831,6 +898,7 @@ __global__ void __launch_bounds__(128) k_ale_flux3_32(const __grid_constant__ Al
       for (int v = 0; v < 5; ++v)
         acc[v] += wgt * (0.5f * dfs[v] + 0.5f * (dm[v] + dp[v]) * n[3] - 0.5f * sm * (dQ[v] + dp[v] - dm[v]));
     }
+  }
   double FL[3][5], FR[3][5];
   euler_xyz64(QL, gamma64, FL);
   euler_xyz64(QR, gamma64, FR);
