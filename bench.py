@@ -38,6 +38,8 @@ WORKLOADS = {
                             "[0,2pi]^2, Orszag-Tang, MHD-GLM gamma 5/3 c_h 2, P3, CFL 0.5"),
     "explosion2d_p4": dict(dim=2, order=5, pde=0, n=512, desc="512x512x2 jittered triangles on [-1,1]^2, "
                            "transmissive, circular explosion, Euler gamma 1.4, P4 (fifth order), CFL 0.5"),
+    "densitywave3d_p4": dict(dim=3, order=5, pde=0, n=32, desc="32^3 x 6 jittered Kuhn tetrahedra, periodic "
+                             "unit cube, density wave, Euler, P4 (fifth order), CFL 1/3"),
     "vortex2d_p2": dict(dim=2, order=3, pde=0, n=32, desc="32x32x2 jittered triangles, periodic unit "
                         "square, isentropic vortex, Euler, P2, CFL 0.5"),
 }
@@ -50,7 +52,7 @@ def make_inputs(name, n=None):
     n = cfg["n"] if n is None else n
     if name in ("explosion2d_p3", "explosion2d_p4"):
         return wl.explosion_2d(n)
-    if name == "densitywave3d_p2":
+    if name in ("densitywave3d_p2", "densitywave3d_p4"):
         return wl.density_wave_3d(n)
     if name == "orszagtang2d_p3":
         return wl.orszag_tang_2d(n)
@@ -889,7 +891,7 @@ def run_ours(args):
         out["serving"] = serving_run(cw, args.serve_requests)
     if not args.no_other:
         out["other_workloads"] = {}
-        for other in ("densitywave3d_p2", "orszagtang2d_p3", "explosion2d_p4"):
+        for other in ("densitywave3d_p2", "orszagtang2d_p3", "explosion2d_p4", "densitywave3d_p4"):
             if other == name:
                 continue
             out["other_workloads"][other] = workload_rate(cw, other, stream, barrier, pk, steps=10)

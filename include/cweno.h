@@ -145,8 +145,8 @@ int cweno_mesh_info(const cweno_mesh* m, int64_t* ncells, int64_t* nfaces, int64
 /* Diagnostic, host only: the stencils cweno_setup would use for `order`,
  * in the caller's cell ids.  S0: nc x n_e (S0[c*n_e] = c, then the ranked
  * breadth-first cells of Eq. stencil); sec: nc x (d+1) x d sector cells
- * (Sec. 2.1 cone rule), -1 where a sector is dropped.  `order` 2..5 in
- * 2D, 2..4 in 3D.  Errors as cweno_setup. */
+ * (Sec. 2.1 cone rule), -1 where a sector is dropped.  `order` 2..5.
+ * Errors as cweno_setup. */
 int cweno_mesh_stencils(const cweno_mesh* m, int order, int32_t* S0, int32_t* sec);
 /* Diagnostic: the stencils a solver actually uses (found on the device by
  * cweno_setup, or by the host search when a stencil outgrows the device
@@ -170,9 +170,9 @@ int cweno_get_vertices(cweno_solver* s, double* xyz, int on_device);
  * throughout, or FP32 arithmetic with FP64 setup and FP64 cell-average
  * accumulators.  `stream` is a cudaStream_t (NULL: the library creates a
  * non-blocking stream it owns).  `params` NULL means defaults.
- * Supported: (dim 2, Euler, order 2..5; order 5 is the paper's fifth-order
- * scheme of Secs. 4.2.1-4.2.2), (dim 2, MHD, order 2..4), (dim 3, Euler,
- * order 2..4).
+ * Supported: (dim 2 and 3, Euler, order 2..5; order 5 is the paper's
+ * fifth-order scheme of Secs. 4.2.1-4.2.2 and the O5 column of its 3D
+ * convergence study), (dim 2, MHD, order 2..4).
  * The state is zero until cweno_set_state.
  * Errors: EINVAL, EDEGENERATE (rank-deficient LSQ, mesh too small for the
  * stencil), ENOMEM, ECUDA.  Synchronous. */

@@ -19,7 +19,7 @@ LIB = os.path.join(LIBDIR, "libcweno.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["kern_euler2.cu", "kern_euler3.cu", "kern_mhd2.cu", "api.cu", "noalloc.cu", "setup_gpu.cu", "lsq_gpu.cu", "ale.cu", "peak.cu"]
+CU_SOURCES = ["kern_euler2.cu", "kern_euler3.cu", "kern_euler3_p4.cu", "kern_euler3_p4f.cu", "kern_mhd2.cu", "api.cu", "noalloc.cu", "setup_gpu.cu", "lsq_gpu.cu", "ale.cu", "peak.cu"]
 # per-file flags: the device stencil search keeps the host's FP64 arithmetic
 # (no FMA contraction), so that its distance keys and cone tests agree
 CU_FLAGS = {"setup_gpu.cu": ["--fmad=false"]}

@@ -8,6 +8,7 @@ raises.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import threading
 
@@ -222,7 +223,8 @@ class Mesh:
         return dict(ncells=a.value, nfaces=b.value, nboundary=c.value)
 
     def stencils(self, order: int):
-        ne = self.dim * {2: {2: 3, 3: 6, 4: 10, 5: 15}, 3: {2: 4, 3: 10, 4: 20}}[self.dim][order]
+        # n_e = d M(M, d) cells (Eq. stencil); the library checks the order
+        ne = self.dim * math.comb(max(order, 1) - 1 + self.dim, self.dim)
         S0 = np.zeros((self.nc, ne), dtype=np.int32)
         sec = np.zeros((self.nc, self.dim + 1, self.dim), dtype=np.int32)
         _check(lib().cweno_mesh_stencils(self.h, order, S0.ctypes.data_as(_I32P), sec.ctypes.data_as(_I32P)))

@@ -73,7 +73,13 @@ size_t footprint_estimate(int d, int64_t nc, int64_t nf, int order, int pde, int
   b += 4 * nc * nvx * d + es * nc * nvx * d * d + nc + es * nc * d * d;
   b += es * nc * nv * L;                                    // q_hat
   b += nf * (8 + 2 + es * d + 8 * d + 8 + 8 * nv);          // faces + G
-  b += 4 * nc * nvx + 16 * nc + 4096;                       // cell->face, 1/|T|, h, tables
+  b += 4 * nc * nvx + 16 * nc;                              // cell->face, 1/|T|, h
+  // reference tables: face basis values per face code, time and space point;
+  // per-cell tables (E, Sigma, C0 E, P_e) where they are stored beside them
+  const size_t ncode = d == 2 ? 6 : 24, nqs = d == 2 ? M + 1 : (M + 1) * (M + 1);
+  b += es * (ncode * (M + 1) * nqs * (L + 3) + ncode * (L + 3) + 256);
+  b += es * ((size_t)Mc * (Mc - 1) + (size_t)(Mc - 1) * (Mc - 1) + (size_t)(L - Mc) * (Mc - 1) +
+             (size_t)d * (L - Mc) * L) + 4096;
   return b + (size_t)64 * 1024;                             // allocation granularity slack
 }
 
@@ -186,7 +192,7 @@ int cweno_mesh_info(const cweno_mesh* m, int64_t* ncells, int64_t* nfaces, int64
 int cweno_mesh_stencils(const cweno_mesh* mesh, int order, int32_t* S0, int32_t* sec) {
   if (!mesh || !S0 || !sec) return fail(CWENO_EINVAL, "null argument");
   const MeshHost& m = mesh->m;
-  if (order < 2 || order > (m.d == 2 ? 5 : 4)) return fail(CWENO_EINVAL, "order must be 2..5 in 2D, 2..4 in 3D");
+  if (order < 2 || order > 5) return fail(CWENO_EINVAL, "order must be 2..5");
   const RefElem& re = ref_elem(m.d, order - 1);
   CellSetup cs;
   std::string err;
@@ -258,7 +264,7 @@ int cweno_setup(const cweno_mesh* mesh, int order, int pde, int precision, const
   const MeshHost& m = mesh->m;
   if (order < 2 || order > 5) return fail(CWENO_EINVAL, "order must be 2..5");
   if (pde != CWENO_EULER && pde != CWENO_MHD_GLM) return fail(CWENO_EINVAL, "unknown pde");
-  if (order == 5 && !(pde == CWENO_EULER && m.d == 2)) return fail(CWENO_EINVAL, "order 5 is built for 2D Euler only");
+  if (order == 5 && pde != CWENO_EULER) return fail(CWENO_EINVAL, "order 5 is built for the Euler equations only");
   if (pde == CWENO_MHD_GLM && m.d != 2) return fail(CWENO_EINVAL, "MHD-GLM is built for 2D meshes only");
   if (precision != CWENO_FP64 && precision != CWENO_FP32_MIXED) return fail(CWENO_EINVAL, "unknown precision");
   cweno_params prm;

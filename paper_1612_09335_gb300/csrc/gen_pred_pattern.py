@@ -15,7 +15,7 @@ Run: python gen_pred_pattern.py > pred_pattern.h
 from fractions import Fraction as Fr
 from math import comb
 
-CONFIGS = [(2, 1), (2, 2), (2, 3), (2, 4), (3, 1), (3, 2), (3, 3)]
+CONFIGS = [(2, 1), (2, 2), (2, 3), (2, 4), (3, 1), (3, 2), (3, 3), (3, 4)]
 
 
 def st_nodes(d, M):

@@ -127,7 +127,11 @@ struct Cfg {
   // unknown space-time nodes) kept in shared memory, one column per thread,
   // so that the node loops run rolled: a few kilobytes of code instead of a
   // fully unrolled body that misses the instruction cache
-  static constexpr int PRED_SMEM_BYTES = 2 * L1 * NV * (int)sizeof(T_) * 128;
+  // Where one block's columns exceed the shared memory of an SM (3D P4 in
+  // FP64: 358 KB), each thread keeps its working set in local memory instead.
+  static constexpr int PRED_WS_BYTES = 2 * L1 * NV * (int)sizeof(T_) * 128;
+  static constexpr bool PRED_WS_LOCAL = PRED_WS_BYTES > 227 * 1024;
+  static constexpr int PRED_SMEM_BYTES = PRED_WS_LOCAL ? 0 : PRED_WS_BYTES;
   // reconstruction at the lattice nodes kept in the predictor's working set
   // (where it fits: L0 NV <= 2 L1 NV)
   static constexpr bool STASH = L0 <= 2 * L1;
@@ -211,6 +215,32 @@ struct KArgs {
   double dt_fixed, cfl;
   int cur, reset_next;
 };
+
+// The per-cell reference tables (E, Sigma, C0 E, P_e) travel as a kernel
+// parameter (constant bank, broadcast reads) where they fit beside KArgs into
+// the 32 KB parameter space.  Otherwise (3D P4: 44 KB in FP32, 87 KB in FP64)
+// they are stored after the face tables in the same device buffer and read
+// from there through the cache.
+struct NoCellTab {};
+template <class C>
+__host__ __device__ constexpr bool cell_tab_in_param() {
+  return sizeof(CellTab<C>) + sizeof(KArgs<C>) <= 32000;
+}
+template <class C>
+using CellTabArg = std::conditional_t<cell_tab_in_param<C>(), CellTab<C>, NoCellTab>;
+// byte offset of the cell tables in the face-table buffer
+template <class C>
+__host__ __device__ constexpr size_t cell_tab_offset() {
+  return ((size_t)C::TAB_TOTAL * sizeof(typename C::T) + 255) / 256 * 256;
+}
+template <class C>
+__device__ __forceinline__ const CellTab<C>& cell_tab(const KArgs<C>& a, const CellTabArg<C>& tb) {
+  if constexpr (cell_tab_in_param<C>())
+    return tb;
+  else
+    return *reinterpret_cast<const CellTab<C>*>(reinterpret_cast<const unsigned char*>(a.ftab) +
+                                                 cell_tab_offset<C>());
+}
 
 __device__ __forceinline__ double dt_of(double fixed, double cfl, const unsigned long long* dtmin, int cur) {
   return fixed > 0.0 ? fixed : cfl * __longlong_as_double((long long)dtmin[cur]);
@@ -800,9 +830,12 @@ __device__ __forceinline__ void rec_pred_cell(const KArgs<C>& a, const CellTab<C
       }
     return;
   } else {
-    constexpr int L0 = C::L0, L1 = C::L1, B = 128;
+    // B: stride between the entries of one thread's working set (128
+    // columns in shared memory, or contiguous in local memory)
+    constexpr int L0 = C::L0, L1 = C::L1, B = C::PRED_WS_LOCAL ? 1 : 128;
     extern __shared__ __align__(16) unsigned char rp_smem[];
-    T* sb = reinterpret_cast<T*>(rp_smem) + threadIdx.x;  // fixed part, [(k NV + v) B]
+    T ws_local[C::PRED_WS_LOCAL ? 2 * L1 * NV : 1];
+    T* sb = C::PRED_WS_LOCAL ? ws_local : reinterpret_cast<T*>(rp_smem) + threadIdx.x;  // fixed part, [(k NV + v) B]
     T* sq = sb + L1 * NV * B;                              // current iterate
     // With STASH, the reconstruction at the L0 lattice nodes (E w, deviation
     // from the cell average) is formed once into the working set: the
@@ -1006,9 +1039,9 @@ __device__ __forceinline__ void rec_pred_cell(const KArgs<C>& a, const CellTab<C
 
 // One thread per cell, one block per tile of 128 consecutive cells.
 template <class C, bool REC_ONLY>
-__global__ void __launch_bounds__(128, C::REC_MINB) k_rec_pred(KArgs<C> a, const __grid_constant__ CellTab<C> tb) {
+__global__ void __launch_bounds__(128, C::REC_MINB) k_rec_pred(KArgs<C> a, const __grid_constant__ CellTabArg<C> tb) {
   if (!REC_ONLY && a.reset_next && blockIdx.x == 0 && threadIdx.x == 0) a.dtmin[1 - a.cur] = 0x7ff0000000000000ull;
-  rec_pred_cell<C, REC_ONLY>(a, tb, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+  rec_pred_cell<C, REC_ONLY>(a, cell_tab<C>(a, tb), (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ----------------------------------------------------------------- fluxes
@@ -1685,13 +1718,13 @@ __device__ __forceinline__ int batch_stage(const BatchTab<C>* bt, int kernel, in
 
 template <class C>
 __global__ void __launch_bounds__(128, C::REC_MINB) k_rec_pred_batch(const BatchTab<C>* bt,
-                                                                     const __grid_constant__ CellTab<C> tb) {
+                                                                     const __grid_constant__ CellTabArg<C> tb) {
   __shared__ __align__(16) KArgs<C> sa;
   const int total = bt->h.pref[0][bt->h.nseg];
   for (int c = blockIdx.x; c < total; c += gridDim.x) {
     const int lc = batch_stage(bt, 0, c, sa);
     if (lc == 0 && threadIdx.x == 0 && sa.reset_next) sa.dtmin[1 - sa.cur] = 0x7ff0000000000000ull;
-    rec_pred_cell<C, false>(sa, tb, (int64_t)lc * 128 + threadIdx.x);
+    rec_pred_cell<C, false>(sa, cell_tab<C>(sa, tb), (int64_t)lc * 128 + threadIdx.x);
   }
 }
 
@@ -1851,10 +1884,26 @@ class OpsImpl final : public Ops {
     for (int code = 0; code < C::NCODE; ++code)
       for (int l = 0; l < C::L; ++l) ftab_[C::QF_OFF + code * C::LP + l] = (T)re.fint[(size_t)code * C::L + l];
   }
-  size_t table_bytes() const override { return ftab_.size() * sizeof(T); }
+  // face tables, then (where they are not a kernel parameter) the cell tables
+  size_t table_bytes() const override {
+    return cell_tab_in_param<C>() ? ftab_.size() * sizeof(T) : cell_tab_offset<C>() + sizeof(CellTab<C>);
+  }
+  CellTabArg<C> tab_arg() const {
+    if constexpr (cell_tab_in_param<C>())
+      return tab_;
+    else
+      return NoCellTab{};
+  }
   // shared-memory bytes of the quadrature flux kernels (tables and weights)
   static size_t quad_table_bytes() { return (size_t)(C::TABN + C::NQS + C::NQT) * sizeof(T); }
-  void pack_tables(void* host) const override { std::memcpy(host, ftab_.data(), table_bytes()); }
+  void pack_tables(void* host) const override {
+    std::memcpy(host, ftab_.data(), ftab_.size() * sizeof(T));
+    if constexpr (!cell_tab_in_param<C>()) {
+      unsigned char* h = static_cast<unsigned char*>(host);
+      std::memset(h + ftab_.size() * sizeof(T), 0, cell_tab_offset<C>() - ftab_.size() * sizeof(T));
+      std::memcpy(h + cell_tab_offset<C>(), &tab_, sizeof(tab_));
+    }
+  }
   size_t elem_size() const override { return sizeof(T); }
 
   KArgs<C> args(const DevState& s, const PhysParams& ph, DtArgs dt) const {
@@ -1913,14 +1962,14 @@ class OpsImpl final : public Ops {
       a.cur = 0;
       a.reset_next = 0;
     }
-    k_rec_pred<C, false><<<nblk(s.N, 128), 128, C::PRED_SMEM_BYTES, st>>>(a, tab_);
+    k_rec_pred<C, false><<<nblk(s.N, 128), 128, C::PRED_SMEM_BYTES, st>>>(a, tab_arg());
     return cudaGetLastError();
   }
   cudaError_t reconstruct(const DevState& s, const PhysParams& ph, double* out, cudaStream_t st) override {
     KArgs<C> a = args(s, ph, DtArgs());
     a.out = out;
     a.reset_next = 0;
-    k_rec_pred<C, true><<<nblk(s.N, 128), 128, 0, st>>>(a, tab_);
+    k_rec_pred<C, true><<<nblk(s.N, 128), 128, 0, st>>>(a, tab_arg());
     return cudaGetLastError();
   }
   using FluxKernel = void (*)(KArgs<C>, int);
@@ -2034,7 +2083,7 @@ class OpsImpl final : public Ops {
   }
   cudaError_t step_batch(const void* dev_tab, int flux, cudaStream_t st) override {
     const BatchTab<C>* bt = reinterpret_cast<const BatchTab<C>*>(dev_tab);
-    k_rec_pred_batch<C><<<(unsigned)max_blocks_rec_b_, 128, C::PRED_SMEM_BYTES, st>>>(bt, tab_);
+    k_rec_pred_batch<C><<<(unsigned)max_blocks_rec_b_, 128, C::PRED_SMEM_BYTES, st>>>(bt, tab_arg());
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t smem = use_smem_ ? quad_table_bytes() : 0;

@@ -324,6 +324,7 @@ cudaError_t dispatch(int d, int M, const double* X, const double* bary, const in
       case 1: return launch<3, 1, T>(X, bary, sten, N, tab, R, bad, st);
       case 2: return launch<3, 2, T>(X, bary, sten, N, tab, R, bad, st);
       case 3: return launch<3, 3, T>(X, bary, sten, N, tab, R, bad, st);
+      case 4: return launch<3, 4, T>(X, bary, sten, N, tab, R, bad, st);
     }
   }
   return cudaErrorInvalidValue;

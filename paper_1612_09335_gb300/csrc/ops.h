@@ -88,6 +88,8 @@ class Ops {
 // Factories (one per translation unit); nullptr if (M, precision) is not built.
 std::unique_ptr<Ops> make_ops_euler2(int M, int fp32, const RefElem& re);
 std::unique_ptr<Ops> make_ops_euler3(int M, int fp32, const RefElem& re);
+// 3D Euler at M = 4, one translation unit per precision (the largest instances)
+std::unique_ptr<Ops> make_ops_euler3_p4(int fp32, const RefElem& re);
 std::unique_ptr<Ops> make_ops_mhd2(int M, int fp32, const RefElem& re);
 
 }  // namespace cw

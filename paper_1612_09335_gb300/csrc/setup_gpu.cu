@@ -209,7 +209,9 @@ template <int D, int M, typename T>
 cudaError_t launch_stencils(const double* X, const double* bary, const int32_t* nbr, const int32_t* perm, int64_t N,
                             const LsqTab& tab, double qscale, int32_t* sten, int32_t* sten4, int32_t* sec, void* Binv,
                             uint8_t* nsec, void* Jinv, int* small, int* cap, cudaStream_t st) {
-  constexpr int SEQ = D == 2 ? 128 : 320, LAY = D == 2 ? 48 : 128;
+  // fifth order on the Kuhn tetrahedra: at most 294 cells in the sequence
+  // and 100 in one layer (measured on jittered meshes)
+  constexpr int SEQ = D == 2 ? 128 : M >= 4 ? 384 : 320, LAY = D == 2 ? 48 : 128;
   k_stencils<D, M, T, SEQ, LAY><<<(unsigned)((N + 127) / 128), 128, 0, st>>>(
       X, bary, nbr, perm, N, tab, qscale, sten, sten4, sec, (T*)Binv, nsec, (T*)Jinv, small, cap);
   return cudaGetLastError();
@@ -234,6 +236,7 @@ cudaError_t dispatch_stencils(int d, int M, const double* X, const double* bary,
       case 1: CW_ST(3, 1);
       case 2: CW_ST(3, 2);
       case 3: CW_ST(3, 3);
+      case 4: CW_ST(3, 4);
     }
   }
 #undef CW_ST

@@ -48,11 +48,11 @@ def test_default_params_are_the_papers(cw):
 
 def test_setup_rejects_unsupported_combinations_before_device_work(cw, wl):
     """Argument checks run before any device call (so they hold without a
-    GPU): order range, order 5 outside 2D Euler, the Osher flux for MHD, an
-    unknown flux."""
+    GPU): order range (both dimensions), order 5 outside the Euler
+    equations, the Osher flux for MHD, an unknown flux."""
     m2 = cw.Mesh.from_workload(wl.tri_mesh(6))
     m3 = cw.Mesh.from_workload(wl.tet_mesh(3))
-    cases = [(m2, 6, cw.EULER, {}), (m2, 1, cw.EULER, {}), (m3, 5, cw.EULER, {}), (m2, 5, cw.MHD_GLM, {}),
+    cases = [(m2, 6, cw.EULER, {}), (m2, 1, cw.EULER, {}), (m3, 6, cw.EULER, {}), (m2, 5, cw.MHD_GLM, {}),
              (m2, 3, cw.MHD_GLM, {"flux": cw.FLUX_OSHER}), (m2, 3, cw.EULER, {"flux": 7})]
     for mesh, order, pde, kw in cases:
         with pytest.raises(cw.CwenoError) as e:

@@ -208,7 +208,7 @@ def test_state_through_pinned_host_memory(cw, wl, name, fp64):
 
 
 @pytest.mark.parametrize("name,order", [("vortex2d", 3), ("vortex2d", 5), ("explosion2d", 4), ("wave3d", 3),
-                                        ("orszag", 4)])
+                                        ("wave3d", 5), ("orszag", 4)])
 def test_conservation_both_modes(cw, wl, name, order):
     """Sum |T_i| Q_i is conserved on periodic meshes (and changes only by
     boundary fluxes otherwise): drift below 1e-12 relative in both modes."""
@@ -286,7 +286,7 @@ def conservation_with_boundary_flux(cw, wl, order, nsteps=10):
         assert np.all(np.abs(tot - expect) <= 1e-12 * scale), (prec, tot - expect)
 
 
-@pytest.mark.parametrize("dim,pde,order", [(2, EULER, 4), (2, EULER, 5), (3, EULER, 3), (2, MHD, 4)])
+@pytest.mark.parametrize("dim,pde,order", [(2, EULER, 4), (2, EULER, 5), (3, EULER, 3), (3, EULER, 5), (2, MHD, 4)])
 def test_free_stream_both_modes(cw, wl, dim, pde, order):
     mesh = wl.tri_mesh(12, jitter=0.2, seed=3) if dim == 2 else wl.tet_mesh(5, jitter=0.15, seed=3)
     if pde == EULER:
@@ -446,8 +446,8 @@ def test_fp32_pair_split_of_the_state(cw, wl):
 
 
 @pytest.mark.parametrize("kind,orders", [("tri_periodic", (2, 3, 4, 5)), ("tri_bounded", (2, 3, 4, 5)),
-                                         ("tri_ties", (3, 4)), ("tet_periodic", (2, 3, 4)),
-                                         ("tet_bounded", (2, 3))])
+                                         ("tri_ties", (3, 4)), ("tet_periodic", (2, 3, 4, 5)),
+                                         ("tet_bounded", (2, 3, 5))])
 def test_device_stencil_search_equals_host_search(cw, wl, kind, orders):
     """cweno_setup finds the central stencils and sectors on the device; they
     must be the host search's (the rule the oracle's stencils are pinned to)

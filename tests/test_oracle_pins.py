@@ -168,7 +168,7 @@ def test_geometry_3d_insphere(orc, wl):
 
 
 # ---------------------------------------------------------------- stencils
-@pytest.mark.parametrize("dim,order", [(2, 2), (2, 3), (2, 4), (2, 5), (3, 3)])
+@pytest.mark.parametrize("dim,order", [(2, 2), (2, 3), (2, 4), (2, 5), (3, 3), (3, 5)])
 def test_central_stencil_is_ranked_bfs(orc, wl, dim, order):
     mesh = wl.tri_mesh(10, jitter=0.2, seed=11) if dim == 2 else wl.tet_mesh(5, jitter=0.15, seed=11)
     o = orc.Oracle(mesh, order, EULER)
@@ -190,7 +190,7 @@ def test_central_stencil_is_ranked_bfs(orc, wl, dim, order):
         assert set(last[:need]) == set(S0.tolist()) - set(inner)
 
 
-@pytest.mark.parametrize("dim,order", [(2, 3), (2, 4), (2, 5), (3, 3)])
+@pytest.mark.parametrize("dim,order", [(2, 3), (2, 4), (2, 5), (3, 3), (3, 5)])
 def test_sector_cells_lie_in_open_cone(orc, wl, dim, order):
     mesh = wl.tri_mesh(10, jitter=0.2, seed=13) if dim == 2 else wl.tet_mesh(5, jitter=0.15, seed=13)
     o = orc.Oracle(mesh, order, EULER)
@@ -213,7 +213,7 @@ def test_sector_cells_lie_in_open_cone(orc, wl, dim, order):
 
 
 # ------------------------------------------------------- reconstruction pins
-@pytest.mark.parametrize("dim,order", [(2, 2), (2, 3), (2, 4), (2, 5), (3, 2), (3, 3)])
+@pytest.mark.parametrize("dim,order", [(2, 2), (2, 3), (2, 4), (2, 5), (3, 2), (3, 3), (3, 5)])
 def test_popt_reproduces_polynomials(orc, wl, dim, order):
     """p1: P_opt is exact for data that are averages of a degree-M polynomial."""
     M = order - 1
@@ -227,7 +227,7 @@ def test_popt_reproduces_polynomials(orc, wl, dim, order):
     assert np.abs(out["popt"] - ref).max() < 1e-11 * scale
 
 
-@pytest.mark.parametrize("dim,order", [(2, 3), (2, 4), (2, 5), (3, 3)])
+@pytest.mark.parametrize("dim,order", [(2, 3), (2, 4), (2, 5), (3, 3), (3, 5)])
 def test_linear_weights_mode_reproduces_polynomials(orc, wl, dim, order):
     """p1: with omega := lambda the CWENO polynomial equals P_opt (Eq. CWENO:P0)."""
     M = order - 1
@@ -242,7 +242,7 @@ def test_linear_weights_mode_reproduces_polynomials(orc, wl, dim, order):
     assert np.abs(w - ref).max() < 1e-11 * np.abs(ref).max()
 
 
-@pytest.mark.parametrize("dim,order", [(2, 2), (2, 4), (2, 5), (3, 3)])
+@pytest.mark.parametrize("dim,order", [(2, 2), (2, 4), (2, 5), (3, 3), (3, 5)])
 def test_nonlinear_weights_exact_for_linear_data(orc, wl, dim, order):
     """p1: for degree-1 data every candidate equals P_opt, so w is exact."""
     M = order - 1
@@ -266,7 +266,7 @@ def _interp_average(dim, M, vals, wl):
     return gw @ (Vg @ coef)
 
 
-@pytest.mark.parametrize("dim,order", [(2, 2), (2, 3), (2, 4), (2, 5), (3, 3)])
+@pytest.mark.parametrize("dim,order", [(2, 2), (2, 3), (2, 4), (2, 5), (3, 3), (3, 5)])
 def test_reconstruction_preserves_cell_average(orc, wl, dim, order):
     """p2: avg_{T_i} w_i = Q_i for discontinuous data (Eqs. CWENO:Popt, CWENO:Ps)."""
     M = order - 1
@@ -303,7 +303,7 @@ def test_weights_positive_and_normalised(orc, wl):
     assert kept.any()
 
 
-@pytest.mark.parametrize("dim,M", [(2, 1), (2, 2), (2, 3), (2, 4), (3, 2)])
+@pytest.mark.parametrize("dim,M", [(2, 1), (2, 2), (2, 3), (2, 4), (3, 2), (3, 4)])
 def test_oscillation_indicator_matches_sympy(orc, wl, dim, M):
     """p4: sigma = sum_{1<=|a|<=M} int_{T_E} (d^a p)^2, integrated exactly by sympy."""
     sp = pytest.importorskip("sympy")
@@ -461,7 +461,7 @@ def test_mhd_glm_flux_jacobian_eigenvalues(orc):
 
 # ----------------------------------------------------------------- predictor
 @pytest.mark.parametrize("dim,order,pde", [(2, 2, EULER), (2, 3, EULER), (2, 4, EULER), (2, 5, EULER),
-                                           (3, 2, EULER), (3, 3, EULER), (2, 4, MHD)])
+                                           (3, 2, EULER), (3, 3, EULER), (3, 5, EULER), (2, 4, MHD)])
 def test_predictor_exact_for_advected_polynomial(orc, wl, dim, order, pde):
     """p5: constant velocity/pressure (and B) with polynomial density of degree M
     reduce the system to linear advection; M+1 Picard iterations of Eq. (CGfinal)
@@ -498,14 +498,15 @@ def test_predictor_exact_for_advected_polynomial(orc, wl, dim, order, pde):
 
 @pytest.mark.parametrize("dim,order,pde,tol", [(2, 2, EULER, 1e-12), (2, 3, EULER, 1e-12), (2, 4, EULER, 1e-11),
                                                (3, 2, EULER, 1e-12), (3, 3, EULER, 1e-10), (2, 4, MHD, 1e-11),
-                                               (2, 5, EULER, 1e-7)])
+                                               (2, 5, EULER, 1e-7), (3, 5, EULER, 1e-8)])
 def test_predictor_closed_form_equals_galerkin_solve(orc, wl, dim, order, pde, tol):
     """p5b: the predictor's closed form (w - dt int_0^tau H_h at the unknown
     nodes) equals the Galerkin solve of Eq. (CGfinal) as written, for a
     nonlinear state (Euler / MHD fluxes, random smooth data) over all M+1
     Picard iterations.  The difference is the rounding of the Galerkin solve,
     which scales with the condition number of K_tau^1 (about 5e1, 1.5e4, 1.4e6
-    for 2D M = 2, 3, 4), hence the tolerances."""
+    for 2D M = 2, 3, 4; at 3D M = 4 the measured difference is 3e-9), hence
+    the tolerances."""
     M = order - 1
     mesh = wl.tri_mesh(4, periodic=False, jitter=0.2, seed=2) if dim == 2 else \
         wl.tet_mesh(2, periodic=False, jitter=0.1, seed=2)
@@ -543,7 +544,7 @@ def test_patch_test_linear_data(orc, wl):
     assert np.abs(Q1 - ref).max() < 1e-12 * np.abs(ref).max()
 
 
-@pytest.mark.parametrize("dim,order,pde", [(2, 3, EULER), (3, 3, EULER), (2, 4, MHD)])
+@pytest.mark.parametrize("dim,order,pde", [(2, 3, EULER), (3, 3, EULER), (3, 5, EULER), (2, 4, MHD)])
 def test_constant_state_preserved(orc, wl, dim, order, pde):
     """p7: free stream is preserved (Eulerian shadow of the GCL, Eq. gcl)."""
     mesh = wl.tri_mesh(8, jitter=0.2, seed=1) if dim == 2 else wl.tet_mesh(4, jitter=0.15, seed=1)
