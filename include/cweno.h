@@ -268,9 +268,9 @@ int cweno_profile_read_stages(cweno_solver* s, double* ms, int64_t* launches, in
 int cweno_measure_fma_peak(int fp64, double* tflops, double* ms);
 
 /* CFL time-step bound without any allocation.  The paper has no counterpart:
- * this is for callers that cannot call cudaMalloc (work inside a captured
- * CUDA graph, inside another framework's memory pool, or in a process whose
- * device memory is reserved up front).  It computes
+ * this is for callers that cannot call cudaMalloc (work inside another
+ * framework's memory pool, or in a process whose device memory is reserved
+ * up front).  It computes
  * cfl * min_i h_i / |lambda_max(Q_i)| like cweno_stable_dt, but for a state in
  * the caller's own buffers:
  *   Q      device, ncells x nvars FP64, AoS by cell (as cweno_set_state)
@@ -284,13 +284,12 @@ int cweno_measure_fma_peak(int fp64, double* tflops, double* ms);
  * (512 KiB), held by every GPU that loads the library until the process
  * exits, so ncells must not exceed CWENO_NOALLOC_MAX_CELLS (EINVAL
  * otherwise).  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  The address is kept for the life of the
- * process: after cudaDeviceReset (or any other teardown of the device's
- * primary context) the array lives at a new address, so do not call this
- * entry point again in that process.  Calls that overlap on the GPU share the
- * scratch and race; serialise them (one stream, or events).  Nothing is
- * allocated and nothing is freed. */
+ * address (cudaGetSymbolAddress) with that device current.  The address is
+ * kept for the life of the process: after cudaDeviceReset (or any other
+ * teardown of the device's primary context) the array lives at a new
+ * address, so do not call this entry point again in that process.  Calls
+ * that overlap on the GPU share the scratch and race; serialise them (one
+ * stream, or events).  Nothing is allocated and nothing is freed. */
 #define CWENO_NOALLOC_MAX_CELLS (65536 * 256)
 int cweno_stable_dt_noalloc(int dim, int pde, int64_t ncells, const double* Q, const double* h, double gamma,
                             double c_h, double cfl, double* dt, void* stream);

@@ -1,9 +1,8 @@
 // Time-step bound for callers that cannot allocate device memory.
 //
 // Some callers own a CUDA context in which they may not call cudaMalloc:
-// code running inside a captured CUDA graph, inside another framework's
-// memory pool or allocator, or in a process whose device memory is fully
-// reserved up front.  cweno_stable_dt_noalloc gives them the CFL bound of a
+// code running inside another framework's memory pool or allocator, or in a
+// process whose device memory is fully reserved up front.  cweno_stable_dt_noalloc gives them the CFL bound of a
 // state that lives in their own buffers without allocating anything: the
 // per-block partial minima live in a file-scope device array that every GPU
 // loading the library holds until the process exits.

@@ -1,6 +1,6 @@
 """cweno_stable_dt_noalloc: the CFL bound for callers that cannot allocate
-device memory (inside graph capture, a foreign memory pool, or with all
-device memory reserved up front).  Its scratch is a static device array, so
+device memory (inside a foreign memory pool, or with all device memory
+reserved up front).  Its scratch is a static device array, so
 the test checks, through the C ABI, that two calls in a row (different
 states, different sizes) each give the bound the allocating entry point
 cweno_stable_dt gives for the same state, to 1e-12 relative."""
