@@ -281,6 +281,44 @@ def test_reconstruction_preserves_cell_average(orc, wl, dim, order):
     assert np.abs(avg - Q).max() < 1e-12 * np.abs(Q).max()
 
 
+@pytest.mark.parametrize("dim,order", [(2, 3), (3, 3), (3, 5)])
+def test_sectorial_indicators_from_barycentre_interpolation(orc, wl, dim, order):
+    """Eqs. (CWENO:Ps) and (weights2) for the sectorial polynomials, rebuilt
+    independently: the degree-1 polynomial through the averages of the cell
+    and its d sector cells (a linear polynomial's average is its value at the
+    barycentre; minimum-image barycentres on the periodic mesh) has gradient
+    g, and its indicator is the integral of |grad_xi P|^2 over T_E, i.e.
+    |T_E| |J^T g|^2 with J = dx/dxi.  Must equal the oracle's sigma_s for
+    every kept sector and variable (smooth data of O(1) amplitude)."""
+    if dim == 2:
+        mesh, Q = wl.vortex_2d(12)
+    else:
+        mesh, Q = wl.density_wave_3d(5)
+    o = orc.Oracle(mesh, order, EULER)
+    sig = o.reconstruct(Q, want_weights=True)["sigma"]
+    X = mesh.cell_vertices()
+    area = 0.5 if dim == 2 else 1.0 / 6.0
+    checked = 0
+    for c in range(0, mesh.nc, max(1, mesh.nc // 40)):
+        _, sec = o.stencil(c)
+        J = (X[c, 1:] - X[c, 0]).T
+        for s in range(dim + 1):
+            if sec[s, 0] < 0:
+                continue
+            cells = [c] + [int(j) for j in sec[s]]
+            B = np.array([min_image_bary(mesh, c, j)[1] for j in cells])
+            A = np.hstack([np.ones((dim + 1, 1)), B - B[0]])
+            g = np.linalg.solve(A, Q[cells])[1:]          # dim x nvars
+            ref = area * np.sum((J.T @ g) ** 2, axis=0)
+            # rounding of the averages (~1e-16 |Q|) moves |J^T g| by as much,
+            # so sigma by ~2 sqrt(|T_E| sigma) 1e-16 |Q| (far-field cells of
+            # the vortex hold sigma ~ 1e-29)
+            tol = 1e-10 * ref + 1e-14 * np.sqrt(area * ref) * np.abs(Q[cells]).max(axis=0)
+            assert np.all(np.abs(sig[c, 1 + s] - ref) <= tol), (c, s, sig[c, 1 + s], ref)
+            checked += 1
+    assert checked >= 40
+
+
 def test_weights_positive_and_normalised(orc, wl):
     """p3: omega_s > 0, sum = 1; sigma = 0 (constant data) gives omega = lambda."""
     mesh = wl.tri_mesh(8, lo=(-1, -1), hi=(1, 1), periodic=False, jitter=0.2, seed=4)
